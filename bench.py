@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the multigrid pressure-Poisson path inside the projection
+step (Algorithm 1), GB300.
+
+Headline workload (default ``--config ns2d``): incompressible flow past a
+square block, 2048 x 1024 cells (h = 1), a 64 x 64 solid block centred at
+(512, 512), inflow u = 1, nu = 0.64 (Re = 100 on the block side),
+dt = 0.1, initial velocity = inflow + 1% seeded Gaussian noise (seed 0).  One
+bench step = one full projection step: two-pass momentum, divergence RHS,
+the pressure-correction solve to relative residual 1e-6 (float64 iterate)
+and the velocity/pressure correction.  Metric: solved pressure unknowns
+(fluid cells) per second.
+
+Other configs (``--config``): ``poisson2d`` (256^2, 8 blobs, zero
+Dirichlet), ``poisson3d`` (256^3, 8 blobs; ``--prec fp32|fp16|bf16``).
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (each step one oracle step of a bounded
+sample of the workload).
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2402_17913_gb300 import inputs as I  # noqa: E402
+
+METRIC = "solved unknowns/sec to 1e-6 rel residual"
+UNIT = "unknowns/s"
+TOL = 1e-6
+
+# Algorithmic bytes per fine-grid cell of one launch of each kernel class
+# (float32 storage, the method's own minimum: each array read or written
+# once per launch; masked levels read one cell byte more).  Only classes
+# that dominate a step are listed.
+ALGO_BYTES_PER_CELL = {
+    "down_fine": 4 + 4 + 1,          # read b (= CG residual); write x, coarse b (1/4)
+    "up_fine": 4 + 4 + 1 + 4,        # read b, x, coarse e (1/4); write z
+    "p_update": 4 + 4 + 4 + 4,       # read z, p_old; write p, Ap
+    "xr_update": 4 + 4 + 8 + 8,      # read p, Ap; read+write d, r
+    "outer": 4 + 8 + 4 + 8 + 4,      # read b, x64, d; write x64, r'
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="ns2d", choices=["ns2d", "poisson2d", "poisson3d"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run warm-up and timed steps only (for launch-list captures)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workloads
+class NS2D:
+    name = "ns2d_block_2048x1024"
+    dim = 2
+
+    def __init__(self, scale=1):
+        self.cells = (2048 // scale, 1024 // scale)
+        self.block = 64 // scale
+        self.centre = (512 // scale, 512 // scale)
+        self.nu, self.dt, self.uin = 0.64 / scale, 0.1, 1.0
+        self.solid = I.block_mask(self.cells, self.centre, self.block)
+        self.units = int((~self.solid).sum())
+
+    def config(self):
+        return {"workload": "2D projection step, flow past a square block", "cells": list(self.cells),
+                "block": self.block, "nu": self.nu, "dt": self.dt, "u_inflow": self.uin,
+                "solve_rel_tol": TOL, "unknowns_per_step": self.units,
+                "l2": "256 MiB buffer written between timed steps"}
+
+
+class Poisson:
+    def __init__(self, shape, prec):
+        self.shape = shape
+        self.dim = len(shape)
+        self.prec = prec
+        self.units = int(np.prod(shape))
+        self.name = "poisson%dd_%s_%s" % (self.dim, "x".join(map(str, shape)), prec)
+
+    def config(self):
+        return {"workload": "%dD pressure Poisson, 8 Gaussian blobs, zero Dirichlet" % self.dim,
+                "shape": list(reversed(self.shape)), "solve_rel_tol": TOL, "inner_precision": self.prec,
+                "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
+
+
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+
+# ---------------------------------------------------------------------------
+def clocks_sampler():
+    path = tempfile.mktemp(suffix=".csv")
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f, path
+    except Exception:
+        return None, None, path
+
+
+def clocks_summary(p, f, path):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    p.wait()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [t.strip() for t in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2402_17913_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(workload, cls):
+    """DRAM bytes per launch of kernel class `cls` from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    src = source_hash()
+    for line in open(path):
+        m = re.match(r"\s*traffic_bytes_per_launch:\s*(\w+)\s+([0-9.eE+]+)\s+src=(\w+)", line)
+        if m and m.group(1) == cls and m.group(3) == src:
+            return float(m.group(2))
+    return None
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2402_17913_gb300 import build, lib as L
+    build.build()
+    L.load()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    dev = torch.device("cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.config == "ns2d":
+        wl = NS2D()
+        solid_t = torch.from_numpy(wl.solid.astype(np.uint8)).to(dev)
+        ns = L.ns_create(2, wl.cells, 1.0, solid_t)
+        mg = L.ns_pressure_handle(ns)
+        q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
+        host = [torch.from_numpy(a).pin_memory() for a in (q[0], q[1], np.zeros(wl.solid.shape, np.float32))]
+        u, v, p = (t.to(dev) for t in host)
+        stats = []
+
+        def step():
+            _, st = L.ns_step(ns, u, v, None, p, wl.dt, wl.nu, wl.uin, TOL)
+            stats.append(st)
+
+        def e2e_step():
+            for d, hsrc in zip((u, v, p), host):
+                d.copy_(hsrc, non_blocking=True)
+            step()
+            for d, hdst in zip((u, v, p), host):
+                hdst.copy_(d, non_blocking=True)
+        io_bytes = sum(t.numel() * 4 for t in host)
+        cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
+    else:
+        shape = (256, 256) if args.config == "poisson2d" else (256, 256, 256)
+        wl = Poisson(shape, args.prec)
+        h = I.poisson_spacing(shape)
+        opt = L.default_options(prec=PREC[args.prec])
+        mg = L.mg_create(wl.dim, tuple(reversed(shape)), h, (0,) * (2 * wl.dim), None, opt)
+        b_host = torch.from_numpy(I.blob_rhs(shape, 0).astype(np.float32)).pin_memory()
+        x_host = torch.zeros_like(b_host).pin_memory()
+        b = b_host.to(dev)
+        x = torch.zeros_like(b)
+        stats = []
+
+        def step():
+            x.zero_()
+            _, st = L.mg_solve(mg, b, x, TOL)
+            stats.append(st)
+
+        def e2e_step():
+            b.copy_(b_host, non_blocking=True)
+            step()
+            x_host.copy_(x, non_blocking=True)
+        io_bytes = b_host.numel() * 4
+        cleanup = lambda: L.mg_destroy(mg)  # noqa: E731
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats.clear()
+    dist_barrier(world)
+    # ---- timed: device-resident inputs, L2 flushed between steps
+    launches0 = L.mg_kernel_launches(mg)
+    cp, cf, cpath = clocks_sampler()
+    times = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    clocks = clocks_summary(cp, cf, cpath)
+    times = [a.elapsed_time(b) for a, b in ev]
+    launches = L.mg_kernel_launches(mg) - launches0
+    step_stats = list(stats)
+    total_ms = sum(times)
+    total_ms = dist_max(total_ms, world)
+    if args.only_timed:
+        cleanup()
+        return {"metric": METRIC, "value": wl.units * args.steps * world / (total_ms * 1e-3), "unit": UNIT,
+                "steps": args.steps, "only_timed": True, "gpu_launches": int(launches)}, wl
+    # ---- end to end: host buffers, copies inside the timed region
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        e2e_step()
+        t1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(t0.elapsed_time(t1))
+    e2e_total = dist_max(sum(e2e_ms), world)
+    # ---- profiled pass: per-kernel-class event times (graph off)
+    L.mg_profile_enable(mg, True)
+    L.mg_profile_read(mg, reset=True)
+    nprof = min(args.steps, 5)
+    for i in range(nprof):
+        flush.fill_(float(i))
+        step()
+    prof = L.mg_profile_read(mg, reset=True)
+    L.mg_profile_enable(mg, False)
+    cleanup()
+
+    tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
+    dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
+    ms_dom, n_dom = prof[dom]
+    ncell = int(np.prod(wl.cells)) if args.config == "ns2d" else wl.units
+    per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config == "ns2d" and dom != "xr_update" else 0)
+    if args.prec != "fp32" and args.config != "ns2d":
+        per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
+    algo = per_cell * ncell
+    achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": recorded_traffic(wl.name, dom), "algorithmic_bytes_per_launch": algo,
+                "avg_launch_us": round(ms_dom / max(n_dom, 1) * 1e3, 2),
+                "share_of_step": round(ms_dom / tot_prof, 3),
+                "class_shares": {k: round(v[0] / tot_prof, 3) for k, v in prof.items() if v[1]}}
+    units_total = wl.units * args.steps * world
+    value = units_total / (total_ms * 1e-3)
+    its = [s["iters"] for s in step_stats]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
+        "data": "synthetic", "config": dict(wl.config(), parallelism="replicas" if world > 1 else "single"),
+        "clocks": clocks, "gpu_launches": int(launches),
+        "e2e": {"value": wl.units * args.steps * world / (e2e_total * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "roofline": roofline,
+        "solve": {"cg_iters_mean": statistics.mean(its) if its else None,
+                  "relres_max": max(s["relres"] for s in step_stats) if step_stats else None,
+                  "outer_mean": statistics.mean(s["outer"] for s in step_stats) if step_stats else None},
+    }
+    return out, wl
+
+
+def oracle_step_time(wl, budget_s=30.0, max_steps=3):
+    """Time the FP64 oracle (as it stands) on a bounded sample of workload
+    `wl`; returns (unknowns/s, sample description, steps timed)."""
+    from oracle import ns as N
+    from oracle import poisson as P
+    t_total, steps, units = 0.0, 0, 0
+    if isinstance(wl, NS2D):
+        g = N.MacGrid(wl.cells, 1.0, wl.solid)
+        hier = P.build_hierarchy(g.shape, (1.0, 1.0), g.p_bc, wl.solid)
+        mg = P.Multigrid(hier, s=1.0)
+        q = I.ns_initial_velocity(wl.cells, 0)
+        p = np.zeros(g.shape)
+        while steps < max_steps and t_total < budget_s:
+            t0 = time.perf_counter()
+            q, p, _, _, _ = N.ns_step(g, q, p, wl.dt, wl.nu, wl.uin,
+                                      solve=lambda b: P.pcg_ir(mg, b, tol=TOL)[0])
+            t_total += time.perf_counter() - t0
+            steps += 1
+            units += wl.units
+        sample = "%d oracle step(s) of the %dx%d projection workload (pressure solve to 1e-6)" % (
+            steps, wl.cells[0], wl.cells[1])
+    else:
+        shape = wl.shape
+        h = I.poisson_spacing(shape)
+        hier = P.build_hierarchy(shape, h, (0,) * (2 * len(shape)))
+        mg = P.Multigrid(hier, s=1.0)
+        b = I.blob_rhs(shape, 0).astype(np.float32).astype(np.float64)
+        while steps < max_steps and t_total < budget_s:
+            t0 = time.perf_counter()
+            P.pcg_ir(mg, b, tol=TOL)
+            t_total += time.perf_counter() - t0
+            steps += 1
+            units += wl.units
+        sample = "%d oracle solve(s) of the %s workload to 1e-6" % (steps, "x".join(map(str, shape)))
+    return units / t_total, sample, steps
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world = dist_init()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        wl = NS2D(scale=4) if args.config == "ns2d" else Poisson((256, 256), args.prec)
+        t0 = time.perf_counter()
+        rate, sample, n = oracle_step_time(wl, budget_s=1e9, max_steps=args.warmup + args.steps)
+        cores = 1
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(wl.config(), sample="quarter-resolution copy of the workload (512x256 cells, "
+                               "16-cell block, nu scaled to keep Re = 100)" if args.config == "ns2d" else None),
+                "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+    out, wl = run_gpu(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1 and not args.only_timed:
+            rate, sample, n = oracle_step_time(wl, budget_s=25.0, max_steps=1 if args.config != "poisson2d" else 5)
+            out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * npmg.h -- C ABI of the GB300 multigrid pressure-Poisson library.
+ *
+ * The library solves the discrete pressure-Poisson system of the Neural
+ * Physics projection method (Chen, Heaney & Pain, arXiv 2402.17913):
+ *
+ *     A_h x = b,   A_h = -Laplacian_h
+ *
+ * where A_h is the paper's fixed-weight diffusion filter with unit
+ * coefficient (Sec. 2.1 and App. A: the 2D 5-point filter
+ * [0 -1 0; -1 4 -1; 0 -1 0] / h^2 and the 3D 7-point filter with centre 6),
+ * applied as a cross-correlation (Eq. define_convolution) over an L x M (x N)
+ * grid whose padding ring holds the boundary values (Sec. 2.1: zero padding =
+ * Dirichlet 0; Sec. 2.3: copy padding = zero normal derivative).  The solver
+ * is the multigrid cycle of Sec. 2.2 (Jacobi smoothing, Eq. Jacobi-1-relax;
+ * 2x2(x2) average restriction; copy prolongation; filters re-discretised per
+ * level, App. B) used as the preconditioner of conjugate gradients, inside an
+ * iterative-refinement loop whose solution accumulator and outer residual are
+ * float64.  ns_step() runs one projection step of Algorithm 1.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  * Arrays are dense, row-major with x fastest: index = (z*ny + y)*nx + x.
+ *    shape[] and spacing[] are given in the order (x, y, z); bc[] lists the
+ *    faces x-, x+, y-, y+, z-, z+ (MG_BC_DIRICHLET or MG_BC_NEUMANN).
+ *  * Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *    pointers.  The library owns only what it allocates in *_create and
+ *    frees in *_destroy.  Solves and steps allocate nothing.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it; a call that returns statistics
+ *    (non-NULL out-stats pointer) synchronises that stream before returning.
+ *  * Every call returns an mg_status.  On MG_ERR_* the message is available
+ *    from mg_last_error() (thread-local, valid until the next failing call
+ *    on the same thread).  MG_NOT_CONVERGED / MG_DIVERGED still leave the
+ *    best iterate in the output buffer.
+ *  * Handles are not thread-safe; use one handle per host thread.  All
+ *    handles work on the CUDA device that was current at *_create.
+ *  * Solid cells (mask byte 1) are not unknowns: they are returned as 0, and
+ *    a fluid/solid face is a zero-normal-derivative face.
+ */
+#ifndef NPMG_H
+#define NPMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,     /* bad argument; nothing was enqueued          */
+  MG_ERR_CUDA = 2,        /* a CUDA call failed; see mg_last_error()     */
+  MG_ERR_OOM = 3,         /* device allocation failed in *_create        */
+  MG_NOT_CONVERGED = 4,   /* iteration limit reached before rel_tol      */
+  MG_DIVERGED = 5,        /* residual became non-finite or grew > 1e3x   */
+  MG_TIMEOUT = 6          /* a bounded device-side wait gave up          */
+} mg_status;
+
+enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 };
+
+typedef enum {
+  MG_FP32 = 0,        /* inner vectors and hierarchy stored in float32     */
+  MG_MIXED_FP16 = 1,  /* inner storage float16, float32 arithmetic         */
+  MG_MIXED_BF16 = 2   /* inner storage bfloat16, float32 arithmetic        */
+} mg_precision;
+
+typedef struct {
+  int pre;              /* Jacobi sweeps before restriction (default 2)        */
+  int post;             /* Jacobi sweeps after prolongation (default 2)        */
+  double omega;         /* Jacobi relaxation, Eq. Jacobi-1-relax (2/3)         */
+  double coarse_scale;  /* factor s on every coarse correction (1.0)           */
+  int levels;           /* grid levels, 0 = coarsen until the smallest side
+                           is 4 (e.g. 256^2 -> 7 levels)                       */
+  int krylov;           /* 1 = cycle preconditions CG (default); 0 = plain
+                           stationary cycles                                    */
+  int max_inner;        /* CG iterations per refinement step (default 200)     */
+  int max_outer;        /* refinement steps (default 12)                       */
+  mg_precision prec;    /* inner storage precision (default MG_FP32)           */
+  double inner_floor;   /* smallest relative tolerance asked of one inner
+                           solve; 0 = default for prec (1e-4 / 4e-3 / 2e-2)    */
+} mg_options;
+
+typedef struct {
+  int status;           /* mg_status of the solve                             */
+  int iters;            /* CG iterations (cycles when krylov = 0), all steps   */
+  int outer;            /* refinement steps taken                             */
+  int levels;           /* grid levels used                                   */
+  double relres0;       /* ||b - A x0|| / ||b|| of the initial guess (float64) */
+  double relres;        /* final ||b - A x|| / ||b||, x = float64 iterate      */
+  double bnorm;         /* ||b||_2                                            */
+  float ms;             /* device time of the solve, milliseconds             */
+  double history[32];   /* relres after each refinement step (first `outer`+1) */
+} mg_stats;
+
+typedef struct mg_handle_s* mg_handle;
+typedef struct ns_handle_s* ns_handle;
+
+/* Fill *opt with the defaults listed above. */
+void mg_default_options(mg_options* opt);
+
+/* Thread-local text of the last error (never NULL). */
+const char* mg_last_error(void);
+
+/*
+ * mg_create: build the level hierarchy of A_h (Sec. 2.2 / App. B: level k
+ * has half the cells of level k-1 per axis and spacing 2^k h).
+ *   dim        2 or 3.
+ *   shape      cells per axis (x, y[, z]); each must be divisible by
+ *              2^(levels-1) and the coarsest side must be >= 2.
+ *   spacing    h per axis (x, y[, z]), > 0.
+ *   bc         2*dim face types (x-, x+, y-, y+[, z-, z+]).
+ *   d_solid    device uint8 array of shape cells (1 = solid) or NULL.  Read
+ *              during the call only.  Every fluid component must touch a
+ *              Dirichlet face (otherwise A_h is singular).
+ *   opt        NULL = defaults.
+ * Allocates the workspace (hierarchy, CG vectors, float64 accumulator,
+ * coarsest-level inverse) on the current device and factors the coarsest
+ * level.  Errors: MG_ERR_INVALID (bad shape/bc/options), MG_ERR_OOM,
+ * MG_ERR_CUDA.  *out is NULL on error.
+ */
+mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3],
+                    const double spacing[3], const int bc[6],
+                    const uint8_t* d_solid, const mg_options* opt,
+                    void* stream);
+
+/*
+ * mg_solve: solve A_h x = b until ||b - A_h x||_2 <= rel_tol * ||b||_2, with
+ * the residual of the float64 iterate evaluated in float64.
+ *   d_b   device float32 right-hand side (values on solid cells ignored).
+ *   d_x   device float32: initial guess on entry, solution on exit (the
+ *         float64 iterate rounded to float32; fetch the float64 iterate with
+ *         mg_get_solution_f64).
+ *   rel_tol  > 0.
+ *   out   host stats or NULL (NULL keeps the call asynchronous).
+ * Returns MG_OK, MG_NOT_CONVERGED, MG_DIVERGED, or an error.  The returned
+ * status is that of the solve only when out != NULL (otherwise MG_OK once
+ * enqueued; the device-side status is then in the next stats read).
+ */
+mg_status mg_solve(mg_handle h, const float* d_b, float* d_x, double rel_tol,
+                   void* stream, mg_stats* out);
+
+/* Copy the float64 iterate of the last solve into d_x64 (device, cells). */
+mg_status mg_get_solution_f64(mg_handle h, double* d_x64, void* stream);
+
+/* Number of levels and cells per axis of level k (host ints). */
+mg_status mg_level_shape(mg_handle h, int k, int64_t shape_out[3]);
+int mg_num_levels(mg_handle h);
+
+/*
+ * Building blocks, one kernel each, on caller-provided float32 device
+ * arrays of level k's shape.  They use the operator of level k scaled by
+ * (h_0x / h_kx)^2 ... i.e. the coefficients w_a = h_0x^2 / h_{k,a}^2 (the
+ * finest x-spacing squared times the paper's filter), which is the form the
+ * solver iterates on; multiply by 1/h_0x^2 to get A_h itself.
+ *   mg_apply_operator: d_y = A'_k d_x (0 on solid cells).
+ *   mg_smooth: `sweeps` weighted-Jacobi sweeps of A'_k x = b in place.
+ *   mg_residual_restrict: d_bc (level k+1) = R (b - A'_k x).
+ *   mg_prolong_correct: x += s * P e (e on level k+1), 0 on solid cells.
+ *   mg_precondition: d_z = one cycle of the preconditioner on r, level 0.
+ */
+mg_status mg_apply_operator(mg_handle h, int k, const float* d_x, float* d_y,
+                            void* stream);
+mg_status mg_smooth(mg_handle h, int k, float* d_x, const float* d_b,
+                    int sweeps, void* stream);
+mg_status mg_residual_restrict(mg_handle h, int k, const float* d_x,
+                               const float* d_b, float* d_bc, void* stream);
+mg_status mg_prolong_correct(mg_handle h, int k, const float* d_e, float* d_x,
+                             void* stream);
+mg_status mg_precondition(mg_handle h, const float* d_r, float* d_z,
+                          void* stream);
+
+mg_status mg_destroy(mg_handle h);
+
+/*
+ * Instrumentation (no counterpart in the paper).  With profiling on, every
+ * kernel launch of the handle (solves, and the projection steps of the
+ * ns_handle that owns it) is bracketed by CUDA events on its stream and the
+ * solve runs without its CUDA graph; mg_profile_read adds up the event
+ * times per kernel class (milliseconds) and launch counts into the caller's
+ * host arrays of MG_K_COUNT entries, synchronising the handle's last stream.
+ * mg_kernel_launches counts every kernel the handle has launched (the nodes
+ * of each graph launch included) whether or not profiling is on.
+ */
+typedef enum {
+  MG_K_DOWN_FINE = 0,   /* smoothing + residual + restriction, finest level  */
+  MG_K_UP_FINE = 1,     /* prolongation + correction + smoothing, finest     */
+  MG_K_DOWN = 2,        /* the same on the other multi-block levels          */
+  MG_K_UP = 3,
+  MG_K_COARSE = 4,      /* single-block cycle of the coarse levels           */
+  MG_K_P_UPDATE = 5,    /* CG: p = z + beta p, Ap, (p, Ap)                   */
+  MG_K_XR_UPDATE = 6,   /* CG: d += alpha p, r -= alpha Ap, ||r||            */
+  MG_K_OUTER = 7,       /* float64 refinement residual                       */
+  MG_K_INIT_FINISH = 8,
+  MG_K_MOMENTUM = 9,
+  MG_K_DIVERGENCE = 10,
+  MG_K_CORRECT = 11,
+  MG_K_COUNT = 12
+} mg_kernel_class;
+mg_status mg_profile_enable(mg_handle h, int on);
+mg_status mg_profile_read(mg_handle h, double* h_ms, int64_t* h_launches, int reset);
+int64_t mg_kernel_launches(mg_handle h);
+
+/*
+ * Projection step (Algorithm 1) on a staggered grid of cells (x, y[, z])
+ * with spacing h in every direction.  Pressure at cell centres (cells);
+ * u on x-faces (nx+1, ny[, nz]), v on y-faces (nx, ny+1[, nz]), w on z-faces
+ * (nx, ny, nz+1), each x fastest.  Boundaries: x- inflow (u = u_inflow,
+ * tangential 0), x+ outflow (zero-gradient velocity, p = 0), other faces
+ * free-slip walls.  d_solid (cells, 1 = solid, nullable) marks the body:
+ * faces touching it get the implicit absorption sigma (Eq. Tn+1); its cells
+ * are not pressure unknowns.
+ *
+ * ns_create: allocates the pressure hierarchy (Neumann except x+ Dirichlet)
+ *   and the momentum workspace.  sigma: absorption on solid faces (1e8).
+ * ns_step: momentum predictor + corrector (Sec. 2.3 two-pass scheme with
+ *   frozen time-n advecting velocity), b = -(1/dt) D q*, pressure correction
+ *   solve A_h dp = b from dp = 0 to rel_tol, q -= dt G dp, p += dp.  u, v,
+ *   (w), p are updated in place.  out: stats of the pressure solve or NULL.
+ */
+mg_status ns_create(ns_handle* out, int dim, const int64_t cells[3], double h,
+                    const uint8_t* d_solid, double sigma,
+                    const mg_options* opt, void* stream);
+mg_status ns_step(ns_handle ns, float* d_u, float* d_v, float* d_w,
+                  float* d_p, double dt, double nu, double u_inflow,
+                  double rel_tol, void* stream, mg_stats* out);
+/* Step 1 only: q* from q^n and p^n into d_us, d_vs, d_ws (face arrays). */
+mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v,
+                      const float* d_w, const float* d_p, float* d_us,
+                      float* d_vs, float* d_ws, double dt, double nu,
+                      double u_inflow, void* stream);
+/* Step 2 RHS only: d_b = -(1/dt) D q* on fluid cells, 0 on solid cells. */
+mg_status ns_divergence_rhs(ns_handle ns, const float* d_us, const float* d_vs,
+                            const float* d_ws, double dt, float* d_b,
+                            void* stream);
+/* Steps 3-5 only: q -= dt G dp (faces that G corrects), p += dp. */
+mg_status ns_correct(ns_handle ns, float* d_u, float* d_v, float* d_w,
+                     float* d_p, const float* d_dp, double dt, void* stream);
+/* The pressure handle inside ns (owned by ns; do not destroy). */
+mg_handle ns_pressure_handle(ns_handle ns);
+mg_status ns_destroy(ns_handle ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPMG_H */

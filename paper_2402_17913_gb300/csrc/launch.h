@@ -1,0 +1,73 @@
+// Kernel launchers exported between the library's translation units.
+#pragma once
+#include "npmg_internal.cuh"
+
+namespace npmg {
+
+struct CoarseArgs {
+  int nlev;                    // levels handled by the single-block kernel
+  int dim;
+  LevelDev lv[kMaxLevels];     // lv[0] = first level handled
+  int off[kMaxLevels];         // float offset of level l's arrays (x0, x1, b)
+  int moff[kMaxLevels];        // byte offset of level l's cell bytes
+  int ncoarse;                 // cells of the coarsest level
+  const double* inv;           // inverse of the coarsest operator, column-major
+  int pre, post;
+  float omega, s;
+  int finest;                  // lv[0] is the finest level: reduce (r, z)
+};
+
+template <int DIM, typename T, bool MASKED>
+cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,
+                        const SolveState* st, cudaStream_t s);
+template <int DIM, typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, int post,
+                      float omega, float sc, SolveState* st, double* partials, cudaStream_t s);
+
+template <int DIM, typename T, bool MASKED>
+cudaError_t prepare_level_kernels(int pre, int post);
+template <typename T>
+cudaError_t prepare_coarse(size_t smem_bytes);
+
+template <typename T>
+cudaError_t launch_coarse(const CoarseArgs& a, size_t smem_bytes, const void* b, void* x, SolveState* st,
+                          cudaStream_t s);
+template <int DIM, typename T, bool MASKED>
+cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, void* pnew, void* Ap,
+                            SolveState* st, double* partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_xr_update(const LevelDev& L, const void* p, const void* Ap, void* d, void* r, SolveState* st,
+                             double* partials, cudaStream_t s);
+// x: float-float iterate (float2 per cell); w: operator weights c / h_a^2.
+template <int DIM, typename T, bool MASKED, bool UPDATE>
+cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
+                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s);
+
+struct SolveParams {
+  double tol, inner_floor;
+  int max_inner, max_outer, krylov, n_fluid;
+};
+cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, void* x, double c, SolveParams prm,
+                        SolveState* st, double* partials, cudaStream_t s);
+cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s);
+cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s);
+
+// set-up kernels
+cudaError_t launch_coarsen_solid(int dim, const int64_t fine[3], const uint8_t* sf, uint8_t* sc, cudaStream_t s);
+cudaError_t launch_cell_bytes(int dim, const int64_t n[3], int bcD, const uint8_t* solid, uint8_t* cell,
+                              cudaStream_t s);
+cudaError_t launch_coarse_inverse(int dim, const int64_t n[3], const double w[3], int bcD, const uint8_t* cell,
+                                  double* mat, cudaStream_t s);
+
+// per-kernel building blocks (float32 only)
+template <int DIM, bool MASKED>
+cudaError_t launch_apply(const LevelDev& L, const float* x, float* y, cudaStream_t s);
+template <int DIM, bool MASKED>
+cudaError_t launch_smooth_once(const LevelDev& L, const float* x, float* y, const float* b, float omega,
+                               cudaStream_t s);
+template <int DIM, bool MASKED>
+cudaError_t launch_restrict_residual(const LevelDev& L, const float* x, const float* b, float* bc, cudaStream_t s);
+template <int DIM, bool MASKED>
+cudaError_t launch_prolong_correct(const LevelDev& L, const float* e, float* x, float sc, cudaStream_t s);
+
+}  // namespace npmg

@@ -1,0 +1,574 @@
+// Conjugate-gradient vector kernels and the refinement loop's residual.
+//
+// Row mapping: a block of 256 threads covers 8 rows x 128 cells; each thread
+// owns 4 consecutive cells of one row (one 16-byte load per float32 array),
+// and blocks stride over z.  Partial sums are accumulated in float32 per
+// thread and in float64 across the block and the grid (fixed order, so
+// results are reproducible run to run).
+#include <math.h>
+
+#include "launch.h"
+#include "mg_kernels.cuh"
+
+namespace npmg {
+
+// ---------------------------------------------------------------------------
+// 4-cell row access (vector loads when the row length is a multiple of 4,
+// otherwise guarded scalar loads; cells past the row end read as 0).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* __restrict__ p, size_t i, int x0, int nx, float v[4]) {
+  if ((nx & 3) == 0) {
+    if constexpr (std::is_same<T, float>::value) {
+      const float4 q = *reinterpret_cast<const float4*>(p + i);
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (std::is_same<T, __half>::value) {
+      const uint2 q = *reinterpret_cast<const uint2*>(p + i);
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+      const uint2 q = *reinterpret_cast<const uint2*>(p + i);
+      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (x0 + k < nx) ? ld(p, i + k) : 0.f;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* __restrict__ p, size_t i, int x0, int nx, const float v[4]) {
+  if ((nx & 3) == 0) {
+    if constexpr (std::is_same<T, float>::value) {
+      *reinterpret_cast<float4*>(p + i) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (std::is_same<T, __half>::value) {
+      __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+      uint2 q;
+      q.x = *reinterpret_cast<unsigned*>(&a);
+      q.y = *reinterpret_cast<unsigned*>(&b);
+      *reinterpret_cast<uint2*>(p + i) = q;
+    } else {
+      __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+      uint2 q;
+      q.x = *reinterpret_cast<unsigned*>(&a);
+      q.y = *reinterpret_cast<unsigned*>(&b);
+      *reinterpret_cast<uint2*>(p + i) = q;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (x0 + k < nx) p[i + k] = cvt<T>(v[k]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ float rnd(float v) {
+  const T t = cvt<T>(v);
+  return ld(&t, 0);
+}
+
+__device__ __forceinline__ void ld4_cell(const uint8_t* __restrict__ c, size_t i, int x0, int nx, uint8_t m[4]) {
+  if ((nx & 3) == 0) {
+    const uchar4 q = *reinterpret_cast<const uchar4*>(c + i);
+    m[0] = q.x; m[1] = q.y; m[2] = q.z; m[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[k] = (x0 + k < nx) ? c[i + k] : 0;
+  }
+}
+
+template <bool MASKED>
+__device__ __forceinline__ void cells4(const LevelDev& L, size_t i, int x0, uint8_t m[4]) {
+  if (MASKED) {
+    ld4_cell(L.cell, i, x0, L.nx, m);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[k] = (x0 + k < L.nx) ? kFluidBit : 0;
+  }
+}
+
+__device__ __forceinline__ void row_thread(int& x0, int& y) {
+  x0 = (blockIdx.x * 32 + (threadIdx.x & 31)) * 4;
+  y = blockIdx.y * 8 + (threadIdx.x >> 5);
+}
+
+static dim3 row_grid(const LevelDev& L) {
+  const int gx = (L.nx + 127) / 128, gy = (L.ny + 7) / 8;
+  int gz = L.nz;
+  while ((long)gx * gy * gz > 16384 && gz > 1) gz = (gz + 1) / 2;
+  return dim3(gx, gy, gz);
+}
+
+__device__ __forceinline__ double pow2_floor(double v) {
+  if (!(v > 0.0) || !isfinite(v)) return 1.0;
+  int e;
+  frexp(v, &e);
+  return ldexp(1.0, e - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (Dekker 1971; Knuth, TAOCP vol. 2, Sec. 4.2.2):
+// a value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.
+// GB300 runs float64 at 1/64 of the float32 rate, so the refinement
+// residual uses these float32 sequences instead.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// (a.hi + a.lo) * (w.hi + w.lo), dropping the lo * lo term.
+__device__ __forceinline__ ff ff_mul(ff a, ff w) {
+  const float p = a.hi * w.hi;
+  float e = fmaf(a.hi, w.hi, -p);
+  e = fmaf(a.hi, w.lo, e);
+  e = fmaf(a.lo, w.hi, e);
+  return quick_two_sum(p, e);
+}
+
+// ---------------------------------------------------------------------------
+// CG: p = z + beta p ; Ap = A' p ; (p, Ap) -> alpha = (r, z) / (p, Ap).
+// p is double-buffered (pold -> pnew) because Ap needs p at neighbours.
+template <int DIM, typename T, bool MASKED>
+__global__ void __launch_bounds__(256) k_p_update(LevelDev L, const T* __restrict__ z, const T* __restrict__ pold,
+                                                  T* __restrict__ pnew, T* __restrict__ Ap,
+                                                  SolveState* __restrict__ st, double* __restrict__ partials) {
+  if (st->inner_done) return;
+  const bool first = st->first || !st->krylov;
+  const float beta = first ? 0.f : (float)st->beta;
+  int x0, y;
+  row_thread(x0, y);
+  float acc = 0.f;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  auto pvec = [&](size_t j, float out[4]) {
+    ld4(z, j, x0, L.nx, out);
+    if (!first) {
+      float t[4];
+      ld4(pold, j, x0, L.nx, t);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out[k] = fmaf(beta, t[k], out[k]);
+    }
+  };
+  auto psc = [&](size_t j) {
+    float v = ld(z, j);
+    if (!first) v = fmaf(beta, ld(pold, j), v);
+    return v;
+  };
+  if (x0 < L.nx && y < L.ny) {
+    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
+      float pc[4], nb[4], t[4];
+      pvec(i, pc);
+      const float pl = x0 > 0 ? psc(i - 1) : 0.f;
+      const float pr = x0 + 4 < L.nx ? psc(i + 4) : 0.f;
+      nb[0] = L.wx * (pl + pc[1]);
+      nb[1] = L.wx * (pc[0] + pc[2]);
+      nb[2] = L.wx * (pc[1] + pc[3]);
+      nb[3] = L.wx * (pc[2] + pr);
+      if (y > 0) {
+        pvec(i - L.nx, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wy, t[k], nb[k]);
+      }
+      if (y < L.ny - 1) {
+        pvec(i + L.nx, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wy, t[k], nb[k]);
+      }
+      if (DIM == 3) {
+        if (zz > 0) {
+          pvec(i - sxy, t);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wz, t[k], nb[k]);
+        }
+        if (zz < L.nz - 1) {
+          pvec(i + sxy, t);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wz, t[k], nb[k]);
+        }
+      }
+      uint8_t m[4];
+      cells4<MASKED>(L, i, x0, m);
+      float ap[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (m[k]) {
+          ap[k] = diag_at<DIM, MASKED>(L, x0 + k, y, zz, m[k]) * pc[k] - nb[k];
+        } else {
+          pc[k] = 0.f;
+          ap[k] = 0.f;
+        }
+        acc = fmaf(rnd<T>(pc[k]), rnd<T>(ap[k]), acc);
+      }
+      st4(pnew, i, x0, L.nx, pc);
+      st4(Ap, i, x0, L.nx, ap);
+    }
+  }
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntPAP], &tot)) {
+    if (threadIdx.x == 0) {
+      st->pAp = tot;
+      st->alpha = st->krylov ? st->rz / tot : 1.0;
+    }
+  }
+}
+
+// CG: d += alpha p ; r -= alpha Ap ; ||r||^2 ; convergence test.
+template <typename T>
+__global__ void __launch_bounds__(256) k_xr_update(LevelDev L, const T* __restrict__ p, const T* __restrict__ Ap,
+                                                   T* __restrict__ d, T* __restrict__ r, SolveState* __restrict__ st,
+                                                   double* __restrict__ partials) {
+  if (st->inner_done) return;
+  const float alpha = (float)st->alpha;
+  const bool first = st->first;
+  int x0, y;
+  row_thread(x0, y);
+  float acc = 0.f;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  if (x0 < L.nx && y < L.ny) {
+    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
+      float pv[4], av[4], dv[4], rv[4];
+      ld4(p, i, x0, L.nx, pv);
+      ld4(Ap, i, x0, L.nx, av);
+      ld4(r, i, x0, L.nx, rv);
+      if (first) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dv[k] = alpha * pv[k];
+      } else {
+        ld4(d, i, x0, L.nx, dv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dv[k] = fmaf(alpha, pv[k], dv[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rv[k] = fmaf(-alpha, av[k], rv[k]);
+        const float rr = rnd<T>(rv[k]);
+        acc = fmaf(rr, rr, acc);
+      }
+      st4(d, i, x0, L.nx, dv);
+      st4(r, i, x0, L.nx, rv);
+    }
+  }
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntRR], &tot)) {
+    if (threadIdx.x == 0) {
+      st->rnorm2 = tot;
+      st->it += 1;
+      st->iters_total += 1;
+      st->first = 0;
+      if (!isfinite(tot) || tot > 1e12 * st->r0norm2) {
+        st->status = MG_DIVERGED;
+        st->inner_done = 1;
+        st->outer_done = 1;
+      } else if (tot <= st->eta * st->eta * st->r0norm2 || st->it >= st->max_inner) {
+        st->inner_done = 1;
+      }
+    }
+  }
+}
+
+template <int DIM, typename T, bool MASKED>
+cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, void* pnew, void* Ap,
+                            SolveState* st, double* partials, cudaStream_t s) {
+  k_p_update<DIM, T, MASKED><<<row_grid(L), 256, 0, s>>>(L, (const T*)z, (const T*)pold, (T*)pnew, (T*)Ap, st,
+                                                         partials);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_xr_update(const LevelDev& L, const void* p, const void* Ap, void* d, void* r, SolveState* st,
+                             double* partials, cudaStream_t s) {
+  k_xr_update<T><<<row_grid(L), 256, 0, s>>>(L, (const T*)p, (const T*)Ap, (T*)d, (T*)r, st, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Refinement residual in float-float.  x is kept as (hi, lo) pairs.  With
+// UPDATE it first applies x <- x + sigma d' (sigma a power of two, so
+// sigma d' is exact).  Then, in the scaled units of the inner solve
+// (A' = c A_h), r = c b - A' x is formed to ~48 bits, ||r|| reduced, and
+// r' = r / sigma_new rounded to the inner storage type (sigma_new a power of
+// two near rms(r)).  The last block decides: converged, diverged,
+// stalled, or the tolerance of the next inner solve.
+struct OuterArgs {
+  ff w[3];        // c / h_a^2 per axis as float-float
+  ff c;           // h_0x^2 as float-float
+  double c2;      // c^2 (to turn ||r||^2 back into unscaled units)
+};
+
+template <int DIM, typename T, bool MASKED, bool UPDATE>
+__global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const float* __restrict__ b,
+                                               const float2* __restrict__ xin, float2* __restrict__ xout,
+                                               const T* __restrict__ dprime, T* __restrict__ rprime,
+                                               SolveState* __restrict__ st, double* __restrict__ partials) {
+  const double sig_old_d = st->sigma;
+  double sig_new_d = sig_old_d;
+  if (UPDATE) sig_new_d = pow2_floor(sig_old_d * sqrt(fmax(st->rnorm2, 1e-300) / (double)st->n_fluid));
+  const float sig_old = (float)sig_old_d;
+  const float inv_sig_new = (float)(1.0 / sig_new_d);
+  int x0, y;
+  row_thread(x0, y);
+  float acc = 0.f;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  auto xv = [&](size_t j) -> ff {
+    const float2 q = xin[j];
+    if (!UPDATE) return {q.x, q.y};
+    const ff s = two_sum(q.x, sig_old * ld(dprime, j));
+    return quick_two_sum(s.hi, s.lo + q.y);
+  };
+  if (x0 < L.nx && y < L.ny) {
+    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
+      uint8_t m[4];
+      cells4<MASKED>(L, i, x0, m);
+      ff xc[6];  // x0-1 .. x0+4
+      xc[0] = x0 > 0 ? xv(i - 1) : ff{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xc[k + 1] = (x0 + k < L.nx) ? xv(i + k) : ff{0.f, 0.f};
+      xc[5] = x0 + 4 < L.nx ? xv(i + 4) : ff{0.f, 0.f};
+      float rv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rv[k] = 0.f;
+        if (!m[k]) {
+          if (UPDATE && x0 + k < L.nx) xout[i + k] = make_float2(0.f, 0.f);
+          continue;
+        }
+        const int cx = x0 + k;
+        int kx, ky, kz = 0;
+        if (MASKED) {
+          kx = m[k] & 3;
+          ky = (m[k] >> 2) & 3;
+          kz = (m[k] >> 4) & 3;
+        } else {
+          kx = axis_count(cx, L.nx, L.bcD, 0);
+          ky = axis_count(y, L.ny, L.bcD, 2);
+          if (DIM == 3) kz = axis_count(zz, L.nz, L.bcD, 4);
+        }
+        // A' x = sum_a w_a (k_a x_c - x_left - x_right)
+        ff ax = ff_mul(ff_add(ff_mul(xc[k + 1], ff{(float)kx, 0.f}), ff_neg(ff_add(xc[k], xc[k + 2]))), oa.w[0]);
+        {
+          ff s = ff_mul(xc[k + 1], ff{(float)ky, 0.f});
+          if (y > 0) s = ff_add(s, ff_neg(xv(i + k - L.nx)));
+          if (y < L.ny - 1) s = ff_add(s, ff_neg(xv(i + k + L.nx)));
+          ax = ff_add(ax, ff_mul(s, oa.w[1]));
+        }
+        if (DIM == 3) {
+          ff s = ff_mul(xc[k + 1], ff{(float)kz, 0.f});
+          if (zz > 0) s = ff_add(s, ff_neg(xv(i + k - sxy)));
+          if (zz < L.nz - 1) s = ff_add(s, ff_neg(xv(i + k + sxy)));
+          ax = ff_add(ax, ff_mul(s, oa.w[2]));
+        }
+        const ff r = ff_add(ff_mul(ff{b[i + k], 0.f}, oa.c), ff_neg(ax));
+        const float rs = r.hi + r.lo;
+        rv[k] = rs * inv_sig_new;
+        acc = fmaf(rs, rs, acc);
+        if (UPDATE) xout[i + k] = make_float2(xc[k + 1].hi, xc[k + 1].lo);
+      }
+      st4(rprime, i, x0, L.nx, rv);
+    }
+  }
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntOuter], &tot)) {
+    if (threadIdx.x == 0) {
+      const double bn2 = st->bnorm2;
+      const double rel = bn2 > 0.0 ? sqrt(tot / (oa.c2 * bn2)) : 0.0;
+      const double prev = st->relres;
+      if (UPDATE) st->outer += 1;
+      const int o = st->outer;
+      if (o < kHistory) st->hist[o] = rel;
+      if (!UPDATE) st->relres0 = rel;
+      st->relres = rel;
+      st->sigma = sig_new_d;
+      bool done = false;
+      if (bn2 == 0.0 || rel <= st->tol) {
+        st->status = MG_OK;
+        done = true;
+      } else if (!isfinite(rel) || rel > 1e3 * fmax(st->relres0, 1.0) || st->status == MG_DIVERGED) {
+        st->status = MG_DIVERGED;
+        done = true;
+      } else if (o >= st->max_outer) {
+        st->status = MG_NOT_CONVERGED;
+        done = true;
+      } else {
+        if (UPDATE && rel > 0.9 * prev) st->stall += 1;
+        if (st->stall >= 3) {
+          st->status = MG_NOT_CONVERGED;
+          done = true;
+        }
+      }
+      st->outer_done = done ? 1 : 0;
+      if (!done) {
+        st->eta = fmax(0.5 * st->tol / rel, st->inner_floor);
+        st->r0norm2 = tot / (sig_new_d * sig_new_d);
+        st->inner_done = 0;
+        st->it = 0;
+        st->first = 1;
+      } else {
+        st->inner_done = 1;
+      }
+    }
+  }
+}
+
+static OuterArgs outer_args(const double w[3], double c) {
+  OuterArgs a;
+  for (int k = 0; k < 3; ++k) {
+    a.w[k].hi = (float)w[k];
+    a.w[k].lo = (float)(w[k] - (double)a.w[k].hi);
+  }
+  a.c.hi = (float)c;
+  a.c.lo = (float)(c - (double)a.c.hi);
+  a.c2 = c * c;
+  return a;
+}
+
+template <int DIM, typename T, bool MASKED, bool UPDATE>
+cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
+                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s) {
+  k_outer<DIM, T, MASKED, UPDATE><<<row_grid(L), 256, 0, s>>>(L, outer_args(w, c), b, (const float2*)xin,
+                                                              (float2*)xout, (const T*)dprime, (T*)rprime, st,
+                                                              partials);
+  return cudaGetLastError();
+}
+
+#define NPMG_INST_VEC(DIM, T, M)                                                                                \
+  template cudaError_t launch_p_update<DIM, T, M>(const LevelDev&, const void*, const void*, void*, void*,       \
+                                                  SolveState*, double*, cudaStream_t);                           \
+  template cudaError_t launch_outer<DIM, T, M, false>(const LevelDev&, const double*, double, const float*,     \
+                                                      const void*, void*, const void*, void*, SolveState*,       \
+                                                      double*, cudaStream_t);                                    \
+  template cudaError_t launch_outer<DIM, T, M, true>(const LevelDev&, const double*, double, const float*,      \
+                                                     const void*, void*, const void*, void*, SolveState*,        \
+                                                     double*, cudaStream_t);
+
+NPMG_INST_VEC(2, float, false)
+NPMG_INST_VEC(2, float, true)
+NPMG_INST_VEC(3, float, false)
+NPMG_INST_VEC(3, float, true)
+NPMG_INST_VEC(2, __half, false)
+NPMG_INST_VEC(2, __half, true)
+NPMG_INST_VEC(3, __half, false)
+NPMG_INST_VEC(3, __half, true)
+NPMG_INST_VEC(2, __nv_bfloat16, false)
+NPMG_INST_VEC(2, __nv_bfloat16, true)
+NPMG_INST_VEC(3, __nv_bfloat16, false)
+NPMG_INST_VEC(3, __nv_bfloat16, true)
+
+template cudaError_t launch_xr_update<float>(const LevelDev&, const void*, const void*, void*, void*, SolveState*,
+                                             double*, cudaStream_t);
+template cudaError_t launch_xr_update<__half>(const LevelDev&, const void*, const void*, void*, void*, SolveState*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_xr_update<__nv_bfloat16>(const LevelDev&, const void*, const void*, void*, void*,
+                                                     SolveState*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Solve start: x = (guess, 0) on fluid cells; ||b||^2; reset the state.
+__global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restrict__ b, const float* __restrict__ xg,
+                                              float2* __restrict__ x, double c, SolveParams prm,
+                                              SolveState* __restrict__ st, double* __restrict__ partials) {
+  int x0, y;
+  row_thread(x0, y);
+  float acc = 0.f;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  if (x0 < L.nx && y < L.ny) {
+    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
+      uint8_t m[4];
+      if (L.cell) ld4_cell(L.cell, i, x0, L.nx, m);
+      else cells4<false>(L, i, x0, m);
+      float bv[4], xv[4];
+      ld4(b, i, x0, L.nx, bv);
+      ld4(xg, i, x0, L.nx, xv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (x0 + k >= L.nx) continue;
+        x[i + k] = make_float2(m[k] ? xv[k] : 0.f, 0.f);
+        if (m[k]) acc = fmaf(bv[k], bv[k], acc);
+      }
+    }
+  }
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntInit], &tot)) {
+    if (threadIdx.x == 0) {
+      st->tol = prm.tol;
+      st->inner_floor = prm.inner_floor;
+      st->max_inner = prm.max_inner;
+      st->max_outer = prm.max_outer;
+      st->krylov = prm.krylov;
+      st->n_fluid = prm.n_fluid;
+      st->bnorm2 = tot;
+      st->relres = 1.0;
+      st->relres0 = 1.0;
+      st->sigma = tot > 0.0 ? pow2_floor(c * sqrt(tot / (double)prm.n_fluid)) : 1.0;
+      st->eta = 1.0;
+      st->outer = 0;
+      st->outer_done = 0;
+      st->status = MG_OK;
+      st->stall = 0;
+      for (int k = 0; k < kHistory; ++k) st->hist[k] = 0.0;
+      st->inner_done = 1;
+      st->it = 0;
+      st->iters_total = 0;
+      st->first = 1;
+      st->r0norm2 = 0.0;
+      st->rz = st->rz_old = st->alpha = st->beta = st->rnorm2 = st->pAp = 0.0;
+    }
+  }
+}
+
+cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, void* x, double c, SolveParams prm,
+                        SolveState* st, double* partials, cudaStream_t s) {
+  k_init<<<row_grid(L), 256, 0, s>>>(L, b, xguess, (float2*)x, c, prm, st, partials);
+  return cudaGetLastError();
+}
+
+// Solve end: the float32 output is hi (hi + lo rounded); a zero right-hand
+// side has the zero solution.
+__global__ void k_finish(size_t n, float2* __restrict__ x, float* __restrict__ out,
+                         const SolveState* __restrict__ st) {
+  const bool zero = st->bnorm2 == 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (zero) {
+      x[i] = make_float2(0.f, 0.f);
+      out[i] = 0.f;
+    } else {
+      const float2 v = x[i];
+      out[i] = v.x + v.y;
+    }
+  }
+}
+
+cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s) {
+  k_finish<<<nblocks, 256, 0, s>>>(n, (float2*)x, out, st);
+  return cudaGetLastError();
+}
+
+// The float64 value of the iterate: (double)hi + (double)lo.
+__global__ void k_ff_to_f64(size_t n, const float2* __restrict__ x, double* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = x[i];
+    out[i] = (double)v.x + (double)v.y;
+  }
+}
+
+cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s) {
+  k_ff_to_f64<<<nblocks, 256, 0, s>>>(n, (const float2*)x, out);
+  return cudaGetLastError();
+}
+
+}  // namespace npmg

@@ -1,0 +1,76 @@
+// Definition of the opaque solver handle (host side).
+#pragma once
+#include <type_traits>
+
+#include "launch.h"
+
+namespace npmg {
+
+constexpr int kChunk = 4;              // CG iterations per graph launch
+constexpr int kMaxPartials = 1 << 16;  // per-block partial sums
+constexpr int kProfEvents = 4096;      // event pairs buffered by the profiler
+
+}  // namespace npmg
+
+struct mg_handle_s {
+  int dim, L, kc, device, nsm, esz, use_graph;
+  int64_t n[npmg::kMaxLevels][3];
+  double h[npmg::kMaxLevels][3];
+  size_t ncell[npmg::kMaxLevels];
+  int bc[6], bcD;
+  bool masked;
+  mg_options opt;
+  double inner_floor;
+  double c;        // h_0x^2: A' = c A_h
+  double w0[3];    // finest-level operator weights c / h_0a^2
+  int n_fluid;
+  npmg::LevelDev lv[npmg::kMaxLevels];
+  // device workspace (one allocation)
+  char* pool;
+  size_t pool_bytes;
+  uint8_t* solid[npmg::kMaxLevels];
+  uint8_t* cell[npmg::kMaxLevels];
+  void* xk[npmg::kMaxLevels];
+  void* yk[npmg::kMaxLevels];
+  void* bk[npmg::kMaxLevels];
+  void *r, *z, *p[2], *Ap, *d;
+  void* xff[2];    // float-float iterate (hi, lo) per cell, double-buffered
+  int cur64;
+  double* inv;
+  int ncoarse;
+  double* partials;
+  npmg::SolveState* st;
+  npmg::SolveState* st_host;  // pinned
+  npmg::CoarseArgs ca;
+  size_t ca_smem;
+  int nb1d;
+  cudaEvent_t ev0, ev1;
+  cudaGraphExec_t graph_exec;
+  int64_t chunk_kernels;   // kernels in one graph launch
+  // instrumentation
+  int64_t launches;
+  int prof;
+  int capturing;
+  cudaEvent_t* pev;        // 2 * kProfEvents events (created on enable)
+  int pcls[npmg::kProfEvents];
+  int pused;
+  cudaStream_t plast;
+  double prof_ms[MG_K_COUNT];
+  int64_t prof_n[MG_K_COUNT];
+};
+
+namespace npmg {
+// Brackets one kernel launch: counts it and, with profiling on, records a
+// start/end event pair on the launch stream.
+struct LaunchScope {
+  mg_handle_s* h;
+  int idx;
+  cudaStream_t s;
+  LaunchScope(mg_handle_s* hh, int cls, cudaStream_t ss);
+  ~LaunchScope();
+};
+cudaError_t prof_flush(mg_handle_s* h);
+const char* last_error();
+mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaStream_t s, mg_stats* out);
+int default_blocks_1d(const mg_handle_s* h, size_t n);
+}  // namespace npmg

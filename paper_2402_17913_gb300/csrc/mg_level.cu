@@ -1,0 +1,231 @@
+// Level kernels of the multigrid cycle (Sec. 2.2): launchers and the
+// single-pass building blocks used by the per-kernel entry points.
+#include "launch.h"
+#include "mg_kernels.cuh"
+
+namespace npmg {
+
+template <int DIM>
+static dim3 tile_grid(const LevelDev& L) {
+  using TS = TileShape<DIM>;
+  return dim3((L.nx + TS::X - 1) / TS::X, (L.ny + TS::Y - 1) / TS::Y, DIM == 3 ? (L.nz + TS::Z - 1) / TS::Z : 1);
+}
+
+template <int DIM>
+static size_t tile_smem(int halo) {
+  using TS = TileShape<DIM>;
+  const int h = halo > 0 ? halo : 1;
+  const size_t R = (size_t)(TS::X + 2 * h) * (TS::Y + 2 * h) * (DIM == 3 ? TS::Z + 2 * h : 1);
+  return 3 * R * sizeof(float) + ((R + 15) & ~size_t(15));
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  // always opt in: static shared memory of the reductions adds to `bytes`
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Two sweeps (the default) use the compile-time-halo instantiation.
+template <int DIM, typename T, bool MASKED>
+cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,
+                        const SolveState* st, cudaStream_t s) {
+  const size_t sm = tile_smem<DIM>(pre);
+  if (pre == 2)
+    k_down<DIM, 2, T, MASKED><<<tile_grid<DIM>(L), kThreads, sm, s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, pre,
+                                                                       omega, st);
+  else
+    k_down<DIM, 0, T, MASKED><<<tile_grid<DIM>(L), kThreads, sm, s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, pre,
+                                                                       omega, st);
+  return cudaGetLastError();
+}
+
+template <int DIM, typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, int post,
+                      float omega, float sc, SolveState* st, double* partials, cudaStream_t s) {
+  const size_t sm = tile_smem<DIM>(post);
+  if (post == 2)
+    k_up<DIM, 2, T, MASKED, FINEST><<<tile_grid<DIM>(L), kThreads, sm, s>>>(
+        L, (const T*)b, (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
+  else
+    k_up<DIM, 0, T, MASKED, FINEST><<<tile_grid<DIM>(L), kThreads, sm, s>>>(
+        L, (const T*)b, (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
+  return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of the level kernels once (at
+// create, outside any stream capture).
+template <int DIM, typename T, bool MASKED>
+cudaError_t prepare_level_kernels(int pre, int post) {
+  cudaError_t e = allow_smem(k_down<DIM, 2, T, MASKED>, tile_smem<DIM>(pre));
+  if (e == cudaSuccess) e = allow_smem(k_down<DIM, 0, T, MASKED>, tile_smem<DIM>(pre));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, false>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, true>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, false>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, true>, tile_smem<DIM>(post));
+  return e;
+}
+
+#define NPMG_INST_LEVEL(DIM, T, M)                                                                           \
+  template cudaError_t prepare_level_kernels<DIM, T, M>(int, int);                                            \
+  template cudaError_t launch_down<DIM, T, M>(const LevelDev&, const void*, void*, void*, int, float,          \
+                                              const SolveState*, cudaStream_t);                                \
+  template cudaError_t launch_up<DIM, T, M, false>(const LevelDev&, const void*, const void*, void*,          \
+                                                   const void*, int, float, float, SolveState*, double*,       \
+                                                   cudaStream_t);                                              \
+  template cudaError_t launch_up<DIM, T, M, true>(const LevelDev&, const void*, const void*, void*,           \
+                                                  const void*, int, float, float, SolveState*, double*,        \
+                                                  cudaStream_t);
+
+NPMG_INST_LEVEL(2, float, false)
+NPMG_INST_LEVEL(2, float, true)
+NPMG_INST_LEVEL(3, float, false)
+NPMG_INST_LEVEL(3, float, true)
+NPMG_INST_LEVEL(2, __half, false)
+NPMG_INST_LEVEL(2, __half, true)
+NPMG_INST_LEVEL(3, __half, false)
+NPMG_INST_LEVEL(3, __half, true)
+NPMG_INST_LEVEL(2, __nv_bfloat16, false)
+NPMG_INST_LEVEL(2, __nv_bfloat16, true)
+NPMG_INST_LEVEL(3, __nv_bfloat16, false)
+NPMG_INST_LEVEL(3, __nv_bfloat16, true)
+
+// ---------------------------------------------------------------------------
+// Single-pass building blocks (float32), one thread per cell.
+template <int DIM>
+__device__ __forceinline__ bool cell_coords(const LevelDev& L, size_t i, int& x, int& y, int& z) {
+  x = (int)(i % L.nx);
+  const size_t t = i / L.nx;
+  y = (int)(t % L.ny);
+  z = (int)(t / L.ny);
+  return true;
+}
+
+template <int DIM, bool MASKED>
+__device__ __forceinline__ float apply_at(const LevelDev& L, const float* __restrict__ x, size_t i, int cx, int cy,
+                                          int cz, uint8_t m) {
+  const float d = diag_at<DIM, MASKED>(L, cx, cy, cz, m);
+  float nb = 0.f;
+  if (cx > 0) nb += L.wx * x[i - 1];
+  if (cx < L.nx - 1) nb += L.wx * x[i + 1];
+  if (cy > 0) nb += L.wy * x[i - L.nx];
+  if (cy < L.ny - 1) nb += L.wy * x[i + L.nx];
+  if (DIM == 3) {
+    const size_t sxy = (size_t)L.nx * L.ny;
+    if (cz > 0) nb += L.wz * x[i - sxy];
+    if (cz < L.nz - 1) nb += L.wz * x[i + sxy];
+  }
+  return d * x[i] - nb;
+}
+
+template <int DIM, bool MASKED>
+__global__ void k_apply(LevelDev L, const float* __restrict__ x, float* __restrict__ y) {
+  const size_t n = (size_t)L.nx * L.ny * L.nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int cx, cy, cz;
+    cell_coords<DIM>(L, i, cx, cy, cz);
+    const uint8_t m = MASKED ? L.cell[i] : kFluidBit;
+    y[i] = m ? apply_at<DIM, MASKED>(L, x, i, cx, cy, cz, m) : 0.f;
+  }
+}
+
+template <int DIM, bool MASKED>
+__global__ void k_smooth_once(LevelDev L, const float* __restrict__ x, float* __restrict__ y,
+                              const float* __restrict__ b, float omega) {
+  const size_t n = (size_t)L.nx * L.ny * L.nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int cx, cy, cz;
+    cell_coords<DIM>(L, i, cx, cy, cz);
+    const uint8_t m = MASKED ? L.cell[i] : kFluidBit;
+    float v = 0.f;
+    if (m) {
+      const float d = diag_at<DIM, MASKED>(L, cx, cy, cz, m);
+      v = x[i] + omega * (b[i] - apply_at<DIM, MASKED>(L, x, i, cx, cy, cz, m)) / d;
+    }
+    y[i] = v;
+  }
+}
+
+template <int DIM, bool MASKED>
+__global__ void k_restrict_residual(LevelDev L, const float* __restrict__ x, const float* __restrict__ b,
+                                    float* __restrict__ bc) {
+  const int cnx = L.nx / 2, cny = L.ny / 2, cnz = DIM == 3 ? L.nz / 2 : 1;
+  const size_t n = (size_t)cnx * cny * cnz;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+    const int X = (int)(j % cnx);
+    const size_t t = j / cnx;
+    const int Y = (int)(t % cny);
+    const int Z = (int)(t / cny);
+    float sum = 0.f;
+    for (int az = 0; az < (DIM == 3 ? 2 : 1); ++az)
+      for (int ay = 0; ay < 2; ++ay)
+        for (int ax = 0; ax < 2; ++ax) {
+          const int cx = 2 * X + ax, cy = 2 * Y + ay, cz = DIM == 3 ? 2 * Z + az : 0;
+          const size_t i = gidx(L, cx, cy, cz);
+          const uint8_t m = MASKED ? L.cell[i] : kFluidBit;
+          if (m) sum += b[i] - apply_at<DIM, MASKED>(L, x, i, cx, cy, cz, m);
+        }
+    bc[j] = sum * (DIM == 3 ? 0.125f : 0.25f);
+  }
+}
+
+template <int DIM, bool MASKED>
+__global__ void k_prolong_correct(LevelDev L, const float* __restrict__ e, float* __restrict__ x, float sc) {
+  const size_t n = (size_t)L.nx * L.ny * L.nz;
+  const int cnx = L.nx / 2, cny = L.ny / 2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    int cx, cy, cz;
+    cell_coords<DIM>(L, i, cx, cy, cz);
+    const uint8_t m = MASKED ? L.cell[i] : kFluidBit;
+    if (!m) {
+      x[i] = 0.f;
+      continue;
+    }
+    const size_t ci = ((size_t)(cz >> 1) * cny + (cy >> 1)) * cnx + (cx >> 1);
+    x[i] += sc * e[ci];
+  }
+}
+
+static int blocks_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <int DIM, bool MASKED>
+cudaError_t launch_apply(const LevelDev& L, const float* x, float* y, cudaStream_t s) {
+  k_apply<DIM, MASKED><<<blocks_for((size_t)L.nx * L.ny * L.nz), 256, 0, s>>>(L, x, y);
+  return cudaGetLastError();
+}
+template <int DIM, bool MASKED>
+cudaError_t launch_smooth_once(const LevelDev& L, const float* x, float* y, const float* b, float omega,
+                               cudaStream_t s) {
+  k_smooth_once<DIM, MASKED><<<blocks_for((size_t)L.nx * L.ny * L.nz), 256, 0, s>>>(L, x, y, b, omega);
+  return cudaGetLastError();
+}
+template <int DIM, bool MASKED>
+cudaError_t launch_restrict_residual(const LevelDev& L, const float* x, const float* b, float* bc, cudaStream_t s) {
+  k_restrict_residual<DIM, MASKED><<<blocks_for((size_t)L.nx * L.ny * L.nz / (DIM == 3 ? 8 : 4)), 256, 0, s>>>(
+      L, x, b, bc);
+  return cudaGetLastError();
+}
+template <int DIM, bool MASKED>
+cudaError_t launch_prolong_correct(const LevelDev& L, const float* e, float* x, float sc, cudaStream_t s) {
+  k_prolong_correct<DIM, MASKED><<<blocks_for((size_t)L.nx * L.ny * L.nz), 256, 0, s>>>(L, e, x, sc);
+  return cudaGetLastError();
+}
+
+#define NPMG_INST_BB(DIM, M)                                                                                  \
+  template cudaError_t launch_apply<DIM, M>(const LevelDev&, const float*, float*, cudaStream_t);             \
+  template cudaError_t launch_smooth_once<DIM, M>(const LevelDev&, const float*, float*, const float*, float, \
+                                                  cudaStream_t);                                              \
+  template cudaError_t launch_restrict_residual<DIM, M>(const LevelDev&, const float*, const float*, float*,  \
+                                                        cudaStream_t);                                        \
+  template cudaError_t launch_prolong_correct<DIM, M>(const LevelDev&, const float*, float*, float, cudaStream_t);
+
+NPMG_INST_BB(2, false)
+NPMG_INST_BB(2, true)
+NPMG_INST_BB(3, false)
+NPMG_INST_BB(3, true)
+
+}  // namespace npmg

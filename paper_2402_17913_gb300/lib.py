@@ -1,0 +1,259 @@
+"""ctypes binding of ``libnpmg.so`` (declarations in ``include/npmg.h``).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name.  Device arrays are passed as torch CUDA tensors (or raw
+integer pointers); streams default to torch's current stream.  There is no
+fallback: if the library is missing, ``load()`` raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnpmg.so")
+
+MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_NOT_CONVERGED, MG_DIVERGED, MG_TIMEOUT = range(7)
+MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1
+MG_FP32, MG_MIXED_FP16, MG_MIXED_BF16 = 0, 1, 2
+
+STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
+                4: "MG_NOT_CONVERGED", 5: "MG_DIVERGED", 6: "MG_TIMEOUT"}
+
+EXPORTED = [
+    "mg_default_options", "mg_last_error", "mg_create", "mg_solve", "mg_get_solution_f64",
+    "mg_level_shape", "mg_num_levels", "mg_apply_operator", "mg_smooth", "mg_residual_restrict",
+    "mg_prolong_correct", "mg_precondition", "mg_destroy", "ns_create", "ns_step", "ns_momentum",
+    "ns_divergence_rhs", "ns_correct", "ns_pressure_handle", "ns_destroy",
+    "mg_profile_enable", "mg_profile_read", "mg_kernel_launches",
+]
+KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
+                  "init_finish", "momentum", "divergence", "correct"]
+
+
+class MgOptions(ctypes.Structure):
+    _fields_ = [("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
+                ("coarse_scale", ctypes.c_double), ("levels", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("prec", ctypes.c_int),
+                ("inner_floor", ctypes.c_double)]
+
+
+class MgStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int),
+                ("levels", ctypes.c_int), ("relres0", ctypes.c_double), ("relres", ctypes.c_double),
+                ("bnorm", ctypes.c_double), ("ms", ctypes.c_float), ("history", ctypes.c_double * 32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "history"}
+        d["history"] = [self.history[i] for i in range(min(self.outer + 1, 32))]
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64_3 = ctypes.c_int64 * 3
+_d3 = ctypes.c_double * 3
+_i6 = ctypes.c_int * 6
+
+
+def load():
+    """Load the library (built by ``paper_2402_17913_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libnpmg.so is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "mg_default_options": (None, [ctypes.POINTER(MgOptions)]),
+        "mg_last_error": (ctypes.c_char_p, []),
+        "mg_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64_3, _d3, _i6, _vp,
+                                     ctypes.POINTER(MgOptions), _vp]),
+        "mg_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, ctypes.POINTER(MgStats)]),
+        "mg_get_solution_f64": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mg_level_shape": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3]),
+        "mg_num_levels": (ctypes.c_int, [_vp]),
+        "mg_apply_operator": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+        "mg_smooth": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
+        "mg_residual_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+        "mg_prolong_correct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+        "mg_precondition": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "mg_destroy": (ctypes.c_int, [_vp]),
+        "ns_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64_3, ctypes.c_double, _vp,
+                                     ctypes.c_double, ctypes.POINTER(MgOptions), _vp]),
+        "ns_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, _vp, ctypes.POINTER(MgStats)]),
+        "ns_momentum": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _vp]),
+        "ns_divergence_rhs": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp]),
+        "ns_correct": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _vp]),
+        "ns_pressure_handle": (_vp, [_vp]),
+        "ns_destroy": (ctypes.c_int, [_vp]),
+        "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "mg_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.c_int]),
+        "mg_kernel_launches": (ctypes.c_int64, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error():
+    return load().mg_last_error().decode()
+
+
+def _check(status, allow=(MG_OK,)):
+    if status not in allow:
+        raise MGError(status, last_error())
+    return status
+
+
+def ptr(t):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def default_options(**kw):
+    o = MgOptions()
+    load().mg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def mg_create(dim, shape, spacing, bc, solid=None, options=None, stream=None):
+    """Returns an mg_handle (int).  shape/spacing in (x, y[, z]) order."""
+    lib = load()
+    h = _vp()
+    shp = _i64_3(*(list(shape) + [1] * (3 - len(shape))))
+    sp = _d3(*(list(spacing) + [1.0] * (3 - len(spacing))))
+    b6 = _i6(*(list(bc) + [0] * (6 - len(bc))))
+    opt = options if options is not None else default_options()
+    _check(lib.mg_create(ctypes.byref(h), dim, shp, sp, b6, ptr(solid), ctypes.byref(opt), stream_ptr(stream)))
+    return h.value
+
+
+def mg_solve(h, b, x, rel_tol, stream=None, stats=True):
+    """Solve in place into x; returns (status, stats dict or None)."""
+    lib = load()
+    st = MgStats() if stats else None
+    status = lib.mg_solve(h, ptr(b), ptr(x), rel_tol, stream_ptr(stream), ctypes.byref(st) if stats else None)
+    _check(status, allow=(MG_OK, MG_NOT_CONVERGED, MG_DIVERGED))
+    return status, (st.as_dict() if stats else None)
+
+
+def mg_get_solution_f64(h, x64, stream=None):
+    _check(load().mg_get_solution_f64(h, ptr(x64), stream_ptr(stream)))
+
+
+def mg_num_levels(h):
+    return load().mg_num_levels(h)
+
+
+def mg_level_shape(h, k):
+    out = _i64_3()
+    _check(load().mg_level_shape(h, k, out))
+    return tuple(out)
+
+
+def mg_apply_operator(h, k, x, y, stream=None):
+    _check(load().mg_apply_operator(h, k, ptr(x), ptr(y), stream_ptr(stream)))
+
+
+def mg_smooth(h, k, x, b, sweeps, stream=None):
+    _check(load().mg_smooth(h, k, ptr(x), ptr(b), sweeps, stream_ptr(stream)))
+
+
+def mg_residual_restrict(h, k, x, b, bc, stream=None):
+    _check(load().mg_residual_restrict(h, k, ptr(x), ptr(b), ptr(bc), stream_ptr(stream)))
+
+
+def mg_prolong_correct(h, k, e, x, stream=None):
+    _check(load().mg_prolong_correct(h, k, ptr(e), ptr(x), stream_ptr(stream)))
+
+
+def mg_precondition(h, r, z, stream=None):
+    _check(load().mg_precondition(h, ptr(r), ptr(z), stream_ptr(stream)))
+
+
+def mg_destroy(h):
+    if h:
+        load().mg_destroy(h)
+
+
+def ns_create(dim, cells, h, solid=None, sigma=1e8, options=None, stream=None):
+    lib = load()
+    out = _vp()
+    c = _i64_3(*(list(cells) + [1] * (3 - len(cells))))
+    opt = options if options is not None else default_options()
+    _check(lib.ns_create(ctypes.byref(out), dim, c, h, ptr(solid), sigma, ctypes.byref(opt), stream_ptr(stream)))
+    return out.value
+
+
+def ns_step(ns, u, v, w, p, dt, nu, u_inflow, rel_tol, stream=None, stats=True):
+    lib = load()
+    st = MgStats() if stats else None
+    status = lib.ns_step(ns, ptr(u), ptr(v), ptr(w), ptr(p), dt, nu, u_inflow, rel_tol, stream_ptr(stream),
+                         ctypes.byref(st) if stats else None)
+    _check(status, allow=(MG_OK, MG_NOT_CONVERGED, MG_DIVERGED))
+    return status, (st.as_dict() if stats else None)
+
+
+def ns_momentum(ns, u, v, w, p, us, vs, ws, dt, nu, u_inflow, stream=None):
+    _check(load().ns_momentum(ns, ptr(u), ptr(v), ptr(w), ptr(p), ptr(us), ptr(vs), ptr(ws), dt, nu, u_inflow,
+                              stream_ptr(stream)))
+
+
+def ns_divergence_rhs(ns, us, vs, ws, dt, b, stream=None):
+    _check(load().ns_divergence_rhs(ns, ptr(us), ptr(vs), ptr(ws), dt, ptr(b), stream_ptr(stream)))
+
+
+def ns_correct(ns, u, v, w, p, dp, dt, stream=None):
+    _check(load().ns_correct(ns, ptr(u), ptr(v), ptr(w), ptr(p), ptr(dp), dt, stream_ptr(stream)))
+
+
+def ns_pressure_handle(ns):
+    return load().ns_pressure_handle(ns)
+
+
+def mg_profile_enable(h, on=True):
+    _check(load().mg_profile_enable(h, 1 if on else 0))
+
+
+def mg_profile_read(h, reset=True):
+    """{class: (ms, launches)} accumulated since the last reset."""
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(load().mg_profile_read(h, ms, cnt, 1 if reset else 0))
+    return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def mg_kernel_launches(h):
+    return load().mg_kernel_launches(h)
+
+
+def ns_destroy(ns):
+    if ns:
+        load().ns_destroy(ns)

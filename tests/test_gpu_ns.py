@@ -1,0 +1,126 @@
+"""GPU parity of the projection step (Algorithm 1 on a staggered grid)
+against the FP64 oracle, through the C ABI.  Single float32 passes are
+compared elementwise (tolerance a few float32 ulps of the field scale times
+the stencil's dt/h factors); full steps by relative L2 error, and by the
+divergence left after the projection."""
+import numpy as np
+import pytest
+
+from oracle import ns as N
+from paper_2402_17913_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2402_17913_gb300 import build, lib
+    build.build()
+    lib.load()
+    return lib
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+CASES = [((64, 32), 8, (16, 16)), ((48, 16, 16), 4, (12, 8, 8)), ((96, 32), 0, None)]
+
+
+def setup(L, cells, block, centre, seed=0):
+    solid = I.block_mask(cells, centre, block) if block else np.zeros(tuple(reversed(cells)), bool)
+    q = [a.astype(np.float32) for a in I.ns_initial_velocity(cells, seed, noise=0.05)]
+    rng = np.random.default_rng(seed + 1)
+    p = (0.1 * rng.standard_normal(solid.shape) * (~solid)).astype(np.float32)
+    ns = L.ns_create(len(cells), cells, 1.0, dev(solid.astype(np.uint8)) if block else None)
+    g = N.MacGrid(cells, 1.0, solid if block else None)
+    return ns, g, solid, q, p
+
+
+@pytest.mark.parametrize("cells,block,centre", CASES)
+def test_momentum_matches_oracle(L, cells, block, centre):
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        outs = [torch.zeros_like(a) for a in qd]
+        w = qd[2] if len(cells) == 3 else None
+        wo = outs[2] if len(cells) == 3 else None
+        L.ns_momentum(ns, qd[0], qd[1], w, dev(p), outs[0], outs[1], wo, 0.1, 0.64, 1.0)
+        ref = N.momentum(g, [a.astype(np.float64) for a in q], p.astype(np.float64), 0.1, 0.64, 1.0)
+        for c in range(len(cells)):
+            err = np.max(np.abs(outs[c].cpu().numpy() - ref[c]))
+            assert err <= 2e-6 * max(1.0, np.abs(ref[c]).max()), (c, err)
+    finally:
+        L.ns_destroy(ns)
+
+
+@pytest.mark.parametrize("cells,block,centre", CASES)
+def test_divergence_and_correction_match_oracle(L, cells, block, centre):
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        w = qd[2] if len(cells) == 3 else None
+        b = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
+        L.ns_divergence_rhs(ns, qd[0], qd[1], w, 0.1, b)
+        q64 = [a.astype(np.float64) for a in q]
+        ref = N.divergence_rhs(g, q64, 0.1)
+        assert np.max(np.abs(b.cpu().numpy() - ref)) <= 1e-5 * np.abs(ref).max()
+        rng = np.random.default_rng(9)
+        dp = (rng.standard_normal(solid.shape) * (~solid)).astype(np.float32)
+        pd = dev(p)
+        L.ns_correct(ns, qd[0], qd[1], w, pd, dev(dp), 0.1)
+        qr, pr = N.correct(g, q64, p.astype(np.float64), dp.astype(np.float64), 0.1)
+        for c in range(len(cells)):
+            assert np.max(np.abs(qd[c].cpu().numpy() - qr[c])) <= 1e-6 * max(1, np.abs(qr[c]).max())
+        assert np.max(np.abs(pd.cpu().numpy() - pr)) <= 1e-6 * np.abs(pr).max()
+    finally:
+        L.ns_destroy(ns)
+
+
+@pytest.mark.parametrize("cells,block,centre", CASES)
+def test_step_matches_oracle_and_is_divergence_free(L, cells, block, centre):
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        pd = dev(p)
+        w = qd[2] if len(cells) == 3 else None
+        status, st = L.ns_step(ns, qd[0], qd[1], w, pd, 0.1, 0.64, 1.0, 1e-6)
+        assert status == L.MG_OK, st
+        assert st["relres"] <= 1e-6
+        q64 = [a.astype(np.float64) for a in q]
+        qn, pn, dp, qs, b = N.ns_step(g, q64, p.astype(np.float64), 0.1, 0.64, 1.0)
+        for c in range(len(cells)):
+            e = np.linalg.norm(qd[c].cpu().numpy() - qn[c]) / np.linalg.norm(qn[c])
+            assert e <= 1e-5, (c, e)
+        e = np.linalg.norm(pd.cpu().numpy() - pn) / np.linalg.norm(pn)
+        assert e <= 1e-4, e
+        # divergence left by the GPU step, evaluated in float64 on its output
+        fl = ~solid
+        qg = [qd[c].cpu().numpy().astype(np.float64) for c in range(len(cells))]
+        d_new = np.linalg.norm(g.divergence(qg)[fl])
+        d_star = np.linalg.norm(g.divergence(qs)[fl])
+        # bound: the solve's relres plus float32 rounding of q (|q|~1, h=1)
+        bound = 10 * 1e-6 * d_star + 4 * 6e-8 * np.sqrt(fl.sum()) * 2
+        assert d_new <= bound, (d_new, d_star, bound)
+    finally:
+        L.ns_destroy(ns)
+
+
+def test_several_steps_track_oracle(L):
+    """Five steps of the 2D block case stay within 1e-4 of the oracle."""
+    cells, block, centre = (64, 32), 8, (16, 16)
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        pd = dev(p)
+        q64 = [a.astype(np.float64) for a in q]
+        p64 = p.astype(np.float64)
+        for _ in range(5):
+            L.ns_step(ns, qd[0], qd[1], None, pd, 0.1, 0.64, 1.0, 1e-6)
+            q64, p64, _, _, _ = N.ns_step(g, q64, p64, 0.1, 0.64, 1.0)
+        for c in range(2):
+            e = np.linalg.norm(qd[c].cpu().numpy() - q64[c]) / np.linalg.norm(q64[c])
+            assert e <= 1e-4, (c, e)
+    finally:
+        L.ns_destroy(ns)

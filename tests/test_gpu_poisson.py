@@ -1,0 +1,300 @@
+"""GPU parity of the multigrid Poisson path against the FP64 oracle, through
+the C ABI.  Tolerances: single float32 kernels are compared elementwise to
+~1e-5 of the field's scale (a few float32 ulps times the stencil growth);
+whole solves must reach relres <= 1e-6 (float64 iterate, checked here with
+the oracle's operator) and relative L2 error <= 1e-5 against x*."""
+import numpy as np
+import pytest
+
+from oracle import poisson as P
+from paper_2402_17913_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2402_17913_gb300 import build, lib
+    build.build()
+    lib.load()
+    return lib
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def np_shape(xyz):
+    return tuple(reversed(xyz))
+
+
+CASES = [
+    # (numpy shape [y,x] / [z,y,x], bc, solid fraction)
+    ((64, 64), (0, 0, 0, 0), 0.0),
+    ((48, 96), (1, 0, 1, 1), 0.08),        # ragged tiles along x, mixed BCs, masked
+    ((32, 32, 32), (0,) * 6, 0.0),
+    ((16, 24, 40), (1, 0, 1, 1, 0, 1), 0.06),
+]
+
+
+def make_case(shape, bc, frac, seed=5):
+    rng = np.random.default_rng(seed)
+    solid = None
+    if frac > 0:
+        solid = I.flood_fill_unreachable(rng.random(shape) < frac, bc)
+    h = tuple(1.0 / (s + 1) for s in reversed(shape))
+    return solid, h
+
+
+def create(L, shape, bc, solid, h, **opt):
+    o = L.default_options(**opt)
+    st = None if solid is None else dev(solid.astype(np.uint8))
+    hdl = L.mg_create(len(shape), tuple(reversed(shape)), h, bc, st, o)
+    return hdl
+
+
+@pytest.mark.parametrize("shape,bc,frac", CASES)
+def test_building_blocks_match_oracle(L, shape, bc, frac):
+    """Operator, Jacobi sweeps, residual+restriction and prolongation+
+    correction on every level, float32 vs the float64 oracle."""
+    solid, h = make_case(shape, bc, frac)
+    hdl = create(L, shape, bc, solid, h)
+    try:
+        nl = L.mg_num_levels(hdl)
+        hier = P.build_hierarchy(shape, h, bc, solid, levels=nl)
+        c = h[0] ** 2
+        rng = np.random.default_rng(11)
+        for k in range(nl):
+            lv = hier[k]
+            assert np_shape(L.mg_level_shape(hdl, k)[:len(shape)]) == lv.shape
+            x = (rng.standard_normal(lv.shape) * lv.fluid).astype(np.float32)
+            b = (rng.standard_normal(lv.shape) * lv.fluid).astype(np.float32)
+            x64, b64 = x.astype(np.float64), b.astype(np.float64)
+            # operator
+            y = torch.zeros(lv.shape, dtype=torch.float32, device="cuda")
+            L.mg_apply_operator(hdl, k, dev(x), y)
+            ref = c * P.apply_A(lv, x64)
+            scale = np.abs(c * lv.diag).max() * np.abs(x64).max()
+            assert np.max(np.abs(y.cpu().numpy() - ref)) <= 2e-6 * scale
+            # two Jacobi sweeps (A' x = b with b scaled like A')
+            bs = (b64 * np.abs(c * lv.diag).max()).astype(np.float32)
+            xt = dev(x)
+            L.mg_smooth(hdl, k, xt, dev(bs), 2)
+            ref = x64
+            for _ in range(2):
+                ref = P.jacobi(lv, ref, bs.astype(np.float64) / c, 2.0 / 3.0)
+            assert np.max(np.abs(xt.cpu().numpy() - ref)) <= 1e-5 * max(np.abs(ref).max(), 1.0)
+            if k + 1 < nl:
+                co = hier[k + 1]
+                bc_t = torch.zeros(co.shape, dtype=torch.float32, device="cuda")
+                L.mg_residual_restrict(hdl, k, dev(x), dev(bs), bc_t)
+                ref = P.restrict(P.residual(lv, bs.astype(np.float64) / c, x64)) * c
+                assert np.max(np.abs(bc_t.cpu().numpy() - ref)) <= 2e-6 * np.abs(bs).max() * 4
+                e = (rng.standard_normal(co.shape) * co.fluid).astype(np.float32)
+                xt = dev(x)
+                L.mg_prolong_correct(hdl, k, dev(e), xt)
+                ref = x64 * lv.fluid + 1.0 * P.prolong(e.astype(np.float64), lv)
+                assert np.max(np.abs(xt.cpu().numpy() - ref)) <= 1e-6 * (np.abs(ref).max() + 1)
+    finally:
+        L.mg_destroy(hdl)
+
+
+@pytest.mark.parametrize("shape,bc,frac", CASES)
+def test_one_cycle_matches_oracle(L, shape, bc, frac):
+    """One preconditioner cycle (V(2,2), omega 2/3, exact coarsest solve)
+    equals the oracle's cycle; the GPU works on A' = h_0x^2 A_h, so
+    z_gpu = z_oracle / h_0x^2."""
+    solid, h = make_case(shape, bc, frac)
+    hdl = create(L, shape, bc, solid, h)
+    try:
+        nl = L.mg_num_levels(hdl)
+        mg = P.Multigrid(P.build_hierarchy(shape, h, bc, solid, levels=nl), s=1.0)
+        r = I.blob_rhs(shape, 3, solid=solid).astype(np.float32)
+        z = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        L.mg_precondition(hdl, dev(r), z)
+        ref = mg.precondition(r.astype(np.float64)) / h[0] ** 2
+        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= 2e-5, err
+    finally:
+        L.mg_destroy(hdl)
+
+
+def solve_and_check(L, shape, bc, solid, h, b, tol=1e-6, relerr=1e-5, **opt):
+    hdl = create(L, shape, bc, solid, h, **opt)
+    try:
+        bt = dev(b)
+        xt = torch.zeros_like(bt)
+        status, st = L.mg_solve(hdl, bt, xt, tol)
+        x64 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        L.mg_get_solution_f64(hdl, x64)
+        x64 = x64.cpu().numpy()
+        x32 = xt.cpu().numpy()
+    finally:
+        L.mg_destroy(hdl)
+    assert status == L.MG_OK, st
+    lv = P.Level(shape, h, bc, solid)
+    b64 = b.astype(np.float64)
+    rr = P.relres(lv, b64, x64)
+    assert rr <= tol, (rr, st)
+    assert abs(rr - st["relres"]) <= 1e-3 * tol + 1e-3 * rr
+    xs = P.solve_reference(shape, h, bc, b64, solid, tol=1e-12, s=1.0)
+    e64 = np.linalg.norm(x64 - xs) / np.linalg.norm(xs)
+    e32 = np.linalg.norm(x32 - xs) / np.linalg.norm(xs)
+    assert e64 <= relerr and e32 <= relerr, (e64, e32)
+    assert np.all(x32[solid] == 0) if solid is not None else True
+    return st
+
+
+@pytest.mark.parametrize("shape,bc,frac", CASES)
+def test_solve_matches_oracle(L, shape, bc, frac):
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 0, solid=solid).astype(np.float32)
+    solve_and_check(L, shape, bc, solid, h, b)
+
+
+def test_solve_256_blob_iterations_match_oracle(L):
+    """256^2, zero Dirichlet, 8-blob RHS (seed 0), 7 levels: relres 1e-6;
+    the refinement loop takes the oracle's number of CG iterations (+-2)."""
+    shape = (256, 256)
+    h = I.poisson_spacing(shape)
+    b = I.blob_rhs(shape, 0).astype(np.float32)
+    st = solve_and_check(L, shape, (0, 0, 0, 0), None, h, b)
+    assert st["levels"] == 7
+    mg = P.Multigrid(P.build_hierarchy(shape, h, (0, 0, 0, 0)), s=1.0)
+    _, hist, inner = P.pcg_ir(mg, b.astype(np.float64), tol=1e-6, inner_floor=1e-4)
+    assert abs(st["iters"] - inner) <= 2, (st["iters"], inner)
+    assert st["outer"] == len(hist) - 1
+
+
+def test_manufactured_solution_second_order(L):
+    """The GPU solution of b = 2 pi^2 sin sin equals the closed form
+    (2 pi^2 / lambda_11) v_11 and converges at second order to sin sin."""
+    errs = []
+    for N in (64, 128, 256):
+        shape = (N, N)
+        h = I.poisson_spacing(shape)
+        b = I.manufactured_rhs(shape).astype(np.float32)
+        hdl = create(L, shape, (0, 0, 0, 0), None, h)
+        try:
+            bt = dev(b)
+            xt = torch.zeros_like(bt)
+            L.mg_solve(hdl, bt, xt, 1e-10)
+            x64 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+            L.mg_get_solution_f64(hdl, x64)
+            x64 = x64.cpu().numpy()
+        finally:
+            L.mg_destroy(hdl)
+        X = I.node_coords(shape)
+        v = np.sin(np.pi * X[0]) * np.sin(np.pi * X[1])
+        lam = 2 * 4 / h[0] ** 2 * np.sin(np.pi * h[0] / 2) ** 2
+        exact = 2 * np.pi ** 2 / lam * v
+        # the RHS was rounded to float32: error bound ~ 1e-7 relative
+        assert np.max(np.abs(x64 - exact)) <= 1e-6
+        errs.append(np.max(np.abs(x64 - v)))
+    assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_reaches_tolerance(L, prec):
+    """FP16 / BF16 inner storage with float64 refinement: same relres and
+    error bound as float32 (2D masked and 3D)."""
+    for shape, bc, frac in (CASES[1], CASES[2]):
+        solid, h = make_case(shape, bc, frac)
+        b = I.blob_rhs(shape, 1, solid=solid).astype(np.float32)
+        st = solve_and_check(L, shape, bc, solid, h, b, prec=prec)
+        assert st["outer"] >= 2
+
+
+def test_stationary_cycle_with_unscaled_correction_diverges(L):
+    """krylov = 0 with s = 1: the bare V-cycle diverges (oracle pin); the
+    device guard reports MG_DIVERGED instead of looping."""
+    shape = (256, 256)
+    h = I.poisson_spacing(shape)
+    b = dev(I.blob_rhs(shape, 0).astype(np.float32))
+    hdl = create(L, shape, (0, 0, 0, 0), None, h, krylov=0, coarse_scale=1.0)
+    try:
+        x = torch.zeros_like(b)
+        status, st = L.mg_solve(hdl, b, x, 1e-6)
+    finally:
+        L.mg_destroy(hdl)
+    assert status == L.MG_DIVERGED, st
+
+
+def test_stationary_cycle_with_scaled_correction_converges(L):
+    """krylov = 0 with s = 0.7 converges (oracle pin: < 0.5 after 6 cycles)."""
+    shape = (128, 128)
+    h = I.poisson_spacing(shape)
+    b = I.blob_rhs(shape, 0).astype(np.float32)
+    solve_and_check(L, shape, (0, 0, 0, 0), None, h, b, krylov=0, coarse_scale=0.7)
+
+
+def test_iteration_limit_reports_not_converged(L):
+    """max_inner = 2, max_outer = 1: MG_NOT_CONVERGED with the partial
+    iterate, whose relres equals the oracle's after two PCG iterations
+    (2.0499: the residual norm of MG-PCG may grow in early iterations)."""
+    shape = (128, 128)
+    h = I.poisson_spacing(shape)
+    b32 = I.blob_rhs(shape, 0).astype(np.float32)
+    b = dev(b32)
+    hdl = create(L, shape, (0, 0, 0, 0), None, h, max_inner=2, max_outer=1)
+    try:
+        x = torch.zeros_like(b)
+        status, st = L.mg_solve(hdl, b, x, 1e-6)
+    finally:
+        L.mg_destroy(hdl)
+    assert status == L.MG_NOT_CONVERGED
+    mg = P.Multigrid(P.build_hierarchy(shape, h, (0, 0, 0, 0)), s=1.0)
+    _, hist, _ = P.pcg(mg, b32.astype(np.float64), tol=1e-6, max_iters=2)
+    assert abs(st["relres"] - hist[-1]) <= 1e-4 * hist[-1], (st["relres"], hist)
+
+
+def test_zero_rhs_and_exact_guess(L):
+    shape = (64, 64)
+    h = I.poisson_spacing(shape)
+    hdl = create(L, shape, (0, 0, 0, 0), None, h)
+    try:
+        b = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        x = torch.ones_like(b)
+        status, st = L.mg_solve(hdl, b, x, 1e-6)
+        assert status == L.MG_OK and st["iters"] == 0
+        assert torch.count_nonzero(x).item() == 0
+    finally:
+        L.mg_destroy(hdl)
+
+
+def test_repeat_solves_are_deterministic(L):
+    shape = (128, 64)
+    solid, h = make_case(shape, (1, 0, 1, 1), 0.05)
+    b = dev(I.blob_rhs(shape, 4, solid=solid).astype(np.float32))
+    hdl = create(L, shape, (1, 0, 1, 1), solid, h)
+    try:
+        outs = []
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            L.mg_solve(hdl, b, x, 1e-6)
+            outs.append(x.clone())
+    finally:
+        L.mg_destroy(hdl)
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_misaligned_pointer_is_rejected_on_the_host(L):
+    """Vector loads need 16-byte aligned arrays: a view at a 4-byte offset
+    is rejected with MG_ERR_INVALID before anything is launched."""
+    shape = (64, 64)
+    h = I.poisson_spacing(shape)
+    hdl = create(L, shape, (0, 0, 0, 0), None, h)
+    try:
+        buf = torch.zeros(64 * 64 + 1, dtype=torch.float32, device="cuda")
+        b = buf[1:]
+        x = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        import ctypes
+        st = L.load().mg_solve(hdl, b.data_ptr(), x.data_ptr(), 1e-6, L.stream_ptr(), None)
+        assert st == L.MG_ERR_INVALID
+        assert "aligned" in L.last_error()
+    finally:
+        L.mg_destroy(hdl)

@@ -1,0 +1,81 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every entry point declared in include/npmg.h, and rejects invalid
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_17913_gb300 import build, lib as L
+    build.build()
+    return L.load()
+
+
+def declared_functions():
+    names = []
+    for path in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not path.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", path)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:mg|ns)_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2402_17913_gb300 import lib as L
+    assert sorted(L.EXPORTED) == declared_functions()
+
+
+def test_default_options(lib):
+    from paper_2402_17913_gb300 import lib as L
+    o = L.default_options()
+    assert (o.pre, o.post, o.krylov, o.levels, o.prec) == (2, 2, 1, 0, 0)
+    assert abs(o.omega - 2.0 / 3.0) < 1e-15 and o.coarse_scale == 1.0
+
+
+@pytest.mark.parametrize("dim,shape,bc,why", [
+    (4, (8, 8, 8), (0,) * 6, "dim"),
+    (2, (1, 8, 1), (0,) * 6, "shape"),
+    (2, (8, 8, 1), (0, 0, 7, 0, 0, 0), "bc"),
+    (2, (8, 8, 1), (1, 1, 1, 1, 0, 0), "singular"),
+])
+def test_create_rejects_invalid_arguments(lib, dim, shape, bc, why):
+    from paper_2402_17913_gb300 import lib as L
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 3)(*shape)
+    sp = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    b6 = (ctypes.c_int * 6)(*bc)
+    st = lib.mg_create(ctypes.byref(h), dim, shp, sp, b6, None, None, None)
+    assert st == L.MG_ERR_INVALID, why
+    assert h.value is None
+    assert len(lib.mg_last_error()) > 0
+
+
+def test_create_rejects_bad_options(lib):
+    from paper_2402_17913_gb300 import lib as L
+    o = L.default_options(pre=9)
+    h = ctypes.c_void_p()
+    st = lib.mg_create(ctypes.byref(h), 2, (ctypes.c_int64 * 3)(8, 8, 1), (ctypes.c_double * 3)(1, 1, 1),
+                       (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0), None, ctypes.byref(o), None)
+    assert st == L.MG_ERR_INVALID
+
+
+def test_solve_rejects_null(lib):
+    from paper_2402_17913_gb300 import lib as L
+    assert lib.mg_solve(None, None, None, 1e-6, None, None) == L.MG_ERR_INVALID
+    assert lib.ns_step(None, None, None, None, None, 0.1, 0.1, 1.0, 1e-6, None, None) == L.MG_ERR_INVALID
