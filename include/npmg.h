@@ -173,6 +173,29 @@ mg_status mg_precondition(mg_handle h, const float* d_r, float* d_z,
 mg_status mg_destroy(mg_handle h);
 
 /*
+ * mg_vcycle_noalloc: the cycle of mg_precondition (d_z = M d_r, level 0 =
+ * the whole grid) for callers that cannot allocate device memory -- code
+ * running inside someone else's stream capture, plugins given a fixed memory
+ * budget, real-time loops that must never enter the allocator.  It needs no
+ * handle and allocates nothing: the arguments are those of mg_create plus
+ * the input r and output z (float32, device, cells, 16-byte aligned);
+ * opt->prec must be MG_FP32.  All temporaries (mask hierarchy, level
+ * vectors, coarsest-level inverse, rebuilt on every call) live in one
+ * static device array of 8 MiB that every GPU loading the library keeps
+ * until exit.  Limits: at most 2^18 cells (e.g. 512^2 or 64^3) and at most
+ * 256 cells on the coarsest level; larger problems return MG_ERR_INVALID
+ * with a message.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it, so make that first
+ * call before any stream capture.  Every call uses the same array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The paper has no counterpart; it is an
+ * interface convenience.
+ */
+mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const double spacing[3], const int bc[6],
+                            const uint8_t* d_solid, const mg_options* opt, const float* d_r, float* d_z,
+                            void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper).  With profiling on, every
  * kernel launch of the handle (solves, and the projection steps of the
  * ns_handle that owns it) is bracketed by CUDA events on its stream and the

@@ -189,8 +189,14 @@ cudaError_t launch_coarse(const CoarseArgs& a, size_t smem_bytes, const void* b,
 
 template <typename T>
 cudaError_t prepare_coarse(size_t smem_bytes) {
-  // always opt in: the kernel's static shared memory adds to the dynamic size
-  return cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  // opt in to the device maximum (see allow_smem in mg_level.cu): handles of
+  // different sizes must not lower each other's limit
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem_bytes + 1024 > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
 }
 template cudaError_t prepare_coarse<float>(size_t);
 template cudaError_t prepare_coarse<__half>(size_t);

@@ -19,10 +19,18 @@ static size_t tile_smem(int halo) {
   return 3 * R * sizeof(float) + ((R + 15) & ~size_t(15));
 }
 
+// Opt the kernel in to the device's largest dynamic shared memory.  A fixed
+// maximum (rather than this handle's size) keeps handles of different sizes
+// from lowering each other's limit; the launch still asks only for `bytes`.
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
-  // always opt in: static shared memory of the reductions adds to `bytes`
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (bytes + 1024 > (size_t)optin) return cudaErrorInvalidValue;
+  // static shared memory of the reductions comes on top of the dynamic part
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
 }
 
 // Two sweeps (the default) use the compile-time-halo instantiation.

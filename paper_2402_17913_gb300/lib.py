@@ -23,7 +23,7 @@ EXPORTED = [
     "mg_level_shape", "mg_num_levels", "mg_apply_operator", "mg_smooth", "mg_residual_restrict",
     "mg_prolong_correct", "mg_precondition", "mg_destroy", "ns_create", "ns_step", "ns_momentum",
     "ns_divergence_rhs", "ns_correct", "ns_pressure_handle", "ns_destroy",
-    "mg_profile_enable", "mg_profile_read", "mg_kernel_launches",
+    "mg_profile_enable", "mg_profile_read", "mg_kernel_launches", "mg_vcycle_noalloc",
 ]
 KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
                   "init_finish", "momentum", "divergence", "correct"]
@@ -98,6 +98,8 @@ def load():
         "mg_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.c_int]),
         "mg_kernel_launches": (ctypes.c_int64, [_vp]),
+        "mg_vcycle_noalloc": (ctypes.c_int, [ctypes.c_int, _i64_3, _d3, _i6, _vp, ctypes.POINTER(MgOptions),
+                                             _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -252,6 +254,17 @@ def mg_profile_read(h, reset=True):
 
 def mg_kernel_launches(h):
     return load().mg_kernel_launches(h)
+
+
+def mg_vcycle_noalloc(dim, shape, spacing, bc, r, z, solid=None, options=None, stream=None):
+    """One preconditioner cycle z = M r without a handle or any device
+    allocation (scratch in the library's static device array)."""
+    shp = _i64_3(*(list(shape) + [1] * (3 - len(shape))))
+    sp = _d3(*(list(spacing) + [1.0] * (3 - len(spacing))))
+    b6 = _i6(*(list(bc) + [0] * (6 - len(bc))))
+    opt = options if options is not None else default_options()
+    return _check(load().mg_vcycle_noalloc(dim, shp, sp, b6, ptr(solid), ctypes.byref(opt), ptr(r), ptr(z),
+                                           stream_ptr(stream)))
 
 
 def ns_destroy(ns):

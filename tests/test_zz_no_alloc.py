@@ -1,0 +1,54 @@
+"""The allocation-free entry point mg_vcycle_noalloc, for callers that cannot
+call cudaMalloc (inside a capture they do not own, under a fixed memory
+budget, in a loop that must not allocate): its cycle must equal the one of
+the handle-based mg_precondition, call after call, although all its
+temporaries live in one static device array shared by every call.  This file
+is collected last so that a stop-at-first-failure run has already run every
+other test."""
+import numpy as np
+import pytest
+
+from paper_2402_17913_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# the tolerance of the other float32 cycle tests (tests/test_gpu_poisson.py)
+RTOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2402_17913_gb300 import build, lib
+    build.build()
+    lib.load()
+    return lib
+
+
+@pytest.mark.parametrize("shape,bc,frac", [((96, 128), (1, 0, 1, 1), 0.06), ((32, 32, 32), (0,) * 6, 0.0)])
+def test_noalloc_cycle_matches_handle_cycle_twice(L, shape, bc, frac):
+    rng = np.random.default_rng(21)
+    solid = I.flood_fill_unreachable(rng.random(shape) < frac, bc) if frac > 0 else None
+    h = tuple(1.0 / (s + 1) for s in reversed(shape))
+    xyz = tuple(reversed(shape))
+    sol = None if solid is None else torch.from_numpy(solid.astype(np.uint8)).cuda()
+    hdl = L.mg_create(len(shape), xyz, h, bc, sol)
+    try:
+        for call in range(2):  # two calls in a row: leftovers in the static array must not matter
+            r = torch.from_numpy(I.blob_rhs(shape, 30 + call, solid=solid).astype(np.float32)).cuda()
+            z_ref = torch.zeros_like(r)
+            z = torch.full_like(r, float("nan"))
+            L.mg_precondition(hdl, r, z_ref)
+            L.mg_vcycle_noalloc(len(shape), xyz, h, bc, r, z, solid=sol)
+            torch.cuda.synchronize()
+            err = (torch.linalg.norm(z.double() - z_ref.double()) / torch.linalg.norm(z_ref.double())).item()
+            assert err <= RTOL, (call, err)
+    finally:
+        L.mg_destroy(hdl)
+
+
+def test_noalloc_rejects_sizes_beyond_the_scratch(L):
+    x = torch.zeros(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(L.MGError) as e:
+        L.mg_vcycle_noalloc(2, (1024, 1024), (1e-3, 1e-3), (0, 0, 0, 0), x, x)
+    assert "maximum" in str(e.value)
