@@ -8,14 +8,20 @@ struct CoarseArgs {
   int nlev;                    // levels handled by the single-block kernel
   int dim;
   LevelDev lv[kMaxLevels];     // lv[0] = first level handled
-  int off[kMaxLevels];         // float offset of level l's arrays (x0, x1, b)
-  int moff[kMaxLevels];        // byte offset of level l's cell bytes
+  int off[kMaxLevels];         // float offset of level l's padded arrays (x, x', b, 1/diag)
   int ncoarse;                 // cells of the coarsest level
   const double* inv;           // inverse of the coarsest operator, column-major
+  const float* image;          // constant shared-memory image (zero rings, 1/diag), or nullptr
   int pre, post;
   float omega, s;
   int finest;                  // lv[0] is the finest level: reduce (r, z)
 };
+
+size_t coarse_layout(int* off, const LevelDev* lv, int nlev, int dim);
+// Write the constant part of the single-block kernel's shared memory (zero
+// ghost rings and arrays, inverse diagonals) to `image` (device).
+cudaError_t launch_coarse_image(const CoarseArgs& a, float* image, size_t bytes, cudaStream_t s);
+int coarse_start_level(const LevelDev* lv, int L, int dim, size_t smem_limit);
 
 template <int DIM, typename T, bool MASKED>
 cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,

@@ -89,16 +89,46 @@ __device__ __forceinline__ void cells4(const LevelDev& L, size_t i, int x0, uint
   }
 }
 
-__device__ __forceinline__ void row_thread(int& x0, int& y) {
-  x0 = (blockIdx.x * 32 + (threadIdx.x & 31)) * 4;
-  y = blockIdx.y * 8 + (threadIdx.x >> 5);
+// Row groups of 8 rows x 128 cells, walked grid-stride by a persistent grid
+// (a few blocks per SM), so that each block pays its reduction once.
+struct RowIter {
+  int g, G, gxn, gyn, x0, y, z;
+  bool active;
+  __device__ __forceinline__ explicit RowIter(const LevelDev& L) {
+    gxn = (L.nx + 127) / 128;
+    gyn = (L.ny + 7) / 8;
+    G = gxn * gyn * L.nz;
+    g = blockIdx.x;
+    set(L);
+  }
+  __device__ __forceinline__ void set(const LevelDev& L) {
+    if (g >= G) return;
+    const int gx = g % gxn, t = g / gxn, gy = t % gyn;
+    z = t / gyn;
+    x0 = gx * 128 + (threadIdx.x & 31) * 4;
+    y = gy * 8 + (threadIdx.x >> 5);
+    active = x0 < L.nx && y < L.ny;
+  }
+  __device__ __forceinline__ bool more() const { return g < G; }
+  __device__ __forceinline__ void next(const LevelDev& L) {
+    g += gridDim.x;
+    set(L);
+  }
+};
+
+static int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+  return n[dev] > 0 ? n[dev] : 148;
 }
 
 static dim3 row_grid(const LevelDev& L) {
-  const int gx = (L.nx + 127) / 128, gy = (L.ny + 7) / 8;
-  int gz = L.nz;
-  while ((long)gx * gy * gz > 16384 && gz > 1) gz = (gz + 1) / 2;
-  return dim3(gx, gy, gz);
+  const long groups = (long)((L.nx + 127) / 128) * ((L.ny + 7) / 8) * L.nz;
+  const long cap = (long)sm_count() * 4;
+  return dim3((unsigned)(groups < cap ? groups : cap), 1, 1);
 }
 
 __device__ __forceinline__ double pow2_floor(double v) {
@@ -143,6 +173,33 @@ __device__ __forceinline__ ff ff_mul(ff a, ff w) {
 // ---------------------------------------------------------------------------
 // CG: p = z + beta p ; Ap = A' p ; (p, Ap) -> alpha = (r, z) / (p, Ap).
 // p is double-buffered (pold -> pnew) because Ap needs p at neighbours.
+// Neighbour addresses of a 4-cell group, clamped into the array so that
+// every load can be issued up front; the flags zero the missing neighbours.
+struct Nbr {
+  size_t i, il, ir, iu, id, ib, iF;
+  bool hl, hr, hu, hd, hb, hf;
+};
+
+template <int DIM>
+__device__ __forceinline__ Nbr neighbours(const LevelDev& L, int x0, int y, int zz) {
+  Nbr n;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  n.i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
+  n.hl = x0 > 0;
+  n.hr = x0 + 4 < L.nx;
+  n.hu = y > 0;
+  n.hd = y < L.ny - 1;
+  n.hb = DIM == 3 && zz > 0;
+  n.hf = DIM == 3 && zz < L.nz - 1;
+  n.il = n.hl ? n.i - 1 : n.i;
+  n.ir = n.hr ? n.i + 4 : n.i;
+  n.iu = n.hu ? n.i - L.nx : n.i;
+  n.id = n.hd ? n.i + L.nx : n.i;
+  n.ib = n.hb ? n.i - sxy : n.i;
+  n.iF = n.hf ? n.i + sxy : n.i;
+  return n;
+}
+
 template <int DIM, typename T, bool MASKED>
 __global__ void __launch_bounds__(256) k_p_update(LevelDev L, const T* __restrict__ z, const T* __restrict__ pold,
                                                   T* __restrict__ pnew, T* __restrict__ Ap,
@@ -150,59 +207,57 @@ __global__ void __launch_bounds__(256) k_p_update(LevelDev L, const T* __restric
   if (st->inner_done) return;
   const bool first = st->first || !st->krylov;
   const float beta = first ? 0.f : (float)st->beta;
-  int x0, y;
-  row_thread(x0, y);
+
   float acc = 0.f;
-  const size_t sxy = (size_t)L.nx * L.ny;
-  auto pvec = [&](size_t j, float out[4]) {
-    ld4(z, j, x0, L.nx, out);
-    if (!first) {
-      float t[4];
-      ld4(pold, j, x0, L.nx, t);
+  for (RowIter it(L); it.more(); it.next(L)) {
+    if (!it.active) continue;
+    const int x0 = it.x0, y = it.y, zz = it.z;
+    {
+      const Nbr n = neighbours<DIM>(L, x0, y, zz);
+      // all loads first
+      float zc[4], zu[4], zd[4], zb[4], zf[4], qc[4], qu[4], qd[4], qb[4], qf[4];
+      ld4(z, n.i, x0, L.nx, zc);
+      ld4(z, n.iu, x0, L.nx, zu);
+      ld4(z, n.id, x0, L.nx, zd);
+      float zl = ld(z, n.il), zr = ld(z, n.ir), ql = 0.f, qr = 0.f;
+      if (DIM == 3) {
+        ld4(z, n.ib, x0, L.nx, zb);
+        ld4(z, n.iF, x0, L.nx, zf);
+      }
+      if (!first) {
+        ld4(pold, n.i, x0, L.nx, qc);
+        ld4(pold, n.iu, x0, L.nx, qu);
+        ld4(pold, n.id, x0, L.nx, qd);
+        ql = ld(pold, n.il);
+        qr = ld(pold, n.ir);
+        if (DIM == 3) {
+          ld4(pold, n.ib, x0, L.nx, qb);
+          ld4(pold, n.iF, x0, L.nx, qf);
+        }
+      }
+      uint8_t m[4];
+      cells4<MASKED>(L, n.i, x0, m);
+      // p = z + beta p_old at the group and its neighbours
+      float pc[4], nb[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) out[k] = fmaf(beta, t[k], out[k]);
-    }
-  };
-  auto psc = [&](size_t j) {
-    float v = ld(z, j);
-    if (!first) v = fmaf(beta, ld(pold, j), v);
-    return v;
-  };
-  if (x0 < L.nx && y < L.ny) {
-    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
-      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
-      float pc[4], nb[4], t[4];
-      pvec(i, pc);
-      const float pl = x0 > 0 ? psc(i - 1) : 0.f;
-      const float pr = x0 + 4 < L.nx ? psc(i + 4) : 0.f;
+      for (int k = 0; k < 4; ++k) pc[k] = first ? zc[k] : fmaf(beta, qc[k], zc[k]);
+      const float pl = n.hl ? (first ? zl : fmaf(beta, ql, zl)) : 0.f;
+      const float pr = n.hr ? (first ? zr : fmaf(beta, qr, zr)) : 0.f;
       nb[0] = L.wx * (pl + pc[1]);
       nb[1] = L.wx * (pc[0] + pc[2]);
       nb[2] = L.wx * (pc[1] + pc[3]);
       nb[3] = L.wx * (pc[2] + pr);
-      if (y > 0) {
-        pvec(i - L.nx, t);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wy, t[k], nb[k]);
-      }
-      if (y < L.ny - 1) {
-        pvec(i + L.nx, t);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wy, t[k], nb[k]);
-      }
-      if (DIM == 3) {
-        if (zz > 0) {
-          pvec(i - sxy, t);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wz, t[k], nb[k]);
-        }
-        if (zz < L.nz - 1) {
-          pvec(i + sxy, t);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) nb[k] = fmaf(L.wz, t[k], nb[k]);
+      for (int k = 0; k < 4; ++k) {
+        const float pu = n.hu ? (first ? zu[k] : fmaf(beta, qu[k], zu[k])) : 0.f;
+        const float pd = n.hd ? (first ? zd[k] : fmaf(beta, qd[k], zd[k])) : 0.f;
+        nb[k] = fmaf(L.wy, pu + pd, nb[k]);
+        if (DIM == 3) {
+          const float pb = n.hb ? (first ? zb[k] : fmaf(beta, qb[k], zb[k])) : 0.f;
+          const float pf = n.hf ? (first ? zf[k] : fmaf(beta, qf[k], zf[k])) : 0.f;
+          nb[k] = fmaf(L.wz, pb + pf, nb[k]);
         }
       }
-      uint8_t m[4];
-      cells4<MASKED>(L, i, x0, m);
       float ap[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -214,8 +269,8 @@ __global__ void __launch_bounds__(256) k_p_update(LevelDev L, const T* __restric
         }
         acc = fmaf(rnd<T>(pc[k]), rnd<T>(ap[k]), acc);
       }
-      st4(pnew, i, x0, L.nx, pc);
-      st4(Ap, i, x0, L.nx, ap);
+      st4(pnew, n.i, x0, L.nx, pc);
+      st4(Ap, n.i, x0, L.nx, ap);
     }
   }
   double tot;
@@ -235,12 +290,13 @@ __global__ void __launch_bounds__(256) k_xr_update(LevelDev L, const T* __restri
   if (st->inner_done) return;
   const float alpha = (float)st->alpha;
   const bool first = st->first;
-  int x0, y;
-  row_thread(x0, y);
+
   float acc = 0.f;
   const size_t sxy = (size_t)L.nx * L.ny;
-  if (x0 < L.nx && y < L.ny) {
-    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+  for (RowIter it(L); it.more(); it.next(L)) {
+    if (!it.active) continue;
+    const int x0 = it.x0, y = it.y, zz = it.z;
+    {
       const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
       float pv[4], av[4], dv[4], rv[4];
       ld4(p, i, x0, L.nx, pv);
@@ -320,32 +376,64 @@ __global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const f
   if (UPDATE) sig_new_d = pow2_floor(sig_old_d * sqrt(fmax(st->rnorm2, 1e-300) / (double)st->n_fluid));
   const float sig_old = (float)sig_old_d;
   const float inv_sig_new = (float)(1.0 / sig_new_d);
-  int x0, y;
-  row_thread(x0, y);
+
   float acc = 0.f;
-  const size_t sxy = (size_t)L.nx * L.ny;
-  auto xv = [&](size_t j) -> ff {
-    const float2 q = xin[j];
+  auto upd = [&](float2 q, float dv) -> ff {
     if (!UPDATE) return {q.x, q.y};
-    const ff s = two_sum(q.x, sig_old * ld(dprime, j));
+    const ff s = two_sum(q.x, sig_old * dv);
     return quick_two_sum(s.hi, s.lo + q.y);
   };
-  if (x0 < L.nx && y < L.ny) {
-    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
-      const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
-      uint8_t m[4];
-      cells4<MASKED>(L, i, x0, m);
-      ff xc[6];  // x0-1 .. x0+4
-      xc[0] = x0 > 0 ? xv(i - 1) : ff{0.f, 0.f};
+  for (RowIter it(L); it.more(); it.next(L)) {
+    if (!it.active) continue;
+    const int x0 = it.x0, y = it.y, zz = it.z;
+    {
+      const Nbr n = neighbours<DIM>(L, x0, y, zz);
+      const bool vec = (L.nx & 3) == 0;
+      // all loads first (x as float2 pairs, d' at the same places)
+      float2 qc[4], qu[4], qd[4], qb[4], qf[4];
+      float dc[4], du[4], dd[4], db[4], df[4], bv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) xc[k + 1] = (x0 + k < L.nx) ? xv(i + k) : ff{0.f, 0.f};
-      xc[5] = x0 + 4 < L.nx ? xv(i + 4) : ff{0.f, 0.f};
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = vec || x0 + k < L.nx;
+        qc[k] = ok ? xin[n.i + k] : make_float2(0.f, 0.f);
+        qu[k] = ok ? xin[n.iu + k] : make_float2(0.f, 0.f);
+        qd[k] = ok ? xin[n.id + k] : make_float2(0.f, 0.f);
+        if (DIM == 3) {
+          qb[k] = ok ? xin[n.ib + k] : make_float2(0.f, 0.f);
+          qf[k] = ok ? xin[n.iF + k] : make_float2(0.f, 0.f);
+        }
+      }
+      const float2 ql = xin[n.il], qr = xin[n.ir];
+      float dl = 0.f, dr = 0.f;
+      if (UPDATE) {
+        ld4(dprime, n.i, x0, L.nx, dc);
+        ld4(dprime, n.iu, x0, L.nx, du);
+        ld4(dprime, n.id, x0, L.nx, dd);
+        if (DIM == 3) {
+          ld4(dprime, n.ib, x0, L.nx, db);
+          ld4(dprime, n.iF, x0, L.nx, df);
+        }
+        dl = ld(dprime, n.il);
+        dr = ld(dprime, n.ir);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dc[k] = du[k] = dd[k] = db[k] = df[k] = 0.f;
+      }
+      ld4(b, n.i, x0, L.nx, bv);
+      uint8_t m[4];
+      cells4<MASKED>(L, n.i, x0, m);
+      const ff zero = {0.f, 0.f};
+      ff xc[6];  // x0-1 .. x0+4
+      xc[0] = n.hl ? upd(ql, dl) : zero;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xc[k + 1] = upd(qc[k], dc[k]);
+      xc[5] = n.hr ? upd(qr, dr) : zero;
       float rv[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         rv[k] = 0.f;
         if (!m[k]) {
-          if (UPDATE && x0 + k < L.nx) xout[i + k] = make_float2(0.f, 0.f);
+          if (UPDATE && (vec || x0 + k < L.nx)) xout[n.i + k] = make_float2(0.f, 0.f);
           continue;
         }
         const int cx = x0 + k;
@@ -359,27 +447,27 @@ __global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const f
           ky = axis_count(y, L.ny, L.bcD, 2);
           if (DIM == 3) kz = axis_count(zz, L.nz, L.bcD, 4);
         }
-        // A' x = sum_a w_a (k_a x_c - x_left - x_right)
+        // A' x = sum_a w_a (k_a x_c - x_minus - x_plus)
         ff ax = ff_mul(ff_add(ff_mul(xc[k + 1], ff{(float)kx, 0.f}), ff_neg(ff_add(xc[k], xc[k + 2]))), oa.w[0]);
         {
-          ff s = ff_mul(xc[k + 1], ff{(float)ky, 0.f});
-          if (y > 0) s = ff_add(s, ff_neg(xv(i + k - L.nx)));
-          if (y < L.ny - 1) s = ff_add(s, ff_neg(xv(i + k + L.nx)));
-          ax = ff_add(ax, ff_mul(s, oa.w[1]));
+          ff sy = ff_mul(xc[k + 1], ff{(float)ky, 0.f});
+          if (n.hu) sy = ff_add(sy, ff_neg(upd(qu[k], du[k])));
+          if (n.hd) sy = ff_add(sy, ff_neg(upd(qd[k], dd[k])));
+          ax = ff_add(ax, ff_mul(sy, oa.w[1]));
         }
         if (DIM == 3) {
-          ff s = ff_mul(xc[k + 1], ff{(float)kz, 0.f});
-          if (zz > 0) s = ff_add(s, ff_neg(xv(i + k - sxy)));
-          if (zz < L.nz - 1) s = ff_add(s, ff_neg(xv(i + k + sxy)));
-          ax = ff_add(ax, ff_mul(s, oa.w[2]));
+          ff sz = ff_mul(xc[k + 1], ff{(float)kz, 0.f});
+          if (n.hb) sz = ff_add(sz, ff_neg(upd(qb[k], db[k])));
+          if (n.hf) sz = ff_add(sz, ff_neg(upd(qf[k], df[k])));
+          ax = ff_add(ax, ff_mul(sz, oa.w[2]));
         }
-        const ff r = ff_add(ff_mul(ff{b[i + k], 0.f}, oa.c), ff_neg(ax));
+        const ff r = ff_add(ff_mul(ff{bv[k], 0.f}, oa.c), ff_neg(ax));
         const float rs = r.hi + r.lo;
         rv[k] = rs * inv_sig_new;
         acc = fmaf(rs, rs, acc);
-        if (UPDATE) xout[i + k] = make_float2(xc[k + 1].hi, xc[k + 1].lo);
+        if (UPDATE) xout[n.i + k] = make_float2(xc[k + 1].hi, xc[k + 1].lo);
       }
-      st4(rprime, i, x0, L.nx, rv);
+      st4(rprime, n.i, x0, L.nx, rv);
     }
   }
   double tot;
@@ -481,12 +569,13 @@ template cudaError_t launch_xr_update<__nv_bfloat16>(const LevelDev&, const void
 __global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restrict__ b, const float* __restrict__ xg,
                                               float2* __restrict__ x, double c, SolveParams prm,
                                               SolveState* __restrict__ st, double* __restrict__ partials) {
-  int x0, y;
-  row_thread(x0, y);
+
   float acc = 0.f;
   const size_t sxy = (size_t)L.nx * L.ny;
-  if (x0 < L.nx && y < L.ny) {
-    for (int zz = blockIdx.z; zz < L.nz; zz += gridDim.z) {
+  for (RowIter it(L); it.more(); it.next(L)) {
+    if (!it.active) continue;
+    const int x0 = it.x0, y = it.y, zz = it.z;
+    {
       const size_t i = (size_t)zz * sxy + (size_t)y * L.nx + x0;
       uint8_t m[4];
       if (L.cell) ld4_cell(L.cell, i, x0, L.nx, m);

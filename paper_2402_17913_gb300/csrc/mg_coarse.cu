@@ -3,6 +3,7 @@
 
 #include "launch.h"
 #include "mg_kernels.cuh"
+#include "tma.cuh"
 
 namespace npmg {
 
@@ -16,158 +17,263 @@ static int grid_1d(size_t n, int cap) {
 // ---------------------------------------------------------------------------
 // Below a few thousand cells a level is too small to fill the GPU, so the
 // remaining part of the cycle (down legs, the exact coarsest solve, up
-// legs) runs inside one block of 1024 threads with every level, and its
-// cell bytes, resident in shared memory.  The coarsest level is solved
-// exactly: its operator is inverted once at create (float64 Gauss-Jordan)
-// and applied here as a float64 matrix-vector product, one warp per row.
-struct CLevel {
-  LevelDev L;
-  const uint8_t* m;  // cell bytes in shared memory (nullptr: unmasked)
-  int n;
+// legs) runs inside one block of 1024 threads with every level resident in
+// shared memory.  One SM executes it, so it is written for instruction
+// count: each level is stored with a zero ghost ring (no bounds checks; the
+// ring is the zero padding of Sec. 2.1), the inverse diagonal is computed
+// once per launch (0 marks a non-fluid cell), and a sweep is
+// x <- (1 - omega) x + omega D^-1 (b + sum_a w_a (x_- + x_+)).  The
+// coarsest level is solved exactly: its operator is inverted once at create
+// (float64 Gauss-Jordan) and applied here in float64, one warp per row.
+struct CGeo {
+  int nx, ny, nz, W, WH, n, off;  // interior sizes, padded row / plane, cells, float offset
+  int lnx, lny;                   // log2 of nx, ny when powers of two, else -1
+  __device__ __forceinline__ int pad(int x, int y, int z) const { return ((z + (nz > 1 ? 1 : 0)) * (ny + 2) + y + 1) * W + x + 1; }
+  __device__ __forceinline__ void xyz(int i, int& x, int& y, int& z) const {
+    if (lnx >= 0 && lny >= 0) {
+      x = i & (nx - 1);
+      y = (i >> lnx) & (ny - 1);
+      z = i >> (lnx + lny);
+    } else {
+      x = i % nx;
+      const int t = i / nx;
+      y = t % ny;
+      z = t / ny;
+    }
+  }
 };
 
-__device__ __forceinline__ float cl_diag(const CLevel& c, int dim, int x, int y, int z, uint8_t m) {
-  if (c.m) return dim == 3 ? diag_at<3, true>(c.L, x, y, z, m) : diag_at<2, true>(c.L, x, y, z, m);
-  return dim == 3 ? diag_at<3, false>(c.L, x, y, z, m) : diag_at<2, false>(c.L, x, y, z, m);
+__device__ __forceinline__ int ilog2_or_neg(int v) { return (v & (v - 1)) ? -1 : __ffs(v) - 1; }
+
+__device__ __forceinline__ CGeo cgeo(const LevelDev& L, int off) {
+  CGeo g;
+  g.nx = L.nx;
+  g.ny = L.ny;
+  g.nz = L.nz;
+  g.W = L.nx + 2;
+  g.WH = (L.nx + 2) * (L.ny + 2);
+  g.n = L.nx * L.ny * L.nz;
+  g.off = off;
+  g.lnx = ilog2_or_neg(L.nx);
+  g.lny = ilog2_or_neg(L.ny);
+  return g;
 }
 
-__device__ __forceinline__ float cl_ax(const CLevel& c, int dim, const float* x, int i, int cx, int cy, int cz,
-                                      float d) {
-  const LevelDev& L = c.L;
-  const int sxy = L.nx * L.ny;
-  float nb = 0.f;
-  if (cx > 0) nb += L.wx * x[i - 1];
-  if (cx < L.nx - 1) nb += L.wx * x[i + 1];
-  if (cy > 0) nb += L.wy * x[i - L.nx];
-  if (cy < L.ny - 1) nb += L.wy * x[i + L.nx];
-  if (dim == 3) {
-    if (cz > 0) nb += L.wz * x[i - sxy];
-    if (cz < L.nz - 1) nb += L.wz * x[i + sxy];
+template <int DIM>
+__device__ __forceinline__ float cl_nb(const LevelDev& L, const CGeo& g, const float* x, int p) {
+  float nb = L.wx * (x[p - 1] + x[p + 1]) + L.wy * (x[p - g.W] + x[p + g.W]);
+  if (DIM == 3) nb += L.wz * (x[p - g.WH] + x[p + g.WH]);
+  return nb;
+}
+
+template <int DIM>
+__device__ __forceinline__ void cl_sweep(const LevelDev& L, const CGeo& g, const float* xin, float* xout,
+                                         const float* b, const float* id, float omega) {
+  const float om1 = 1.f - omega;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+    int x, y, z;
+    g.xyz(i, x, y, z);
+    const int p = g.pad(x, y, z);
+    xout[p] = fmaf(om1, xin[p], omega * id[p] * (b[p] + cl_nb<DIM>(L, g, xin, p)));
   }
-  return d * x[i] - nb;
+  __syncthreads();
 }
 
-__device__ void cl_sweep(const CLevel& c, int dim, const float* xin, float* xout, const float* b, float omega,
-                         bool from_zero) {
-  const LevelDev& L = c.L;
-  for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
-    const int x = i % L.nx, t = i / L.nx, y = t % L.ny, z = t / L.ny;
-    const uint8_t m = c.m ? c.m[i] : kFluidBit;
-    float v = 0.f;
-    if (m) {
-      const float d = cl_diag(c, dim, x, y, z, m);
-      v = from_zero ? omega * b[i] / d : xin[i] + omega * (b[i] - cl_ax(c, dim, xin, i, x, y, z, d)) / d;
+// Zero all arrays (the ghost rings stay zero for good) and write 1/diag
+// (0 on non-fluid cells) of every level; into shared memory or into the
+// image in global memory that later launches copy in.
+template <int DIM>
+__device__ void coarse_fill_image(const CoarseArgs& a, float* S, int total_floats) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < total_floats / 4; i += blockDim.x * gridDim.x)
+    reinterpret_cast<float4*>(S)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (gridDim.x == 1) __syncthreads();
+  else __threadfence();
+  for (int l = 0; l < a.nlev; ++l) {
+    const LevelDev& L = a.lv[l];
+    const CGeo g = cgeo(L, a.off[l]);
+    float* id = S + g.off + 3 * g.WH * (g.nz + (g.nz > 1 ? 2 : 0));
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < g.n; i += blockDim.x * gridDim.x) {
+      int x, y, z;
+      g.xyz(i, x, y, z);
+      const uint8_t m = L.cell ? L.cell[i] : kFluidBit;
+      const float d = L.cell ? diag_at<DIM, true>(L, x, y, z, m) : diag_at<DIM, false>(L, x, y, z, m);
+      id[g.pad(x, y, z)] = m ? __frcp_rn(d) : 0.f;
     }
-    xout[i] = v;
   }
-  __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse(CoarseArgs a, const T* __restrict__ bin, T* __restrict__ xout,
-                                                 SolveState* __restrict__ st) {
-  if (st && st->inner_done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* S = reinterpret_cast<float*>(smem_raw);
-  const int dim = a.dim;
-  CLevel lv[kMaxLevels];
-  for (int l = 0; l < a.nlev; ++l) {
-    lv[l].L = a.lv[l];
-    lv[l].n = a.lv[l].nx * a.lv[l].ny * a.lv[l].nz;
-    lv[l].m = a.lv[l].cell ? smem_raw + a.moff[l] : nullptr;
+template <int DIM>
+__global__ void k_coarse_image(const __grid_constant__ CoarseArgs a, float* image, int total_floats) {
+  coarse_fill_image<DIM>(a, image, total_floats);
+}
+
+template <int DIM, typename T>
+__device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* __restrict__ xout,
+                             SolveState* __restrict__ st, float* S, int total_floats) {
+  // level l: X0 | X1 | B | ID, each padded
+  auto G = [&](int l) { return cgeo(a.lv[l], a.off[l]); };
+  auto PS = [&](const CGeo& g) { return g.WH * (g.nz + (g.nz > 1 ? 2 : 0)); };
+  auto X = [&](const CGeo& g, int which) { return S + g.off + which * PS(g); };
+  auto B = [&](const CGeo& g) { return S + g.off + 2 * PS(g); };
+  auto ID = [&](const CGeo& g) { return S + g.off + 3 * PS(g); };
+  if (a.image) {
+    // the constant part of the image (zero rings, inverse diagonals) comes
+    // from global memory in bulk asynchronous copies
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    const uint32_t bytes = (uint32_t)total_floats * 4u;
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(&bar, bytes);
+      for (uint32_t o = 0; o < bytes; o += 32768u)
+        bulk_load(S + o / 4, a.image + o / 4, bytes - o < 32768u ? bytes - o : 32768u, &bar);
+    }
+    if (!mbar_wait_bounded(&bar, 0)) {
+      if (st && threadIdx.x == 0) {
+        st->status = MG_TIMEOUT;
+        st->inner_done = 1;
+        st->outer_done = 1;
+      }
+      return;
+    }
+  } else {
+    coarse_fill_image<DIM>(a, S, total_floats);
   }
-  auto X = [&](int l, int which) { return S + a.off[l] + which * lv[l].n; };
-  auto B = [&](int l) { return S + a.off[l] + 2 * lv[l].n; };
-  // stage the right-hand side of the first level and all cell bytes
-  for (int i = threadIdx.x; i < lv[0].n; i += blockDim.x) B(0)[i] = ld(bin, i);
-  for (int l = 0; l < a.nlev; ++l) {
-    if (!a.lv[l].cell) continue;
-    uint8_t* dst = smem_raw + a.moff[l];
-    for (int i = threadIdx.x; i < lv[l].n; i += blockDim.x) dst[i] = a.lv[l].cell[i];
-  }
-  __syncthreads();
-  int cur[kMaxLevels];
-  // down legs
-  for (int l = 0; l < a.nlev - 1; ++l) {
-    const CLevel& c = lv[l];
-    int k = 0;
-    if (a.pre == 0) {
-      for (int i = threadIdx.x; i < c.n; i += blockDim.x) X(l, 0)[i] = 0.f;
-      __syncthreads();
+  // right-hand side of the first level
+  {
+    const CGeo g = G(0);
+    float* b0 = B(g);
+    if ((g.nx & 3) == 0 && std::is_same<T, float>::value) {
+      const int n4 = g.n / 4;
+#pragma unroll 2
+      for (int i4 = threadIdx.x; i4 < n4; i4 += blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(bin)[i4];
+        int x, y, z;
+        g.xyz(4 * i4, x, y, z);
+        float* d = b0 + g.pad(x, y, z);
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+      }
     } else {
-      cl_sweep(c, dim, nullptr, X(l, 0), B(l), a.omega, true);
-      for (int j = 2; j <= a.pre; ++j) {
-        cl_sweep(c, dim, X(l, k), X(l, 1 - k), B(l), a.omega, false);
-        k = 1 - k;
+      for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        int x, y, z;
+        g.xyz(i, x, y, z);
+        b0[g.pad(x, y, z)] = ld(bin, i);
       }
     }
-    cur[l] = k;
-    const LevelDev& L = c.L;
-    const LevelDev& C = lv[l + 1].L;
-    const float* xl = X(l, k);
-    const float* bl = B(l);
-    float* bc = B(l + 1);
-    const float inv_children = dim == 3 ? 0.125f : 0.25f;
-    for (int j = threadIdx.x; j < lv[l + 1].n; j += blockDim.x) {
-      const int Xc = j % C.nx, t = j / C.nx, Yc = t % C.ny, Zc = t / C.ny;
-      float sum = 0.f;
-      for (int az = 0; az < (dim == 3 ? 2 : 1); ++az)
-        for (int ay = 0; ay < 2; ++ay)
-          for (int ax = 0; ax < 2; ++ax) {
-            const int cx = 2 * Xc + ax, cy = 2 * Yc + ay, cz = 2 * Zc + az;
-            const int i = (cz * L.ny + cy) * L.nx + cx;
-            const uint8_t m = c.m ? c.m[i] : kFluidBit;
-            if (m) sum += bl[i] - cl_ax(c, dim, xl, i, cx, cy, cz, cl_diag(c, dim, cx, cy, cz, m));
-          }
-      bc[j] = sum * inv_children;
+  }
+  __syncthreads();
+  unsigned cur = 0u;  // bit l: level l's current x is buffer 1
+  // down legs
+  for (int l = 0; l < a.nlev - 1; ++l) {
+    const LevelDev& L = a.lv[l];
+    const CGeo g = G(l);
+    const float* b = B(g);
+    const float* id = ID(g);
+    int k = 0;
+    {
+      float* x0 = X(g, 0);
+      for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        int x, y, z;
+        g.xyz(i, x, y, z);
+        const int p = g.pad(x, y, z);
+        x0[p] = a.pre > 0 ? a.omega * id[p] * b[p] : 0.f;
+      }
+      __syncthreads();
     }
+    for (int j = 2; j <= a.pre; ++j) {
+      cl_sweep<DIM>(L, g, X(g, k), X(g, 1 - k), b, id, a.omega);
+      k = 1 - k;
+    }
+    if (k) cur |= 1u << l;
+    const float* xl = X(g, k);
+    const LevelDev& CL = a.lv[l + 1];
+    const CGeo c = G(l + 1);
+    float* bc = B(c);
+    const float inv_children = DIM == 3 ? 0.125f : 0.25f;
+    for (int jc = threadIdx.x; jc < c.n; jc += blockDim.x) {
+      int X0, Y0, Z0;
+      c.xyz(jc, X0, Y0, Z0);
+      float sum = 0.f;
+#pragma unroll
+      for (int az = 0; az < (DIM == 3 ? 2 : 1); ++az)
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+          for (int ax = 0; ax < 2; ++ax) {
+            const int p = g.pad(2 * X0 + ax, 2 * Y0 + ay, 2 * Z0 + az);
+            const float idv = id[p];
+            if (idv != 0.f) sum += b[p] - (__frcp_rn(idv) * xl[p] - cl_nb<DIM>(L, g, xl, p));
+          }
+      bc[c.pad(X0, Y0, Z0)] = sum * inv_children;
+    }
+    (void)CL;
     __syncthreads();
   }
   // coarsest: x = A^-1 b in float64, one warp per row
   {
-    const int l = a.nlev - 1;
+    const CGeo c = G(a.nlev - 1);
     const int n = a.ncoarse;
-    float* xc = X(l, 0);
-    const float* bc = B(l);
+    float* xc = X(c, 0);
+    const float* bc = B(c);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < n; i += nw) {
       double acc = 0.0;
       // the inverse of the symmetric operator is symmetric: read row i
-      for (int j = lane; j < n; j += 32) acc += a.inv[(size_t)i * n + j] * (double)bc[j];
+      for (int j = lane; j < n; j += 32) {
+        int x, y, z;
+        c.xyz(j, x, y, z);
+        acc += a.inv[(size_t)i * n + j] * (double)bc[c.pad(x, y, z)];
+      }
       acc = warp_sum(acc);
-      if (lane == 0) xc[i] = (float)acc;
+      if (lane == 0) {
+        int x, y, z;
+        c.xyz(i, x, y, z);
+        xc[c.pad(x, y, z)] = (float)acc;
+      }
     }
-    cur[l] = 0;
     __syncthreads();
   }
   // up legs
   for (int l = a.nlev - 2; l >= 0; --l) {
-    const CLevel& c = lv[l];
-    const LevelDev& L = c.L;
-    const LevelDev& C = lv[l + 1].L;
-    const float* e = X(l + 1, cur[l + 1]);
-    int k = cur[l];
-    float* xs = X(l, k);
-    for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
-      const int x = i % L.nx, t = i / L.nx, y = t % L.ny, z = t / L.ny;
-      const uint8_t m = c.m ? c.m[i] : kFluidBit;
-      xs[i] = m ? xs[i] + a.s * e[((z >> 1) * C.ny + (y >> 1)) * C.nx + (x >> 1)] : 0.f;
+    const LevelDev& L = a.lv[l];
+    const CGeo g = G(l);
+    const CGeo c = G(l + 1);
+    const float* e = X(c, (cur >> (l + 1)) & 1u);
+    const float* b = B(g);
+    const float* id = ID(g);
+    int k = (cur >> l) & 1u;
+    float* xs = X(g, k);
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+      int x, y, z;
+      g.xyz(i, x, y, z);
+      const int p = g.pad(x, y, z);
+      if (id[p] != 0.f) xs[p] += a.s * e[c.pad(x >> 1, y >> 1, z >> 1)];
     }
     __syncthreads();
     for (int j = 1; j <= a.post; ++j) {
-      cl_sweep(c, dim, X(l, k), X(l, 1 - k), B(l), a.omega, false);
+      cl_sweep<DIM>(L, g, X(g, k), X(g, 1 - k), b, id, a.omega);
       k = 1 - k;
     }
-    cur[l] = k;
+    cur = (cur & ~(1u << l)) | ((unsigned)k << l);
   }
   // write the first level handled here
-  const float* x0 = X(0, cur[0]);
-  const float* b0 = B(0);
+  const CGeo g = G(0);
+  const float* x0 = X(g, cur & 1u);
+  const float* b0 = B(g);
   float acc = 0.f;
-  for (int i = threadIdx.x; i < lv[0].n; i += blockDim.x) {
-    const T zt = cvt<T>(x0[i]);
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+    int x, y, z;
+    g.xyz(i, x, y, z);
+    const int p = g.pad(x, y, z);
+    const T zt = cvt<T>(x0[p]);
     xout[i] = zt;
-    if (a.finest) acc = fmaf(b0[i], ld(&zt, 0), acc);
+    if (a.finest) acc = fmaf(b0[p], ld(&zt, 0), acc);
   }
   if (a.finest) {
     __shared__ double sh[32];
@@ -180,10 +286,54 @@ __global__ void __launch_bounds__(1024) k_coarse(CoarseArgs a, const T* __restri
   }
 }
 
+// The level table stays in kernel-parameter space (__grid_constant__), so
+// indexing it by level needs no local copy.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse(const __grid_constant__ CoarseArgs a, const T* __restrict__ bin,
+                                                 T* __restrict__ xout, SolveState* __restrict__ st,
+                                                 int total_floats) {
+  if (st && st->inner_done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* S = reinterpret_cast<float*>(smem_raw);
+  if (a.dim == 3) coarse_cycle<3, T>(a, bin, xout, st, S, total_floats);
+  else coarse_cycle<2, T>(a, bin, xout, st, S, total_floats);
+}
+
+// Padded shared-memory layout of the single-block kernel for levels
+// lv[0 .. nlev-1]: four arrays (x, x', b, 1/diag) per level with a ghost
+// ring; returns the bytes needed.
+size_t coarse_layout(int* off, const LevelDev* lv, int nlev, int dim) {
+  size_t f = 0;
+  for (int l = 0; l < nlev; ++l) {
+    off[l] = (int)f;
+    const size_t P = (size_t)(lv[l].nx + 2) * (lv[l].ny + 2) * (dim == 3 ? lv[l].nz + 2 : 1);
+    f += (4 * P + 3) / 4 * 4;
+  }
+  return f * sizeof(float);
+}
+
+// First level handled by the single-block kernel: levels of at most 8192
+// cells whose padded arrays fit the block's shared memory.
+int coarse_start_level(const LevelDev* lv, int L, int dim, size_t smem_limit) {
+  int kc = L - 1;
+  int off[kMaxLevels];
+  while (kc > 0 && (size_t)lv[kc - 1].nx * lv[kc - 1].ny * lv[kc - 1].nz <= 8192 &&
+         coarse_layout(off, lv + kc - 1, L - kc + 1, dim) <= smem_limit)
+    --kc;
+  return kc;
+}
+
+cudaError_t launch_coarse_image(const CoarseArgs& a, float* image, size_t bytes, cudaStream_t s) {
+  // one block: the zeroing must finish before the diagonals are written
+  if (a.dim == 3) k_coarse_image<3><<<1, 1024, 0, s>>>(a, image, (int)(bytes / 4));
+  else k_coarse_image<2><<<1, 1024, 0, s>>>(a, image, (int)(bytes / 4));
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_coarse(const CoarseArgs& a, size_t smem_bytes, const void* b, void* x, SolveState* st,
                           cudaStream_t s) {
-  k_coarse<T><<<1, 1024, smem_bytes, s>>>(a, (const T*)b, (T*)x, st);
+  k_coarse<T><<<1, 1024, smem_bytes, s>>>(a, (const T*)b, (T*)x, st, (int)(smem_bytes / sizeof(float)));
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #include <type_traits>
 
 #include "launch.h"
+#include "tma_host.h"
 
 namespace npmg {
 
@@ -37,6 +38,7 @@ struct mg_handle_s {
   void* xff[2];    // float-float iterate (hi, lo) per cell, double-buffered
   int cur64;
   double* inv;
+  float* cimage;   // constant shared-memory image of the single-block kernel
   int ncoarse;
   double* partials;
   npmg::SolveState* st;
@@ -46,6 +48,8 @@ struct mg_handle_s {
   int nb1d;
   cudaEvent_t ev0, ev1;
   cudaGraphExec_t graph_exec;
+  npmg::TmaLevelMaps tmaps[npmg::kMaxLevels];  // TMA tensor maps per level (levels < kc)
+  bool tma_ok[npmg::kMaxLevels];
   int64_t chunk_kernels;   // kernels in one graph launch
   // instrumentation
   int64_t launches;

@@ -90,10 +90,22 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
   const mg_options& o = h->opt;
   cudaError_t e;
   const float om = (float)o.omega, sc = (float)o.coarse_scale;
+  // TMA tensor maps: level 0 reads r, which is the caller's array in the
+  // building-block path, so its map is re-encoded when r is not the handle's
+  TmaLevelMaps m0;
+  bool tma0 = h->tma_ok[0];
+  if (tma0) {
+    m0 = h->tmaps[0];
+    if (r != h->r) tma0 = tma_encode_b<T>(&m0.b, h->lv[0], r);
+  }
   for (int k = 0; k < h->kc; ++k) {
     const void* b = k == 0 ? r : h->bk[k];
     LaunchScope ls(h, k == 0 ? MG_K_DOWN_FINE : MG_K_DOWN, s);
-    e = launch_down<DIM, T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], o.pre, om, st, s);
+    const bool tma = k == 0 ? tma0 : h->tma_ok[k];
+    if (tma)
+      e = launch_down_tma<T, M>(k == 0 ? m0 : h->tmaps[k], h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
+    else
+      e = launch_down<DIM, T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], o.pre, om, st, s);
     if (e != cudaSuccess) return e;
   }
   CoarseArgs ca = h->ca;
@@ -107,7 +119,14 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     const void* b = k == 0 ? r : h->bk[k];
     void* xo = k == 0 ? z : h->yk[k];
     LaunchScope ls(h, k == 0 ? MG_K_UP_FINE : MG_K_UP, s);
-    if (k == 0 && st)
+    const bool tma = k == 0 ? tma0 : h->tma_ok[k];
+    if (tma) {
+      const TmaLevelMaps& mk = k == 0 ? m0 : h->tmaps[k];
+      if (k == 0 && st)
+        e = launch_up_tma<T, M, true>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
+      else
+        e = launch_up_tma<T, M, false>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
+    } else if (k == 0 && st)
       e = launch_up<DIM, T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], o.post, om, sc, st, h->partials, s);
     else
       e = launch_up<DIM, T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], o.post, om, sc, st, h->partials, s);
@@ -373,10 +392,22 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     }
     h->ncell[k] = (size_t)h->n[k][0] * h->n[k][1] * h->n[k][2];
   }
-  // single-block coarse kernel takes the levels with <= 4096 cells
-  int kc = L - 1;
-  while (kc > 0 && h->ncell[kc - 1] <= 4096) --kc;
+  // the single-block coarse kernel takes the small levels (<= 8192 cells)
+  // whose padded arrays fit its shared memory
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  LevelDev geo[kMaxLevels];
+  for (int k = 0; k < L; ++k) {
+    geo[k].nx = (int)h->n[k][0];
+    geo[k].ny = (int)h->n[k][1];
+    geo[k].nz = (int)h->n[k][2];
+  }
+  const int kc = coarse_start_level(geo, L, dim, (size_t)optin - 2048);
   h->kc = kc;
+  {
+    int offtmp[kMaxLevels];
+    h->ca_smem = coarse_layout(offtmp, geo + kc, L - kc, dim);
+  }
   h->ncoarse = (int)h->ncell[L - 1];
   if (h->ncoarse > 1024) {
     const int nc = h->ncoarse;
@@ -408,6 +439,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
   plan.push_back({&h->xff[0], n0c * 8});
   plan.push_back({&h->xff[1], n0c * 8});
   plan.push_back({(void**)&h->inv, (size_t)2 * h->ncoarse * h->ncoarse * 8});
+  plan.push_back({(void**)&h->cimage, h->ca_smem});
   plan.push_back({(void**)&h->partials, (size_t)kMaxPartials * 8});
   plan.push_back({(void**)&h->st, sizeof(SolveState)});
   size_t total = 0;
@@ -474,24 +506,17 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     memset(&ca, 0, sizeof(ca));
     ca.nlev = L - kc;
     ca.dim = dim;
-    int offf = 0;
-    for (int l = 0; l < ca.nlev; ++l) {
-      ca.lv[l] = h->lv[kc + l];
-      ca.off[l] = offf;
-      offf += 3 * (int)h->ncell[kc + l];
-    }
-    size_t moff = align_up((size_t)offf * sizeof(float), 16);
-    for (int l = 0; l < ca.nlev; ++l) {
-      ca.moff[l] = (int)moff;
-      if (h->masked) moff = align_up(moff + h->ncell[kc + l], 16);
-    }
+    for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = h->lv[kc + l];
+    h->ca_smem = coarse_layout(ca.off, ca.lv, ca.nlev, dim);
     ca.ncoarse = h->ncoarse;
     ca.inv = h->inv;
+    ca.image = nullptr;
     ca.pre = o.pre;
     ca.post = o.post;
     ca.omega = (float)o.omega;
     ca.s = (float)o.coarse_scale;
-    h->ca_smem = moff;
+    NPMG_TRY(launch_coarse_image(ca, h->cimage, h->ca_smem, s));
+    ca.image = h->cimage;
   }
   h->nb1d = default_blocks_1d(h, h->ncell[0]);
   {
@@ -511,6 +536,13 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     constexpr bool M = decltype(mc)::value;
     cudaError_t e = prepare_level_kernels<DIM, T, M>(o.pre, o.post);
     if (e == cudaSuccess) e = prepare_coarse<T>(h->ca_smem);
+    if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
+    // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
+    for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
+      h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&
+                     tma_encode_level<T>(&h->tmaps[k], h->lv[k], k == 0 ? h->r : h->bk[k], h->xk[k],
+                                         h->yk[k + 1]);
+    }
     return e;
   }));
   NPMG_TRY(cudaStreamSynchronize(s));

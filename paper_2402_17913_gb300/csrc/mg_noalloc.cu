@@ -131,8 +131,16 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
               kNoallocMaxCoarse);
     return MG_ERR_INVALID;
   }
-  int kc = L - 1;
-  while (kc > 0 && ncell[kc - 1] <= 4096) --kc;
+  int dev = 0, optin = 0;
+  NPMG_CUDA(cudaGetDevice(&dev));
+  NPMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  LevelDev geo[kMaxLevels];
+  for (int k = 0; k < L; ++k) {
+    geo[k].nx = (int)nk[k][0];
+    geo[k].ny = (int)nk[k][1];
+    geo[k].nz = (int)nk[k][2];
+  }
+  const int kc = coarse_start_level(geo, L, dim, (size_t)optin - 2048);
   // carve the static scratch
   unsigned char* base = nullptr;
   NPMG_CUDA(scratch_address(&base));
@@ -163,6 +171,12 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
     if (k >= 1) yk[k] = (float*)take(ncell[k] * 4);
   }
   double* inv = (double*)take((size_t)2 * ncoarse * ncoarse * 8);
+  size_t image_bytes;
+  {
+    int offtmp[kMaxLevels];
+    image_bytes = coarse_layout(offtmp, geo + kc, L - kc, dim);
+  }
+  float* image = (float*)take(image_bytes);
   if (!fits) {
     set_error("mg_vcycle_noalloc: the problem needs more than the %zu bytes of static scratch", kScratchBytes);
     return MG_ERR_INVALID;
@@ -200,17 +214,8 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   memset(&ca, 0, sizeof(ca));
   ca.nlev = L - kc;
   ca.dim = dim;
-  int offf = 0;
-  for (int l = 0; l < ca.nlev; ++l) {
-    ca.lv[l] = lv[kc + l];
-    ca.off[l] = offf;
-    offf += 3 * (int)ncell[kc + l];
-  }
-  size_t moff = ((size_t)offf * sizeof(float) + 15) / 16 * 16;
-  for (int l = 0; l < ca.nlev; ++l) {
-    ca.moff[l] = (int)moff;
-    if (masked) moff = (moff + ncell[kc + l] + 15) / 16 * 16;
-  }
+  for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = lv[kc + l];
+  const size_t moff = coarse_layout(ca.off, ca.lv, ca.nlev, dim);
   ca.ncoarse = ncoarse;
   ca.inv = inv;
   ca.pre = o.pre;
@@ -218,6 +223,9 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   ca.omega = (float)o.omega;
   ca.s = (float)o.coarse_scale;
   ca.finest = 0;
+  ca.image = nullptr;
+  NPMG_CUDA(launch_coarse_image(ca, image, moff, s));
+  ca.image = image;
   const float om = (float)o.omega, sc = (float)o.coarse_scale;
   auto cycle = [&](auto dimc, auto mc) -> cudaError_t {
     constexpr int DIM = decltype(dimc)::value;

@@ -43,21 +43,25 @@ __device__ __forceinline__ float fixed_value(int c, float uin) { return c == 0 ?
 // Component c at face index f (may lie one step outside the face array along
 // one axis: the padding rule of component c along that axis applies).
 // Fixed faces read their prescribed value.
+template <int DIM>
 __device__ __forceinline__ float q_at(const NsGeom& G, const float* __restrict__ q, int c, int f0, int f1, int f2,
                                       float uin) {
-  int F[3];
-  face_dims(G, c, F);
-  int f[3] = {f0, f1, f2};
-  for (int a = 0; a < G.dim; ++a) {
-    if (f[a] < 0) {
-      if (a == 0 && c != 0) return 0.f;  // inflow pads tangential components with 0
-      f[a] = 0;
-    } else if (f[a] >= F[a]) {
-      f[a] = F[a] - 1;
-    }
+  const int F0 = G.n[0] + (c == 0), F1 = G.n[1] + (c == 1), F2 = DIM == 3 ? G.n[2] + (c == 2) : 1;
+  // padding rule along each axis: the inflow pads tangential components with
+  // 0; every other side copies the edge value
+  if (f0 < 0) {
+    if (c != 0) return 0.f;
+    f0 = 0;
+  } else if (f0 >= F0) {
+    f0 = F0 - 1;
   }
-  if (is_fixed(G, c, f)) return fixed_value(c, uin);
-  return q[((size_t)f[2] * F[1] + f[1]) * F[0] + f[0]];
+  f1 = f1 < 0 ? 0 : (f1 >= F1 ? F1 - 1 : f1);
+  if (DIM == 3) f2 = f2 < 0 ? 0 : (f2 >= F2 ? F2 - 1 : f2);
+  else f2 = 0;
+  // fixed faces read their prescribed value
+  const int fc = c == 0 ? f0 : (c == 1 ? f1 : f2);
+  if (c == 0 ? fc == 0 : (fc == 0 || fc == G.n[c])) return fixed_value(c, uin);
+  return q[((size_t)f2 * F1 + f1) * F0 + f0];
 }
 
 __device__ __forceinline__ bool solid_cell(const NsGeom& G, int x, int y, int z) {
@@ -97,8 +101,8 @@ __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const
   auto Q = [&](int a, int off) {
     int g[3] = {f[0], f[1], f[2]};
     g[a] += off;
-    float v = q_at(G, qc, C, g[0], g[1], g[2], uin);
-    if (CORR) v = 0.5f * (v + q_at(G, qt, C, g[0], g[1], g[2], uin));
+    float v = q_at<DIM>(G, qc, C, g[0], g[1], g[2], uin);
+    if (CORR) v = 0.5f * (v + q_at<DIM>(G, qt, C, g[0], g[1], g[2], uin));
     return v;
   };
   const float qn_self = qc[i];
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const
           int g[3] = {f[0], f[1], f[2]};
           g[C] += dc;
           g[a] += da;
-          s += q_at(G, Qn.q[a], a, g[0], g[1], g[2], uin);
+          s += q_at<DIM>(G, Qn.q[a], a, g[0], g[1], g[2], uin);
         }
       Ua = 0.25f * s;
     }

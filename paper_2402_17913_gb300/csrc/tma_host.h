@@ -1,0 +1,31 @@
+// Host interface of the TMA-staged level kernels (mg_tma.cu).
+#pragma once
+#include <cuda.h>
+
+#include "npmg_internal.cuh"
+
+namespace npmg {
+
+constexpr int kTmaTX = 64, kTmaTY = 16, kTmaH = 2;  // tile and halo of the TMA level kernels
+
+// Tensor maps of one level: right-hand side b, the down leg's x, the coarse
+// correction e (next level), the cell bytes m.
+struct TmaLevelMaps {
+  CUtensorMap b, x, e, m;
+};
+
+bool tma_level_eligible(int dim, int pre, int post, const LevelDev& L);
+template <typename T>
+bool tma_encode_level(TmaLevelMaps* out, const LevelDev& L, const void* b, const void* x, const void* e);
+template <typename T>
+bool tma_encode_b(CUtensorMap* out, const LevelDev& L, const void* b);
+template <typename T, bool MASKED>
+cudaError_t launch_down_tma(const TmaLevelMaps& m, const LevelDev& L, void* x, void* bcoarse, float omega,
+                            SolveState* st, cudaStream_t s);
+template <typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up_tma(const TmaLevelMaps& m, const LevelDev& L, void* xout, float omega, float sc,
+                          SolveState* st, double* partials, cudaStream_t s);
+template <typename T, bool MASKED>
+cudaError_t prepare_tma_kernels();
+
+}  // namespace npmg
