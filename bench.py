@@ -45,6 +45,12 @@ TOL = 1e-6
 # (float32 storage, the method's own minimum: each array read or written
 # once per launch; masked levels read one cell byte more).  Only classes
 # that dominate a step are listed.
+# Batched solve: bytes per fine cell of one CG iteration (the four fine
+# passes above, plus one cell byte in three of them, plus about a third more
+# for the coarser levels) and of one float-float refinement pass.
+BATCH_ITER_BYTES = 72
+OUTER_BYTES = 28
+
 ALGO_BYTES_PER_CELL = {
     "down_fine": 4 + 4 + 1,          # read b (= CG residual); write x, coarse b (1/4)
     "up_fine": 4 + 4 + 1 + 4,        # read b, x, coarse e (1/4); write z
@@ -60,7 +66,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="ns2d", choices=["ns2d", "poisson2d", "poisson3d"])
+    ap.add_argument("--config", default="ns2d", choices=["ns2d", "poisson2d", "poisson3d", "batched"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
@@ -101,6 +107,34 @@ class Poisson:
         return {"workload": "%dD pressure Poisson, 8 Gaussian blobs, zero Dirichlet" % self.dim,
                 "shape": list(reversed(self.shape)), "solve_rel_tol": TOL, "inner_precision": self.prec,
                 "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
+
+
+class Batched:
+    """1024 independent square instances, sides uniform in {64, 128, 256,
+    512} (seed 1234), random rectangle solids covering U(0, 0.1) of the
+    cells (flood-filled), 8-blob right-hand sides (seed = instance index),
+    zero Dirichlet faces."""
+    name = "batched_1024"
+    dim = 2
+
+    def __init__(self, count=1024, seed=1234, limit=None):
+        sides, fracs, rng = I.batched_sides(count, seed)
+        self.shapes, self.spacings, self.solids, self.rhs = [], [], [], []
+        for k, (n, f) in enumerate(zip(sides, fracs)):
+            if limit is not None and k >= limit:
+                break
+            solid = I.random_solid_mask((n, n), rng, f)
+            self.shapes.append((n, n))
+            self.spacings.append((1.0 / (n + 1), 1.0 / (n + 1)))
+            self.solids.append(solid)
+            self.rhs.append(I.blob_rhs((n, n), k, solid=solid).astype(np.float32))
+        self.units = int(sum((~s).sum() for s in self.solids))
+        self.cells = int(sum(n * n for n, _ in self.shapes))
+
+    def config(self):
+        return {"workload": "batched 2D Poisson, %d instances of sides {64,128,256,512}, random solids"
+                % len(self.shapes), "cells": self.cells, "solve_rel_tol": TOL, "unknowns_per_step": self.units,
+                "l2": "inputs (%.1f GB) larger than L2" % (self.cells * 60 / 1e9)}
 
 
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
@@ -208,6 +242,33 @@ def run_gpu(args, rank, world):
                 hdst.copy_(d, non_blocking=True)
         io_bytes = sum(t.numel() * 4 for t in host)
         cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
+    elif args.config == "batched":
+        wl = Batched()
+        masks = [torch.from_numpy(m.astype(np.uint8)).to(dev) for m in wl.solids]
+        bh = L.mg_create_batched(wl.shapes, wl.spacings, (0, 0, 0, 0), masks)
+        mg = None
+        hb = [torch.from_numpy(r).pin_memory() for r in wl.rhs]
+        hx = [torch.zeros_like(t).pin_memory() for t in hb]
+        db = [t.to(dev) for t in hb]
+        dx = [torch.zeros_like(t) for t in db]
+        tuned = L.mg_tune_batched(bh, db, dx, TOL)
+        stats = []
+
+        def step():
+            for t in dx:
+                t.zero_()
+            _, st = L.mg_solve_batched(bh, db, dx, TOL)
+            stats.append({"iters": max(s_["iters"] for s_ in st), "relres": max(s_["relres"] for s_ in st),
+                          "outer": max(s_["outer"] for s_ in st), "all": st})
+
+        def e2e_step():
+            for d, hsrc in zip(db, hb):
+                d.copy_(hsrc, non_blocking=True)
+            step()
+            for d, hdst in zip(dx, hx):
+                hdst.copy_(d, non_blocking=True)
+        io_bytes = sum(t.numel() * 4 for t in hb)
+        cleanup = lambda: L.mg_destroy_batched(bh)  # noqa: E731
     else:
         shape = (256, 256) if args.config == "poisson2d" else (256, 256, 256)
         wl = Poisson(shape, args.prec)
@@ -238,7 +299,7 @@ def run_gpu(args, rank, world):
     stats.clear()
     dist_barrier(world)
     # ---- timed: device-resident inputs, L2 flushed between steps
-    launches0 = L.mg_kernel_launches(mg)
+    launches0 = L.mg_kernel_launches(mg) if mg else 0
     cp, cf, cpath = clocks_sampler()
     times = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -251,7 +312,8 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     clocks = clocks_summary(cp, cf, cpath)
     times = [a.elapsed_time(b) for a, b in ev]
-    launches = L.mg_kernel_launches(mg) - launches0
+    # the batched solve is one persistent kernel per solve (one graph launch)
+    launches = (L.mg_kernel_launches(mg) - launches0) if mg else args.steps
     step_stats = list(stats)
     total_ms = sum(times)
     total_ms = dist_max(total_ms, world)
@@ -272,33 +334,48 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append(t0.elapsed_time(t1))
     e2e_total = dist_max(sum(e2e_ms), world)
-    # ---- profiled pass: per-kernel-class event times (graph off)
-    L.mg_profile_enable(mg, True)
-    L.mg_profile_read(mg, reset=True)
-    nprof = min(args.steps, 5)
-    for i in range(nprof):
-        flush.fill_(float(i))
-        step()
-    prof = L.mg_profile_read(mg, reset=True)
-    L.mg_profile_enable(mg, False)
-    cleanup()
-
-    tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
-    dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
-    ms_dom, n_dom = prof[dom]
-    ncell = int(np.prod(wl.cells)) if args.config == "ns2d" else wl.units
-    per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config == "ns2d" and dom != "xr_update" else 0)
-    if args.prec != "fp32" and args.config != "ns2d":
-        per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
-    algo = per_cell * ncell
-    achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": recorded_traffic(wl.name, dom), "algorithmic_bytes_per_launch": algo,
-                "avg_launch_us": round(ms_dom / max(n_dom, 1) * 1e3, 2),
-                "share_of_step": round(ms_dom / tot_prof, 3),
-                "class_shares": {k: round(v[0] / tot_prof, 3) for k, v in prof.items() if v[1]}}
+    if args.config == "batched":
+        # the whole solve is one persistent kernel: its algorithmic bytes are
+        # the per-cell bytes of each CG iteration and refinement pass of every
+        # instance (BATCH_ITER_BYTES, OUTER_BYTES), over the event-timed solve
+        cleanup()
+        last = step_stats[-1]["all"]
+        algo = sum((st["iters"] * BATCH_ITER_BYTES + (st["outer"] + 1) * OUTER_BYTES) * n * n
+                   for st, (n, _) in zip(last, wl.shapes))
+        ms_solve = total_ms / args.steps
+        achieved = algo / (ms_solve * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_batched (persistent)", "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                    "traffic": recorded_traffic(wl.name, "k_batched"), "algorithmic_bytes_per_launch": algo,
+                    "avg_launch_us": round(ms_solve * 1e3, 2), "share_of_step": 1.0,
+                    "autotuned": {"tile": [tuned[0], tuned[1]], "sweeps": tuned[2]}}
+    else:
+        # ---- profiled pass: per-kernel-class event times (graph off)
+        L.mg_profile_enable(mg, True)
+        L.mg_profile_read(mg, reset=True)
+        nprof = min(args.steps, 5)
+        for i in range(nprof):
+            flush.fill_(float(i))
+            step()
+        prof = L.mg_profile_read(mg, reset=True)
+        L.mg_profile_enable(mg, False)
+        cleanup()
+        tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
+        dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
+        ms_dom, n_dom = prof[dom]
+        ncell = int(np.prod(wl.cells)) if args.config == "ns2d" else wl.units
+        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config == "ns2d" and dom != "xr_update" else 0)
+        if args.prec != "fp32" and args.config != "ns2d":
+            per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
+        algo = per_cell * ncell
+        achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                    "traffic": recorded_traffic(wl.name, dom), "algorithmic_bytes_per_launch": algo,
+                    "avg_launch_us": round(ms_dom / max(n_dom, 1) * 1e3, 2),
+                    "share_of_step": round(ms_dom / tot_prof, 3),
+                    "class_shares": {k: round(v[0] / tot_prof, 3) for k, v in prof.items() if v[1]}}
     units_total = wl.units * args.steps * world
     value = units_total / (total_ms * 1e-3)
     its = [s["iters"] for s in step_stats]
@@ -339,6 +416,20 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
             units += wl.units
         sample = "%d oracle step(s) of the %dx%d projection workload (pressure solve to 1e-6)" % (
             steps, wl.cells[0], wl.cells[1])
+    elif isinstance(wl, Batched):
+        for k in range(len(wl.shapes)):
+            if steps >= max_steps or t_total >= budget_s:
+                break
+            n = wl.shapes[k][0]
+            hier = P.build_hierarchy((n, n), wl.spacings[k], (0, 0, 0, 0), wl.solids[k])
+            mg = P.Multigrid(hier, s=1.0)
+            b = wl.rhs[k].astype(np.float64)
+            t0 = time.perf_counter()
+            P.pcg_ir(mg, b, tol=TOL)
+            t_total += time.perf_counter() - t0
+            steps += 1
+            units += int((~wl.solids[k]).sum())
+        sample = "the first %d instances of the batch, each solved by the oracle to 1e-6" % steps
     else:
         shape = wl.shape
         h = I.poisson_spacing(shape)
@@ -387,6 +478,8 @@ def main():
         if rank != 0:
             return
         wl = NS2D(scale=4) if args.config == "ns2d" else Poisson((256, 256), args.prec)
+        if args.config == "batched":
+            wl = Batched(limit=16)
         t0 = time.perf_counter()
         rate, sample, n = oracle_step_time(wl, budget_s=1e9, max_steps=args.warmup + args.steps)
         cores = 1
@@ -403,7 +496,8 @@ def main():
     out, wl = run_gpu(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
-            rate, sample, n = oracle_step_time(wl, budget_s=25.0, max_steps=1 if args.config != "poisson2d" else 5)
+            ms = {"poisson2d": 5, "batched": 64}.get(args.config, 1)
+            rate, sample, n = oracle_step_time(wl, budget_s=25.0, max_steps=ms)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
         print(json.dumps(out))
 

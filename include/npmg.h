@@ -259,6 +259,50 @@ mg_status ns_divergence_rhs(ns_handle ns, const float* d_us, const float* d_vs,
 /* Steps 3-5 only: q -= dt G dp (faces that G corrects), p += dp. */
 mg_status ns_correct(ns_handle ns, float* d_u, float* d_v, float* d_w,
                      float* d_p, const float* d_dp, double dt, void* stream);
+/*
+ * Batched solves: `count` independent 2D problems A_h x = b of different
+ * sizes (each the operator of mg_create), all solved to rel_tol by ONE
+ * persistent cooperative launch that a CUDA graph replays.  The launch walks
+ * the phases of the refinement / MG-PCG algorithm in lockstep over the
+ * instances (work items: (instance, tile) pairs per level, or whole
+ * instances), with grid-wide barriers between phases; converged instances
+ * drop out of the work lists.  Barrier waits are bounded: a barrier that
+ * cannot complete within the timeout makes the solve return MG_TIMEOUT.
+ *
+ * mg_create_batched:
+ *   shapes    count x 2 int64 (nx, ny) per instance; multiples of 4 with
+ *             more than 1024 cells each.
+ *   spacing   count x 2 doubles (hx, hy).
+ *   bc        4 face types shared by all instances (x-, x+, y-, y+).
+ *   d_masks   host array of `count` device uint8 pointers (1 = solid), each
+ *             may be NULL; or NULL for no masks.  Read during the call.
+ *   opt       only MG_FP32; pre/post give the initial sweep depth.
+ *   Allocates all instances' workspace.  A tile shape and sweep depth found
+ *   earlier by mg_tune_batched for the same GPU and batch (cache file
+ *   $NPMG_TUNE_CACHE, default ~/.cache/npmg_batched_tune.txt) is reused.
+ * mg_solve_batched: d_rhs / d_x are host arrays of `count` device pointers
+ *   (float32, instance-shaped; d_x = initial guess in, solution out).  `out`
+ *   = host array of `count` stats or NULL.  Synchronises the stream.  Returns
+ *   MG_OK when every instance converged, else the first non-OK status.
+ * mg_tune_batched: the autotuner.  Solves the given batch with every tile
+ *   shape (64x16, 32x16, 128x8) and sweep depth (1, 2, 3 Jacobi sweeps per
+ *   level and leg), keeps the fastest time to rel_tol, writes it to the cache
+ *   and reports it (host ints, each nullable).  d_x is overwritten.
+ * mg_batched_config: set the tile shape, sweep depth, barrier timeout
+ *   (seconds) and a test hook: with withhold_first_arrival != 0 one block
+ *   never arrives at the first barrier, so the solve must end in MG_TIMEOUT.
+ */
+typedef struct mg_batch_s* mg_batch;
+mg_status mg_create_batched(mg_batch* out, int count, const int64_t* shapes, const double* spacing, const int bc[4],
+                            const uint8_t* const* d_masks, const mg_options* opt, void* stream);
+mg_status mg_solve_batched(mg_batch b, const float* const* d_rhs, float* const* d_x, double rel_tol, void* stream,
+                           mg_stats* out);
+mg_status mg_tune_batched(mg_batch b, const float* const* d_rhs, float* const* d_x, double rel_tol, void* stream,
+                          int* out_tile_x, int* out_tile_y, int* out_sweeps);
+mg_status mg_batched_config(mg_batch b, int tile_x, int tile_y, int sweeps, double barrier_timeout_s,
+                            int withhold_first_arrival);
+mg_status mg_destroy_batched(mg_batch b);
+
 /* The pressure handle inside ns (owned by ns; do not destroy). */
 mg_handle ns_pressure_handle(ns_handle ns);
 mg_status ns_destroy(ns_handle ns);

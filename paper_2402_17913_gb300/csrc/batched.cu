@@ -1,0 +1,1202 @@
+// Batched solver: many independent 2D pressure-Poisson instances of uneven
+// size solved by ONE persistent launch (captured once in a CUDA graph).
+//
+// Every instance runs the single-grid algorithm (float-float refinement
+// around MG-PCG with the V(pre,post) cycle of Sec. 2.2).  The launch walks the
+// phases of that algorithm in lockstep over all instances; within a phase the
+// blocks share out work items -- (instance, tile) pairs on one level, or
+// whole instances for the per-instance steps -- and a grid-wide barrier
+// separates phases.  Phases are aligned by level counted from the finest
+// grid, so a small instance simply has no items in some phases.  An
+// instance that has converged leaves every later work list.  Each
+// instance's levels with <= 1024 cells are one block-local item (the same
+// cycle code as the single-grid coarse kernel).  Reductions are per
+// instance, in a fixed order over per-tile partial slots.
+//
+// The grid barrier spins a bounded number of times: if a block never
+// arrives, the others give up, raise an error flag and return, and the
+// solve reports MG_TIMEOUT instead of hanging.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <sys/stat.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "coarse.cuh"
+#include "launch.h"
+#include "mg_kernels.cuh"
+#include "refine.cuh"
+
+namespace npmg {
+
+constexpr int kBThreads = 256;
+constexpr int kBCoarseCells = 1024;
+
+struct BInst {
+  int L, kc, nfluid, nx, ny;
+  LevelDev lv[kMaxLevels];
+  float* b[kMaxLevels];  // right-hand side of level k (k >= 1)
+  float* x[kMaxLevels];  // down-leg x of level k (k < kc)
+  float* y[kMaxLevels];  // up-leg output of level k (1 <= k <= kc; y[kc] = coarse item output)
+  float *r, *z, *p0, *p1, *Ap, *d;
+  float2 *xf0, *xf1;
+  ff wff[2];             // finest operator weights c / h^2 (float-float)
+  ff cff;                // c = h_x^2
+  double c, c2;
+  int slot0, ntiles0;    // partial-sum slots of the level-0 tiles
+  int cfloats;           // shared floats of the coarse item
+  CoarseArgs ca;
+};
+
+struct BatchArgs {
+  BInst* inst;
+  SolveState* st;
+  int* cur;              // per instance: which xf buffer holds the iterate
+  const float* const* rhs;
+  float* const* xout;
+  int count;
+  const int4* items[kMaxLevels];  // (instance, tile x, tile y, slot) per level
+  int nitems[kMaxLevels];
+  int ntile_levels;      // max kc over instances
+  double* partials;      // one per level-0 tile
+  unsigned* bar;         // [0] arrivals, [1] generation, [2] error, [4..5] active counts
+  int sweeps;
+  float omega, s;
+  SolveParams prm;
+  long long spin_limit;
+  int withhold;          // test hook: block 0 never arrives at the first barrier
+};
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier
+__device__ __forceinline__ bool bwait(const BatchArgs& A, unsigned g) {
+  volatile unsigned* gen = A.bar + 1;
+  volatile unsigned* err = A.bar + 2;
+  for (long long i = 0; i < A.spin_limit; ++i) {
+    if (*gen != g) return true;
+    if (*err) return false;
+    __nanosleep(128);
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool grid_barrier(const BatchArgs& A, unsigned& epoch) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned*)(A.bar + 1);
+    __threadfence();
+    bool res;
+    if (A.withhold && blockIdx.x == 0 && epoch == 0) {
+      res = bwait(A, g);  // withheld arrival: nobody can pass this barrier
+    } else {
+      const unsigned t = atomicAdd(A.bar + 0, 1u);
+      if (t == gridDim.x - 1) {
+        atomicExch(A.bar + 0, 0u);
+        __threadfence();
+        atomicAdd(A.bar + 1, 1u);
+        res = true;
+      } else {
+        res = bwait(A, g);
+      }
+    }
+    if (!res) atomicExch(A.bar + 2, 1u);
+    __threadfence();
+    ok = res && *(volatile unsigned*)(A.bar + 2) == 0;
+  }
+  __syncthreads();
+  ++epoch;
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// tile work (2D, tile TX x TY, halo H = sweeps), explicit tile coordinates
+template <int TX, int TY>
+struct BReg {
+  int H, RX, RY, R, ox, oy;
+  __device__ __forceinline__ BReg(int h, int tx, int ty) {
+    H = h;
+    RX = TX + 2 * h;
+    RY = TY + 2 * h;
+    R = RX * RY;
+    ox = tx * TX - h;
+    oy = ty * TY - h;
+  }
+};
+
+template <int TX, int TY>
+__device__ __forceinline__ void b_load(const BReg<TX, TY>& g, const LevelDev& L, const float* __restrict__ f, float* s,
+                                       uint8_t* sm) {
+  for (int i = threadIdx.x; i < g.R; i += blockDim.x) {
+    const int lx = i % g.RX, ly = i / g.RX;
+    const int gx = g.ox + lx, gy = g.oy + ly;
+    float v = 0.f;
+    uint8_t m = 0;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      const size_t gi = (size_t)gy * L.nx + gx;
+      m = L.cell ? L.cell[gi] : kFluidBit;
+      if (m) v = f[gi];
+    }
+    s[i] = v;
+    sm[i] = m;
+  }
+}
+
+template <int TX, int TY>
+__device__ __forceinline__ float b_diag(const BReg<TX, TY>& g, const LevelDev& L, int lx, int ly, uint8_t m) {
+  return L.cell ? diag_at<2, true>(L, g.ox + lx, g.oy + ly, 0, m) : diag_at<2, false>(L, g.ox + lx, g.oy + ly, 0, m);
+}
+
+template <int TX, int TY>
+__device__ __forceinline__ void b_sweep(const BReg<TX, TY>& g, const LevelDev& L, const float* xin, float* xout,
+                                        const float* sb, const uint8_t* sm, int m, float omega, bool from_zero) {
+  const int SX = TX + 2 * m, SY = TY + 2 * m;
+  for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
+    const int lx = i % SX + g.H - m, ly = i / SX + g.H - m;
+    const int li = ly * g.RX + lx;
+    const uint8_t mm = sm[li];
+    float v = 0.f;
+    if (mm) {
+      const float d = b_diag(g, L, lx, ly, mm);
+      if (from_zero) {
+        v = omega * sb[li] / d;
+      } else {
+        const float nb = L.wx * (xin[li - 1] + xin[li + 1]) + L.wy * (xin[li - g.RX] + xin[li + g.RX]);
+        v = xin[li] + omega * (sb[li] - (d * xin[li] - nb)) / d;
+      }
+    }
+    xout[li] = v;
+  }
+  __syncthreads();
+}
+
+// down leg of one tile: sweeps from zero, x, restricted residual
+template <int TX, int TY>
+__device__ void b_down(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
+                       float* __restrict__ bc, int sweeps, float omega, float* S) {
+  const BReg<TX, TY> g(sweeps > 0 ? sweeps : 1, tx, ty);
+  float* sb = S;
+  float* s0 = sb + g.R;
+  float* s1 = s0 + g.R;
+  uint8_t* sm = reinterpret_cast<uint8_t*>(s1 + g.R);
+  __syncthreads();
+  b_load<TX, TY>(g, L, b, sb, sm);
+  __syncthreads();
+  float* cur = s0;
+  float* nxt = s1;
+  if (sweeps == 0) {
+    for (int i = threadIdx.x; i < g.R; i += blockDim.x) s0[i] = 0.f;
+    __syncthreads();
+  } else {
+    b_sweep<TX, TY>(g, L, nullptr, s0, sb, sm, sweeps, omega, true);
+    for (int j = 2; j <= sweeps; ++j) {
+      b_sweep<TX, TY>(g, L, cur, nxt, sb, sm, sweeps - j + 1, omega, false);
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+  for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+    const int lx = i % TX + g.H, ly = i / TX + g.H;
+    const int gx = g.ox + lx, gy = g.oy + ly;
+    if (gx < L.nx && gy < L.ny) x[(size_t)gy * L.nx + gx] = cur[ly * g.RX + lx];
+  }
+  const int cnx = L.nx / 2, cny = L.ny / 2;
+  for (int i = threadIdx.x; i < (TX / 2) * (TY / 2); i += blockDim.x) {
+    const int cx = i % (TX / 2), cy = i / (TX / 2);
+    const int gcx = tx * (TX / 2) + cx, gcy = ty * (TY / 2) + cy;
+    if (gcx >= cnx || gcy >= cny) continue;
+    float sum = 0.f;
+    for (int ay = 0; ay < 2; ++ay)
+      for (int ax = 0; ax < 2; ++ax) {
+        const int lx = g.H + 2 * cx + ax, ly = g.H + 2 * cy + ay;
+        const int li = ly * g.RX + lx;
+        const uint8_t mm = sm[li];
+        if (!mm) continue;
+        const float d = b_diag(g, L, lx, ly, mm);
+        const float nb = L.wx * (cur[li - 1] + cur[li + 1]) + L.wy * (cur[li - g.RX] + cur[li + g.RX]);
+        sum += sb[li] - (d * cur[li] - nb);
+      }
+    bc[(size_t)gcy * cnx + gcx] = 0.25f * sum;
+  }
+}
+
+// up leg of one tile: x + s P e, sweeps, output; returns this thread's
+// share of (b, out) when `dot`
+template <int TX, int TY>
+__device__ float b_up(const LevelDev& L, int tx, int ty, const float* __restrict__ b, const float* __restrict__ xin,
+                      float* __restrict__ xout, const float* __restrict__ e, int sweeps, float omega, float s,
+                      bool dot, float* S) {
+  const BReg<TX, TY> g(sweeps > 0 ? sweeps : 1, tx, ty);
+  float* sb = S;
+  float* s0 = sb + g.R;
+  float* s1 = s0 + g.R;
+  uint8_t* sm = reinterpret_cast<uint8_t*>(s1 + g.R);
+  __syncthreads();
+  const int cnx = L.nx / 2;
+  for (int i = threadIdx.x; i < g.R; i += blockDim.x) {
+    const int lx = i % g.RX, ly = i / g.RX;
+    const int gx = g.ox + lx, gy = g.oy + ly;
+    float v = 0.f, bv = 0.f;
+    uint8_t m = 0;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      const size_t gi = (size_t)gy * L.nx + gx;
+      m = L.cell ? L.cell[gi] : kFluidBit;
+      if (m) {
+        v = xin[gi] + s * e[(size_t)(gy >> 1) * cnx + (gx >> 1)];
+        bv = b[gi];
+      }
+    }
+    s0[i] = v;
+    sb[i] = bv;
+    sm[i] = m;
+  }
+  __syncthreads();
+  float* cur = s0;
+  float* nxt = s1;
+  for (int j = 1; j <= sweeps; ++j) {
+    b_sweep<TX, TY>(g, L, cur, nxt, sb, sm, sweeps - j, omega, false);
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+    const int lx = i % TX + g.H, ly = i / TX + g.H;
+    const int gx = g.ox + lx, gy = g.oy + ly;
+    if (gx < L.nx && gy < L.ny) {
+      const int li = ly * g.RX + lx;
+      xout[(size_t)gy * L.nx + gx] = cur[li];
+      if (dot) acc = fmaf(sb[li], cur[li], acc);
+    }
+  }
+  return acc;
+}
+
+// cells of a level-0 tile, one by one: callback(i, x, y)
+template <int TX, int TY, typename F>
+__device__ __forceinline__ void b_cells(const BInst& I, int tx, int ty, F&& f) {
+  for (int j = threadIdx.x; j < TX * TY; j += blockDim.x) {
+    const int x = tx * TX + j % TX, y = ty * TY + j / TX;
+    if (x < I.nx && y < I.ny) f((size_t)y * I.nx + x, x, y);
+  }
+}
+
+__device__ __forceinline__ double block_total(float v) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  const double t = block_sum((double)v, sh);
+  if (threadIdx.x == 0) tot = t;
+  __syncthreads();
+  return tot;
+}
+
+// per-instance fixed-order reduction of the level-0 tile partial slots
+__device__ __forceinline__ double reduce_slots(const BatchArgs& A, const BInst& I) {
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < I.ntiles0; j += blockDim.x) acc += __ldcg(A.partials + I.slot0 + j);
+  __shared__ double sh[32];
+  __shared__ double tot;
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) tot = t;
+  __syncthreads();
+  return tot;
+}
+
+// active-instance counters alternate between two slots (the reducing phase
+// clears the other one for the next count)
+__device__ __forceinline__ void count_active(const BatchArgs& A, int slot, bool active) {
+  if (threadIdx.x == 0 && active) atomicAdd(A.bar + 4 + slot, 1u);
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(kBThreads) k_batched(const __grid_constant__ BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* S = reinterpret_cast<float*>(smem_raw);
+  unsigned epoch = 0;
+  int cslot = 0;
+  const int4* it0 = A.items[0];
+  const int n0 = A.nitems[0];
+  const float omega = A.omega;
+  // ---- init: x = (guess, 0) on fluid cells, ||b||^2 per tile
+  for (int w = blockIdx.x; w < n0; w += gridDim.x) {
+    const int4 item = it0[w];
+    const BInst& I = A.inst[item.x];
+    const float* b = A.rhs[item.x];
+    const float* xg = A.xout[item.x];
+    float acc = 0.f;
+    b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
+      const bool fl = I.lv[0].cell ? I.lv[0].cell[i] != 0 : true;
+      I.xf0[i] = make_float2(fl ? xg[i] : 0.f, 0.f);
+      if (fl) acc = fmaf(b[i], b[i], acc);
+    });
+    const double t = block_total(acc);
+    if (threadIdx.x == 0) A.partials[item.w] = t;
+  }
+  if (!grid_barrier(A, epoch)) return;
+  for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+    const BInst& I = A.inst[w];
+    const double tot = reduce_slots(A, I);
+    if (threadIdx.x == 0) {
+      SolveParams prm = A.prm;
+      prm.n_fluid = I.nfluid > 0 ? I.nfluid : 1;
+      init_state(&A.st[w], prm, tot, I.c);
+      A.cur[w] = 0;
+    }
+  }
+  if (!grid_barrier(A, epoch)) return;
+  // ---- refinement loop
+  for (int outer = 0; outer <= A.prm.max_outer; ++outer) {
+    const bool update = outer > 0;
+    // residual of the float-float iterate (after x += sigma d')
+    for (int w = blockIdx.x; w < n0; w += gridDim.x) {
+      const int4 item = it0[w];
+      SolveState& st = A.st[item.x];
+      if (st.outer_done) continue;
+      const BInst& I = A.inst[item.x];
+      const LevelDev& L = I.lv[0];
+      const float* b = A.rhs[item.x];
+      const int cur = A.cur[item.x];
+      const float2* xin = cur ? I.xf1 : I.xf0;
+      float2* xo = cur ? I.xf0 : I.xf1;
+      const double sig_old_d = st.sigma;
+      const double sig_new_d =
+          update ? pow2_floor(sig_old_d * sqrt(fmax(st.rnorm2, 1e-300) / (double)st.n_fluid)) : sig_old_d;
+      const float sig_old = (float)sig_old_d, inv_sig_new = (float)(1.0 / sig_new_d);
+      auto xv = [&](size_t j) -> ff {
+        const float2 q = xin[j];
+        if (!update) return {q.x, q.y};
+        const ff s2 = two_sum(q.x, sig_old * I.d[j]);
+        return quick_two_sum(s2.hi, s2.lo + q.y);
+      };
+      float acc = 0.f;
+      b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int cx, int cy) {
+        const uint8_t m = L.cell ? L.cell[i] : kFluidBit;
+        if (!m) {
+          if (update) xo[i] = make_float2(0.f, 0.f);
+          I.r[i] = 0.f;
+          return;
+        }
+        const int kx = L.cell ? (m & 3) : axis_count(cx, L.nx, L.bcD, 0);
+        const int ky = L.cell ? ((m >> 2) & 3) : axis_count(cy, L.ny, L.bcD, 2);
+        const ff zero = {0.f, 0.f};
+        const ff xc = xv(i);
+        const ff xl = cx > 0 ? xv(i - 1) : zero, xr = cx < L.nx - 1 ? xv(i + 1) : zero;
+        const ff xd = cy > 0 ? xv(i - L.nx) : zero, xu = cy < L.ny - 1 ? xv(i + L.nx) : zero;
+        ff ax = ff_mul(ff_add(ff_mul(xc, ff{(float)kx, 0.f}), ff_neg(ff_add(xl, xr))), I.wff[0]);
+        ax = ff_add(ax, ff_mul(ff_add(ff_mul(xc, ff{(float)ky, 0.f}), ff_neg(ff_add(xd, xu))), I.wff[1]));
+        const ff r = ff_add(ff_mul(ff{b[i], 0.f}, I.cff), ff_neg(ax));
+        const float rs = r.hi + r.lo;
+        I.r[i] = rs * inv_sig_new;
+        acc = fmaf(rs, rs, acc);
+        if (update) xo[i] = make_float2(xc.hi, xc.lo);
+      });
+      const double t = block_total(acc);
+      if (threadIdx.x == 0) A.partials[item.w] = t;
+    }
+    if (!grid_barrier(A, epoch)) return;
+    for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+      SolveState& st = A.st[w];
+      if (st.outer_done) continue;
+      const BInst& I = A.inst[w];
+      const double tot = reduce_slots(A, I);
+      if (threadIdx.x == 0) {
+        const double sig_old_d = st.sigma;
+        const double sig_new_d =
+            update ? pow2_floor(sig_old_d * sqrt(fmax(st.rnorm2, 1e-300) / (double)st.n_fluid)) : sig_old_d;
+        if (update) A.cur[w] ^= 1;
+        outer_decide(&st, tot, I.c2, sig_new_d, update);
+        st.first = 1;
+      }
+      __syncthreads();
+      count_active(A, cslot, !st.outer_done);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.bar[4 + (cslot ^ 1)] = 0u;
+    if (!grid_barrier(A, epoch)) return;
+    const unsigned active_outer = *(volatile unsigned*)(A.bar + 4 + cslot);
+    cslot ^= 1;
+    if (active_outer == 0) break;
+    // ---- CG iterations
+    for (int iter = 0; iter < A.prm.max_inner; ++iter) {
+      // down legs, level by level
+      for (int k = 0; k < A.ntile_levels; ++k) {
+        const int4* its = A.items[k];
+        for (int w = blockIdx.x; w < A.nitems[k]; w += gridDim.x) {
+          const int4 item = its[w];
+          if (A.st[item.x].inner_done) continue;
+          const BInst& I = A.inst[item.x];
+          b_down<TX, TY>(I.lv[k], item.y, item.z, k == 0 ? I.r : I.b[k], I.x[k], I.b[k + 1], A.sweeps, omega, S);
+        }
+        if (!grid_barrier(A, epoch)) return;
+      }
+      // block-local coarse part of each instance
+      for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+        if (A.st[w].inner_done) continue;
+        const BInst& I = A.inst[w];
+        __syncthreads();
+        coarse_cycle<2, float>(I.ca, I.kc == 0 ? I.r : I.b[I.kc], I.kc == 0 ? I.z : I.y[I.kc], nullptr, S,
+                               I.cfloats);
+      }
+      if (!grid_barrier(A, epoch)) return;
+      // up legs; the finest produces z = M r and (r, z)
+      for (int k = A.ntile_levels - 1; k >= 0; --k) {
+        const int4* its = A.items[k];
+        for (int w = blockIdx.x; w < A.nitems[k]; w += gridDim.x) {
+          const int4 item = its[w];
+          if (A.st[item.x].inner_done) continue;
+          const BInst& I = A.inst[item.x];
+          const float acc = b_up<TX, TY>(I.lv[k], item.y, item.z, k == 0 ? I.r : I.b[k], I.x[k],
+                                         k == 0 ? I.z : I.y[k], I.y[k + 1], A.sweeps, omega, A.s, k == 0, S);
+          if (k == 0) {
+            const double t = block_total(acc);
+            if (threadIdx.x == 0) A.partials[item.w] = t;
+          }
+        }
+        if (!grid_barrier(A, epoch)) return;
+      }
+      // (r, z) per instance -> beta
+      for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+        SolveState& st = A.st[w];
+        if (st.inner_done) continue;
+        const BInst& I = A.inst[w];
+        const double tot = reduce_slots(A, I);
+        if (threadIdx.x == 0) {
+          st.rz = tot;
+          st.beta = (st.first || !st.krylov) ? 0.0 : tot / st.rz_old;
+          st.rz_old = tot;
+        }
+      }
+      if (!grid_barrier(A, epoch)) return;
+      // p = z + beta p, Ap, (p, Ap)
+      for (int w = blockIdx.x; w < n0; w += gridDim.x) {
+        const int4 item = it0[w];
+        const SolveState& st = A.st[item.x];
+        if (st.inner_done) continue;
+        const BInst& I = A.inst[item.x];
+        const LevelDev& L = I.lv[0];
+        const bool first = st.first || !st.krylov;
+        const float beta = first ? 0.f : (float)st.beta;
+        const float* pold = (st.it & 1) ? I.p1 : I.p0;
+        float* pnew = (st.it & 1) ? I.p0 : I.p1;
+        auto pv = [&](size_t j) { return first ? I.z[j] : fmaf(beta, pold[j], I.z[j]); };
+        float acc = 0.f;
+        b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int cx, int cy) {
+          const uint8_t m = L.cell ? L.cell[i] : kFluidBit;
+          if (!m) {
+            pnew[i] = 0.f;
+            I.Ap[i] = 0.f;
+            return;
+          }
+          const float pc = pv(i);
+          float nb = 0.f;
+          if (cx > 0) nb += L.wx * pv(i - 1);
+          if (cx < L.nx - 1) nb += L.wx * pv(i + 1);
+          if (cy > 0) nb += L.wy * pv(i - L.nx);
+          if (cy < L.ny - 1) nb += L.wy * pv(i + L.nx);
+          const float dg = L.cell ? diag_at<2, true>(L, cx, cy, 0, m) : diag_at<2, false>(L, cx, cy, 0, m);
+          const float ap = dg * pc - nb;
+          pnew[i] = pc;
+          I.Ap[i] = ap;
+          acc = fmaf(pc, ap, acc);
+        });
+        const double t = block_total(acc);
+        if (threadIdx.x == 0) A.partials[item.w] = t;
+      }
+      if (!grid_barrier(A, epoch)) return;
+      for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+        SolveState& st = A.st[w];
+        if (st.inner_done) continue;
+        const double tot = reduce_slots(A, A.inst[w]);
+        if (threadIdx.x == 0) {
+          st.pAp = tot;
+          st.alpha = st.krylov ? st.rz / tot : 1.0;
+        }
+      }
+      if (!grid_barrier(A, epoch)) return;
+      // d += alpha p, r -= alpha Ap, ||r||^2
+      for (int w = blockIdx.x; w < n0; w += gridDim.x) {
+        const int4 item = it0[w];
+        const SolveState& st = A.st[item.x];
+        if (st.inner_done) continue;
+        const BInst& I = A.inst[item.x];
+        const float alpha = (float)st.alpha;
+        const bool first = st.first;
+        const float* p = (st.it & 1) ? I.p0 : I.p1;
+        float acc = 0.f;
+        b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
+          I.d[i] = first ? alpha * p[i] : fmaf(alpha, p[i], I.d[i]);
+          const float rv = fmaf(-alpha, I.Ap[i], I.r[i]);
+          I.r[i] = rv;
+          acc = fmaf(rv, rv, acc);
+        });
+        const double t = block_total(acc);
+        if (threadIdx.x == 0) A.partials[item.w] = t;
+      }
+      if (!grid_barrier(A, epoch)) return;
+      for (int w = blockIdx.x; w < A.count; w += gridDim.x) {
+        SolveState& st = A.st[w];
+        if (st.inner_done) continue;
+        const double tot = reduce_slots(A, A.inst[w]);
+        if (threadIdx.x == 0) inner_decide(&st, tot);
+        __syncthreads();
+        count_active(A, cslot, !st.inner_done);
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) A.bar[4 + (cslot ^ 1)] = 0u;
+      if (!grid_barrier(A, epoch)) return;
+      const unsigned active = *(volatile unsigned*)(A.bar + 4 + cslot);
+      cslot ^= 1;
+      if (active == 0) break;
+    }
+  }
+  // ---- result: float output = hi + lo; zero right-hand side -> zero solution
+  for (int w = blockIdx.x; w < n0; w += gridDim.x) {
+    const int4 item = it0[w];
+    const BInst& I = A.inst[item.x];
+    const SolveState& st = A.st[item.x];
+    const float2* xf = A.cur[item.x] ? I.xf1 : I.xf0;
+    float* out = A.xout[item.x];
+    const bool zero = st.bnorm2 == 0.0;
+    b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
+      const float2 v = xf[i];
+      out[i] = zero ? 0.f : v.x + v.y;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+struct TileChoice {
+  int tx, ty;
+};
+static const TileChoice kTiles[3] = {{64, 16}, {32, 16}, {128, 8}};
+
+template <int TX, int TY>
+static void* kernel_ptr() {
+  return (void*)k_batched<TX, TY>;
+}
+static void* batched_kernel(int t) {
+  if (t == 0) return kernel_ptr<64, 16>();
+  if (t == 1) return kernel_ptr<32, 16>();
+  return kernel_ptr<128, 8>();
+}
+
+}  // namespace npmg
+
+using namespace npmg;
+
+struct GraphKey {
+  double tol, timeout;
+  int withhold;
+  bool operator==(const GraphKey& o) const { return tol == o.tol && timeout == o.timeout && withhold == o.withhold; }
+};
+
+struct mg_batch_s {
+  int count, device, nsm;
+  mg_options opt;
+  double inner_floor;
+  std::vector<BInst> inst;       // host copy
+  BInst* d_inst;
+  SolveState* d_st;
+  SolveState* h_st;              // pinned
+  int* d_cur;
+  const float** d_rhs;
+  float** d_xout;
+  void** h_ptrs;                 // pinned staging of the pointer tables
+  std::vector<int4*> d_items;
+  int nitems[kMaxLevels];
+  int ntile_levels;
+  double* d_partials;
+  unsigned* d_bar;
+  char* pool;
+  size_t pool_bytes;
+  int tile, sweeps;              // current choice (autotuned)
+  size_t smem[3][4];             // dynamic shared memory per (tile, sweeps)
+  int grid[3][4];
+  cudaGraphExec_t graph[3][4];
+  GraphKey gkey[3][4];
+  int withhold;
+  double timeout_s;
+  cudaEvent_t ev0, ev1;
+  std::string tune_key;
+};
+
+static size_t batched_smem(int tx, int ty, int sweeps, size_t coarse_bytes) {
+  const int h = sweeps > 0 ? sweeps : 1;
+  const size_t R = (size_t)(tx + 2 * h) * (ty + 2 * h);
+  size_t t = 3 * R * 4 + ((R + 15) & ~size_t(15));
+  return t > coarse_bytes ? t : coarse_bytes;
+}
+
+static std::string tune_cache_path() {
+  const char* e = getenv("NPMG_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/npmg_batched_tune.txt";
+}
+
+// cache lines: "<key> <tile> <sweeps> <ms>"
+static bool tune_lookup(const std::string& key, int* tile, int* sweeps) {
+  FILE* f = fopen(tune_cache_path().c_str(), "r");
+  if (!f) return false;
+  char k[512];
+  int t, s;
+  double ms;
+  bool found = false;
+  while (fscanf(f, "%511s %d %d %lf", k, &t, &s, &ms) == 4)
+    if (key == k && t >= 0 && t < 3 && s >= 1 && s <= 3) {
+      *tile = t;
+      *sweeps = s;
+      found = true;
+    }
+  fclose(f);
+  return found;
+}
+
+static void tune_store(const std::string& key, int tile, int sweeps, double ms) {
+  std::string path = tune_cache_path();
+  std::string dir = path.substr(0, path.find_last_of('/'));
+  if (!dir.empty()) mkdir(dir.c_str(), 0755);  // may already exist
+  FILE* f = fopen(path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %.4f\n", key.c_str(), tile, sweeps, ms);
+  fclose(f);
+}
+
+static mg_status batched_launch(mg_batch_s* B, int tile, int sweeps, double tol, cudaStream_t s) {
+  BatchArgs A;
+  memset(&A, 0, sizeof(A));
+  A.inst = B->d_inst;
+  A.st = B->d_st;
+  A.cur = B->d_cur;
+  A.rhs = B->d_rhs;
+  A.xout = B->d_xout;
+  A.count = B->count;
+  for (int k = 0; k < kMaxLevels; ++k) {
+    A.items[k] = k < (int)B->d_items.size() ? B->d_items[k] : nullptr;
+    A.nitems[k] = B->nitems[k];
+  }
+  A.ntile_levels = B->ntile_levels;
+  A.partials = B->d_partials;
+  A.bar = B->d_bar;
+  A.sweeps = sweeps;
+  A.omega = (float)B->opt.omega;
+  A.s = (float)B->opt.coarse_scale;
+  A.prm.tol = tol;
+  A.prm.inner_floor = B->inner_floor;
+  A.prm.max_inner = B->opt.max_inner;
+  A.prm.max_outer = B->opt.max_outer;
+  A.prm.krylov = B->opt.krylov;
+  A.spin_limit = (long long)(B->timeout_s * 1e9 / 200.0) + 1;
+  A.withhold = B->withhold;
+  void* args[] = {&A};
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(B->grid[tile][sweeps], 1, 1);
+  cfg.blockDim = dim3(kBThreads, 1, 1);
+  cfg.dynamicSmemBytes = B->smem[tile][sweeps];
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  // one persistent launch per solve, captured once in a CUDA graph (per tile
+  // shape and sweep depth; recaptured when the tolerance or hooks change)
+  GraphKey key{tol, B->timeout_s, B->withhold};
+  if (!B->graph[tile][sweeps] || !(B->gkey[tile][sweeps] == key)) {
+    if (B->graph[tile][sweeps]) cudaGraphExecDestroy(B->graph[tile][sweeps]);
+    B->graph[tile][sweeps] = nullptr;
+    cudaStream_t cs;
+    NPMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cfg.stream = cs;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(B->d_bar, 0, 8 * sizeof(unsigned), cs);
+      cudaError_t e2 = cudaLaunchKernelExC(&cfg, batched_kernel(tile), args);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e1 != cudaSuccess) e = e1;
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph[tile][sweeps], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      set_error("batched solve: graph capture failed: %s", cudaGetErrorString(e));
+      return MG_ERR_CUDA;
+    }
+    B->gkey[tile][sweeps] = key;
+  }
+  NPMG_CUDA(cudaGraphLaunch(B->graph[tile][sweeps], s));
+  return MG_OK;
+}
+
+static mg_status build_items(mg_batch_s* B, int tile, cudaStream_t s);
+
+extern "C" {
+
+mg_status mg_create_batched(mg_batch* out, int count, const int64_t* shapes, const double* spacing, const int bc[4],
+                            const uint8_t* const* d_masks, const mg_options* opt, void* stream) {
+  if (!out || count <= 0 || !shapes || !spacing || !bc) {
+    set_error("mg_create_batched: invalid arguments");
+    return MG_ERR_INVALID;
+  }
+  *out = nullptr;
+  mg_options o;
+  if (opt) o = *opt;
+  else mg_default_options(&o);
+  if (o.prec != MG_FP32) {
+    set_error("mg_create_batched: only MG_FP32 inner storage");
+    return MG_ERR_INVALID;
+  }
+  int bcD = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (bc[f] != MG_BC_DIRICHLET && bc[f] != MG_BC_NEUMANN) {
+      set_error("mg_create_batched: bad bc[%d]", f);
+      return MG_ERR_INVALID;
+    }
+    if (bc[f] == MG_BC_DIRICHLET) bcD |= 1 << f;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_batch_s* B = new mg_batch_s();
+  B->count = count;
+  B->opt = o;
+  B->inner_floor = o.inner_floor > 0 ? o.inner_floor : 1e-4;
+  B->timeout_s = 2.0;
+  B->withhold = 0;
+  cudaGetDevice(&B->device);
+  cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device);
+  B->inst.resize(count);
+  // --- geometry and memory plan
+  size_t bytes = 0;
+  auto reserve = [&](size_t n) {
+    const size_t o2 = (bytes + 255) / 256 * 256;
+    bytes = o2 + n;
+    return o2;
+  };
+  struct Off {
+    size_t solid[kMaxLevels], cell[kMaxLevels], b[kMaxLevels], x[kMaxLevels], y[kMaxLevels];
+    size_t r, z, p0, p1, Ap, d, xf0, xf1, inv;
+  };
+  std::vector<Off> off(count);
+  int max_kc = 0;
+  size_t coarse_bytes = 0;
+  long long total_cells = 0;
+  int max_side = 0;
+  for (int i = 0; i < count; ++i) {
+    BInst& I = B->inst[i];
+    memset(&I, 0, sizeof(I));
+    const int nx = (int)shapes[2 * i], ny = (int)shapes[2 * i + 1];
+    if (nx % 4 || ny % 4 || (long long)nx * ny <= kBCoarseCells || !(spacing[2 * i] > 0) ||
+        !(spacing[2 * i + 1] > 0)) {
+      delete B;
+      set_error("mg_create_batched: instance %d: sides must be multiples of 4 with more than %d cells", i,
+                kBCoarseCells);
+      return MG_ERR_INVALID;
+    }
+    if (!d_masks || !d_masks[i]) {
+      if (!bcD) {
+        delete B;
+        set_error("mg_create_batched: instance %d is singular (all Neumann, no mask)", i);
+        return MG_ERR_INVALID;
+      }
+    }
+    I.nx = nx;
+    I.ny = ny;
+    total_cells += (long long)nx * ny;
+    max_side = nx > max_side ? nx : max_side;
+    int L = 1;
+    while ((nx >> (L - 1)) % 2 == 0 && (ny >> (L - 1)) % 2 == 0 && (nx >> L) >= 4 && (ny >> L) >= 4 && L < kMaxLevels)
+      ++L;
+    I.L = L;
+    int kc = L - 1;
+    while (kc > 0 && (size_t)(nx >> (kc - 1)) * (ny >> (kc - 1)) <= (size_t)kBCoarseCells) --kc;
+    I.kc = kc;
+    max_kc = kc > max_kc ? kc : max_kc;
+    const double c = spacing[2 * i] * spacing[2 * i];
+    I.c = c;
+    I.c2 = c * c;
+    const double w[2] = {1.0, c / (spacing[2 * i + 1] * spacing[2 * i + 1])};
+    for (int a = 0; a < 2; ++a) {
+      I.wff[a].hi = (float)w[a];
+      I.wff[a].lo = (float)(w[a] - (double)I.wff[a].hi);
+    }
+    I.cff.hi = (float)c;
+    I.cff.lo = (float)(c - (double)I.cff.hi);
+    const bool masked = d_masks && d_masks[i];
+    Off& f = off[i];
+    for (int k = 0; k < L; ++k) {
+      LevelDev& lv = I.lv[k];
+      lv.nx = nx >> k;
+      lv.ny = ny >> k;
+      lv.nz = 1;
+      const double hx = spacing[2 * i] * (1 << k), hy = spacing[2 * i + 1] * (1 << k);
+      lv.wx = (float)(c / (hx * hx));
+      lv.wy = (float)(c / (hy * hy));
+      lv.wz = 0.f;
+      lv.bcD = bcD;
+      const size_t n = (size_t)lv.nx * lv.ny;
+      if (masked) {
+        f.solid[k] = reserve(n);
+        f.cell[k] = reserve(n);
+      }
+      if (k >= 1 && k <= kc) f.b[k] = reserve(n * 4);
+      if (k < kc) f.x[k] = reserve(n * 4);
+      if (k >= 1 && k <= kc) f.y[k] = reserve(n * 4);
+    }
+    const size_t n0 = (size_t)nx * ny;
+    f.r = reserve(n0 * 4);
+    f.z = reserve(n0 * 4);
+    f.p0 = reserve(n0 * 4);
+    f.p1 = reserve(n0 * 4);
+    f.Ap = reserve(n0 * 4);
+    f.d = reserve(n0 * 4);
+    f.xf0 = reserve(n0 * 8);
+    f.xf1 = reserve(n0 * 8);
+    const int nc = (nx >> (L - 1)) * (ny >> (L - 1));
+    if (nc > 1024) {
+      delete B;
+      set_error("mg_create_batched: instance %d coarsest level too large", i);
+      return MG_ERR_INVALID;
+    }
+    f.inv = reserve((size_t)2 * nc * nc * 8);
+    // tiles of every level handled as tiles (k < kc), tile 64 x 16 grid as the
+    // slot basis (the item lists are rebuilt per tile shape below)
+    I.cfloats = 0;
+  }
+  B->ntile_levels = max_kc;
+  // partial slots: worst case over tile shapes = the smallest tile (32 x 16)
+  long long max_slots = 0;
+  for (int i = 0; i < count; ++i) max_slots += (long long)((B->inst[i].nx + 31) / 32) * ((B->inst[i].ny + 15) / 16);
+  const size_t off_partials = reserve((size_t)max_slots * 8);
+  const size_t off_bar = reserve(64);
+  cudaError_t ce = cudaMalloc((void**)&B->pool, bytes);
+  if (ce != cudaSuccess) {
+    delete B;
+    set_error("mg_create_batched: cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(ce));
+    return MG_ERR_OOM;
+  }
+  B->pool_bytes = bytes;
+  mg_status st = MG_OK;
+#define NPMG_BTRY(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_error("mg_create_batched: %s: %s", #call, cudaGetErrorString(e_));               \
+      st = MG_ERR_CUDA;                                                                    \
+      goto fail;                                                                           \
+    }                                                                                      \
+  } while (0)
+  NPMG_BTRY(cudaMemsetAsync(B->pool, 0, bytes, s));
+  B->d_partials = (double*)(B->pool + off_partials);
+  B->d_bar = (unsigned*)(B->pool + off_bar);
+  for (int i = 0; i < count; ++i) {
+    BInst& I = B->inst[i];
+    Off& f = off[i];
+    char* P = B->pool;
+    const bool masked = d_masks && d_masks[i];
+    int nf = I.nx * I.ny;
+    for (int k = 0; k < I.L; ++k) {
+      if (masked) {
+        uint8_t* sd = (uint8_t*)(P + f.solid[k]);
+        if (k == 0) NPMG_BTRY(cudaMemcpyAsync(sd, d_masks[i], (size_t)I.nx * I.ny, cudaMemcpyDeviceToDevice, s));
+        else {
+          const int64_t fine[3] = {I.lv[k - 1].nx, I.lv[k - 1].ny, 1};
+          NPMG_BTRY(launch_coarsen_solid(2, fine, (uint8_t*)(P + f.solid[k - 1]), sd, s));
+        }
+        const int64_t n3[3] = {I.lv[k].nx, I.lv[k].ny, 1};
+        NPMG_BTRY(launch_cell_bytes(2, n3, I.lv[k].bcD, sd, (uint8_t*)(P + f.cell[k]), s));
+        I.lv[k].cell = (uint8_t*)(P + f.cell[k]);
+      } else {
+        I.lv[k].cell = nullptr;
+      }
+      if (k >= 1 && k <= I.kc) {
+        I.b[k] = (float*)(P + f.b[k]);
+        I.y[k] = (float*)(P + f.y[k]);
+      }
+      if (k < I.kc) I.x[k] = (float*)(P + f.x[k]);
+    }
+    if (masked) {
+      std::vector<uint8_t> hm((size_t)I.nx * I.ny);
+      NPMG_BTRY(cudaMemcpyAsync(hm.data(), d_masks[i], hm.size(), cudaMemcpyDeviceToHost, s));
+      NPMG_BTRY(cudaStreamSynchronize(s));
+      nf = 0;
+      for (uint8_t v : hm) nf += v ? 0 : 1;
+    }
+    I.nfluid = nf;
+    I.r = (float*)(P + f.r);
+    I.z = (float*)(P + f.z);
+    I.p0 = (float*)(P + f.p0);
+    I.p1 = (float*)(P + f.p1);
+    I.Ap = (float*)(P + f.Ap);
+    I.d = (float*)(P + f.d);
+    I.xf0 = (float2*)(P + f.xf0);
+    I.xf1 = (float2*)(P + f.xf1);
+    // coarsest inverse and the block-local coarse item
+    {
+      const int Lc = I.L - 1;
+      const double hx = std::ldexp(1.0, Lc), c = I.c;
+      (void)hx;
+      const double wc[3] = {(double)I.lv[Lc].wx, (double)I.lv[Lc].wy, 0.0};
+      const double wd[3] = {c / (spacing[2 * i] * spacing[2 * i] * std::ldexp(1.0, 2 * Lc)),
+                            c / (spacing[2 * i + 1] * spacing[2 * i + 1] * std::ldexp(1.0, 2 * Lc)), 0.0};
+      (void)wc;
+      const int64_t n3[3] = {I.lv[Lc].nx, I.lv[Lc].ny, 1};
+      NPMG_BTRY(launch_coarse_inverse(2, n3, wd, I.lv[Lc].bcD, I.lv[Lc].cell, (double*)(P + f.inv), s));
+      CoarseArgs& ca = I.ca;
+      memset(&ca, 0, sizeof(ca));
+      ca.nlev = I.L - I.kc;
+      ca.dim = 2;
+      for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = I.lv[I.kc + l];
+      const size_t cb = coarse_layout(ca.off, ca.lv, ca.nlev, 2);
+      I.cfloats = (int)(cb / 4);
+      coarse_bytes = cb > coarse_bytes ? cb : coarse_bytes;
+      ca.ncoarse = I.lv[Lc].nx * I.lv[Lc].ny;
+      ca.inv = (double*)(P + f.inv);
+      ca.image = nullptr;
+      ca.pre = o.pre;
+      ca.post = o.post;
+      ca.omega = (float)o.omega;
+      ca.s = (float)o.coarse_scale;
+      ca.finest = 0;
+    }
+  }
+  NPMG_BTRY(cudaMalloc((void**)&B->d_inst, sizeof(BInst) * count));
+  NPMG_BTRY(cudaMalloc((void**)&B->d_st, sizeof(SolveState) * count));
+  NPMG_BTRY(cudaMalloc((void**)&B->d_cur, sizeof(int) * count));
+  NPMG_BTRY(cudaMalloc((void**)&B->d_rhs, sizeof(void*) * count));
+  NPMG_BTRY(cudaMalloc((void**)&B->d_xout, sizeof(void*) * count));
+  NPMG_BTRY(cudaMallocHost((void**)&B->h_st, sizeof(SolveState) * count));
+  NPMG_BTRY(cudaMallocHost((void**)&B->h_ptrs, sizeof(void*) * 2 * count));
+  NPMG_BTRY(cudaMemsetAsync(B->d_st, 0, sizeof(SolveState) * count, s));
+  NPMG_BTRY(cudaEventCreate(&B->ev0));
+  NPMG_BTRY(cudaEventCreate(&B->ev1));
+  // shared memory, occupancy and grid per (tile, sweeps)
+  for (int t = 0; t < 3; ++t)
+    for (int sw = 1; sw <= 3; ++sw) {
+      B->smem[t][sw] = batched_smem(kTiles[t].tx, kTiles[t].ty, sw, coarse_bytes);
+      NPMG_BTRY(cudaFuncSetAttribute(batched_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)B->smem[t][sw] + 1024));
+      int per_sm = 0;
+      NPMG_BTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(t), kBThreads, B->smem[t][sw]));
+      if (per_sm < 1) {
+        set_error("mg_create_batched: kernel does not fit on an SM");
+        st = MG_ERR_INVALID;
+        goto fail;
+      }
+      B->grid[t][sw] = B->nsm * (per_sm > 4 ? 4 : per_sm);
+    }
+  {
+    char name[256] = {0};
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, B->device) == cudaSuccess) snprintf(name, sizeof name, "%s", prop.name);
+    for (char* c = name; *c; ++c)
+      if (*c == ' ') *c = '_';
+    char key[512];
+    snprintf(key, sizeof key, "%s|n%d|cells%lld|max%d|p%d", name, count, total_cells, max_side, o.pre);
+    B->tune_key = key;
+  }
+  B->tile = 0;
+  B->sweeps = o.pre >= 1 && o.pre <= 3 ? o.pre : 2;
+  tune_lookup(B->tune_key, &B->tile, &B->sweeps);
+  NPMG_BTRY(cudaStreamSynchronize(s));
+#undef NPMG_BTRY
+  // work lists of the initial tile shape (a solve itself allocates nothing)
+  st = build_items(B, B->tile, s);
+  if (st != MG_OK) goto fail;
+  *out = B;
+  return MG_OK;
+fail:
+  mg_destroy_batched(B);
+  return st;
+}
+
+}  // extern "C"
+
+// Item lists of the current tile shape (rebuilt when the tuner switches).
+static mg_status build_items(mg_batch_s* B, int tile, cudaStream_t s) {
+  const int TX = kTiles[tile].tx, TY = kTiles[tile].ty;
+  std::vector<std::vector<int4>> items(kMaxLevels);
+  int slot = 0;
+  for (int i = 0; i < B->count; ++i) {
+    BInst& I = B->inst[i];
+    I.slot0 = slot;
+    for (int k = 0; k < I.kc; ++k) {
+      const int nx = I.lv[k].nx, ny = I.lv[k].ny;
+      for (int ty = 0; ty < (ny + TY - 1) / TY; ++ty)
+        for (int tx = 0; tx < (nx + TX - 1) / TX; ++tx) items[k].push_back(make_int4(i, tx, ty, k == 0 ? slot++ : -1));
+    }
+    I.ntiles0 = slot - I.slot0;
+  }
+  for (int4* p : B->d_items) cudaFree(p);
+  B->d_items.assign(kMaxLevels, nullptr);
+  for (int k = 0; k < kMaxLevels; ++k) {
+    B->nitems[k] = (int)items[k].size();
+    if (items[k].empty()) continue;
+    NPMG_CUDA(cudaMalloc((void**)&B->d_items[k], items[k].size() * sizeof(int4)));
+    NPMG_CUDA(cudaMemcpyAsync(B->d_items[k], items[k].data(), items[k].size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              s));
+  }
+  for (int i = 0; i < B->count; ++i) {
+    B->inst[i].ca.pre = B->sweeps;
+    B->inst[i].ca.post = B->sweeps;
+  }
+  NPMG_CUDA(cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(BInst) * B->count, cudaMemcpyHostToDevice, s));
+  NPMG_CUDA(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+static mg_status set_pointers(mg_batch_s* B, const float* const* d_rhs, float* const* d_x, cudaStream_t s) {
+  for (int i = 0; i < B->count; ++i) {
+    if (!d_rhs[i] || !d_x[i]) {
+      set_error("batched solve: NULL array for instance %d", i);
+      return MG_ERR_INVALID;
+    }
+    B->h_ptrs[i] = (void*)d_rhs[i];
+    B->h_ptrs[B->count + i] = (void*)d_x[i];
+  }
+  NPMG_CUDA(cudaMemcpyAsync((void*)B->d_rhs, B->h_ptrs, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
+  NPMG_CUDA(
+      cudaMemcpyAsync((void*)B->d_xout, B->h_ptrs + B->count, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
+  return MG_OK;
+}
+
+static mg_status run_batched(mg_batch_s* B, double tol, cudaStream_t s, mg_stats* out, float* ms_out) {
+  if (B->d_items.empty()) {
+    mg_status st = build_items(B, B->tile, s);
+    if (st != MG_OK) return st;
+  }
+  NPMG_CUDA(cudaEventRecord(B->ev0, s));
+  mg_status st = batched_launch(B, B->tile, B->sweeps, tol, s);
+  if (st != MG_OK) return st;
+  NPMG_CUDA(cudaEventRecord(B->ev1, s));
+  NPMG_CUDA(cudaMemcpyAsync(B->h_st, B->d_st, sizeof(SolveState) * B->count, cudaMemcpyDeviceToHost, s));
+  unsigned err = 0;
+  NPMG_CUDA(cudaMemcpyAsync(&err, B->d_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  NPMG_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, B->ev0, B->ev1);
+  if (ms_out) *ms_out = ms;
+  mg_status worst = MG_OK;
+  for (int i = 0; i < B->count; ++i) {
+    const SolveState& S = B->h_st[i];
+    mg_status si = err ? MG_TIMEOUT : (mg_status)S.status;
+    if (!err && !S.outer_done && si == MG_OK) si = MG_NOT_CONVERGED;
+    if (si != MG_OK && worst == MG_OK) worst = si;
+    if (out) {
+      memset(&out[i], 0, sizeof(mg_stats));
+      out[i].status = si;
+      out[i].iters = S.iters_total;
+      out[i].outer = S.outer;
+      out[i].levels = B->inst[i].L;
+      out[i].relres0 = S.relres0;
+      out[i].relres = S.relres;
+      out[i].bnorm = sqrt(S.bnorm2);
+      out[i].ms = ms;
+      for (int k = 0; k < 32; ++k) out[i].history[k] = S.hist[k];
+    }
+  }
+  if (err) set_error("batched solve: a grid barrier timed out");
+  return err ? MG_TIMEOUT : worst;
+}
+
+extern "C" {
+
+mg_status mg_solve_batched(mg_batch B, const float* const* d_rhs, float* const* d_x, double rel_tol, void* stream,
+                           mg_stats* out) {
+  if (!B || !d_rhs || !d_x || !(rel_tol > 0)) {
+    set_error("mg_solve_batched: invalid arguments");
+    return MG_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = set_pointers(B, d_rhs, d_x, s);
+  if (st != MG_OK) return st;
+  return run_batched(B, rel_tol, s, out, nullptr);
+}
+
+mg_status mg_tune_batched(mg_batch B, const float* const* d_rhs, float* const* d_x, double rel_tol, void* stream,
+                          int* out_tile_x, int* out_tile_y, int* out_sweeps) {
+  if (!B || !d_rhs || !d_x || !(rel_tol > 0)) {
+    set_error("mg_tune_batched: invalid arguments");
+    return MG_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = set_pointers(B, d_rhs, d_x, s);
+  if (st != MG_OK) return st;
+  int best_t = B->tile, best_s = B->sweeps;
+  float best = 1e30f;
+  for (int t = 0; t < 3; ++t) {
+    for (int sw = 1; sw <= 3; ++sw) {
+      B->tile = t;
+      B->sweeps = sw;
+      st = build_items(B, t, s);
+      if (st != MG_OK) return st;
+      float ms = 0.f;
+      st = run_batched(B, rel_tol, s, nullptr, nullptr);  // warm
+      if (st != MG_OK && st != MG_NOT_CONVERGED) continue;
+      st = run_batched(B, rel_tol, s, nullptr, &ms);
+      if (st == MG_OK && ms < best) {
+        best = ms;
+        best_t = t;
+        best_s = sw;
+      }
+    }
+  }
+  B->tile = best_t;
+  B->sweeps = best_s;
+  st = build_items(B, best_t, s);
+  if (st != MG_OK) return st;
+  tune_store(B->tune_key, best_t, best_s, best);
+  if (out_tile_x) *out_tile_x = kTiles[best_t].tx;
+  if (out_tile_y) *out_tile_y = kTiles[best_t].ty;
+  if (out_sweeps) *out_sweeps = best_s;
+  return MG_OK;
+}
+
+mg_status mg_batched_config(mg_batch B, int tile_x, int tile_y, int sweeps, double barrier_timeout_s,
+                            int withhold_first_arrival) {
+  if (!B || sweeps < 1 || sweeps > 3 || !(barrier_timeout_s > 0)) {
+    set_error("mg_batched_config: invalid arguments");
+    return MG_ERR_INVALID;
+  }
+  int t = -1;
+  for (int k = 0; k < 3; ++k)
+    if (kTiles[k].tx == tile_x && kTiles[k].ty == tile_y) t = k;
+  if (t < 0) {
+    set_error("mg_batched_config: tile must be 64x16, 32x16 or 128x8");
+    return MG_ERR_INVALID;
+  }
+  const bool rebuild = t != B->tile || sweeps != B->sweeps || B->d_items.empty();
+  B->tile = t;
+  B->sweeps = sweeps;
+  B->timeout_s = barrier_timeout_s;
+  B->withhold = withhold_first_arrival ? 1 : 0;
+  if (rebuild) return build_items(B, t, nullptr);
+  return MG_OK;
+}
+
+mg_status mg_destroy_batched(mg_batch B) {
+  if (!B) return MG_OK;
+  for (int t = 0; t < 3; ++t)
+    for (int k = 0; k < 4; ++k)
+      if (B->graph[t][k]) cudaGraphExecDestroy(B->graph[t][k]);
+  for (int4* p : B->d_items) cudaFree(p);
+  if (B->pool) cudaFree(B->pool);
+  if (B->d_inst) cudaFree(B->d_inst);
+  if (B->d_st) cudaFree(B->d_st);
+  if (B->d_cur) cudaFree(B->d_cur);
+  if (B->d_rhs) cudaFree((void*)B->d_rhs);
+  if (B->d_xout) cudaFree(B->d_xout);
+  if (B->h_st) cudaFreeHost(B->h_st);
+  if (B->h_ptrs) cudaFreeHost(B->h_ptrs);
+  if (B->ev0) cudaEventDestroy(B->ev0);
+  if (B->ev1) cudaEventDestroy(B->ev1);
+  delete B;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -50,16 +50,21 @@ def blob_rhs(shape, seed, n_blobs=8, solid=None, zero_mean=True):
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     dim = len(shape)
-    X = node_coords(shape)
     f = np.zeros(shape)
     for _ in range(n_blobs):
         amp = rng.uniform(-1.0, 1.0)
         w = rng.uniform(0.02, 0.1)
         c = rng.uniform(0.1, 0.9, size=dim)
-        d2 = np.zeros(shape)
+        # the Gaussian factorises over the axes: a product of 1D profiles
+        g = np.full(shape, amp)
         for a in range(dim):
-            d2 = d2 + (X[a] - c[a]) ** 2
-        f = f + amp * np.exp(-d2 / (2.0 * w * w))
+            ax = dim - 1 - a
+            n = shape[ax]
+            xa = (np.arange(n) + 1.0) / (n + 1)
+            sh = [1] * dim
+            sh[ax] = n
+            g = g * np.exp(-((xa - c[a]) ** 2) / (2.0 * w * w)).reshape(sh)
+        f = f + g
     fluid = np.ones(shape, bool) if solid is None else ~np.asarray(solid, bool)
     f = f * fluid
     if zero_mean and fluid.any():
@@ -85,6 +90,25 @@ def flood_fill_unreachable(solid, bc):
     solid = np.asarray(solid, bool).copy()
     fluid = ~solid
     dim = solid.ndim
+    try:
+        from scipy import ndimage
+    except ImportError:
+        ndimage = None
+    if ndimage is not None:
+        # face-connected fluid components; keep those touching a Dirichlet face
+        lab, _ = ndimage.label(fluid)
+        keep = set()
+        for a in range(dim):
+            ax = dim - 1 - a
+            for side in (0, 1):
+                if bc[2 * a + side] != 0:
+                    continue
+                sl = [slice(None)] * dim
+                sl[ax] = 0 if side == 0 else -1
+                keep.update(np.unique(lab[tuple(sl)]).tolist())
+        keep.discard(0)
+        reach = np.isin(lab, np.array(sorted(keep), dtype=lab.dtype)) & fluid
+        return solid | (fluid & ~reach)
     reach = np.zeros_like(fluid)
     frontier = np.zeros_like(fluid)
     for a in range(dim):

@@ -24,6 +24,7 @@ EXPORTED = [
     "mg_prolong_correct", "mg_precondition", "mg_destroy", "ns_create", "ns_step", "ns_momentum",
     "ns_divergence_rhs", "ns_correct", "ns_pressure_handle", "ns_destroy",
     "mg_profile_enable", "mg_profile_read", "mg_kernel_launches", "mg_vcycle_noalloc",
+    "mg_create_batched", "mg_solve_batched", "mg_tune_batched", "mg_batched_config", "mg_destroy_batched",
 ]
 KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
                   "init_finish", "momentum", "divergence", "correct"]
@@ -100,6 +101,17 @@ def load():
         "mg_kernel_launches": (ctypes.c_int64, [_vp]),
         "mg_vcycle_noalloc": (ctypes.c_int, [ctypes.c_int, _i64_3, _d3, _i6, _vp, ctypes.POINTER(MgOptions),
                                              _vp, _vp, _vp]),
+        "mg_create_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_int * 4,
+                                             ctypes.POINTER(_vp), ctypes.POINTER(MgOptions), _vp]),
+        "mg_solve_batched": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_double, _vp,
+                                            ctypes.POINTER(MgStats)]),
+        "mg_tune_batched": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_double, _vp,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+        "mg_batched_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int]),
+        "mg_destroy_batched": (ctypes.c_int, [_vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,6 +277,50 @@ def mg_vcycle_noalloc(dim, shape, spacing, bc, r, z, solid=None, options=None, s
     opt = options if options is not None else default_options()
     return _check(load().mg_vcycle_noalloc(dim, shp, sp, b6, ptr(solid), ctypes.byref(opt), ptr(r), ptr(z),
                                            stream_ptr(stream)))
+
+
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[ptr(t) for t in ts])
+
+
+def mg_create_batched(shapes, spacings, bc, masks=None, options=None, stream=None):
+    """shapes: list of (nx, ny); spacings: list of (hx, hy); masks: list of
+    device uint8 tensors or None entries (or None)."""
+    n = len(shapes)
+    shp = (ctypes.c_int64 * (2 * n))(*[int(v) for s_ in shapes for v in s_])
+    sp = (ctypes.c_double * (2 * n))(*[float(v) for s_ in spacings for v in s_])
+    b4 = (ctypes.c_int * 4)(*bc)
+    m = None if masks is None else _ptr_array(masks)
+    opt = options if options is not None else default_options()
+    out = _vp()
+    _check(load().mg_create_batched(ctypes.byref(out), n, shp, sp, b4, m, ctypes.byref(opt), stream_ptr(stream)))
+    return out.value
+
+
+def mg_solve_batched(b, rhs, x, rel_tol, stream=None, stats=True):
+    """rhs, x: lists of device tensors.  Returns (status, list of stats dicts)."""
+    n = len(rhs)
+    st = (MgStats * n)() if stats else None
+    status = load().mg_solve_batched(b, _ptr_array(rhs), _ptr_array(x), rel_tol, stream_ptr(stream),
+                                     st if stats else None)
+    _check(status, allow=(MG_OK, MG_NOT_CONVERGED, MG_DIVERGED, MG_TIMEOUT))
+    return status, ([s_.as_dict() for s_ in st] if stats else None)
+
+
+def mg_tune_batched(b, rhs, x, rel_tol, stream=None):
+    tx, ty, sw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().mg_tune_batched(b, _ptr_array(rhs), _ptr_array(x), rel_tol, stream_ptr(stream), ctypes.byref(tx),
+                                  ctypes.byref(ty), ctypes.byref(sw)))
+    return tx.value, ty.value, sw.value
+
+
+def mg_batched_config(b, tile_x, tile_y, sweeps, barrier_timeout_s=2.0, withhold_first_arrival=False):
+    _check(load().mg_batched_config(b, tile_x, tile_y, sweeps, barrier_timeout_s, 1 if withhold_first_arrival else 0))
+
+
+def mg_destroy_batched(b):
+    if b:
+        load().mg_destroy_batched(b)
 
 
 def ns_destroy(ns):
