@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="ns2d", choices=["ns2d", "poisson2d", "poisson3d", "batched"])
+    ap.add_argument("--config", default="ns2d", choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
@@ -93,6 +93,27 @@ class NS2D:
                 "block": self.block, "nu": self.nu, "dt": self.dt, "u_inflow": self.uin,
                 "solve_rel_tol": TOL, "unknowns_per_step": self.units,
                 "l2": "256 MiB buffer written between timed steps"}
+
+
+class NS3D:
+    """3D flow past a cube: 256 x 128 x 128 cells (h = 1), a 32^3 solid cube
+    centred at (64, 64, 64), inflow u = 1, nu = 0.32 (Re = 100 on the cube
+    side), dt = 0.1, initial velocity = inflow + 1% noise (seed 0)."""
+    name = "ns3d_cube_256x128x128"
+    dim = 3
+
+    def __init__(self, scale=1):
+        self.cells = (256 // scale, 128 // scale, 128 // scale)
+        self.block = 32 // scale
+        self.centre = (64 // scale, 64 // scale, 64 // scale)
+        self.nu, self.dt, self.uin = 0.32 / scale, 0.1, 1.0
+        self.solid = I.block_mask(self.cells, self.centre, self.block)
+        self.units = int((~self.solid).sum())
+
+    def config(self):
+        return {"workload": "3D projection step, flow past a cube", "cells": list(self.cells), "block": self.block,
+                "nu": self.nu, "dt": self.dt, "u_inflow": self.uin, "solve_rel_tol": TOL,
+                "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
 
 
 class Poisson:
@@ -220,25 +241,27 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    if args.config == "ns2d":
-        wl = NS2D()
+    if args.config in ("ns2d", "ns3d"):
+        wl = NS2D() if args.config == "ns2d" else NS3D()
         solid_t = torch.from_numpy(wl.solid.astype(np.uint8)).to(dev)
-        ns = L.ns_create(2, wl.cells, 1.0, solid_t)
+        ns = L.ns_create(wl.dim, wl.cells, 1.0, solid_t)
         mg = L.ns_pressure_handle(ns)
         q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
-        host = [torch.from_numpy(a).pin_memory() for a in (q[0], q[1], np.zeros(wl.solid.shape, np.float32))]
-        u, v, p = (t.to(dev) for t in host)
+        host = [torch.from_numpy(a).pin_memory() for a in q + [np.zeros(wl.solid.shape, np.float32)]]
+        fields = [t.to(dev) for t in host]
+        u, v, p = fields[0], fields[1], fields[-1]
+        w = fields[2] if wl.dim == 3 else None
         stats = []
 
         def step():
-            _, st = L.ns_step(ns, u, v, None, p, wl.dt, wl.nu, wl.uin, TOL)
+            _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)
             stats.append(st)
 
         def e2e_step():
-            for d, hsrc in zip((u, v, p), host):
+            for d, hsrc in zip(fields, host):
                 d.copy_(hsrc, non_blocking=True)
             step()
-            for d, hdst in zip((u, v, p), host):
+            for d, hdst in zip(fields, host):
                 hdst.copy_(d, non_blocking=True)
         io_bytes = sum(t.numel() * 4 for t in host)
         cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
@@ -364,9 +387,9 @@ def run_gpu(args, rank, world):
         tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
         dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
         ms_dom, n_dom = prof[dom]
-        ncell = int(np.prod(wl.cells)) if args.config == "ns2d" else wl.units
-        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config == "ns2d" and dom != "xr_update" else 0)
-        if args.prec != "fp32" and args.config != "ns2d":
+        ncell = int(np.prod(wl.cells)) if args.config in ("ns2d", "ns3d") else wl.units
+        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config in ("ns2d", "ns3d") and dom != "xr_update" else 0)
+        if args.prec != "fp32" and args.config not in ("ns2d", "ns3d"):
             per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
         algo = per_cell * ncell
         achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
@@ -401,9 +424,9 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
     from oracle import ns as N
     from oracle import poisson as P
     t_total, steps, units = 0.0, 0, 0
-    if isinstance(wl, NS2D):
+    if isinstance(wl, (NS2D, NS3D)):
         g = N.MacGrid(wl.cells, 1.0, wl.solid)
-        hier = P.build_hierarchy(g.shape, (1.0, 1.0), g.p_bc, wl.solid)
+        hier = P.build_hierarchy(g.shape, (1.0,) * wl.dim, g.p_bc, wl.solid)
         mg = P.Multigrid(hier, s=1.0)
         q = I.ns_initial_velocity(wl.cells, 0)
         p = np.zeros(g.shape)
@@ -414,8 +437,8 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
             t_total += time.perf_counter() - t0
             steps += 1
             units += wl.units
-        sample = "%d oracle step(s) of the %dx%d projection workload (pressure solve to 1e-6)" % (
-            steps, wl.cells[0], wl.cells[1])
+        sample = "%d oracle step(s) of the %s projection workload (pressure solve to 1e-6)" % (
+            steps, "x".join(map(str, wl.cells)))
     elif isinstance(wl, Batched):
         for k in range(len(wl.shapes)):
             if steps >= max_steps or t_total >= budget_s:
@@ -477,17 +500,23 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        wl = NS2D(scale=4) if args.config == "ns2d" else Poisson((256, 256), args.prec)
-        if args.config == "batched":
-            wl = Batched(limit=16)
+        # each reference step is one oracle step of a bounded sample of the
+        # workload (same structure, fewer cells), so the run ends in minutes
+        samples = {"ns2d": lambda: NS2D(scale=4), "ns3d": lambda: NS3D(scale=4),
+                   "poisson2d": lambda: Poisson((256, 256), args.prec),
+                   "poisson3d": lambda: Poisson((64, 64, 64), args.prec), "batched": lambda: Batched(limit=16)}
+        wl = samples[args.config]()
         t0 = time.perf_counter()
         rate, sample, n = oracle_step_time(wl, budget_s=1e9, max_steps=args.warmup + args.steps)
         cores = 1
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": dict(wl.config(), sample="quarter-resolution copy of the workload (512x256 cells, "
-                               "16-cell block, nu scaled to keep Re = 100)" if args.config == "ns2d" else None),
+                "config": dict(wl.config(), sample={
+                    "ns2d": "quarter-resolution copy (512x256 cells, 16-cell block, Re kept at 100)",
+                    "ns3d": "quarter-resolution copy (64x32x32 cells, 8-cell cube, Re kept at 100)",
+                    "poisson3d": "64^3 copy of the blob workload",
+                    "batched": "the first 16 instances of the batch"}.get(args.config, "the workload itself")),
                 "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
                 "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
@@ -497,7 +526,10 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
             ms = {"poisson2d": 5, "batched": 64}.get(args.config, 1)
-            rate, sample, n = oracle_step_time(wl, budget_s=25.0, max_steps=ms)
+            # 3D: the full-size oracle step takes minutes; time a smaller copy
+            cpu_wl = {"ns3d": lambda: NS3D(scale=2), "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
+                args.config, lambda: wl)()
+            rate, sample, n = oracle_step_time(cpu_wl, budget_s=25.0, max_steps=ms)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
         print(json.dumps(out))
 

@@ -1,0 +1,169 @@
+"""FP64 oracle of the learned initial-guess network (test infrastructure
+only; see the package docstring).
+
+The paper couples trained networks with its physics solvers only as a
+motivation (Sec. 1 (iii), Sec. 5 items (3) and (4)); the network itself is
+the workload's definition: a bias-free 3D U-Net with 16 channels and three
+resolutions.  Everything here is plain numpy in float64:
+
+* ``conv3d``: 3x3x3 cross-correlation with zero padding (the convention of
+  Eq. define_convolution), arrays ``[C, Z, Y, X]``, weights ``[27, Cin, Cout]``
+  with tap t = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1).
+* ``forward``: e1 = R(W1 x), e1 = R(W2 e1); e2 = R(W3 P e1), e2 = R(W4 e2);
+  e3 = R(W5 P e2), e3 = R(W6 e3); d2 = R(W7 (U e3 + e2)); d1 = R(W8 (U d2 + e1));
+  y = W9 d1 -- R = ReLU, P = 2x2x2 average, U = nearest (copy) upsampling.
+  No biases, so the network is positively homogeneous: f(c x) = c f(x).
+* ``backward``: the analytic gradient of 0.5 * mean((y - t)^2), checked
+  against finite differences in the tests.
+* ``adam``: Kingma & Ba's update (beta1 0.9, beta2 0.999, eps 1e-8).
+"""
+import numpy as np
+
+NLAYERS = 9
+LAYER_IO = [(2, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 1)]
+
+
+def tap_offsets():
+    """(dz, dy, dx) of tap t, t = (dz+1)*9 + (dy+1)*3 + (dx+1)."""
+    return [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
+def shifted(x, dz, dy, dx):
+    """x[:, z+dz, y+dy, x+dx] with zeros outside (zero padding)."""
+    out = np.zeros_like(x)
+    C, Z, Y, X = x.shape
+    zs, ys, xs = slice(max(0, -dz), Z - max(0, dz)), slice(max(0, -dy), Y - max(0, dy)), slice(max(0, -dx), X - max(0, dx))
+    zs2, ys2, xs2 = slice(max(0, dz), Z + min(0, dz)), slice(max(0, dy), Y + min(0, dy)), slice(max(0, dx), X + min(0, dx))
+    out[:, zs, ys, xs] = x[:, zs2, ys2, xs2]
+    return out
+
+
+def conv3d(x, w):
+    """y[co] = sum_t sum_ci w[t, ci, co] * x[ci] shifted by tap t."""
+    y = np.zeros((w.shape[2],) + x.shape[1:])
+    for t, (dz, dy, dx) in enumerate(tap_offsets()):
+        xs = shifted(x, dz, dy, dx)
+        y += np.einsum("czyx,cd->dzyx", xs, w[t])
+    return y
+
+
+def conv3d_dgrad(g, w):
+    """Gradient of conv3d with respect to its input: correlation of g with
+    the transposed weights at the mirrored taps."""
+    gx = np.zeros((w.shape[1],) + g.shape[1:])
+    for t, (dz, dy, dx) in enumerate(tap_offsets()):
+        gs = shifted(g, -dz, -dy, -dx)
+        gx += np.einsum("dzyx,cd->czyx", gs, w[t])
+    return gx
+
+
+def conv3d_wgrad(x, g):
+    """Gradient of conv3d with respect to its weights."""
+    dw = np.zeros((27, x.shape[0], g.shape[0]))
+    for t, (dz, dy, dx) in enumerate(tap_offsets()):
+        xs = shifted(x, dz, dy, dx)
+        dw[t] = np.einsum("czyx,dzyx->cd", xs, g)
+    return dw
+
+
+def pool(x):
+    C, Z, Y, X = x.shape
+    return x.reshape(C, Z // 2, 2, Y // 2, 2, X // 2, 2).mean(axis=(2, 4, 6))
+
+
+def pool_bwd(g):
+    return np.repeat(np.repeat(np.repeat(g, 2, 1), 2, 2), 2, 3) / 8.0
+
+
+def up(x):
+    return np.repeat(np.repeat(np.repeat(x, 2, 1), 2, 2), 2, 3)
+
+
+def up_bwd(g):
+    C, Z, Y, X = g.shape
+    return g.reshape(C, Z // 2, 2, Y // 2, 2, X // 2, 2).sum(axis=(2, 4, 6))
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def forward(W, x):
+    """Returns (y, cache)."""
+    c = {"x": x}
+    c["a1"] = conv3d(x, W[0]); c["e1a"] = relu(c["a1"])
+    c["a2"] = conv3d(c["e1a"], W[1]); c["e1"] = relu(c["a2"])
+    c["p1"] = pool(c["e1"])
+    c["a3"] = conv3d(c["p1"], W[2]); c["e2a"] = relu(c["a3"])
+    c["a4"] = conv3d(c["e2a"], W[3]); c["e2"] = relu(c["a4"])
+    c["p2"] = pool(c["e2"])
+    c["a5"] = conv3d(c["p2"], W[4]); c["e3a"] = relu(c["a5"])
+    c["a6"] = conv3d(c["e3a"], W[5]); c["e3"] = relu(c["a6"])
+    c["s2"] = up(c["e3"]) + c["e2"]
+    c["a7"] = conv3d(c["s2"], W[6]); c["d2"] = relu(c["a7"])
+    c["s1"] = up(c["d2"]) + c["e1"]
+    c["a8"] = conv3d(c["s1"], W[7]); c["d1"] = relu(c["a8"])
+    y = conv3d(c["d1"], W[8])
+    return y, c
+
+
+def loss(y, t):
+    """0.5 * mean((y - t)^2) over all output entries."""
+    return 0.5 * float(np.mean((y - t) ** 2))
+
+
+def backward(W, c, y, t):
+    """Gradients of ``loss(forward(W, x), t)`` with respect to every W[k]."""
+    dW = [None] * NLAYERS
+    g = (y - t) / y.size
+    dW[8] = conv3d_wgrad(c["d1"], g)
+    g = conv3d_dgrad(g, W[8]) * (c["a8"] > 0)
+    dW[7] = conv3d_wgrad(c["s1"], g)
+    g_s1 = conv3d_dgrad(g, W[7])
+    g_e1 = g_s1.copy()
+    g = up_bwd(g_s1) * (c["a7"] > 0)
+    dW[6] = conv3d_wgrad(c["s2"], g)
+    g_s2 = conv3d_dgrad(g, W[6])
+    g_e2 = g_s2.copy()
+    g = up_bwd(g_s2) * (c["a6"] > 0)
+    dW[5] = conv3d_wgrad(c["e3a"], g)
+    g = conv3d_dgrad(g, W[5]) * (c["a5"] > 0)
+    dW[4] = conv3d_wgrad(c["p2"], g)
+    g_e2 = g_e2 + pool_bwd(conv3d_dgrad(g, W[4]))
+    g = g_e2 * (c["a4"] > 0)
+    dW[3] = conv3d_wgrad(c["e2a"], g)
+    g = conv3d_dgrad(g, W[3]) * (c["a3"] > 0)
+    dW[2] = conv3d_wgrad(c["p1"], g)
+    g_e1 = g_e1 + pool_bwd(conv3d_dgrad(g, W[2]))
+    g = g_e1 * (c["a2"] > 0)
+    dW[1] = conv3d_wgrad(c["e1a"], g)
+    g = conv3d_dgrad(g, W[1]) * (c["a1"] > 0)
+    dW[0] = conv3d_wgrad(c["x"], g)
+    return dW
+
+
+class Adam:
+    def __init__(self, W, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.m = [np.zeros_like(w) for w in W]
+        self.v = [np.zeros_like(w) for w in W]
+        self.t = 0
+
+    def step(self, W, dW):
+        self.t += 1
+        out = []
+        for k, (w, g) in enumerate(zip(W, dW)):
+            self.m[k] = self.b1 * self.m[k] + (1 - self.b1) * g
+            self.v[k] = self.b2 * self.v[k] + (1 - self.b2) * g * g
+            mh = self.m[k] / (1 - self.b1 ** self.t)
+            vh = self.v[k] / (1 - self.b2 ** self.t)
+            out.append(w - self.lr * mh / (np.sqrt(vh) + self.eps))
+        return out
+
+
+def net_input(b, p):
+    """The network's input: (b, p^n) scaled by 1 / rms(b) -> [2, Z, Y, X];
+    returns (x, rms).  The output is multiplied back by rms."""
+    rms = float(np.sqrt(np.mean(b * b)))
+    s = 1.0 / rms if rms > 0 else 1.0
+    return np.stack([b * s, p * s]), (rms if rms > 0 else 1.0)

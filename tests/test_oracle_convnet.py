@@ -1,0 +1,79 @@
+"""Pins of the FP64 initial-guess network oracle: brute-force convolution,
+adjoint identities of every backward piece, finite-difference gradients,
+positive homogeneity, and a hand-worked Adam step (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import convnet as C
+from paper_2402_17913_gb300 import inputs as I
+
+
+def test_conv3d_matches_brute_force_loops():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((3, 4, 5, 6))
+    w = rng.standard_normal((27, 3, 2))
+    y = C.conv3d(x, w)
+    Cin, Z, Y, X = x.shape
+    ref = np.zeros((2, Z, Y, X))
+    for co in range(2):
+        for z in range(Z):
+            for yy in range(Y):
+                for xx in range(X):
+                    s = 0.0
+                    for t, (dz, dy, dx) in enumerate(C.tap_offsets()):
+                        zz, y2, x2 = z + dz, yy + dy, xx + dx
+                        if 0 <= zz < Z and 0 <= y2 < Y and 0 <= x2 < X:
+                            s += sum(w[t, ci, co] * x[ci, zz, y2, x2] for ci in range(Cin))
+                    ref[co, z, yy, xx] = s
+    assert np.allclose(y, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_backward_pieces_are_adjoints():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((4, 6, 4, 8))
+    w = rng.standard_normal((27, 4, 3))
+    g = rng.standard_normal((3, 6, 4, 8))
+    lhs = np.vdot(C.conv3d(x, w), g)
+    assert np.isclose(lhs, np.vdot(x, C.conv3d_dgrad(g, w)), rtol=1e-12)
+    assert np.isclose(lhs, np.vdot(w, C.conv3d_wgrad(x, g)), rtol=1e-12)
+    p = rng.standard_normal((4, 3, 2, 4))
+    assert np.isclose(np.vdot(C.pool(x), p), np.vdot(x, C.pool_bwd(p)), rtol=1e-12)
+    assert np.isclose(np.vdot(C.up(p), x), np.vdot(p, C.up_bwd(x)), rtol=1e-12)
+
+
+def test_full_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    W = I.convnet_weights(5)
+    x = rng.standard_normal((2, 8, 8, 8))
+    t = rng.standard_normal((1, 8, 8, 8))
+    y, c = C.forward(W, x)
+    dW = C.backward(W, c, y, t)
+    eps = 1e-6
+    for k in range(C.NLAYERS):
+        for _ in range(3):
+            idx = tuple(rng.integers(0, s) for s in W[k].shape)
+            Wp = [w.copy() for w in W]
+            Wm = [w.copy() for w in W]
+            Wp[k][idx] += eps
+            Wm[k][idx] -= eps
+            fd = (C.loss(C.forward(Wp, x)[0], t) - C.loss(C.forward(Wm, x)[0], t)) / (2 * eps)
+            assert abs(fd - dW[k][idx]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-10, (k, idx, fd, dW[k][idx])
+
+
+def test_network_is_positively_homogeneous():
+    rng = np.random.default_rng(3)
+    W = I.convnet_weights(6)
+    x = rng.standard_normal((2, 8, 8, 8))
+    y1, _ = C.forward(W, x)
+    y2, _ = C.forward(W, 2.5 * x)
+    assert np.allclose(y2, 2.5 * y1, rtol=1e-12, atol=1e-14)
+
+
+def test_adam_step_hand_worked():
+    """One step from m = v = 0 with gradient g: m_hat = g, v_hat = g^2, so
+    w <- w - lr * g / (|g| + eps)."""
+    w = [np.array([1.0, -2.0])]
+    g = [np.array([0.5, -4.0])]
+    opt = C.Adam(w, lr=0.1)
+    w2 = opt.step(w, g)[0]
+    assert np.allclose(w2, [1.0 - 0.1 * 0.5 / (0.5 + 1e-8), -2.0 + 0.1 * 4.0 / (4.0 + 1e-8)], rtol=1e-15)
