@@ -91,6 +91,11 @@ typedef struct {
   double bnorm;         /* ||b||_2                                            */
   float ms;             /* device time of the solve, milliseconds             */
   double history[32];   /* relres after each refinement step (first `outer`+1) */
+  double guess_relres;  /* relres of the caller's initial guess (= relres0
+                           unless the guess was rejected)                     */
+  int guess_rejected;   /* 1 when a checked guess (ns_step with a learned
+                           guess) had relres > 1 and the solve restarted
+                           from zero                                          */
 } mg_stats;
 
 typedef struct mg_handle_s* mg_handle;
@@ -302,6 +307,89 @@ mg_status mg_tune_batched(mg_batch b, const float* const* d_rhs, float* const* d
 mg_status mg_batched_config(mg_batch b, int tile_x, int tile_y, int sweeps, double barrier_timeout_s,
                             int withhold_first_arrival);
 mg_status mg_destroy_batched(mg_batch b);
+
+/*
+ * Learned initial guess (the warm start of the pressure solve).
+ *
+ * A bias-free 3D U-Net with 3 resolutions and 16 channels maps the
+ * divergence right-hand side b and the previous pressure p^n of a
+ * projection step (Algorithm 1) to a guess of the pressure increment dp that
+ * the solve then refines; multigrid from the guess still runs to the same
+ * tolerance and, in ns_step, restarts from zero when the guess is worse than
+ * zero (relres > 1).  Sec. 1 and Sec. 5 of the paper motivate coupling such
+ * networks with the solver; the network and its training are defined here:
+ *   x = (b, p^n) / rms(b)             (2 channels, rms over the sample)
+ *   e1 = R(W1 x), e1 = R(W2 e1)        full resolution
+ *   e2 = R(W3 P e1), e2 = R(W4 e2)     half           (P = 2x2x2 average)
+ *   e3 = R(W5 P e2), e3 = R(W6 e3)     quarter
+ *   d2 = R(W7 (U e3 + e2))             half           (U = copy upsampling)
+ *   d1 = R(W8 (U d2 + e1))             full
+ *   dp_guess = rms(b) * W9 d1          (1 channel)
+ * with R = ReLU and Wk 3x3x3 cross-correlations with zero padding.  Weights
+ * are FP32 masters; activations and tensor-core operands are BF16 with FP32
+ * accumulation.  Training minimises 0.5 * mean((net(x) - dp / rms(b))^2)
+ * with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on 3D crops of solver runs.
+ *
+ * Weights on the host are the 9 layers back to back, layer k as
+ * [27 taps][c_in][c_out] float32, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1),
+ * (c_in, c_out) = (2,16), (16,16) x 7, (16,1): GN_NUM_WEIGHTS floats.
+ * Device fields are float32 [n][z][y][x] (x fastest), 16-byte aligned; every
+ * cell count must be divisible by 4.  Calls are asynchronous on `stream`
+ * unless they return host values.
+ *
+ * gn_create: weights from h_weights (required); allocates the FP32 masters,
+ *   Adam moments and packed operands.  Activation workspaces are allocated
+ *   on first use of a shape and kept.
+ * gn_forward: d_out[n] = dp_guess for samples (d_b[n], d_p[n]).
+ * gn_gradients: loss and gradient (host, weight layout; nullable) for
+ *   targets d_t (the solver's dp); synchronises.
+ * gn_adam_step: one Adam step with h_grad (weight layout) or, when NULL,
+ *   the last gn_gradients result; lr > 0.
+ * gn_dataset_reserve: room for `capacity` crops of size crop (x, y, z).
+ * gn_dataset_add: cuts full fields (cells) into non-overlapping crops and
+ *   appends (b, p^n = d_p_next - d_dp, dp) for each until full.
+ * gn_train: `steps` Adam steps on minibatches of `batch` crops drawn with a
+ *   seeded generator; h_losses (nullable) receives each step's loss;
+ *   synchronises.
+ * gn_conv3d (building block): one convolution of a BF16 NDHWC16 tensor
+ *   d_x ([n][z][y][x][16]) with FP32 weights d_w ([27][16][16], device).
+ *   mode GN_CONV_F32: d_y = float [..][16]; GN_CONV_RELU: bf16 ReLU output;
+ *   GN_CONV_DGRAD: float output of the data gradient (mirrored taps,
+ *   transposed channels); GN_CONV_LIN: bf16 linear output.
+ *   d_scratch: device, GN_CONV_SCRATCH_BYTES, 256-byte aligned; synchronises.
+ * gn_conv3d_wgrad (building block): d_dw[t][ci][co] = sum over voxels of
+ *   x[v + o_t][ci] * g[v][co]; d_scratch >= GN_WGRAD_SCRATCH_MIN bytes (more
+ *   bytes = more blocks); synchronises.
+ * ns_set_guess: attach (g != NULL) or detach the guess network of ns_step;
+ *   ns does not own g.
+ * Errors: MG_ERR_INVALID (bad shape, NULL, misaligned), MG_ERR_OOM,
+ * MG_ERR_CUDA, MG_TIMEOUT (a tile load or MMA that did not complete in its
+ * bounded wait).
+ */
+#define GN_NUM_WEIGHTS 49680
+#define GN_CONV_SCRATCH_BYTES 28160
+#define GN_WGRAD_SCRATCH_MIN (256 + 27 * 16 * 16 * 4)
+enum { GN_CONV_F32 = 0, GN_CONV_RELU = 1, GN_CONV_DGRAD = 2, GN_CONV_LIN = 3 };
+typedef struct gn_handle_s* gn_handle;
+mg_status gn_create(gn_handle* out, const float* h_weights, void* stream);
+mg_status gn_set_weights(gn_handle g, const float* h_weights);
+mg_status gn_get_weights(gn_handle g, float* h_weights);
+mg_status gn_forward(gn_handle g, int n, const int64_t cells[3], const float* d_b, const float* d_p, float* d_out,
+                     void* stream);
+mg_status gn_gradients(gn_handle g, int n, const int64_t cells[3], const float* d_b, const float* d_p,
+                       const float* d_t, double* h_loss, float* h_grad, void* stream);
+mg_status gn_adam_step(gn_handle g, const float* h_grad, double lr, void* stream);
+mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity);
+mg_status gn_dataset_add(gn_handle g, const int64_t cells[3], const float* d_b, const float* d_p_next,
+                         const float* d_dp, void* stream);
+int gn_dataset_size(gn_handle g);
+mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, double* h_losses, void* stream);
+mg_status gn_conv3d(const void* d_x, const float* d_w, void* d_y, int n, const int64_t cells[3], int mode,
+                    void* d_scratch, void* stream);
+mg_status gn_conv3d_wgrad(const void* d_x, const void* d_g, float* d_dw, int n, const int64_t cells[3],
+                          void* d_scratch, size_t scratch_bytes, void* stream);
+mg_status gn_destroy(gn_handle g);
+mg_status ns_set_guess(ns_handle ns, gn_handle g);
 
 /* The pressure handle inside ns (owned by ns; do not destroy). */
 mg_handle ns_pressure_handle(ns_handle ns);

@@ -1,0 +1,713 @@
+// Kernels of the learned initial-guess network: the BF16 implicit-GEMM 3D
+// convolution on the fifth-generation tensor cores (forward and data
+// gradient), the weight gradient on warp-level tensor-core MMAs, and the
+// memory-bound glue (pooling, upsampling, skip sums, ReLU masks, input
+// scaling, loss, Adam).
+//
+// Convolution as a GEMM.  For an output tile of M = 128 voxels (16 along x,
+// 8 along y, one z-plane) the 3x3x3 correlation with 16 input and 16 output
+// channels is 27 MMAs of shape M x N x K = 128 x 16 x 16, one per tap t:
+//     D[v][co] += sum_ci X[v + o_t][ci] * W[t][ci][co].
+// A block stages, by TMA, three copies of its input tile (x shifted by
+// dx = -1, 0, +1) in the no-swizzle K-major core-matrix layout
+// [channel group][z][y][x][8 channels]; the copies carry a one-voxel halo in
+// y and z.  The A operand of tap (dz, dy, dx) is then a contiguous 2 KB run of
+// copy dx starting at row (z + dz, y + dy): each descriptor differs only in
+// its start address, and out-of-range voxels arrive as zeros (the zero
+// padding).  One thread issues the 27 MMAs per z-plane into a TMEM
+// accumulator (128 lanes x 16 FP32 columns); the four warps read it back
+// with tcgen05.ld, apply the epilogue and store 32 bytes per voxel.
+//
+// The data gradient is the same kernel with the mirrored, transposed taps
+// (W'[26 - t][co][ci] = W[t][ci][co]).  The weight gradient
+//     dW[t][ci][co] = sum_v X[v + o_t][ci] G[v][co]
+// reduces over voxels and has M = 27 x 16 rows whose shared-memory views
+// are not a single strided pattern, so it uses m16n8k16 MMAs fed by
+// ldmatrix.trans, which gathers any eight 16-byte rows.
+#include <cudaTypedefs.h>
+
+#include "gn.h"
+#include "tma_host.h"
+#include "umma.cuh"
+
+namespace npmg {
+namespace gn {
+
+namespace {
+
+constexpr int kPlane = (kTZ + 2) * (kTY + 2) * kTX * 16;  // bytes of one staged (copy, channel group) plane
+constexpr int kAOff = 14336;                             // A planes start (1024-aligned, after the weights)
+constexpr int kConvSmem = kAOff + 6 * kPlane + 1024;     // + alignment slack
+constexpr int kConvThreads = 128;
+constexpr uint32_t kConvCols = 32;                       // TMEM columns (kTZ accumulators of 16, min 32)
+static_assert(kTZ * 16 <= (int)kConvCols, "TMEM columns");
+static_assert(kPlane % 1024 == 0, "TMA destinations stay 1024-aligned");
+
+constexpr int kXPlane = (kWTX + 2) * (kWTY + 2) * (kWTZ + 2) * 16;
+constexpr int kGPlane = kWTX * kWTY * kWTZ * 16;
+constexpr int kWgSmem = 2 * kXPlane + 2 * kGPlane + 128;
+constexpr int kWgThreads = 288;  // 9 warps: warp w owns taps 3w .. 3w+2 (dz, dy fixed, dx = -1, 0, 1)
+static_assert(kXPlane % 128 == 0 && kGPlane % 128 == 0, "TMA destinations stay 128-aligned");
+
+struct ConvArgs {
+  int nx, ny, nz, nn;
+  int tx, ty, tz;
+  long long ntiles;
+  void* out;
+  const __nv_bfloat16* mask;
+  const float* scale;
+  int* err;
+};
+
+struct WgArgs {
+  int nx, ny, nz, nn;
+  int tx, ty, tz;
+  long long ntiles;
+  float* partials;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ bool bf_pos(uint32_t h16) { return !(h16 & 0x8000u) && (h16 & 0x7fffu); }
+
+template <int EPI>
+__device__ __forceinline__ void store_epi(const ConvArgs& a, size_t vox, int n, const float (&v)[16]) {
+  if (EPI == kEpiF32) {
+    float4* o = reinterpret_cast<float4*>(static_cast<float*>(a.out) + vox * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else if (EPI == kEpiOut0) {
+    static_cast<float*>(a.out)[vox] = v[0] * (a.scale ? a.scale[n] : 1.f);
+  } else {
+    float w[16];
+    if (EPI == kEpiMask) {
+      const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * kC);
+      const uint4 m0 = mp[0], m1 = mp[1];
+      const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        w[2 * k] = bf_pos(mw[k] & 0xffffu) ? v[2 * k] : 0.f;
+        w[2 * k + 1] = bf_pos(mw[k] >> 16) ? v[2 * k + 1] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) w[k] = EPI == kEpiRelu ? fmaxf(v[k], 0.f) : v[k];
+    }
+    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + vox * kC);
+    o[0] = make_uint4(pack_bf2(w[0], w[1]), pack_bf2(w[2], w[3]), pack_bf2(w[4], w[5]), pack_bf2(w[6], w[7]));
+    o[1] = make_uint4(pack_bf2(w[8], w[9]), pack_bf2(w[10], w[11]), pack_bf2(w[12], w[13]), pack_bf2(w[14], w[15]));
+  }
+}
+
+// Persistent implicit-GEMM convolution (see the file comment).
+template <int EPI>
+__global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ CUtensorMap xmap,
+                                                     const uint4* __restrict__ wpack, ConvArgs a) {
+  extern __shared__ unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar_ld;
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_slot;
+  const uint32_t pad = (1024u - (smem_u32(dsm) & 1023u)) & 1023u;
+  unsigned char* sW = dsm + pad;
+  unsigned char* sA = sW + kAOff;
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  for (int i = tid; i < kPackBytes / 16; i += kConvThreads) reinterpret_cast<uint4*>(sW)[i] = wpack[i];
+  fence_proxy_async_smem();
+  if (tid == 0) {
+    mbar_init(&bar_ld, 1);
+    mbar_init(&bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, kConvCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t sW_u = smem_u32(sW), sA_u = smem_u32(sA);
+  constexpr uint32_t idesc = idesc_bf16(128, 16);
+  uint32_t phase = 0;
+
+  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    long long r = tile;
+    const int bx = (int)(r % a.tx);
+    r /= a.tx;
+    const int by = (int)(r % a.ty);
+    r /= a.ty;
+    const int bz = (int)(r % a.tz);
+    const int n = (int)(r / a.tz);
+    const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bar_ld, 6 * kPlane);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+          tma_load_5d(sA + (c * 2 + g) * kPlane, &xmap, &bar_ld, g * 8, x0 + c - 1, y0 - 1, z0 - 1, n);
+    }
+    const bool ok_ld = mbar_wait_bounded(&bar_ld, phase);
+    if (__syncthreads_or(!ok_ld)) {
+      // a tile that never lands: report it, give the copies in flight a
+      // bounded wait, and stop (no MMA was issued for this tile)
+      if (tid == 0) atomicExch(a.err, 1);
+      mbar_wait_bounded(&bar_ld, phase);
+      break;
+    }
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int zi = 0; zi < kTZ; ++zi) {
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+          const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+          const uint32_t aoff =
+              (uint32_t)((dx + 1) * 2 * kPlane + ((zi + dz + 1) * (kTY + 2) + (dy + 1)) * kTX * 16);
+          umma_bf16(tmem + (uint32_t)(zi * 16), smem_desc(sA_u + aoff, kPlane, 128),
+                    smem_desc(sW_u + (uint32_t)(t * 512), 256, 128), idesc, t > 0 ? 1u : 0u);
+        }
+      }
+      umma_commit(&bar_mma);
+    }
+    const bool ok_mma = mbar_wait_bounded(&bar_mma, phase);
+    if (__syncthreads_or(!ok_mma)) {
+      if (tid == 0) atomicExch(a.err, 2);
+      mbar_wait_bounded(&bar_mma, phase);
+      break;
+    }
+    tc_fence_after();
+    const int row = tid;  // TMEM lane = M row = thread (warp w reads lanes 32w .. 32w + 31)
+    const int x = x0 + (row & 15), y = y0 + (row >> 4);
+#pragma unroll
+    for (int zi = 0; zi < kTZ; ++zi) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zi * 16), v);
+      const int z = z0 + zi;
+      if (x < a.nx && y < a.ny && z < a.nz) store_epi<EPI>(a, (((size_t)n * a.nz + z) * a.ny + y) * a.nx + x, n, v);
+    }
+    tc_fence_before();
+    __syncthreads();
+    phase ^= 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kConvCols);
+}
+
+// Weight gradient: per-block partial sums of dW over the block's tiles.
+__global__ void __launch_bounds__(kWgThreads) k_wgrad(const __grid_constant__ CUtensorMap xmap,
+                                                    const __grid_constant__ CUtensorMap gmap, WgArgs a) {
+  extern __shared__ unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t pad = (128u - (smem_u32(dsm) & 127u)) & 127u;
+  unsigned char* sX = dsm + pad;
+  unsigned char* sG = sX + 2 * kXPlane;
+  const uint32_t sX_u = smem_u32(sX), sG_u = smem_u32(sG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int dz = warp / 3 - 1, dy = warp % 3 - 1;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  float acc[3][2][4];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[j][q][k] = 0.f;
+  // ldmatrix row of this lane: matrix mi = lane / 8, row rr = lane % 8.
+  // G (B operand): matrix mi = (channel group mi / 2, voxels 8 (mi % 2) ..).
+  // X (A operand): matrix mi = (channel group mi % 2, voxels 8 (mi / 2) ..).
+  const int mi = lane >> 3, rr = lane & 7;
+  const uint32_t gofs = (uint32_t)((mi >> 1) * kGPlane + ((mi & 1) * 8 + rr) * 16);
+  const uint32_t xofs = (uint32_t)((mi & 1) * kXPlane + ((mi >> 1) * 8 + rr) * 16);
+  uint32_t phase = 0;
+  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    long long r = tile;
+    const int bx = (int)(r % a.tx);
+    r /= a.tx;
+    const int by = (int)(r % a.ty);
+    r /= a.ty;
+    const int bz = (int)(r % a.tz);
+    const int n = (int)(r / a.tz);
+    const int x0 = bx * kWTX, y0 = by * kWTY, z0 = bz * kWTZ;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bar, 2 * kXPlane + 2 * kGPlane);
+      for (int g = 0; g < 2; ++g) tma_load_5d(sX + g * kXPlane, &xmap, &bar, g * 8, x0 - 1, y0 - 1, z0 - 1, n);
+      for (int g = 0; g < 2; ++g) tma_load_5d(sG + g * kGPlane, &gmap, &bar, g * 8, x0, y0, z0, n);
+    }
+    const bool ok = mbar_wait_bounded(&bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(a.err, 3);
+      mbar_wait_bounded(&bar, phase);
+      break;
+    }
+#pragma unroll 2
+    for (int line = 0; line < kWTY * kWTZ; ++line) {
+      const int yi = line % kWTY, zi = line / kWTY;
+      uint32_t b[4];
+      ldsm_x4_trans(sG_u + gofs + (uint32_t)((zi * kWTY + yi) * kWTX * 16), b);
+      const uint32_t xl =
+          sX_u + xofs + (uint32_t)((((zi + dz + 1) * (kWTY + 2) + (yi + dy + 1)) * (kWTX + 2)) * 16);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t av[4];
+        ldsm_x4_trans(xl + (uint32_t)(j * 16), av);
+        mma_16816(acc[j][0], av, b[0], b[1]);
+        mma_16816(acc[j][1], av, b[2], b[3]);
+      }
+    }
+    __syncthreads();
+    phase ^= 1;
+  }
+  // accumulator fragment: c0, c1 = (row g, cols 2q, 2q+1), c2, c3 = row g + 8
+  float* P = a.partials + (size_t)blockIdx.x * kWElems;
+  const int g = lane >> 2, c2 = (lane & 3) * 2;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int t = 3 * warp + j;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int co = q * 8 + c2;
+      *reinterpret_cast<float2*>(P + (t * kC + g) * kC + co) = make_float2(acc[j][q][0], acc[j][q][1]);
+      *reinterpret_cast<float2*>(P + (t * kC + g + 8) * kC + co) = make_float2(acc[j][q][2], acc[j][q][3]);
+    }
+  }
+}
+
+__global__ void k_wgrad_reduce(const float* __restrict__ partials, int nblocks, float* __restrict__ dw, float scale,
+                               int accumulate) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kWElems) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * kWElems + e];
+  dw[e] = (accumulate ? dw[e] : 0.f) + scale * s;
+}
+
+// ---------------------------------------------------------------------------
+// glue kernels; one thread per (voxel, channel group of 8) = one uint4
+__device__ __forceinline__ void unpack8(uint4 u, float (&f)[8]) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 p = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+    f[2 * k] = p.x;
+    f[2 * k + 1] = p.y;
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+  return make_uint4(pack_bf2(f[0], f[1]), pack_bf2(f[2], f[3]), pack_bf2(f[4], f[5]), pack_bf2(f[6], f[7]));
+}
+__device__ __forceinline__ void mask8(uint4 act, float (&f)[8]) {
+  const uint32_t w[4] = {act.x, act.y, act.z, act.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!bf_pos(w[k] & 0xffffu)) f[2 * k] = 0.f;
+    if (!bf_pos(w[k] >> 16)) f[2 * k + 1] = 0.f;
+  }
+}
+
+// index helpers: element (n, z, y, x, group) of a level with dims (nx, ny, nz)
+struct Lv {
+  int nx, ny, nz;
+  __device__ size_t u4(size_t n, int z, int y, int x, int g) const {
+    return ((((n * nz + z) * ny + y) * nx + x) << 1) + g;
+  }
+};
+
+__global__ void k_pool(const uint4* __restrict__ fine, uint4* __restrict__ coarse, Lv F, Lv Cc, size_t total) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i & 1);
+    size_t v = i >> 1;
+    const int x = (int)(v % Cc.nx);
+    v /= Cc.nx;
+    const int y = (int)(v % Cc.ny);
+    v /= Cc.ny;
+    const int z = (int)(v % Cc.nz);
+    const size_t n = v / Cc.nz;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float f[8];
+      unpack8(fine[F.u4(n, 2 * z + (c >> 2), 2 * y + ((c >> 1) & 1), 2 * x + (c & 1), g)], f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += f[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
+    coarse[i] = pack8(s);
+  }
+}
+
+__global__ void k_up_add(const uint4* __restrict__ coarse, const uint4* __restrict__ fine, uint4* __restrict__ out,
+                         Lv F, Lv Cc, size_t total) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i & 1);
+    size_t v = i >> 1;
+    const int x = (int)(v % F.nx);
+    v /= F.nx;
+    const int y = (int)(v % F.ny);
+    v /= F.ny;
+    const int z = (int)(v % F.nz);
+    const size_t n = v / F.nz;
+    float a[8], b[8];
+    unpack8(coarse[Cc.u4(n, z >> 1, y >> 1, x >> 1, g)], a);
+    unpack8(fine[i], b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += b[k];
+    out[i] = pack8(a);
+  }
+}
+
+__global__ void k_upbwd_mask(const uint4* __restrict__ gfine, const uint4* __restrict__ act, uint4* __restrict__ out,
+                             Lv F, Lv Cc, size_t total) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i & 1);
+    size_t v = i >> 1;
+    const int x = (int)(v % Cc.nx);
+    v /= Cc.nx;
+    const int y = (int)(v % Cc.ny);
+    v /= Cc.ny;
+    const int z = (int)(v % Cc.nz);
+    const size_t n = v / Cc.nz;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float f[8];
+      unpack8(gfine[F.u4(n, 2 * z + (c >> 2), 2 * y + ((c >> 1) & 1), 2 * x + (c & 1), g)], f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += f[k];
+    }
+    mask8(act[i], s);
+    out[i] = pack8(s);
+  }
+}
+
+__global__ void k_poolbwd_add_mask(const uint4* __restrict__ gskip, const uint4* __restrict__ gcoarse,
+                                   const uint4* __restrict__ act, uint4* __restrict__ out, Lv F, Lv Cc,
+                                   size_t total) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i & 1);
+    size_t v = i >> 1;
+    const int x = (int)(v % F.nx);
+    v /= F.nx;
+    const int y = (int)(v % F.ny);
+    v /= F.ny;
+    const int z = (int)(v % F.nz);
+    const size_t n = v / F.nz;
+    float a[8], b[8];
+    unpack8(gskip[i], a);
+    unpack8(gcoarse[Cc.u4(n, z >> 1, y >> 1, x >> 1, g)], b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += 0.125f * b[k];
+    mask8(act[i], a);
+    out[i] = pack8(a);
+  }
+}
+
+__device__ __forceinline__ const float* field(const float* base, const Fields& f, int n) {
+  const size_t s = f.idx ? (size_t)f.idx[n] : (size_t)n;
+  return base + s * f.stride;
+}
+
+// per-sample sum of squares of b: grid (blocks, n), partials[n * blocks + b]
+__global__ void k_sumsq_b(Fields f, size_t vox, float* __restrict__ partials) {
+  __shared__ double sh[32];
+  const float* b = field(f.b, f, blockIdx.y);
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x)
+    acc = fmaf(b[i], b[i], acc);
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (float)s;
+}
+
+__global__ void k_rms_final(const float* __restrict__ partials, int nblk, size_t vox, int n, float* __restrict__ rms,
+                            float* __restrict__ inv) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += (double)partials[s * nblk + b];
+  const double r = sqrt(acc / (double)vox);
+  rms[s] = r > 0.0 ? (float)r : 1.f;
+  inv[s] = r > 0.0 ? (float)(1.0 / r) : 1.f;
+}
+
+__global__ void k_pack_input(Fields f, const float* __restrict__ inv, uint4* __restrict__ x0, size_t vox, int n) {
+  const size_t total = vox * (size_t)n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / vox);
+    const size_t v = i - (size_t)s * vox;
+    const float q = inv[s];
+    const float bv = field(f.b, f, s)[v] * q, pv = field(f.p, f, s)[v] * q;
+    x0[2 * i] = make_uint4(pack_bf2(bv, pv), 0u, 0u, 0u);
+    x0[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+__global__ void k_loss_grad(const float* __restrict__ y, Fields f, const float* __restrict__ inv,
+                            uint4* __restrict__ gy, size_t vox, int n, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const size_t total = vox * (size_t)n;
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / vox);
+    const size_t v = i - (size_t)s * vox;
+    const float d = y[i] - field(f.t, f, s)[v] * inv[s];
+    acc = fmaf(d, d, acc);
+    gy[2 * i] = make_uint4(pack_bf2(d, 0.f), 0u, 0u, 0u);
+    gy[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  const double t = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partials[b];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = 0.5 * t;
+}
+
+// fwd operand: [t][ci / 8][co][ci % 8]; data-gradient operand: tap 26 - t,
+// [co / 8][ci][co % 8] (K = output channel, N = input channel).
+__global__ void k_adam_pack(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ grad, int update, AdamArgs a, __nv_bfloat16* __restrict__ wf,
+                            __nv_bfloat16* __restrict__ wd) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kLayers * kWElems) return;
+  float wv = w[e];
+  if (update) {
+    const float g = grad[e];
+    const float mv = a.b1 * m[e] + (1.f - a.b1) * g;
+    const float vv = a.b2 * v[e] + (1.f - a.b2) * g * g;
+    m[e] = mv;
+    v[e] = vv;
+    wv -= a.lr * (mv * a.c1) / (sqrtf(vv * a.c2) + a.eps);
+    w[e] = wv;
+  }
+  const int k = e / kWElems, rem = e % kWElems;
+  const int t = rem / (kC * kC), ci = (rem / kC) % kC, co = rem % kC;
+  const __nv_bfloat16 h = __float2bfloat16_rn(wv);
+  const size_t lb = (size_t)k * kTaps;
+  wf[((lb + t) * 2 + (ci >> 3)) * 128 + co * 8 + (ci & 7)] = h;
+  wd[((lb + (kTaps - 1 - t)) * 2 + (co >> 3)) * 128 + ci * 8 + (co & 7)] = h;
+}
+
+__global__ void k_pack_layer(const float* __restrict__ w, __nv_bfloat16* __restrict__ wf,
+                             __nv_bfloat16* __restrict__ wd) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kWElems) return;
+  const int t = e / (kC * kC), ci = (e / kC) % kC, co = e % kC;
+  const __nv_bfloat16 h = __float2bfloat16_rn(w[e]);
+  wf[(t * 2 + (ci >> 3)) * 128 + co * 8 + (ci & 7)] = h;
+  wd[((kTaps - 1 - t) * 2 + (co >> 3)) * 128 + ci * 8 + (co & 7)] = h;
+}
+
+__global__ void k_crop(const float* __restrict__ b, const float* __restrict__ p_next, const float* __restrict__ dp,
+                       long long fx, long long fy, long long cx, long long cy, long long cz, long long ox,
+                       long long oy, long long oz, float* __restrict__ dst) {
+  const size_t vox = (size_t)(cx * cy * cz);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x) {
+    const long long x = (long long)(i % cx), y = (long long)((i / cx) % cy), z = (long long)(i / (cx * cy));
+    const size_t src = (size_t)(((z + oz) * fy + (y + oy)) * fx + (x + ox));
+    const float d = dp[src];
+    dst[i] = b[src];
+    dst[vox + i] = p_next[src] - d;
+    dst[2 * vox + i] = d;
+  }
+}
+
+template <typename K>
+int occupancy_blocks(K kernel, int threads, size_t smem) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+  return nsm * (occ > 0 ? occ : 1);
+}
+
+int grid_1d(size_t work, int threads = 256) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t want = (work + threads - 1) / threads;
+  const size_t cap = (size_t)nsm * 8;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+
+bool encode_act(CUtensorMap* m, const void* base, const Dims& d, int bx, int by, int bz) {
+  auto fn = (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
+  if (!fn || ((uintptr_t)base & 15)) return false;
+  cuuint64_t gdim[5] = {(cuuint64_t)kC, (cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)d.n};
+  cuuint64_t gstride[4] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * 2 * d.nx, (cuuint64_t)kC * 2 * d.nx * d.ny,
+                           (cuuint64_t)kC * 2 * d.nx * d.ny * d.nz};
+  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int EPI>
+static cudaError_t conv_epi(const CUtensorMap& map, const void* wpack, const ConvArgs& a, cudaStream_t s) {
+  static int grid_cache = 0;
+  if (!grid_cache) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+    if (e != cudaSuccess) return e;
+    grid_cache = occupancy_blocks(k_conv<EPI>, kConvThreads, kConvSmem);
+  }
+  const long long g = a.ntiles < grid_cache ? a.ntiles : grid_cache;
+  k_conv<EPI><<<(unsigned)(g > 0 ? g : 1), kConvThreads, kConvSmem, s>>>(map, (const uint4*)wpack, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv(const void* x, const void* wpack, void* out, int epi, const void* mask, const float* scale,
+                        const Dims& d, int* err, cudaStream_t s) {
+  if (d.n <= 0 || d.vox() == 0) return cudaSuccess;
+  CUtensorMap map;
+  if (!encode_act(&map, x, d, kTX, kTY + 2, kTZ + 2)) return cudaErrorInvalidValue;
+  ConvArgs a;
+  a.nx = d.nx;
+  a.ny = d.ny;
+  a.nz = d.nz;
+  a.nn = d.n;
+  a.tx = (d.nx + kTX - 1) / kTX;
+  a.ty = (d.ny + kTY - 1) / kTY;
+  a.tz = (d.nz + kTZ - 1) / kTZ;
+  a.ntiles = (long long)a.tx * a.ty * a.tz * d.n;
+  a.out = out;
+  a.mask = (const __nv_bfloat16*)mask;
+  a.scale = scale;
+  a.err = err;
+  switch (epi) {
+    case kEpiF32: return conv_epi<kEpiF32>(map, wpack, a, s);
+    case kEpiRelu: return conv_epi<kEpiRelu>(map, wpack, a, s);
+    case kEpiLin: return conv_epi<kEpiLin>(map, wpack, a, s);
+    case kEpiMask: return conv_epi<kEpiMask>(map, wpack, a, s);
+    case kEpiOut0: return conv_epi<kEpiOut0>(map, wpack, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wgrad(const void* x, const void* g, float* partials, int max_blocks, int* nblocks, const Dims& d,
+                         int* err, cudaStream_t s) {
+  static int grid_cache = 0;
+  if (!grid_cache) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    if (e != cudaSuccess) return e;
+    grid_cache = occupancy_blocks(k_wgrad, kWgThreads, kWgSmem);
+  }
+  CUtensorMap xm, gm;
+  if (!encode_act(&xm, x, d, kWTX + 2, kWTY + 2, kWTZ + 2) || !encode_act(&gm, g, d, kWTX, kWTY, kWTZ))
+    return cudaErrorInvalidValue;
+  WgArgs a;
+  a.nx = d.nx;
+  a.ny = d.ny;
+  a.nz = d.nz;
+  a.nn = d.n;
+  a.tx = (d.nx + kWTX - 1) / kWTX;
+  a.ty = (d.ny + kWTY - 1) / kWTY;
+  a.tz = (d.nz + kWTZ - 1) / kWTZ;
+  a.ntiles = (long long)a.tx * a.ty * a.tz * d.n;
+  a.partials = partials;
+  a.err = err;
+  long long gsz = a.ntiles < grid_cache ? a.ntiles : grid_cache;
+  if (gsz > max_blocks) gsz = max_blocks;
+  if (gsz < 1) gsz = 1;
+  *nblocks = (int)gsz;
+  k_wgrad<<<(unsigned)gsz, kWgThreads, kWgSmem, s>>>(xm, gm, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad_reduce(const float* partials, int nblocks, float* dw, float scale, bool accumulate,
+                                cudaStream_t s) {
+  k_wgrad_reduce<<<(kWElems + 255) / 256, 256, 0, s>>>(partials, nblocks, dw, scale, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+static Lv lv_of(const Dims& d, int shift) { return Lv{d.nx >> shift, d.ny >> shift, d.nz >> shift}; }
+
+cudaError_t launch_pool(const void* fine, void* coarse, const Dims& d, cudaStream_t s) {
+  const size_t total = d.vox() / 8 * d.n * 2;
+  k_pool<<<grid_1d(total), 256, 0, s>>>((const uint4*)fine, (uint4*)coarse, lv_of(d, 0), lv_of(d, 1), total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_up_add(const void* coarse, const void* fine, void* out, const Dims& d, cudaStream_t s) {
+  const size_t total = d.vox() * d.n * 2;
+  k_up_add<<<grid_1d(total), 256, 0, s>>>((const uint4*)coarse, (const uint4*)fine, (uint4*)out, lv_of(d, 0),
+                                          lv_of(d, 1), total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upbwd_mask(const void* gfine, const void* act_coarse, void* out_coarse, const Dims& d,
+                              cudaStream_t s) {
+  const size_t total = d.vox() / 8 * d.n * 2;
+  k_upbwd_mask<<<grid_1d(total), 256, 0, s>>>((const uint4*)gfine, (const uint4*)act_coarse, (uint4*)out_coarse,
+                                              lv_of(d, 0), lv_of(d, 1), total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poolbwd_add_mask(const void* gskip, const void* gcoarse, const void* act, void* out,
+                                    const Dims& d, cudaStream_t s) {
+  const size_t total = d.vox() * d.n * 2;
+  k_poolbwd_add_mask<<<grid_1d(total), 256, 0, s>>>((const uint4*)gskip, (const uint4*)gcoarse, (const uint4*)act,
+                                                    (uint4*)out, lv_of(d, 0), lv_of(d, 1), total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rms(const Fields& f, const Dims& d, float* partials, float* rms, float* inv_rms,
+                       cudaStream_t s) {
+  const int nblk = 64;
+  k_sumsq_b<<<dim3(nblk, d.n), 256, 0, s>>>(f, d.vox(), partials);
+  k_rms_final<<<(d.n + 127) / 128, 128, 0, s>>>(partials, nblk, d.vox(), d.n, rms, inv_rms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_input(const Fields& f, const float* inv_rms, void* x0, const Dims& d, cudaStream_t s) {
+  k_pack_input<<<grid_1d(d.vox() * d.n), 256, 0, s>>>(f, inv_rms, (uint4*)x0, d.vox(), d.n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad(const float* y, const Fields& f, const float* inv_rms, void* gy, double* partials,
+                             double* loss, const Dims& d, cudaStream_t s) {
+  const int g = grid_1d(d.vox() * d.n);
+  k_loss_grad<<<g, 256, 0, s>>>(y, f, inv_rms, (uint4*)gy, d.vox(), d.n, partials);
+  k_sum_partials<<<1, 256, 0, s>>>(partials, g, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_pack(float* w, float* m, float* v, const float* grad, bool update, AdamArgs a, void* wf,
+                             void* wd, cudaStream_t s) {
+  k_adam_pack<<<(kLayers * kWElems + 255) / 256, 256, 0, s>>>(w, m, v, grad, update ? 1 : 0, a,
+                                                              (__nv_bfloat16*)wf, (__nv_bfloat16*)wd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, const int64_t full[3],
+                        const int64_t crop[3], const int64_t origin[3], float* dst, cudaStream_t s) {
+  const size_t vox = (size_t)(crop[0] * crop[1] * crop[2]);
+  k_crop<<<grid_1d(vox), 256, 0, s>>>(b, p_next, dp, full[0], full[1], crop[0], crop[1], crop[2], origin[0],
+                                      origin[1], origin[2], dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_layer(const float* w, void* wf, void* wd, cudaStream_t s) {
+  k_pack_layer<<<(kWElems + 255) / 256, 256, 0, s>>>(w, (__nv_bfloat16*)wf, (__nv_bfloat16*)wd);
+  return cudaGetLastError();
+}
+
+}  // namespace gn
+}  // namespace npmg

@@ -495,7 +495,8 @@ __global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restric
       else cells4<false>(L, i, x0, m);
       float bv[4], xv[4];
       ld4(b, i, x0, L.nx, bv);
-      ld4(xg, i, x0, L.nx, xv);
+      if (xg) ld4(xg, i, x0, L.nx, xv);
+      else xv[0] = xv[1] = xv[2] = xv[3] = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (x0 + k >= L.nx) continue;

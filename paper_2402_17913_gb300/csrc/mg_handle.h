@@ -15,6 +15,7 @@ constexpr int kProfEvents = 4096;      // event pairs buffered by the profiler
 
 struct mg_handle_s {
   int dim, L, kc, device, nsm, esz, use_graph;
+  int guess_check;  // restart from zero when the initial guess has relres > 1
   int64_t n[npmg::kMaxLevels][3];
   double h[npmg::kMaxLevels][3];
   size_t ncell[npmg::kMaxLevels];

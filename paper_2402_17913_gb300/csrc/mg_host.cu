@@ -225,6 +225,17 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
   }
   NPMG_CUDA(enqueue_outer(h, b, false, s));
   NPMG_CUDA(read_state(h, s));
+  const double guess_relres = h->st_host->relres0;
+  const bool rejected = h->guess_check && !h->st_host->outer_done && guess_relres > 1.0;
+  if (rejected) {
+    // the guess is worse than zero: the plain solve from x = 0 takes over
+    {
+      LaunchScope ls(h, MG_K_INIT_FINISH, s);
+      NPMG_CUDA(launch_init(h->lv[0], b, nullptr, h->xff[h->cur64], h->c, prm, h->st, h->partials, s));
+    }
+    NPMG_CUDA(enqueue_outer(h, b, false, s));
+    NPMG_CUDA(read_state(h, s));
+  }
   const bool graph = h->use_graph && !h->prof;
   if (graph) NPMG_CUDA(ensure_graph(h, s));
   int guard = 0;
@@ -268,6 +279,8 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     out->ms = ms;
     for (int k = 0; k < kHistory && k < 32; ++k) out->history[k] = st.hist[k];
+    out->guess_relres = guess_relres;
+    out->guess_rejected = rejected ? 1 : 0;
   }
   return status;
 }

@@ -255,17 +255,21 @@ k_up_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtenso
 
 // ---------------------------------------------------------------------------
 // host side
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+void* tensor_map_encoder() {
+  static void* fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+      fn = p;
   }
   return fn;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  return (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
 }
 
 static bool encode_2d(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int esz, int64_t nx, int64_t ny,

@@ -227,6 +227,7 @@ struct ns_handle_s {
   float* dp;
   size_t nfaces[3], ncells;
   int nsm;
+  gn_handle guess;  // learned initial guess of dp (not owned), or nullptr
 };
 
 static int ns_blocks(const ns_handle_s* n, size_t count) {
@@ -339,6 +340,19 @@ mg_status ns_create(ns_handle* out, int dim, const int64_t cells[3], double h, c
 
 mg_handle ns_pressure_handle(ns_handle ns) { return ns ? ns->mg : nullptr; }
 
+mg_status ns_set_guess(ns_handle ns, gn_handle g) {
+  if (!ns) {
+    set_error("ns_set_guess: NULL handle");
+    return MG_ERR_INVALID;
+  }
+  if (g && (ns->dim != 3 || (ns->cells[0] % 4) || (ns->cells[1] % 4) || (ns->cells[2] % 4))) {
+    set_error("ns_set_guess: the guess network needs a 3D grid with sides divisible by 4");
+    return MG_ERR_INVALID;
+  }
+  ns->guess = g;
+  return MG_OK;
+}
+
 mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v, const float* d_w, const float* d_p,
                       float* d_us, float* d_vs, float* d_ws, double dt, double nu, double u_inflow, void* stream) {
   if (!ns || !d_u || !d_v || !d_p || !d_us || !d_vs || (ns->dim == 3 && (!d_w || !d_ws))) {
@@ -434,8 +448,18 @@ mg_status ns_step(ns_handle ns, float* d_u, float* d_v, float* d_w, float* d_p, 
   if (st != MG_OK) return st;
   st = ns_divergence_rhs(ns, ns->star[0], ns->star[1], ns->dim == 3 ? ns->star[2] : nullptr, dt, ns->b, stream);
   if (st != MG_OK) return st;
-  NPMG_CUDA(cudaMemsetAsync(ns->dp, 0, ns->ncells * 4, s));
+  if (ns->guess) {
+    // warm start: dp from the network on (b, p^n); the solve restarts from
+    // zero when the guess is worse than zero
+    const int64_t cells[3] = {ns->cells[0], ns->cells[1], ns->cells[2]};
+    st = gn_forward(ns->guess, 1, cells, ns->b, d_p, ns->dp, stream);
+    if (st != MG_OK) return st;
+  } else {
+    NPMG_CUDA(cudaMemsetAsync(ns->dp, 0, ns->ncells * 4, s));
+  }
+  ns->mg->guess_check = ns->guess ? 1 : 0;
   mg_status solve = mg_solve(ns->mg, ns->b, ns->dp, rel_tol, stream, out);
+  ns->mg->guess_check = 0;
   if (solve != MG_OK && solve != MG_NOT_CONVERGED && solve != MG_DIVERGED) return solve;
   const NsGeom G = geom_of(ns);
   float* qs[3] = {d_u, d_v, d_w};

@@ -14,6 +14,9 @@ struct TmaLevelMaps {
   CUtensorMap b, x, e, m;
 };
 
+// The driver's cuTensorMapEncodeTiled (version 12000), or nullptr.
+void* tensor_map_encoder();
+
 bool tma_level_eligible(int dim, int pre, int post, const LevelDev& L);
 template <typename T>
 bool tma_encode_level(TmaLevelMaps* out, const LevelDev& L, const void* b, const void* x, const void* e);

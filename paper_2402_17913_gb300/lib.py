@@ -25,7 +25,14 @@ EXPORTED = [
     "ns_divergence_rhs", "ns_correct", "ns_pressure_handle", "ns_destroy",
     "mg_profile_enable", "mg_profile_read", "mg_kernel_launches", "mg_vcycle_noalloc",
     "mg_create_batched", "mg_solve_batched", "mg_tune_batched", "mg_batched_config", "mg_destroy_batched",
+    "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
+    "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
+    "gn_destroy", "ns_set_guess",
 ]
+GN_NUM_WEIGHTS = 49680
+GN_CONV_SCRATCH_BYTES = 28160
+GN_WGRAD_SCRATCH_MIN = 256 + 27 * 16 * 16 * 4
+GN_CONV_F32, GN_CONV_RELU, GN_CONV_DGRAD, GN_CONV_LIN = range(4)
 KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
                   "init_finish", "momentum", "divergence", "correct"]
 
@@ -40,7 +47,8 @@ class MgOptions(ctypes.Structure):
 class MgStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int),
                 ("levels", ctypes.c_int), ("relres0", ctypes.c_double), ("relres", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("ms", ctypes.c_float), ("history", ctypes.c_double * 32)]
+                ("bnorm", ctypes.c_double), ("ms", ctypes.c_float), ("history", ctypes.c_double * 32),
+                ("guess_relres", ctypes.c_double), ("guess_rejected", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "history"}
@@ -112,6 +120,21 @@ def load():
         "mg_batched_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int]),
         "mg_destroy_batched": (ctypes.c_int, [_vp]),
+        "gn_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp]),
+        "gn_set_weights": (ctypes.c_int, [_vp, _vp]),
+        "gn_get_weights": (ctypes.c_int, [_vp, _vp]),
+        "gn_forward": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3, _vp, _vp, _vp, _vp]),
+        "gn_gradients": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3, _vp, _vp, _vp,
+                                        ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+        "gn_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
+        "gn_dataset_reserve": (ctypes.c_int, [_vp, _i64_3, ctypes.c_int]),
+        "gn_dataset_add": (ctypes.c_int, [_vp, _i64_3, _vp, _vp, _vp, _vp]),
+        "gn_dataset_size": (ctypes.c_int, [_vp]),
+        "gn_train": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, _vp, _vp]),
+        "gn_conv3d": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, ctypes.c_int, _vp, _vp]),
+        "gn_conv3d_wgrad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, _vp, ctypes.c_size_t, _vp]),
+        "gn_destroy": (ctypes.c_int, [_vp]),
+        "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -326,3 +349,115 @@ def mg_destroy_batched(b):
 def ns_destroy(ns):
     if ns:
         load().ns_destroy(ns)
+
+
+# ---------------------------------------------------------------------------
+# learned initial guess
+def _host_f32(a, n=None):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32).ravel()
+    if n is not None and a.size != n:
+        raise ValueError("expected %d floats, got %d" % (n, a.size))
+    return a
+
+
+def gn_flatten(weights):
+    """Concatenate per-layer arrays [27][c_in][c_out] into the C layout."""
+    import numpy as np
+    return np.concatenate([np.asarray(w, dtype=np.float32).ravel() for w in weights])
+
+
+def gn_unflatten(flat):
+    """Inverse of gn_flatten (float64 arrays per layer)."""
+    import numpy as np
+    io = [(2, 16)] + [(16, 16)] * 7 + [(16, 1)]
+    out, o = [], 0
+    for ci, co in io:
+        k = 27 * ci * co
+        out.append(np.asarray(flat[o:o + k], dtype=np.float64).reshape(27, ci, co))
+        o += k
+    return out
+
+
+def gn_create(weights, stream=None):
+    """weights: list of 9 arrays [27][c_in][c_out] or the flat C layout."""
+    w = _host_f32(gn_flatten(weights) if isinstance(weights, (list, tuple)) else weights, GN_NUM_WEIGHTS)
+    out = _vp()
+    _check(load().gn_create(ctypes.byref(out), w.ctypes.data, stream_ptr(stream)))
+    return out.value
+
+
+def gn_set_weights(g, weights):
+    w = _host_f32(gn_flatten(weights) if isinstance(weights, (list, tuple)) else weights, GN_NUM_WEIGHTS)
+    _check(load().gn_set_weights(g, w.ctypes.data))
+
+
+def gn_get_weights(g):
+    import numpy as np
+    w = np.empty(GN_NUM_WEIGHTS, np.float32)
+    _check(load().gn_get_weights(g, w.ctypes.data))
+    return w
+
+
+def gn_forward(g, cells, b, p, out, n=1, stream=None):
+    _check(load().gn_forward(g, n, _i64_3(*cells), ptr(b), ptr(p), ptr(out), stream_ptr(stream)))
+
+
+def gn_gradients(g, cells, b, p, t, n=1, stream=None):
+    """Returns (loss, flat float32 gradient)."""
+    import numpy as np
+    loss = ctypes.c_double()
+    grad = np.empty(GN_NUM_WEIGHTS, np.float32)
+    _check(load().gn_gradients(g, n, _i64_3(*cells), ptr(b), ptr(p), ptr(t), ctypes.byref(loss), grad.ctypes.data,
+                               stream_ptr(stream)))
+    return loss.value, grad
+
+
+def gn_adam_step(g, lr, grad=None, stream=None):
+    gp = None if grad is None else _host_f32(grad, GN_NUM_WEIGHTS)
+    _check(load().gn_adam_step(g, None if gp is None else gp.ctypes.data, lr, stream_ptr(stream)))
+
+
+def gn_dataset_reserve(g, crop, capacity):
+    _check(load().gn_dataset_reserve(g, _i64_3(*crop), capacity))
+
+
+def gn_dataset_add(g, cells, b, p_next, dp, stream=None):
+    _check(load().gn_dataset_add(g, _i64_3(*cells), ptr(b), ptr(p_next), ptr(dp), stream_ptr(stream)))
+
+
+def gn_dataset_size(g):
+    return load().gn_dataset_size(g)
+
+
+def gn_train(g, steps, batch, seed, lr, stream=None):
+    """Returns the per-step losses (numpy float64)."""
+    import numpy as np
+    losses = np.zeros(steps, np.float64)
+    _check(load().gn_train(g, steps, batch, seed, lr, losses.ctypes.data, stream_ptr(stream)))
+    return losses
+
+
+def gn_conv3d(x, w, y, cells, n=1, mode=GN_CONV_F32, scratch=None, stream=None):
+    """x: bf16 tensor [n][z][y][x][16]; w: float32 CUDA tensor [27][16][16]."""
+    import torch
+    if scratch is None:
+        scratch = torch.empty(GN_CONV_SCRATCH_BYTES, dtype=torch.uint8, device=x.device)
+    _check(load().gn_conv3d(ptr(x), ptr(w), ptr(y), n, _i64_3(*cells), mode, ptr(scratch), stream_ptr(stream)))
+
+
+def gn_conv3d_wgrad(x, gr, dw, cells, n=1, scratch_bytes=None, stream=None):
+    import torch
+    nbytes = scratch_bytes or (GN_WGRAD_SCRATCH_MIN + 511 * 27 * 16 * 16 * 4)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    _check(load().gn_conv3d_wgrad(ptr(x), ptr(gr), ptr(dw), n, _i64_3(*cells), ptr(scratch), nbytes,
+                                  stream_ptr(stream)))
+
+
+def gn_destroy(g):
+    if g:
+        load().gn_destroy(g)
+
+
+def ns_set_guess(ns, g):
+    _check(load().ns_set_guess(ns, g))

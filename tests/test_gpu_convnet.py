@@ -1,0 +1,235 @@
+"""GPU parity of the learned initial-guess network against the FP64 oracle
+(oracle/convnet.py).
+
+Single kernels (forward / data-gradient convolution on the tcgen05 tensor
+cores, weight gradient on warp MMAs) get exactly representable BF16 inputs
+and weights, so the only difference from the oracle is FP32 accumulation:
+each output must lie within gamma_n = n * 2^-24 of the sum of absolute
+terms (n = terms summed), the textbook bound for recursive summation in any
+order.  Whole-network results carry BF16 rounding of every activation and
+are compared in relative L2 with a tolerance derived in the test."""
+import numpy as np
+import pytest
+
+from oracle import convnet as C
+from paper_2402_17913_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2402_17913_gb300 import build, lib
+    build.build()
+    lib.load()
+    return lib
+
+
+def bf16_exact(a):
+    """float64 array of BF16-representable values (round to nearest even)."""
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().double().numpy()
+
+
+def to_ndhwc(x):
+    """[n][C][Z][Y][X] -> [n][Z][Y][X][16] (zero-padded channels)."""
+    n, c, z, y, xx = x.shape
+    out = np.zeros((n, z, y, xx, 16))
+    out[..., :c] = np.moveaxis(x, 1, -1)
+    return out
+
+
+def from_ndhwc(a, c=16):
+    return np.moveaxis(a[..., :c], -1, 1)
+
+
+def dev_bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).bfloat16().cuda()
+
+
+SHAPES = [(2, 20, 12, 6), (1, 16, 8, 2), (1, 37, 9, 5), (3, 8, 4, 4)]  # (n, x, y, z): ragged tails, tiny grids
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_conv_forward_matches_oracle_within_fp32_bound(L, shape):
+    n, nx, ny, nz = shape
+    rng = np.random.default_rng(1)
+    x = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    w = bf16_exact(rng.standard_normal((27, 16, 16)) * 0.2)
+    y = torch.empty((n, nz, ny, nx, 16), dtype=torch.float32, device="cuda")
+    L.gn_conv3d(dev_bf16(to_ndhwc(x)), torch.from_numpy(w.astype(np.float32)).cuda(), y, (nx, ny, nz), n=n,
+                mode=L.GN_CONV_F32)
+    got = from_ndhwc(y.cpu().numpy().astype(np.float64))
+    for s in range(n):
+        ref = C.conv3d(x[s], w)
+        bound = 432 * U32 * C.conv3d(np.abs(x[s]), np.abs(w)) + 1e-30
+        assert np.all(np.abs(got[s] - ref) <= bound), (s, np.max(np.abs(got[s] - ref) / bound))
+
+
+def test_conv_relu_and_linear_bf16_outputs(L):
+    n, nx, ny, nz = 2, 20, 12, 6
+    rng = np.random.default_rng(2)
+    x = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    w = bf16_exact(rng.standard_normal((27, 16, 16)) * 0.2)
+    xd, wd = dev_bf16(to_ndhwc(x)), torch.from_numpy(w.astype(np.float32)).cuda()
+    for mode, f in ((L.GN_CONV_RELU, C.relu), (L.GN_CONV_LIN, lambda a: a)):
+        y = torch.empty((n, nz, ny, nx, 16), dtype=torch.bfloat16, device="cuda")
+        L.gn_conv3d(xd, wd, y, (nx, ny, nz), n=n, mode=mode)
+        got = from_ndhwc(y.float().cpu().numpy().astype(np.float64))
+        for s in range(n):
+            ref = C.conv3d(x[s], w)
+            bound = 432 * U32 * C.conv3d(np.abs(x[s]), np.abs(w))
+            # FP32 sum within `bound`, then one BF16 rounding (relative 2^-8
+            # at most, round to nearest)
+            tol = 2.0 ** -8 * (np.abs(f(ref)) + bound) + bound
+            assert np.all(np.abs(got[s] - f(ref)) <= tol), mode
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3])
+def test_conv_data_gradient_matches_oracle(L, shape):
+    n, nx, ny, nz = shape
+    rng = np.random.default_rng(3)
+    g = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    w = bf16_exact(rng.standard_normal((27, 16, 16)) * 0.2)
+    y = torch.empty((n, nz, ny, nx, 16), dtype=torch.float32, device="cuda")
+    L.gn_conv3d(dev_bf16(to_ndhwc(g)), torch.from_numpy(w.astype(np.float32)).cuda(), y, (nx, ny, nz), n=n,
+                mode=L.GN_CONV_DGRAD)
+    got = from_ndhwc(y.cpu().numpy().astype(np.float64))
+    for s in range(n):
+        ref = C.conv3d_dgrad(g[s], w)
+        bound = 432 * U32 * C.conv3d_dgrad(np.abs(g[s]), np.abs(w)) + 1e-30
+        assert np.all(np.abs(got[s] - ref) <= bound)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3])
+def test_conv_weight_gradient_matches_oracle(L, shape):
+    n, nx, ny, nz = shape
+    rng = np.random.default_rng(4)
+    x = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    g = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    dw = torch.empty((27, 16, 16), dtype=torch.float32, device="cuda")
+    L.gn_conv3d_wgrad(dev_bf16(to_ndhwc(x)), dev_bf16(to_ndhwc(g)), dw, (nx, ny, nz), n=n)
+    got = dw.cpu().numpy().astype(np.float64)
+    ref = sum(C.conv3d_wgrad(x[s], g[s]) for s in range(n))
+    terms = n * nx * ny * nz
+    bound = terms * U32 * sum(C.conv3d_wgrad(np.abs(x[s]), np.abs(g[s])) for s in range(n))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_wgrad_with_one_block_or_many_stays_within_bound(L):
+    """One block (every voxel summed serially) or many (per-block partials
+    summed in a fixed order): both within the FP32 summation bound."""
+    n, nx, ny, nz = 1, 48, 24, 12
+    rng = np.random.default_rng(5)
+    x = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    g = bf16_exact(rng.standard_normal((n, 16, nz, ny, nx)))
+    xd, gd = dev_bf16(to_ndhwc(x)), dev_bf16(to_ndhwc(g))
+    ref = C.conv3d_wgrad(x[0], g[0])
+    bound = nx * ny * nz * U32 * C.conv3d_wgrad(np.abs(x[0]), np.abs(g[0]))
+    for sb in (L.GN_WGRAD_SCRATCH_MIN, L.GN_WGRAD_SCRATCH_MIN + 63 * 27 * 16 * 16 * 4):
+        dw = torch.empty((27, 16, 16), dtype=torch.float32, device="cuda")
+        L.gn_conv3d_wgrad(xd, gd, dw, (nx, ny, nz), n=n, scratch_bytes=sb)
+        assert np.all(np.abs(dw.cpu().numpy().astype(np.float64) - ref) <= bound), sb
+
+
+# ---------------------------------------------------------------------------
+# whole network
+def fields(shape, seed):
+    """(b, p) of a smooth-plus-noise pair and a target dp, float32-exact."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    b = I.blob_rhs(shape, seed) + 0.05 * rng.standard_normal(shape)
+    p = I.blob_rhs(shape, seed + 1)
+    t = I.blob_rhs(shape, seed + 2) * 0.01
+    return [np.asarray(a, np.float32).astype(np.float64) for a in (b, p, t)]
+
+
+def bf16_weights(seed):
+    return [bf16_exact(w) for w in I.convnet_weights(seed)]
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_network_forward_matches_oracle(L):
+    cells = (32, 24, 16)
+    shape = (16, 24, 32)
+    W = bf16_weights(11)
+    g = L.gn_create(W)
+    try:
+        for n in (1, 2):
+            fs = [fields(shape, 20 + 3 * s) for s in range(n)]
+            bd = torch.from_numpy(np.stack([f[0] for f in fs]).astype(np.float32)).cuda()
+            pd = torch.from_numpy(np.stack([f[1] for f in fs]).astype(np.float32)).cuda()
+            out = torch.empty_like(bd)
+            L.gn_forward(g, cells, bd, pd, out, n=n)
+            got = out.cpu().numpy().astype(np.float64)
+            for s in range(n):
+                x, rms = C.net_input(fs[s][0], fs[s][1])
+                ref = C.forward(W, x)[0][0] * rms
+                # BF16 storage of the input and of 8 hidden activations:
+                # each rounding perturbs relatively by <= 2^-9; through 9
+                # layers the errors add up to a few 1e-3 (rel L2)
+                assert rel_l2(got[s], ref) <= 1.5e-2, (n, s, rel_l2(got[s], ref))
+    finally:
+        L.gn_destroy(g)
+
+
+def test_gradients_match_oracle(L):
+    cells = (32, 16, 16)
+    shape = (16, 16, 32)
+    W = bf16_weights(12)
+    b, p, t = fields(shape, 40)
+    g = L.gn_create(W)
+    try:
+        dev = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (b, p, t)]
+        loss, grad = L.gn_gradients(g, cells, *dev)
+    finally:
+        L.gn_destroy(g)
+    x, rms = C.net_input(b, p)
+    y, cache = C.forward(W, x)
+    tgt = (t / rms)[None]
+    ref_loss = C.loss(y, tgt)
+    ref = C.backward(W, cache, y, tgt)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
+    got = L.gn_unflatten(grad)
+    for k in range(9):
+        cos = float(np.sum(got[k] * ref[k]) / (np.linalg.norm(got[k]) * np.linalg.norm(ref[k])))
+        assert cos >= 0.999, (k, cos)
+        assert rel_l2(got[k], ref[k]) <= 5e-2, (k, rel_l2(got[k], ref[k]))
+
+
+def test_adam_steps_match_oracle(L):
+    W = I.convnet_weights(13)
+    rng = np.random.default_rng(14)
+    grads = [[rng.standard_normal(w.shape) * 10.0 ** rng.uniform(-6, 0) for w in W] for _ in range(3)]
+    grads = [[np.asarray(a, np.float32).astype(np.float64) for a in G] for G in grads]
+    W32 = [np.asarray(w, np.float32).astype(np.float64) for w in W]
+    g = L.gn_create(W32)
+    try:
+        opt = C.Adam(W32, lr=1e-3)
+        cur = W32
+        for G in grads:
+            L.gn_adam_step(g, 1e-3, grad=L.gn_flatten(G))
+            cur = opt.step(cur, G)
+            got = L.gn_unflatten(L.gn_get_weights(g))
+            for k in range(9):
+                # float32 update: |w| + lr, each rounded at 2^-24 relative
+                assert np.all(np.abs(got[k] - cur[k]) <= 4 * U32 * (np.abs(cur[k]) + 1e-3) + 1e-9)
+    finally:
+        L.gn_destroy(g)
+
+
+def test_weights_round_trip_and_padding_stays_zero(L):
+    W = I.convnet_weights(15)
+    g = L.gn_create(W)
+    try:
+        got = L.gn_unflatten(L.gn_get_weights(g))
+        for k in range(9):
+            assert np.array_equal(got[k], np.asarray(W[k], np.float32).astype(np.float64))
+    finally:
+        L.gn_destroy(g)

@@ -24,7 +24,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", path)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:mg|ns)_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:mg|ns|gn)_\w+)\s*\(", text, flags=re.M):
             names.append(m.group(1))
     return sorted(set(names))
 
@@ -79,3 +79,21 @@ def test_solve_rejects_null(lib):
     from paper_2402_17913_gb300 import lib as L
     assert lib.mg_solve(None, None, None, 1e-6, None, None) == L.MG_ERR_INVALID
     assert lib.ns_step(None, None, None, None, None, 0.1, 0.1, 1.0, 1e-6, None, None) == L.MG_ERR_INVALID
+
+
+def test_guess_network_rejects_invalid_arguments(lib):
+    """Argument checks of the gn_* entry points run before any device work."""
+    from paper_2402_17913_gb300 import lib as L
+    vp = ctypes.c_void_p
+    cells = (ctypes.c_int64 * 3)(8, 8, 8)
+    assert lib.gn_create(None, None, None) == L.MG_ERR_INVALID
+    out = vp()
+    assert lib.gn_create(ctypes.byref(out), None, None) == L.MG_ERR_INVALID and not out.value
+    assert lib.gn_forward(None, 1, cells, None, None, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_gradients(None, 1, cells, None, None, None, None, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_conv3d(None, None, None, 1, cells, 0, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_conv3d_wgrad(None, None, None, 1, cells, None, 0, None) == L.MG_ERR_INVALID
+    assert lib.gn_train(None, 1, 1, 0, 1e-3, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_dataset_size(None) == 0
+    assert lib.ns_set_guess(None, None) == L.MG_ERR_INVALID
+    assert "ns_set_guess" in L.last_error()
