@@ -16,6 +16,12 @@ resolutions.  Everything here is plain numpy in float64:
 * ``backward``: the analytic gradient of 0.5 * mean((y - t)^2), checked
   against finite differences in the tests.
 * ``adam``: Kingma & Ba's update (beta1 0.9, beta2 0.999, eps 1e-8).
+* ``residual_loss``: the warm-start objective.  The solve that follows
+  stops on ||b - A x|| / ||b||, so a guess is worth what its residual is
+  worth: 0.5 * sum over interior fluid cells of (A_crop y - b)^2 / size,
+  with A_crop the 7-point pressure operator of the crop (spacing h; links
+  only between fluid cells inside the crop).  On cells whose six neighbours
+  all lie inside the crop it equals the full grid's operator.
 """
 import numpy as np
 
@@ -114,8 +120,13 @@ def loss(y, t):
 
 def backward(W, c, y, t):
     """Gradients of ``loss(forward(W, x), t)`` with respect to every W[k]."""
+    return backward_from(W, c, (y - t) / y.size)
+
+
+def backward_from(W, c, g):
+    """Gradients of a loss with respect to every W[k], given its gradient
+    ``g`` with respect to the network output y ([1, Z, Y, X])."""
     dW = [None] * NLAYERS
-    g = (y - t) / y.size
     dW[8] = conv3d_wgrad(c["d1"], g)
     g = conv3d_dgrad(g, W[8]) * (c["a8"] > 0)
     dW[7] = conv3d_wgrad(c["s1"], g)
@@ -167,3 +178,40 @@ def net_input(b, p):
     rms = float(np.sqrt(np.mean(b * b)))
     s = 1.0 / rms if rms > 0 else 1.0
     return np.stack([b * s, p * s]), (rms if rms > 0 else 1.0)
+
+
+def crop_operator(v, fluid, h=1.0):
+    """(A_crop v)_c = (1/h^2) sum over fluid face neighbours n inside the
+    array of (v_c - v_n), on fluid cells c; 0 on solid cells.  v, fluid:
+    [Z, Y, X] (fluid boolean)."""
+    fl = np.asarray(fluid, bool)
+    out = np.zeros_like(v, dtype=np.float64)
+    Z, Y, X = v.shape
+    for axis in range(3):
+        n = v.shape[axis]
+        for d in (-1, 1):
+            src = [slice(None)] * 3
+            dst = [slice(None)] * 3
+            dst[axis] = slice(max(0, -d), n - max(0, d))
+            src[axis] = slice(max(0, d), n + min(0, d))
+            both = fl[tuple(dst)] & fl[tuple(src)]
+            out[tuple(dst)] += both * (v[tuple(dst)] - v[tuple(src)])
+    return out * fl / (h * h)
+
+
+def interior(shape):
+    """Cells whose six face neighbours all lie inside the array."""
+    m = np.zeros(shape, bool)
+    m[1:-1, 1:-1, 1:-1] = True
+    return m
+
+
+def residual_loss(y, b, fluid, h=1.0):
+    """(loss, dloss/dy) of 0.5 * sum_{interior fluid} (A_crop y - b)^2 / size
+    for one sample; y, b: [Z, Y, X]."""
+    w = interior(y.shape) & np.asarray(fluid, bool)
+    r = (crop_operator(y, fluid, h) - b) * w
+    loss = 0.5 * float(np.sum(r * r)) / y.size
+    # A_crop is symmetric, so the gradient is A_crop applied to the masked
+    # residual
+    return loss, crop_operator(r, fluid, h) / y.size

@@ -77,3 +77,62 @@ def test_adam_step_hand_worked():
     opt = C.Adam(w, lr=0.1)
     w2 = opt.step(w, g)[0]
     assert np.allclose(w2, [1.0 - 0.1 * 0.5 / (0.5 + 1e-8), -2.0 + 0.1 * 4.0 / (4.0 + 1e-8)], rtol=1e-15)
+
+
+def test_crop_operator_equals_full_operator_on_interior_cells():
+    """On cells whose neighbours all lie in the crop, A_crop is the full
+    grid's pressure operator (poisson.Level with the same solid and any
+    face types), for h != 1 too."""
+    from oracle import poisson as P
+    rng = np.random.default_rng(7)
+    shape = (10, 12, 14)
+    solid = rng.random(shape) < 0.15
+    v = rng.standard_normal(shape)
+    h = 0.5
+    lv = P.Level(shape, (h, h, h), (1, 0, 1, 1, 0, 1), solid)
+    full = P.apply_A(lv, v)
+    z0, y0, x0 = 2, 3, 4
+    crop = (slice(z0, z0 + 6), slice(y0, y0 + 7), slice(x0, x0 + 8))
+    got = C.crop_operator(v[crop], ~solid[crop], h)
+    inner = C.interior(got.shape)
+    assert np.allclose(got[inner], full[crop][inner], rtol=1e-13, atol=1e-12)
+
+
+def test_crop_operator_is_symmetric_and_kills_constants():
+    rng = np.random.default_rng(8)
+    shape = (6, 7, 8)
+    fluid = rng.random(shape) > 0.2
+    u, v = rng.standard_normal(shape), rng.standard_normal(shape)
+    assert np.isclose(np.vdot(C.crop_operator(u, fluid), v), np.vdot(u, C.crop_operator(v, fluid)), rtol=1e-12)
+    assert np.allclose(C.crop_operator(np.full(shape, 3.0), fluid), 0.0)
+
+
+def test_residual_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(9)
+    shape = (5, 6, 7)
+    fluid = rng.random(shape) > 0.2
+    y, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    loss, g = C.residual_loss(y, b, fluid, h=0.7)
+    eps = 1e-6
+    for _ in range(12):
+        idx = tuple(rng.integers(0, s) for s in shape)
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += eps
+        ym[idx] -= eps
+        fd = (C.residual_loss(yp, b, fluid, 0.7)[0] - C.residual_loss(ym, b, fluid, 0.7)[0]) / (2 * eps)
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(fd), 1e-6), (idx, fd, g[idx])
+    # the exact solution of the interior equations has zero loss
+    r_only_boundary = C.interior(shape) & fluid
+    assert loss > 0 and np.all(g[~fluid] == 0) and r_only_boundary.any()
+
+
+def test_backward_from_matches_backward_for_the_l2_loss():
+    rng = np.random.default_rng(10)
+    W = I.convnet_weights(3)
+    x = rng.standard_normal((2, 8, 8, 8))
+    t = rng.standard_normal((1, 8, 8, 8))
+    y, c = C.forward(W, x)
+    a = C.backward(W, c, y, t)
+    b = C.backward_from(W, c, (y - t) / y.size)
+    for k in range(C.NLAYERS):
+        assert np.array_equal(a[k], b[k])
