@@ -328,7 +328,11 @@ mg_status mg_destroy_batched(mg_batch b);
  * with R = ReLU and Wk 3x3x3 cross-correlations with zero padding.  Weights
  * are FP32 masters; activations and tensor-core operands are BF16 with FP32
  * accumulation.  Training minimises 0.5 * mean((net(x) - dp / rms(b))^2)
- * with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on 3D crops of solver runs.
+ * (GN_LOSS_L2) or the residual of the guess, 0.5 * sum over interior
+ * fluid cells of (A_crop y - b / rms(b))^2 / size (GN_LOSS_RESIDUAL; A_crop
+ * = the 7-point pressure operator of the crop with spacing h, links only
+ * between fluid cells inside the crop), with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on 3D crops of solver runs.
  *
  * Weights on the host are the 9 layers back to back, layer k as
  * [27 taps][c_in][c_out] float32, tap t = (dz+1)*9 + (dy+1)*3 + (dx+1),
@@ -341,16 +345,23 @@ mg_status mg_destroy_batched(mg_batch b);
  *   Adam moments and packed operands.  Activation workspaces are allocated
  *   on first use of a shape and kept.
  * gn_forward: d_out[n] = dp_guess for samples (d_b[n], d_p[n]).
- * gn_gradients: loss and gradient (host, weight layout; nullable) for
- *   targets d_t (the solver's dp); synchronises.
+ * gn_gradients: loss and gradient (host, weight layout; nullable) under
+ *   loss_mode: targets d_t (the solver's dp) for GN_LOSS_L2; fluid flags
+ *   d_fluid (float 1/0, NULL = all fluid) and spacing h for
+ *   GN_LOSS_RESIDUAL; synchronises.
  * gn_adam_step: one Adam step with h_grad (weight layout) or, when NULL,
  *   the last gn_gradients result; lr > 0.
- * gn_dataset_reserve: room for `capacity` crops of size crop (x, y, z).
+ * gn_dataset_reserve: room for `capacity` crops of size crop (x, y, z)
+ *   of a grid with spacing h.
  * gn_dataset_add: cuts full fields (cells) into non-overlapping crops and
- *   appends (b, p^n = d_p_next - d_dp, dp) for each until full.
+ *   appends (b, p^n = d_p_next - d_dp, dp, fluid) for each until full;
+ *   d_solid = uint8 solid flags of the grid or NULL.
  * gn_train: `steps` Adam steps on minibatches of `batch` crops drawn with a
- *   seeded generator; h_losses (nullable) receives each step's loss;
- *   synchronises.
+ *   seeded generator under loss_mode, the learning rate decaying from lr to
+ *   lr / 20 along a half cosine; a minibatch's inputs are scaled by the rms
+ *   of b over the whole minibatch (so the residual loss is the minibatch's
+ *   squared relative residual / 2); h_losses (nullable) receives each
+ *   step's loss; synchronises.
  * gn_conv3d (building block): one convolution of a BF16 NDHWC16 tensor
  *   d_x ([n][z][y][x][16]) with FP32 weights d_w ([27][16][16], device).
  *   mode GN_CONV_F32: d_y = float [..][16]; GN_CONV_RELU: bf16 ReLU output;
@@ -370,6 +381,7 @@ mg_status mg_destroy_batched(mg_batch b);
 #define GN_CONV_SCRATCH_BYTES 28160
 #define GN_WGRAD_SCRATCH_MIN (256 + 27 * 16 * 16 * 4)
 enum { GN_CONV_F32 = 0, GN_CONV_RELU = 1, GN_CONV_DGRAD = 2, GN_CONV_LIN = 3 };
+enum { GN_LOSS_L2 = 0, GN_LOSS_RESIDUAL = 1 };
 typedef struct gn_handle_s* gn_handle;
 mg_status gn_create(gn_handle* out, const float* h_weights, void* stream);
 mg_status gn_set_weights(gn_handle g, const float* h_weights);
@@ -377,19 +389,24 @@ mg_status gn_get_weights(gn_handle g, float* h_weights);
 mg_status gn_forward(gn_handle g, int n, const int64_t cells[3], const float* d_b, const float* d_p, float* d_out,
                      void* stream);
 mg_status gn_gradients(gn_handle g, int n, const int64_t cells[3], const float* d_b, const float* d_p,
-                       const float* d_t, double* h_loss, float* h_grad, void* stream);
+                       const float* d_t, const float* d_fluid, int loss_mode, double h, double* h_loss,
+                       float* h_grad, void* stream);
 mg_status gn_adam_step(gn_handle g, const float* h_grad, double lr, void* stream);
-mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity);
+mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity, double h);
 mg_status gn_dataset_add(gn_handle g, const int64_t cells[3], const float* d_b, const float* d_p_next,
-                         const float* d_dp, void* stream);
+                         const float* d_dp, const uint8_t* d_solid, void* stream);
 int gn_dataset_size(gn_handle g);
-mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, double* h_losses, void* stream);
+mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, int loss_mode, double* h_losses,
+                   void* stream);
 mg_status gn_conv3d(const void* d_x, const float* d_w, void* d_y, int n, const int64_t cells[3], int mode,
                     void* d_scratch, void* stream);
 mg_status gn_conv3d_wgrad(const void* d_x, const void* d_g, float* d_dw, int n, const int64_t cells[3],
                           void* d_scratch, size_t scratch_bytes, void* stream);
 mg_status gn_destroy(gn_handle g);
 mg_status ns_set_guess(ns_handle ns, gn_handle g);
+/* Device pointers (owned by ns, valid until the next ns_step) of the last
+   step's right-hand side b and pressure increment dp (cells each). */
+mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp);
 
 /* The pressure handle inside ns (owned by ns; do not destroy). */
 mg_handle ns_pressure_handle(ns_handle ns);

@@ -46,7 +46,8 @@ struct Dims {
 };
 
 // Encodes the 5D tensor map (16 channels, x, y, z, n) of an NDHWC16 BF16
-// tensor with a box of 8 channels x bx x by x bz x 1.
+// tensor with a box of 16 channels x bx x by x bz x 1, 32-byte swizzled
+// (rows of one voxel; halves exchanged on rows with address bit 7 set).
 bool encode_act(CUtensorMap* m, const void* base, const Dims& d, int bx, int by, int bz);
 
 // y = conv(x, W) with the packed operand `wpack` (kPackBytes, 16-byte
@@ -74,30 +75,40 @@ cudaError_t launch_poolbwd_add_mask(const void* gskip, const void* gcoarse, cons
 struct Fields {
   const float* b;
   const float* p;
-  const float* t;  // target dp (loss only)
-  size_t stride;   // floats between samples
-  const int* idx;  // device sample indices or nullptr
+  const float* t;      // target dp (L2 loss only)
+  const float* fluid;  // 1 on fluid cells, 0 on solid (residual loss; nullptr = all fluid)
+  size_t stride;       // floats between samples
+  const int* idx;      // device sample indices or nullptr
 };
-// sumsq per sample -> inv_rms[n] = 1 / rms(b) (1 when b == 0), rms[n].
-cudaError_t launch_rms(const Fields& f, const Dims& d, float* partials, float* rms, float* inv_rms,
+// rms[n] = rms of b over sample n (pooled: over all samples), 1 when b == 0;
+// inv_rms = 1 / rms.
+cudaError_t launch_rms(const Fields& f, const Dims& d, bool pooled, float* partials, float* rms, float* inv_rms,
                        cudaStream_t s);
 cudaError_t launch_pack_input(const Fields& f, const float* inv_rms, void* x0, const Dims& d, cudaStream_t s);
-// gy[vox][16] = (y - t * inv_rms) in channel 0, 0 elsewhere; loss partials
-// reduced into *loss (0.5 * sum of squares, float64).
+// L2 loss: gy[vox][16] = (y - t * inv_rms) in channel 0, 0 elsewhere;
+// *loss = 0.5 * mean of the squares (float64, fixed-order sum).
 cudaError_t launch_loss_grad(const float* y, const Fields& f, const float* inv_rms, void* gy, double* partials,
                              double* loss, const Dims& d, cudaStream_t s);
+// Residual loss: r = (A_crop y - b * inv_rms) on interior fluid cells (0
+// elsewhere), *loss = 0.5 * sum r^2 / (n * vox); gy = A_crop r in channel 0.
+cudaError_t launch_residual_loss_grad(const float* y, const Fields& f, const float* inv_rms, float inv_h2, float* r,
+                                      void* gy, double* partials, double* loss, const Dims& d, cudaStream_t s);
 
 // Adam update of every padded layer (update == false: pack only) and the
 // BF16 operand packing for the forward (wf) and data-gradient (wd) kernels.
 struct AdamArgs {
-  float lr, b1, b2, eps, c1, c2;  // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+  // betas, 1 - betas (each rounded from float64), eps; c1 = 1 / (1 - b1^t),
+  // c2 = 1 / (1 - b2^t)
+  float lr, b1, b2, omb1, omb2, eps, c1, c2;
 };
 cudaError_t launch_adam_pack(float* w, float* m, float* v, const float* grad, bool update, AdamArgs a, void* wf,
                              void* wd, cudaStream_t s);
 
-// Crop extraction: dataset sample i (b, p^n = p - dp, dp) from full fields.
-cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, const int64_t full[3],
-                        const int64_t crop[3], const int64_t origin[3], float* dst, cudaStream_t s);
+// Crop extraction: dataset sample (b, p^n = p - dp, dp, fluid) from full
+// fields (solid: uint8, nullable).
+cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, const uint8_t* solid,
+                        const int64_t full[3], const int64_t crop[3], const int64_t origin[3], float* dst,
+                        cudaStream_t s);
 
 // Packs one FP32 layer [27][16][16] into the forward and data-gradient
 // operands (building-block convolutions).

@@ -35,7 +35,7 @@ struct Work {
   void *gy, *ga8, *gs1, *ga2, *ga1;
   void *ga7, *gs2, *ga4, *ga3, *gp1;
   void *ga6, *ga5, *gp2;
-  float* y;
+  float *y, *r;
   float *rms, *inv, *rpart;
   double* lpart;
   bool same(int n, const int64_t c[3], bool tr) const {
@@ -51,7 +51,7 @@ struct Work {
     for (int l = 0; l < 3; ++l) d[l] = Dims{n, (int)(c[0] >> l), (int)(c[1] >> l), (int)(c[2] >> l)};
     const size_t t[3] = {round256(d[0].vox() * n * 32), round256(d[1].vox() * n * 32), round256(d[2].vox() * n * 32)};
     const int n0 = tr ? 10 : 5, n1 = tr ? 10 : 5, n2 = tr ? 6 : 3;
-    const size_t total = n0 * t[0] + n1 * t[1] + n2 * t[2] + round256(d[0].vox() * n * 4) + 3 * round256(n * 4) +
+    const size_t total = n0 * t[0] + n1 * t[1] + n2 * t[2] + 2 * round256(d[0].vox() * n * 4) + 3 * round256(n * 4) +
                          round256((size_t)n * kRmsBlocks * 4) + round256(8 * 1024 * 8);
     cudaError_t e = cudaMalloc((void**)&pool, total);
     if (e != cudaSuccess) {
@@ -73,6 +73,7 @@ struct Work {
       ga6 = take(t[2]), ga5 = take(t[2]), gp2 = take(t[2]);
     }
     y = (float*)take(d[0].vox() * n * 4);
+    r = (float*)take(d[0].vox() * n * 4);
     rms = (float*)take(n * 4);
     inv = (float*)take(n * 4);
     take(n * 4);
@@ -96,9 +97,10 @@ struct gn_handle_s {
   char* pool = nullptr;
   int adam_t = 0;
   Work infer, train;
-  float* ds = nullptr;
+  float* ds = nullptr;  // crops: [b, p^n, dp, fluid][z][y][x] each
   int ds_cap = 0, ds_n = 0;
   int64_t crop[3] = {0, 0, 0};
+  double ds_h = 1.0;    // grid spacing of the dataset's pressure operator
 };
 
 namespace {
@@ -149,10 +151,12 @@ mg_status ensure_work(Work& W, int n, const int64_t c[3], bool train) {
 }
 
 // Forward pass; output channel 0 into `out` scaled by `scale` (per sample,
-// or nullptr for 1).
-mg_status forward(gn_handle_s* g, Work& W, const Fields& f, float* out, const float* scale, cudaStream_t s) {
+// or nullptr for 1).  Inputs are scaled by 1 / rms(b), the rms taken per
+// sample or pooled over the samples.
+mg_status forward(gn_handle_s* g, Work& W, const Fields& f, float* out, const float* scale, bool pooled,
+                  cudaStream_t s) {
   const Dims* d = W.d;
-  GN_TRY(launch_rms(f, d[0], W.rpart, W.rms, W.inv, s));
+  GN_TRY(launch_rms(f, d[0], pooled, W.rpart, W.rms, W.inv, s));
   GN_TRY(launch_pack_input(f, W.inv, W.x0, d[0], s));
   GN_TRY(launch_conv(W.x0, pf(g, 0), W.e1a, kEpiRelu, nullptr, nullptr, d[0], g->err, s));
   GN_TRY(launch_conv(W.e1a, pf(g, 1), W.e1, kEpiRelu, nullptr, nullptr, d[0], g->err, s));
@@ -184,12 +188,17 @@ mg_status wgrad_into(gn_handle_s* g, const void* x, const void* gr, int layer, c
     if (st_ != MG_OK) return st_; \
   } while (0)
 
-// Loss of the last forward (W.y, normalised units) against f.t into
-// *loss (device) and the gradient of every layer into g->grad.
-mg_status backward(gn_handle_s* g, Work& W, const Fields& f, double* loss, cudaStream_t s) {
+// Loss of the last forward (W.y, normalised units) into *loss (device) and
+// the gradient of every layer into g->grad.  mode GN_LOSS_L2: against the
+// target f.t; GN_LOSS_RESIDUAL: the residual of the guess on the crop's
+// interior fluid cells (operator spacing h).
+mg_status backward(gn_handle_s* g, Work& W, const Fields& f, int mode, double h, double* loss, cudaStream_t s) {
   const Dims* d = W.d;
   const float sc = (float)(1.0 / ((double)d[0].vox() * d[0].n));
-  GN_TRY(launch_loss_grad(W.y, f, W.inv, W.gy, W.lpart, loss, d[0], s));
+  if (mode == GN_LOSS_RESIDUAL)
+    GN_TRY(launch_residual_loss_grad(W.y, f, W.inv, (float)(1.0 / (h * h)), W.r, W.gy, W.lpart, loss, d[0], s));
+  else
+    GN_TRY(launch_loss_grad(W.y, f, W.inv, W.gy, W.lpart, loss, d[0], s));
   GN_STEP(wgrad_into(g, W.d1, W.gy, 8, d[0], sc, s));
   GN_TRY(launch_conv(W.gy, pd(g, 8), W.ga8, kEpiMask, W.d1, nullptr, d[0], g->err, s));
   GN_STEP(wgrad_into(g, W.s1, W.ga8, 7, d[0], sc, s));
@@ -220,6 +229,8 @@ mg_status adam(gn_handle_s* g, double lr, cudaStream_t s) {
   a.lr = (float)lr;
   a.b1 = 0.9f;
   a.b2 = 0.999f;
+  a.omb1 = (float)(1.0 - 0.9);
+  a.omb2 = (float)(1.0 - 0.999);
   a.eps = 1e-8f;
   a.c1 = (float)(1.0 / (1.0 - pow(0.9, g->adam_t)));
   a.c2 = (float)(1.0 / (1.0 - pow(0.999, g->adam_t)));
@@ -339,22 +350,25 @@ mg_status gn_forward(gn_handle g, int n, const int64_t cells[3], const float* d_
   cudaStream_t s = (cudaStream_t)stream;
   GN_STEP(ensure_work(g->infer, n, cells, false));
   const size_t vox = (size_t)(cells[0] * cells[1] * cells[2]);
-  Fields f = {d_b, d_p, nullptr, vox, nullptr};
-  return forward(g, g->infer, f, d_out, g->infer.rms, s);
+  Fields f = {d_b, d_p, nullptr, nullptr, vox, nullptr};
+  return forward(g, g->infer, f, d_out, g->infer.rms, false, s);
 }
 
 mg_status gn_gradients(gn_handle g, int n, const int64_t cells[3], const float* d_b, const float* d_p,
-                       const float* d_t, double* h_loss, float* h_grad, void* stream) {
-  if (!g || !cells || !d_b || !d_p || !d_t || n <= 0 || !cells_ok(cells)) {
+                       const float* d_t, const float* d_fluid, int loss_mode, double h, double* h_loss,
+                       float* h_grad, void* stream) {
+  if (!g || !cells || !d_b || !d_p || n <= 0 || !cells_ok(cells) ||
+      (loss_mode != GN_LOSS_L2 && loss_mode != GN_LOSS_RESIDUAL) || (loss_mode == GN_LOSS_L2 && !d_t) ||
+      !(h > 0)) {
     set_error("gn_gradients: invalid argument (cells must be multiples of 4)");
     return MG_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
   GN_STEP(ensure_work(g->train, n, cells, true));
   const size_t vox = (size_t)(cells[0] * cells[1] * cells[2]);
-  Fields f = {d_b, d_p, d_t, vox, nullptr};
-  GN_STEP(forward(g, g->train, f, g->train.y, nullptr, s));
-  GN_STEP(backward(g, g->train, f, g->loss_dev, s));
+  Fields f = {d_b, d_p, d_t, d_fluid, vox, nullptr};
+  GN_STEP(forward(g, g->train, f, g->train.y, nullptr, false, s));
+  GN_STEP(backward(g, g->train, f, loss_mode, h, g->loss_dev, s));
   GN_STEP(check_err(g, s, "gn_gradients"));
   if (h_loss) GN_TRY(cudaMemcpy(h_loss, g->loss_dev, sizeof(double), cudaMemcpyDeviceToHost));
   if (h_grad) {
@@ -382,8 +396,8 @@ mg_status gn_adam_step(gn_handle g, const float* h_grad, double lr, void* stream
   return MG_OK;
 }
 
-mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity) {
-  if (!g || !crop || capacity <= 0 || !cells_ok(crop)) {
+mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity, double h) {
+  if (!g || !crop || capacity <= 0 || !cells_ok(crop) || !(h > 0)) {
     set_error("gn_dataset_reserve: invalid argument (crop sides must be multiples of 4)");
     return MG_ERR_INVALID;
   }
@@ -391,12 +405,13 @@ mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity) {
   g->ds = nullptr;
   g->ds_cap = g->ds_n = 0;
   const size_t vox = (size_t)(crop[0] * crop[1] * crop[2]);
-  if (cudaMalloc((void**)&g->ds, (size_t)capacity * 3 * vox * 4) != cudaSuccess) {
+  if (cudaMalloc((void**)&g->ds, (size_t)capacity * 4 * vox * 4) != cudaSuccess) {
     g->ds = nullptr;
     set_error("gn_dataset_reserve: cudaMalloc of %d crops failed", capacity);
     return MG_ERR_OOM;
   }
   g->ds_cap = capacity;
+  g->ds_h = h;
   for (int a = 0; a < 3; ++a) g->crop[a] = crop[a];
   return MG_OK;
 }
@@ -404,7 +419,7 @@ mg_status gn_dataset_reserve(gn_handle g, const int64_t crop[3], int capacity) {
 int gn_dataset_size(gn_handle g) { return g ? g->ds_n : 0; }
 
 mg_status gn_dataset_add(gn_handle g, const int64_t cells[3], const float* d_b, const float* d_p_next,
-                         const float* d_dp, void* stream) {
+                         const float* d_dp, const uint8_t* d_solid, void* stream) {
   if (!g || !cells || !d_b || !d_p_next || !d_dp || !g->ds) {
     set_error("gn_dataset_add: invalid argument or no dataset reserved");
     return MG_ERR_INVALID;
@@ -421,15 +436,17 @@ mg_status gn_dataset_add(gn_handle g, const int64_t cells[3], const float* d_b, 
       for (int64_t i = 0; i < nc[0]; ++i) {
         if (g->ds_n >= g->ds_cap) return MG_OK;
         const int64_t org[3] = {i * g->crop[0], j * g->crop[1], k * g->crop[2]};
-        GN_TRY(launch_crop(d_b, d_p_next, d_dp, cells, g->crop, org, g->ds + (size_t)g->ds_n * 3 * vox,
+        GN_TRY(launch_crop(d_b, d_p_next, d_dp, d_solid, cells, g->crop, org, g->ds + (size_t)g->ds_n * 4 * vox,
                            (cudaStream_t)stream));
         g->ds_n += 1;
       }
   return MG_OK;
 }
 
-mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, double* h_losses, void* stream) {
-  if (!g || steps <= 0 || batch <= 0 || !(lr > 0) || g->ds_n <= 0) {
+mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, int loss_mode, double* h_losses,
+                    void* stream) {
+  if (!g || steps <= 0 || batch <= 0 || !(lr > 0) || g->ds_n <= 0 ||
+      (loss_mode != GN_LOSS_L2 && loss_mode != GN_LOSS_RESIDUAL)) {
     set_error("gn_train: invalid argument or empty dataset");
     return MG_ERR_INVALID;
   }
@@ -450,10 +467,12 @@ mg_status gn_train(gn_handle g, int steps, int batch, uint64_t seed, double lr, 
   GN_TRY(cudaStreamSynchronize(s));
   const size_t vox = (size_t)(g->crop[0] * g->crop[1] * g->crop[2]);
   for (int k = 0; k < steps; ++k) {
-    Fields f = {g->ds, g->ds + vox, g->ds + 2 * vox, 3 * vox, g->idx_dev + (size_t)k * batch};
-    GN_STEP(forward(g, g->train, f, g->train.y, nullptr, s));
-    GN_STEP(backward(g, g->train, f, g->loss_dev + (k % kLossSlots), s));
-    GN_STEP(adam(g, lr, s));
+    Fields f = {g->ds, g->ds + vox, g->ds + 2 * vox, g->ds + 3 * vox, 4 * vox, g->idx_dev + (size_t)k * batch};
+    GN_STEP(forward(g, g->train, f, g->train.y, nullptr, true, s));
+    GN_STEP(backward(g, g->train, f, loss_mode, g->ds_h, g->loss_dev + (k % kLossSlots), s));
+    // cosine decay from lr to lr / 20 over the call
+    const double lr_k = lr * (0.05 + 0.95 * 0.5 * (1.0 + cos(M_PI * (double)k / (double)steps)));
+    GN_STEP(adam(g, lr_k, s));
     if (h_losses && (k % kLossSlots == kLossSlots - 1 || k == steps - 1)) {
       // the device keeps kLossSlots step losses; drain them to the host
       const int first = k - k % kLossSlots;

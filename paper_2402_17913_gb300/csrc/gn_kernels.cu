@@ -8,22 +8,27 @@
 // 8 along y, one z-plane) the 3x3x3 correlation with 16 input and 16 output
 // channels is 27 MMAs of shape M x N x K = 128 x 16 x 16, one per tap t:
 //     D[v][co] += sum_ci X[v + o_t][ci] * W[t][ci][co].
-// A block stages, by TMA, three copies of its input tile (x shifted by
-// dx = -1, 0, +1) in the no-swizzle K-major core-matrix layout
-// [channel group][z][y][x][8 channels]; the copies carry a one-voxel halo in
-// y and z.  The A operand of tap (dz, dy, dx) is then a contiguous 2 KB run of
-// copy dx starting at row (z + dz, y + dy): each descriptor differs only in
-// its start address, and out-of-range voxels arrive as zeros (the zero
-// padding).  One thread issues the 27 MMAs per z-plane into a TMEM
-// accumulator (128 lanes x 16 FP32 columns); the four warps read it back
-// with tcgen05.ld, apply the epilogue and store 32 bytes per voxel.
-//
+// A block fetches, by TMA, three copies of its input tile (x shifted by
+// dx = -1, 0, +1), each with a one-voxel halo in y and z, as rows of one
+// voxel's 16 channels (32 bytes) in the 32-byte-swizzled K-major layout that
+// the tensor core reads directly.  The A operand of tap (dz, dy, dx) is then
+// a contiguous 4 KB run of copy dx starting at row (z + dz, y + dy): each
+// descriptor differs only in its start address (a multiple of 512 bytes, so
+// the swizzle phase never shifts), and out-of-range voxels arrive as zeros
+// (the zero padding).  One thread issues the 27 MMAs per z-plane into a
+// TMEM accumulator (128 lanes x 16 FP32 columns) from a table of
+// precomputed descriptors, then, once they are done, the TMA of the block's
+// next tile; the four warps read the accumulator back with tcgen05.ld,
+// apply the epilogue and store 32 bytes per voxel.
+
 // The data gradient is the same kernel with the mirrored, transposed taps
 // (W'[26 - t][co][ci] = W[t][ci][co]).  The weight gradient
 //     dW[t][ci][co] = sum_v X[v + o_t][ci] G[v][co]
 // reduces over voxels and has M = 27 x 16 rows whose shared-memory views
 // are not a single strided pattern, so it uses m16n8k16 MMAs fed by
-// ldmatrix.trans, which gathers any eight 16-byte rows.
+// ldmatrix.trans, which gathers any eight 16-byte rows from the same
+// swizzled [z][y][x][16 channels] tiles (the swizzle puts the 8 rows of one
+// channel group in 8 different bank quads).
 #include <cudaTypedefs.h>
 
 #include "gn.h"
@@ -35,19 +40,25 @@ namespace gn {
 
 namespace {
 
-constexpr int kPlane = (kTZ + 2) * (kTY + 2) * kTX * 16;  // bytes of one staged (copy, channel group) plane
-constexpr int kAOff = 14336;                             // A planes start (1024-aligned, after the weights)
-constexpr int kConvSmem = kAOff + 6 * kPlane + 1024;     // + alignment slack
+constexpr int kPlane = (kTZ + 2) * (kTY + 2) * kTX * 32;  // bytes of one staged copy: [z][y][x][16 ch]
+constexpr int kDescOff = 13824;                           // descriptor table after the 13824-byte weights
+constexpr int kAOff = 14592;                              // copies start (256-aligned: the swizzle atom)
+constexpr int kConvSmem = kAOff + 3 * kPlane + 256;       // + alignment slack; 3 blocks fit an SM
 constexpr int kConvThreads = 128;
-constexpr uint32_t kConvCols = 32;                       // TMEM columns (kTZ accumulators of 16, min 32)
+constexpr uint32_t kConvCols = 32;                        // TMEM columns (kTZ accumulators of 16, min 32)
 static_assert(kTZ * 16 <= (int)kConvCols, "TMEM columns");
-static_assert(kPlane % 1024 == 0, "TMA destinations stay 1024-aligned");
+static_assert(kPlane % 256 == 0 && kAOff % 256 == 0, "swizzled TMA destinations stay 256-aligned");
+static_assert(kDescOff + 8 * kTaps * (kTZ + 1) <= kAOff, "descriptor table fits");
 
-constexpr int kXPlane = (kWTX + 2) * (kWTY + 2) * (kWTZ + 2) * 16;
-constexpr int kGPlane = kWTX * kWTY * kWTZ * 16;
-constexpr int kWgSmem = 2 * kXPlane + 2 * kGPlane + 128;
+constexpr int kXTile = (kWTX + 2) * (kWTY + 2) * (kWTZ + 2) * 32;  // wgrad x tile with halo
+constexpr int kGTile = kWTX * kWTY * kWTZ * 32;
+constexpr int kWgSmem = kXTile + kGTile + 1024;
 constexpr int kWgThreads = 288;  // 9 warps: warp w owns taps 3w .. 3w+2 (dz, dy fixed, dx = -1, 0, 1)
-static_assert(kXPlane % 128 == 0 && kGPlane % 128 == 0, "TMA destinations stay 128-aligned");
+static_assert(kXTile % 256 == 0 && kGTile % 256 == 0, "swizzled TMA destinations stay 256-aligned");
+
+// byte offset of channel group g of voxel v in a 32-byte-swizzled tile
+// whose base is 256-byte aligned
+__device__ __forceinline__ uint32_t sw32(uint32_t v, uint32_t g) { return v * 32u + ((g ^ ((v >> 2) & 1u)) << 4); }
 
 struct ConvArgs {
   int nx, ny, nz, nn;
@@ -111,12 +122,24 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
   __shared__ __align__(8) uint64_t bar_ld;
   __shared__ __align__(8) uint64_t bar_mma;
   __shared__ uint32_t tmem_slot;
-  const uint32_t pad = (1024u - (smem_u32(dsm) & 1023u)) & 1023u;
+  const uint32_t pad = (256u - (smem_u32(dsm) & 255u)) & 255u;
   unsigned char* sW = dsm + pad;
+  uint64_t* sD = reinterpret_cast<uint64_t*>(sW + kDescOff);  // [zi][t] A descriptors, then [t] B
   unsigned char* sA = sW + kAOff;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sW_u = smem_u32(sW), sA_u = smem_u32(sA);
 
   for (int i = tid; i < kPackBytes / 16; i += kConvThreads) reinterpret_cast<uint4*>(sW)[i] = wpack[i];
+  for (int i = tid; i < kTaps * (kTZ + 1); i += kConvThreads) {
+    const int t = i % kTaps, zi = i / kTaps;
+    if (zi < kTZ) {
+      const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+      sD[i] = smem_desc_sw32(sA_u + (uint32_t)((dx + 1) * kPlane + ((zi + dz + 1) * (kTY + 2) + (dy + 1)) * kTX * 32),
+                             256);
+    } else {
+      sD[i] = smem_desc(sW_u + (uint32_t)(t * 512), 256, 128);
+    }
+  }
   fence_proxy_async_smem();
   if (tid == 0) {
     mbar_init(&bar_ld, 1);
@@ -131,47 +154,47 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t sW_u = smem_u32(sW), sA_u = smem_u32(sA);
   constexpr uint32_t idesc = idesc_bf16(128, 16);
-  uint32_t phase = 0;
 
-  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  auto origin = [&](long long tile, int& x0, int& y0, int& z0, int& n) {
     long long r = tile;
-    const int bx = (int)(r % a.tx);
+    x0 = (int)(r % a.tx) * kTX;
     r /= a.tx;
-    const int by = (int)(r % a.ty);
+    y0 = (int)(r % a.ty) * kTY;
     r /= a.ty;
-    const int bz = (int)(r % a.tz);
-    const int n = (int)(r / a.tz);
-    const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
-    if (tid == 0) {
-      mbar_arrive_expect_tx(&bar_ld, 6 * kPlane);
+    z0 = (int)(r % a.tz) * kTZ;
+    n = (int)(r / a.tz);
+  };
+  auto fetch = [&](long long tile) {
+    int x0, y0, z0, n;
+    origin(tile, x0, y0, z0, n);
+    mbar_arrive_expect_tx(&bar_ld, 3 * kPlane);
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-          tma_load_5d(sA + (c * 2 + g) * kPlane, &xmap, &bar_ld, g * 8, x0 + c - 1, y0 - 1, z0 - 1, n);
-    }
+    for (int c = 0; c < 3; ++c) tma_load_5d(sA + c * kPlane, &xmap, &bar_ld, 0, x0 + c - 1, y0 - 1, z0 - 1, n);
+  };
+
+  uint32_t phase = 0;
+  long long tile = blockIdx.x;
+  if (tid == 0 && tile < a.ntiles) fetch(tile);
+  bool pending = tile < a.ntiles;
+  for (; tile < a.ntiles; tile += gridDim.x) {
     const bool ok_ld = mbar_wait_bounded(&bar_ld, phase);
     if (__syncthreads_or(!ok_ld)) {
-      // a tile that never lands: report it, give the copies in flight a
-      // bounded wait, and stop (no MMA was issued for this tile)
+      // a tile that never lands: report it, give the copy in flight a
+      // bounded wait, and stop (no MMA reads it)
       if (tid == 0) atomicExch(a.err, 1);
       mbar_wait_bounded(&bar_ld, phase);
+      pending = false;
       break;
     }
+    pending = false;
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll 1
       for (int zi = 0; zi < kTZ; ++zi) {
 #pragma unroll
-        for (int t = 0; t < kTaps; ++t) {
-          const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-          const uint32_t aoff =
-              (uint32_t)((dx + 1) * 2 * kPlane + ((zi + dz + 1) * (kTY + 2) + (dy + 1)) * kTX * 16);
-          umma_bf16(tmem + (uint32_t)(zi * 16), smem_desc(sA_u + aoff, kPlane, 128),
-                    smem_desc(sW_u + (uint32_t)(t * 512), 256, 128), idesc, t > 0 ? 1u : 0u);
-        }
+        for (int t = 0; t < kTaps; ++t)
+          umma_bf16(tmem + (uint32_t)(zi * 16), sD[zi * kTaps + t], sD[kTZ * kTaps + t], idesc, t > 0 ? 1u : 0u);
       }
       umma_commit(&bar_mma);
     }
@@ -182,6 +205,12 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
       break;
     }
     tc_fence_after();
+    // the copies are free: prefetch the next tile under the epilogue
+    const long long next = tile + gridDim.x;
+    if (tid == 0 && next < a.ntiles) fetch(next);
+    pending = next < a.ntiles;
+    int x0, y0, z0, n;
+    origin(tile, x0, y0, z0, n);
     const int row = tid;  // TMEM lane = M row = thread (warp w reads lanes 32w .. 32w + 31)
     const int x = x0 + (row & 15), y = y0 + (row >> 4);
 #pragma unroll
@@ -195,6 +224,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
     __syncthreads();
     phase ^= 1;
   }
+  // a prefetch still in flight after an early exit: bounded wait before the
+  // block's shared memory goes away
+  if (pending) mbar_wait_bounded(&bar_ld, phase ^ 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -202,13 +234,15 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
 }
 
 // Weight gradient: per-block partial sums of dW over the block's tiles.
+// Staged (32-byte swizzled): x as [z][y][18][16 ch] covering x0 - 1 ..
+// x0 + 16, g as [z][y][16][16 ch].
 __global__ void __launch_bounds__(kWgThreads) k_wgrad(const __grid_constant__ CUtensorMap xmap,
                                                     const __grid_constant__ CUtensorMap gmap, WgArgs a) {
   extern __shared__ unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
-  const uint32_t pad = (128u - (smem_u32(dsm) & 127u)) & 127u;
+  const uint32_t pad = (1024u - (smem_u32(dsm) & 1023u)) & 1023u;
   unsigned char* sX = dsm + pad;
-  unsigned char* sG = sX + 2 * kXPlane;
+  unsigned char* sG = sX + kXTile;
   const uint32_t sX_u = smem_u32(sX), sG_u = smem_u32(sG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int dz = warp / 3 - 1, dy = warp % 3 - 1;
@@ -228,8 +262,8 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const __grid_constant__ CU
   // G (B operand): matrix mi = (channel group mi / 2, voxels 8 (mi % 2) ..).
   // X (A operand): matrix mi = (channel group mi % 2, voxels 8 (mi / 2) ..).
   const int mi = lane >> 3, rr = lane & 7;
-  const uint32_t gofs = (uint32_t)((mi >> 1) * kGPlane + ((mi & 1) * 8 + rr) * 16);
-  const uint32_t xofs = (uint32_t)((mi & 1) * kXPlane + ((mi >> 1) * 8 + rr) * 16);
+  const uint32_t gk = (uint32_t)((mi & 1) * 8 + rr), gg = (uint32_t)(mi >> 1);
+  const uint32_t xk = (uint32_t)((mi >> 1) * 8 + rr), xg = (uint32_t)(mi & 1);
   uint32_t phase = 0;
   for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     long long r = tile;
@@ -241,9 +275,9 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const __grid_constant__ CU
     const int n = (int)(r / a.tz);
     const int x0 = bx * kWTX, y0 = by * kWTY, z0 = bz * kWTZ;
     if (tid == 0) {
-      mbar_arrive_expect_tx(&bar, 2 * kXPlane + 2 * kGPlane);
-      for (int g = 0; g < 2; ++g) tma_load_5d(sX + g * kXPlane, &xmap, &bar, g * 8, x0 - 1, y0 - 1, z0 - 1, n);
-      for (int g = 0; g < 2; ++g) tma_load_5d(sG + g * kGPlane, &gmap, &bar, g * 8, x0, y0, z0, n);
+      mbar_arrive_expect_tx(&bar, kXTile + kGTile);
+      tma_load_5d(sX, &xmap, &bar, 0, x0 - 1, y0 - 1, z0 - 1, n);
+      tma_load_5d(sG, &gmap, &bar, 0, x0, y0, z0, n);
     }
     const bool ok = mbar_wait_bounded(&bar, phase);
     if (__syncthreads_or(!ok)) {
@@ -255,13 +289,12 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const __grid_constant__ CU
     for (int line = 0; line < kWTY * kWTZ; ++line) {
       const int yi = line % kWTY, zi = line / kWTY;
       uint32_t b[4];
-      ldsm_x4_trans(sG_u + gofs + (uint32_t)((zi * kWTY + yi) * kWTX * 16), b);
-      const uint32_t xl =
-          sX_u + xofs + (uint32_t)((((zi + dz + 1) * (kWTY + 2) + (yi + dy + 1)) * (kWTX + 2)) * 16);
+      ldsm_x4_trans(sG_u + sw32((uint32_t)((zi * kWTY + yi) * kWTX) + gk, gg), b);
+      const uint32_t xl = (uint32_t)(((zi + dz + 1) * (kWTY + 2) + (yi + dy + 1)) * (kWTX + 2));
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         uint32_t av[4];
-        ldsm_x4_trans(xl + (uint32_t)(j * 16), av);
+        ldsm_x4_trans(sX_u + sw32(xl + xk + (uint32_t)j, xg), av);
         mma_16816(acc[j][0], av, b[0], b[1]);
         mma_16816(acc[j][1], av, b[2], b[3]);
       }
@@ -430,13 +463,15 @@ __global__ void k_sumsq_b(Fields f, size_t vox, float* __restrict__ partials) {
   if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (float)s;
 }
 
-__global__ void k_rms_final(const float* __restrict__ partials, int nblk, size_t vox, int n, float* __restrict__ rms,
-                            float* __restrict__ inv) {
+__global__ void k_rms_final(const float* __restrict__ partials, int nblk, size_t vox, int n, int pooled,
+                            float* __restrict__ rms, float* __restrict__ inv) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   double acc = 0.0;
-  for (int b = 0; b < nblk; ++b) acc += (double)partials[s * nblk + b];
-  const double r = sqrt(acc / (double)vox);
+  const int s0 = pooled ? 0 : s, s1 = pooled ? n : s + 1;
+  for (int q = s0; q < s1; ++q)
+    for (int b = 0; b < nblk; ++b) acc += (double)partials[q * nblk + b];
+  const double r = sqrt(acc / ((double)vox * (s1 - s0)));
   rms[s] = r > 0.0 ? (float)r : 1.f;
   inv[s] = r > 0.0 ? (float)(1.0 / r) : 1.f;
 }
@@ -470,12 +505,69 @@ __global__ void k_loss_grad(const float* __restrict__ y, Fields f, const float* 
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-__global__ void k_sum_partials(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+__global__ void k_sum_partials(const double* __restrict__ partials, int nblk, double scale,
+                               double* __restrict__ out) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partials[b];
   const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = 0.5 * t;
+  if (threadIdx.x == 0) *out = scale * t;
+}
+
+// (A_crop v)_c * h^2 on a fluid cell c: sum over fluid face neighbours n in
+// the crop of (v_c - v_n).
+__device__ __forceinline__ float crop_stencil(const float* v, const float* fl, size_t i, int x, int y, int z, int nx,
+                                              int ny, int nz) {
+  const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+  const float vc = v[i];
+  float acc = 0.f;
+  auto nb = [&](bool inside, size_t j) {
+    if (inside && (!fl || fl[j] > 0.5f)) acc += vc - v[j];
+  };
+  nb(x > 0, i - 1);
+  nb(x < nx - 1, i + 1);
+  nb(y > 0, i - sy);
+  nb(y < ny - 1, i + sy);
+  nb(z > 0, i - sz);
+  nb(z < nz - 1, i + sz);
+  return acc;
+}
+
+__global__ void k_residual(const float* __restrict__ y, Fields f, const float* __restrict__ inv, int nx, int ny,
+                           int nz, int n, float inv_h2, float* __restrict__ r, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const size_t vox = (size_t)nx * ny * nz, total = vox * n;
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / vox);
+    const size_t v = i - (size_t)s * vox;
+    const int x = (int)(v % nx), yy = (int)((v / nx) % ny), z = (int)(v / ((size_t)nx * ny));
+    const float* fl = f.fluid ? field(f.fluid, f, s) : nullptr;
+    const bool inner = x > 0 && x < nx - 1 && yy > 0 && yy < ny - 1 && z > 0 && z < nz - 1;
+    float rv = 0.f;
+    if (inner && (!fl || fl[v] > 0.5f)) {
+      rv = crop_stencil(y + (size_t)s * vox, fl, v, x, yy, z, nx, ny, nz) * inv_h2 - field(f.b, f, s)[v] * inv[s];
+      acc = fmaf(rv, rv, acc);
+    }
+    r[i] = rv;
+  }
+  const double t = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void k_apply_crop(const float* __restrict__ r, Fields f, int nx, int ny, int nz, int n, float inv_h2,
+                             uint4* __restrict__ gy) {
+  const size_t vox = (size_t)nx * ny * nz, total = vox * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / vox);
+    const size_t v = i - (size_t)s * vox;
+    const int x = (int)(v % nx), yy = (int)((v / nx) % ny), z = (int)(v / ((size_t)nx * ny));
+    const float* fl = f.fluid ? field(f.fluid, f, s) : nullptr;
+    float g = 0.f;
+    if (!fl || fl[v] > 0.5f) g = crop_stencil(r + (size_t)s * vox, fl, v, x, yy, z, nx, ny, nz) * inv_h2;
+    gy[2 * i] = make_uint4(pack_bf2(g, 0.f), 0u, 0u, 0u);
+    gy[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 // fwd operand: [t][ci / 8][co][ci % 8]; data-gradient operand: tap 26 - t,
@@ -488,8 +580,8 @@ __global__ void k_adam_pack(float* __restrict__ w, float* __restrict__ m, float*
   float wv = w[e];
   if (update) {
     const float g = grad[e];
-    const float mv = a.b1 * m[e] + (1.f - a.b1) * g;
-    const float vv = a.b2 * v[e] + (1.f - a.b2) * g * g;
+    const float mv = a.b1 * m[e] + a.omb1 * g;
+    const float vv = a.b2 * v[e] + a.omb2 * g * g;
     m[e] = mv;
     v[e] = vv;
     wv -= a.lr * (mv * a.c1) / (sqrtf(vv * a.c2) + a.eps);
@@ -514,8 +606,8 @@ __global__ void k_pack_layer(const float* __restrict__ w, __nv_bfloat16* __restr
 }
 
 __global__ void k_crop(const float* __restrict__ b, const float* __restrict__ p_next, const float* __restrict__ dp,
-                       long long fx, long long fy, long long cx, long long cy, long long cz, long long ox,
-                       long long oy, long long oz, float* __restrict__ dst) {
+                       const uint8_t* __restrict__ solid, long long fx, long long fy, long long cx, long long cy,
+                       long long cz, long long ox, long long oy, long long oz, float* __restrict__ dst) {
   const size_t vox = (size_t)(cx * cy * cz);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x) {
     const long long x = (long long)(i % cx), y = (long long)((i / cx) % cy), z = (long long)(i / (cx * cy));
@@ -524,6 +616,7 @@ __global__ void k_crop(const float* __restrict__ b, const float* __restrict__ p_
     dst[i] = b[src];
     dst[vox + i] = p_next[src] - d;
     dst[2 * vox + i] = d;
+    dst[3 * vox + i] = (solid && solid[src]) ? 0.f : 1.f;
   }
 }
 
@@ -553,21 +646,27 @@ bool encode_act(CUtensorMap* m, const void* base, const Dims& d, int bx, int by,
   cuuint64_t gdim[5] = {(cuuint64_t)kC, (cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)d.n};
   cuuint64_t gstride[4] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * 2 * d.nx, (cuuint64_t)kC * 2 * d.nx * d.ny,
                            (cuuint64_t)kC * 2 * d.nx * d.ny * d.nz};
-  cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  cuuint32_t box[5] = {(cuuint32_t)kC, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), gdim, gstride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename K>
+static int grid_for(K kernel, int threads, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return -1;
+  return occupancy_blocks(kernel, threads, smem);
 }
 
 template <int EPI>
 static cudaError_t conv_epi(const CUtensorMap& map, const void* wpack, const ConvArgs& a, cudaStream_t s) {
   static int grid_cache = 0;
-  if (!grid_cache) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
-    if (e != cudaSuccess) return e;
-    grid_cache = occupancy_blocks(k_conv<EPI>, kConvThreads, kConvSmem);
-  }
+  if (!grid_cache) grid_cache = grid_for(k_conv<EPI>, kConvThreads, kConvSmem);
+  if (grid_cache < 0) return cudaErrorInvalidValue;
   const long long g = a.ntiles < grid_cache ? a.ntiles : grid_cache;
   k_conv<EPI><<<(unsigned)(g > 0 ? g : 1), kConvThreads, kConvSmem, s>>>(map, (const uint4*)wpack, a);
   return cudaGetLastError();
@@ -604,11 +703,8 @@ cudaError_t launch_conv(const void* x, const void* wpack, void* out, int epi, co
 cudaError_t launch_wgrad(const void* x, const void* g, float* partials, int max_blocks, int* nblocks, const Dims& d,
                          int* err, cudaStream_t s) {
   static int grid_cache = 0;
-  if (!grid_cache) {
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
-    if (e != cudaSuccess) return e;
-    grid_cache = occupancy_blocks(k_wgrad, kWgThreads, kWgSmem);
-  }
+  if (!grid_cache) grid_cache = grid_for(k_wgrad, kWgThreads, kWgSmem);
+  if (grid_cache < 0) return cudaErrorInvalidValue;
   CUtensorMap xm, gm;
   if (!encode_act(&xm, x, d, kWTX + 2, kWTY + 2, kWTZ + 2) || !encode_act(&gm, g, d, kWTX, kWTY, kWTZ))
     return cudaErrorInvalidValue;
@@ -668,11 +764,11 @@ cudaError_t launch_poolbwd_add_mask(const void* gskip, const void* gcoarse, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_rms(const Fields& f, const Dims& d, float* partials, float* rms, float* inv_rms,
+cudaError_t launch_rms(const Fields& f, const Dims& d, bool pooled, float* partials, float* rms, float* inv_rms,
                        cudaStream_t s) {
   const int nblk = 64;
   k_sumsq_b<<<dim3(nblk, d.n), 256, 0, s>>>(f, d.vox(), partials);
-  k_rms_final<<<(d.n + 127) / 128, 128, 0, s>>>(partials, nblk, d.vox(), d.n, rms, inv_rms);
+  k_rms_final<<<(d.n + 127) / 128, 128, 0, s>>>(partials, nblk, d.vox(), d.n, pooled ? 1 : 0, rms, inv_rms);
   return cudaGetLastError();
 }
 
@@ -685,7 +781,16 @@ cudaError_t launch_loss_grad(const float* y, const Fields& f, const float* inv_r
                              double* loss, const Dims& d, cudaStream_t s) {
   const int g = grid_1d(d.vox() * d.n);
   k_loss_grad<<<g, 256, 0, s>>>(y, f, inv_rms, (uint4*)gy, d.vox(), d.n, partials);
-  k_sum_partials<<<1, 256, 0, s>>>(partials, g, loss);
+  k_sum_partials<<<1, 256, 0, s>>>(partials, g, 0.5 / ((double)d.vox() * d.n), loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_loss_grad(const float* y, const Fields& f, const float* inv_rms, float inv_h2, float* r,
+                                      void* gy, double* partials, double* loss, const Dims& d, cudaStream_t s) {
+  const int g = grid_1d(d.vox() * d.n);
+  k_residual<<<g, 256, 0, s>>>(y, f, inv_rms, d.nx, d.ny, d.nz, d.n, inv_h2, r, partials);
+  k_sum_partials<<<1, 256, 0, s>>>(partials, g, 0.5 / ((double)d.vox() * d.n), loss);
+  k_apply_crop<<<g, 256, 0, s>>>(r, f, d.nx, d.ny, d.nz, d.n, inv_h2, (uint4*)gy);
   return cudaGetLastError();
 }
 
@@ -696,10 +801,11 @@ cudaError_t launch_adam_pack(float* w, float* m, float* v, const float* grad, bo
   return cudaGetLastError();
 }
 
-cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, const int64_t full[3],
-                        const int64_t crop[3], const int64_t origin[3], float* dst, cudaStream_t s) {
+cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, const uint8_t* solid,
+                        const int64_t full[3], const int64_t crop[3], const int64_t origin[3], float* dst,
+                        cudaStream_t s) {
   const size_t vox = (size_t)(crop[0] * crop[1] * crop[2]);
-  k_crop<<<grid_1d(vox), 256, 0, s>>>(b, p_next, dp, full[0], full[1], crop[0], crop[1], crop[2], origin[0],
+  k_crop<<<grid_1d(vox), 256, 0, s>>>(b, p_next, dp, solid, full[0], full[1], crop[0], crop[1], crop[2], origin[0],
                                       origin[1], origin[2], dst);
   return cudaGetLastError();
 }

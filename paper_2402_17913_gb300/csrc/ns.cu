@@ -340,6 +340,16 @@ mg_status ns_create(ns_handle* out, int dim, const int64_t cells[3], double h, c
 
 mg_handle ns_pressure_handle(ns_handle ns) { return ns ? ns->mg : nullptr; }
 
+mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp) {
+  if (!ns || !d_b || !d_dp) {
+    set_error("ns_last_fields: NULL argument");
+    return MG_ERR_INVALID;
+  }
+  *d_b = ns->b;
+  *d_dp = ns->dp;
+  return MG_OK;
+}
+
 mg_status ns_set_guess(ns_handle ns, gn_handle g) {
   if (!ns) {
     set_error("ns_set_guess: NULL handle");

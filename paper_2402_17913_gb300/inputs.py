@@ -199,9 +199,12 @@ def ns_initial_velocity(cells, seed, u_inflow=1.0, noise=0.01):
 
 
 def convnet_weights(seed, layer_io=((2, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16),
-                                    (16, 1))):
+                                    (16, 1)), last_scale=1.0):
     """He-normal initial weights of the 9 bias-free 3x3x3 convolutions of the
     initial-guess network: arrays [27, Cin, Cout] with std sqrt(2 / (27 Cin))
-    (seeded; drawn layer by layer)."""
+    (seeded; drawn layer by layer); the last layer is multiplied by
+    last_scale (a small value starts training from a near-zero guess)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    return [rng.standard_normal((27, ci, co)) * np.sqrt(2.0 / (27 * ci)) for ci, co in layer_io]
+    w = [rng.standard_normal((27, ci, co)) * np.sqrt(2.0 / (27 * ci)) for ci, co in layer_io]
+    w[-1] = w[-1] * last_scale
+    return w

@@ -27,12 +27,13 @@ EXPORTED = [
     "mg_create_batched", "mg_solve_batched", "mg_tune_batched", "mg_batched_config", "mg_destroy_batched",
     "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
-    "gn_destroy", "ns_set_guess",
+    "gn_destroy", "ns_set_guess", "ns_last_fields",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
 GN_WGRAD_SCRATCH_MIN = 256 + 27 * 16 * 16 * 4
 GN_CONV_F32, GN_CONV_RELU, GN_CONV_DGRAD, GN_CONV_LIN = range(4)
+GN_LOSS_L2, GN_LOSS_RESIDUAL = 0, 1
 KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
                   "init_finish", "momentum", "divergence", "correct"]
 
@@ -124,17 +125,19 @@ def load():
         "gn_set_weights": (ctypes.c_int, [_vp, _vp]),
         "gn_get_weights": (ctypes.c_int, [_vp, _vp]),
         "gn_forward": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3, _vp, _vp, _vp, _vp]),
-        "gn_gradients": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3, _vp, _vp, _vp,
-                                        ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+        "gn_gradients": (ctypes.c_int, [_vp, ctypes.c_int, _i64_3, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
         "gn_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
-        "gn_dataset_reserve": (ctypes.c_int, [_vp, _i64_3, ctypes.c_int]),
-        "gn_dataset_add": (ctypes.c_int, [_vp, _i64_3, _vp, _vp, _vp, _vp]),
+        "gn_dataset_reserve": (ctypes.c_int, [_vp, _i64_3, ctypes.c_int, ctypes.c_double]),
+        "gn_dataset_add": (ctypes.c_int, [_vp, _i64_3, _vp, _vp, _vp, _vp, _vp]),
         "gn_dataset_size": (ctypes.c_int, [_vp]),
-        "gn_train": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, _vp, _vp]),
+        "gn_train": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                    _vp, _vp]),
         "gn_conv3d": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, ctypes.c_int, _vp, _vp]),
         "gn_conv3d_wgrad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, _vp, ctypes.c_size_t, _vp]),
         "gn_destroy": (ctypes.c_int, [_vp]),
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
+        "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -403,13 +406,13 @@ def gn_forward(g, cells, b, p, out, n=1, stream=None):
     _check(load().gn_forward(g, n, _i64_3(*cells), ptr(b), ptr(p), ptr(out), stream_ptr(stream)))
 
 
-def gn_gradients(g, cells, b, p, t, n=1, stream=None):
+def gn_gradients(g, cells, b, p, t=None, n=1, fluid=None, loss_mode=GN_LOSS_L2, h=1.0, stream=None):
     """Returns (loss, flat float32 gradient)."""
     import numpy as np
     loss = ctypes.c_double()
     grad = np.empty(GN_NUM_WEIGHTS, np.float32)
-    _check(load().gn_gradients(g, n, _i64_3(*cells), ptr(b), ptr(p), ptr(t), ctypes.byref(loss), grad.ctypes.data,
-                               stream_ptr(stream)))
+    _check(load().gn_gradients(g, n, _i64_3(*cells), ptr(b), ptr(p), ptr(t), ptr(fluid), loss_mode, h,
+                               ctypes.byref(loss), grad.ctypes.data, stream_ptr(stream)))
     return loss.value, grad
 
 
@@ -418,23 +421,23 @@ def gn_adam_step(g, lr, grad=None, stream=None):
     _check(load().gn_adam_step(g, None if gp is None else gp.ctypes.data, lr, stream_ptr(stream)))
 
 
-def gn_dataset_reserve(g, crop, capacity):
-    _check(load().gn_dataset_reserve(g, _i64_3(*crop), capacity))
+def gn_dataset_reserve(g, crop, capacity, h=1.0):
+    _check(load().gn_dataset_reserve(g, _i64_3(*crop), capacity, h))
 
 
-def gn_dataset_add(g, cells, b, p_next, dp, stream=None):
-    _check(load().gn_dataset_add(g, _i64_3(*cells), ptr(b), ptr(p_next), ptr(dp), stream_ptr(stream)))
+def gn_dataset_add(g, cells, b, p_next, dp, solid=None, stream=None):
+    _check(load().gn_dataset_add(g, _i64_3(*cells), ptr(b), ptr(p_next), ptr(dp), ptr(solid), stream_ptr(stream)))
 
 
 def gn_dataset_size(g):
     return load().gn_dataset_size(g)
 
 
-def gn_train(g, steps, batch, seed, lr, stream=None):
+def gn_train(g, steps, batch, seed, lr, loss_mode=GN_LOSS_RESIDUAL, stream=None):
     """Returns the per-step losses (numpy float64)."""
     import numpy as np
     losses = np.zeros(steps, np.float64)
-    _check(load().gn_train(g, steps, batch, seed, lr, losses.ctypes.data, stream_ptr(stream)))
+    _check(load().gn_train(g, steps, batch, seed, lr, loss_mode, losses.ctypes.data, stream_ptr(stream)))
     return losses
 
 
@@ -461,3 +464,10 @@ def gn_destroy(g):
 
 def ns_set_guess(ns, g):
     _check(load().ns_set_guess(ns, g))
+
+
+def ns_last_fields(ns):
+    """(b, dp) device pointers (ints) of the last ns_step."""
+    b, dp = _vp(), _vp()
+    _check(load().ns_last_fields(ns, ctypes.byref(b), ctypes.byref(dp)))
+    return b.value, dp.value

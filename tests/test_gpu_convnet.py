@@ -193,14 +193,44 @@ def test_gradients_match_oracle(L):
     x, rms = C.net_input(b, p)
     y, cache = C.forward(W, x)
     tgt = (t / rms)[None]
-    ref_loss = C.loss(y, tgt)
-    ref = C.backward(W, cache, y, tgt)
+    check_grads(L, loss, grad, C.loss(y, tgt), C.backward(W, cache, y, tgt))
+
+
+def check_grads(L, loss, grad, ref_loss, ref, min_cos=0.999, max_rel=5e-2):
+    # BF16 activations and gradients: each rounding perturbs by <= 2^-9
+    # relative, the backward pass rounds 9 times, and ReLU masks flip on
+    # near-zero pre-activations; the first layer collects all of it
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
     got = L.gn_unflatten(grad)
     for k in range(9):
         cos = float(np.sum(got[k] * ref[k]) / (np.linalg.norm(got[k]) * np.linalg.norm(ref[k])))
-        assert cos >= 0.999, (k, cos)
-        assert rel_l2(got[k], ref[k]) <= 5e-2, (k, rel_l2(got[k], ref[k]))
+        assert cos >= min_cos, (k, cos)
+        assert rel_l2(got[k], ref[k]) <= max_rel, (k, rel_l2(got[k], ref[k]))
+
+
+def test_residual_loss_gradients_match_oracle(L):
+    cells = (32, 16, 16)
+    shape = (16, 16, 32)
+    W = bf16_weights(16)
+    b, p, _ = fields(shape, 50)
+    solid = I.block_mask(cells, (12, 8, 8), 6)
+    fluid = (~solid).astype(np.float64)
+    b = b * fluid
+    h = 0.5
+    g = L.gn_create(W)
+    try:
+        dev = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (b, p, fluid)]
+        loss, grad = L.gn_gradients(g, cells, dev[0], dev[1], fluid=dev[2], loss_mode=L.GN_LOSS_RESIDUAL, h=h)
+    finally:
+        L.gn_destroy(g)
+    x, rms = C.net_input(b, p)
+    y, cache = C.forward(W, x)
+    ref_loss, gy = C.residual_loss(y[0], b / rms, fluid > 0, h)
+    # the output gradient A_crop r is oscillatory: pooled to the coarse
+    # levels it largely cancels, so the coarse layers' weight gradients are
+    # small sums of large BF16-rounded terms (relative error amplified by
+    # sum|terms| / |sum|)
+    check_grads(L, loss, grad, ref_loss, C.backward_from(W, cache, gy[None]), min_cos=0.995, max_rel=0.1)
 
 
 def test_adam_steps_match_oracle(L):

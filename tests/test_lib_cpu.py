@@ -90,10 +90,10 @@ def test_guess_network_rejects_invalid_arguments(lib):
     out = vp()
     assert lib.gn_create(ctypes.byref(out), None, None) == L.MG_ERR_INVALID and not out.value
     assert lib.gn_forward(None, 1, cells, None, None, None, None) == L.MG_ERR_INVALID
-    assert lib.gn_gradients(None, 1, cells, None, None, None, None, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_gradients(None, 1, cells, None, None, None, None, 0, 1.0, None, None, None) == L.MG_ERR_INVALID
     assert lib.gn_conv3d(None, None, None, 1, cells, 0, None, None) == L.MG_ERR_INVALID
     assert lib.gn_conv3d_wgrad(None, None, None, 1, cells, None, 0, None) == L.MG_ERR_INVALID
-    assert lib.gn_train(None, 1, 1, 0, 1e-3, None, None) == L.MG_ERR_INVALID
+    assert lib.gn_train(None, 1, 1, 0, 1e-3, 1, None, None) == L.MG_ERR_INVALID
     assert lib.gn_dataset_size(None) == 0
     assert lib.ns_set_guess(None, None) == L.MG_ERR_INVALID
     assert "ns_set_guess" in L.last_error()
