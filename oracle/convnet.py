@@ -172,12 +172,19 @@ class Adam:
         return out
 
 
+def rms_or_one(a):
+    r = float(np.sqrt(np.mean(a * a)))
+    return r if r > 0 else 1.0
+
+
 def net_input(b, p):
-    """The network's input: (b, p^n) scaled by 1 / rms(b) -> [2, Z, Y, X];
-    returns (x, rms).  The output is multiplied back by rms."""
-    rms = float(np.sqrt(np.mean(b * b)))
-    s = 1.0 / rms if rms > 0 else 1.0
-    return np.stack([b * s, p * s]), (rms if rms > 0 else 1.0)
+    """The network's input: (b / rms(b), p^n / rms(p^n)) -> [2, Z, Y, X];
+    returns (x, rms(b)).  The output is multiplied back by rms(b), so the
+    guess is positively homogeneous in b (as the solution of A dp = b is
+    linear in b) while p^n enters by its shape only (its scale relative to
+    b spans orders of magnitude between flows and time steps)."""
+    rb, rp = rms_or_one(b), rms_or_one(p)
+    return np.stack([b / rb, p / rp]), rb
 
 
 def crop_operator(v, fluid, h=1.0):

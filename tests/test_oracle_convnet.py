@@ -136,3 +136,21 @@ def test_backward_from_matches_backward_for_the_l2_loss():
     b = C.backward_from(W, c, (y - t) / y.size)
     for k in range(C.NLAYERS):
         assert np.array_equal(a[k], b[k])
+
+
+def test_net_input_scales_each_field_by_its_own_rms():
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal((8, 8, 8)) * 3.0
+    p = rng.standard_normal((8, 8, 8)) * 1e6
+    x, rb = C.net_input(b, p)
+    assert np.isclose(rb, np.sqrt(np.mean(b * b)), rtol=1e-14)
+    assert np.isclose(np.sqrt(np.mean(x[0] ** 2)), 1.0, rtol=1e-13)
+    assert np.isclose(np.sqrt(np.mean(x[1] ** 2)), 1.0, rtol=1e-13)
+    # the guess rms(b) * net(x) is positively homogeneous in b and ignores
+    # the scale of p
+    W = I.convnet_weights(4)
+    y1 = C.forward(W, C.net_input(b, p)[0])[0] * C.net_input(b, p)[1]
+    y2 = C.forward(W, C.net_input(2.0 * b, 7.0 * p)[0])[0] * C.net_input(2.0 * b, 7.0 * p)[1]
+    assert np.allclose(y2, 2.0 * y1, rtol=1e-12)
+    z, rz = C.net_input(np.zeros_like(b), np.zeros_like(p))
+    assert rz == 1.0 and not z.any()
