@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="ns2d", choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--guess", default="zero", choices=["zero", "net"],
+                    help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="run warm-up and timed steps only (for launch-list captures)")
@@ -232,6 +235,73 @@ def recorded_traffic(workload, cls):
 
 
 # ---------------------------------------------------------------------------
+# learned initial guess (3D flow): solver pairs from the seeded run, training
+GUESS_PAIRS, GUESS_CROP, GUESS_BATCH, GUESS_LR = 5000, 64, 8, 1e-3
+
+
+def train_guess(L, ns, wl, u, v, w, p, solid_t, train_steps):
+    """Runs the seeded flow from its initial state, cutting each step's
+    (b, p^n, dp) into 64^3 crops until GUESS_PAIRS are stored, then trains
+    the network on them with the residual loss; returns a dict with the
+    handle and the training record."""
+    import torch
+    g = L.gn_create(I.convnet_weights(0, last_scale=1e-3))
+    L.gn_dataset_reserve(g, (GUESS_CROP,) * 3, GUESS_PAIRS, 1.0)
+    t0 = time.perf_counter()
+    gen_steps = 0
+    while L.gn_dataset_size(g) < GUESS_PAIRS:
+        L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL, stats=False)
+        b_ptr, dp_ptr = L.ns_last_fields(ns)
+        L.gn_dataset_add(g, wl.cells, b_ptr, p, dp_ptr, solid_t)
+        gen_steps += 1
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = L.gn_train(g, train_steps, GUESS_BATCH, 1, GUESS_LR, L.GN_LOSS_RESIDUAL)
+    t2 = time.perf_counter()
+    L.ns_set_guess(ns, g)
+    tail = float(np.mean(losses[-50:]))
+    return {"handle": g, "pairs": GUESS_PAIRS, "crop": GUESS_CROP, "generation_steps": gen_steps,
+            "generation_s": round(t1 - t0, 2), "train_steps": train_steps, "batch": GUESS_BATCH, "lr": GUESS_LR,
+            "train_s": round(t2 - t1, 2), "loss_first50": float(np.mean(losses[:50])), "loss_last50": tail,
+            "train_relres_last50": float(np.sqrt(2.0 * tail))}
+
+
+def guess_report(L, guess, step_stats, ns, wl, u, v, w, p, compare=5):
+    """Guess quality over the timed steps, then the same states solved from
+    the guess and from zero side by side (iterations and device ms)."""
+    import torch
+    rel = [s["guess_relres"] for s in step_stats]
+    rej = sum(s["guess_rejected"] for s in step_stats)
+    pairs = []
+    for _ in range(compare):
+        state = [t.clone() for t in (u, v, w, p)]
+        L.ns_set_guess(ns, guess["handle"])
+        _, sg = L.ns_step(ns, state[0], state[1], state[2], state[3], wl.dt, wl.nu, wl.uin, TOL)
+        L.ns_set_guess(ns, None)
+        _, sz = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)
+        pairs.append((sg["iters"], sz["iters"], sg["ms"], sz["ms"], sg["guess_relres"]))
+    # the network's own forward time at this size
+    out = torch.empty_like(p)
+    b_ptr, _ = L.ns_last_fields(ns)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    L.gn_forward(guess["handle"], wl.cells, b_ptr, p, out)
+    e0.record()
+    for _ in range(5):
+        L.gn_forward(guess["handle"], wl.cells, b_ptr, p, out)
+    e1.record()
+    torch.cuda.synchronize()
+    L.gn_destroy(guess["handle"])
+    a = np.array(pairs)
+    rec = {k: v_ for k, v_ in guess.items() if k != "handle"}
+    rec.update({"guess_relres_mean": float(np.mean(rel)) if rel else None,
+                "guess_relres_max": float(np.max(rel)) if rel else None, "rejected_steps": int(rej),
+                "forward_ms": round(e0.elapsed_time(e1) / 5, 4),
+                "same_state": {"steps": compare, "iters_guess": float(a[:, 0].mean()),
+                               "iters_zero": float(a[:, 1].mean()),
+                               "solve_ms_guess": float(a[:, 2].mean()), "solve_ms_zero": float(a[:, 3].mean())}})
+    return rec
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2402_17913_gb300 import build, lib as L
@@ -240,6 +310,7 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
     dev = torch.device("cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    guess = None
 
     if args.config in ("ns2d", "ns3d"):
         wl = NS2D() if args.config == "ns2d" else NS3D()
@@ -252,6 +323,12 @@ def run_gpu(args, rank, world):
         u, v, p = fields[0], fields[1], fields[-1]
         w = fields[2] if wl.dim == 3 else None
         stats = []
+        guess = None
+        if args.config == "ns3d" and args.guess == "net":
+            guess = train_guess(L, ns, wl, u, v, w, p, solid_t, args.train_steps)
+            # the timed run continues from the state the pairs came from
+            for d, t in zip(host, fields):
+                d.copy_(t)
 
         def step():
             _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)
@@ -320,6 +397,7 @@ def run_gpu(args, rank, world):
         step()
     torch.cuda.synchronize()
     stats.clear()
+    gn_launches0 = L.gn_kernel_launches()
     dist_barrier(world)
     # ---- timed: device-resident inputs, L2 flushed between steps
     launches0 = L.mg_kernel_launches(mg) if mg else 0
@@ -337,6 +415,7 @@ def run_gpu(args, rank, world):
     times = [a.elapsed_time(b) for a, b in ev]
     # the batched solve is one persistent kernel per solve (one graph launch)
     launches = (L.mg_kernel_launches(mg) - launches0) if mg else args.steps
+    launches += L.gn_kernel_launches() - gn_launches0
     step_stats = list(stats)
     total_ms = sum(times)
     total_ms = dist_max(total_ms, world)
@@ -357,6 +436,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append(t0.elapsed_time(t1))
     e2e_total = dist_max(sum(e2e_ms), world)
+    guess_rec = guess_report(L, guess, step_stats, ns, wl, u, v, w, p) if guess else None
     peak, peak_kind = measured_peak()
     if args.config == "batched":
         # the whole solve is one persistent kernel: its algorithmic bytes are
@@ -411,6 +491,7 @@ def run_gpu(args, rank, world):
         "e2e": {"value": wl.units * args.steps * world / (e2e_total * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "roofline": roofline,
+        "guess": guess_rec,
         "solve": {"cg_iters_mean": statistics.mean(its) if its else None,
                   "relres_max": max(s["relres"] for s in step_stats) if step_stats else None,
                   "outer_mean": statistics.mean(s["outer"] for s in step_stats) if step_stats else None},

@@ -318,7 +318,7 @@ mg_status mg_destroy_batched(mg_batch b);
  * tolerance and, in ns_step, restarts from zero when the guess is worse than
  * zero (relres > 1).  Sec. 1 and Sec. 5 of the paper motivate coupling such
  * networks with the solver; the network and its training are defined here:
- *   x = (b, p^n) / rms(b)             (2 channels, rms over the sample)
+ *   x = (b / rms(b), p^n / rms(p^n))  (2 channels, rms over the sample)
  *   e1 = R(W1 x), e1 = R(W2 e1)        full resolution
  *   e2 = R(W3 P e1), e2 = R(W4 e2)     half           (P = 2x2x2 average)
  *   e3 = R(W5 P e2), e3 = R(W6 e3)     quarter
@@ -358,10 +358,10 @@ mg_status mg_destroy_batched(mg_batch b);
  *   d_solid = uint8 solid flags of the grid or NULL.
  * gn_train: `steps` Adam steps on minibatches of `batch` crops drawn with a
  *   seeded generator under loss_mode, the learning rate decaying from lr to
- *   lr / 20 along a half cosine; a minibatch's inputs are scaled by the rms
- *   of b over the whole minibatch (so the residual loss is the minibatch's
- *   squared relative residual / 2); h_losses (nullable) receives each
- *   step's loss; synchronises.
+ *   lr / 20 along a half cosine; a minibatch's inputs b and p^n are scaled
+ *   by their rms over the whole minibatch (so the residual loss is the
+ *   minibatch's squared relative residual / 2); h_losses (nullable)
+ *   receives each step's loss; synchronises.
  * gn_conv3d (building block): one convolution of a BF16 NDHWC16 tensor
  *   d_x ([n][z][y][x][16]) with FP32 weights d_w ([27][16][16], device).
  *   mode GN_CONV_F32: d_y = float [..][16]; GN_CONV_RELU: bf16 ReLU output;
@@ -402,6 +402,8 @@ mg_status gn_conv3d(const void* d_x, const float* d_w, void* d_y, int n, const i
                     void* d_scratch, void* stream);
 mg_status gn_conv3d_wgrad(const void* d_x, const void* d_g, float* d_dw, int n, const int64_t cells[3],
                           void* d_scratch, size_t scratch_bytes, void* stream);
+/* Kernels the guess network's calls have launched so far (process-wide). */
+int64_t gn_kernel_launches(void);
 mg_status gn_destroy(gn_handle g);
 mg_status ns_set_guess(ns_handle ns, gn_handle g);
 /* Device pointers (owned by ns, valid until the next ns_step) of the last

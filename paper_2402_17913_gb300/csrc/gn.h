@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "npmg_internal.cuh"
 
 namespace npmg {
@@ -39,6 +41,9 @@ enum Epi {
   kEpiMask = 3,   // out: bf16 [vox][16] = acc where mask[vox][c] > 0, else 0
   kEpiOut0 = 4,   // out: float [vox] = acc[channel 0] * scale[n]
 };
+
+// Kernels launched by this file's launchers (process-wide).
+extern std::atomic<int64_t> g_launches;
 
 struct Dims {
   int n, nx, ny, nz;
@@ -80,10 +85,12 @@ struct Fields {
   size_t stride;       // floats between samples
   const int* idx;      // device sample indices or nullptr
 };
-// rms[n] = rms of b over sample n (pooled: over all samples), 1 when b == 0;
-// inv_rms = 1 / rms.
+// rms[s] = rms of b over sample s, rms[n + s] = rms of p (pooled: over all
+// samples), 1 for an all-zero field; inv_rms = 1 / rms.  partials: 2 * n *
+// 64 floats.
 cudaError_t launch_rms(const Fields& f, const Dims& d, bool pooled, float* partials, float* rms, float* inv_rms,
                        cudaStream_t s);
+// x0 = (b * inv_rms[s], p * inv_rms[n + s], 0, ...)
 cudaError_t launch_pack_input(const Fields& f, const float* inv_rms, void* x0, const Dims& d, cudaStream_t s);
 // L2 loss: gy[vox][16] = (y - t * inv_rms) in channel 0, 0 elsewhere;
 // *loss = 0.5 * mean of the squares (float64, fixed-order sum).

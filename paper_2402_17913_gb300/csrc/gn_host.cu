@@ -51,8 +51,8 @@ struct Work {
     for (int l = 0; l < 3; ++l) d[l] = Dims{n, (int)(c[0] >> l), (int)(c[1] >> l), (int)(c[2] >> l)};
     const size_t t[3] = {round256(d[0].vox() * n * 32), round256(d[1].vox() * n * 32), round256(d[2].vox() * n * 32)};
     const int n0 = tr ? 10 : 5, n1 = tr ? 10 : 5, n2 = tr ? 6 : 3;
-    const size_t total = n0 * t[0] + n1 * t[1] + n2 * t[2] + 2 * round256(d[0].vox() * n * 4) + 3 * round256(n * 4) +
-                         round256((size_t)n * kRmsBlocks * 4) + round256(8 * 1024 * 8);
+    const size_t total = n0 * t[0] + n1 * t[1] + n2 * t[2] + 2 * round256(d[0].vox() * n * 4) + 3 * round256(2 * n * 4) +
+                         round256((size_t)2 * n * kRmsBlocks * 4) + round256(8 * 1024 * 8);
     cudaError_t e = cudaMalloc((void**)&pool, total);
     if (e != cudaSuccess) {
       pool = nullptr;
@@ -74,10 +74,10 @@ struct Work {
     }
     y = (float*)take(d[0].vox() * n * 4);
     r = (float*)take(d[0].vox() * n * 4);
-    rms = (float*)take(n * 4);
-    inv = (float*)take(n * 4);
-    take(n * 4);
-    rpart = (float*)take((size_t)n * kRmsBlocks * 4);
+    rms = (float*)take(2 * n * 4);  // b then p
+    inv = (float*)take(2 * n * 4);
+    take(2 * n * 4);
+    rpart = (float*)take((size_t)2 * n * kRmsBlocks * 4);
     lpart = (double*)take(8 * 1024 * 8);
     return cudaSuccess;
   }
@@ -151,8 +151,8 @@ mg_status ensure_work(Work& W, int n, const int64_t c[3], bool train) {
 }
 
 // Forward pass; output channel 0 into `out` scaled by `scale` (per sample,
-// or nullptr for 1).  Inputs are scaled by 1 / rms(b), the rms taken per
-// sample or pooled over the samples.
+// or nullptr for 1).  Inputs are (b / rms(b), p / rms(p)), the rms taken
+// per sample or pooled over the samples.
 mg_status forward(gn_handle_s* g, Work& W, const Fields& f, float* out, const float* scale, bool pooled,
                   cudaStream_t s) {
   const Dims* d = W.d;
@@ -547,6 +547,8 @@ mg_status gn_conv3d_wgrad(const void* d_x, const void* d_g, float* d_dw, int n, 
   }
   return MG_OK;
 }
+
+int64_t gn_kernel_launches(void) { return g_launches.load(); }
 
 mg_status gn_destroy(gn_handle g) {
   if (!g) return MG_OK;

@@ -31,6 +31,8 @@
 // channel group in 8 different bank quads).
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "gn.h"
 #include "tma_host.h"
 #include "umma.cuh"
@@ -452,28 +454,32 @@ __device__ __forceinline__ const float* field(const float* base, const Fields& f
   return base + s * f.stride;
 }
 
-// per-sample sum of squares of b: grid (blocks, n), partials[n * blocks + b]
-__global__ void k_sumsq_b(Fields f, size_t vox, float* __restrict__ partials) {
+// per-sample sums of squares of b (blockIdx.z = 0) and p (= 1): grid
+// (blocks, n, 2), partials[(field * n + sample) * blocks + block]
+__global__ void k_sumsq(Fields f, size_t vox, float* __restrict__ partials) {
   __shared__ double sh[32];
-  const float* b = field(f.b, f, blockIdx.y);
+  const float* a = field(blockIdx.z ? f.p : f.b, f, blockIdx.y);
   float acc = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < vox; i += (size_t)gridDim.x * blockDim.x)
-    acc = fmaf(b[i], b[i], acc);
-  const double s = block_sum((double)acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (float)s;
+    acc = fmaf(a[i], a[i], acc);
+  const double t = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (float)t;
 }
 
+// rms / inverse rms per (field, sample), pooled over the samples if asked;
+// 1 for an all-zero field
 __global__ void k_rms_final(const float* __restrict__ partials, int nblk, size_t vox, int n, int pooled,
                             float* __restrict__ rms, float* __restrict__ inv) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  const int fld = i / n, s = i % n;
   double acc = 0.0;
   const int s0 = pooled ? 0 : s, s1 = pooled ? n : s + 1;
   for (int q = s0; q < s1; ++q)
-    for (int b = 0; b < nblk; ++b) acc += (double)partials[q * nblk + b];
+    for (int b = 0; b < nblk; ++b) acc += (double)partials[(fld * n + q) * nblk + b];
   const double r = sqrt(acc / ((double)vox * (s1 - s0)));
-  rms[s] = r > 0.0 ? (float)r : 1.f;
-  inv[s] = r > 0.0 ? (float)(1.0 / r) : 1.f;
+  rms[i] = r > 0.0 ? (float)r : 1.f;
+  inv[i] = r > 0.0 ? (float)(1.0 / r) : 1.f;
 }
 
 __global__ void k_pack_input(Fields f, const float* __restrict__ inv, uint4* __restrict__ x0, size_t vox, int n) {
@@ -481,8 +487,7 @@ __global__ void k_pack_input(Fields f, const float* __restrict__ inv, uint4* __r
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int s = (int)(i / vox);
     const size_t v = i - (size_t)s * vox;
-    const float q = inv[s];
-    const float bv = field(f.b, f, s)[v] * q, pv = field(f.p, f, s)[v] * q;
+    const float bv = field(f.b, f, s)[v] * inv[s], pv = field(f.p, f, s)[v] * inv[n + s];
     x0[2 * i] = make_uint4(pack_bf2(bv, pv), 0u, 0u, 0u);
     x0[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
   }
@@ -640,6 +645,8 @@ int grid_1d(size_t work, int threads = 256) {
 
 }  // namespace
 
+std::atomic<int64_t> g_launches{0};
+
 bool encode_act(CUtensorMap* m, const void* base, const Dims& d, int bx, int by, int bz) {
   auto fn = (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
   if (!fn || ((uintptr_t)base & 15)) return false;
@@ -669,6 +676,7 @@ static cudaError_t conv_epi(const CUtensorMap& map, const void* wpack, const Con
   if (grid_cache < 0) return cudaErrorInvalidValue;
   const long long g = a.ntiles < grid_cache ? a.ntiles : grid_cache;
   k_conv<EPI><<<(unsigned)(g > 0 ? g : 1), kConvThreads, kConvSmem, s>>>(map, (const uint4*)wpack, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -724,12 +732,14 @@ cudaError_t launch_wgrad(const void* x, const void* g, float* partials, int max_
   if (gsz < 1) gsz = 1;
   *nblocks = (int)gsz;
   k_wgrad<<<(unsigned)gsz, kWgThreads, kWgSmem, s>>>(xm, gm, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad_reduce(const float* partials, int nblocks, float* dw, float scale, bool accumulate,
                                 cudaStream_t s) {
   k_wgrad_reduce<<<(kWElems + 255) / 256, 256, 0, s>>>(partials, nblocks, dw, scale, accumulate ? 1 : 0);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -738,6 +748,7 @@ static Lv lv_of(const Dims& d, int shift) { return Lv{d.nx >> shift, d.ny >> shi
 cudaError_t launch_pool(const void* fine, void* coarse, const Dims& d, cudaStream_t s) {
   const size_t total = d.vox() / 8 * d.n * 2;
   k_pool<<<grid_1d(total), 256, 0, s>>>((const uint4*)fine, (uint4*)coarse, lv_of(d, 0), lv_of(d, 1), total);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -745,6 +756,7 @@ cudaError_t launch_up_add(const void* coarse, const void* fine, void* out, const
   const size_t total = d.vox() * d.n * 2;
   k_up_add<<<grid_1d(total), 256, 0, s>>>((const uint4*)coarse, (const uint4*)fine, (uint4*)out, lv_of(d, 0),
                                           lv_of(d, 1), total);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -753,6 +765,7 @@ cudaError_t launch_upbwd_mask(const void* gfine, const void* act_coarse, void* o
   const size_t total = d.vox() / 8 * d.n * 2;
   k_upbwd_mask<<<grid_1d(total), 256, 0, s>>>((const uint4*)gfine, (const uint4*)act_coarse, (uint4*)out_coarse,
                                               lv_of(d, 0), lv_of(d, 1), total);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -761,19 +774,23 @@ cudaError_t launch_poolbwd_add_mask(const void* gskip, const void* gcoarse, cons
   const size_t total = d.vox() * d.n * 2;
   k_poolbwd_add_mask<<<grid_1d(total), 256, 0, s>>>((const uint4*)gskip, (const uint4*)gcoarse, (const uint4*)act,
                                                     (uint4*)out, lv_of(d, 0), lv_of(d, 1), total);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rms(const Fields& f, const Dims& d, bool pooled, float* partials, float* rms, float* inv_rms,
                        cudaStream_t s) {
   const int nblk = 64;
-  k_sumsq_b<<<dim3(nblk, d.n), 256, 0, s>>>(f, d.vox(), partials);
-  k_rms_final<<<(d.n + 127) / 128, 128, 0, s>>>(partials, nblk, d.vox(), d.n, pooled ? 1 : 0, rms, inv_rms);
+  k_sumsq<<<dim3(nblk, d.n, 2), 256, 0, s>>>(f, d.vox(), partials);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_rms_final<<<(2 * d.n + 127) / 128, 128, 0, s>>>(partials, nblk, d.vox(), d.n, pooled ? 1 : 0, rms, inv_rms);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_input(const Fields& f, const float* inv_rms, void* x0, const Dims& d, cudaStream_t s) {
   k_pack_input<<<grid_1d(d.vox() * d.n), 256, 0, s>>>(f, inv_rms, (uint4*)x0, d.vox(), d.n);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -781,7 +798,9 @@ cudaError_t launch_loss_grad(const float* y, const Fields& f, const float* inv_r
                              double* loss, const Dims& d, cudaStream_t s) {
   const int g = grid_1d(d.vox() * d.n);
   k_loss_grad<<<g, 256, 0, s>>>(y, f, inv_rms, (uint4*)gy, d.vox(), d.n, partials);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sum_partials<<<1, 256, 0, s>>>(partials, g, 0.5 / ((double)d.vox() * d.n), loss);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -789,8 +808,11 @@ cudaError_t launch_residual_loss_grad(const float* y, const Fields& f, const flo
                                       void* gy, double* partials, double* loss, const Dims& d, cudaStream_t s) {
   const int g = grid_1d(d.vox() * d.n);
   k_residual<<<g, 256, 0, s>>>(y, f, inv_rms, d.nx, d.ny, d.nz, d.n, inv_h2, r, partials);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sum_partials<<<1, 256, 0, s>>>(partials, g, 0.5 / ((double)d.vox() * d.n), loss);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   k_apply_crop<<<g, 256, 0, s>>>(r, f, d.nx, d.ny, d.nz, d.n, inv_h2, (uint4*)gy);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -798,6 +820,7 @@ cudaError_t launch_adam_pack(float* w, float* m, float* v, const float* grad, bo
                              void* wd, cudaStream_t s) {
   k_adam_pack<<<(kLayers * kWElems + 255) / 256, 256, 0, s>>>(w, m, v, grad, update ? 1 : 0, a,
                                                               (__nv_bfloat16*)wf, (__nv_bfloat16*)wd);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
@@ -807,11 +830,13 @@ cudaError_t launch_crop(const float* b, const float* p_next, const float* dp, co
   const size_t vox = (size_t)(crop[0] * crop[1] * crop[2]);
   k_crop<<<grid_1d(vox), 256, 0, s>>>(b, p_next, dp, solid, full[0], full[1], crop[0], crop[1], crop[2], origin[0],
                                       origin[1], origin[2], dst);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_layer(const float* w, void* wf, void* wd, cudaStream_t s) {
   k_pack_layer<<<(kWElems + 255) / 256, 256, 0, s>>>(w, (__nv_bfloat16*)wf, (__nv_bfloat16*)wd);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 

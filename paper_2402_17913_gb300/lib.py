@@ -27,7 +27,7 @@ EXPORTED = [
     "mg_create_batched", "mg_solve_batched", "mg_tune_batched", "mg_batched_config", "mg_destroy_batched",
     "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
-    "gn_destroy", "ns_set_guess", "ns_last_fields",
+    "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
@@ -137,6 +137,7 @@ def load():
         "gn_conv3d_wgrad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, _vp, ctypes.c_size_t, _vp]),
         "gn_destroy": (ctypes.c_int, [_vp]),
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
+        "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     }
     for name, (res, args) in sig.items():
@@ -455,6 +456,10 @@ def gn_conv3d_wgrad(x, gr, dw, cells, n=1, scratch_bytes=None, stream=None):
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
     _check(load().gn_conv3d_wgrad(ptr(x), ptr(gr), ptr(dw), n, _i64_3(*cells), ptr(scratch), nbytes,
                                   stream_ptr(stream)))
+
+
+def gn_kernel_launches():
+    return load().gn_kernel_launches()
 
 
 def gn_destroy(g):
