@@ -31,6 +31,7 @@
 // channel group in 8 different bank quads).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "gn.h"
@@ -625,13 +626,25 @@ __global__ void k_crop(const float* __restrict__ b, const float* __restrict__ p_
   }
 }
 
+// Resident blocks of `kernel` on all SMs, from its shared memory (dynamic +
+// static + the per-block reservation), registers and threads.
 template <typename K>
 int occupancy_blocks(K kernel, int threads, size_t smem) {
-  int dev = 0, nsm = 0, occ = 0;
+  int dev = 0, nsm = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
-  return nsm * (occ > 0 ? occ : 1);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return nsm;
+  const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+  int occ = (int)((size_t)smem_sm / per_block);
+  const int regs_block = ((fa.numRegs * 32 + 255) / 256) * 256 * ((threads + 31) / 32);
+  if (regs_block > 0) occ = std::min(occ, regs_sm / regs_block);
+  occ = std::min(occ, thr_sm / threads);
+  return nsm * std::max(occ, 1);
 }
 
 int grid_1d(size_t work, int threads = 256) {
