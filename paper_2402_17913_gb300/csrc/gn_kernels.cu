@@ -8,18 +8,20 @@
 // 8 along y, one z-plane) the 3x3x3 correlation with 16 input and 16 output
 // channels is 27 MMAs of shape M x N x K = 128 x 16 x 16, one per tap t:
 //     D[v][co] += sum_ci X[v + o_t][ci] * W[t][ci][co].
-// A block fetches, by TMA, three copies of its input tile (x shifted by
-// dx = -1, 0, +1), each with a one-voxel halo in y and z, as rows of one
-// voxel's 16 channels (32 bytes) in the 32-byte-swizzled K-major layout that
-// the tensor core reads directly.  The A operand of tap (dz, dy, dx) is then
-// a contiguous 4 KB run of copy dx starting at row (z + dz, y + dy): each
-// descriptor differs only in its start address (a multiple of 512 bytes, so
-// the swizzle phase never shifts), and out-of-range voxels arrive as zeros
-// (the zero padding).  One thread issues the 27 MMAs per z-plane into a
-// TMEM accumulator (128 lanes x 16 FP32 columns) from a table of
-// precomputed descriptors, then, once they are done, the TMA of the block's
-// next tile; the four warps read the accumulator back with tcgen05.ld,
-// apply the epilogue and store 32 bytes per voxel.
+// A block walks a run of z-planes of one 16 x 8 column.  It keeps, for
+// each of three copies of the input (x shifted by dx = -1, 0, +1, with a
+// one-voxel halo in y), a ring of four z-planes fetched by TMA as rows of
+// one voxel's 16 channels (32 bytes) in the 32-byte-swizzled K-major layout
+// that the tensor core reads directly; each step of two output planes
+// fetches only the two planes it adds.  The A operand of tap (dz, dy, dx)
+// is then a contiguous 4 KB run of copy dx starting at line dy + 1 of the
+// ring slot holding plane z + dz: descriptors differ only in their start
+// address (a multiple of 256 bytes, so the swizzle phase never shifts) and
+// take two values per tap as the ring turns; out-of-range voxels arrive as
+// zeros (the zero padding).  One thread issues the 27 MMAs per z-plane into
+// a TMEM accumulator (128 lanes x 16 FP32 columns), then, once they are
+// done, the next fetch; the four warps read the accumulator back with
+// tcgen05.ld, apply the epilogue and store 32 bytes per voxel.
 
 // The data gradient is the same kernel with the mirrored, transposed taps
 // (W'[26 - t][co][ci] = W[t][ci][co]).  The weight gradient
@@ -43,15 +45,19 @@ namespace gn {
 
 namespace {
 
-constexpr int kPlane = (kTZ + 2) * (kTY + 2) * kTX * 32;  // bytes of one staged copy: [z][y][x][16 ch]
-constexpr int kDescOff = 13824;                           // descriptor table after the 13824-byte weights
-constexpr int kAOff = 14592;                              // copies start (256-aligned: the swizzle atom)
-constexpr int kConvSmem = kAOff + 3 * kPlane + 256;       // + alignment slack; 3 blocks fit an SM
+constexpr int kPlaneZ = (kTY + 2) * kTX * 32;               // one z-plane of one copy: [y][x][16 ch]
+constexpr int kRing = kTZ + 2;                               // z-planes kept per copy
+constexpr int kCopy = kRing * kPlaneZ;
+constexpr int kDescOff = 13824;                              // descriptor table after the 13824-byte weights
+constexpr int kDescA = 2 * kTZ * kTaps;                      // A descriptors: [ring phase][zi][tap]
+constexpr int kAOff = 14592;                                 // copies start (256-aligned: the swizzle atom)
+constexpr int kConvSmem = kAOff + 3 * kCopy + 256;           // + alignment slack; 3 blocks fit an SM
 constexpr int kConvThreads = 128;
-constexpr uint32_t kConvCols = 32;                        // TMEM columns (kTZ accumulators of 16, min 32)
+constexpr uint32_t kConvCols = 32;                           // TMEM columns (kTZ accumulators of 16, min 32)
+static_assert(kTZ == 2, "the ring turns by two planes per step");
 static_assert(kTZ * 16 <= (int)kConvCols, "TMEM columns");
-static_assert(kPlane % 256 == 0 && kAOff % 256 == 0, "swizzled TMA destinations stay 256-aligned");
-static_assert(kDescOff + 8 * kTaps * (kTZ + 1) <= kAOff, "descriptor table fits");
+static_assert(kPlaneZ % 256 == 0 && kAOff % 256 == 0, "swizzled TMA destinations stay 256-aligned");
+static_assert(kDescOff + 4 * (kDescA + kTaps) <= kAOff, "descriptor table fits");
 
 constexpr int kXTile = (kWTX + 2) * (kWTY + 2) * (kWTZ + 2) * 32;  // wgrad x tile with halo
 constexpr int kGTile = kWTX * kWTY * kWTZ * 32;
@@ -65,8 +71,9 @@ __device__ __forceinline__ uint32_t sw32(uint32_t v, uint32_t g) { return v * 32
 
 struct ConvArgs {
   int nx, ny, nz, nn;
-  int tx, ty, tz;
-  long long ntiles;
+  int tx, ty;
+  int zc, nzc;  // planes per z-run (a multiple of kTZ) and runs per column
+  long long nitems;
   void* out;
   const __nv_bfloat16* mask;
   const float* scale;
@@ -117,9 +124,11 @@ __device__ __forceinline__ void store_epi(const ConvArgs& a, size_t vox, int n, 
   }
 }
 
-// Persistent implicit-GEMM convolution (see the file comment).
+// Persistent implicit-GEMM convolution (see the file comment).  map4 /
+// map2 fetch four / two z-planes of the three copies.
 template <int EPI>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ CUtensorMap xmap,
+__global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ CUtensorMap map4,
+                                                     const __grid_constant__ CUtensorMap map2,
                                                      const uint4* __restrict__ wpack, ConvArgs a) {
   extern __shared__ unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar_ld;
@@ -127,22 +136,24 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
   __shared__ uint32_t tmem_slot;
   const uint32_t pad = (256u - (smem_u32(dsm) & 255u)) & 255u;
   unsigned char* sW = dsm + pad;
-  uint64_t* sD = reinterpret_cast<uint64_t*>(sW + kDescOff);  // [zi][t] A descriptors, then [t] B
+  uint32_t* sD = reinterpret_cast<uint32_t*>(sW + kDescOff);  // low words: [ph][zi][t] A, then [t] B
   unsigned char* sA = sW + kAOff;
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t sW_u = smem_u32(sW), sA_u = smem_u32(sA);
 
   for (int i = tid; i < kPackBytes / 16; i += kConvThreads) reinterpret_cast<uint4*>(sW)[i] = wpack[i];
-  for (int i = tid; i < kTaps * (kTZ + 1); i += kConvThreads) {
-    const int t = i % kTaps, zi = i / kTaps;
-    if (zi < kTZ) {
+  for (int i = tid; i < kDescA + kTaps; i += kConvThreads) {
+    if (i < kDescA) {
+      const int t = i % kTaps, zi = (i / kTaps) % kTZ, ph = i / (kTaps * kTZ);
       const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-      sD[i] = smem_desc_sw32(sA_u + (uint32_t)((dx + 1) * kPlane + ((zi + dz + 1) * (kTY + 2) + (dy + 1)) * kTX * 32),
-                             256);
+      const int slot = (2 * ph + zi + dz + 1) & (kRing - 1);
+      sD[i] = (uint32_t)smem_desc_sw32(sA_u + (uint32_t)((dx + 1) * kCopy + slot * kPlaneZ + (dy + 1) * kTX * 32),
+                                       256);
     } else {
-      sD[i] = smem_desc(sW_u + (uint32_t)(t * 512), 256, 128);
+      sD[i] = (uint32_t)smem_desc(sW_u + (uint32_t)((i - kDescA) * 512), 256, 128);
     }
   }
+  const uint32_t hiA = (uint32_t)(smem_desc_sw32(0, 256) >> 32), hiB = (uint32_t)(smem_desc(0, 256, 128) >> 32);
   fence_proxy_async_smem();
   if (tid == 0) {
     mbar_init(&bar_ld, 1);
@@ -159,75 +170,103 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = idesc_bf16(128, 16);
 
-  auto origin = [&](long long tile, int& x0, int& y0, int& z0, int& n) {
-    long long r = tile;
+  // item = (x tile, y tile, z run, sample)
+  auto origin = [&](long long item, int& x0, int& y0, int& zr0, int& n) {
+    long long r = item;
     x0 = (int)(r % a.tx) * kTX;
     r /= a.tx;
     y0 = (int)(r % a.ty) * kTY;
     r /= a.ty;
-    z0 = (int)(r % a.tz) * kTZ;
-    n = (int)(r / a.tz);
+    zr0 = (int)(r % a.nzc) * a.zc;
+    n = (int)(r / a.nzc);
   };
-  auto fetch = [&](long long tile) {
-    int x0, y0, z0, n;
-    origin(tile, x0, y0, z0, n);
-    mbar_arrive_expect_tx(&bar_ld, 3 * kPlane);
+  // four planes z0 - 1 .. z0 + 2 (ring slots 0..3) or the two planes z0 + 1,
+  // z0 + 2 of the tile starting at z0 (ring slots `slot`, `slot` + 1)
+  auto fetch = [&](bool full, int x0, int y0, int z0, int n, int slot) {
+    mbar_arrive_expect_tx(&bar_ld, (full ? kRing : 2) * 3 * kPlaneZ);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tma_load_5d(sA + c * kPlane, &xmap, &bar_ld, 0, x0 + c - 1, y0 - 1, z0 - 1, n);
+    for (int c = 0; c < 3; ++c) {
+      if (full)
+        tma_load_5d(sA + c * kCopy, &map4, &bar_ld, 0, x0 + c - 1, y0 - 1, z0 - 1, n);
+      else
+        tma_load_5d(sA + c * kCopy + slot * kPlaneZ, &map2, &bar_ld, 0, x0 + c - 1, y0 - 1, z0 + 1, n);
+    }
   };
 
   uint32_t phase = 0;
-  long long tile = blockIdx.x;
-  if (tid == 0 && tile < a.ntiles) fetch(tile);
-  bool pending = tile < a.ntiles;
-  for (; tile < a.ntiles; tile += gridDim.x) {
-    const bool ok_ld = mbar_wait_bounded(&bar_ld, phase);
-    if (__syncthreads_or(!ok_ld)) {
-      // a tile that never lands: report it, give the copy in flight a
-      // bounded wait, and stop (no MMA reads it)
-      if (tid == 0) atomicExch(a.err, 1);
-      mbar_wait_bounded(&bar_ld, phase);
-      pending = false;
-      break;
-    }
-    pending = false;
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll 1
-      for (int zi = 0; zi < kTZ; ++zi) {
-#pragma unroll
-        for (int t = 0; t < kTaps; ++t)
-          umma_bf16(tmem + (uint32_t)(zi * 16), sD[zi * kTaps + t], sD[kTZ * kTaps + t], idesc, t > 0 ? 1u : 0u);
-      }
-      umma_commit(&bar_mma);
-    }
-    const bool ok_mma = mbar_wait_bounded(&bar_mma, phase);
-    if (__syncthreads_or(!ok_mma)) {
-      if (tid == 0) atomicExch(a.err, 2);
-      mbar_wait_bounded(&bar_mma, phase);
-      break;
-    }
-    tc_fence_after();
-    // the copies are free: prefetch the next tile under the epilogue
-    const long long next = tile + gridDim.x;
-    if (tid == 0 && next < a.ntiles) fetch(next);
-    pending = next < a.ntiles;
-    int x0, y0, z0, n;
-    origin(tile, x0, y0, z0, n);
-    const int row = tid;  // TMEM lane = M row = thread (warp w reads lanes 32w .. 32w + 31)
-    const int x = x0 + (row & 15), y = y0 + (row >> 4);
-#pragma unroll
-    for (int zi = 0; zi < kTZ; ++zi) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zi * 16), v);
-      const int z = z0 + zi;
-      if (x < a.nx && y < a.ny && z < a.nz) store_epi<EPI>(a, (((size_t)n * a.nz + z) * a.ny + y) * a.nx + x, n, v);
-    }
-    tc_fence_before();
-    __syncthreads();
-    phase ^= 1;
+  long long item = blockIdx.x;
+  bool pending = false;
+  if (tid == 0 && item < a.nitems) {
+    int x0, y0, zr0, n;
+    origin(item, x0, y0, zr0, n);
+    fetch(true, x0, y0, zr0, n, 0);
   }
-  // a prefetch still in flight after an early exit: bounded wait before the
+  pending = item < a.nitems;
+  bool stop = false;
+  for (; item < a.nitems && !stop; item += gridDim.x) {
+    int x0, y0, zr0, n;
+    origin(item, x0, y0, zr0, n);
+    const int zend = min(zr0 + a.zc, a.nz);
+    for (int z0 = zr0, j = 0; z0 < zend; z0 += kTZ, ++j) {
+      const int ph = j & 1;
+      const bool ok_ld = mbar_wait_bounded(&bar_ld, phase);
+      if (__syncthreads_or(!ok_ld)) {
+        // a tile that never lands: report it, give the copy in flight a
+        // bounded wait, and stop (no MMA reads it)
+        if (tid == 0) atomicExch(a.err, 1);
+        mbar_wait_bounded(&bar_ld, phase);
+        pending = false;
+        stop = true;
+        break;
+      }
+      pending = false;
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int zi = 0; zi < kTZ; ++zi) {
+          const uint32_t* dA = sD + (ph * kTZ + zi) * kTaps;
+#pragma unroll
+          for (int t = 0; t < kTaps; ++t)
+            umma_bf16(tmem + (uint32_t)(zi * 16), ((uint64_t)hiA << 32) | dA[t],
+                      ((uint64_t)hiB << 32) | sD[kDescA + t], idesc, t > 0 ? 1u : 0u);
+        }
+        umma_commit(&bar_mma);
+      }
+      const bool ok_mma = mbar_wait_bounded(&bar_mma, phase);
+      if (__syncthreads_or(!ok_mma)) {
+        if (tid == 0) atomicExch(a.err, 2);
+        mbar_wait_bounded(&bar_mma, phase);
+        stop = true;
+        break;
+      }
+      tc_fence_after();
+      // the planes this tile alone needed are free: fetch the next ones
+      // (the next tile of this run, else the first tile of the next item)
+      if (z0 + kTZ < zend) {
+        if (tid == 0) fetch(false, x0, y0, z0 + kTZ, n, (2 * (ph ^ 1) + 2) & (kRing - 1));
+        pending = true;
+      } else if (item + gridDim.x < a.nitems) {
+        int x1, y1, zr1, n1;
+        origin(item + gridDim.x, x1, y1, zr1, n1);
+        if (tid == 0) fetch(true, x1, y1, zr1, n1, 0);
+        pending = true;
+      }
+      const int row = tid;  // TMEM lane = M row = thread (warp w reads lanes 32w .. 32w + 31)
+      const int x = x0 + (row & 15), y = y0 + (row >> 4);
+#pragma unroll
+      for (int zi = 0; zi < kTZ; ++zi) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zi * 16), v);
+        const int z = z0 + zi;
+        if (x < a.nx && y < a.ny && z < a.nz)
+          store_epi<EPI>(a, (((size_t)n * a.nz + z) * a.ny + y) * a.nx + x, n, v);
+      }
+      tc_fence_before();
+      __syncthreads();
+      phase ^= 1;
+    }
+  }
+  // a fetch still in flight after an early exit: bounded wait before the
   // block's shared memory goes away
   if (pending) mbar_wait_bounded(&bar_ld, phase ^ 1);
   tc_fence_before();
@@ -683,12 +722,21 @@ static int grid_for(K kernel, int threads, int smem) {
 }
 
 template <int EPI>
-static cudaError_t conv_epi(const CUtensorMap& map, const void* wpack, const ConvArgs& a, cudaStream_t s) {
+static cudaError_t conv_epi(const CUtensorMap& m4, const CUtensorMap& m2, const void* wpack, ConvArgs a,
+                            cudaStream_t s) {
   static int grid_cache = 0;
   if (!grid_cache) grid_cache = grid_for(k_conv<EPI>, kConvThreads, kConvSmem);
   if (grid_cache < 0) return cudaErrorInvalidValue;
-  const long long g = a.ntiles < grid_cache ? a.ntiles : grid_cache;
-  k_conv<EPI><<<(unsigned)(g > 0 ? g : 1), kConvThreads, kConvSmem, s>>>(map, (const uint4*)wpack, a);
+  // z-runs: long enough to amortise the four-plane start, short enough for
+  // about three items per resident block
+  const long long columns = (long long)a.tx * a.ty * a.nn;
+  long long zc = (a.nz * columns + 3LL * grid_cache - 1) / (3LL * grid_cache);
+  zc = std::max(2LL, std::min(32LL, (zc + 1) / 2 * 2));
+  a.zc = (int)zc;
+  a.nzc = (int)((a.nz + zc - 1) / zc);
+  a.nitems = columns * a.nzc;
+  const long long g = a.nitems < grid_cache ? a.nitems : grid_cache;
+  k_conv<EPI><<<(unsigned)(g > 0 ? g : 1), kConvThreads, kConvSmem, s>>>(m4, m2, (const uint4*)wpack, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
@@ -696,8 +744,9 @@ static cudaError_t conv_epi(const CUtensorMap& map, const void* wpack, const Con
 cudaError_t launch_conv(const void* x, const void* wpack, void* out, int epi, const void* mask, const float* scale,
                         const Dims& d, int* err, cudaStream_t s) {
   if (d.n <= 0 || d.vox() == 0) return cudaSuccess;
-  CUtensorMap map;
-  if (!encode_act(&map, x, d, kTX, kTY + 2, kTZ + 2)) return cudaErrorInvalidValue;
+  CUtensorMap m4, m2;
+  if (!encode_act(&m4, x, d, kTX, kTY + 2, kRing) || !encode_act(&m2, x, d, kTX, kTY + 2, 2))
+    return cudaErrorInvalidValue;
   ConvArgs a;
   a.nx = d.nx;
   a.ny = d.ny;
@@ -705,18 +754,18 @@ cudaError_t launch_conv(const void* x, const void* wpack, void* out, int epi, co
   a.nn = d.n;
   a.tx = (d.nx + kTX - 1) / kTX;
   a.ty = (d.ny + kTY - 1) / kTY;
-  a.tz = (d.nz + kTZ - 1) / kTZ;
-  a.ntiles = (long long)a.tx * a.ty * a.tz * d.n;
+  a.zc = a.nzc = 0;
+  a.nitems = 0;
   a.out = out;
   a.mask = (const __nv_bfloat16*)mask;
   a.scale = scale;
   a.err = err;
   switch (epi) {
-    case kEpiF32: return conv_epi<kEpiF32>(map, wpack, a, s);
-    case kEpiRelu: return conv_epi<kEpiRelu>(map, wpack, a, s);
-    case kEpiLin: return conv_epi<kEpiLin>(map, wpack, a, s);
-    case kEpiMask: return conv_epi<kEpiMask>(map, wpack, a, s);
-    case kEpiOut0: return conv_epi<kEpiOut0>(map, wpack, a, s);
+    case kEpiF32: return conv_epi<kEpiF32>(m4, m2, wpack, a, s);
+    case kEpiRelu: return conv_epi<kEpiRelu>(m4, m2, wpack, a, s);
+    case kEpiLin: return conv_epi<kEpiLin>(m4, m2, wpack, a, s);
+    case kEpiMask: return conv_epi<kEpiMask>(m4, m2, wpack, a, s);
+    case kEpiOut0: return conv_epi<kEpiOut0>(m4, m2, wpack, a, s);
   }
   return cudaErrorInvalidValue;
 }
