@@ -32,6 +32,17 @@ cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* x
 
 template <int DIM, typename T, bool MASKED>
 cudaError_t prepare_level_kernels(int pre, int post);
+
+// 3D level kernels streamed along z (two sweeps; mg_stream3d.cu).
+bool stream3d_eligible(int dim, int pre, int post, const LevelDev& L);
+template <typename T, bool MASKED>
+cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega,
+                           const SolveState* st, cudaStream_t s);
+template <typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
+                         float sc, SolveState* st, double* partials, cudaStream_t s);
+template <typename T, bool MASKED>
+cudaError_t prepare_s3_kernels();
 template <typename T>
 cudaError_t prepare_coarse(size_t smem_bytes);
 

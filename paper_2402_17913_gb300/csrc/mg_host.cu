@@ -104,6 +104,8 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     const bool tma = k == 0 ? tma0 : h->tma_ok[k];
     if (tma)
       e = launch_down_tma<T, M>(k == 0 ? m0 : h->tmaps[k], h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
+    else if (DIM == 3 && h->s3_ok[k])
+      e = launch_down_s3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
     else
       e = launch_down<DIM, T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], o.pre, om, st, s);
     if (e != cudaSuccess) return e;
@@ -126,6 +128,11 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
         e = launch_up_tma<T, M, true>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
       else
         e = launch_up_tma<T, M, false>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
+    } else if (DIM == 3 && h->s3_ok[k]) {
+      if (k == 0 && st)
+        e = launch_up_s3<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+      else
+        e = launch_up_s3<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
     } else if (k == 0 && st)
       e = launch_up<DIM, T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], o.post, om, sc, st, h->partials, s);
     else
@@ -550,6 +557,9 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     cudaError_t e = prepare_level_kernels<DIM, T, M>(o.pre, o.post);
     if (e == cudaSuccess) e = prepare_coarse<T>(h->ca_smem);
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
+    if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
+    for (int k = 0; k < h->kc; ++k)
+      h->s3_ok[k] = getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
       h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&

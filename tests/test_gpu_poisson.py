@@ -38,6 +38,7 @@ CASES = [
     ((48, 96), (1, 0, 1, 1), 0.08),        # ragged tiles along x, mixed BCs, masked
     ((32, 32, 32), (0,) * 6, 0.0),
     ((16, 24, 40), (1, 0, 1, 1, 0, 1), 0.06),
+    ((40, 40, 136), (0, 1, 0, 0, 1, 0), 0.05),  # several x/y tiles and z-runs, ragged tails in x and y
 ]
 
 
