@@ -25,79 +25,85 @@ namespace npmg {
 namespace {
 
 constexpr int SX = 64, SY = 16;             // output cells of a block per plane
-constexpr int RX = SX + 4, RY = SY + 4;     // region with a 2-cell halo
-constexpr int RN = RX * RY;                 // 1360
-constexpr int QX = SX + 2, QY = SY + 2;     // second-stage region (1-cell halo)
-constexpr int QN = QX * QY;                 // 1188
-constexpr int TN = SX * SY;                 // 1024
-constexpr int NT = 256;                     // threads
-constexpr int LPT = (RN + NT - 1) / NT;     // region cells loaded per thread (6)
+constexpr int RX = SX + 4, RY = SY + 4;     // region with a 2-cell halo (68 x 20)
+constexpr int RN = RX * RY;
+constexpr int TN = SX * SY;
+constexpr int BY = 4;                        // thread rows: RX x BY working threads
+constexpr int NW = RX * BY;                  // 272 working threads
+constexpr int NT = 288;                      // block: 9 full warps (the last 16 threads only sync and reduce)
+constexpr int KA = RY / BY;                  // region rows per thread (5)
+static_assert(RY % BY == 0 && SY % BY == 0, "rows split evenly");
 
-struct Geo {
-  int x0, y0, z0, z1;  // output column origin and z-run [z0, z1)
+// Per-thread geometry: the thread owns region column tx (global x = gx) and
+// rows ty, ty + 4, ...; xs / dxx are its x validity and x part of the
+// unmasked diagonal.
+struct Col {
+  int tx, ty, gx, z0, z1, y0;
+  bool xs, on;  // on: a working thread
+  float dxx;
 };
 
-__device__ __forceinline__ Geo geo_of(const LevelDev& L, int zr) {
-  Geo g;
-  g.x0 = blockIdx.x * SX;
-  g.y0 = blockIdx.y * SY;
-  g.z0 = blockIdx.z * zr;
-  g.z1 = min(g.z0 + zr, L.nz);
-  return g;
+__device__ __forceinline__ Col col_of(const LevelDev& L, int zr) {
+  Col c;
+  c.on = threadIdx.x < NW;
+  c.tx = c.on ? (int)threadIdx.x % RX : 0;
+  c.ty = c.on ? (int)threadIdx.x / RX : 0;
+  c.gx = blockIdx.x * SX - 2 + c.tx;
+  c.y0 = blockIdx.y * SY;
+  c.z0 = blockIdx.z * zr;
+  c.z1 = min(c.z0 + zr, L.nz);
+  c.xs = c.on && c.gx >= 0 && c.gx < L.nx;
+  c.dxx = L.wx * (float)axis_count(c.gx, L.nx, L.bcD, 0);
+  return c;
 }
 
-// Registers holding one plane of the region for this thread.
-template <typename T>
+// One plane of this thread's region cells in registers.
 struct PlaneRegs {
-  float a[LPT];      // b (down) or x + s P e (up)
-  float bb[LPT];     // b (up only)
-  uint8_t m[LPT];
+  float a[KA];   // b (down) or x + s P e (up)
+  float bb[KA];  // b (up only)
+  uint8_t m[KA];
 };
 
-// Global loads of plane p (down leg: b and the cell bytes).
 template <typename T, bool MASKED>
-__device__ __forceinline__ void fetch_down(const LevelDev& L, const Geo& g, int p, const T* __restrict__ b,
-                                           PlaneRegs<T>& r) {
+__device__ __forceinline__ void fetch_down(const LevelDev& L, const Col& c, int p, const T* __restrict__ b,
+                                           PlaneRegs& r) {
+  const bool zin = p >= 0 && p < L.nz;
+  const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
 #pragma unroll
-  for (int k = 0; k < LPT; ++k) {
-    const int i = threadIdx.x + k * NT;
+  for (int k = 0; k < KA; ++k) {
+    const int gy = c.y0 - 2 + c.ty + BY * k;
     r.a[k] = 0.f;
     r.m[k] = 0;
-    if (i < RN && p >= 0 && p < L.nz) {
-      const int gx = g.x0 - 2 + i % RX, gy = g.y0 - 2 + i / RX;
-      if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-        const size_t gi = gidx(L, gx, gy, p);
-        const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
-        r.m[k] = m;
-        if (m) r.a[k] = ld(b, gi);
-      }
+    if (zin && c.xs && gy >= 0 && gy < L.ny) {
+      const size_t gi = base + (size_t)gy * L.nx + c.gx;
+      const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
+      r.m[k] = m;
+      if (m) r.a[k] = ld(b, gi);
     }
   }
 }
 
-// Global loads of plane p (up leg: x + s e_coarse, b, the cell bytes).
 template <typename T, bool MASKED>
-__device__ __forceinline__ void fetch_up(const LevelDev& L, const Geo& g, int p, const T* __restrict__ b,
+__device__ __forceinline__ void fetch_up(const LevelDev& L, const Col& c, int p, const T* __restrict__ b,
                                          const T* __restrict__ xin, const T* __restrict__ e, float s,
-                                         PlaneRegs<T>& r) {
-  const int cnx = L.nx / 2, cny = L.ny / 2;
+                                         PlaneRegs& r) {
+  const bool zin = p >= 0 && p < L.nz;
+  const int cnx = L.nx >> 1, cny = L.ny >> 1;
+  const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
+  const size_t cbase = (size_t)(zin ? p >> 1 : 0) * cny * cnx + (c.gx >> 1);
 #pragma unroll
-  for (int k = 0; k < LPT; ++k) {
-    const int i = threadIdx.x + k * NT;
+  for (int k = 0; k < KA; ++k) {
+    const int gy = c.y0 - 2 + c.ty + BY * k;
     r.a[k] = 0.f;
     r.bb[k] = 0.f;
     r.m[k] = 0;
-    if (i < RN && p >= 0 && p < L.nz) {
-      const int gx = g.x0 - 2 + i % RX, gy = g.y0 - 2 + i / RX;
-      if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-        const size_t gi = gidx(L, gx, gy, p);
-        const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
-        r.m[k] = m;
-        if (m) {
-          const size_t ci = ((size_t)(p >> 1) * cny + (gy >> 1)) * cnx + (gx >> 1);
-          r.a[k] = ld(xin, gi) + s * ld(e, ci);
-          r.bb[k] = ld(b, gi);
-        }
+    if (zin && c.xs && gy >= 0 && gy < L.ny) {
+      const size_t gi = base + (size_t)gy * L.nx + c.gx;
+      const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
+      r.m[k] = m;
+      if (m) {
+        r.a[k] = ld(xin, gi) + s * ld(e, cbase + (size_t)(gy >> 1) * cnx);
+        r.bb[k] = ld(b, gi);
       }
     }
   }
@@ -105,18 +111,31 @@ __device__ __forceinline__ void fetch_up(const LevelDev& L, const Geo& g, int p,
 
 __device__ __forceinline__ int slot3(int p) { return (p + 3) % 3; }  // p >= -2
 
-// One weighted-Jacobi update at region index i of plane q from the ring of
-// iterates X (planes q-1, q, q+1 in slots), b and the diagonal.
-__device__ __forceinline__ float jacobi_at(const LevelDev& L, const float* Xm, const float* Xc, const float* Xp,
-                                           float bv, float d, float wd, int i) {
-  const float xc = Xc[i];
-  const float nb = L.wx * (Xc[i - 1] + Xc[i + 1]) + L.wy * (Xc[i - RX] + Xc[i + RX]) + L.wz * (Xm[i] + Xp[i]);
-  return xc + wd * (bv - (d * xc - nb));
+// omega / d through the hardware reciprocal (a few ulps from a division;
+// the level kernels' results are compared to the oracle at 1e-5)
+__device__ __forceinline__ float omega_over(float omega, float d) { return omega * __frcp_rn(d); }
+
+// Diagonal of region row k of plane p for this thread (0 off the fluid).
+template <bool MASKED>
+__device__ __forceinline__ float diag_k(const LevelDev& L, const Col& c, int k, uint8_t m, float dz) {
+  if (!m) return 0.f;
+  if (MASKED) return L.wx * (float)(m & 3) + L.wy * (float)((m >> 2) & 3) + L.wz * (float)((m >> 4) & 3);
+  const int gy = c.y0 - 2 + c.ty + BY * k;
+  return c.dxx + L.wy * (float)axis_count(gy, L.ny, L.bcD, 2) + dz;
 }
 
-// omega / d as omega times the correctly rounded reciprocal (one rounding
-// more than a division; the sweeps' results move by at most an ulp)
-__device__ __forceinline__ float omega_over(float omega, float d) { return omega * __frcp_rn(d); }
+// Weighted neighbour sum at region index i of the middle plane Xc
+// (neighbours in x, y from Xc, in z from Xm / Xp).
+__device__ __forceinline__ float nbsum(const LevelDev& L, const float* Xm, const float* Xc, const float* Xp, int i) {
+  return L.wx * (Xc[i - 1] + Xc[i + 1]) + L.wy * (Xc[i - RX] + Xc[i + RX]) + L.wz * (Xm[i] + Xp[i]);
+}
+
+// b - (d x - nb) at region index i of the middle plane Xc.
+__device__ __forceinline__ float defect(const LevelDev& L, const float* Xm, const float* Xc, const float* Xp,
+                                        float bv, float d, int i) {
+  const float nb = L.wx * (Xc[i - 1] + Xc[i + 1]) + L.wy * (Xc[i - RX] + Xc[i + RX]) + L.wz * (Xm[i] + Xp[i]);
+  return bv - (d * Xc[i] - nb);
+}
 
 }  // namespace
 
@@ -132,70 +151,68 @@ __global__ void __launch_bounds__(NT) k_down_s3(LevelDev L, const T* __restrict_
   float* s1 = sD + 3 * RN;                           // [3][RN] first sweep
   float* s2 = s1 + 3 * RN;                           // [3][RN] second sweep
   float* sR = s2 + 3 * RN;                           // [2][TN] residual
-  const Geo g = geo_of(L, zr);
+  const Col c = col_of(L, zr);
   const int tid = threadIdx.x;
-  PlaneRegs<T> nxt;
-  fetch_down<T, MASKED>(L, g, g.z0 - 2, b, nxt);
-  for (int p = g.z0 - 2; p <= g.z1 + 1; ++p) {
-    // stage A: plane p into the rings; first sweep from zero is pointwise
+  PlaneRegs nxt;
+  fetch_down<T, MASKED>(L, c, c.z0 - 2, b, nxt);
+  for (int p = c.z0 - 2; p <= c.z1 + 1; ++p) {
+    // stage A: plane p into the rings; the first sweep from zero is pointwise
     {
-      const int sl = slot3(p);
+      const int sl = slot3(p) * RN;
+      const float dz = L.wz * (float)axis_count(p, L.nz, L.bcD, 4);
 #pragma unroll
-      for (int k = 0; k < LPT; ++k) {
-        const int i = tid + k * NT;
-        if (i < RN) {
-          const int gx = g.x0 - 2 + i % RX, gy = g.y0 - 2 + i / RX;
-          const float d = nxt.m[k] ? diag_at<3, MASKED>(L, gx, gy, p, nxt.m[k]) : 0.f;
-          sB[sl * RN + i] = nxt.a[k];
-          sD[sl * RN + i] = d;
-          s1[sl * RN + i] = d > 0.f ? omega_over(omega, d) * nxt.a[k] : 0.f;
-        }
+      for (int k = 0; k < KA; ++k) {
+        if (!c.on) break;
+        const int i = (c.ty + BY * k) * RX + c.tx;
+        const float d = diag_k<MASKED>(L, c, k, nxt.m[k], dz);
+        sB[sl + i] = nxt.a[k];
+        sD[sl + i] = d;
+        s1[sl + i] = d > 0.f ? omega_over(omega, d) * nxt.a[k] : 0.f;
       }
     }
-    if (p + 1 <= g.z1 + 1) fetch_down<T, MASKED>(L, g, p + 1, b, nxt);
+    if (p + 1 <= c.z1 + 1) fetch_down<T, MASKED>(L, c, p + 1, b, nxt);
     __syncthreads();
-    // stage B: second sweep on plane q = p - 1 (region less one cell)
+    // stage B: second sweep on plane q = p - 1, region less one cell
     const int q = p - 1;
-    if (q >= g.z0 - 1) {
+    if (q >= c.z0 - 1 && c.on && c.tx >= 1 && c.tx <= RX - 2) {
       const float* Xm = s1 + slot3(q - 1) * RN;
       const float* Xc = s1 + slot3(q) * RN;
       const float* Xp = s1 + slot3(q + 1) * RN;
-      const int sq = slot3(q);
-      for (int j = tid; j < QN; j += NT) {
-        const int i = (1 + j / QX) * RX + 1 + j % QX;
-        const float d = sD[sq * RN + i];
-        s2[sq * RN + i] = d > 0.f ? jacobi_at(L, Xm, Xc, Xp, sB[sq * RN + i], d, omega_over(omega, d), i) : 0.f;
+      const int sq = slot3(q) * RN;
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        const int ly = 1 + c.ty + BY * k;
+        if (ly <= RY - 2) {
+          const int i = ly * RX + c.tx;
+          const float d = sD[sq + i];
+          s2[sq + i] = d > 0.f ? Xc[i] + omega_over(omega, d) * defect(L, Xm, Xc, Xp, sB[sq + i], d, i) : 0.f;
+        }
       }
     }
     __syncthreads();
     // stage C: x and the residual on plane o = p - 2 (the tile)
     const int o = p - 2;
-    if (o >= g.z0 && o < g.z1) {
+    if (o >= c.z0 && o < c.z1 && c.on && c.tx >= 2 && c.tx <= RX - 3) {
       const float* Xm = s2 + slot3(o - 1) * RN;
       const float* Xc = s2 + slot3(o) * RN;
       const float* Xp = s2 + slot3(o + 1) * RN;
-      const int so = slot3(o);
+      const int so = slot3(o) * RN;
       float* R = sR + (o & 1) * TN;
-      for (int c = tid; c < TN; c += NT) {
-        const int lx = 2 + c % SX, ly = 2 + c / SX, i = ly * RX + lx;
-        const int gx = g.x0 + lx - 2, gy = g.y0 + ly - 2;
-        const float d = sD[so * RN + i];
-        const float xc = Xc[i];
-        float r = 0.f;
-        if (d > 0.f) {
-          const float nb =
-              L.wx * (Xc[i - 1] + Xc[i + 1]) + L.wy * (Xc[i - RX] + Xc[i + RX]) + L.wz * (Xm[i] + Xp[i]);
-          r = sB[so * RN + i] - (d * xc - nb);
-        }
-        R[c] = r;
-        if (gx < L.nx && gy < L.ny) x[gidx(L, gx, gy, o)] = cvt<T>(xc);
+      const size_t base = (size_t)o * L.ny * L.nx + c.gx;
+#pragma unroll
+      for (int k = 0; k < SY / BY; ++k) {
+        const int ly = 2 + c.ty + BY * k, i = ly * RX + c.tx;
+        const int gy = c.y0 + ly - 2;
+        const float d = sD[so + i];
+        R[(ly - 2) * SX + c.tx - 2] = d > 0.f ? defect(L, Xm, Xc, Xp, sB[so + i], d, i) : 0.f;
+        if (c.gx < L.nx && gy < L.ny) x[base + (size_t)gy * L.nx] = cvt<T>(Xc[i]);
       }
     }
     __syncthreads();
     // restriction of the plane pair (o - 1, o) when o is odd
-    if (o >= g.z0 && o < g.z1 && (o & 1)) {
-      const int cx = tid % (SX / 2), cy = tid / (SX / 2);  // 32 x 8 coarse cells, one per thread
-      const int gcx = g.x0 / 2 + cx, gcy = g.y0 / 2 + cy;
+    if (o >= c.z0 && o < c.z1 && (o & 1) && tid < (SX / 2) * (SY / 2)) {
+      const int cx = tid % (SX / 2), cy = tid / (SX / 2);
+      const int gcx = blockIdx.x * (SX / 2) + cx, gcy = c.y0 / 2 + cy;
       if (gcx < L.nx / 2 && gcy < L.ny / 2) {
         float sum = 0.f;
 #pragma unroll
@@ -220,58 +237,63 @@ __global__ void __launch_bounds__(NT) k_up_s3(LevelDev L, const T* __restrict__ 
   if (st && st->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sB = reinterpret_cast<float*>(smem_raw);  // [3][RN]
-  float* sD = sB + 3 * RN;                           // [3][RN]
-  float* s0 = sD + 3 * RN;                           // [3][RN] x + s P e
+  float* sW = sB + 3 * RN;                           // [3][RN] omega / d, 0 off the fluid
+  float* s0 = sW + 3 * RN;                           // [3][RN] x + s P e
   float* s1 = s0 + 3 * RN;                           // [3][RN] first sweep
-  const Geo g = geo_of(L, zr);
-  const int tid = threadIdx.x;
+  const Col c = col_of(L, zr);
+  const float keep = 1.f - omega;  // x + (omega/d)(b - d x + nb) = (1 - omega) x + (omega/d)(b + nb)
   float acc = 0.f;
-  PlaneRegs<T> nxt;
-  fetch_up<T, MASKED>(L, g, g.z0 - 2, b, xin, e, s, nxt);
-  for (int p = g.z0 - 2; p <= g.z1 + 1; ++p) {
+  PlaneRegs nxt;
+  fetch_up<T, MASKED>(L, c, c.z0 - 2, b, xin, e, s, nxt);
+  for (int p = c.z0 - 2; p <= c.z1 + 1; ++p) {
     {
-      const int sl = slot3(p);
+      const int sl = slot3(p) * RN;
+      const float dz = L.wz * (float)axis_count(p, L.nz, L.bcD, 4);
 #pragma unroll
-      for (int k = 0; k < LPT; ++k) {
-        const int i = tid + k * NT;
-        if (i < RN) {
-          const int gx = g.x0 - 2 + i % RX, gy = g.y0 - 2 + i / RX;
-          sB[sl * RN + i] = nxt.bb[k];
-          sD[sl * RN + i] = nxt.m[k] ? diag_at<3, MASKED>(L, gx, gy, p, nxt.m[k]) : 0.f;
-          s0[sl * RN + i] = nxt.a[k];
-        }
+      for (int k = 0; k < KA; ++k) {
+        if (!c.on) break;
+        const int i = (c.ty + BY * k) * RX + c.tx;
+        const float d = diag_k<MASKED>(L, c, k, nxt.m[k], dz);
+        sB[sl + i] = nxt.bb[k];
+        sW[sl + i] = d > 0.f ? omega_over(omega, d) : 0.f;
+        s0[sl + i] = nxt.a[k];
       }
     }
-    if (p + 1 <= g.z1 + 1) fetch_up<T, MASKED>(L, g, p + 1, b, xin, e, s, nxt);
+    if (p + 1 <= c.z1 + 1) fetch_up<T, MASKED>(L, c, p + 1, b, xin, e, s, nxt);
     __syncthreads();
     const int q = p - 1;
-    if (q >= g.z0 - 1) {
+    if (q >= c.z0 - 1 && c.on && c.tx >= 1 && c.tx <= RX - 2) {
       const float* Xm = s0 + slot3(q - 1) * RN;
       const float* Xc = s0 + slot3(q) * RN;
       const float* Xp = s0 + slot3(q + 1) * RN;
-      const int sq = slot3(q);
-      for (int j = tid; j < QN; j += NT) {
-        const int i = (1 + j / QX) * RX + 1 + j % QX;
-        const float d = sD[sq * RN + i];
-        s1[sq * RN + i] = d > 0.f ? jacobi_at(L, Xm, Xc, Xp, sB[sq * RN + i], d, omega_over(omega, d), i) : 0.f;
+      const int sq = slot3(q) * RN;
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        const int ly = 1 + c.ty + BY * k;
+        if (ly <= RY - 2) {
+          const int i = ly * RX + c.tx;
+          const float w = sW[sq + i];
+          s1[sq + i] = w > 0.f ? keep * Xc[i] + w * (sB[sq + i] + nbsum(L, Xm, Xc, Xp, i)) : 0.f;
+        }
       }
     }
     __syncthreads();
     const int o = p - 2;
-    if (o >= g.z0 && o < g.z1) {
+    if (o >= c.z0 && o < c.z1 && c.on && c.tx >= 2 && c.tx <= RX - 3 && c.gx < L.nx) {
       const float* Xm = s1 + slot3(o - 1) * RN;
       const float* Xc = s1 + slot3(o) * RN;
       const float* Xp = s1 + slot3(o + 1) * RN;
-      const int so = slot3(o);
-      for (int c = tid; c < TN; c += NT) {
-        const int lx = 2 + c % SX, ly = 2 + c / SX, i = ly * RX + lx;
-        const int gx = g.x0 + lx - 2, gy = g.y0 + ly - 2;
-        if (gx < L.nx && gy < L.ny) {
-          const float d = sD[so * RN + i];
-          const float bv = sB[so * RN + i];
-          const float v = d > 0.f ? jacobi_at(L, Xm, Xc, Xp, bv, d, omega_over(omega, d), i) : 0.f;
+      const int so = slot3(o) * RN;
+      const size_t base = (size_t)o * L.ny * L.nx + c.gx;
+#pragma unroll
+      for (int k = 0; k < SY / BY; ++k) {
+        const int ly = 2 + c.ty + BY * k, i = ly * RX + c.tx;
+        const int gy = c.y0 + ly - 2;
+        if (gy < L.ny) {
+          const float w = sW[so + i], bv = sB[so + i];
+          const float v = w > 0.f ? keep * Xc[i] + w * (bv + nbsum(L, Xm, Xc, Xp, i)) : 0.f;
           const T zt = cvt<T>(v);
-          xout[gidx(L, gx, gy, o)] = zt;
+          xout[base + (size_t)gy * L.nx] = zt;
           if (FINEST) acc = fmaf(bv, ld(&zt, 0), acc);
         }
       }
