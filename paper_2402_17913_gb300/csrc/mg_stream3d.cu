@@ -35,12 +35,14 @@ constexpr int KA = RY / BY;                  // region rows per thread (5)
 static_assert(RY % BY == 0 && SY % BY == 0, "rows split evenly");
 
 // Per-thread geometry: the thread owns region column tx (global x = gx) and
-// rows ty, ty + 4, ...; xs / dxx are its x validity and x part of the
-// unmasked diagonal.
+// rows ty, ty + 4, ...; per row the in-plane offset of the cell (-1 outside
+// the domain), of its coarse parent, and the x + y part of the unmasked
+// diagonal, all fixed for the whole run.
 struct Col {
   int tx, ty, gx, z0, z1, y0;
-  bool xs, on;  // on: a working thread
-  float dxx;
+  bool on;  // a working thread
+  int off[KA], coff[KA];
+  float dxy[KA];
 };
 
 __device__ __forceinline__ Col col_of(const LevelDev& L, int zr) {
@@ -52,8 +54,16 @@ __device__ __forceinline__ Col col_of(const LevelDev& L, int zr) {
   c.y0 = blockIdx.y * SY;
   c.z0 = blockIdx.z * zr;
   c.z1 = min(c.z0 + zr, L.nz);
-  c.xs = c.on && c.gx >= 0 && c.gx < L.nx;
-  c.dxx = L.wx * (float)axis_count(c.gx, L.nx, L.bcD, 0);
+  const bool xs = c.on && c.gx >= 0 && c.gx < L.nx;
+  const float dxx = L.wx * (float)axis_count(c.gx, L.nx, L.bcD, 0);
+#pragma unroll
+  for (int k = 0; k < KA; ++k) {
+    const int gy = c.y0 - 2 + c.ty + BY * k;
+    const bool in = xs && gy >= 0 && gy < L.ny;
+    c.off[k] = in ? gy * L.nx + c.gx : -1;
+    c.coff[k] = in ? (gy >> 1) * (L.nx >> 1) + (c.gx >> 1) : 0;
+    c.dxy[k] = in ? dxx + L.wy * (float)axis_count(gy, L.ny, L.bcD, 2) : 0.f;
+  }
   return c;
 }
 
@@ -69,16 +79,16 @@ __device__ __forceinline__ void fetch_down(const LevelDev& L, const Col& c, int 
                                            PlaneRegs& r) {
   const bool zin = p >= 0 && p < L.nz;
   const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
+  const T* bp = b + base;
+  const uint8_t* mp = MASKED ? L.cell + base : nullptr;
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
-    const int gy = c.y0 - 2 + c.ty + BY * k;
     r.a[k] = 0.f;
     r.m[k] = 0;
-    if (zin && c.xs && gy >= 0 && gy < L.ny) {
-      const size_t gi = base + (size_t)gy * L.nx + c.gx;
-      const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
+    if (zin && c.off[k] >= 0) {
+      const uint8_t m = MASKED ? mp[c.off[k]] : kFluidBit;
       r.m[k] = m;
-      if (m) r.a[k] = ld(b, gi);
+      if (m) r.a[k] = ld(bp, c.off[k]);
     }
   }
 }
@@ -88,22 +98,22 @@ __device__ __forceinline__ void fetch_up(const LevelDev& L, const Col& c, int p,
                                          const T* __restrict__ xin, const T* __restrict__ e, float s,
                                          PlaneRegs& r) {
   const bool zin = p >= 0 && p < L.nz;
-  const int cnx = L.nx >> 1, cny = L.ny >> 1;
   const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
-  const size_t cbase = (size_t)(zin ? p >> 1 : 0) * cny * cnx + (c.gx >> 1);
+  const T* bp = b + base;
+  const T* xp = xin + base;
+  const T* ep = e + (size_t)(zin ? p >> 1 : 0) * (L.ny >> 1) * (L.nx >> 1);
+  const uint8_t* mp = MASKED ? L.cell + base : nullptr;
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
-    const int gy = c.y0 - 2 + c.ty + BY * k;
     r.a[k] = 0.f;
     r.bb[k] = 0.f;
     r.m[k] = 0;
-    if (zin && c.xs && gy >= 0 && gy < L.ny) {
-      const size_t gi = base + (size_t)gy * L.nx + c.gx;
-      const uint8_t m = MASKED ? L.cell[gi] : kFluidBit;
+    if (zin && c.off[k] >= 0) {
+      const uint8_t m = MASKED ? mp[c.off[k]] : kFluidBit;
       r.m[k] = m;
       if (m) {
-        r.a[k] = ld(xin, gi) + s * ld(e, cbase + (size_t)(gy >> 1) * cnx);
-        r.bb[k] = ld(b, gi);
+        r.a[k] = ld(xp, c.off[k]) + s * ld(ep, c.coff[k]);
+        r.bb[k] = ld(bp, c.off[k]);
       }
     }
   }
@@ -111,17 +121,17 @@ __device__ __forceinline__ void fetch_up(const LevelDev& L, const Col& c, int p,
 
 __device__ __forceinline__ int slot3(int p) { return (p + 3) % 3; }  // p >= -2
 
-// omega / d through the hardware reciprocal (a few ulps from a division;
-// the level kernels' results are compared to the oracle at 1e-5)
-__device__ __forceinline__ float omega_over(float omega, float d) { return omega * __frcp_rn(d); }
+// omega / d through the hardware's approximate reciprocal (a couple of ulps
+// from a division; the level kernels are compared to the oracle at 1e-5)
+__device__ __forceinline__ float omega_over(float omega, float d) { return __fdividef(omega, d); }
 
-// Diagonal of region row k of plane p for this thread (0 off the fluid).
+// Diagonal of region row k of plane p for this thread (0 off the fluid);
+// dz is the plane's z part of the unmasked diagonal.
 template <bool MASKED>
 __device__ __forceinline__ float diag_k(const LevelDev& L, const Col& c, int k, uint8_t m, float dz) {
   if (!m) return 0.f;
   if (MASKED) return L.wx * (float)(m & 3) + L.wy * (float)((m >> 2) & 3) + L.wz * (float)((m >> 4) & 3);
-  const int gy = c.y0 - 2 + c.ty + BY * k;
-  return c.dxx + L.wy * (float)axis_count(gy, L.ny, L.bcD, 2) + dz;
+  return c.dxy[k] + dz;
 }
 
 // Weighted neighbour sum at region index i of the middle plane Xc
@@ -141,7 +151,7 @@ __device__ __forceinline__ float defect(const LevelDev& L, const float* Xm, cons
 
 // Down leg: x = two sweeps from zero, bcoarse = R (b - A' x).
 template <typename T, bool MASKED>
-__global__ void __launch_bounds__(NT) k_down_s3(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
+__global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
                                                T* __restrict__ bcoarse, float omega, int zr,
                                                const SolveState* __restrict__ st) {
   if (st && st->inner_done) return;
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_down_s3(LevelDev L, const T* __restrict_
 // Up leg: xout = two sweeps from x + s P e; on the finest level (r, z) and
 // CG's beta.
 template <typename T, bool MASKED, bool FINEST>
-__global__ void __launch_bounds__(NT) k_up_s3(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
+__global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
                                              T* __restrict__ xout, const T* __restrict__ e, float omega, float s,
                                              int zr, SolveState* __restrict__ st, double* __restrict__ partials) {
   if (st && st->inner_done) return;
