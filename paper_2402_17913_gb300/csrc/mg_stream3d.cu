@@ -349,8 +349,8 @@ static int s3_per_sm(size_t smem) {
 }
 
 // z-run length: even, so that the grid is about one wave of resident blocks
-// (0 when the level is too small for runs of at least 8 planes to fill the
-// GPU; the cube-tile kernels take those levels)
+// (0 when the level is too small for runs of at least 4 planes to cover
+// every SM; the cube-tile kernels take those levels)
 static int s3_run(const LevelDev& L, int nsm, int per_sm) {
   const int tiles = ((L.nx + SX - 1) / SX) * ((L.ny + SY - 1) / SY);
   const int resident = nsm * per_sm;
@@ -358,7 +358,7 @@ static int s3_run(const LevelDev& L, int nsm, int per_sm) {
   if (runs < 1) return ((L.nz + 1) / 2) * 2 >= 8 ? ((L.nz + 1) / 2) * 2 : 0;
   int zr = (L.nz + runs - 1) / runs;
   zr = ((zr + 1) / 2) * 2;
-  if (zr < 8 || tiles * ((L.nz + zr - 1) / zr) < nsm) return 0;
+  if (zr < 4 || tiles * ((L.nz + zr - 1) / zr) < nsm) return 0;
   return zr;
 }
 
