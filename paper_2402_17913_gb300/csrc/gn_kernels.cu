@@ -18,9 +18,9 @@
 // ring slot holding plane z + dz: descriptors differ only in their start
 // address (a multiple of 256 bytes, so the swizzle phase never shifts) and
 // take two values per tap as the ring turns; out-of-range voxels arrive as
-// zeros (the zero padding).  One thread issues the 27 MMAs per z-plane into
-// a TMEM accumulator (128 lanes x 16 FP32 columns), then, once they are
-// done, the next fetch; the four warps read the accumulator back with
+// zeros (the zero padding).  Lane 0 of warp zi issues the 27 MMAs of output
+// plane zi into its TMEM accumulator (128 lanes x 16 FP32 columns), then,
+// once they are done, the next fetch; the four warps read the accumulator back with
 // tcgen05.ld, apply the epilogue and store 32 bytes per voxel.
 
 // The data gradient is the same kernel with the mirrored, transposed taps
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
   fence_proxy_async_smem();
   if (tid == 0) {
     mbar_init(&bar_ld, 1);
-    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_mma, kTZ);  // one commit per issuing warp
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -220,16 +220,16 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
         break;
       }
       pending = false;
-      if (tid == 0) {
+      // lane 0 of warp zi issues the 27 MMAs of output plane zi (its own
+      // accumulator columns) and commits them
+      if (warp < kTZ && (tid & 31) == 0) {
         tc_fence_after();
-#pragma unroll 1
-        for (int zi = 0; zi < kTZ; ++zi) {
-          const uint32_t* dA = sD + (ph * kTZ + zi) * kTaps;
+        const int zi = warp;
+        const uint32_t* dA = sD + (ph * kTZ + zi) * kTaps;
 #pragma unroll
-          for (int t = 0; t < kTaps; ++t)
-            umma_bf16(tmem + (uint32_t)(zi * 16), ((uint64_t)hiA << 32) | dA[t],
-                      ((uint64_t)hiB << 32) | sD[kDescA + t], idesc, t > 0 ? 1u : 0u);
-        }
+        for (int t = 0; t < kTaps; ++t)
+          umma_bf16(tmem + (uint32_t)(zi * 16), ((uint64_t)hiA << 32) | dA[t],
+                    ((uint64_t)hiB << 32) | sD[kDescA + t], idesc, t > 0 ? 1u : 0u);
         umma_commit(&bar_mma);
       }
       const bool ok_mma = mbar_wait_bounded(&bar_mma, phase);
