@@ -130,17 +130,20 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3],
                     void* stream);
 
 /*
- * mg_solve: solve A_h x = b until ||b - A_h x||_2 <= rel_tol * ||b||_2, with
- * the residual of the float64 iterate evaluated in float64.
- *   d_b   device float32 right-hand side (values on solid cells ignored).
- *   d_x   device float32: initial guess on entry, solution on exit (the
- *         float64 iterate rounded to float32; fetch the float64 iterate with
- *         mg_get_solution_f64).
+ * mg_solve: solve A_h x = b until ||b - A_h x||_2 <= rel_tol * ||b||_2.  The
+ * iterate is kept in float-float (pairs of floats, about 48 significant
+ * bits) and the refinement residual is evaluated in that precision.
+ *   d_b   device float32 right-hand side (values on solid cells ignored),
+ *         16-byte aligned.
+ *   d_x   device float32, 16-byte aligned: initial guess on entry, solution
+ *         on exit (the iterate rounded to float32 once; fetch the iterate
+ *         as float64 with mg_get_solution_f64).
  *   rel_tol  > 0.
- *   out   host stats or NULL (NULL keeps the call asynchronous).
- * Returns MG_OK, MG_NOT_CONVERGED, MG_DIVERGED, or an error.  The returned
- * status is that of the solve only when out != NULL (otherwise MG_OK once
- * enqueued; the device-side status is then in the next stats read).
+ *   out   host stats or NULL.
+ * Synchronises the stream: the host launches CUDA graphs of 4 CG iterations
+ * and reads the device control block between them.  Returns MG_OK,
+ * MG_NOT_CONVERGED, MG_DIVERGED, or an error (MG_ERR_INVALID for NULL or
+ * misaligned pointers or rel_tol <= 0).
  */
 mg_status mg_solve(mg_handle h, const float* d_b, float* d_x, double rel_tol,
                    void* stream, mg_stats* out);

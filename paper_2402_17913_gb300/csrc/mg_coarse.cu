@@ -1,6 +1,8 @@
 // Coarse levels of the cycle in one thread block, and the set-up kernels.
 #include <math.h>
 
+#include <stdlib.h>
+
 #include "launch.h"
 #include "mg_kernels.cuh"
 #include "tma.cuh"
@@ -52,12 +54,24 @@ size_t coarse_layout(int* off, const LevelDev* lv, int nlev, int dim) {
   return f * sizeof(float);
 }
 
-// First level handled by the single-block kernel: levels of at most 8192
-// cells whose padded arrays fit the block's shared memory.
+// Largest level (cells) the single-block kernel takes: 2048 in 2D and 8192
+// in 3D (measured on GB300: the 2048x1024 flow step is 4% faster when the
+// 128x64 level runs on the tiled kernels, the 256^3 solve is not), or
+// NPMG_COARSE_CELLS (64 .. 8192) to tune it.
+static size_t coarse_cells_limit(int dim) {
+  const char* e = getenv("NPMG_COARSE_CELLS");
+  const long v = e ? atol(e) : 0;
+  if (v >= 64 && v <= 8192) return (size_t)v;
+  return dim == 3 ? 8192 : 2048;
+}
+
+// First level handled by the single-block kernel: levels within the cell
+// limit whose padded arrays fit the block's shared memory.
 int coarse_start_level(const LevelDev* lv, int L, int dim, size_t smem_limit) {
   int kc = L - 1;
   int off[kMaxLevels];
-  while (kc > 0 && (size_t)lv[kc - 1].nx * lv[kc - 1].ny * lv[kc - 1].nz <= 8192 &&
+  const size_t lim = coarse_cells_limit(dim);
+  while (kc > 0 && (size_t)lv[kc - 1].nx * lv[kc - 1].ny * lv[kc - 1].nz <= lim &&
          coarse_layout(off, lv + kc - 1, L - kc + 1, dim) <= smem_limit)
     --kc;
   return kc;
