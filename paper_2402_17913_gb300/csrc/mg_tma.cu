@@ -78,8 +78,33 @@ __device__ __forceinline__ void tma_fail(SolveState* st) {
   }
 }
 
+// Thread layout of the level kernels: 288 threads, the first 272 a 68 x 4
+// grid over the 68-wide region (tile + 2 cells each side): thread (tx, ty)
+// owns region column tx and rows ty, ty + 4, ...; the last 16 threads fill
+// the diagonal tables.
+constexpr int kTmaThreads = 288;
+constexpr int kRX = kTmaTX + 4, kRY = kTmaTY + 4, kRowStep = 4;
+static_assert(kRX * kRowStep + 16 == kTmaThreads, "thread layout");
+
+// d and 1/d of a 2D cell by its link counts (kx + 4 ky, each 0..2): with
+// no division per cell, a sweep is x <- (1 - omega) x + omega D^-1 (b + nb).
+__device__ __forceinline__ void fill_diag_tables(const LevelDev& L, float* dtab, float* itab) {
+  const int j = (int)threadIdx.x - kRX * kRowStep;
+  if (j >= 0 && j < 16) {
+    const int kx = j & 3, ky = j >> 2;
+    const float d = (kx <= 2 && ky <= 2) ? L.wx * (float)kx + L.wy * (float)ky : 0.f;
+    dtab[j] = d;
+    itab[j] = d > 0.f ? 1.f / d : 0.f;
+  }
+}
+
+template <bool MASKED>
+__device__ __forceinline__ int diag_index(const LevelDev& L, uint8_t m, int kxu, int gy) {
+  return MASKED ? (m & 15) : kxu + 4 * axis_count(gy, L.ny, L.bcD, 2);
+}
+
 template <typename T, bool MASKED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kTmaThreads)
 k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap tm, LevelDev L,
            T* __restrict__ x, T* __restrict__ bcoarse, float omega, SolveState* __restrict__ st) {
   if (st && st->inner_done) return;
@@ -91,7 +116,9 @@ k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUten
   float* s1 = reinterpret_cast<float*>(smem + Lo::X1);
   float* s2 = reinterpret_cast<float*>(smem + Lo::X2);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Lo::BAR);
+  __shared__ float dtab[16], itab[16];
   const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * kTmaTY;
+  fill_diag_tables(L, dtab, itab);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -106,21 +133,24 @@ k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUten
     tma_fail(st);
     return;
   }
-  // With D^-1 stored per cell (0 on non-fluid cells), a weighted-Jacobi
-  // sweep is x <- (1 - omega) x + omega D^-1 (b + sum_a w_a (x_- + x_+)):
-  // no division and no branch in the sweeps.
   float* sdg = reinterpret_cast<float*>(smem + Lo::DG);
   float* sid = reinterpret_cast<float*>(smem + Lo::ID);
   const float om1 = 1.f - omega;
+  const int tid = threadIdx.x;
+  const bool on = tid < kRX * kRowStep;
+  const int tx = on ? tid % kRX : 0, ty = on ? tid / kRX : 0;
+  const int gx = x0 - 2 + tx;
+  const bool xin = gx >= 0 && gx < L.nx;
+  const int kxu = MASKED ? 0 : axis_count(gx, L.nx, L.bcD, 0);
   // sweep 1 from zero on the tile + 2: x1 = omega b / d
-  {
-    constexpr int SW = kTmaTX + 4, SH = kTmaTY + 4;
-    for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-      const int ly = i / SW, gx = x0 - 2 + i % SW, gy = y0 - 2 + ly;
-      const int li = ly * G::BW + (gx - x0 + G::MX);
-      const uint8_t m = tma_cell<T, MASKED>(L, sm, x0, gx, gy, ly);
-      const float d = m ? diag_at<2, MASKED>(L, gx, gy, 0, m) : 0.f;
-      const float id = m ? __frcp_rn(d) : 0.f;
+  if (on) {
+#pragma unroll
+    for (int k = 0; k < kRY / kRowStep; ++k) {
+      const int ly = ty + kRowStep * k, gy = y0 - 2 + ly;
+      const int li = ly * G::BW + tx + (G::MX - 2);
+      const uint8_t m = MASKED ? sm[ly * G::BWM + tx + 14] : ((xin && gy >= 0 && gy < L.ny) ? kFluidBit : 0);
+      const int q = diag_index<MASKED>(L, m, kxu, gy);
+      const float d = m ? dtab[q] : 0.f, id = m ? itab[q] : 0.f;
       sdg[li] = d;
       sid[li] = id;
       s1[li] = omega * lds(sb, li) * id;
@@ -128,19 +158,21 @@ k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUten
   }
   __syncthreads();
   // sweep 2 on the tile + 1
-  {
-    constexpr int SW = kTmaTX + 2, SH = kTmaTY + 2;
-    for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-      const int ly = 1 + i / SW, lx = (G::MX - 1) + i % SW;
-      const int li = ly * G::BW + lx;
-      const float nb = L.wx * (s1[li - 1] + s1[li + 1]) + L.wy * (s1[li - G::BW] + s1[li + G::BW]);
-      s2[li] = fmaf(om1, s1[li], omega * sid[li] * (lds(sb, li) + nb));
+  if (on && tx >= 1 && tx <= kRX - 2) {
+#pragma unroll
+    for (int k = 0; k < kRY / kRowStep; ++k) {
+      const int ly = 1 + ty + kRowStep * k;
+      if (ly <= kRY - 2) {
+        const int li = ly * G::BW + tx + (G::MX - 2);
+        const float nb = L.wx * (s1[li - 1] + s1[li + 1]) + L.wy * (s1[li - G::BW] + s1[li + G::BW]);
+        s2[li] = fmaf(om1, s1[li], omega * sid[li] * (lds(sb, li) + nb));
+      }
     }
   }
   __syncthreads();
   // residual on the tile, its 2x2 average, and x: one coarse cell per thread
-  {
-    const int cx = threadIdx.x & 31, cy = threadIdx.x >> 5;  // 32 x 8 coarse cells
+  if (tid < 256) {
+    const int cx = tid & 31, cy = tid >> 5;  // 32 x 8 coarse cells
     const int gcx = (x0 >> 1) + cx, gcy = (y0 >> 1) + cy;
     float sum = 0.f;
     float xo[2][2];
@@ -169,8 +201,8 @@ k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUten
 }
 
 template <typename T, bool MASKED, bool FINEST>
-__global__ void __launch_bounds__(256)
-k_up_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tb,
+__global__ void __launch_bounds__(kTmaThreads)
+k_up_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tb,
          const __grid_constant__ CUtensorMap te, const __grid_constant__ CUtensorMap tm, LevelDev L,
          T* __restrict__ xout, float omega, float s, SolveState* __restrict__ st, double* __restrict__ partials) {
   if (st && st->inner_done) return;
@@ -184,8 +216,10 @@ k_up_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtenso
   float* s0 = reinterpret_cast<float*>(smem + Lo::S0);
   float* s1 = reinterpret_cast<float*>(smem + Lo::S1);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Lo::BAR);
+  __shared__ float dtab[16], itab[16];
   const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * kTmaTY;
   const int ex0 = (x0 >> 1) - G::MX, ey0 = (y0 >> 1) - 1;
+  fill_diag_tables(L, dtab, itab);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -193,7 +227,7 @@ k_up_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtenso
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(bar, (2 * G::NF + G::NE) * sizeof(T) + (MASKED ? G::NM : 0));
-    tma_load_2d(sx, &tx, bar, x0 - G::MX, y0 - kTmaH);
+    tma_load_2d(sx, &tmx, bar, x0 - G::MX, y0 - kTmaH);
     tma_load_2d(sb, &tb, bar, x0 - G::MX, y0 - kTmaH);
     tma_load_2d(se, &te, bar, ex0, ey0);
     if (MASKED) tma_load_2d(sm, &tm, bar, x0 - 16, y0 - kTmaH);
@@ -204,42 +238,55 @@ k_up_tma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtenso
   }
   float* sid = reinterpret_cast<float*>(smem + Lo::ID);
   const float om1 = 1.f - omega;
+  const int tid = threadIdx.x;
+  const bool on = tid < kRX * kRowStep;
+  const int tx = on ? tid % kRX : 0, ty = on ? tid / kRX : 0;
+  const int gx = x0 - 2 + tx;
+  const bool xin = gx >= 0 && gx < L.nx;
+  const int kxu = MASKED ? 0 : axis_count(gx, L.nx, L.bcD, 0);
+  const int lex = (gx >> 1) - ex0;
   // x + s P e and D^-1 on the tile + 2
-  {
-    constexpr int SW = kTmaTX + 4, SH = kTmaTY + 4;
-    for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-      const int ly = i / SW, gx = x0 - 2 + i % SW, gy = y0 - 2 + ly;
-      const int li = ly * G::BW + (gx - x0 + G::MX);
-      const uint8_t m = tma_cell<T, MASKED>(L, sm, x0, gx, gy, ly);
-      const int le = ((gy >> 1) - ey0) * G::BWE + ((gx >> 1) - ex0);
+  if (on) {
+#pragma unroll
+    for (int k = 0; k < kRY / kRowStep; ++k) {
+      const int ly = ty + kRowStep * k, gy = y0 - 2 + ly;
+      const int li = ly * G::BW + tx + (G::MX - 2);
+      const uint8_t m = MASKED ? sm[ly * G::BWM + tx + 14] : ((xin && gy >= 0 && gy < L.ny) ? kFluidBit : 0);
+      const int le = ((gy >> 1) - ey0) * G::BWE + lex;
       s0[li] = m ? lds(sx, li) + s * lds(se, le) : 0.f;
-      sid[li] = m ? __frcp_rn(diag_at<2, MASKED>(L, gx, gy, 0, m)) : 0.f;
+      sid[li] = m ? itab[diag_index<MASKED>(L, m, kxu, gy)] : 0.f;
     }
   }
   __syncthreads();
   // sweep 1 on the tile + 1
-  {
-    constexpr int SW = kTmaTX + 2, SH = kTmaTY + 2;
-    for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-      const int ly = 1 + i / SW, lx = (G::MX - 1) + i % SW;
-      const int li = ly * G::BW + lx;
-      const float nb = L.wx * (s0[li - 1] + s0[li + 1]) + L.wy * (s0[li - G::BW] + s0[li + G::BW]);
-      s1[li] = fmaf(om1, s0[li], omega * sid[li] * (lds(sb, li) + nb));
+  if (on && tx >= 1 && tx <= kRX - 2) {
+#pragma unroll
+    for (int k = 0; k < kRY / kRowStep; ++k) {
+      const int ly = 1 + ty + kRowStep * k;
+      if (ly <= kRY - 2) {
+        const int li = ly * G::BW + tx + (G::MX - 2);
+        const float nb = L.wx * (s0[li - 1] + s0[li + 1]) + L.wy * (s0[li - G::BW] + s0[li + G::BW]);
+        s1[li] = fmaf(om1, s0[li], omega * sid[li] * (lds(sb, li) + nb));
+      }
     }
   }
   __syncthreads();
   // sweep 2 on the tile, straight to global memory
   float acc = 0.f;
-  for (int i = threadIdx.x; i < kTmaTX * kTmaTY; i += blockDim.x) {
-    const int ty = i / kTmaTX, tx = i % kTmaTX, gx = x0 + tx, gy = y0 + ty;
-    if (gx >= L.nx || gy >= L.ny) continue;
-    const int li = (ty + 2) * G::BW + (G::MX + tx);
-    const float nb = L.wx * (s1[li - 1] + s1[li + 1]) + L.wy * (s1[li - G::BW] + s1[li + G::BW]);
-    const float bv = lds(sb, li);
-    const float v = fmaf(om1, s1[li], omega * sid[li] * (bv + nb));
-    const T zt = cvt<T>(v);
-    xout[(size_t)gy * L.nx + gx] = zt;
-    if (FINEST) acc = fmaf(bv, ld(&zt, 0), acc);
+  if (on && tx >= 2 && tx <= kRX - 3 && gx < L.nx) {
+#pragma unroll
+    for (int k = 0; k < kTmaTY / kRowStep; ++k) {
+      const int ly = 2 + ty + kRowStep * k, gy = y0 - 2 + ly;
+      if (gy < L.ny) {
+        const int li = ly * G::BW + tx + (G::MX - 2);
+        const float nb = L.wx * (s1[li - 1] + s1[li + 1]) + L.wy * (s1[li - G::BW] + s1[li + G::BW]);
+        const float bv = lds(sb, li);
+        const float v = fmaf(om1, s1[li], omega * sid[li] * (bv + nb));
+        const T zt = cvt<T>(v);
+        xout[(size_t)gy * L.nx + gx] = zt;
+        if (FINEST) acc = fmaf(bv, ld(&zt, 0), acc);
+      }
+    }
   }
   if (FINEST) {
     double tot;
@@ -321,14 +368,14 @@ static dim3 tma_grid(const LevelDev& L) {
 template <typename T, bool MASKED>
 cudaError_t launch_down_tma(const TmaLevelMaps& m, const LevelDev& L, void* x, void* bcoarse, float omega,
                             SolveState* st, cudaStream_t s) {
-  k_down_tma<T, MASKED><<<tma_grid(L), 256, DownLayout<T>::BYTES, s>>>(m.b, m.m, L, (T*)x, (T*)bcoarse, omega, st);
+  k_down_tma<T, MASKED><<<tma_grid(L), kTmaThreads, DownLayout<T>::BYTES, s>>>(m.b, m.m, L, (T*)x, (T*)bcoarse, omega, st);
   return cudaGetLastError();
 }
 
 template <typename T, bool MASKED, bool FINEST>
 cudaError_t launch_up_tma(const TmaLevelMaps& m, const LevelDev& L, void* xout, float omega, float sc,
                           SolveState* st, double* partials, cudaStream_t s) {
-  k_up_tma<T, MASKED, FINEST><<<tma_grid(L), 256, UpLayout<T>::BYTES, s>>>(m.x, m.b, m.e, m.m, L, (T*)xout, omega,
+  k_up_tma<T, MASKED, FINEST><<<tma_grid(L), kTmaThreads, UpLayout<T>::BYTES, s>>>(m.x, m.b, m.e, m.m, L, (T*)xout, omega,
                                                                           sc, st, partials);
   return cudaGetLastError();
 }
