@@ -114,96 +114,97 @@ __device__ __forceinline__ bool grid_barrier(const BatchArgs& A, unsigned& epoch
 }
 
 // ---------------------------------------------------------------------------
-// tile work (2D, tile TX x TY, halo H = sweeps), explicit tile coordinates
-template <int TX, int TY>
+// tile work (2D, tile TX x TY, halo H = sweeps), explicit tile coordinates.
+// The sweep depth is a compile-time parameter (1..3, dispatched once per
+// call), so every region width is a constant; the tile stores omega / d per
+// cell (0 off the fluid) and a sweep is x <- (1 - omega) x + (omega/d)(b + nb).
+template <int TX, int TY, int H>
 struct BReg {
-  int H, RX, RY, R, ox, oy;
-  __device__ __forceinline__ BReg(int h, int tx, int ty) {
-    H = h;
-    RX = TX + 2 * h;
-    RY = TY + 2 * h;
-    R = RX * RY;
-    ox = tx * TX - h;
-    oy = ty * TY - h;
+  static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
+  int ox, oy;
+  __device__ __forceinline__ BReg(int tx, int ty) : ox(tx * TX - H), oy(ty * TY - H) {}
+};
+
+__device__ __forceinline__ float b_diag(const LevelDev& L, int gx, int gy, uint8_t m) {
+  return L.cell ? diag_at<2, true>(L, gx, gy, 0, m) : diag_at<2, false>(L, gx, gy, 0, m);
+}
+
+// smem of one tile: b, two iterates, omega / d (floats), cell bytes
+template <int TX, int TY, int H>
+struct BSmem {
+  float *sb, *s0, *s1, *sw;
+  uint8_t* sm;
+  __device__ __forceinline__ explicit BSmem(float* S) {
+    constexpr int R = BReg<TX, TY, H>::R;
+    sb = S;
+    s0 = sb + R;
+    s1 = s0 + R;
+    sw = s1 + R;
+    sm = reinterpret_cast<uint8_t*>(sw + R);
   }
 };
 
-template <int TX, int TY>
-__device__ __forceinline__ void b_load(const BReg<TX, TY>& g, const LevelDev& L, const float* __restrict__ f, float* s,
-                                       uint8_t* sm) {
-  for (int i = threadIdx.x; i < g.R; i += blockDim.x) {
-    const int lx = i % g.RX, ly = i / g.RX;
-    const int gx = g.ox + lx, gy = g.oy + ly;
-    float v = 0.f;
-    uint8_t m = 0;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-      const size_t gi = (size_t)gy * L.nx + gx;
-      m = L.cell ? L.cell[gi] : kFluidBit;
-      if (m) v = f[gi];
-    }
-    s[i] = v;
-    sm[i] = m;
-  }
-}
-
-template <int TX, int TY>
-__device__ __forceinline__ float b_diag(const BReg<TX, TY>& g, const LevelDev& L, int lx, int ly, uint8_t m) {
-  return L.cell ? diag_at<2, true>(L, g.ox + lx, g.oy + ly, 0, m) : diag_at<2, false>(L, g.ox + lx, g.oy + ly, 0, m);
-}
-
-template <int TX, int TY>
-__device__ __forceinline__ void b_sweep(const BReg<TX, TY>& g, const LevelDev& L, const float* xin, float* xout,
-                                        const float* sb, const uint8_t* sm, int m, float omega, bool from_zero) {
-  const int SX = TX + 2 * m, SY = TY + 2 * m;
+// one sweep over the tile grown by M cells; from_zero: x_in = 0
+template <int TX, int TY, int H, int M>
+__device__ __forceinline__ void b_sweep(const LevelDev& L, const float* xin, float* xout, const float* sb,
+                                        const float* sw, float omega, bool from_zero) {
+  using G = BReg<TX, TY, H>;
+  constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
+  const float keep = 1.f - omega;
   for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
-    const int lx = i % SX + g.H - m, ly = i / SX + g.H - m;
-    const int li = ly * g.RX + lx;
-    const uint8_t mm = sm[li];
-    float v = 0.f;
-    if (mm) {
-      const float d = b_diag(g, L, lx, ly, mm);
-      if (from_zero) {
-        v = omega * sb[li] / d;
-      } else {
-        const float nb = L.wx * (xin[li - 1] + xin[li + 1]) + L.wy * (xin[li - g.RX] + xin[li + g.RX]);
-        v = xin[li] + omega * (sb[li] - (d * xin[li] - nb)) / d;
-      }
+    const int li = (i / SX + H - M) * G::RX + i % SX + H - M;
+    const float w = sw[li];
+    float v;
+    if (from_zero) {
+      v = w * sb[li];
+    } else {
+      const float nb = L.wx * (xin[li - 1] + xin[li + 1]) + L.wy * (xin[li - G::RX] + xin[li + G::RX]);
+      v = w > 0.f ? keep * xin[li] + w * (sb[li] + nb) : 0.f;
     }
     xout[li] = v;
   }
   __syncthreads();
 }
 
-// down leg of one tile: sweeps from zero, x, restricted residual
-template <int TX, int TY>
-__device__ void b_down(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
-                       float* __restrict__ bc, int sweeps, float omega, float* S) {
-  const BReg<TX, TY> g(sweeps > 0 ? sweeps : 1, tx, ty);
-  float* sb = S;
-  float* s0 = sb + g.R;
-  float* s1 = s0 + g.R;
-  uint8_t* sm = reinterpret_cast<uint8_t*>(s1 + g.R);
+// down leg of one tile: H sweeps from zero, x, restricted residual
+template <int TX, int TY, int H>
+__device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
+                         float* __restrict__ bc, float omega, float* S) {
+  using G = BReg<TX, TY, H>;
+  const G g(tx, ty);
+  const BSmem<TX, TY, H> M(S);
   __syncthreads();
-  b_load<TX, TY>(g, L, b, sb, sm);
-  __syncthreads();
-  float* cur = s0;
-  float* nxt = s1;
-  if (sweeps == 0) {
-    for (int i = threadIdx.x; i < g.R; i += blockDim.x) s0[i] = 0.f;
-    __syncthreads();
-  } else {
-    b_sweep<TX, TY>(g, L, nullptr, s0, sb, sm, sweeps, omega, true);
-    for (int j = 2; j <= sweeps; ++j) {
-      b_sweep<TX, TY>(g, L, cur, nxt, sb, sm, sweeps - j + 1, omega, false);
-      float* t = cur;
-      cur = nxt;
-      nxt = t;
+  for (int i = threadIdx.x; i < G::R; i += blockDim.x) {
+    const int gx = g.ox + i % G::RX, gy = g.oy + i / G::RX;
+    float v = 0.f, w = 0.f;
+    uint8_t m = 0;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      const size_t gi = (size_t)gy * L.nx + gx;
+      m = L.cell ? L.cell[gi] : kFluidBit;
+      if (m) {
+        v = b[gi];
+        w = __fdividef(omega, b_diag(L, gx, gy, m));
+      }
     }
+    M.sb[i] = v;
+    M.sw[i] = w;
+    M.sm[i] = m;
+  }
+  __syncthreads();
+  b_sweep<TX, TY, H, H>(L, nullptr, M.s0, M.sb, M.sw, omega, true);
+  float* cur = M.s0;
+  if (H >= 2) {
+    b_sweep<TX, TY, H, (H >= 2 ? H - 1 : 1)>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
+  }
+  if (H >= 3) {
+    b_sweep<TX, TY, H, 1>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+    cur = M.s0;
   }
   for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
-    const int lx = i % TX + g.H, ly = i / TX + g.H;
+    const int lx = i % TX + H, ly = i / TX + H;
     const int gx = g.ox + lx, gy = g.oy + ly;
-    if (gx < L.nx && gy < L.ny) x[(size_t)gy * L.nx + gx] = cur[ly * g.RX + lx];
+    if (gx < L.nx && gy < L.ny) x[(size_t)gy * L.nx + gx] = cur[ly * G::RX + lx];
   }
   const int cnx = L.nx / 2, cny = L.ny / 2;
   for (int i = threadIdx.x; i < (TX / 2) * (TY / 2); i += blockDim.x) {
@@ -211,37 +212,36 @@ __device__ void b_down(const LevelDev& L, int tx, int ty, const float* __restric
     const int gcx = tx * (TX / 2) + cx, gcy = ty * (TY / 2) + cy;
     if (gcx >= cnx || gcy >= cny) continue;
     float sum = 0.f;
+#pragma unroll
     for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
       for (int ax = 0; ax < 2; ++ax) {
-        const int lx = g.H + 2 * cx + ax, ly = g.H + 2 * cy + ay;
-        const int li = ly * g.RX + lx;
-        const uint8_t mm = sm[li];
+        const int lx = H + 2 * cx + ax, ly = H + 2 * cy + ay;
+        const int li = ly * G::RX + lx;
+        const uint8_t mm = M.sm[li];
         if (!mm) continue;
-        const float d = b_diag(g, L, lx, ly, mm);
-        const float nb = L.wx * (cur[li - 1] + cur[li + 1]) + L.wy * (cur[li - g.RX] + cur[li + g.RX]);
-        sum += sb[li] - (d * cur[li] - nb);
+        const float d = b_diag(L, g.ox + lx, g.oy + ly, mm);
+        const float nb = L.wx * (cur[li - 1] + cur[li + 1]) + L.wy * (cur[li - G::RX] + cur[li + G::RX]);
+        sum += M.sb[li] - (d * cur[li] - nb);
       }
     bc[(size_t)gcy * cnx + gcx] = 0.25f * sum;
   }
 }
 
-// up leg of one tile: x + s P e, sweeps, output; returns this thread's
+// up leg of one tile: x + s P e, H sweeps, output; returns this thread's
 // share of (b, out) when `dot`
-template <int TX, int TY>
-__device__ float b_up(const LevelDev& L, int tx, int ty, const float* __restrict__ b, const float* __restrict__ xin,
-                      float* __restrict__ xout, const float* __restrict__ e, int sweeps, float omega, float s,
-                      bool dot, float* S) {
-  const BReg<TX, TY> g(sweeps > 0 ? sweeps : 1, tx, ty);
-  float* sb = S;
-  float* s0 = sb + g.R;
-  float* s1 = s0 + g.R;
-  uint8_t* sm = reinterpret_cast<uint8_t*>(s1 + g.R);
+template <int TX, int TY, int H>
+__device__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+                        const float* __restrict__ xin, float* __restrict__ xout, const float* __restrict__ e,
+                        float omega, float s, bool dot, float* S) {
+  using G = BReg<TX, TY, H>;
+  const G g(tx, ty);
+  const BSmem<TX, TY, H> M(S);
   __syncthreads();
   const int cnx = L.nx / 2;
-  for (int i = threadIdx.x; i < g.R; i += blockDim.x) {
-    const int lx = i % g.RX, ly = i / g.RX;
-    const int gx = g.ox + lx, gy = g.oy + ly;
-    float v = 0.f, bv = 0.f;
+  for (int i = threadIdx.x; i < G::R; i += blockDim.x) {
+    const int gx = g.ox + i % G::RX, gy = g.oy + i / G::RX;
+    float v = 0.f, bv = 0.f, w = 0.f;
     uint8_t m = 0;
     if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
       const size_t gi = (size_t)gy * L.nx + gx;
@@ -249,32 +249,58 @@ __device__ float b_up(const LevelDev& L, int tx, int ty, const float* __restrict
       if (m) {
         v = xin[gi] + s * e[(size_t)(gy >> 1) * cnx + (gx >> 1)];
         bv = b[gi];
+        w = __fdividef(omega, b_diag(L, gx, gy, m));
       }
     }
-    s0[i] = v;
-    sb[i] = bv;
-    sm[i] = m;
+    M.s0[i] = v;
+    M.sb[i] = bv;
+    M.sw[i] = w;
+    M.sm[i] = m;
   }
   __syncthreads();
-  float* cur = s0;
-  float* nxt = s1;
-  for (int j = 1; j <= sweeps; ++j) {
-    b_sweep<TX, TY>(g, L, cur, nxt, sb, sm, sweeps - j, omega, false);
-    float* t = cur;
-    cur = nxt;
-    nxt = t;
+  float* cur = M.s0;
+  if (H == 1) {
+    b_sweep<TX, TY, H, 0>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
+  } else if (H == 2) {
+    b_sweep<TX, TY, H, 1>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    b_sweep<TX, TY, H, 0>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+  } else {
+    b_sweep<TX, TY, H, (H >= 3 ? 2 : 0)>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    b_sweep<TX, TY, H, 1>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+    b_sweep<TX, TY, H, 0>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
   }
   float acc = 0.f;
   for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
-    const int lx = i % TX + g.H, ly = i / TX + g.H;
+    const int lx = i % TX + H, ly = i / TX + H;
     const int gx = g.ox + lx, gy = g.oy + ly;
     if (gx < L.nx && gy < L.ny) {
-      const int li = ly * g.RX + lx;
+      const int li = ly * G::RX + lx;
       xout[(size_t)gy * L.nx + gx] = cur[li];
-      if (dot) acc = fmaf(sb[li], cur[li], acc);
+      if (dot) acc = fmaf(M.sb[li], cur[li], acc);
     }
   }
   return acc;
+}
+
+template <int TX, int TY>
+__device__ __forceinline__ void b_down(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+                                       float* __restrict__ x, float* __restrict__ bc, int sweeps, float omega,
+                                       float* S) {
+  if (sweeps <= 1) b_down_h<TX, TY, 1>(L, tx, ty, b, x, bc, omega, S);
+  else if (sweeps == 2) b_down_h<TX, TY, 2>(L, tx, ty, b, x, bc, omega, S);
+  else b_down_h<TX, TY, 3>(L, tx, ty, b, x, bc, omega, S);
+}
+
+template <int TX, int TY>
+__device__ __forceinline__ float b_up(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+                                      const float* __restrict__ xin, float* __restrict__ xout,
+                                      const float* __restrict__ e, int sweeps, float omega, float s, bool dot,
+                                      float* S) {
+  if (sweeps <= 1) return b_up_h<TX, TY, 1>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+  if (sweeps == 2) return b_up_h<TX, TY, 2>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+  return b_up_h<TX, TY, 3>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
 }
 
 // cells of a level-0 tile, one by one: callback(i, x, y)
@@ -625,9 +651,9 @@ struct mg_batch_s {
 };
 
 static size_t batched_smem(int tx, int ty, int sweeps, size_t coarse_bytes) {
-  const int h = sweeps > 0 ? sweeps : 1;
+  const int h = sweeps < 1 ? 1 : (sweeps > 3 ? 3 : sweeps);
   const size_t R = (size_t)(tx + 2 * h) * (ty + 2 * h);
-  size_t t = 3 * R * 4 + ((R + 15) & ~size_t(15));
+  size_t t = 4 * R * 4 + ((R + 15) & ~size_t(15));  // b, two iterates, omega/d; cell bytes
   return t > coarse_bytes ? t : coarse_bytes;
 }
 
