@@ -417,8 +417,7 @@ def run_gpu(args, rank, world):
     launches = (L.mg_kernel_launches(mg) - launches0) if mg else args.steps
     launches += L.gn_kernel_launches() - gn_launches0
     step_stats = list(stats)
-    total_ms = sum(times)
-    total_ms = dist_max(total_ms, world)
+    total_ms = dist_max(sum(times), world)
     if args.only_timed:
         cleanup()
         return {"metric": METRIC, "value": wl.units * args.steps * world / (total_ms * 1e-3), "unit": UNIT,
@@ -479,8 +478,7 @@ def run_gpu(args, rank, world):
                     "avg_launch_us": round(ms_dom / max(n_dom, 1) * 1e3, 2),
                     "share_of_step": round(ms_dom / tot_prof, 3),
                     "class_shares": {k: round(v[0] / tot_prof, 3) for k, v in prof.items() if v[1]}}
-    units_total = wl.units * args.steps * world
-    value = units_total / (total_ms * 1e-3)
+    value = job_rate(wl.units, args.steps, world, total_ms)
     its = [s["iters"] for s in step_stats]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -563,6 +561,12 @@ def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_rate(units_per_step, steps, world, max_ms):
+    """Whole-job throughput of `world` replicas that each did `steps` steps
+    of `units_per_step` unknowns, timed by the slowest rank (max_ms)."""
+    return units_per_step * steps * world / (max_ms * 1e-3)
 
 
 def dist_max(v, world):

@@ -17,6 +17,8 @@
 // 2x2x2 average restriction (App. B), copy prolongation plus scaled
 // correction and two post sweeps on the up leg (Sec. 2.2), (r, z) and CG's
 // beta on the finest level.
+#include <algorithm>
+
 #include "launch.h"
 #include "mg_kernels.cuh"
 
@@ -338,13 +340,23 @@ bool stream3d_eligible(int dim, int pre, int post, const LevelDev& L) {
 static size_t s3_smem_down() { return (size_t)(12 * RN + 2 * TN) * sizeof(float); }
 static size_t s3_smem_up() { return (size_t)(12 * RN) * sizeof(float); }
 
-// Resident blocks of a streaming kernel per SM (shared memory bound).
-static int s3_per_sm(size_t smem) {
-  int dev = 0, smem_sm = 0, reserved = 0;
+// Resident blocks of a streaming kernel per SM (shared memory, registers,
+// threads).
+template <typename K>
+static int s3_per_sm(K kernel, size_t smem) {
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  const int per = (int)((size_t)smem_sm / (smem + 512 + (size_t)reserved));
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  int per = (int)((size_t)smem_sm / (smem + 512 + (size_t)reserved));
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && fa.numRegs > 0) {
+    const int regs_block = ((fa.numRegs * 32 + 255) / 256) * 256 * (NT / 32);
+    per = std::min(per, regs_sm / regs_block);
+  }
+  per = std::min(per, thr_sm / NT);
   return per < 1 ? 1 : per;
 }
 
@@ -353,12 +365,13 @@ static int s3_per_sm(size_t smem) {
 // every SM; the cube-tile kernels take those levels)
 static int s3_run(const LevelDev& L, int nsm, int per_sm) {
   const int tiles = ((L.nx + SX - 1) / SX) * ((L.ny + SY - 1) / SY);
-  const int resident = nsm * per_sm;
-  const int runs = resident / tiles;
-  if (runs < 1) return ((L.nz + 1) / 2) * 2 >= 8 ? ((L.nz + 1) / 2) * 2 : 0;
+  int runs = std::max(1, nsm * per_sm / tiles);
+  runs = std::min(runs, std::max(1, L.nz / 4));  // runs of at least 4 planes
   int zr = (L.nz + runs - 1) / runs;
   zr = ((zr + 1) / 2) * 2;
-  if (zr < 4 || tiles * ((L.nz + zr - 1) / zr) < nsm) return 0;
+  // more resident blocks only lengthen the grid, so eligibility checked
+  // with 2 blocks per SM holds for every launch
+  if (tiles * ((L.nz + zr - 1) / zr) < nsm) return 0;
   return zr;
 }
 
@@ -379,7 +392,7 @@ static int device_sms() {
 template <typename T, bool MASKED>
 cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega,
                            const SolveState* st, cudaStream_t s) {
-  static const int per = s3_per_sm(s3_smem_down());
+  static const int per = s3_per_sm(k_down_s3<T, MASKED>, s3_smem_down());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
   k_down_s3<T, MASKED><<<s3_grid(L, zr), NT, s3_smem_down(), s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, omega, zr,
@@ -390,7 +403,7 @@ cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoa
 template <typename T, bool MASKED, bool FINEST>
 cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s) {
-  static const int per = s3_per_sm(s3_smem_up());
+  static const int per = s3_per_sm(k_up_s3<T, MASKED, FINEST>, s3_smem_up());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
   k_up_s3<T, MASKED, FINEST><<<s3_grid(L, zr), NT, s3_smem_up(), s>>>(L, (const T*)b, (const T*)xin, (T*)xout,
@@ -402,6 +415,7 @@ template <typename T, bool MASKED>
 cudaError_t prepare_s3_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_down_s3<T, MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)s3_smem_down());
+
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_up_s3<T, MASKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s3_smem_up());
