@@ -1,8 +1,28 @@
 // Kernel launchers exported between the library's translation units.
 #pragma once
+#include <utility>
+
 #include "npmg_internal.cuh"
 
 namespace npmg {
+
+// Launch a kernel of the solve's launch chain (it starts with chain_enter):
+// with the programmatic-serialization attribute unless NPMG_NO_PDL is set.
+bool chain_launch_enabled();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = chain_launch_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 struct CoarseArgs {
   int nlev;                    // levels handled by the single-block kernel
@@ -43,6 +63,17 @@ cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void
                          float sc, SolveState* st, double* partials, cudaStream_t s);
 template <typename T, bool MASKED>
 cudaError_t prepare_s3_kernels();
+// 2D level kernels streamed along y by single warps (two sweeps;
+// mg_stream2d.cu); arrays 16-byte aligned.
+bool stream2d_eligible(int dim, int pre, int post, const LevelDev& L);
+bool stream2d_aligned(const void* p);
+size_t stream2d_min_cells();
+template <typename T, bool MASKED>
+cudaError_t launch_down_w(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
+                          cudaStream_t s);
+template <typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up_w(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
+                        float sc, SolveState* st, double* partials, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_coarse(size_t smem_bytes);
 

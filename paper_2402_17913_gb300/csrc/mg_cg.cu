@@ -166,6 +166,7 @@ template <int DIM, typename T, bool MASKED>
 __global__ void __launch_bounds__(256) k_p_update(LevelDev L, const T* __restrict__ z, const T* __restrict__ pold,
                                                   T* __restrict__ pnew, T* __restrict__ Ap,
                                                   SolveState* __restrict__ st, double* __restrict__ partials) {
+  chain_enter();
   if (st->inner_done) return;
   const bool first = st->first || !st->krylov;
   const float beta = first ? 0.f : (float)st->beta;
@@ -249,6 +250,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_xr_update(LevelDev L, const T* __restrict__ p, const T* __restrict__ Ap,
                                                    T* __restrict__ d, T* __restrict__ r, SolveState* __restrict__ st,
                                                    double* __restrict__ partials) {
+  chain_enter();
   if (st->inner_done) return;
   const float alpha = (float)st->alpha;
   const bool first = st->first;
@@ -291,15 +293,13 @@ __global__ void __launch_bounds__(256) k_xr_update(LevelDev L, const T* __restri
 template <int DIM, typename T, bool MASKED>
 cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, void* pnew, void* Ap,
                             SolveState* st, double* partials, cudaStream_t s) {
-  k_p_update<DIM, T, MASKED><<<row_grid(L), 256, 0, s>>>(L, (const T*)z, (const T*)pold, (T*)pnew, (T*)Ap, st,
-                                                         partials);
-  return cudaGetLastError();
+  return launch_chain(k_p_update<DIM, T, MASKED>, row_grid(L), 256, 0, s, L, (const T*)z, (const T*)pold, (T*)pnew,
+                      (T*)Ap, st, partials);
 }
 template <typename T>
 cudaError_t launch_xr_update(const LevelDev& L, const void* p, const void* Ap, void* d, void* r, SolveState* st,
                              double* partials, cudaStream_t s) {
-  k_xr_update<T><<<row_grid(L), 256, 0, s>>>(L, (const T*)p, (const T*)Ap, (T*)d, (T*)r, st, partials);
-  return cudaGetLastError();
+  return launch_chain(k_xr_update<T>, row_grid(L), 256, 0, s, L, (const T*)p, (const T*)Ap, (T*)d, (T*)r, st, partials);
 }
 
 // ---------------------------------------------------------------------------

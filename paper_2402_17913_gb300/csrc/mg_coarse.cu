@@ -34,6 +34,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse(const __grid_constant__ CoarseArgs a, const T* __restrict__ bin,
                                                  T* __restrict__ xout, SolveState* __restrict__ st,
                                                  int total_floats) {
+  chain_enter();
   if (st && st->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* S = reinterpret_cast<float*>(smem_raw);
@@ -87,8 +88,7 @@ cudaError_t launch_coarse_image(const CoarseArgs& a, float* image, size_t bytes,
 template <typename T>
 cudaError_t launch_coarse(const CoarseArgs& a, size_t smem_bytes, const void* b, void* x, SolveState* st,
                           cudaStream_t s) {
-  k_coarse<T><<<1, 1024, smem_bytes, s>>>(a, (const T*)b, (T*)x, st, (int)(smem_bytes / sizeof(float)));
-  return cudaGetLastError();
+  return launch_chain(k_coarse<T>, 1, 1024, smem_bytes, s, a, (const T*)b, (T*)x, st, (int)(smem_bytes / sizeof(float)));
 }
 
 template <typename T>

@@ -52,6 +52,7 @@ struct mg_handle_s {
   npmg::TmaLevelMaps tmaps[npmg::kMaxLevels];  // TMA tensor maps per level (levels < kc)
   bool tma_ok[npmg::kMaxLevels];
   bool s3_ok[npmg::kMaxLevels];   // 3D levels on the z-streaming kernels
+  bool s2_ok[npmg::kMaxLevels];   // 2D levels on the y-streaming warp kernels
   int64_t chunk_kernels;   // kernels in one graph launch
   // instrumentation
   int64_t launches;

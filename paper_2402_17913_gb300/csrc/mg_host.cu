@@ -23,6 +23,11 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_err; }
 
+bool chain_launch_enabled() {
+  static const bool on = getenv("NPMG_NO_PDL") == nullptr;
+  return on;
+}
+
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 LaunchScope::LaunchScope(mg_handle_s* hh, int cls, cudaStream_t ss) : h(hh), idx(-1), s(ss) {
@@ -102,7 +107,9 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     const void* b = k == 0 ? r : h->bk[k];
     LaunchScope ls(h, k == 0 ? MG_K_DOWN_FINE : MG_K_DOWN, s);
     const bool tma = k == 0 ? tma0 : h->tma_ok[k];
-    if (tma)
+    if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
+      e = launch_down_w<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
+    else if (tma)
       e = launch_down_tma<T, M>(k == 0 ? m0 : h->tmaps[k], h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
     else if (DIM == 3 && h->s3_ok[k])
       e = launch_down_s3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
@@ -122,7 +129,12 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     void* xo = k == 0 ? z : h->yk[k];
     LaunchScope ls(h, k == 0 ? MG_K_UP_FINE : MG_K_UP, s);
     const bool tma = k == 0 ? tma0 : h->tma_ok[k];
-    if (tma) {
+    if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b)) {
+      if (k == 0 && st)
+        e = launch_up_w<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+      else
+        e = launch_up_w<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+    } else if (tma) {
       const TmaLevelMaps& mk = k == 0 ? m0 : h->tmaps[k];
       if (k == 0 && st)
         e = launch_up_tma<T, M, true>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
@@ -558,8 +570,11 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (e == cudaSuccess) e = prepare_coarse<T>(h->ca_smem);
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
-    for (int k = 0; k < h->kc; ++k)
+    for (int k = 0; k < h->kc; ++k) {
       h->s3_ok[k] = getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
+      h->s2_ok[k] = getenv("NPMG_NO_STREAM2D") == nullptr && stream2d_eligible(dim, o.pre, o.post, h->lv[k]) &&
+                    h->ncell[k] >= stream2d_min_cells();
+    }
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
       h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&

@@ -126,6 +126,7 @@ template <int DIM, int HT, typename T, bool MASKED>
 __global__ void __launch_bounds__(kThreads)
 k_down(LevelDev L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse, int pre, float omega,
        const SolveState* __restrict__ st) {
+  chain_enter();
   if (st && st->inner_done) return;
   using TS = TileShape<DIM>;
   const int pre_c = HT > 0 ? HT : pre;
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(kThreads)
 k_up(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
      const T* __restrict__ e, int post, float omega, float s, SolveState* __restrict__ st,
      double* __restrict__ partials) {
+  chain_enter();
   if (st && st->inner_done) return;
   using TS = TileShape<DIM>;
   const int post_c = HT > 0 ? HT : post;

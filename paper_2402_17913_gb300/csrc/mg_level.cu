@@ -39,12 +39,10 @@ cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse
                         const SolveState* st, cudaStream_t s) {
   const size_t sm = tile_smem<DIM>(pre);
   if (pre == 2)
-    k_down<DIM, 2, T, MASKED><<<tile_grid<DIM>(L), kThreads, sm, s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, pre,
-                                                                       omega, st);
-  else
-    k_down<DIM, 0, T, MASKED><<<tile_grid<DIM>(L), kThreads, sm, s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, pre,
-                                                                       omega, st);
-  return cudaGetLastError();
+    return launch_chain(k_down<DIM, 2, T, MASKED>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b, (T*)x,
+                        (T*)bcoarse, pre, omega, st);
+  return launch_chain(k_down<DIM, 0, T, MASKED>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b, (T*)x,
+                      (T*)bcoarse, pre, omega, st);
 }
 
 template <int DIM, typename T, bool MASKED, bool FINEST>
@@ -52,12 +50,10 @@ cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* x
                       float omega, float sc, SolveState* st, double* partials, cudaStream_t s) {
   const size_t sm = tile_smem<DIM>(post);
   if (post == 2)
-    k_up<DIM, 2, T, MASKED, FINEST><<<tile_grid<DIM>(L), kThreads, sm, s>>>(
-        L, (const T*)b, (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
-  else
-    k_up<DIM, 0, T, MASKED, FINEST><<<tile_grid<DIM>(L), kThreads, sm, s>>>(
-        L, (const T*)b, (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
-  return cudaGetLastError();
+    return launch_chain(k_up<DIM, 2, T, MASKED, FINEST>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b,
+                        (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
+  return launch_chain(k_up<DIM, 0, T, MASKED, FINEST>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b,
+                      (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
 }
 
 // Raise the dynamic shared-memory limit of the level kernels once (at

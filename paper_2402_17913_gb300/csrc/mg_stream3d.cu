@@ -156,6 +156,7 @@ template <typename T, bool MASKED>
 __global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
                                                T* __restrict__ bcoarse, float omega, int zr,
                                                const SolveState* __restrict__ st) {
+  chain_enter();
   if (st && st->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sB = reinterpret_cast<float*>(smem_raw);  // [3][RN]
@@ -246,6 +247,7 @@ template <typename T, bool MASKED, bool FINEST>
 __global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
                                              T* __restrict__ xout, const T* __restrict__ e, float omega, float s,
                                              int zr, SolveState* __restrict__ st, double* __restrict__ partials) {
+  chain_enter();
   if (st && st->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sB = reinterpret_cast<float*>(smem_raw);  // [3][RN]
@@ -395,9 +397,8 @@ cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoa
   static const int per = s3_per_sm(k_down_s3<T, MASKED>, s3_smem_down());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
-  k_down_s3<T, MASKED><<<s3_grid(L, zr), NT, s3_smem_down(), s>>>(L, (const T*)b, (T*)x, (T*)bcoarse, omega, zr,
-                                                                   st);
-  return cudaGetLastError();
+  return launch_chain(k_down_s3<T, MASKED>, s3_grid(L, zr), NT, s3_smem_down(), s, L, (const T*)b, (T*)x, (T*)bcoarse,
+                      omega, zr, st);
 }
 
 template <typename T, bool MASKED, bool FINEST>
@@ -406,9 +407,8 @@ cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void
   static const int per = s3_per_sm(k_up_s3<T, MASKED, FINEST>, s3_smem_up());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
-  k_up_s3<T, MASKED, FINEST><<<s3_grid(L, zr), NT, s3_smem_up(), s>>>(L, (const T*)b, (const T*)xin, (T*)xout,
-                                                                      (const T*)e, omega, sc, zr, st, partials);
-  return cudaGetLastError();
+  return launch_chain(k_up_s3<T, MASKED, FINEST>, s3_grid(L, zr), NT, s3_smem_up(), s, L, (const T*)b, (const T*)xin,
+                      (T*)xout, (const T*)e, omega, sc, zr, st, partials);
 }
 
 template <typename T, bool MASKED>

@@ -107,6 +107,7 @@ template <typename T, bool MASKED>
 __global__ void __launch_bounds__(kTmaThreads)
 k_down_tma(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap tm, LevelDev L,
            T* __restrict__ x, T* __restrict__ bcoarse, float omega, SolveState* __restrict__ st) {
+  chain_enter();
   if (st && st->inner_done) return;
   using G = TmaGeom<T>;
   using Lo = DownLayout<T>;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kTmaThreads)
 k_up_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tb,
          const __grid_constant__ CUtensorMap te, const __grid_constant__ CUtensorMap tm, LevelDev L,
          T* __restrict__ xout, float omega, float s, SolveState* __restrict__ st, double* __restrict__ partials) {
+  chain_enter();
   if (st && st->inner_done) return;
   using G = TmaGeom<T>;
   using Lo = UpLayout<T>;
@@ -368,16 +370,15 @@ static dim3 tma_grid(const LevelDev& L) {
 template <typename T, bool MASKED>
 cudaError_t launch_down_tma(const TmaLevelMaps& m, const LevelDev& L, void* x, void* bcoarse, float omega,
                             SolveState* st, cudaStream_t s) {
-  k_down_tma<T, MASKED><<<tma_grid(L), kTmaThreads, DownLayout<T>::BYTES, s>>>(m.b, m.m, L, (T*)x, (T*)bcoarse, omega, st);
-  return cudaGetLastError();
+  return launch_chain(k_down_tma<T, MASKED>, tma_grid(L), kTmaThreads, DownLayout<T>::BYTES, s, m.b, m.m, L, (T*)x,
+                      (T*)bcoarse, omega, st);
 }
 
 template <typename T, bool MASKED, bool FINEST>
 cudaError_t launch_up_tma(const TmaLevelMaps& m, const LevelDev& L, void* xout, float omega, float sc,
                           SolveState* st, double* partials, cudaStream_t s) {
-  k_up_tma<T, MASKED, FINEST><<<tma_grid(L), kTmaThreads, UpLayout<T>::BYTES, s>>>(m.x, m.b, m.e, m.m, L, (T*)xout, omega,
-                                                                          sc, st, partials);
-  return cudaGetLastError();
+  return launch_chain(k_up_tma<T, MASKED, FINEST>, tma_grid(L), kTmaThreads, UpLayout<T>::BYTES, s, m.x, m.b, m.e, m.m,
+                      L, (T*)xout, omega, sc, st, partials);
 }
 
 template <typename K>

@@ -52,6 +52,18 @@ struct SolveState {
 enum Counter { kCntInit = 0, kCntOuter = 1, kCntRZ = 2, kCntPAP = 3, kCntRR = 4, kCntMisc = 5 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a solve's launch chain
+// (level legs, coarse block, CG updates) are launched so that the next one
+// may be scheduled while the previous one drains; each first waits until
+// the preceding grid has completed and its writes are visible (a no-op when
+// it was launched without the dependency), then lets its own successor be
+// scheduled.  Nothing may be read or written before this call.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // storage conversions
 template <typename T> __device__ __forceinline__ float ld(const T* p, size_t i);
 template <> __device__ __forceinline__ float ld<float>(const float* p, size_t i) { return p[i]; }
