@@ -53,15 +53,15 @@ enum Counter { kCntInit = 0, kCntOuter = 1, kCntRZ = 2, kCntPAP = 3, kCntRR = 4,
 
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of a solve's launch chain
-// (level legs, coarse block, CG updates) are launched so that the next one
-// may be scheduled while the previous one drains; each first waits until
-// the preceding grid has completed and its writes are visible (a no-op when
-// it was launched without the dependency), then lets its own successor be
-// scheduled.  Nothing may be read or written before this call.
-__device__ __forceinline__ void chain_enter() {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
+// (level legs, coarse block, CG updates) are launched with a programmatic
+// dependency on the previous one, so that their launch overlaps its drain;
+// each first waits until the preceding grid has completed and its writes
+// are visible (a no-op when it was launched without the dependency).
+// Nothing may be read or written before this call.  No grid releases its
+// successor early: measured on GB300, successors parked on the SMs from the
+// start of the previous grid made the 2D and 3D solves 5-8% slower, while
+// the release at exit makes the 2D flow step about 1.5% faster.
+__device__ __forceinline__ void chain_enter() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // storage conversions
