@@ -74,6 +74,17 @@ cudaError_t launch_down_w(const LevelDev& L, const void* b, void* x, void* bcoar
 template <typename T, bool MASKED, bool FINEST>
 cudaError_t launch_up_w(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                         float sc, SolveState* st, double* partials, cudaStream_t s);
+// 3D level kernels, a block per 128 x 16 column streamed along z with a
+// warp per row (two sweeps; mg_rows3d.cu); arrays 16-byte aligned.
+bool rows3d_eligible(int dim, int pre, int post, const LevelDev& L);
+template <typename T, bool MASKED>
+cudaError_t launch_down_r3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
+                           cudaStream_t s);
+template <typename T, bool MASKED, bool FINEST>
+cudaError_t launch_up_r3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
+                         float sc, SolveState* st, double* partials, cudaStream_t s);
+template <typename T, bool MASKED>
+cudaError_t prepare_r3_kernels();
 template <typename T>
 cudaError_t prepare_coarse(size_t smem_bytes);
 

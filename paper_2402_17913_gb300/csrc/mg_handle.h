@@ -53,6 +53,7 @@ struct mg_handle_s {
   bool tma_ok[npmg::kMaxLevels];
   bool s3_ok[npmg::kMaxLevels];   // 3D levels on the z-streaming kernels
   bool s2_ok[npmg::kMaxLevels];   // 2D levels on the y-streaming warp kernels
+  bool r3_ok[npmg::kMaxLevels];   // 3D levels on the row-warp z-streaming kernels
   int64_t chunk_kernels;   // kernels in one graph launch
   // instrumentation
   int64_t launches;

@@ -111,6 +111,8 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
       e = launch_down_w<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
     else if (tma)
       e = launch_down_tma<T, M>(k == 0 ? m0 : h->tmaps[k], h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
+    else if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
+      e = launch_down_r3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
     else if (DIM == 3 && h->s3_ok[k])
       e = launch_down_s3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
     else
@@ -140,6 +142,11 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
         e = launch_up_tma<T, M, true>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
       else
         e = launch_up_tma<T, M, false>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
+    } else if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b)) {
+      if (k == 0 && st)
+        e = launch_up_r3<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+      else
+        e = launch_up_r3<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
     } else if (DIM == 3 && h->s3_ok[k]) {
       if (k == 0 && st)
         e = launch_up_s3<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
@@ -570,10 +577,12 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (e == cudaSuccess) e = prepare_coarse<T>(h->ca_smem);
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
+    if (e == cudaSuccess && DIM == 3) e = prepare_r3_kernels<T, M>();
     for (int k = 0; k < h->kc; ++k) {
       h->s3_ok[k] = getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
       h->s2_ok[k] = getenv("NPMG_NO_STREAM2D") == nullptr && stream2d_eligible(dim, o.pre, o.post, h->lv[k]) &&
                     h->ncell[k] >= stream2d_min_cells();
+      h->r3_ok[k] = getenv("NPMG_NO_ROWS3D") == nullptr && rows3d_eligible(dim, o.pre, o.post, h->lv[k]);
     }
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
