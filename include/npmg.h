@@ -59,10 +59,16 @@ typedef enum {
 
 enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 };
 
+/* Storage of the cycle's level arrays (Sec. 2.2 smoothing, restriction and
+ * prolongation): the iterate, right-hand side and correction of every level
+ * but the finest.  The CG vectors (residual, preconditioned residual,
+ * search direction, A p, inner correction) stay float32 and the refinement
+ * loop's residual and iterate float64 at every setting; arithmetic is
+ * float32 throughout. */
 typedef enum {
-  MG_FP32 = 0,        /* inner vectors and hierarchy stored in float32     */
-  MG_MIXED_FP16 = 1,  /* inner storage float16, float32 arithmetic         */
-  MG_MIXED_BF16 = 2   /* inner storage bfloat16, float32 arithmetic        */
+  MG_FP32 = 0,        /* level arrays float32                              */
+  MG_MIXED_FP16 = 1,  /* level arrays float16                              */
+  MG_MIXED_BF16 = 2   /* level arrays bfloat16                             */
 } mg_precision;
 
 typedef struct {
@@ -76,9 +82,9 @@ typedef struct {
                            stationary cycles                                    */
   int max_inner;        /* CG iterations per refinement step (default 200)     */
   int max_outer;        /* refinement steps (default 12)                       */
-  mg_precision prec;    /* inner storage precision (default MG_FP32)           */
+  mg_precision prec;    /* level-array storage (default MG_FP32)               */
   double inner_floor;   /* smallest relative tolerance asked of one inner
-                           solve; 0 = default for prec (1e-4 / 4e-3 / 2e-2)    */
+                           solve; 0 = default (1e-4)                           */
 } mg_options;
 
 typedef struct {

@@ -43,10 +43,13 @@ size_t coarse_layout(int* off, const LevelDev* lv, int nlev, int dim);
 cudaError_t launch_coarse_image(const CoarseArgs& a, float* image, size_t bytes, cudaStream_t s);
 int coarse_start_level(const LevelDev* lv, int L, int dim, size_t smem_limit);
 
-template <int DIM, typename T, bool MASKED>
+// Level legs: T is the storage of a level's iterate and of its coarse-side
+// arrays, TB that of its right-hand side b and of the up leg's output (the
+// float32 CG vectors on the finest level, else T).
+template <int DIM, typename T, bool MASKED, typename TB = T>
 cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,
                         const SolveState* st, cudaStream_t s);
-template <int DIM, typename T, bool MASKED, bool FINEST>
+template <int DIM, typename T, bool MASKED, bool FINEST, typename TB = T>
 cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, int post,
                       float omega, float sc, SolveState* st, double* partials, cudaStream_t s);
 
@@ -55,10 +58,10 @@ cudaError_t prepare_level_kernels(int pre, int post);
 
 // 3D level kernels streamed along z (two sweeps; mg_stream3d.cu).
 bool stream3d_eligible(int dim, int pre, int post, const LevelDev& L);
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB = T>
 cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega,
                            const SolveState* st, cudaStream_t s);
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB = T>
 cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s);
 template <typename T, bool MASKED>
@@ -68,19 +71,19 @@ cudaError_t prepare_s3_kernels();
 bool stream2d_eligible(int dim, int pre, int post, const LevelDev& L);
 bool stream2d_aligned(const void* p);
 size_t stream2d_min_cells();
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB = T>
 cudaError_t launch_down_w(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
                           cudaStream_t s);
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB = T>
 cudaError_t launch_up_w(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                         float sc, SolveState* st, double* partials, cudaStream_t s);
 // 3D level kernels, a block per 128 x 16 column streamed along z with a
 // warp per row (two sweeps; mg_rows3d.cu); arrays 16-byte aligned.
 bool rows3d_eligible(int dim, int pre, int post, const LevelDev& L);
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB = T>
 cudaError_t launch_down_r3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
                            cudaStream_t s);
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB = T>
 cudaError_t launch_up_r3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s);
 template <typename T, bool MASKED>

@@ -90,72 +90,83 @@ static cudaError_t dispatch(const mg_handle_s* h, F&& f) {
 // down legs on levels 0 .. kc-1, the single-block kernel for kc .. L-1, up
 // legs back to level 0.  With `st` it is the CG preconditioner (kernels skip
 // once CG converged; the finest up leg reduces (r, z)).
+// Down / up leg of level k with right-hand-side storage TB (float on the
+// finest level, whose b and z are CG vectors; T elsewhere).  `tma` selects
+// the TMA tile kernels (only for TB == T).
+template <int DIM, typename T, bool M, typename TB>
+static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevelMaps* tm, SolveState* st,
+                            cudaStream_t s) {
+  const float om = (float)h->opt.omega;
+  if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
+    return launch_down_w<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
+  if constexpr (std::is_same<T, TB>::value) {
+    if (tm) return launch_down_tma<T, M>(*tm, h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
+  }
+  if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
+    return launch_down_r3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
+  if (DIM == 3 && h->s3_ok[k]) return launch_down_s3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
+  return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], h->opt.pre, om, st, s);
+}
+
+template <int DIM, typename T, bool M, bool F, typename TB>
+static cudaError_t up_leg(mg_handle_s* h, int k, const void* b, void* xo, const TmaLevelMaps* tm, SolveState* st,
+                          cudaStream_t s) {
+  const float om = (float)h->opt.omega, sc = (float)h->opt.coarse_scale;
+  if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
+    return launch_up_w<T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+  if constexpr (std::is_same<T, TB>::value) {
+    if (tm) return launch_up_tma<T, M, F>(*tm, h->lv[k], xo, om, sc, st, h->partials, s);
+  }
+  if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
+    return launch_up_r3<T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+  if (DIM == 3 && h->s3_ok[k])
+    return launch_up_s3<T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
+  return launch_up<DIM, T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], h->opt.post, om, sc, st, h->partials,
+                                     s);
+}
+
+// One application of the preconditioner M (one cycle from a zero guess):
+// down legs on levels 0 .. kc-1, the single-block kernel for kc .. L-1, up
+// legs back to level 0.  r and z (level 0's right-hand side and output) are
+// float32; the level arrays below are T.  With `st` it is the CG
+// preconditioner (kernels skip once CG converged; the finest up leg reduces
+// (r, z)).
 template <int DIM, typename T, bool M>
 static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveState* st, cudaStream_t s) {
-  const mg_options& o = h->opt;
   cudaError_t e;
-  const float om = (float)o.omega, sc = (float)o.coarse_scale;
-  // TMA tensor maps: level 0 reads r, which is the caller's array in the
-  // building-block path, so its map is re-encoded when r is not the handle's
+  // TMA tensor maps (float32 handles): level 0 reads r, which is the
+  // caller's array in the building-block path, so its map is re-encoded
+  // when r is not the handle's
   TmaLevelMaps m0;
   bool tma0 = h->tma_ok[0];
   if (tma0) {
     m0 = h->tmaps[0];
-    if (r != h->r) tma0 = tma_encode_b<T>(&m0.b, h->lv[0], r);
+    if (r != h->r) tma0 = tma_encode_b<float>(&m0.b, h->lv[0], r);
   }
   for (int k = 0; k < h->kc; ++k) {
-    const void* b = k == 0 ? r : h->bk[k];
     LaunchScope ls(h, k == 0 ? MG_K_DOWN_FINE : MG_K_DOWN, s);
-    const bool tma = k == 0 ? tma0 : h->tma_ok[k];
-    if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
-      e = launch_down_w<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
-    else if (tma)
-      e = launch_down_tma<T, M>(k == 0 ? m0 : h->tmaps[k], h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
-    else if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
-      e = launch_down_r3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
-    else if (DIM == 3 && h->s3_ok[k])
-      e = launch_down_s3<T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
+    if (k == 0)
+      e = down_leg<DIM, T, M, float>(h, 0, r, tma0 ? &m0 : nullptr, st, s);
     else
-      e = launch_down<DIM, T, M>(h->lv[k], b, h->xk[k], h->bk[k + 1], o.pre, om, st, s);
+      e = down_leg<DIM, T, M, T>(h, k, h->bk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, st, s);
     if (e != cudaSuccess) return e;
   }
   CoarseArgs ca = h->ca;
   ca.finest = (h->kc == 0 && st) ? 1 : 0;
   {
     LaunchScope ls(h, MG_K_COARSE, s);
-    e = launch_coarse<T>(ca, h->ca_smem, h->kc == 0 ? r : h->bk[h->kc], h->kc == 0 ? z : h->yk[h->kc], st, s);
+    e = h->kc == 0 ? launch_coarse<float>(ca, h->ca_smem, r, z, st, s)
+                   : launch_coarse<T>(ca, h->ca_smem, h->bk[h->kc], h->yk[h->kc], st, s);
   }
   if (e != cudaSuccess) return e;
   for (int k = h->kc - 1; k >= 0; --k) {
-    const void* b = k == 0 ? r : h->bk[k];
-    void* xo = k == 0 ? z : h->yk[k];
     LaunchScope ls(h, k == 0 ? MG_K_UP_FINE : MG_K_UP, s);
-    const bool tma = k == 0 ? tma0 : h->tma_ok[k];
-    if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b)) {
-      if (k == 0 && st)
-        e = launch_up_w<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-      else
-        e = launch_up_w<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-    } else if (tma) {
-      const TmaLevelMaps& mk = k == 0 ? m0 : h->tmaps[k];
-      if (k == 0 && st)
-        e = launch_up_tma<T, M, true>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
-      else
-        e = launch_up_tma<T, M, false>(mk, h->lv[k], xo, om, sc, st, h->partials, s);
-    } else if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b)) {
-      if (k == 0 && st)
-        e = launch_up_r3<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-      else
-        e = launch_up_r3<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-    } else if (DIM == 3 && h->s3_ok[k]) {
-      if (k == 0 && st)
-        e = launch_up_s3<T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-      else
-        e = launch_up_s3<T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
-    } else if (k == 0 && st)
-      e = launch_up<DIM, T, M, true>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], o.post, om, sc, st, h->partials, s);
+    if (k == 0 && st)
+      e = up_leg<DIM, T, M, true, float>(h, 0, r, z, tma0 ? &m0 : nullptr, st, s);
+    else if (k == 0)
+      e = up_leg<DIM, T, M, false, float>(h, 0, r, z, tma0 ? &m0 : nullptr, st, s);
     else
-      e = launch_up<DIM, T, M, false>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], o.post, om, sc, st, h->partials, s);
+      e = up_leg<DIM, T, M, false, T>(h, k, h->bk[k], h->yk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, st, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -169,11 +180,11 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(h, MG_K_P_UPDATE, s);
-    e = launch_p_update<DIM, T, M>(h->lv[0], h->z, h->p[parity], h->p[1 - parity], h->Ap, h->st, h->partials, s);
+    e = launch_p_update<DIM, float, M>(h->lv[0], h->z, h->p[parity], h->p[1 - parity], h->Ap, h->st, h->partials, s);
   }
   if (e != cudaSuccess) return e;
   LaunchScope ls(h, MG_K_XR_UPDATE, s);
-  return launch_xr_update<T>(h->lv[0], h->p[1 - parity], h->Ap, h->d, h->r, h->st, h->partials, s);
+  return launch_xr_update<float>(h->lv[0], h->p[1 - parity], h->Ap, h->d, h->r, h->st, h->partials, s);
 }
 
 cudaError_t enqueue_chunk(mg_handle_s* h, cudaStream_t s) {
@@ -198,8 +209,8 @@ static cudaError_t enqueue_outer(mg_handle_s* h, const float* b, bool update, cu
     void* xout = h->xff[1 - h->cur64];
     LaunchScope ls(h, MG_K_OUTER, s);
     if (update)
-      return launch_outer<DIM, T, M, true>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
-    return launch_outer<DIM, T, M, false>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
+      return launch_outer<DIM, float, M, true>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
+    return launch_outer<DIM, float, M, false>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
   });
 }
 
@@ -417,7 +428,9 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
   h->use_graph = getenv("NPMG_NO_GRAPH") ? 0 : 1;
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
   h->esz = o.prec == MG_FP32 ? 4 : 2;
-  h->inner_floor = o.inner_floor > 0 ? o.inner_floor : (o.prec == MG_FP32 ? 1e-4 : (o.prec == MG_MIXED_FP16 ? 4e-3 : 2e-2));
+  // the CG vectors are float32 at every precision, so one inner solve can
+  // reach the same relative tolerance whatever the cycle's storage
+  h->inner_floor = o.inner_floor > 0 ? o.inner_floor : 1e-4;
   for (int f = 0; f < 2 * dim; ++f) {
     h->bc[f] = bc[f];
     if (bc[f] == MG_BC_DIRICHLET) h->bcD |= 1 << f;
@@ -469,12 +482,14 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (k >= 1) plan.push_back({&h->yk[k], h->ncell[k] * h->esz});
   }
   const size_t n0c = h->ncell[0];
-  plan.push_back({&h->r, n0c * h->esz});
-  plan.push_back({&h->z, n0c * h->esz});
-  plan.push_back({&h->p[0], n0c * h->esz});
-  plan.push_back({&h->p[1], n0c * h->esz});
-  plan.push_back({&h->Ap, n0c * h->esz});
-  plan.push_back({&h->d, n0c * h->esz});
+  // CG vectors: float32 at every precision (the 16-bit storage is the
+  // cycle's level arrays)
+  plan.push_back({&h->r, n0c * 4});
+  plan.push_back({&h->z, n0c * 4});
+  plan.push_back({&h->p[0], n0c * 4});
+  plan.push_back({&h->p[1], n0c * 4});
+  plan.push_back({&h->Ap, n0c * 4});
+  plan.push_back({&h->d, n0c * 4});
   plan.push_back({&h->xff[0], n0c * 8});
   plan.push_back({&h->xff[1], n0c * 8});
   plan.push_back({(void**)&h->inv, (size_t)2 * h->ncoarse * h->ncoarse * 8});
@@ -575,6 +590,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     constexpr bool M = decltype(mc)::value;
     cudaError_t e = prepare_level_kernels<DIM, T, M>(o.pre, o.post);
     if (e == cudaSuccess) e = prepare_coarse<T>(h->ca_smem);
+    if (e == cudaSuccess && !std::is_same<T, float>::value) e = prepare_coarse<float>(h->ca_smem);
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_r3_kernels<T, M>();
@@ -586,7 +602,9 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     }
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
+      // level 0 of a 16-bit handle reads float32 r: no TMA tile kernels there
       h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&
+                     (k > 0 || std::is_same<T, float>::value) &&
                      tma_encode_level<T>(&h->tmaps[k], h->lv[k], k == 0 ? h->r : h->bk[k], h->xk[k],
                                          h->yk[k + 1]);
     }

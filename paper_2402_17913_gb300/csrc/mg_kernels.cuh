@@ -117,14 +117,19 @@ __device__ __forceinline__ float residual_at(const Region<DIM, HT>& g, const Lev
 }
 
 // ---------------------------------------------------------------------------
+// Storage types: T for a level's own iterate x, its coarse right-hand side
+// and the coarse correction e; TB for the level's right-hand side b and the
+// up leg's output (T on every level but the finest, where b and z are the
+// float32 CG vectors).
+//
 // Down leg of one level: `pre` sweeps from x = 0 (the cycle starts every
 // level from a zero guess, Sec. 2.2 step list), then r = b - A' x and its
 // 2x2(x2) average written to the coarse right-hand side (Sec. 2.2
 // restriction filter of 1/4, App. B eight eighths in 3D).  All sweeps of a
 // tile run in shared memory (temporal blocking: halo = pre).
-template <int DIM, int HT, typename T, bool MASKED>
+template <int DIM, int HT, typename T, bool MASKED, typename TB = T>
 __global__ void __launch_bounds__(kThreads)
-k_down(LevelDev L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse, int pre, float omega,
+k_down(LevelDev L, const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse, int pre, float omega,
        const SolveState* __restrict__ st) {
   chain_enter();
   if (st && st->inner_done) return;
@@ -136,7 +141,7 @@ k_down(LevelDev L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ b
   float* s0 = sb + g.R;
   float* s1 = s0 + g.R;
   uint8_t* sm = reinterpret_cast<uint8_t*>(s1 + g.R);
-  load_region<DIM, HT, T, MASKED>(g, L, b, sb, sm);
+  load_region<DIM, HT, TB, MASKED>(g, L, b, sb, sm);
   __syncthreads();
   float* cur = s0;
   float* nxt = s1;
@@ -193,9 +198,9 @@ k_down(LevelDev L, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ b
 // 2^dim children, Sec. 2.2 prolongation filter of ones), then `post` sweeps;
 // written to xout (xin is not modified, so tiles never race).  On the finest
 // level of the preconditioner it also reduces (r, z) and sets CG's beta.
-template <int DIM, int HT, typename T, bool MASKED, bool FINEST>
+template <int DIM, int HT, typename T, bool MASKED, bool FINEST, typename TB = T>
 __global__ void __launch_bounds__(kThreads)
-k_up(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+k_up(LevelDev L, const TB* __restrict__ b, const T* __restrict__ xin, TB* __restrict__ xout,
      const T* __restrict__ e, int post, float omega, float s, SolveState* __restrict__ st,
      double* __restrict__ partials) {
   chain_enter();
@@ -248,7 +253,7 @@ k_up(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin, T* __restri
     const int gx = g.ox + lx, gy = g.oy + ly, gz = g.oz + lz;
     if (inside<DIM>(L, gx, gy, gz)) {
       const int li = g.idx(lx, ly, lz);
-      const T zt = cvt<T>(cur[li]);
+      const TB zt = cvt<TB>(cur[li]);
       xout[gidx(L, gx, gy, gz)] = zt;
       if (FINEST) acc = fmaf(sb[li], ld(&zt, 0), acc);
     }

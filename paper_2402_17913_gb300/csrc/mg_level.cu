@@ -1,5 +1,7 @@
 // Level kernels of the multigrid cycle (Sec. 2.2): launchers and the
 // single-pass building blocks used by the per-kernel entry points.
+#include <type_traits>
+
 #include "launch.h"
 #include "mg_kernels.cuh"
 
@@ -34,56 +36,71 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 // Two sweeps (the default) use the compile-time-halo instantiation.
-template <int DIM, typename T, bool MASKED>
+template <int DIM, typename T, bool MASKED, typename TB>
 cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,
                         const SolveState* st, cudaStream_t s) {
   const size_t sm = tile_smem<DIM>(pre);
   if (pre == 2)
-    return launch_chain(k_down<DIM, 2, T, MASKED>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b, (T*)x,
+    return launch_chain(k_down<DIM, 2, T, MASKED, TB>, tile_grid<DIM>(L), kThreads, sm, s, L, (const TB*)b, (T*)x,
                         (T*)bcoarse, pre, omega, st);
-  return launch_chain(k_down<DIM, 0, T, MASKED>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b, (T*)x,
+  return launch_chain(k_down<DIM, 0, T, MASKED, TB>, tile_grid<DIM>(L), kThreads, sm, s, L, (const TB*)b, (T*)x,
                       (T*)bcoarse, pre, omega, st);
 }
 
-template <int DIM, typename T, bool MASKED, bool FINEST>
+template <int DIM, typename T, bool MASKED, bool FINEST, typename TB>
 cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, int post,
                       float omega, float sc, SolveState* st, double* partials, cudaStream_t s) {
   const size_t sm = tile_smem<DIM>(post);
   if (post == 2)
-    return launch_chain(k_up<DIM, 2, T, MASKED, FINEST>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b,
-                        (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
-  return launch_chain(k_up<DIM, 0, T, MASKED, FINEST>, tile_grid<DIM>(L), kThreads, sm, s, L, (const T*)b,
-                      (const T*)xin, (T*)xout, (const T*)e, post, omega, sc, st, partials);
+    return launch_chain(k_up<DIM, 2, T, MASKED, FINEST, TB>, tile_grid<DIM>(L), kThreads, sm, s, L, (const TB*)b,
+                        (const T*)xin, (TB*)xout, (const T*)e, post, omega, sc, st, partials);
+  return launch_chain(k_up<DIM, 0, T, MASKED, FINEST, TB>, tile_grid<DIM>(L), kThreads, sm, s, L, (const TB*)b,
+                      (const T*)xin, (TB*)xout, (const T*)e, post, omega, sc, st, partials);
 }
 
 // Raise the dynamic shared-memory limit of the level kernels once (at
 // create, outside any stream capture).
-template <int DIM, typename T, bool MASKED>
-cudaError_t prepare_level_kernels(int pre, int post) {
-  cudaError_t e = allow_smem(k_down<DIM, 2, T, MASKED>, tile_smem<DIM>(pre));
-  if (e == cudaSuccess) e = allow_smem(k_down<DIM, 0, T, MASKED>, tile_smem<DIM>(pre));
-  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, false>, tile_smem<DIM>(post));
-  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, true>, tile_smem<DIM>(post));
-  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, false>, tile_smem<DIM>(post));
-  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, true>, tile_smem<DIM>(post));
+template <int DIM, typename T, bool MASKED, typename TB>
+static cudaError_t prepare_level_pair(int pre, int post) {
+  cudaError_t e = allow_smem(k_down<DIM, 2, T, MASKED, TB>, tile_smem<DIM>(pre));
+  if (e == cudaSuccess) e = allow_smem(k_down<DIM, 0, T, MASKED, TB>, tile_smem<DIM>(pre));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, false, TB>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 2, T, MASKED, true, TB>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, false, TB>, tile_smem<DIM>(post));
+  if (e == cudaSuccess) e = allow_smem(k_up<DIM, 0, T, MASKED, true, TB>, tile_smem<DIM>(post));
   return e;
 }
 
-#define NPMG_INST_LEVEL(DIM, T, M)                                                                           \
-  template cudaError_t prepare_level_kernels<DIM, T, M>(int, int);                                            \
-  template cudaError_t launch_down<DIM, T, M>(const LevelDev&, const void*, void*, void*, int, float,          \
-                                              const SolveState*, cudaStream_t);                                \
-  template cudaError_t launch_up<DIM, T, M, false>(const LevelDev&, const void*, const void*, void*,          \
-                                                   const void*, int, float, float, SolveState*, double*,       \
-                                                   cudaStream_t);                                              \
-  template cudaError_t launch_up<DIM, T, M, true>(const LevelDev&, const void*, const void*, void*,           \
-                                                  const void*, int, float, float, SolveState*, double*,        \
-                                                  cudaStream_t);
+// Both storage pairs of a precision: (T, T) and, for 16-bit T, the finest
+// level's (T, float).
+template <int DIM, typename T, bool MASKED>
+cudaError_t prepare_level_kernels(int pre, int post) {
+  cudaError_t e = prepare_level_pair<DIM, T, MASKED, T>(pre, post);
+  if (e == cudaSuccess && !std::is_same<T, float>::value) e = prepare_level_pair<DIM, T, MASKED, float>(pre, post);
+  return e;
+}
 
-NPMG_INST_LEVEL(2, float, false)
-NPMG_INST_LEVEL(2, float, true)
-NPMG_INST_LEVEL(3, float, false)
-NPMG_INST_LEVEL(3, float, true)
+#define NPMG_INST_LEVEL_TB(DIM, T, M, TB)                                                                    \
+  template cudaError_t launch_down<DIM, T, M, TB>(const LevelDev&, const void*, void*, void*, int, float,      \
+                                                  const SolveState*, cudaStream_t);                            \
+  template cudaError_t launch_up<DIM, T, M, false, TB>(const LevelDev&, const void*, const void*, void*,      \
+                                                       const void*, int, float, float, SolveState*, double*,   \
+                                                       cudaStream_t);                                          \
+  template cudaError_t launch_up<DIM, T, M, true, TB>(const LevelDev&, const void*, const void*, void*,       \
+                                                      const void*, int, float, float, SolveState*, double*,    \
+                                                      cudaStream_t);
+#define NPMG_INST_LEVEL(DIM, T, M)                                 \
+  template cudaError_t prepare_level_kernels<DIM, T, M>(int, int); \
+  NPMG_INST_LEVEL_TB(DIM, T, M, T)                                 \
+  NPMG_INST_LEVEL_TB(DIM, T, M, float)
+
+#define NPMG_INST_LEVEL_F(DIM, M)                                      \
+  template cudaError_t prepare_level_kernels<DIM, float, M>(int, int); \
+  NPMG_INST_LEVEL_TB(DIM, float, M, float)
+NPMG_INST_LEVEL_F(2, false)
+NPMG_INST_LEVEL_F(2, true)
+NPMG_INST_LEVEL_F(3, false)
+NPMG_INST_LEVEL_F(3, true)
 NPMG_INST_LEVEL(2, __half, false)
 NPMG_INST_LEVEL(2, __half, true)
 NPMG_INST_LEVEL(3, __half, false)

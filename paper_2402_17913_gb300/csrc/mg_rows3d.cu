@@ -25,6 +25,7 @@
 // hold 0 (the zero padding of Sec. 2.1).  On the finest level the up leg
 // also reduces (r, z) and CG's beta.
 #include <algorithm>
+#include <type_traits>
 #include <stdlib.h>
 
 #include "launch.h"
@@ -43,13 +44,13 @@ constexpr int kRS = kD + 1;     // ring slots per warp
 constexpr int ROWF = 136;       // floats per buffered row: local x -4 .. 131
 constexpr int PLANE = NW * ROWF;
 
-template <typename T, bool MASKED, bool UP>
+template <typename T, typename TB, bool MASKED, bool UP>
 struct Lay {
-  static constexpr int SZ = (int)sizeof(T);
+  static constexpr int SZ = (int)sizeof(T), SB = (int)sizeof(TB);
   // ring slot of one warp (bytes): x (up), b, e (up), cell bytes (masked),
   // halo pairs of lane 0 (side 0) and lane 31 (side 1)
   static constexpr int BO = UP ? 128 * SZ : 0;
-  static constexpr int EO = BO + 128 * SZ;
+  static constexpr int EO = BO + 128 * SB;
   static constexpr int MO = EO + (UP ? 64 * SZ : 0);
   static constexpr int HO = MO + (MASKED ? 128 : 0);
   static constexpr int SLOT = HO + 64;
@@ -217,10 +218,10 @@ __device__ __forceinline__ void store_row(const Lane& c, float* buf, int pl, con
 }
 
 // ---- up leg ------------------------------------------------------------------
-template <typename T, bool MASKED>
-__device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int p, bool want, const T* __restrict__ b,
+template <typename T, typename TB, bool MASKED>
+__device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int p, bool want, const TB* __restrict__ b,
                                          const T* __restrict__ xin, const T* __restrict__ e, unsigned char* slot) {
-  using S = Lay<T, MASKED, true>;
+  using S = Lay<T, TB, MASKED, true>;
   if (want) {
     const bool rin = p >= 0 && p < L.nz && c.yin;
     const bool fo = rin && c.ox, fh = rin && c.hok;
@@ -229,13 +230,13 @@ __device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int p
     const int go = fo ? c.gx : 0;  // zero-fill copies keep an in-bounds source
     const uint32_t sl = smem_addr(slot);
     cp_async<4 * S::SZ>(sl + c.lane * 4 * S::SZ, xin + row + go, fo);
-    cp_async<4 * S::SZ>(sl + S::BO + c.lane * 4 * S::SZ, b + row + go, fo);
+    cp_async<4 * S::SB>(sl + S::BO + c.lane * 4 * S::SB, b + row + go, fo);
     cp_async<2 * S::SZ>(sl + S::EO + c.lane * 2 * S::SZ, e + crow + (go >> 1), fo);
     if (MASKED) cp_async<4>(sl + S::MO + c.lane * 4, L.cell + row + go, fo);
     if (c.lane == 0 || c.lane == 31) {
       const uint32_t hs = sl + S::HO + (c.lane == 31 ? 32 : 0);
       cp_async<2 * S::SZ>(hs, xin + row + (fh ? c.hpair : 0), fh);
-      cp_async<2 * S::SZ>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
+      cp_async<2 * S::SB>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
       cp_async<2 * S::SZ>(hs + 16, e + crow + (fh ? c.epair : 0), fh);
       if (MASKED) cp_async<4>(hs + 24, L.cell + row + (fh ? c.mword : 0), fh);
     }
@@ -263,11 +264,11 @@ struct UpRegs {
 
 // Step i (plane p = z0 - 2 + i) with phase slots C = i % 3, P = (i - 1) % 3,
 // Q = (i - 2) % 3.
-template <typename T, bool MASKED, bool FINEST, int C, int P, int Q>
+template <typename T, typename TB, bool MASKED, bool FINEST, int C, int P, int Q>
 __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i, int z0, int z1, float omega, float s,
-                                        const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ e,
-                                        T* __restrict__ xout, unsigned char* sm, UpRegs& R, float& acc) {
-  using S = Lay<T, MASKED, true>;
+                                        const TB* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ e,
+                                        TB* __restrict__ xout, unsigned char* sm, UpRegs& R, float& acc) {
+  using S = Lay<T, TB, MASKED, true>;
   const int p = z0 - 2 + i;
   float* B0 = reinterpret_cast<float*>(sm + S::P0);
   float* B1 = reinterpret_cast<float*>(sm + S::P1);
@@ -279,12 +280,12 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
     const unsigned char* sl = ring + (i % kRS) * S::SLOT;
     float xv[V], bv[V];
     lds4<T>(sl + c.lane * 4 * S::SZ, xv);
-    lds4<T>(sl + S::BO + c.lane * 4 * S::SZ, bv);
+    lds4<TB>(sl + S::BO + c.lane * 4 * S::SB, bv);
     const float2 ev = lds2<T>(sl + S::EO + c.lane * 2 * S::SZ);
     const unsigned char* hs = sl + S::HO + (c.lane == 31 ? 32 : 0);
     float xh, xo, bh, bo, eh, eo;
     halo_pair<T>(c, hs, 0, xh, xo);
-    halo_pair<T>(c, hs, 8, bh, bo);
+    halo_pair<TB>(c, hs, 8, bh, bo);
     halo_pair<T>(c, hs, 16, eh, eo);
     (void)bo;
     (void)eo;
@@ -315,7 +316,7 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
       B0[C * PLANE + c.warp * ROWF + c.hout_off] = flo ? fmaf(s, eh, xo) : 0.f;
     }
   }
-  up_issue<T, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, xin, e, ring + ((i + kD) % kRS) * S::SLOT);
+  up_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, xin, e, ring + ((i + kD) % kRS) * S::SLOT);
   __syncthreads();
   const float keep = 1.f - omega;
   // B: first sweep on plane p - 1, rows 1 .. NW - 2
@@ -332,11 +333,11 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
     sweep_row(L, c, B1, C, Q, P, false, keep, R.b[Q], R.w[Q], z);
     if (c.ox) {
       float zv[V] = {z[0], z[1], z[2], z[3]};
-      stv<T, V>(xout + ((size_t)o * L.ny + c.y) * L.nx + c.gx, zv);
+      stv<TB, V>(xout + ((size_t)o * L.ny + c.y) * L.nx + c.gx, zv);
       if (FINEST) {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-          const T zt = cvt<T>(z[j]);  // (r, z) of the stored z
+          const TB zt = cvt<TB>(z[j]);  // (r, z) of the stored z
           acc = fmaf(R.b[Q][j], ld(&zt, 0), acc);
         }
       }
@@ -344,13 +345,13 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
   }
 }
 
-template <typename T, bool MASKED, bool FINEST>
-__global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
-                                                 T* __restrict__ xout, const T* __restrict__ e, float omega, float s,
+template <typename T, bool MASKED, bool FINEST, typename TB>
+__global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const TB* __restrict__ b, const T* __restrict__ xin,
+                                                 TB* __restrict__ xout, const T* __restrict__ e, float omega, float s,
                                                  int zr, SolveState* __restrict__ st, double* __restrict__ partials) {
   chain_enter();
   if (st && st->inner_done) return;
-  using S = Lay<T, MASKED, true>;
+  using S = Lay<T, TB, MASKED, true>;
   extern __shared__ __align__(16) unsigned char smem_r3[];
   const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zr, z1 = min(z0 + zr, L.nz);
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const T* __restrict
   const Lane c = lane_of(L, x0, y0);
   unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
 #pragma unroll
-  for (int i = 0; i < kD; ++i) up_issue<T, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, xin, e, ring + i * S::SLOT);
+  for (int i = 0; i < kD; ++i) up_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, xin, e, ring + i * S::SLOT);
   __syncthreads();
   UpRegs R;
 #pragma unroll
@@ -371,11 +372,11 @@ __global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const T* __restrict
   float acc = 0.f;
   const int n = z1 - z0 + 4;
   for (int i = 0; i < n; i += 3) {
-    up_step<T, MASKED, FINEST, 0, 2, 1>(L, c, i, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+    up_step<T, TB, MASKED, FINEST, 0, 2, 1>(L, c, i, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
     if (i + 1 >= n) break;
-    up_step<T, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+    up_step<T, TB, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
     if (i + 2 >= n) break;
-    up_step<T, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+    up_step<T, TB, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   if (FINEST) {
@@ -391,21 +392,21 @@ __global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const T* __restrict
 }
 
 // ---- down leg ----------------------------------------------------------------
-template <typename T, bool MASKED>
-__device__ __forceinline__ void down_issue(const LevelDev& L, const Lane& c, int p, bool want, const T* __restrict__ b,
+template <typename T, typename TB, bool MASKED>
+__device__ __forceinline__ void down_issue(const LevelDev& L, const Lane& c, int p, bool want, const TB* __restrict__ b,
                                            unsigned char* slot) {
-  using S = Lay<T, MASKED, false>;
+  using S = Lay<T, TB, MASKED, false>;
   if (want) {
     const bool rin = p >= 0 && p < L.nz && c.yin;
     const bool fo = rin && c.ox, fh = rin && c.hok;
     const size_t row = rin ? ((size_t)p * L.ny + c.y) * L.nx : 0;
     const int go = fo ? c.gx : 0;
     const uint32_t sl = smem_addr(slot);
-    cp_async<4 * S::SZ>(sl + S::BO + c.lane * 4 * S::SZ, b + row + go, fo);
+    cp_async<4 * S::SB>(sl + S::BO + c.lane * 4 * S::SB, b + row + go, fo);
     if (MASKED) cp_async<4>(sl + S::MO + c.lane * 4, L.cell + row + go, fo);
     if (c.lane == 0 || c.lane == 31) {
       const uint32_t hs = sl + S::HO + (c.lane == 31 ? 32 : 0);
-      cp_async<2 * S::SZ>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
+      cp_async<2 * S::SB>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
       if (MASKED) cp_async<4>(hs + 24, L.cell + row + (fh ? c.mword : 0), fh);
     }
   }
@@ -418,11 +419,11 @@ struct DownRegs {
   float d[3][V];      // d of the own cells
 };
 
-template <typename T, bool MASKED, int C, int P, int Q>
+template <typename T, typename TB, bool MASKED, int C, int P, int Q>
 __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int i, int z0, int z1, float omega,
-                                          const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse,
+                                          const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse,
                                           unsigned char* sm, DownRegs& R) {
-  using S = Lay<T, MASKED, false>;
+  using S = Lay<T, TB, MASKED, false>;
   const int p = z0 - 2 + i;
   float* B0 = reinterpret_cast<float*>(sm + S::P0);  // first sweep
   float* B1 = reinterpret_cast<float*>(sm + S::P1);  // second sweep
@@ -434,10 +435,10 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
   {
     const unsigned char* sl = ring + (i % kRS) * S::SLOT;
     float bv[V];
-    lds4<T>(sl + S::BO + c.lane * 4 * S::SZ, bv);
+    lds4<TB>(sl + S::BO + c.lane * 4 * S::SB, bv);
     const unsigned char* hs = sl + S::HO + (c.lane == 31 ? 32 : 0);
     float bh, bo;
-    halo_pair<T>(c, hs, 8, bh, bo);
+    halo_pair<TB>(c, hs, 8, bh, bo);
     unsigned m[V + 2];
     const int kyz = MASKED ? 0 : kyz_of(L, c, p);
     if (MASKED) {
@@ -465,7 +466,7 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
       B0[C * PLANE + c.warp * ROWF + c.hout_off] = lut[64 + qo] * bo;
     }
   }
-  down_issue<T, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, ring + ((i + kD) % kRS) * S::SLOT);
+  down_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, ring + ((i + kD) % kRS) * S::SLOT);
   __syncthreads();
   const float keep = 1.f - omega;
   // B: second sweep on plane p - 1, rows 1 .. NW - 2
@@ -523,13 +524,13 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
 }
 
 
-template <typename T, bool MASKED>
-__global__ void __launch_bounds__(NT, 1) k_down_r3(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
+template <typename T, bool MASKED, typename TB>
+__global__ void __launch_bounds__(NT, 1) k_down_r3(LevelDev L, const TB* __restrict__ b, T* __restrict__ x,
                                                    T* __restrict__ bcoarse, float omega, int zr,
                                                    const SolveState* __restrict__ st) {
   chain_enter();
   if (st && st->inner_done) return;
-  using S = Lay<T, MASKED, false>;
+  using S = Lay<T, TB, MASKED, false>;
   extern __shared__ __align__(16) unsigned char smem_r3[];
   const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zr, z1 = min(z0 + zr, L.nz);
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(NT, 1) k_down_r3(LevelDev L, const T* __restri
   const Lane c = lane_of(L, x0, y0);
   unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
 #pragma unroll
-  for (int i = 0; i < kD; ++i) down_issue<T, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, ring + i * S::SLOT);
+  for (int i = 0; i < kD; ++i) down_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, ring + i * S::SLOT);
   __syncthreads();
   DownRegs R;
 #pragma unroll
@@ -551,11 +552,11 @@ __global__ void __launch_bounds__(NT, 1) k_down_r3(LevelDev L, const T* __restri
     }
   const int n = z1 - z0 + 4;
   for (int i = 0; i < n; i += 3) {
-    down_step<T, MASKED, 0, 2, 1>(L, c, i, z0, z1, omega, b, x, bcoarse, smem_r3, R);
+    down_step<T, TB, MASKED, 0, 2, 1>(L, c, i, z0, z1, omega, b, x, bcoarse, smem_r3, R);
     if (i + 1 >= n) break;
-    down_step<T, MASKED, 1, 0, 2>(L, c, i + 1, z0, z1, omega, b, x, bcoarse, smem_r3, R);
+    down_step<T, TB, MASKED, 1, 0, 2>(L, c, i + 1, z0, z1, omega, b, x, bcoarse, smem_r3, R);
     if (i + 2 >= n) break;
-    down_step<T, MASKED, 2, 1, 0>(L, c, i + 2, z0, z1, omega, b, x, bcoarse, smem_r3, R);
+    down_step<T, TB, MASKED, 2, 1, 0>(L, c, i + 2, z0, z1, omega, b, x, bcoarse, smem_r3, R);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -607,46 +608,58 @@ bool rows3d_eligible(int dim, int pre, int post, const LevelDev& L) {
          (size_t)L.nx * L.ny * L.nz >= lim;
 }
 
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB>
 cudaError_t launch_down_r3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
                            cudaStream_t s) {
   const int zr = r3_run(L);
-  return launch_chain(k_down_r3<T, MASKED>, r3_grid(L, zr), NT, (size_t)Lay<T, MASKED, false>::BYTES, s, L,
-                      (const T*)b, (T*)x, (T*)bcoarse, omega, zr, st);
+  return launch_chain(k_down_r3<T, MASKED, TB>, r3_grid(L, zr), NT, (size_t)Lay<T, TB, MASKED, false>::BYTES, s, L,
+                      (const TB*)b, (T*)x, (T*)bcoarse, omega, zr, st);
 }
 
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB>
 cudaError_t launch_up_r3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s) {
   const int zr = r3_run(L);
-  return launch_chain(k_up_r3<T, MASKED, FINEST>, r3_grid(L, zr), NT, (size_t)Lay<T, MASKED, true>::BYTES, s, L,
-                      (const T*)b, (const T*)xin, (T*)xout, (const T*)e, omega, sc, zr, st, partials);
+  return launch_chain(k_up_r3<T, MASKED, FINEST, TB>, r3_grid(L, zr), NT, (size_t)Lay<T, TB, MASKED, true>::BYTES, s,
+                      L, (const TB*)b, (const T*)xin, (TB*)xout, (const T*)e, omega, sc, zr, st, partials);
+}
+
+template <typename T, bool MASKED, typename TB>
+static cudaError_t prepare_r3_pair() {
+  cudaError_t e = cudaFuncSetAttribute(k_down_r3<T, MASKED, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Lay<T, TB, MASKED, false>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_up_r3<T, MASKED, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Lay<T, TB, MASKED, true>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_up_r3<T, MASKED, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Lay<T, TB, MASKED, true>::BYTES);
+  return e;
 }
 
 template <typename T, bool MASKED>
 cudaError_t prepare_r3_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_down_r3<T, MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Lay<T, MASKED, false>::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_up_r3<T, MASKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Lay<T, MASKED, true>::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_up_r3<T, MASKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Lay<T, MASKED, true>::BYTES);
+  cudaError_t e = prepare_r3_pair<T, MASKED, T>();
+  if (e == cudaSuccess && !std::is_same<T, float>::value) e = prepare_r3_pair<T, MASKED, float>();
   return e;
 }
 
-#define NPMG_INST_R3(T, M)                                                                                       \
-  template cudaError_t launch_down_r3<T, M>(const LevelDev&, const void*, void*, void*, float, const SolveState*, \
-                                            cudaStream_t);                                                       \
-  template cudaError_t launch_up_r3<T, M, false>(const LevelDev&, const void*, const void*, void*, const void*,   \
-                                                 float, float, SolveState*, double*, cudaStream_t);              \
-  template cudaError_t launch_up_r3<T, M, true>(const LevelDev&, const void*, const void*, void*, const void*,    \
-                                                float, float, SolveState*, double*, cudaStream_t);               \
-  template cudaError_t prepare_r3_kernels<T, M>();
+#define NPMG_INST_R3_TB(T, M, TB)                                                                                 \
+  template cudaError_t launch_down_r3<T, M, TB>(const LevelDev&, const void*, void*, void*, float,                 \
+                                                const SolveState*, cudaStream_t);                                 \
+  template cudaError_t launch_up_r3<T, M, false, TB>(const LevelDev&, const void*, const void*, void*,             \
+                                                     const void*, float, float, SolveState*, double*, cudaStream_t); \
+  template cudaError_t launch_up_r3<T, M, true, TB>(const LevelDev&, const void*, const void*, void*,              \
+                                                    const void*, float, float, SolveState*, double*, cudaStream_t);
+#define NPMG_INST_R3(T, M)                       \
+  template cudaError_t prepare_r3_kernels<T, M>(); \
+  NPMG_INST_R3_TB(T, M, T)                       \
+  NPMG_INST_R3_TB(T, M, float)
 
-NPMG_INST_R3(float, false)
-NPMG_INST_R3(float, true)
+template cudaError_t prepare_r3_kernels<float, false>();
+template cudaError_t prepare_r3_kernels<float, true>();
+NPMG_INST_R3_TB(float, false, float)
+NPMG_INST_R3_TB(float, true, float)
 NPMG_INST_R3(__half, false)
 NPMG_INST_R3(__half, true)
 NPMG_INST_R3(__nv_bfloat16, false)

@@ -97,11 +97,11 @@ __device__ __forceinline__ void stv(T* p, const float (&v)[N]) {
 // side 0 is lane 0's (cells x0 - 2, x0 - 1; coarse parent x0/2 - 1; cell
 // bytes x0 - 4 .. x0 - 1), side 1 lane 31's (x0 + 128, x0 + 129; parent
 // x0/2 + 64; bytes x0 + 128 .. x0 + 131), each as an aligned pair / word.
-template <typename T, bool MASKED, bool UP>
+template <typename T, typename TB, bool MASKED, bool UP>
 struct Slot {
-  static constexpr int SZ = (int)sizeof(T);
-  static constexpr int B = UP ? 128 * SZ : 0;              // T[128] b (x, up only, at 0)
-  static constexpr int E = B + 128 * SZ;                   // T[64] e (up)
+  static constexpr int SZ = (int)sizeof(T), SB = (int)sizeof(TB);
+  static constexpr int B = UP ? 128 * SZ : 0;              // TB[128] b (T[128] x at 0, up only)
+  static constexpr int E = B + 128 * SB;                   // T[64] e (up)
   static constexpr int M = E + (UP ? 64 * SZ : 0);         // u8[128] cell bytes (masked)
   static constexpr int H = M + (MASKED ? 128 : 0);         // 2 sides x 32 bytes: x pair, b pair, e pair, bytes
   static constexpr int BYTES = H + 64;
@@ -203,10 +203,10 @@ __device__ __forceinline__ void halo_bytes(const Lane& c, const unsigned char* h
 __device__ __forceinline__ int slot_of(int i) { return i % kSlots; }
 
 // ---- up leg ------------------------------------------------------------------
-template <typename T, bool MASKED>
-__device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int r, bool want, const T* __restrict__ b,
+template <typename T, typename TB, bool MASKED>
+__device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int r, bool want, const TB* __restrict__ b,
                                          const T* __restrict__ xin, const T* __restrict__ e, unsigned char* slot) {
-  using S = Slot<T, MASKED, true>;
+  using S = Slot<T, TB, MASKED, true>;
   if (want) {
     const bool rin = r >= 0 && r < L.ny;
     const bool fo = rin && c.ox, fh = rin && c.hok;
@@ -214,13 +214,13 @@ __device__ __forceinline__ void up_issue(const LevelDev& L, const Lane& c, int r
     const int go = fo ? c.gx : 0;  // zero-fill copies keep an in-bounds source
     const uint32_t sl = smem_addr(slot);
     cp_async<4 * S::SZ>(sl + c.lane * 4 * S::SZ, xin + row + go, fo);
-    cp_async<4 * S::SZ>(sl + S::B + c.lane * 4 * S::SZ, b + row + go, fo);
+    cp_async<4 * S::SB>(sl + S::B + c.lane * 4 * S::SB, b + row + go, fo);
     cp_async<2 * S::SZ>(sl + S::E + c.lane * 2 * S::SZ, e + crow + (go >> 1), fo);
     if (MASKED) cp_async<4>(sl + S::M + c.lane * 4, L.cell + row + go, fo);
     if (c.lane == 0 || c.lane == 31) {
       const uint32_t hs = sl + S::H + (c.lane == 31 ? 32 : 0);
       cp_async<2 * S::SZ>(hs, xin + row + (fh ? c.hpair : 0), fh);
-      cp_async<2 * S::SZ>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
+      cp_async<2 * S::SB>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
       cp_async<2 * S::SZ>(hs + 16, e + crow + (fh ? c.epair : 0), fh);
       if (MASKED) cp_async<4>(hs + 24, L.cell + row + (fh ? c.mword : 0), fh);
     }
@@ -236,11 +236,11 @@ struct UpRegs {
 };
 
 // One row step with register slots C (row p), P (row p - 1), Q (row p - 2).
-template <typename T, bool MASKED, bool FINEST, int C, int P, int Q>
+template <typename T, typename TB, bool MASKED, bool FINEST, int C, int P, int Q>
 __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i, int y0, int y1, float omega, float s,
-                                        const T* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ e,
-                                        T* __restrict__ xout, unsigned char* ring, UpRegs& R, float& acc) {
-  using S = Slot<T, MASKED, true>;
+                                        const TB* __restrict__ b, const T* __restrict__ xin, const T* __restrict__ e,
+                                        TB* __restrict__ xout, unsigned char* ring, UpRegs& R, float& acc) {
+  using S = Slot<T, TB, MASKED, true>;
   const int p = y0 - 2 + i;
   // row p from its slot: x + s P e on the own cells and both halo cells, b
   // and omega / d
@@ -249,12 +249,12 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
     const unsigned char* sl = ring + slot_of(i) * S::BYTES;
     float xv[V], bv[V];
     lds4<T>(sl + c.lane * 4 * S::SZ, xv);
-    lds4<T>(sl + S::B + c.lane * 4 * S::SZ, bv);
+    lds4<TB>(sl + S::B + c.lane * 4 * S::SB, bv);
     const float2 ev = lds2<T>(sl + S::E + c.lane * 2 * S::SZ);
     const unsigned char* hs = sl + S::H + (c.lane == 31 ? 32 : 0);
     float xh, xo, bh, bo, eh, eo;
     halo_of<T>(c, hs, 0, xh, xo);
-    halo_of<T>(c, hs, 8, bh, bo);
+    halo_of<TB>(c, hs, 8, bh, bo);
     halo_of<T>(c, hs, 16, eh, eo);
     (void)bo;
     (void)eo;
@@ -283,7 +283,7 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
     R.b[C][V] = bh;
     R.w[C][V] = w[V];
   }
-  up_issue<T, MASKED>(L, c, p + kD, p + kD <= y1 + 1, b, xin, e, ring + slot_of(i + kD) * S::BYTES);
+  up_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= y1 + 1, b, xin, e, ring + slot_of(i + kD) * S::BYTES);
   const float keep = 1.f - omega;
   // first sweep on row p - 1 (own cells and the inner halo)
   if (p >= y0) {
@@ -316,11 +316,11 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
       z[j] = fmaf(keep, a[j], R.w[Q][j] * (R.b[Q][j] + nb));
     }
     if (c.ox) {
-      stv<T, V>(xout + (size_t)o * L.nx + c.gx, z);
+      stv<TB, V>(xout + (size_t)o * L.nx + c.gx, z);
       if (FINEST) {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-          const T zt = cvt<T>(z[j]);  // (r, z) of the stored z
+          const TB zt = cvt<TB>(z[j]);  // (r, z) of the stored z
           acc = fmaf(R.b[Q][j], ld(&zt, 0), acc);
         }
       }
@@ -328,13 +328,13 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
   }
 }
 
-template <typename T, bool MASKED, bool FINEST>
-__global__ void __launch_bounds__(32 * kWPB) k_up_w(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
-                                                    T* __restrict__ xout, const T* __restrict__ e, float omega, float s,
+template <typename T, bool MASKED, bool FINEST, typename TB>
+__global__ void __launch_bounds__(32 * kWPB) k_up_w(LevelDev L, const TB* __restrict__ b, const T* __restrict__ xin,
+                                                    TB* __restrict__ xout, const T* __restrict__ e, float omega, float s,
                                                     int rows, SolveState* __restrict__ st, double* __restrict__ partials) {
   chain_enter();
   if (st && st->inner_done) return;
-  using S = Slot<T, MASKED, true>;
+  using S = Slot<T, TB, MASKED, true>;
   extern __shared__ __align__(16) unsigned char smem_w[];
   const int nstrips = (L.nx + 32 * V - 1) / (32 * V);
   const int nruns = (L.ny + rows - 1) / rows;
@@ -355,16 +355,16 @@ __global__ void __launch_bounds__(32 * kWPB) k_up_w(LevelDev L, const T* __restr
     }
 #pragma unroll
     for (int i = 0; i < kD; ++i)
-      up_issue<T, MASKED>(L, c, y0 - 2 + i, y0 - 2 + i <= y1 + 1, b, xin, e, ring + i * S::BYTES);
+      up_issue<T, TB, MASKED>(L, c, y0 - 2 + i, y0 - 2 + i <= y1 + 1, b, xin, e, ring + i * S::BYTES);
     // rows y0 - 2 .. y1 + 1 (step i = row y0 - 2 + i); register slots rotate
     // with period 3
     const int n = y1 - y0 + 4;
     for (int i = 0; i < n; i += 3) {
-      up_step<T, MASKED, FINEST, 0, 2, 1>(L, c, i, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
+      up_step<T, TB, MASKED, FINEST, 0, 2, 1>(L, c, i, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
       if (i + 1 >= n) break;
-      up_step<T, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
+      up_step<T, TB, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
       if (i + 2 >= n) break;
-      up_step<T, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
+      up_step<T, TB, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, y0, y1, omega, s, b, xin, e, xout, ring, R, acc);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the warp
   }
@@ -381,21 +381,21 @@ __global__ void __launch_bounds__(32 * kWPB) k_up_w(LevelDev L, const T* __restr
 }
 
 // ---- down leg ----------------------------------------------------------------
-template <typename T, bool MASKED>
-__device__ __forceinline__ void down_issue(const LevelDev& L, const Lane& c, int r, bool want, const T* __restrict__ b,
+template <typename T, typename TB, bool MASKED>
+__device__ __forceinline__ void down_issue(const LevelDev& L, const Lane& c, int r, bool want, const TB* __restrict__ b,
                                            unsigned char* slot) {
-  using S = Slot<T, MASKED, false>;
+  using S = Slot<T, TB, MASKED, false>;
   if (want) {
     const bool rin = r >= 0 && r < L.ny;
     const bool fo = rin && c.ox, fh = rin && c.hok;
     const size_t row = rin ? (size_t)r * L.nx : 0;
     const int go = fo ? c.gx : 0;
     const uint32_t sl = smem_addr(slot);
-    cp_async<4 * S::SZ>(sl + S::B + c.lane * 4 * S::SZ, b + row + go, fo);
+    cp_async<4 * S::SB>(sl + S::B + c.lane * 4 * S::SB, b + row + go, fo);
     if (MASKED) cp_async<4>(sl + S::M + c.lane * 4, L.cell + row + go, fo);
     if (c.lane == 0 || c.lane == 31) {
       const uint32_t hs = sl + S::H + (c.lane == 31 ? 32 : 0);
-      cp_async<2 * S::SZ>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
+      cp_async<2 * S::SB>(hs + 8, b + row + (fh ? c.hpair : 0), fh);
       if (MASKED) cp_async<4>(hs + 24, L.cell + row + (fh ? c.mword : 0), fh);
     }
   }
@@ -411,11 +411,11 @@ struct DownRegs {
   float rp[V / 2];     // restriction: residual pair sums of the even row
 };
 
-template <typename T, bool MASKED, int C, int P, int Q>
+template <typename T, typename TB, bool MASKED, int C, int P, int Q>
 __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int i, int y0, int y1, float omega,
-                                          const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse,
+                                          const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ bcoarse,
                                           unsigned char* ring, DownRegs& R) {
-  using S = Slot<T, MASKED, false>;
+  using S = Slot<T, TB, MASKED, false>;
   const int p = y0 - 2 + i;
   // row p: b, omega / d and the first sweep from zero, on own cells and halo
   cp_wait_ring();
@@ -424,12 +424,12 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
     float bv[V + 2];
     {
       float bo[V];
-      lds4<T>(sl + S::B + c.lane * 4 * S::SZ, bo);
+      lds4<TB>(sl + S::B + c.lane * 4 * S::SB, bo);
 #pragma unroll
       for (int j = 0; j < V; ++j) bv[j] = bo[j];
     }
     const unsigned char* hs = sl + S::H + (c.lane == 31 ? 32 : 0);
-    halo_of<T>(c, hs, 8, bv[V], bv[V + 1]);
+    halo_of<TB>(c, hs, 8, bv[V], bv[V + 1]);
     unsigned m[V + 2], mw = 0u;
     if (MASKED) {
       mw = *reinterpret_cast<const unsigned*>(sl + S::M + c.lane * 4);
@@ -450,7 +450,7 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
     }
     R.m[C] = mw;
   }
-  down_issue<T, MASKED>(L, c, p + kD, p + kD <= y1 + 1, b, ring + slot_of(i + kD) * S::BYTES);
+  down_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= y1 + 1, b, ring + slot_of(i + kD) * S::BYTES);
   const float keep = 1.f - omega;
   // second sweep on row p - 1 (own cells and the inner halo)
   if (p >= y0) {
@@ -509,13 +509,13 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
   }
 }
 
-template <typename T, bool MASKED>
-__global__ void __launch_bounds__(32 * kWPB) k_down_w(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
+template <typename T, bool MASKED, typename TB>
+__global__ void __launch_bounds__(32 * kWPB) k_down_w(LevelDev L, const TB* __restrict__ b, T* __restrict__ x,
                                                       T* __restrict__ bcoarse, float omega, int rows,
                                                       const SolveState* __restrict__ st) {
   chain_enter();
   if (st && st->inner_done) return;
-  using S = Slot<T, MASKED, false>;
+  using S = Slot<T, TB, MASKED, false>;
   extern __shared__ __align__(16) unsigned char smem_w[];
   const int nstrips = (L.nx + 32 * V - 1) / (32 * V);
   const int nruns = (L.ny + rows - 1) / rows;
@@ -537,14 +537,14 @@ __global__ void __launch_bounds__(32 * kWPB) k_down_w(LevelDev L, const T* __res
 #pragma unroll
   for (int k = 0; k < V / 2; ++k) R.rp[k] = 0.f;
 #pragma unroll
-  for (int i = 0; i < kD; ++i) down_issue<T, MASKED>(L, c, y0 - 2 + i, y0 - 2 + i <= y1 + 1, b, ring + i * S::BYTES);
+  for (int i = 0; i < kD; ++i) down_issue<T, TB, MASKED>(L, c, y0 - 2 + i, y0 - 2 + i <= y1 + 1, b, ring + i * S::BYTES);
   const int n = y1 - y0 + 4;
   for (int i = 0; i < n; i += 3) {
-    down_step<T, MASKED, 0, 2, 1>(L, c, i, y0, y1, omega, b, x, bcoarse, ring, R);
+    down_step<T, TB, MASKED, 0, 2, 1>(L, c, i, y0, y1, omega, b, x, bcoarse, ring, R);
     if (i + 1 >= n) break;
-    down_step<T, MASKED, 1, 0, 2>(L, c, i + 1, y0, y1, omega, b, x, bcoarse, ring, R);
+    down_step<T, TB, MASKED, 1, 0, 2>(L, c, i + 1, y0, y1, omega, b, x, bcoarse, ring, R);
     if (i + 2 >= n) break;
-    down_step<T, MASKED, 2, 1, 0>(L, c, i + 2, y0, y1, omega, b, x, bcoarse, ring, R);
+    down_step<T, TB, MASKED, 2, 1, 0>(L, c, i + 2, y0, y1, omega, b, x, bcoarse, ring, R);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -600,37 +600,41 @@ size_t stream2d_min_cells() {
   return e ? (size_t)atol(e) : ((size_t)1 << 19);
 }
 
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB>
 cudaError_t launch_down_w(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
                           cudaStream_t s) {
   const int rows = s2_rows(L);
-  const size_t smem = (size_t)kWPB * kSlots * Slot<T, MASKED, false>::BYTES;
-  return launch_chain(k_down_w<T, MASKED>, s2_blocks(L, rows), 32 * kWPB, smem, s, L, (const T*)b, (T*)x, (T*)bcoarse,
-                      omega, rows, st);
+  const size_t smem = (size_t)kWPB * kSlots * Slot<T, TB, MASKED, false>::BYTES;
+  return launch_chain(k_down_w<T, MASKED, TB>, s2_blocks(L, rows), 32 * kWPB, smem, s, L, (const TB*)b, (T*)x,
+                      (T*)bcoarse, omega, rows, st);
 }
 
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB>
 cudaError_t launch_up_w(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                         float sc, SolveState* st, double* partials, cudaStream_t s) {
   const int rows = s2_rows(L);
-  const size_t smem = (size_t)kWPB * kSlots * Slot<T, MASKED, true>::BYTES;
-  return launch_chain(k_up_w<T, MASKED, FINEST>, s2_blocks(L, rows), 32 * kWPB, smem, s, L, (const T*)b,
-                      (const T*)xin, (T*)xout, (const T*)e, omega, sc, rows, st, partials);
+  const size_t smem = (size_t)kWPB * kSlots * Slot<T, TB, MASKED, true>::BYTES;
+  return launch_chain(k_up_w<T, MASKED, FINEST, TB>, s2_blocks(L, rows), 32 * kWPB, smem, s, L, (const TB*)b,
+                      (const T*)xin, (TB*)xout, (const T*)e, omega, sc, rows, st, partials);
 }
 
-#define NPMG_INST_S2(T, M)                                                                                       \
-  template cudaError_t launch_down_w<T, M>(const LevelDev&, const void*, void*, void*, float, const SolveState*,  \
-                                           cudaStream_t);                                                        \
-  template cudaError_t launch_up_w<T, M, false>(const LevelDev&, const void*, const void*, void*, const void*,    \
-                                                float, float, SolveState*, double*, cudaStream_t);               \
-  template cudaError_t launch_up_w<T, M, true>(const LevelDev&, const void*, const void*, void*, const void*,     \
-                                               float, float, SolveState*, double*, cudaStream_t);
+#define NPMG_INST_S2_TB(T, M, TB)                                                                                \
+  template cudaError_t launch_down_w<T, M, TB>(const LevelDev&, const void*, void*, void*, float,                \
+                                               const SolveState*, cudaStream_t);                                 \
+  template cudaError_t launch_up_w<T, M, false, TB>(const LevelDev&, const void*, const void*, void*, const void*, \
+                                                    float, float, SolveState*, double*, cudaStream_t);           \
+  template cudaError_t launch_up_w<T, M, true, TB>(const LevelDev&, const void*, const void*, void*, const void*,  \
+                                                   float, float, SolveState*, double*, cudaStream_t);
 
-NPMG_INST_S2(float, false)
-NPMG_INST_S2(float, true)
-NPMG_INST_S2(__half, false)
-NPMG_INST_S2(__half, true)
-NPMG_INST_S2(__nv_bfloat16, false)
-NPMG_INST_S2(__nv_bfloat16, true)
+NPMG_INST_S2_TB(float, false, float)
+NPMG_INST_S2_TB(float, true, float)
+NPMG_INST_S2_TB(__half, false, __half)
+NPMG_INST_S2_TB(__half, true, __half)
+NPMG_INST_S2_TB(__half, false, float)
+NPMG_INST_S2_TB(__half, true, float)
+NPMG_INST_S2_TB(__nv_bfloat16, false, __nv_bfloat16)
+NPMG_INST_S2_TB(__nv_bfloat16, true, __nv_bfloat16)
+NPMG_INST_S2_TB(__nv_bfloat16, false, float)
+NPMG_INST_S2_TB(__nv_bfloat16, true, float)
 
 }  // namespace npmg

@@ -18,6 +18,7 @@
 // correction and two post sweeps on the up leg (Sec. 2.2), (r, z) and CG's
 // beta on the finest level.
 #include <algorithm>
+#include <type_traits>
 
 #include "launch.h"
 #include "mg_kernels.cuh"
@@ -76,12 +77,12 @@ struct PlaneRegs {
   uint8_t m[KA];
 };
 
-template <typename T, bool MASKED>
-__device__ __forceinline__ void fetch_down(const LevelDev& L, const Col& c, int p, const T* __restrict__ b,
+template <typename TB, bool MASKED>
+__device__ __forceinline__ void fetch_down(const LevelDev& L, const Col& c, int p, const TB* __restrict__ b,
                                            PlaneRegs& r) {
   const bool zin = p >= 0 && p < L.nz;
   const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
-  const T* bp = b + base;
+  const TB* bp = b + base;
   const uint8_t* mp = MASKED ? L.cell + base : nullptr;
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
@@ -95,13 +96,13 @@ __device__ __forceinline__ void fetch_down(const LevelDev& L, const Col& c, int 
   }
 }
 
-template <typename T, bool MASKED>
-__device__ __forceinline__ void fetch_up(const LevelDev& L, const Col& c, int p, const T* __restrict__ b,
+template <typename T, typename TB, bool MASKED>
+__device__ __forceinline__ void fetch_up(const LevelDev& L, const Col& c, int p, const TB* __restrict__ b,
                                          const T* __restrict__ xin, const T* __restrict__ e, float s,
                                          PlaneRegs& r) {
   const bool zin = p >= 0 && p < L.nz;
   const size_t base = (size_t)(zin ? p : 0) * L.ny * L.nx;
-  const T* bp = b + base;
+  const TB* bp = b + base;
   const T* xp = xin + base;
   const T* ep = e + (size_t)(zin ? p >> 1 : 0) * (L.ny >> 1) * (L.nx >> 1);
   const uint8_t* mp = MASKED ? L.cell + base : nullptr;
@@ -152,8 +153,8 @@ __device__ __forceinline__ float defect(const LevelDev& L, const float* Xm, cons
 }  // namespace
 
 // Down leg: x = two sweeps from zero, bcoarse = R (b - A' x).
-template <typename T, bool MASKED>
-__global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restrict__ b, T* __restrict__ x,
+template <typename T, bool MASKED, typename TB>
+__global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const TB* __restrict__ b, T* __restrict__ x,
                                                T* __restrict__ bcoarse, float omega, int zr,
                                                const SolveState* __restrict__ st) {
   chain_enter();
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restri
   const Col c = col_of(L, zr);
   const int tid = threadIdx.x;
   PlaneRegs nxt;
-  fetch_down<T, MASKED>(L, c, c.z0 - 2, b, nxt);
+  fetch_down<TB, MASKED>(L, c, c.z0 - 2, b, nxt);
   for (int p = c.z0 - 2; p <= c.z1 + 1; ++p) {
     // stage A: plane p into the rings; the first sweep from zero is pointwise
     {
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restri
         s1[sl + i] = d > 0.f ? omega_over(omega, d) * nxt.a[k] : 0.f;
       }
     }
-    if (p + 1 <= c.z1 + 1) fetch_down<T, MASKED>(L, c, p + 1, b, nxt);
+    if (p + 1 <= c.z1 + 1) fetch_down<TB, MASKED>(L, c, p + 1, b, nxt);
     __syncthreads();
     // stage B: second sweep on plane q = p - 1, region less one cell
     const int q = p - 1;
@@ -243,9 +244,9 @@ __global__ void __launch_bounds__(NT, 3) k_down_s3(LevelDev L, const T* __restri
 
 // Up leg: xout = two sweeps from x + s P e; on the finest level (r, z) and
 // CG's beta.
-template <typename T, bool MASKED, bool FINEST>
-__global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict__ b, const T* __restrict__ xin,
-                                             T* __restrict__ xout, const T* __restrict__ e, float omega, float s,
+template <typename T, bool MASKED, bool FINEST, typename TB>
+__global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const TB* __restrict__ b, const T* __restrict__ xin,
+                                             TB* __restrict__ xout, const T* __restrict__ e, float omega, float s,
                                              int zr, SolveState* __restrict__ st, double* __restrict__ partials) {
   chain_enter();
   if (st && st->inner_done) return;
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict
   const float keep = 1.f - omega;  // x + (omega/d)(b - d x + nb) = (1 - omega) x + (omega/d)(b + nb)
   float acc = 0.f;
   PlaneRegs nxt;
-  fetch_up<T, MASKED>(L, c, c.z0 - 2, b, xin, e, s, nxt);
+  fetch_up<T, TB, MASKED>(L, c, c.z0 - 2, b, xin, e, s, nxt);
   for (int p = c.z0 - 2; p <= c.z1 + 1; ++p) {
     {
       const int sl = slot3(p) * RN;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict
         s0[sl + i] = nxt.a[k];
       }
     }
-    if (p + 1 <= c.z1 + 1) fetch_up<T, MASKED>(L, c, p + 1, b, xin, e, s, nxt);
+    if (p + 1 <= c.z1 + 1) fetch_up<T, TB, MASKED>(L, c, p + 1, b, xin, e, s, nxt);
     __syncthreads();
     const int q = p - 1;
     if (q >= c.z0 - 1 && c.on && c.tx >= 1 && c.tx <= RX - 2) {
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(NT, 3) k_up_s3(LevelDev L, const T* __restrict
         if (gy < L.ny) {
           const float w = sW[so + i], bv = sB[so + i];
           const float v = w > 0.f ? keep * Xc[i] + w * (bv + nbsum(L, Xm, Xc, Xp, i)) : 0.f;
-          const T zt = cvt<T>(v);
+          const TB zt = cvt<TB>(v);
           xout[base + (size_t)gy * L.nx] = zt;
           if (FINEST) acc = fmaf(bv, ld(&zt, 0), acc);
         }
@@ -391,51 +392,62 @@ static int device_sms() {
   return nsm;
 }
 
-template <typename T, bool MASKED>
+template <typename T, bool MASKED, typename TB>
 cudaError_t launch_down_s3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega,
                            const SolveState* st, cudaStream_t s) {
-  static const int per = s3_per_sm(k_down_s3<T, MASKED>, s3_smem_down());
+  static const int per = s3_per_sm(k_down_s3<T, MASKED, TB>, s3_smem_down());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
-  return launch_chain(k_down_s3<T, MASKED>, s3_grid(L, zr), NT, s3_smem_down(), s, L, (const T*)b, (T*)x, (T*)bcoarse,
-                      omega, zr, st);
+  return launch_chain(k_down_s3<T, MASKED, TB>, s3_grid(L, zr), NT, s3_smem_down(), s, L, (const TB*)b, (T*)x,
+                      (T*)bcoarse, omega, zr, st);
 }
 
-template <typename T, bool MASKED, bool FINEST>
+template <typename T, bool MASKED, bool FINEST, typename TB>
 cudaError_t launch_up_s3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s) {
-  static const int per = s3_per_sm(k_up_s3<T, MASKED, FINEST>, s3_smem_up());
+  static const int per = s3_per_sm(k_up_s3<T, MASKED, FINEST, TB>, s3_smem_up());
   const int zr = s3_run(L, device_sms(), per);
   if (zr <= 0) return cudaErrorInvalidValue;
-  return launch_chain(k_up_s3<T, MASKED, FINEST>, s3_grid(L, zr), NT, s3_smem_up(), s, L, (const T*)b, (const T*)xin,
-                      (T*)xout, (const T*)e, omega, sc, zr, st, partials);
+  return launch_chain(k_up_s3<T, MASKED, FINEST, TB>, s3_grid(L, zr), NT, s3_smem_up(), s, L, (const TB*)b,
+                      (const T*)xin, (TB*)xout, (const T*)e, omega, sc, zr, st, partials);
 }
 
-template <typename T, bool MASKED>
-cudaError_t prepare_s3_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_down_s3<T, MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename T, bool MASKED, typename TB>
+static cudaError_t prepare_s3_pair() {
+  cudaError_t e = cudaFuncSetAttribute(k_down_s3<T, MASKED, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)s3_smem_down());
-
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_up_s3<T, MASKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_up_s3<T, MASKED, false, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s3_smem_up());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_up_s3<T, MASKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_up_s3<T, MASKED, true, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s3_smem_up());
   return e;
 }
 
-#define NPMG_INST_S3(T, M)                                                                                      \
-  template cudaError_t launch_down_s3<T, M>(const LevelDev&, const void*, void*, void*, float, const SolveState*, \
-                                            cudaStream_t);                                                      \
-  template cudaError_t launch_up_s3<T, M, false>(const LevelDev&, const void*, const void*, void*, const void*,  \
-                                                 float, float, SolveState*, double*, cudaStream_t);             \
-  template cudaError_t launch_up_s3<T, M, true>(const LevelDev&, const void*, const void*, void*, const void*,   \
-                                                float, float, SolveState*, double*, cudaStream_t);              \
-  template cudaError_t prepare_s3_kernels<T, M>();
+template <typename T, bool MASKED>
+cudaError_t prepare_s3_kernels() {
+  cudaError_t e = prepare_s3_pair<T, MASKED, T>();
+  if (e == cudaSuccess && !std::is_same<T, float>::value) e = prepare_s3_pair<T, MASKED, float>();
+  return e;
+}
 
-NPMG_INST_S3(float, false)
-NPMG_INST_S3(float, true)
+#define NPMG_INST_S3_TB(T, M, TB)                                                                                \
+  template cudaError_t launch_down_s3<T, M, TB>(const LevelDev&, const void*, void*, void*, float,                \
+                                                const SolveState*, cudaStream_t);                                \
+  template cudaError_t launch_up_s3<T, M, false, TB>(const LevelDev&, const void*, const void*, void*,            \
+                                                     const void*, float, float, SolveState*, double*, cudaStream_t); \
+  template cudaError_t launch_up_s3<T, M, true, TB>(const LevelDev&, const void*, const void*, void*,             \
+                                                    const void*, float, float, SolveState*, double*, cudaStream_t);
+#define NPMG_INST_S3(T, M)                      \
+  template cudaError_t prepare_s3_kernels<T, M>(); \
+  NPMG_INST_S3_TB(T, M, T)                      \
+  NPMG_INST_S3_TB(T, M, float)
+
+template cudaError_t prepare_s3_kernels<float, false>();
+template cudaError_t prepare_s3_kernels<float, true>();
+NPMG_INST_S3_TB(float, false, float)
+NPMG_INST_S3_TB(float, true, float)
 NPMG_INST_S3(__half, false)
 NPMG_INST_S3(__half, true)
 NPMG_INST_S3(__nv_bfloat16, false)
