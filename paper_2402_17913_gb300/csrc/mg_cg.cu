@@ -6,6 +6,8 @@
 // thread and in float64 across the block and the grid (fixed order, so
 // results are reproducible run to run).
 #include <math.h>
+#include <stdlib.h>
+#include <type_traits>
 
 #include "launch.h"
 #include "mg_kernels.cuh"
@@ -290,9 +292,119 @@ __global__ void __launch_bounds__(256) k_xr_update(LevelDev L, const T* __restri
   }
 }
 
+// The same update for float32 3D vectors, marching along z: a block owns
+// 8 rows x 128 cells (a warp per row, 4 cells per lane) and a run of planes;
+// p = z + beta p_old of the planes below, at and above the current one stay
+// in registers, x-neighbours come by shuffles (lanes 0 and 31 load the cell
+// beyond the strip) and y-neighbours from the rows of the adjacent warps,
+// which those warps have just loaded (L1).  z and p_old are read from DRAM
+// about once instead of once per neighbour.
+__device__ __forceinline__ void p_row(const float* __restrict__ z, const float* __restrict__ pold, size_t i, bool in,
+                                      bool first, float beta, float (&v)[4]) {
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), q = a;
+  if (in) {
+    a = *reinterpret_cast<const float4*>(z + i);
+    if (!first) q = *reinterpret_cast<const float4*>(pold + i);
+  }
+  v[0] = fmaf(beta, q.x, a.x);
+  v[1] = fmaf(beta, q.y, a.y);
+  v[2] = fmaf(beta, q.z, a.z);
+  v[3] = fmaf(beta, q.w, a.w);
+}
+
+template <bool MASKED>
+__global__ void __launch_bounds__(256) k_p_update_z(LevelDev L, const float* __restrict__ z,
+                                                    const float* __restrict__ pold, float* __restrict__ pnew,
+                                                    float* __restrict__ Ap, int zr, SolveState* __restrict__ st,
+                                                    double* __restrict__ partials) {
+  chain_enter();
+  if (st->inner_done) return;
+  const bool first = st->first || !st->krylov;
+  const float beta = first ? 0.f : (float)st->beta;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gx = blockIdx.x * 128 + 4 * lane, y = blockIdx.y * 8 + w;
+  const int zs = blockIdx.z * zr, ze = min(zs + zr, L.nz);
+  const bool ox = gx < L.nx, yin = y < L.ny;
+  const bool own = ox && yin, hasu = own && y > 0, hasd = own && y + 1 < L.ny;
+  const size_t sxy = (size_t)L.nx * L.ny;
+  // the cells beyond the strip: lane 0 the left one, lane 31 the right one
+  const int hx = lane == 0 ? gx - 1 : gx + 4;
+  const bool hin = (lane == 0 || lane == 31) && yin && hx >= 0 && hx < L.nx;
+  float acc = 0.f;
+  float pm[4], pc[4], pp[4];
+  p_row(z, pold, (size_t)(zs - 1) * sxy + (size_t)y * L.nx + gx, own && zs > 0, first, beta, pm);
+  p_row(z, pold, (size_t)zs * sxy + (size_t)y * L.nx + gx, own, first, beta, pc);
+  for (int q = zs; q < ze; ++q) {
+    const size_t i = (size_t)q * sxy + (size_t)y * L.nx + gx;
+    float pu[4], pd[4];
+    p_row(z, pold, i + sxy, own && q + 1 < L.nz, first, beta, pp);
+    p_row(z, pold, i - L.nx, hasu, first, beta, pu);
+    p_row(z, pold, i + L.nx, hasd, first, beta, pd);
+    float ph = 0.f;
+    if (hin) {
+      const size_t ih = (size_t)q * sxy + (size_t)y * L.nx + hx;
+      ph = first ? z[ih] : fmaf(beta, pold[ih], z[ih]);
+    }
+    uint8_t m[4] = {0, 0, 0, 0};
+    if (own) cells4<MASKED>(L, i, gx, m);
+    const float up = __shfl_up_sync(0xffffffffu, pc[3], 1);
+    const float dn = __shfl_down_sync(0xffffffffu, pc[0], 1);
+    const float left = lane == 0 ? ph : up, right = lane == 31 ? ph : dn;
+    float pv[4], av[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float l = k == 0 ? left : pc[k - 1], r = k == 3 ? right : pc[k + 1];
+      const float nb = fmaf(L.wx, l + r, fmaf(L.wy, pu[k] + pd[k], L.wz * (pm[k] + pp[k])));
+      if (own && m[k]) {
+        pv[k] = pc[k];
+        av[k] = diag_at<3, MASKED>(L, gx + k, y, q, m[k]) * pc[k] - nb;
+      } else {
+        pv[k] = 0.f;
+        av[k] = 0.f;
+      }
+      acc = fmaf(pv[k], av[k], acc);
+    }
+    if (own) {
+      *reinterpret_cast<float4*>(pnew + i) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      *reinterpret_cast<float4*>(Ap + i) = make_float4(av[0], av[1], av[2], av[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pm[k] = pc[k];
+      pc[k] = pp[k];
+    }
+  }
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntPAP], &tot)) {
+    if (threadIdx.x == 0) {
+      st->pAp = tot;
+      st->alpha = st->krylov ? st->rz / tot : 1.0;
+    }
+  }
+}
+
+// z-run of the marching update: about four blocks per SM over the level.
+static int pz_run(const LevelDev& L) {
+  const long cols = (long)((L.nx + 127) / 128) * ((L.ny + 7) / 8);
+  const long target = (long)sm_count() * 4;
+  long runs = (target + cols - 1) / cols;
+  if (runs < 1) runs = 1;
+  if (runs > L.nz) runs = L.nz;
+  return (int)((L.nz + runs - 1) / runs);
+}
+
 template <int DIM, typename T, bool MASKED>
 cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, void* pnew, void* Ap,
                             SolveState* st, double* partials, cudaStream_t s) {
+  if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+    const bool aligned = (((uintptr_t)z | (uintptr_t)pold | (uintptr_t)pnew | (uintptr_t)Ap) & 15) == 0;
+    if (aligned && L.nx % 4 == 0 && getenv("NPMG_NO_PZ") == nullptr) {
+      const int zr = pz_run(L);
+      const dim3 g((L.nx + 127) / 128, (L.ny + 7) / 8, (L.nz + zr - 1) / zr);
+      return launch_chain(k_p_update_z<MASKED>, g, 256, 0, s, L, (const float*)z, (const float*)pold, (float*)pnew,
+                          (float*)Ap, zr, st, partials);
+    }
+  }
   return launch_chain(k_p_update<DIM, T, MASKED>, row_grid(L), 256, 0, s, L, (const T*)z, (const T*)pold, (T*)pnew,
                       (T*)Ap, st, partials);
 }
