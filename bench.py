@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--guess", default="zero", choices=["zero", "net"],
                     help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
+    ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1],
+                    help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
@@ -239,28 +241,41 @@ def recorded_traffic(workload, cls):
 GUESS_PAIRS, GUESS_CROP, GUESS_BATCH, GUESS_LR = 5000, 64, 8, 1e-3
 
 
-def train_guess(L, ns, wl, u, v, w, p, solid_t, train_steps):
+def train_guess(L, ns, wl, u, v, w, p, solid_t, train_steps, level):
     """Runs the seeded flow from its initial state, cutting each step's
-    (b, p^n, dp) into 64^3 crops until GUESS_PAIRS are stored, then trains
-    the network on them with the residual loss; returns a dict with the
-    handle and the training record."""
+    (b, p^n, dp) into crops until GUESS_PAIRS are stored, then trains the
+    network on them with the residual loss; returns a dict with the handle
+    and the training record.  At level 1 the fields are first restricted once
+    (the network then runs on the coarsened grid) and crops are 32^3 with
+    spacing 2."""
     import torch
+    crop = GUESS_CROP >> level
     g = L.gn_create(I.convnet_weights(0, last_scale=1e-3))
-    L.gn_dataset_reserve(g, (GUESS_CROP,) * 3, GUESS_PAIRS, 1.0)
+    L.gn_dataset_reserve(g, (crop,) * 3, GUESS_PAIRS, float(1 << level))
+    cells = tuple(c >> level for c in wl.cells)
+    if level:
+        nc = cells[0] * cells[1] * cells[2]
+        coarse = [torch.empty(nc, dtype=torch.float32, device=p.device) for _ in range(3)]
+        solid_c = torch.empty(nc, dtype=torch.uint8, device=p.device)
     t0 = time.perf_counter()
     gen_steps = 0
     while L.gn_dataset_size(g) < GUESS_PAIRS:
         L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL, stats=False)
-        b_ptr, dp_ptr = L.ns_last_fields(ns)
-        L.gn_dataset_add(g, wl.cells, b_ptr, p, dp_ptr, solid_t)
+        if level:
+            L.ns_coarse_fields(ns, p, coarse[0], coarse[1], coarse[2], solid_c)
+            L.gn_dataset_add(g, cells, coarse[0], coarse[1], coarse[2], solid_c)
+        else:
+            b_ptr, dp_ptr = L.ns_last_fields(ns)
+            L.gn_dataset_add(g, cells, b_ptr, p, dp_ptr, solid_t)
         gen_steps += 1
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     losses = L.gn_train(g, train_steps, GUESS_BATCH, 1, GUESS_LR, L.GN_LOSS_RESIDUAL)
     t2 = time.perf_counter()
-    L.ns_set_guess(ns, g)
+    L.ns_set_guess_level(ns, g, level)
     tail = float(np.mean(losses[-50:]))
-    return {"handle": g, "pairs": GUESS_PAIRS, "crop": GUESS_CROP, "generation_steps": gen_steps,
+    return {"handle": g, "level": level, "net_cells": list(cells), "pairs": GUESS_PAIRS, "crop": crop,
+            "generation_steps": gen_steps,
             "generation_s": round(t1 - t0, 2), "train_steps": train_steps, "batch": GUESS_BATCH, "lr": GUESS_LR,
             "train_s": round(t2 - t1, 2), "loss_first50": float(np.mean(losses[:50])), "loss_last50": tail,
             "train_relres_last50": float(np.sqrt(2.0 * tail))}
@@ -275,19 +290,22 @@ def guess_report(L, guess, step_stats, ns, wl, u, v, w, p, compare=5):
     pairs = []
     for _ in range(compare):
         state = [t.clone() for t in (u, v, w, p)]
-        L.ns_set_guess(ns, guess["handle"])
+        L.ns_set_guess_level(ns, guess["handle"], guess["level"])
         _, sg = L.ns_step(ns, state[0], state[1], state[2], state[3], wl.dt, wl.nu, wl.uin, TOL)
         L.ns_set_guess(ns, None)
         _, sz = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)
         pairs.append((sg["iters"], sz["iters"], sg["ms"], sz["ms"], sg["guess_relres"]))
-    # the network's own forward time at this size
-    out = torch.empty_like(p)
-    b_ptr, _ = L.ns_last_fields(ns)
+    # the network's own forward time at the size it runs on
+    cells = tuple(guess["net_cells"])
+    nc = cells[0] * cells[1] * cells[2]
+    bin_ = torch.randn(nc, device=p.device)
+    pin_ = torch.randn(nc, device=p.device)
+    out = torch.empty_like(bin_)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    L.gn_forward(guess["handle"], wl.cells, b_ptr, p, out)
+    L.gn_forward(guess["handle"], cells, bin_, pin_, out)
     e0.record()
     for _ in range(5):
-        L.gn_forward(guess["handle"], wl.cells, b_ptr, p, out)
+        L.gn_forward(guess["handle"], cells, bin_, pin_, out)
     e1.record()
     torch.cuda.synchronize()
     L.gn_destroy(guess["handle"])
@@ -325,7 +343,7 @@ def run_gpu(args, rank, world):
         stats = []
         guess = None
         if args.config == "ns3d" and args.guess == "net":
-            guess = train_guess(L, ns, wl, u, v, w, p, solid_t, args.train_steps)
+            guess = train_guess(L, ns, wl, u, v, w, p, solid_t, args.train_steps, args.guess_level)
             # the timed run continues from the state the pairs came from
             for d, t in zip(host, fields):
                 d.copy_(t)

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "gn.h"
 #include "launch.h"
 #include "mg_handle.h"
 
@@ -228,7 +229,61 @@ struct ns_handle_s {
   size_t nfaces[3], ncells;
   int nsm;
   gn_handle guess;  // learned initial guess of dp (not owned), or nullptr
+  int guess_level;  // the network runs on the grid coarsened this many times (0 or 1)
+  float* gc;        // coarse b, p^n and dp of the guess (3 x ncells / 8), or nullptr
 };
+
+// ---------------------------------------------------------------------------
+// Grid transfer of the coarse guess.  Restriction is the 2x2x2 average of
+// the cycle (App. B); the coarse guess comes back by trilinear interpolation
+// between coarse-cell centres (weights 3/4 and 1/4 per axis, the nearest
+// coarse cell repeated at the domain faces), so that it carries no
+// cell-to-cell jumps into the fine solve; solid fine cells get 0.
+__global__ void k_restrict_avg(int nx, int ny, int nz, const float* __restrict__ f, float* __restrict__ c) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const size_t n = (size_t)cx * cy * cz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % cx), y = (int)((i / cx) % cy), z = (int)(i / ((size_t)cx * cy));
+    float sum = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const size_t r = ((size_t)(2 * z + dz) * ny + (2 * y + dy)) * nx + 2 * x;
+        sum += f[r] + f[r + 1];
+      }
+    c[i] = 0.125f * sum;
+  }
+}
+
+__global__ void k_prolong_tri(int nx, int ny, int nz, const float* __restrict__ c, const uint8_t* __restrict__ solid,
+                              float* __restrict__ f) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (solid && solid[i]) {
+      f[i] = 0.f;
+      continue;
+    }
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+    // the parent, and the neighbour on the fine cell's side of it
+    const int px = x >> 1, py = y >> 1, pz = z >> 1;
+    const int qx = min(max(px + ((x & 1) ? 1 : -1), 0), cx - 1);
+    const int qy = min(max(py + ((y & 1) ? 1 : -1), 0), cy - 1);
+    const int qz = min(max(pz + ((z & 1) ? 1 : -1), 0), cz - 1);
+    const int X[2] = {px, qx}, Y[2] = {py, qy}, Z[2] = {pz, qz};
+    const float wgt[2] = {0.75f, 0.25f};
+    float v = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+        for (int d = 0; d < 2; ++d)
+          v = fmaf(wgt[a] * wgt[b2] * wgt[d], c[((size_t)Z[a] * cy + Y[b2]) * cx + X[d]], v);
+    f[i] = v;
+  }
+}
 
 static int ns_blocks(const ns_handle_s* n, size_t count) {
   size_t b = (count + 255) / 256;
@@ -350,6 +405,31 @@ mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp) {
   return MG_OK;
 }
 
+mg_status ns_coarse_fields(ns_handle ns, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
+                           uint8_t* d_solid_c, void* stream) {
+  if (!ns || !d_p || !d_b_c || !d_p_c || !d_dp_c || !d_solid_c) {
+    set_error("ns_coarse_fields: NULL argument");
+    return MG_ERR_INVALID;
+  }
+  if (ns->dim != 3 || (ns->cells[0] % 2) || (ns->cells[1] % 2) || (ns->cells[2] % 2)) {
+    set_error("ns_coarse_fields: needs a 3D grid with even sides");
+    return MG_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nx = (int)ns->cells[0], ny = (int)ns->cells[1], nz = (int)ns->cells[2];
+  const int nb = ns_blocks(ns, ns->ncells / 8);
+  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->b, d_b_c);
+  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, d_p, d_p_c);
+  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->dp, d_dp_c);
+  if (ns->solid) {
+    NPMG_CUDA(launch_coarsen_solid(3, ns->cells, ns->solid, d_solid_c, s));
+  } else {
+    NPMG_CUDA(cudaMemsetAsync(d_solid_c, 0, ns->ncells / 8, s));
+  }
+  NPMG_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
 mg_status ns_set_guess(ns_handle ns, gn_handle g) {
   if (!ns) {
     set_error("ns_set_guess: NULL handle");
@@ -360,6 +440,29 @@ mg_status ns_set_guess(ns_handle ns, gn_handle g) {
     return MG_ERR_INVALID;
   }
   ns->guess = g;
+  ns->guess_level = 0;
+  return MG_OK;
+}
+
+mg_status ns_set_guess_level(ns_handle ns, gn_handle g, int level) {
+  if (!ns || (level != 0 && level != 1)) {
+    set_error("ns_set_guess_level: NULL handle or level not 0 / 1");
+    return MG_ERR_INVALID;
+  }
+  const int64_t q = 4 << level;
+  if (g && (ns->dim != 3 || (ns->cells[0] % q) || (ns->cells[1] % q) || (ns->cells[2] % q))) {
+    set_error("ns_set_guess_level: the guess network needs a 3D grid with sides divisible by %d", (int)q);
+    return MG_ERR_INVALID;
+  }
+  if (g && level == 1 && !ns->gc) {
+    if (cudaMalloc((void**)&ns->gc, 3 * (ns->ncells / 8) * sizeof(float)) != cudaSuccess) {
+      ns->gc = nullptr;
+      set_error("ns_set_guess_level: cudaMalloc failed");
+      return MG_ERR_OOM;
+    }
+  }
+  ns->guess = g;
+  ns->guess_level = g ? level : 0;
   return MG_OK;
 }
 
@@ -461,8 +564,26 @@ mg_status ns_step(ns_handle ns, float* d_u, float* d_v, float* d_w, float* d_p, 
   if (ns->guess) {
     // warm start: dp from the network on (b, p^n); the solve restarts from
     // zero when the guess is worse than zero
-    const int64_t cells[3] = {ns->cells[0], ns->cells[1], ns->cells[2]};
-    st = gn_forward(ns->guess, 1, cells, ns->b, d_p, ns->dp, stream);
+    if (ns->guess_level == 0) {
+      const int64_t cells[3] = {ns->cells[0], ns->cells[1], ns->cells[2]};
+      st = gn_forward(ns->guess, 1, cells, ns->b, d_p, ns->dp, stream);
+    } else {
+      // on the grid coarsened once: restrict b and p^n, run the network,
+      // interpolate its dp back
+      const int nx = (int)ns->cells[0], ny = (int)ns->cells[1], nz = (int)ns->cells[2];
+      const size_t nc = ns->ncells / 8;
+      float *bc = ns->gc, *pc = ns->gc + nc, *dc = ns->gc + 2 * nc;
+      const int nb = ns_blocks(ns, nc);
+      k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->b, bc);
+      k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, d_p, pc);
+      const int64_t cc[3] = {nx / 2, ny / 2, nz / 2};
+      st = gn_forward(ns->guess, 1, cc, bc, pc, dc, stream);
+      if (st == MG_OK) {
+        k_prolong_tri<<<ns_blocks(ns, ns->ncells), 256, 0, s>>>(nx, ny, nz, dc, ns->solid, ns->dp);
+        NPMG_CUDA(cudaGetLastError());
+        npmg::gn::g_launches += 3;  // counted with the network's kernels
+      }
+    }
     if (st != MG_OK) return st;
   } else {
     NPMG_CUDA(cudaMemsetAsync(ns->dp, 0, ns->ncells * 4, s));
@@ -489,6 +610,7 @@ mg_status ns_destroy(ns_handle ns) {
   if (!ns) return MG_OK;
   if (ns->mg) mg_destroy(ns->mg);
   if (ns->pool) cudaFree(ns->pool);
+  if (ns->gc) cudaFree(ns->gc);
   delete ns;
   return MG_OK;
 }

@@ -27,7 +27,8 @@ EXPORTED = [
     "mg_create_batched", "mg_solve_batched", "mg_tune_batched", "mg_batched_config", "mg_destroy_batched",
     "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
-    "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches",
+    "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches", "ns_set_guess_level",
+    "ns_coarse_fields",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
@@ -137,6 +138,8 @@ def load():
         "gn_conv3d_wgrad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _i64_3, _vp, ctypes.c_size_t, _vp]),
         "gn_destroy": (ctypes.c_int, [_vp]),
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
+        "ns_set_guess_level": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+        "ns_coarse_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     }
@@ -469,6 +472,15 @@ def gn_destroy(g):
 
 def ns_set_guess(ns, g):
     _check(load().ns_set_guess(ns, g))
+
+
+def ns_set_guess_level(ns, g, level):
+    _check(load().ns_set_guess_level(ns, g, int(level)))
+
+
+def ns_coarse_fields(ns, p, b_c, p_c, dp_c, solid_c, stream=None):
+    """Last step's b, dp and the given p restricted once, solid coarsened."""
+    _check(load().ns_coarse_fields(ns, ptr(p), ptr(b_c), ptr(p_c), ptr(dp_c), ptr(solid_c), stream_ptr(stream)))
 
 
 def ns_last_fields(ns):
