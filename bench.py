@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--guess", default="zero", choices=["zero", "net"],
                     help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
-    ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1, 2],
                     help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,7 +262,7 @@ def train_guess(L, ns, wl, u, v, w, p, solid_t, train_steps, level):
     while L.gn_dataset_size(g) < GUESS_PAIRS:
         L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL, stats=False)
         if level:
-            L.ns_coarse_fields(ns, p, coarse[0], coarse[1], coarse[2], solid_c)
+            L.ns_coarse_fields(ns, level, p, coarse[0], coarse[1], coarse[2], solid_c)
             L.gn_dataset_add(g, cells, coarse[0], coarse[1], coarse[2], solid_c)
         else:
             b_ptr, dp_ptr = L.ns_last_fields(ns)
@@ -344,9 +344,11 @@ def run_gpu(args, rank, world):
         guess = None
         if args.config == "ns3d" and args.guess == "net":
             guess = train_guess(L, ns, wl, u, v, w, p, solid_t, args.train_steps, args.guess_level)
-            # the timed run continues from the state the pairs came from
+            # the timed run restarts from the initial state, so that it solves
+            # the same sequence of problems as the zero-guess run
             for d, t in zip(host, fields):
-                d.copy_(t)
+                t.copy_(d)
+            torch.cuda.synchronize()
 
         def step():
             _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)

@@ -416,23 +416,25 @@ int64_t gn_kernel_launches(void);
 mg_status gn_destroy(gn_handle g);
 mg_status ns_set_guess(ns_handle ns, gn_handle g);
 /* ns_set_guess_level: as ns_set_guess, with the network run on the grid
- * coarsened `level` times (0 or 1).  At level 1 ns_step restricts b and
- * p^n by 2x2x2 averages, runs g there and interpolates its dp back
- * trilinearly (0 on solid cells): an eighth of the network's work, for the
- * smooth part of dp that the cycles are slowest to remove.  g must then be
+ * coarsened `level` times (0, 1 or 2).  ns_step then restricts b and p^n
+ * by 2x2x2 averages, runs g there and interpolates its dp back trilinearly
+ * level by level (0 on solid cells): 1/8 or 1/64 of the network's work, for
+ * the smooth part of dp that the cycles are slowest to remove.  g must be
  * trained on fields coarsened the same way (ns_coarse_fields) with the
- * coarse spacing 2h.  Sides divisible by 4 * 2^level; MG_ERR_OOM when the
- * coarse buffers cannot be allocated. */
+ * coarse spacing 2^level h.  Sides divisible by 4 * 2^level; MG_ERR_OOM when
+ * the coarse buffers cannot be allocated. */
 mg_status ns_set_guess_level(ns_handle ns, gn_handle g, int level);
 /* Device pointers (owned by ns, valid until the next ns_step) of the last
    step's right-hand side b and pressure increment dp (cells each). */
 mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp);
 /* ns_coarse_fields: the last step's b and dp and the given pressure d_p
- * (cells each), restricted once by 2x2x2 averages into caller buffers of
- * cells / 8 floats, and the solid mask coarsened (a coarse cell is solid
- * when all its children are) into d_solid_c (cells / 8 bytes); 3D grids with
- * even sides.  Enqueued on stream. */
-mg_status ns_coarse_fields(ns_handle ns, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
+ * (cells each), restricted `level` times (1 or 2) by 2x2x2 averages into
+ * caller buffers of cells / 8^level floats, and the solid mask coarsened as
+ * often (a coarse cell is solid when all its children are) into d_solid_c
+ * (cells / 8^level bytes); 3D grids with sides divisible by 2^level.
+ * Enqueued on stream; the first call allocates the handle's coarse buffers
+ * (MG_ERR_OOM if that fails). */
+mg_status ns_coarse_fields(ns_handle ns, int level, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
                            uint8_t* d_solid_c, void* stream);
 
 /* The pressure handle inside ns (owned by ns; do not destroy). */

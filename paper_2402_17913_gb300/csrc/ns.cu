@@ -229,9 +229,14 @@ struct ns_handle_s {
   size_t nfaces[3], ncells;
   int nsm;
   gn_handle guess;  // learned initial guess of dp (not owned), or nullptr
-  int guess_level;  // the network runs on the grid coarsened this many times (0 or 1)
-  float* gc;        // coarse b, p^n and dp of the guess (3 x ncells / 8), or nullptr
+  int guess_level;  // the network runs on the grid coarsened this many times (0 .. 2)
+  // coarse fields of the guess, level 1 then level 2 (b, p, dp each), and a
+  // level-1 solid mask, or nullptr until a coarse level is first used
+  float* gc;
+  uint8_t* gsolid;
 };
+
+static constexpr int kMaxGuessLevel = 2;
 
 // ---------------------------------------------------------------------------
 // Grid transfer of the coarse guess.  Restriction is the 2x2x2 average of
@@ -405,26 +410,70 @@ mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp) {
   return MG_OK;
 }
 
-mg_status ns_coarse_fields(ns_handle ns, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
-                           uint8_t* d_solid_c, void* stream) {
-  if (!ns || !d_p || !d_b_c || !d_p_c || !d_dp_c || !d_solid_c) {
-    set_error("ns_coarse_fields: NULL argument");
-    return MG_ERR_INVALID;
+// Level-l coarse buffers of the guess (l = 1, 2): b, p, dp.
+static float* gc_level(ns_handle_s* ns, int l, int which) {
+  const size_t n1 = ns->ncells / 8, n2 = ns->ncells / 64;
+  return l == 1 ? ns->gc + which * n1 : ns->gc + 3 * n1 + which * n2;
+}
+
+static mg_status ensure_guess_buffers(ns_handle_s* ns, const char* who) {
+  if (ns->gc) return MG_OK;
+  const size_t n1 = ns->ncells / 8, n2 = ns->ncells / 64;
+  if (cudaMalloc((void**)&ns->gc, 3 * (n1 + n2) * sizeof(float)) != cudaSuccess) {
+    ns->gc = nullptr;
+    set_error("%s: cudaMalloc of the coarse guess buffers failed", who);
+    return MG_ERR_OOM;
   }
-  if (ns->dim != 3 || (ns->cells[0] % 2) || (ns->cells[1] % 2) || (ns->cells[2] % 2)) {
-    set_error("ns_coarse_fields: needs a 3D grid with even sides");
-    return MG_ERR_INVALID;
+  if (cudaMalloc((void**)&ns->gsolid, n1) != cudaSuccess) {
+    cudaFree(ns->gc);
+    ns->gc = nullptr;
+    ns->gsolid = nullptr;
+    set_error("%s: cudaMalloc of the coarse guess buffers failed", who);
+    return MG_ERR_OOM;
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  return MG_OK;
+}
+
+// Restrict `level` times (1 or 2): out receives the last field (the
+// level-1 one goes to scratch1 when level == 2).
+static void restrict_times(ns_handle_s* ns, int level, const float* f, float* scratch1, float* out, cudaStream_t s) {
   const int nx = (int)ns->cells[0], ny = (int)ns->cells[1], nz = (int)ns->cells[2];
-  const int nb = ns_blocks(ns, ns->ncells / 8);
-  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->b, d_b_c);
-  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, d_p, d_p_c);
-  k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->dp, d_dp_c);
-  if (ns->solid) {
-    NPMG_CUDA(launch_coarsen_solid(3, ns->cells, ns->solid, d_solid_c, s));
+  if (level == 1) {
+    k_restrict_avg<<<ns_blocks(ns, ns->ncells / 8), 256, 0, s>>>(nx, ny, nz, f, out);
   } else {
-    NPMG_CUDA(cudaMemsetAsync(d_solid_c, 0, ns->ncells / 8, s));
+    k_restrict_avg<<<ns_blocks(ns, ns->ncells / 8), 256, 0, s>>>(nx, ny, nz, f, scratch1);
+    k_restrict_avg<<<ns_blocks(ns, ns->ncells / 64), 256, 0, s>>>(nx / 2, ny / 2, nz / 2, scratch1, out);
+  }
+}
+
+mg_status ns_coarse_fields(ns_handle ns, int level, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
+                           uint8_t* d_solid_c, void* stream) {
+  if (!ns || !d_p || !d_b_c || !d_p_c || !d_dp_c || !d_solid_c || level < 1 || level > kMaxGuessLevel) {
+    set_error("ns_coarse_fields: NULL argument or level not 1 / 2");
+    return MG_ERR_INVALID;
+  }
+  const int64_t q = (int64_t)1 << level;
+  if (ns->dim != 3 || (ns->cells[0] % q) || (ns->cells[1] % q) || (ns->cells[2] % q)) {
+    set_error("ns_coarse_fields: needs a 3D grid with sides divisible by %d", (int)q);
+    return MG_ERR_INVALID;
+  }
+  mg_status st = ensure_guess_buffers(ns, "ns_coarse_fields");
+  if (st != MG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* tmp = gc_level(ns, 1, 0);  // level-1 scratch
+  restrict_times(ns, level, ns->b, tmp, d_b_c, s);
+  restrict_times(ns, level, d_p, tmp, d_p_c, s);
+  restrict_times(ns, level, ns->dp, tmp, d_dp_c, s);
+  if (ns->solid) {
+    if (level == 1) {
+      NPMG_CUDA(launch_coarsen_solid(3, ns->cells, ns->solid, d_solid_c, s));
+    } else {
+      const int64_t c1[3] = {ns->cells[0] / 2, ns->cells[1] / 2, ns->cells[2] / 2};
+      NPMG_CUDA(launch_coarsen_solid(3, ns->cells, ns->solid, ns->gsolid, s));
+      NPMG_CUDA(launch_coarsen_solid(3, c1, ns->gsolid, d_solid_c, s));
+    }
+  } else {
+    NPMG_CUDA(cudaMemsetAsync(d_solid_c, 0, ns->ncells >> (3 * level), s));
   }
   NPMG_CUDA(cudaGetLastError());
   return MG_OK;
@@ -445,21 +494,18 @@ mg_status ns_set_guess(ns_handle ns, gn_handle g) {
 }
 
 mg_status ns_set_guess_level(ns_handle ns, gn_handle g, int level) {
-  if (!ns || (level != 0 && level != 1)) {
-    set_error("ns_set_guess_level: NULL handle or level not 0 / 1");
+  if (!ns || level < 0 || level > kMaxGuessLevel) {
+    set_error("ns_set_guess_level: NULL handle or level not 0 .. 2");
     return MG_ERR_INVALID;
   }
-  const int64_t q = 4 << level;
+  const int64_t q = (int64_t)4 << level;
   if (g && (ns->dim != 3 || (ns->cells[0] % q) || (ns->cells[1] % q) || (ns->cells[2] % q))) {
     set_error("ns_set_guess_level: the guess network needs a 3D grid with sides divisible by %d", (int)q);
     return MG_ERR_INVALID;
   }
-  if (g && level == 1 && !ns->gc) {
-    if (cudaMalloc((void**)&ns->gc, 3 * (ns->ncells / 8) * sizeof(float)) != cudaSuccess) {
-      ns->gc = nullptr;
-      set_error("ns_set_guess_level: cudaMalloc failed");
-      return MG_ERR_OOM;
-    }
+  if (g && level > 0) {
+    mg_status st = ensure_guess_buffers(ns, "ns_set_guess_level");
+    if (st != MG_OK) return st;
   }
   ns->guess = g;
   ns->guess_level = g ? level : 0;
@@ -568,20 +614,24 @@ mg_status ns_step(ns_handle ns, float* d_u, float* d_v, float* d_w, float* d_p, 
       const int64_t cells[3] = {ns->cells[0], ns->cells[1], ns->cells[2]};
       st = gn_forward(ns->guess, 1, cells, ns->b, d_p, ns->dp, stream);
     } else {
-      // on the grid coarsened once: restrict b and p^n, run the network,
-      // interpolate its dp back
+      // on the coarsened grid: restrict b and p^n, run the network,
+      // interpolate its dp back level by level (solid fine cells get 0)
+      const int lv = ns->guess_level;
       const int nx = (int)ns->cells[0], ny = (int)ns->cells[1], nz = (int)ns->cells[2];
-      const size_t nc = ns->ncells / 8;
-      float *bc = ns->gc, *pc = ns->gc + nc, *dc = ns->gc + 2 * nc;
-      const int nb = ns_blocks(ns, nc);
-      k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, ns->b, bc);
-      k_restrict_avg<<<nb, 256, 0, s>>>(nx, ny, nz, d_p, pc);
-      const int64_t cc[3] = {nx / 2, ny / 2, nz / 2};
+      float *bc = gc_level(ns, lv, 0), *pc = gc_level(ns, lv, 1), *dc = gc_level(ns, lv, 2);
+      restrict_times(ns, lv, ns->b, gc_level(ns, 1, 0), bc, s);
+      restrict_times(ns, lv, d_p, gc_level(ns, 1, 1), pc, s);
+      const int64_t cc[3] = {nx >> lv, ny >> lv, nz >> lv};
       st = gn_forward(ns->guess, 1, cc, bc, pc, dc, stream);
       if (st == MG_OK) {
+        if (lv == 2) {
+          float* d1 = gc_level(ns, 1, 2);
+          k_prolong_tri<<<ns_blocks(ns, ns->ncells / 8), 256, 0, s>>>(nx / 2, ny / 2, nz / 2, dc, nullptr, d1);
+          dc = d1;
+        }
         k_prolong_tri<<<ns_blocks(ns, ns->ncells), 256, 0, s>>>(nx, ny, nz, dc, ns->solid, ns->dp);
         NPMG_CUDA(cudaGetLastError());
-        npmg::gn::g_launches += 3;  // counted with the network's kernels
+        npmg::gn::g_launches += 1 + 2 * lv;  // counted with the network's kernels
       }
     }
     if (st != MG_OK) return st;
@@ -611,6 +661,7 @@ mg_status ns_destroy(ns_handle ns) {
   if (ns->mg) mg_destroy(ns->mg);
   if (ns->pool) cudaFree(ns->pool);
   if (ns->gc) cudaFree(ns->gc);
+  if (ns->gsolid) cudaFree(ns->gsolid);
   delete ns;
   return MG_OK;
 }

@@ -139,7 +139,7 @@ def load():
         "gn_destroy": (ctypes.c_int, [_vp]),
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
         "ns_set_guess_level": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
-        "ns_coarse_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "ns_coarse_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     }
@@ -478,9 +478,10 @@ def ns_set_guess_level(ns, g, level):
     _check(load().ns_set_guess_level(ns, g, int(level)))
 
 
-def ns_coarse_fields(ns, p, b_c, p_c, dp_c, solid_c, stream=None):
-    """Last step's b, dp and the given p restricted once, solid coarsened."""
-    _check(load().ns_coarse_fields(ns, ptr(p), ptr(b_c), ptr(p_c), ptr(dp_c), ptr(solid_c), stream_ptr(stream)))
+def ns_coarse_fields(ns, level, p, b_c, p_c, dp_c, solid_c, stream=None):
+    """Last step's b, dp and the given p restricted `level` times, solid coarsened."""
+    _check(load().ns_coarse_fields(ns, int(level), ptr(p), ptr(b_c), ptr(p_c), ptr(dp_c), ptr(solid_c),
+                                   stream_ptr(stream)))
 
 
 def ns_last_fields(ns):
