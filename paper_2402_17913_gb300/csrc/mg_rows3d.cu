@@ -345,40 +345,69 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
   }
 }
 
+// Work of a block: with `units` == 0 one z-run of zr planes of the column
+// (blockIdx.x, blockIdx.y); otherwise the range [blockIdx.x * units,
+// (blockIdx.x + 1) * units) of column-major (column, plane) units, which may
+// end one column's planes and start the next column's (one run each).
+struct Sched {
+  int zr, units;
+};
+
+template <typename F>
+__device__ __forceinline__ void for_each_run(const LevelDev& L, Sched sc, F&& run) {
+  const int strips = (L.nx + 32 * V - 1) / (32 * V);
+  if (sc.units == 0) {
+    const int z0 = blockIdx.z * sc.zr;
+    run(blockIdx.x * 32 * V, blockIdx.y * TY, z0, min(z0 + sc.zr, L.nz));
+    return;
+  }
+  const long total = (long)strips * ((L.ny + TY - 1) / TY) * L.nz;
+  long u = (long)blockIdx.x * sc.units;
+  const long uend = min(u + sc.units, total);
+  while (u < uend) {
+    const int col = (int)(u / L.nz), z0 = (int)(u % L.nz);
+    const int z1 = (int)min((long)L.nz, z0 + (uend - u));
+    run((col % strips) * 32 * V, (col / strips) * TY, z0, z1);
+    u += z1 - z0;
+    __syncthreads();  // the next run refills the rings and plane buffers
+  }
+}
+
 template <typename T, bool MASKED, bool FINEST, typename TB>
 __global__ void __launch_bounds__(NT, 1) k_up_r3(LevelDev L, const TB* __restrict__ b, const T* __restrict__ xin,
                                                  TB* __restrict__ xout, const T* __restrict__ e, float omega, float s,
-                                                 int zr, SolveState* __restrict__ st, double* __restrict__ partials) {
+                                                 Sched sc, SolveState* __restrict__ st, double* __restrict__ partials) {
   chain_enter();
   if (st && st->inner_done) return;
   using S = Lay<T, TB, MASKED, true>;
   extern __shared__ __align__(16) unsigned char smem_r3[];
-  const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zr, z1 = min(z0 + zr, L.nz);
   fill_lut(L, omega, reinterpret_cast<float*>(smem_r3 + S::LUT));
   // zero the plane buffers (the halo cells of rows no lane writes stay 0)
   for (int k = threadIdx.x; k < 6 * PLANE / 4; k += NT)
     reinterpret_cast<float4*>(smem_r3 + S::P0)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const Lane c = lane_of(L, x0, y0);
-  unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
-#pragma unroll
-  for (int i = 0; i < kD; ++i) up_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, xin, e, ring + i * S::SLOT);
-  __syncthreads();
-  UpRegs R;
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int j = 0; j < V + 1; ++j) R.b[k][j] = R.w[k][j] = 0.f;
   float acc = 0.f;
-  const int n = z1 - z0 + 4;
-  for (int i = 0; i < n; i += 3) {
-    up_step<T, TB, MASKED, FINEST, 0, 2, 1>(L, c, i, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
-    if (i + 1 >= n) break;
-    up_step<T, TB, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
-    if (i + 2 >= n) break;
-    up_step<T, TB, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  for_each_run(L, sc, [&](int x0, int y0, int z0, int z1) {
+    const Lane c = lane_of(L, x0, y0);
+    unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
+#pragma unroll
+    for (int i = 0; i < kD; ++i)
+      up_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, xin, e, ring + i * S::SLOT);
+    __syncthreads();
+    UpRegs R;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < V + 1; ++j) R.b[k][j] = R.w[k][j] = 0.f;
+    const int n = z1 - z0 + 4;
+    for (int i = 0; i < n; i += 3) {
+      up_step<T, TB, MASKED, FINEST, 0, 2, 1>(L, c, i, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+      if (i + 1 >= n) break;
+      up_step<T, TB, MASKED, FINEST, 1, 0, 2>(L, c, i + 1, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+      if (i + 2 >= n) break;
+      up_step<T, TB, MASKED, FINEST, 2, 1, 0>(L, c, i + 2, z0, z1, omega, s, b, xin, e, xout, smem_r3, R, acc);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  });
   if (FINEST) {
     double tot;
     if (grid_sum_last((double)acc, partials, &st->counter[kCntRZ], &tot)) {
@@ -526,39 +555,40 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
 
 template <typename T, bool MASKED, typename TB>
 __global__ void __launch_bounds__(NT, 1) k_down_r3(LevelDev L, const TB* __restrict__ b, T* __restrict__ x,
-                                                   T* __restrict__ bcoarse, float omega, int zr,
+                                                   T* __restrict__ bcoarse, float omega, Sched sc,
                                                    const SolveState* __restrict__ st) {
   chain_enter();
   if (st && st->inner_done) return;
   using S = Lay<T, TB, MASKED, false>;
   extern __shared__ __align__(16) unsigned char smem_r3[];
-  const int x0 = blockIdx.x * 32 * V, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zr, z1 = min(z0 + zr, L.nz);
   fill_lut(L, omega, reinterpret_cast<float*>(smem_r3 + S::LUT));
   for (int k = threadIdx.x; k < 6 * PLANE / 4; k += NT)
     reinterpret_cast<float4*>(smem_r3 + S::P0)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const Lane c = lane_of(L, x0, y0);
-  unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
+  for_each_run(L, sc, [&](int x0, int y0, int z0, int z1) {
+    const Lane c = lane_of(L, x0, y0);
+    unsigned char* ring = smem_r3 + S::RG + c.warp * (kRS * S::SLOT);
 #pragma unroll
-  for (int i = 0; i < kD; ++i) down_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, ring + i * S::SLOT);
-  __syncthreads();
-  DownRegs R;
+    for (int i = 0; i < kD; ++i)
+      down_issue<T, TB, MASKED>(L, c, z0 - 2 + i, z0 - 2 + i <= z1 + 1, b, ring + i * S::SLOT);
+    __syncthreads();
+    DownRegs R;
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int j = 0; j < V + 1; ++j) {
-      R.b[k][j] = R.w[k][j] = 0.f;
-      if (j < V) R.d[k][j] = 0.f;
+      for (int j = 0; j < V + 1; ++j) {
+        R.b[k][j] = R.w[k][j] = 0.f;
+        if (j < V) R.d[k][j] = 0.f;
+      }
+    const int n = z1 - z0 + 4;
+    for (int i = 0; i < n; i += 3) {
+      down_step<T, TB, MASKED, 0, 2, 1>(L, c, i, z0, z1, omega, b, x, bcoarse, smem_r3, R);
+      if (i + 1 >= n) break;
+      down_step<T, TB, MASKED, 1, 0, 2>(L, c, i + 1, z0, z1, omega, b, x, bcoarse, smem_r3, R);
+      if (i + 2 >= n) break;
+      down_step<T, TB, MASKED, 2, 1, 0>(L, c, i + 2, z0, z1, omega, b, x, bcoarse, smem_r3, R);
     }
-  const int n = z1 - z0 + 4;
-  for (int i = 0; i < n; i += 3) {
-    down_step<T, TB, MASKED, 0, 2, 1>(L, c, i, z0, z1, omega, b, x, bcoarse, smem_r3, R);
-    if (i + 1 >= n) break;
-    down_step<T, TB, MASKED, 1, 0, 2>(L, c, i + 1, z0, z1, omega, b, x, bcoarse, smem_r3, R);
-    if (i + 2 >= n) break;
-    down_step<T, TB, MASKED, 2, 1, 0>(L, c, i + 2, z0, z1, omega, b, x, bcoarse, smem_r3, R);
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  });
 }
 
 }  // namespace
@@ -576,10 +606,19 @@ static int r3_sms() {
   return nsm;
 }
 
-// z-run length (even): one block per SM, so the run count minimises
-// waves x (run + 4 halo planes).
-static int r3_run(const LevelDev& L) {
-  const long cols = (long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + TY - 1) / TY);
+// Schedule of a level (one block per SM): uniform z-runs of zr planes per
+// column, the run count minimising waves x (zr + 4 halo planes); or an even
+// split of the column-major (column, plane) units over one block per SM,
+// each block paying 4 halo planes per column it touches.  The cheaper of the
+// two by that count (NPMG_ROWS3D_SPLIT=0 keeps the uniform one).
+struct R3Plan {
+  Sched sc;
+  dim3 grid;
+};
+
+static R3Plan r3_plan(const LevelDev& L) {
+  const long strips = (L.nx + 32 * V - 1) / (32 * V), tiles = (L.ny + TY - 1) / TY;
+  const long cols = strips * tiles;
   const long nsm = r3_sms();
   long best = -1, best_zr = L.nz;
   for (int runs = 1; runs <= L.nz / 2; ++runs) {
@@ -593,11 +632,22 @@ static int r3_run(const LevelDev& L) {
       best_zr = zr;
     }
   }
-  return (int)best_zr;
-}
-
-static dim3 r3_grid(const LevelDev& L, int zr) {
-  return dim3((L.nx + 32 * V - 1) / (32 * V), (L.ny + TY - 1) / TY, (L.nz + zr - 1) / zr);
+  R3Plan p;
+  p.sc.zr = (int)best_zr;
+  p.sc.units = 0;
+  p.grid = dim3((unsigned)strips, (unsigned)tiles, (unsigned)((L.nz + best_zr - 1) / best_zr));
+  const char* e = getenv("NPMG_ROWS3D_SPLIT");
+  if (e && atoi(e) == 0) return p;
+  const long total = cols * L.nz;
+  long units = (total + nsm - 1) / nsm;
+  units = (units + 1) / 2 * 2;  // runs start on even planes (restriction pairs)
+  const long touched = (units + L.nz - 2) / L.nz + 1;  // columns one range can reach
+  const long cost = units + 4 * touched;
+  if (cost < best) {
+    p.sc.units = (int)units;
+    p.grid = dim3((unsigned)((total + units - 1) / units), 1, 1);
+  }
+  return p;
 }
 
 // Smallest level (cells) taken by these kernels: 2^21, or NPMG_ROWS3D_MIN.
@@ -611,17 +661,17 @@ bool rows3d_eligible(int dim, int pre, int post, const LevelDev& L) {
 template <typename T, bool MASKED, typename TB>
 cudaError_t launch_down_r3(const LevelDev& L, const void* b, void* x, void* bcoarse, float omega, const SolveState* st,
                            cudaStream_t s) {
-  const int zr = r3_run(L);
-  return launch_chain(k_down_r3<T, MASKED, TB>, r3_grid(L, zr), NT, (size_t)Lay<T, TB, MASKED, false>::BYTES, s, L,
-                      (const TB*)b, (T*)x, (T*)bcoarse, omega, zr, st);
+  const R3Plan pl = r3_plan(L);
+  return launch_chain(k_down_r3<T, MASKED, TB>, pl.grid, NT, (size_t)Lay<T, TB, MASKED, false>::BYTES, s, L,
+                      (const TB*)b, (T*)x, (T*)bcoarse, omega, pl.sc, st);
 }
 
 template <typename T, bool MASKED, bool FINEST, typename TB>
 cudaError_t launch_up_r3(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, float omega,
                          float sc, SolveState* st, double* partials, cudaStream_t s) {
-  const int zr = r3_run(L);
-  return launch_chain(k_up_r3<T, MASKED, FINEST, TB>, r3_grid(L, zr), NT, (size_t)Lay<T, TB, MASKED, true>::BYTES, s,
-                      L, (const TB*)b, (const T*)xin, (TB*)xout, (const T*)e, omega, sc, zr, st, partials);
+  const R3Plan pl = r3_plan(L);
+  return launch_chain(k_up_r3<T, MASKED, FINEST, TB>, pl.grid, NT, (size_t)Lay<T, TB, MASKED, true>::BYTES, s, L,
+                      (const TB*)b, (const T*)xin, (TB*)xout, (const T*)e, omega, sc, pl.sc, st, partials);
 }
 
 template <typename T, bool MASKED, typename TB>
