@@ -331,13 +331,20 @@ __global__ void __launch_bounds__(256) k_p_update_z(LevelDev L, const float* __r
   const int hx = lane == 0 ? gx - 1 : gx + 4;
   const bool hin = (lane == 0 || lane == 31) && yin && hx >= 0 && hx < L.nx;
   float acc = 0.f;
+  // planes q - 1, q, q + 1 of p, and the raw z / p_old of plane q + 2
+  // loaded one plane ahead (its DRAM latency overlaps plane q's work)
   float pm[4], pc[4], pp[4];
   p_row(z, pold, (size_t)(zs - 1) * sxy + (size_t)y * L.nx + gx, own && zs > 0, first, beta, pm);
   p_row(z, pold, (size_t)zs * sxy + (size_t)y * L.nx + gx, own, first, beta, pc);
+  p_row(z, pold, (size_t)(zs + 1) * sxy + (size_t)y * L.nx + gx, own && zs + 1 < L.nz, first, beta, pp);
   for (int q = zs; q < ze; ++q) {
     const size_t i = (size_t)q * sxy + (size_t)y * L.nx + gx;
+    float4 za = make_float4(0.f, 0.f, 0.f, 0.f), qa = za;
+    if (own && q + 2 < L.nz && q + 1 < ze) {
+      za = *reinterpret_cast<const float4*>(z + i + 2 * sxy);
+      if (!first) qa = *reinterpret_cast<const float4*>(pold + i + 2 * sxy);
+    }
     float pu[4], pd[4];
-    p_row(z, pold, i + sxy, own && q + 1 < L.nz, first, beta, pp);
     p_row(z, pold, i - L.nx, hasu, first, beta, pu);
     p_row(z, pold, i + L.nx, hasd, first, beta, pd);
     float ph = 0.f;
@@ -368,10 +375,12 @@ __global__ void __launch_bounds__(256) k_p_update_z(LevelDev L, const float* __r
       *reinterpret_cast<float4*>(pnew + i) = make_float4(pv[0], pv[1], pv[2], pv[3]);
       *reinterpret_cast<float4*>(Ap + i) = make_float4(av[0], av[1], av[2], av[3]);
     }
+    const float pn[4] = {fmaf(beta, qa.x, za.x), fmaf(beta, qa.y, za.y), fmaf(beta, qa.z, za.z), fmaf(beta, qa.w, za.w)};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       pm[k] = pc[k];
       pc[k] = pp[k];
+      pp[k] = pn[k];
     }
   }
   double tot;
