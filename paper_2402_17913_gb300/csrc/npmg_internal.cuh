@@ -59,8 +59,9 @@ enum Counter { kCntInit = 0, kCntOuter = 1, kCntRZ = 2, kCntPAP = 3, kCntRR = 4,
 // are visible (a no-op when it was launched without the dependency).
 // Nothing may be read or written before this call.  No grid releases its
 // successor early: measured on GB300, successors parked on the SMs from the
-// start of the previous grid made the 2D and 3D solves 5-8% slower, while
-// the release at exit makes the 2D flow step about 1.5% faster.
+// start of the previous grid made the 2D and 3D solves 5-8% slower (1-7%
+// when only grids of at most 32 or 128 blocks release early), while the
+// release at exit makes the 2D flow step about 1.5% faster.
 __device__ __forceinline__ void chain_enter() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
