@@ -650,13 +650,14 @@ static R3Plan r3_plan(const LevelDev& L) {
   return p;
 }
 
-// Smallest level (cells) taken by these kernels: 2^16, or NPMG_ROWS3D_MIN
+// Smallest level (cells) taken by these kernels: 2^15, or NPMG_ROWS3D_MIN
 // (measured on GB300: the 256x128x128 flow step is 15% faster with its
 // 128x64x64 and 64x32x32 levels here than on the z-streaming and tile
-// kernels, the 256^3 solve 1% faster with its 64^3 level here).
+// kernels, the 256^3 solve 3% faster with its 64^3 and 32^3 levels here;
+// the single-block coarse kernel stays faster below).
 bool rows3d_eligible(int dim, int pre, int post, const LevelDev& L) {
   const char* e = getenv("NPMG_ROWS3D_MIN");
-  const size_t lim = e ? (size_t)atol(e) : ((size_t)1 << 16);
+  const size_t lim = e ? (size_t)atol(e) : ((size_t)1 << 15);
   return dim == 3 && pre == 2 && post == 2 && L.nx % 4 == 0 && L.ny % 2 == 0 && L.nz % 2 == 0 && L.nz >= 4 &&
          (size_t)L.nx * L.ny * L.nz >= lim;
 }
