@@ -392,88 +392,6 @@ __global__ void __launch_bounds__(256) k_p_update_z(LevelDev L, const float* __r
   }
 }
 
-// The 2D float32 update marching along y: a warp owns a strip of 128 cells
-// (4 per lane) and a run of rows; p = z + beta p_old of the rows below, at
-// and above the current one stay in registers and the row two ahead is
-// loaded one row early; x-neighbours by shuffles (lanes 0 and 31 load the
-// cell beyond the strip).
-template <bool MASKED>
-__global__ void __launch_bounds__(256) k_p_update_y(LevelDev L, const float* __restrict__ z,
-                                                    const float* __restrict__ pold, float* __restrict__ pnew,
-                                                    float* __restrict__ Ap, int rows, SolveState* __restrict__ st,
-                                                    double* __restrict__ partials) {
-  chain_enter();
-  if (st->inner_done) return;
-  const bool first = st->first || !st->krylov;
-  const float beta = first ? 0.f : (float)st->beta;
-  const int lane = threadIdx.x & 31;
-  const int strips = (L.nx + 127) / 128, runs = (L.ny + rows - 1) / rows;
-  const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
-  float acc = 0.f;
-  if (wid < strips * runs) {  // whole warps
-    const int gx = (wid % strips) * 128 + 4 * lane;
-    const int ys = (wid / strips) * rows, ye = min(ys + rows, L.ny);
-    const bool ox = gx < L.nx;
-    const int hx = lane == 0 ? gx - 1 : gx + 4;
-    const bool hin = (lane == 0 || lane == 31) && hx >= 0 && hx < L.nx;
-    float pm[4], pc[4], pp[4];
-    p_row(z, pold, (size_t)(ys - 1) * L.nx + gx, ox && ys > 0, first, beta, pm);
-    p_row(z, pold, (size_t)ys * L.nx + gx, ox, first, beta, pc);
-    p_row(z, pold, (size_t)(ys + 1) * L.nx + gx, ox && ys + 1 < L.ny, first, beta, pp);
-    for (int y = ys; y < ye; ++y) {
-      const size_t i = (size_t)y * L.nx + gx;
-      float4 za = make_float4(0.f, 0.f, 0.f, 0.f), qa = za;
-      if (ox && y + 2 < L.ny && y + 1 < ye) {
-        za = *reinterpret_cast<const float4*>(z + i + 2 * (size_t)L.nx);
-        if (!first) qa = *reinterpret_cast<const float4*>(pold + i + 2 * (size_t)L.nx);
-      }
-      float ph = 0.f;
-      if (hin) {
-        const size_t ih = (size_t)y * L.nx + hx;
-        ph = first ? z[ih] : fmaf(beta, pold[ih], z[ih]);
-      }
-      uint8_t m[4] = {0, 0, 0, 0};
-      if (ox) cells4<MASKED>(L, i, gx, m);
-      const float up = __shfl_up_sync(0xffffffffu, pc[3], 1);
-      const float dn = __shfl_down_sync(0xffffffffu, pc[0], 1);
-      const float left = lane == 0 ? ph : up, right = lane == 31 ? ph : dn;
-      float pv[4], av[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float l = k == 0 ? left : pc[k - 1], r = k == 3 ? right : pc[k + 1];
-        const float nb = fmaf(L.wx, l + r, L.wy * (pm[k] + pp[k]));
-        if (ox && m[k]) {
-          pv[k] = pc[k];
-          av[k] = diag_at<2, MASKED>(L, gx + k, y, 0, m[k]) * pc[k] - nb;
-        } else {
-          pv[k] = 0.f;
-          av[k] = 0.f;
-        }
-        acc = fmaf(pv[k], av[k], acc);
-      }
-      if (ox) {
-        *reinterpret_cast<float4*>(pnew + i) = make_float4(pv[0], pv[1], pv[2], pv[3]);
-        *reinterpret_cast<float4*>(Ap + i) = make_float4(av[0], av[1], av[2], av[3]);
-      }
-      const float pn[4] = {fmaf(beta, qa.x, za.x), fmaf(beta, qa.y, za.y), fmaf(beta, qa.z, za.z),
-                           fmaf(beta, qa.w, za.w)};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        pm[k] = pc[k];
-        pc[k] = pp[k];
-        pp[k] = pn[k];
-      }
-    }
-  }
-  double tot;
-  if (grid_sum_last((double)acc, partials, &st->counter[kCntPAP], &tot)) {
-    if (threadIdx.x == 0) {
-      st->pAp = tot;
-      st->alpha = st->krylov ? st->rz / tot : 1.0;
-    }
-  }
-}
-
 // z-run of the marching update: about four blocks per SM over the level.
 static int pz_run(const LevelDev& L) {
   const long cols = (long)((L.nx + 127) / 128) * ((L.ny + 7) / 8);
@@ -494,19 +412,6 @@ cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, 
       const dim3 g((L.nx + 127) / 128, (L.ny + 7) / 8, (L.nz + zr - 1) / zr);
       return launch_chain(k_p_update_z<MASKED>, g, 256, 0, s, L, (const float*)z, (const float*)pold, (float*)pnew,
                           (float*)Ap, zr, st, partials);
-    }
-  }
-  if constexpr (DIM == 2 && std::is_same<T, float>::value) {
-    const bool aligned = (((uintptr_t)z | (uintptr_t)pold | (uintptr_t)pnew | (uintptr_t)Ap) & 15) == 0;
-    if (aligned && L.nx % 4 == 0 && L.ny >= 2 && getenv("NPMG_NO_PY") == nullptr) {
-      // rows per warp: about 16 warps per SM, at least 4 rows (so the grid
-      // has no more blocks than the row kernel's)
-      const long strips = (L.nx + 127) / 128;
-      long rows = (strips * L.ny + sm_count() * 16 - 1) / ((long)sm_count() * 16);
-      if (rows < 4) rows = 4;
-      const long warps = strips * ((L.ny + rows - 1) / rows);
-      return launch_chain(k_p_update_y<MASKED>, (unsigned)((warps + 7) / 8), 256, 0, s, L, (const float*)z,
-                          (const float*)pold, (float*)pnew, (float*)Ap, (int)rows, st, partials);
     }
   }
   return launch_chain(k_p_update<DIM, T, MASKED>, row_grid(L), 256, 0, s, L, (const T*)z, (const T*)pold, (T*)pnew,
