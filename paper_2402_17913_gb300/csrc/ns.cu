@@ -109,6 +109,34 @@ __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const
   const float qn_self = qc[i];
   const float q0 = CORR ? 0.5f * (qn_self + qt[i]) : qn_self;
   float adv = 0.f, diff = 0.f;
+  // Faces at least two cells from every side read their neighbours
+  // directly: none of them is clamped, padded or fixed.
+  const bool inner = f[0] >= 2 && f[0] + 2 < F[0] && f[1] >= 2 && f[1] + 2 < F[1] &&
+                     (DIM == 2 || (f[2] >= 2 && f[2] + 2 < F[2]));
+  if (inner) {
+    const size_t sc[3] = {1, (size_t)F[0], (size_t)F[0] * F[1]};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      float Ua;
+      if (a == C) {
+        Ua = qn_self;
+      } else {
+        // component a's face array: cells f-1, f along C, faces j, j+1 along a
+        const size_t A0 = G.n[0] + (a == 0), A1 = G.n[1] + (a == 1);
+        const size_t sa[3] = {1, A0, A0 * A1};
+        const size_t ia = ((size_t)f[2] * A1 + f[1]) * A0 + f[0];
+        const float* qa = Qn.q[a];
+        Ua = 0.25f * ((qa[ia - sa[C]] + qa[ia - sa[C] + sa[a]]) + (qa[ia] + qa[ia + sa[a]]));
+      }
+      float qm = qc[i - sc[a]], qp = qc[i + sc[a]];
+      if (CORR) {
+        qm = 0.5f * (qm + qt[i - sc[a]]);
+        qp = 0.5f * (qp + qt[i + sc[a]]);
+      }
+      adv = fmaf(Ua, (qp - qm) * (0.5f * G.inv_h), adv);
+      diff += (2.f * q0 - qm - qp) * G.inv_h2;
+    }
+  } else {
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     // advecting velocity component a at this C-face (time n)
@@ -132,6 +160,7 @@ __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const
     const float qm = Q(a, -1), qp = Q(a, +1);
     adv = fmaf(Ua, (qp - qm) * (0.5f * G.inv_h), adv);
     diff += (2.f * q0 - qm - qp) * G.inv_h2;
+  }
   }
   // pressure gradient d_C p^n at the face: cells f-1 and f along C; the
   // outflow ghost is 0 (Dirichlet), faces at walls are fixed (skipped above)
