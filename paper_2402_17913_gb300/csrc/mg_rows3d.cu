@@ -41,6 +41,9 @@ constexpr int NW = TY + 4;      // warps = region rows
 constexpr int NT = 32 * NW;     // 640 threads
 constexpr int kD = 2;           // planes in flight ahead of the plane in use
 constexpr int kRS = kD + 1;     // ring slots per warp
+// the register and ring phases coincide: step i uses ring slot i % 3 = C
+// and refills slot (i + kD) % 3 = P (the slot read at step i - 1)
+static_assert(kRS == 3, "ring slots follow the three-step phase");
 constexpr int ROWF = 136;       // floats per buffered row: local x -4 .. 131
 constexpr int PLANE = NW * ROWF;
 
@@ -277,7 +280,7 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
   // A: row (p, y): x + s P e into buffer 0 (own cells and both halo cells)
   cp_wait_ring();
   {
-    const unsigned char* sl = ring + (i % kRS) * S::SLOT;
+    const unsigned char* sl = ring + C * S::SLOT;
     float xv[V], bv[V];
     lds4<T>(sl + c.lane * 4 * S::SZ, xv);
     lds4<TB>(sl + S::BO + c.lane * 4 * S::SB, bv);
@@ -316,7 +319,7 @@ __device__ __forceinline__ void up_step(const LevelDev& L, const Lane& c, int i,
       B0[C * PLANE + c.warp * ROWF + c.hout_off] = flo ? fmaf(s, eh, xo) : 0.f;
     }
   }
-  up_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, xin, e, ring + ((i + kD) % kRS) * S::SLOT);
+  up_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, xin, e, ring + P * S::SLOT);
   __syncthreads();
   const float keep = 1.f - omega;
   // B: first sweep on plane p - 1, rows 1 .. NW - 2
@@ -462,7 +465,7 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
   // A: row (p, y): b, omega / d, d and the first sweep from zero (omega / d) b
   cp_wait_ring();
   {
-    const unsigned char* sl = ring + (i % kRS) * S::SLOT;
+    const unsigned char* sl = ring + C * S::SLOT;
     float bv[V];
     lds4<TB>(sl + S::BO + c.lane * 4 * S::SB, bv);
     const unsigned char* hs = sl + S::HO + (c.lane == 31 ? 32 : 0);
@@ -495,7 +498,7 @@ __device__ __forceinline__ void down_step(const LevelDev& L, const Lane& c, int 
       B0[C * PLANE + c.warp * ROWF + c.hout_off] = lut[64 + qo] * bo;
     }
   }
-  down_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, ring + ((i + kD) % kRS) * S::SLOT);
+  down_issue<T, TB, MASKED>(L, c, p + kD, p + kD <= z1 + 1, b, ring + P * S::SLOT);
   __syncthreads();
   const float keep = 1.f - omega;
   // B: second sweep on plane p - 1, rows 1 .. NW - 2
