@@ -613,7 +613,8 @@ static int r3_sms() {
 // column, the run count minimising waves x (zr + 4 halo planes); or an even
 // split of the column-major (column, plane) units over one block per SM,
 // each block paying 4 halo planes per column it touches.  The cheaper of the
-// two by that count (NPMG_ROWS3D_SPLIT=0 keeps the uniform one).
+// two by that count (NPMG_ROWS3D_SPLIT=0 keeps the uniform one, =2 always
+// splits).
 struct R3Plan {
   Sched sc;
   dim3 grid;
@@ -641,12 +642,13 @@ static R3Plan r3_plan(const LevelDev& L) {
   p.grid = dim3((unsigned)strips, (unsigned)tiles, (unsigned)((L.nz + best_zr - 1) / best_zr));
   const char* e = getenv("NPMG_ROWS3D_SPLIT");
   if (e && atoi(e) == 0) return p;
+  const bool force = e && atoi(e) == 2;
   const long total = cols * L.nz;
   long units = (total + nsm - 1) / nsm;
   units = (units + 1) / 2 * 2;  // runs start on even planes (restriction pairs)
   const long touched = (units + L.nz - 2) / L.nz + 1;  // columns one range can reach
   const long cost = units + 4 * touched;
-  if (cost < best) {
+  if (force || cost < best) {
     p.sc.units = (int)units;
     p.grid = dim3((unsigned)((total + units - 1) / units), 1, 1);
   }

@@ -157,6 +157,23 @@ def test_solve_matches_oracle(L, shape, bc, frac):
     solve_and_check(L, shape, bc, solid, h, b)
 
 
+@pytest.mark.parametrize("shape,bc,frac", CASES)
+def test_streaming_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
+    """The 2D warp and 3D row-warp level kernels, which the default
+    thresholds keep for large levels (>= 2^19 / 2^15 cells), forced onto
+    every eligible level and, in 3D, onto the split (column, plane)
+    schedule: one cycle and full solves (float32 and FP16 level storage)
+    match the oracle with the bounds above."""
+    monkeypatch.setenv("NPMG_STREAM2D_MIN", "0")
+    monkeypatch.setenv("NPMG_ROWS3D_MIN", "0")
+    monkeypatch.setenv("NPMG_ROWS3D_SPLIT", "2")
+    test_one_cycle_matches_oracle(L, shape, bc, frac)
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 2, solid=solid).astype(np.float32)
+    solve_and_check(L, shape, bc, solid, h, b)
+    solve_and_check(L, shape, bc, solid, h, b, prec=1)
+
+
 def test_solve_256_blob_iterations_match_oracle(L):
     """256^2, zero Dirichlet, 8-blob RHS (seed 0), 7 levels: relres 1e-6;
     the refinement loop takes the oracle's number of CG iterations (+-2)."""
