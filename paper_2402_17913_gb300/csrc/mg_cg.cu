@@ -128,9 +128,18 @@ static int sm_count() {
   return n[dev] > 0 ? n[dev] : 148;
 }
 
+static int row_blocks_per_sm() {
+  static int v = 0;
+  if (!v) {
+    const char* e = getenv("NPMG_ROW_BLOCKS_PER_SM");
+    v = (e && atoi(e) > 0) ? atoi(e) : 4;
+  }
+  return v;
+}
+
 static dim3 row_grid(const LevelDev& L) {
   const long groups = (long)((L.nx + 127) / 128) * ((L.ny + 7) / 8) * L.nz;
-  const long cap = (long)sm_count() * 4;
+  const long cap = (long)sm_count() * row_blocks_per_sm();
   return dim3((unsigned)(groups < cap ? groups : cap), 1, 1);
 }
 

@@ -35,10 +35,13 @@ namespace npmg {
 
 namespace {
 
+#ifndef NPMG_R3_TY
+#define NPMG_R3_TY 16
+#endif
 constexpr int V = 4;            // cells per lane
-constexpr int TY = 16;          // output rows of a block
+constexpr int TY = NPMG_R3_TY;  // output rows of a block
 constexpr int NW = TY + 4;      // warps = region rows
-constexpr int NT = 32 * NW;     // 640 threads
+constexpr int NT = 32 * NW;     // threads (640)
 constexpr int kD = 2;           // planes in flight ahead of the plane in use
 constexpr int kRS = kD + 1;     // ring slots per warp
 // the register and ring phases coincide: step i uses ring slot i % 3 = C
