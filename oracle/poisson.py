@@ -236,7 +236,8 @@ class Multigrid:
     Cycle ``'V'``: on each level smooth ``pre`` times, restrict the residual,
     recurse from a zero guess, add ``s`` times the prolonged correction,
     smooth ``post`` times; the coarsest level is solved exactly by a dense LU.
-    ``'W'`` recurses twice.  ``s`` is the coarse-correction scale (1 = the
+    ``'W'`` recurses twice.  ``'sawtooth'`` is the paper's own cycle
+    (``sawtooth_level``).  ``s`` is the coarse-correction scale (1 = the
     plain re-discretised correction).
     """
 
@@ -262,9 +263,41 @@ class Multigrid:
             x = jacobi(lv, x, b, self.omega)
         return x
 
+    def sawtooth_level(self, k, r):
+        """The paper's sawtooth cycle (App. B recursion, under the reading that
+        Eq. e22 is a Jacobi step (r - A T) / A0): the level's residual is
+        restricted to the next level without any smoothing (Eq. r-recur);
+        then, from the coarsest level up, the level's correction is one
+        Jacobi step from zero, r^k / d (Eq. e19), plus s times the prolonged
+        correction of the level below (Eq. e20; at the coarsest level the
+        Jacobi step alone, Eq. e20b), followed by ``post`` relaxed Jacobi
+        sweeps on A x = r^k (Eqs. e21-e23).  No exact coarsest solve."""
+        lv = self.hier[k]
+        d = np.where(lv.diag > 0, lv.diag, 1.0)
+        x = (r / d) * lv.fluid
+        if k < len(self.hier) - 1:
+            ec = self.sawtooth_level(k + 1, restrict(r))
+            x = x + self.s * prolong(ec, lv)
+        for _ in range(self.post):
+            x = jacobi(lv, x, r, self.omega)
+        return x
+
     def precondition(self, r):
         """z = M r: one cycle from a zero guess."""
+        if self.cycle == 'sawtooth':
+            return self.sawtooth_level(0, r)
         return self.cycle_level(0, r, np.zeros_like(r))
+
+    def stationary(self, b, cycles, x0=None):
+        """x <- x + M (b - A x), ``cycles`` times (the cycle as a solver);
+        returns x and the relres after each cycle."""
+        lv = self.hier[0]
+        x = np.zeros_like(b) if x0 is None else x0.copy()
+        hist = []
+        for _ in range(cycles):
+            x = x + self.precondition(residual(lv, b, x))
+            hist.append(relres(lv, b, x))
+        return x, hist
 
 
 # --------------------------------------------------------------------------
