@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--guess", default="zero", choices=["zero", "net"],
                     help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
+    ap.add_argument("--cycle", default="v", choices=["v", "sawtooth"],
+                    help="poisson2d/3d: V(2,2)-preconditioned CG (default) or the paper's sawtooth cycle")
     ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1, 2],
                     help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
@@ -122,17 +124,23 @@ class NS3D:
 
 
 class Poisson:
-    def __init__(self, shape, prec):
+    def __init__(self, shape, prec, cycle="v"):
         self.shape = shape
         self.dim = len(shape)
         self.prec = prec
+        self.cycle = cycle
         self.units = int(np.prod(shape))
         self.name = "poisson%dd_%s_%s" % (self.dim, "x".join(map(str, shape)), prec)
+        if cycle != "v":
+            self.name += "_" + cycle
 
     def config(self):
-        return {"workload": "%dD pressure Poisson, 8 Gaussian blobs, zero Dirichlet" % self.dim,
-                "shape": list(reversed(self.shape)), "solve_rel_tol": TOL, "inner_precision": self.prec,
-                "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
+        c = {"workload": "%dD pressure Poisson, 8 Gaussian blobs, zero Dirichlet" % self.dim,
+             "shape": list(reversed(self.shape)), "solve_rel_tol": TOL, "inner_precision": self.prec,
+             "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
+        if self.cycle == "sawtooth":
+            c["cycle"] = "sawtooth (paper App. B), stationary, coarse scale 1/2, 2 post sweeps"
+        return c
 
 
 class Batched:
@@ -391,9 +399,14 @@ def run_gpu(args, rank, world):
         cleanup = lambda: L.mg_destroy_batched(bh)  # noqa: E731
     else:
         shape = (256, 256) if args.config == "poisson2d" else (256, 256, 256)
-        wl = Poisson(shape, args.prec)
+        wl = Poisson(shape, args.prec, args.cycle)
         h = I.poisson_spacing(shape)
         opt = L.default_options(prec=PREC[args.prec])
+        if args.cycle == "sawtooth":
+            # the paper's cycle as a stationary solver; the re-discretised
+            # coarse levels need the halved correction (the oracle's pin)
+            opt = L.default_options(prec=PREC[args.prec], cycle=L.MG_CYCLE_SAWTOOTH, krylov=0, coarse_scale=0.5,
+                                    max_inner=20000)
         mg = L.mg_create(wl.dim, tuple(reversed(shape)), h, (0,) * (2 * wl.dim), None, opt)
         b_host = torch.from_numpy(I.blob_rhs(shape, 0).astype(np.float32)).pin_memory()
         x_host = torch.zeros_like(b_host).pin_memory()

@@ -85,7 +85,19 @@ typedef struct {
   mg_precision prec;    /* level-array storage (default MG_FP32)               */
   double inner_floor;   /* smallest relative tolerance asked of one inner
                            solve; 0 = default (1e-4)                           */
+  int cycle;            /* MG_CYCLE_V (default): pre sweeps, residual
+                           restriction, exact coarsest solve, post sweeps;
+                           MG_CYCLE_SAWTOOTH: the paper's cycle (App. B
+                           recursion): the residual restricted down with no
+                           smoothing, and on every level from the coarsest up
+                           one Jacobi step from zero r / d plus coarse_scale
+                           times the prolonged correction, then `post` sweeps
+                           (no exact coarsest solve; `pre` is ignored).  With
+                           the re-discretised coarse levels the stationary
+                           sawtooth needs coarse_scale ~ 0.5.                 */
 } mg_options;
+
+enum { MG_CYCLE_V = 0, MG_CYCLE_SAWTOOTH = 1 };
 
 typedef struct {
   int status;           /* mg_status of the solve                             */

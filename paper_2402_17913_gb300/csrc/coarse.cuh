@@ -154,6 +154,11 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
   }
   __syncthreads();
   unsigned cur = 0u;  // bit l: level l's current x is buffer 1
+  // a.pre < 0: the sawtooth recursion (App. B): on the way down x = b / d
+  // (one Jacobi step from zero) and the restricted residual is that of
+  // x = 0, i.e. b; the coarsest level gets the same Jacobi step and the
+  // post sweeps instead of the exact solve
+  const bool saw = a.pre < 0;
   // down legs
   for (int l = 0; l < a.nlev - 1; ++l) {
     const LevelDev& L = a.lv[l];
@@ -167,7 +172,7 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
         int x, y, z;
         g.xyz(i, x, y, z);
         const int p = g.pad(x, y, z);
-        x0[p] = a.pre > 0 ? a.omega * id[p] * b[p] : 0.f;
+        x0[p] = saw ? id[p] * b[p] : (a.pre > 0 ? a.omega * id[p] * b[p] : 0.f);
       }
       __syncthreads();
     }
@@ -193,15 +198,36 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
           for (int ax = 0; ax < 2; ++ax) {
             const int p = g.pad(2 * X0 + ax, 2 * Y0 + ay, 2 * Z0 + az);
             const float idv = id[p];
-            if (idv != 0.f) sum += b[p] - (__frcp_rn(idv) * xl[p] - cl_nb<DIM>(L, g, xl, p));
+            if (idv != 0.f) sum += saw ? b[p] : b[p] - (__frcp_rn(idv) * xl[p] - cl_nb<DIM>(L, g, xl, p));
           }
       bc[c.pad(X0, Y0, Z0)] = sum * inv_children;
     }
     (void)CL;
     __syncthreads();
   }
-  // coarsest: x = A^-1 b in float64, one warp per row
-  {
+  // coarsest: x = A^-1 b in float64, one warp per row (sawtooth: the
+  // Jacobi step from zero and the post sweeps)
+  if (saw) {
+    const int l = a.nlev - 1;
+    const LevelDev& L = a.lv[l];
+    const CGeo c = G(l);
+    const float* bc = B(c);
+    const float* id = ID(c);
+    float* x0 = X(c, 0);
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
+      int x, y, z;
+      c.xyz(i, x, y, z);
+      const int p = c.pad(x, y, z);
+      x0[p] = id[p] * bc[p];
+    }
+    __syncthreads();
+    int k = 0;
+    for (int j = 1; j <= a.post; ++j) {
+      cl_sweep<DIM>(L, c, X(c, k), X(c, 1 - k), bc, id, a.omega);
+      k = 1 - k;
+    }
+    if (k) cur |= 1u << l;
+  } else {
     const CGeo c = G(a.nlev - 1);
     const int n = a.ncoarse;
     float* xc = X(c, 0);

@@ -105,7 +105,9 @@ static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevel
   if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
     return launch_down_r3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
   if (DIM == 3 && h->s3_ok[k]) return launch_down_s3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
-  return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], h->opt.pre, om, st, s);
+  // pre = -1 asks the tile kernel for the sawtooth down leg
+  const int pre = h->opt.cycle == MG_CYCLE_SAWTOOTH ? -1 : h->opt.pre;
+  return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], pre, om, st, s);
 }
 
 template <int DIM, typename T, bool M, bool F, typename TB>
@@ -343,6 +345,7 @@ void mg_default_options(mg_options* o) {
   o->max_outer = 12;
   o->prec = MG_FP32;
   o->inner_floor = 0.0;
+  o->cycle = MG_CYCLE_V;
 }
 
 mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const double spacing[3], const int bc[6],
@@ -368,9 +371,10 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     return MG_ERR_INVALID;
   }
   if (!(o.omega > 0.0 && o.omega <= 2.0) || !(o.coarse_scale > 0.0) || o.max_inner < 1 || o.max_outer < 1 ||
-      o.prec < MG_FP32 || o.prec > MG_MIXED_BF16 || o.levels < 0 || o.levels > kMaxLevels) {
+      o.prec < MG_FP32 || o.prec > MG_MIXED_BF16 || o.levels < 0 || o.levels > kMaxLevels ||
+      (o.cycle != MG_CYCLE_V && o.cycle != MG_CYCLE_SAWTOOTH)) {
     set_error("mg_create: invalid options (omega in (0,2], coarse_scale > 0, max_inner/max_outer >= 1, "
-              "levels in [0,%d])", kMaxLevels);
+              "levels in [0,%d], cycle V or sawtooth)", kMaxLevels);
     return MG_ERR_INVALID;
   }
   int64_t n0[3] = {shape[0], shape[1], dim == 3 ? shape[2] : 1};
@@ -565,7 +569,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     ca.ncoarse = h->ncoarse;
     ca.inv = h->inv;
     ca.image = nullptr;
-    ca.pre = o.pre;
+    ca.pre = o.cycle == MG_CYCLE_SAWTOOTH ? -1 : o.pre;  // -1: the sawtooth recursion
     ca.post = o.post;
     ca.omega = (float)o.omega;
     ca.s = (float)o.coarse_scale;
@@ -595,15 +599,18 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_r3_kernels<T, M>();
     for (int k = 0; k < h->kc; ++k) {
-      h->s3_ok[k] = getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
-      h->s2_ok[k] = getenv("NPMG_NO_STREAM2D") == nullptr && stream2d_eligible(dim, o.pre, o.post, h->lv[k]) &&
-                    h->ncell[k] >= stream2d_min_cells();
-      h->r3_ok[k] = getenv("NPMG_NO_ROWS3D") == nullptr && rows3d_eligible(dim, o.pre, o.post, h->lv[k]);
+      // the sawtooth cycle runs on the general tile kernels only
+      const bool v = o.cycle == MG_CYCLE_V;
+      h->s3_ok[k] = v && getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
+      h->s2_ok[k] = v && getenv("NPMG_NO_STREAM2D") == nullptr &&
+                    stream2d_eligible(dim, o.pre, o.post, h->lv[k]) && h->ncell[k] >= stream2d_min_cells();
+      h->r3_ok[k] = v && getenv("NPMG_NO_ROWS3D") == nullptr && rows3d_eligible(dim, o.pre, o.post, h->lv[k]);
     }
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
       // level 0 of a 16-bit handle reads float32 r: no TMA tile kernels there
-      h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&
+      h->tma_ok[k] = o.cycle == MG_CYCLE_V && getenv("NPMG_NO_TMA") == nullptr &&
+                     tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&
                      (k > 0 || std::is_same<T, float>::value) &&
                      tma_encode_level<T>(&h->tmaps[k], h->lv[k], k == 0 ? h->r : h->bk[k], h->xk[k],
                                          h->yk[k + 1]);

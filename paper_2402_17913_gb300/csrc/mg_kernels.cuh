@@ -145,7 +145,10 @@ k_down(LevelDev L, const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ 
   __syncthreads();
   float* cur = s0;
   float* nxt = s1;
-  if (pre_c == 0) {
+  // pre_c < 0: the sawtooth down leg (App. B): the residual of x = 0 (that
+  // is b) is restricted, and x = b / d (one Jacobi step from zero) is
+  // written for the up leg
+  if (pre_c <= 0) {
     for (int i = threadIdx.x; i < g.R; i += blockDim.x) s0[i] = 0.f;
     __syncthreads();
   } else {
@@ -164,7 +167,15 @@ k_down(LevelDev L, const TB* __restrict__ b, T* __restrict__ x, T* __restrict__ 
     const int tz = t / TS::Y;
     const int lx = tx + g.H, ly = ty + g.H, lz = (DIM == 3) ? tz + g.H : 0;
     const int gx = g.ox + lx, gy = g.oy + ly, gz = g.oz + lz;
-    if (inside<DIM>(L, gx, gy, gz)) x[gidx(L, gx, gy, gz)] = cvt<T>(cur[g.idx(lx, ly, lz)]);
+    if (inside<DIM>(L, gx, gy, gz)) {
+      const int li = g.idx(lx, ly, lz);
+      float v = cur[li];
+      if (pre_c < 0) {
+        const uint8_t mm = sm[li];
+        v = mm ? sb[li] / diag_at<DIM, MASKED>(L, gx, gy, gz, mm) : 0.f;
+      }
+      x[gidx(L, gx, gy, gz)] = cvt<T>(v);
+    }
   }
   // residual and restriction to the coarse right-hand side
   constexpr int CX = TS::X / 2, CY = TS::Y / 2, CZ = (DIM == 3) ? TS::Z / 2 : 1;

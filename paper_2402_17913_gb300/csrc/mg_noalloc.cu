@@ -68,7 +68,7 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   mg_options o;
   if (opt) o = *opt;
   else mg_default_options(&o);
-  if (o.prec != MG_FP32 || o.pre < 0 || o.pre > kMaxHalo || o.post < 0 || o.post > kMaxHalo ||
+  if (o.prec != MG_FP32 || o.cycle != MG_CYCLE_V || o.pre < 0 || o.pre > kMaxHalo || o.post < 0 || o.post > kMaxHalo ||
       !(o.omega > 0.0 && o.omega <= 2.0) || !(o.coarse_scale > 0.0) || o.levels < 0 || o.levels > kMaxLevels) {
     set_error("mg_vcycle_noalloc: invalid options (float32 only, pre/post in [0,%d])", kMaxHalo);
     return MG_ERR_INVALID;

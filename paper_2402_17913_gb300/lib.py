@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libnpmg.so")
 MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_NOT_CONVERGED, MG_DIVERGED, MG_TIMEOUT = range(7)
 MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1
 MG_FP32, MG_MIXED_FP16, MG_MIXED_BF16 = 0, 1, 2
+MG_CYCLE_V, MG_CYCLE_SAWTOOTH = 0, 1
 
 STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
                 4: "MG_NOT_CONVERGED", 5: "MG_DIVERGED", 6: "MG_TIMEOUT"}
@@ -43,7 +44,7 @@ class MgOptions(ctypes.Structure):
     _fields_ = [("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_scale", ctypes.c_double), ("levels", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner_floor", ctypes.c_double)]
+                ("inner_floor", ctypes.c_double), ("cycle", ctypes.c_int)]
 
 
 class MgStats(ctypes.Structure):

@@ -174,6 +174,39 @@ def test_streaming_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
     solve_and_check(L, shape, bc, solid, h, b, prec=1)
 
 
+@pytest.mark.parametrize("shape,bc,frac", CASES)
+def test_sawtooth_cycle_matches_oracle(L, shape, bc, frac):
+    """One cycle of the paper's sawtooth (App. B recursion; omega 2/3, two
+    post sweeps, coarse scale 1/2) equals the oracle's sawtooth cycle, up to
+    the h_0x^2 scaling of A'."""
+    solid, h = make_case(shape, bc, frac)
+    hdl = create(L, shape, bc, solid, h, cycle=L.MG_CYCLE_SAWTOOTH, coarse_scale=0.5)
+    try:
+        nl = L.mg_num_levels(hdl)
+        mg = P.Multigrid(P.build_hierarchy(shape, h, bc, solid, levels=nl), post=2, s=0.5, cycle='sawtooth')
+        r = I.blob_rhs(shape, 3, solid=solid).astype(np.float32)
+        z = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        L.mg_precondition(hdl, dev(r), z)
+        ref = mg.precondition(r.astype(np.float64)) / h[0] ** 2
+        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= 2e-5, err
+    finally:
+        L.mg_destroy(hdl)
+
+
+def test_sawtooth_stationary_solve(L):
+    """The sawtooth as a stationary solver (no CG) with the halved coarse
+    correction reaches relres 1e-6 and the converged oracle solution; it
+    takes many more cycles than V(2,2)-preconditioned CG."""
+    shape = (64, 64)
+    h = I.poisson_spacing(shape)
+    b = I.blob_rhs(shape, 0).astype(np.float32)
+    st = solve_and_check(L, shape, (0, 0, 0, 0), None, h, b, cycle=L.MG_CYCLE_SAWTOOTH, krylov=0,
+                         coarse_scale=0.5, max_inner=4000)
+    st_v = solve_and_check(L, shape, (0, 0, 0, 0), None, h, b)
+    assert st["iters"] > 5 * st_v["iters"], (st["iters"], st_v["iters"])
+
+
 def test_solve_256_blob_iterations_match_oracle(L):
     """256^2, zero Dirichlet, 8-blob RHS (seed 0), 7 levels: relres 1e-6;
     the refinement loop takes the oracle's number of CG iterations (+-2)."""
