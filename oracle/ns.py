@@ -26,12 +26,15 @@ Step (Algorithm 1, with the readings used here):
    with ``Q = q^n`` (predictor) and ``Q = (q~ + q^n) / 2`` (corrector);
    ``U_b^n`` is the frozen advecting velocity at time n (Alg. 1, step 1),
    ``d_b`` the central difference (filters A^u, A^v of Eq. AAA), ``A_nu`` the
-   5/7-point diffusion filter (App. A) divided by h^2;
+   5/7-point diffusion filter (App. A) divided by h^2; or, as an option, the
+   finite-element 9/27-point filters of App. A (``momentum_rate_fe``);
 2. pressure correction ``A_h dp = -(1/dt) D q*``, where the paper's
    "nabla^2" is its diffusion filter, i.e. ``A_h = -Laplacian_h`` (Sec. 2.1),
    and on the staggered grid ``A_h = -D G`` exactly;
 3. ``q <- q* - dt G dp``;  4. ``p <- p + dp``.
 """
+import itertools
+
 import numpy as np
 
 from . import poisson as P
@@ -197,8 +200,87 @@ def momentum_rate(g, q, c, Q, U, nu, gradp):
     return adv + nu * diff + gradp[c]
 
 
-def momentum(g, q, p, dt, nu, u_inflow):
-    """Step 1 of Algorithm 1: predictor, then corrector.  Returns q*."""
+def _pad_all(g, c, Q):
+    """Q padded by one layer along every axis, each axis by component c's
+    ghost rule in turn (so a corner ghost follows both rules)."""
+    Qp = Q
+    for a in range(g.dim):
+        lo, hi = ghost_modes(c, a)
+        Qp = pad(Qp, a, lo, hi)
+    return Qp
+
+
+def _at(Qp, off):
+    """From an array padded along every axis, the values at offset ``off``
+    = (ox, oy[, oz]) for every interior index."""
+    sl = []
+    for ax in range(Qp.ndim):
+        a = Qp.ndim - 1 - ax
+        n = Qp.shape[ax] - 2
+        sl.append(slice(1 + off[a], 1 + off[a] + n))
+    return Qp[tuple(sl)]
+
+
+def fe_diffusion_weights(dim):
+    """The paper's finite-element diffusion filters (App. A) as
+    {offset: weight} with their common factor: 2D 9-point 1/(4 h^2) x
+    [-1 -2 -1; -2 12 -2; -1 -2 -1]; 3D 27-point 1/(26 h^2) x (centre 88,
+    -6 on the 6 face neighbours, -3 on the 12 edge neighbours, -2 on the 8
+    corners).  The weight depends on how many offset components are
+    non-zero."""
+    by_count = {2: {0: 12.0, 1: -2.0, 2: -1.0}, 3: {0: 88.0, 1: -6.0, 2: -3.0, 3: -2.0}}[dim]
+    scale = {2: 4.0, 3: 26.0}[dim]
+    w = {}
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        w[off] = by_count[sum(1 for o in off if o != 0)]
+    return w, scale
+
+
+def fe_advection_weights(dim, a):
+    """The paper's finite-element advection filters along axis ``a`` (App.
+    A) as {offset: weight} and their factor: the central difference along
+    ``a`` smoothed by (1, 4, 1) across each other axis; 2D 1/(12 h), 3D
+    1/(72 h).  The sign is + towards +a on every axis (the printed z filter
+    of the paper carries the opposite sign; read as the same filter)."""
+    side = {-1: 1.0, 0: 4.0, 1: 1.0}
+    w = {}
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        if off[a] == 0:
+            continue
+        v = float(off[a])
+        for b in range(dim):
+            if b != a:
+                v *= side[off[b]]
+        w[off] = v
+    return w, {2: 12.0, 3: 72.0}[dim]
+
+
+def momentum_rate_fe(g, q, c, Q, U, nu, gradp):
+    """Bracket of Eq. predictor-Burgers with the paper's finite-element
+    filters (App. A: 9-point / 27-point diffusion, the advection filters),
+    applied to component c on its own face grid: sum_b U_b d_b^FE Q +
+    nu A_nu^FE Q + d_c p^n."""
+    h = g.h
+    Qp = _pad_all(g, c, Q)
+    wd, sd = fe_diffusion_weights(g.dim)
+    diff = np.zeros_like(Q)
+    for off, w in wd.items():
+        diff = diff + w * _at(Qp, off)
+    diff = diff / (sd * h * h)
+    adv = np.zeros_like(Q)
+    for a in range(g.dim):
+        wa, sa = fe_advection_weights(g.dim, a)
+        da = np.zeros_like(Q)
+        for off, w in wa.items():
+            da = da + w * _at(Qp, off)
+        adv = adv + U[a] * da / (sa * h)
+    return adv + nu * diff + gradp[c]
+
+
+def momentum(g, q, p, dt, nu, u_inflow, fe=False):
+    """Step 1 of Algorithm 1: predictor, then corrector.  Returns q*.
+    ``fe`` selects the finite-element filters (``momentum_rate_fe``)."""
+    rate_fn = momentum_rate_fe if fe else momentum_rate
     q = enforce_bc(g, q, u_inflow)
     gradp = g.pressure_gradient(p)
     U = {c: [advecting_velocity(g, q, c, b) for b in range(g.dim)] for c in range(g.dim)}
@@ -206,13 +288,13 @@ def momentum(g, q, p, dt, nu, u_inflow):
     fixed = [g.fixed_faces(c) for c in range(g.dim)]
     pred = []
     for c in range(g.dim):
-        rate = momentum_rate(g, q, c, q[c], U[c], nu, gradp)
+        rate = rate_fn(g, q, c, q[c], U[c], nu, gradp)
         new = (q[c] - dt * rate) / denom[c]
         pred.append(np.where(fixed[c], q[c], new))
     out = []
     for c in range(g.dim):
         Q = 0.5 * (pred[c] + q[c])
-        rate = momentum_rate(g, q, c, Q, U[c], nu, gradp)
+        rate = rate_fn(g, q, c, Q, U[c], nu, gradp)
         new = (q[c] - dt * rate) / denom[c]
         out.append(np.where(fixed[c], q[c], new))
     return out
@@ -239,12 +321,13 @@ def correct(g, qs, p, dp, dt):
     return [qs[c] - dt * G[c] for c in range(g.dim)], p + dp
 
 
-def ns_step(g, q, p, dt, nu, u_inflow, tol=1e-12, solve=None):
+def ns_step(g, q, p, dt, nu, u_inflow, tol=1e-12, solve=None, fe=False):
     """One full step of Algorithm 1.  The pressure correction is solved to
     relative residual ``tol`` (default 1e-12) by ``solve(b)`` if given, else
-    by the oracle's dense solve (small grids) or MG-PCG.
+    by the oracle's dense solve (small grids) or MG-PCG.  ``fe`` selects the
+    finite-element momentum filters of App. A.
     Returns (q_new, p_new, dp, q_star, b)."""
-    qs = momentum(g, q, p, dt, nu, u_inflow)
+    qs = momentum(g, q, p, dt, nu, u_inflow, fe=fe)
     b = divergence_rhs(g, qs, dt)
     if solve is None:
         dp = P.solve_reference(g.shape, (g.h,) * g.dim, g.p_bc, b, g.solid, tol=tol, s=1.0)
