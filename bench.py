@@ -72,6 +72,8 @@ def parse():
                     help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
     ap.add_argument("--cycle", default="v", choices=["v", "sawtooth"],
                     help="poisson2d/3d: V(2,2)-preconditioned CG (default) or the paper's sawtooth cycle")
+    ap.add_argument("--stencil", default="fd", choices=["fd", "fe"],
+                    help="ns2d/ns3d: momentum filters, 5/7-point (default) or the finite-element 9/27-point ones")
     ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1, 2],
                     help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
@@ -83,11 +85,15 @@ def parse():
 
 # ---------------------------------------------------------------------------
 # workloads
+FILTERS = {False: "5/7-point (App. A)", True: "finite-element 9/27-point (App. A)"}
+
+
 class NS2D:
     name = "ns2d_block_2048x1024"
     dim = 2
 
-    def __init__(self, scale=1):
+    def __init__(self, scale=1, fe=False):
+        self.fe = fe
         self.cells = (2048 // scale, 1024 // scale)
         self.block = 64 // scale
         self.centre = (512 // scale, 512 // scale)
@@ -99,7 +105,7 @@ class NS2D:
         return {"workload": "2D projection step, flow past a square block", "cells": list(self.cells),
                 "block": self.block, "nu": self.nu, "dt": self.dt, "u_inflow": self.uin,
                 "solve_rel_tol": TOL, "unknowns_per_step": self.units,
-                "l2": "256 MiB buffer written between timed steps"}
+                "momentum_filters": FILTERS[self.fe], "l2": "256 MiB buffer written between timed steps"}
 
 
 class NS3D:
@@ -109,7 +115,8 @@ class NS3D:
     name = "ns3d_cube_256x128x128"
     dim = 3
 
-    def __init__(self, scale=1):
+    def __init__(self, scale=1, fe=False):
+        self.fe = fe
         self.cells = (256 // scale, 128 // scale, 128 // scale)
         self.block = 32 // scale
         self.centre = (64 // scale, 64 // scale, 64 // scale)
@@ -120,7 +127,8 @@ class NS3D:
     def config(self):
         return {"workload": "3D projection step, flow past a cube", "cells": list(self.cells), "block": self.block,
                 "nu": self.nu, "dt": self.dt, "u_inflow": self.uin, "solve_rel_tol": TOL,
-                "unknowns_per_step": self.units, "l2": "256 MiB buffer written between timed steps"}
+                "unknowns_per_step": self.units, "momentum_filters": FILTERS[self.fe],
+                "l2": "256 MiB buffer written between timed steps"}
 
 
 class Poisson:
@@ -339,9 +347,12 @@ def run_gpu(args, rank, world):
     guess = None
 
     if args.config in ("ns2d", "ns3d"):
-        wl = NS2D() if args.config == "ns2d" else NS3D()
+        fe = args.stencil == "fe"
+        wl = NS2D(fe=fe) if args.config == "ns2d" else NS3D(fe=fe)
         solid_t = torch.from_numpy(wl.solid.astype(np.uint8)).to(dev)
         ns = L.ns_create(wl.dim, wl.cells, 1.0, solid_t)
+        if fe:
+            L.ns_set_stencils(ns, L.NS_STENCIL_FE)
         mg = L.ns_pressure_handle(ns)
         q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
         host = [torch.from_numpy(a).pin_memory() for a in q + [np.zeros(wl.solid.shape, np.float32)]]
@@ -545,7 +556,7 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
         while steps < max_steps and t_total < budget_s:
             t0 = time.perf_counter()
             q, p, _, _, _ = N.ns_step(g, q, p, wl.dt, wl.nu, wl.uin,
-                                      solve=lambda b: P.pcg_ir(mg, b, tol=TOL)[0])
+                                      solve=lambda b: P.pcg_ir(mg, b, tol=TOL)[0], fe=wl.fe)
             t_total += time.perf_counter() - t0
             steps += 1
             units += wl.units
@@ -620,7 +631,8 @@ def main():
             return
         # each reference step is one oracle step of a bounded sample of the
         # workload (same structure, fewer cells), so the run ends in minutes
-        samples = {"ns2d": lambda: NS2D(scale=4), "ns3d": lambda: NS3D(scale=4),
+        fe = args.stencil == "fe"
+        samples = {"ns2d": lambda: NS2D(scale=4, fe=fe), "ns3d": lambda: NS3D(scale=4, fe=fe),
                    "poisson2d": lambda: Poisson((256, 256), args.prec),
                    "poisson3d": lambda: Poisson((64, 64, 64), args.prec), "batched": lambda: Batched(limit=16)}
         wl = samples[args.config]()
@@ -645,7 +657,7 @@ def main():
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
             ms = {"poisson2d": 5, "batched": 64}.get(args.config, 1)
             # 3D: the full-size oracle step takes minutes; time a smaller copy
-            cpu_wl = {"ns3d": lambda: NS3D(scale=2), "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
+            cpu_wl = {"ns3d": lambda: NS3D(scale=2, fe=wl.fe), "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
                 args.config, lambda: wl)()
             rate, sample, n = oracle_step_time(cpu_wl, budget_s=25.0, max_steps=ms)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}

@@ -273,7 +273,24 @@ mg_status ns_create(ns_handle* out, int dim, const int64_t cells[3], double h,
 mg_status ns_step(ns_handle ns, float* d_u, float* d_v, float* d_w,
                   float* d_p, double dt, double nu, double u_inflow,
                   double rel_tol, void* stream, mg_stats* out);
-/* Step 1 only: q* from q^n and p^n into d_us, d_vs, d_ws (face arrays). */
+/*
+ * ns_set_stencils: the filters of the momentum step (Alg. 1 step 1) for
+ * every later ns_step / ns_momentum on ns.  NS_STENCIL_FD (the default of
+ * ns_create): the 5-point (2D) / 7-point (3D) diffusion filter and central
+ * differences (App. A, Eq. AAA).  NS_STENCIL_FE: the finite-element filters
+ * of App. A: 9-point / 27-point diffusion, 1/(4 h^2) [-1 -2 -1; -2 12 -2;
+ * -1 -2 -1] and 1/(26 h^2) (88 centre, -6 face, -3 edge, -2 corner), and
+ * advection along each axis by the central difference smoothed with weights
+ * (1, 4, 1) across the other axes (1/(12 h), 1/(72 h)); the printed z
+ * filters, whose sign is opposite to the x and y ones, are taken with the
+ * +d/dz sign of those.  Neighbours outside the face array follow the
+ * padding rule of every axis they leave.  MG_ERR_INVALID for a NULL handle
+ * or another value.
+ */
+enum { NS_STENCIL_FD = 0, NS_STENCIL_FE = 1 };
+mg_status ns_set_stencils(ns_handle ns, int stencil);
+/* Step 1 only: q* from q^n and p^n into d_us, d_vs, d_ws (face arrays),
+   with the filters chosen by ns_set_stencils. */
 mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v,
                       const float* d_w, const float* d_p, float* d_us,
                       float* d_vs, float* d_ws, double dt, double nu,

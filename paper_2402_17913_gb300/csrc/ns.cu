@@ -82,11 +82,60 @@ __device__ __forceinline__ bool face_thread(const int F[3], int f[3]) {
   return f[0] < F[0] && f[1] < F[1] && f[2] < F[2];
 }
 
+// Finite-element filters of App. A on the 3^DIM neighbourhood Nb[z][y][x]
+// of a face (offsets -1, 0, +1 per axis; Nb[1][..] in 2D):
+//   diffusion  2D 1/(4 h^2) [-1 -2 -1; -2 12 -2; -1 -2 -1]; 3D 1/(26 h^2) x
+//              (88 centre, -6 face, -3 edge, -2 corner neighbours);
+//   advection  along a: the central difference along a smoothed by
+//              (1, 4, 1) across every other axis; 2D 1/(12 h), 3D 1/(72 h),
+//              + towards +a on every axis.
+template <int DIM>
+__device__ __forceinline__ void fe_filters(const float (&Nb)[3][3][3], const float U[3], float inv_h, float inv_h2,
+                                           float& adv, float& diff) {
+  constexpr int Z0 = DIM == 3 ? 0 : 1, Z1 = DIM == 3 ? 2 : 1;
+  // diffusion: weight by the number of non-zero offset components
+  float faces = 0.f, edges = 0.f, corners = 0.f;
+#pragma unroll
+  for (int z = Z0; z <= Z1; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const int cnt = (x != 1) + (y != 1) + (z != 1);
+        if (cnt == 1) faces += Nb[z][y][x];
+        else if (cnt == 2) edges += Nb[z][y][x];
+        else if (cnt == 3) corners += Nb[z][y][x];
+      }
+  const float ctr = Nb[1][1][1];
+  if (DIM == 2)
+    diff = (12.f * ctr - 2.f * faces - edges) * (0.25f * inv_h2);
+  else
+    diff = (88.f * ctr - 6.f * faces - 3.f * edges - 2.f * corners) * (inv_h2 / 26.f);
+  // advection: smoothing weight 4 on the centre line of an axis, 1 off it
+  float dx = 0.f, dy = 0.f, dz = 0.f;
+#pragma unroll
+  for (int z = Z0; z <= Z1; ++z)
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const float v = Nb[z][y][x];
+        const float wx = x == 1 ? 4.f : 1.f, wy = y == 1 ? 4.f : 1.f, wz = (DIM == 3 && z == 1) ? 4.f : 1.f;
+        if (x != 1) dx = fmaf((x - 1) * (DIM == 3 ? wy * wz : wy), v, dx);
+        if (y != 1) dy = fmaf((y - 1) * (DIM == 3 ? wx * wz : wx), v, dy);
+        if (DIM == 3 && z != 1) dz = fmaf((z - 1) * wx * wy, v, dz);
+      }
+  const float s = inv_h / (DIM == 2 ? 12.f : 72.f);
+  adv = fmaf(U[0], dx * s, U[1] * (dy * s));
+  if (DIM == 3) adv = fmaf(U[2], dz * s, adv);
+}
+
 // One pass of the momentum update of component C (Eq. predictor-Burgers
 // with implicit absorption, Alg. 1 step 1):
 //   (1 + sigma dt) out = q^n - dt [ sum_b U_b^n d_b Q + nu A_nu Q + d_C p^n ]
-// with Q = q^n (predictor) or Q = (qt + q^n) / 2 (corrector, CORR).
-template <int DIM, int C, bool CORR>
+// with Q = q^n (predictor) or Q = (qt + q^n) / 2 (corrector, CORR); d_b and
+// A_nu are the 5/7-point filters, or the finite-element filters (FE).
+template <int DIM, int C, bool CORR, bool FE>
 __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const float* __restrict__ qt,
                                                   const float* __restrict__ p, float* __restrict__ out, float dt,
                                                   float nu, float uin, float sigma) {
@@ -113,7 +162,69 @@ __global__ void __launch_bounds__(256) k_momentum(NsGeom G, FaceArrays Qn, const
   // directly: none of them is clamped, padded or fixed.
   const bool inner = f[0] >= 2 && f[0] + 2 < F[0] && f[1] >= 2 && f[1] + 2 < F[1] &&
                      (DIM == 2 || (f[2] >= 2 && f[2] + 2 < F[2]));
-  if (inner) {
+  if constexpr (FE) {
+    float U[3] = {0.f, 0.f, 0.f};
+    float Nb[3][3][3];
+    constexpr int Z0 = DIM == 3 ? 0 : 1, Z1 = DIM == 3 ? 2 : 1;
+    if (inner) {
+      const size_t sc[3] = {1, (size_t)F[0], (size_t)F[0] * F[1]};
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        if (a == C) {
+          U[a] = qn_self;
+        } else {
+          const size_t A0 = G.n[0] + (a == 0), A1 = G.n[1] + (a == 1);
+          const size_t sa[3] = {1, A0, A0 * A1};
+          const size_t ia = ((size_t)f[2] * A1 + f[1]) * A0 + f[0];
+          const float* qa = Qn.q[a];
+          U[a] = 0.25f * ((qa[ia - sa[C]] + qa[ia - sa[C] + sa[a]]) + (qa[ia] + qa[ia + sa[a]]));
+        }
+      }
+#pragma unroll
+      for (int z = Z0; z <= Z1; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const size_t j = i + (z - 1) * sc[2] + (y - 1) * sc[1] + (x - 1);
+            float v = qc[j];
+            if (CORR) v = 0.5f * (v + qt[j]);
+            Nb[z][y][x] = v;
+          }
+    } else {
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        if (a == C) {
+          U[a] = qn_self;
+        } else {
+          float s = 0.f;
+#pragma unroll
+          for (int dc = -1; dc <= 0; ++dc)
+#pragma unroll
+            for (int da = 0; da <= 1; ++da) {
+              int g[3] = {f[0], f[1], f[2]};
+              g[C] += dc;
+              g[a] += da;
+              s += q_at<DIM>(G, Qn.q[a], a, g[0], g[1], g[2], uin);
+            }
+          U[a] = 0.25f * s;
+        }
+      }
+      // corner neighbours take the padding rule of every axis they leave
+#pragma unroll
+      for (int z = Z0; z <= Z1; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y)
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const int g0 = f[0] + x - 1, g1 = f[1] + y - 1, g2 = f[2] + z - 1;
+            float v = q_at<DIM>(G, qc, C, g0, g1, g2, uin);
+            if (CORR) v = 0.5f * (v + q_at<DIM>(G, qt, C, g0, g1, g2, uin));
+            Nb[z][y][x] = v;
+          }
+    }
+    fe_filters<DIM>(Nb, U, G.inv_h, G.inv_h2, adv, diff);
+  } else if (inner) {
     const size_t sc[3] = {1, (size_t)F[0], (size_t)F[0] * F[1]};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -263,6 +374,7 @@ struct ns_handle_s {
   // level-1 solid mask, or nullptr until a coarse level is first used
   float* gc;
   uint8_t* gsolid;
+  int stencil;  // NS_STENCIL_FD (5/7-point) or NS_STENCIL_FE (9/27-point)
 };
 
 static constexpr int kMaxGuessLevel = 2;
@@ -541,6 +653,15 @@ mg_status ns_set_guess_level(ns_handle ns, gn_handle g, int level) {
   return MG_OK;
 }
 
+mg_status ns_set_stencils(ns_handle ns, int stencil) {
+  if (!ns || (stencil != NS_STENCIL_FD && stencil != NS_STENCIL_FE)) {
+    set_error("ns_set_stencils: NULL handle or stencil not NS_STENCIL_FD / NS_STENCIL_FE");
+    return MG_ERR_INVALID;
+  }
+  ns->stencil = stencil;
+  return MG_OK;
+}
+
 mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v, const float* d_w, const float* d_p,
                       float* d_us, float* d_vs, float* d_ws, double dt, double nu, double u_inflow, void* stream) {
   if (!ns || !d_u || !d_v || !d_p || !d_us || !d_vs || (ns->dim == 3 && (!d_w || !d_ws))) {
@@ -555,15 +676,17 @@ mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v, const fl
   Qn.q[2] = ns->dim == 3 ? d_w : nullptr;
   float* outs[3] = {d_us, d_vs, d_ws};
   const float fdt = (float)dt, fnu = (float)nu, fu = (float)u_inflow, fs = (float)ns->sigma;
+  const bool fe = ns->stencil == NS_STENCIL_FE;
   for (int pass = 0; pass < 2; ++pass) {
     for (int c = 0; c < ns->dim; ++c) {
       LaunchScope ls(ns->mg, MG_K_MOMENTUM, s);
       const dim3 g = face_grid(ns, c);
       const float* qt = pass ? ns->pred[c] : nullptr;
       float* o = pass ? outs[c] : ns->pred[c];
-#define NPMG_MOM(D, CC)                                                                              \
-  (pass ? k_momentum<D, CC, true><<<g, 256, 0, s>>>(G, Qn, qt, d_p, o, fdt, fnu, fu, fs)             \
-        : k_momentum<D, CC, false><<<g, 256, 0, s>>>(G, Qn, qt, d_p, o, fdt, fnu, fu, fs))
+#define NPMG_MOM2(D, CC, FEF)                                                                       \
+  (pass ? k_momentum<D, CC, true, FEF><<<g, 256, 0, s>>>(G, Qn, qt, d_p, o, fdt, fnu, fu, fs)        \
+        : k_momentum<D, CC, false, FEF><<<g, 256, 0, s>>>(G, Qn, qt, d_p, o, fdt, fnu, fu, fs))
+#define NPMG_MOM(D, CC) (fe ? NPMG_MOM2(D, CC, true) : NPMG_MOM2(D, CC, false))
       if (ns->dim == 2) {
         if (c == 0) NPMG_MOM(2, 0);
         else NPMG_MOM(2, 1);
@@ -573,6 +696,7 @@ mg_status ns_momentum(ns_handle ns, const float* d_u, const float* d_v, const fl
         else NPMG_MOM(3, 2);
       }
 #undef NPMG_MOM
+#undef NPMG_MOM2
     }
   }
   NPMG_CUDA(cudaGetLastError());

@@ -15,6 +15,7 @@ MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_NOT_CONVERGED, MG_DIVERGED, M
 MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1
 MG_FP32, MG_MIXED_FP16, MG_MIXED_BF16 = 0, 1, 2
 MG_CYCLE_V, MG_CYCLE_SAWTOOTH = 0, 1
+NS_STENCIL_FD, NS_STENCIL_FE = 0, 1
 
 STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
                 4: "MG_NOT_CONVERGED", 5: "MG_DIVERGED", 6: "MG_TIMEOUT"}
@@ -29,7 +30,7 @@ EXPORTED = [
     "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
     "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches", "ns_set_guess_level",
-    "ns_coarse_fields",
+    "ns_coarse_fields", "ns_set_stencils",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
@@ -140,6 +141,7 @@ def load():
         "gn_destroy": (ctypes.c_int, [_vp]),
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
         "ns_set_guess_level": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+        "ns_set_stencils": (ctypes.c_int, [_vp, ctypes.c_int]),
         "ns_coarse_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -477,6 +479,11 @@ def ns_set_guess(ns, g):
 
 def ns_set_guess_level(ns, g, level):
     _check(load().ns_set_guess_level(ns, g, int(level)))
+
+
+def ns_set_stencils(ns, stencil):
+    """Momentum filters of later steps: NS_STENCIL_FD (5/7-point) or NS_STENCIL_FE (9/27-point)."""
+    _check(load().ns_set_stencils(ns, int(stencil)))
 
 
 def ns_coarse_fields(ns, level, p, b_c, p_c, dp_c, solid_c, stream=None):

@@ -124,3 +124,71 @@ def test_several_steps_track_oracle(L):
             assert e <= 1e-4, (c, e)
     finally:
         L.ns_destroy(ns)
+
+
+FE_CASES = CASES + [((37, 21), 0, None), ((36, 20, 8), 0, None)]  # ragged against the 32x8 face tiles
+
+
+@pytest.mark.parametrize("cells,block,centre", FE_CASES)
+def test_fe_momentum_matches_oracle(L, cells, block, centre):
+    """The finite-element filters of App. A (ns_set_stencils): one
+    predictor-corrector momentum step elementwise against the oracle's
+    momentum_rate_fe path, boundary and corner neighbours included; the
+    default filters are restored by NS_STENCIL_FD."""
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        outs = [torch.zeros_like(a) for a in qd]
+        w = qd[2] if len(cells) == 3 else None
+        wo = outs[2] if len(cells) == 3 else None
+        q64 = [a.astype(np.float64) for a in q]
+        L.ns_set_stencils(ns, L.NS_STENCIL_FE)
+        L.ns_momentum(ns, qd[0], qd[1], w, dev(p), outs[0], outs[1], wo, 0.1, 0.64, 1.0)
+        ref = N.momentum(g, q64, p.astype(np.float64), 0.1, 0.64, 1.0, fe=True)
+        ref5 = N.momentum(g, q64, p.astype(np.float64), 0.1, 0.64, 1.0)
+        for c in range(len(cells)):
+            got = outs[c].cpu().numpy()
+            err = np.max(np.abs(got - ref[c]))
+            assert err <= 2e-6 * max(1.0, np.abs(ref[c]).max()), (c, err)
+            # the two filter sets give visibly different steps
+            assert np.max(np.abs(ref[c] - ref5[c])) > 100 * err, c
+        L.ns_set_stencils(ns, L.NS_STENCIL_FD)
+        L.ns_momentum(ns, qd[0], qd[1], w, dev(p), outs[0], outs[1], wo, 0.1, 0.64, 1.0)
+        for c in range(len(cells)):
+            err = np.max(np.abs(outs[c].cpu().numpy() - ref5[c]))
+            assert err <= 2e-6 * max(1.0, np.abs(ref5[c]).max()), (c, err)
+    finally:
+        L.ns_destroy(ns)
+
+
+@pytest.mark.parametrize("cells,block,centre", CASES)
+def test_fe_step_matches_oracle(L, cells, block, centre):
+    """A full projection step with the finite-element momentum filters
+    against the oracle's step (same tolerances as the 5/7-point step)."""
+    ns, g, solid, q, p = setup(L, cells, block, centre)
+    try:
+        qd = [dev(a) for a in q]
+        pd = dev(p)
+        w = qd[2] if len(cells) == 3 else None
+        L.ns_set_stencils(ns, L.NS_STENCIL_FE)
+        status, st = L.ns_step(ns, qd[0], qd[1], w, pd, 0.1, 0.64, 1.0, 1e-6)
+        assert status == L.MG_OK and st["relres"] <= 1e-6, st
+        q64 = [a.astype(np.float64) for a in q]
+        qn, pn, dp, qs, b = N.ns_step(g, q64, p.astype(np.float64), 0.1, 0.64, 1.0, fe=True)
+        for c in range(len(cells)):
+            e = np.linalg.norm(qd[c].cpu().numpy() - qn[c]) / np.linalg.norm(qn[c])
+            assert e <= 1e-5, (c, e)
+        e = np.linalg.norm(pd.cpu().numpy() - pn) / np.linalg.norm(pn)
+        assert e <= 1e-4, e
+    finally:
+        L.ns_destroy(ns)
+
+
+def test_set_stencils_rejects_unknown_value(L):
+    ns = L.ns_create(2, (16, 8), 1.0, None)
+    try:
+        with pytest.raises(L.MGError) as e:
+            L.ns_set_stencils(ns, 2)
+        assert e.value.status == L.MG_ERR_INVALID
+    finally:
+        L.ns_destroy(ns)

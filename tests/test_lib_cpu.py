@@ -79,6 +79,7 @@ def test_solve_rejects_null(lib):
     from paper_2402_17913_gb300 import lib as L
     assert lib.mg_solve(None, None, None, 1e-6, None, None) == L.MG_ERR_INVALID
     assert lib.ns_step(None, None, None, None, None, 0.1, 0.1, 1.0, 1e-6, None, None) == L.MG_ERR_INVALID
+    assert lib.ns_set_stencils(None, L.NS_STENCIL_FE) == L.MG_ERR_INVALID
 
 
 def test_guess_network_rejects_invalid_arguments(lib):
