@@ -12,7 +12,12 @@ and the velocity/pressure correction.  Metric: solved pressure unknowns
 (fluid cells) per second.
 
 Other configs (``--config``): ``poisson2d`` (256^2, 8 blobs, zero
-Dirichlet), ``poisson3d`` (256^3, 8 blobs; ``--prec fp32|fp16|bf16``).
+Dirichlet), ``poisson3d`` (256^3, 8 blobs; ``--prec fp32|fp16|bf16``),
+``ns3d`` (256 x 128 x 128, 32^3 cube), ``batched`` (1024 uneven 2D
+instances) and ``timing3d`` (the paper's timing workload of Sec. 3.4: flow
+past a cube in an n^3 domain, ``--size 128|256|512``, 20 multigrid
+iterations per time step with the finite-element filters; metric: seconds
+for five time steps).
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (each step one oracle step of a bounded
@@ -38,6 +43,7 @@ import numpy as np  # noqa: E402
 from paper_2402_17913_gb300 import inputs as I  # noqa: E402
 
 METRIC = "solved unknowns/sec to 1e-6 rel residual"
+TIMING_METRIC = "seconds for 5 time steps of the 3D flow past a cube"
 UNIT = "unknowns/s"
 TOL = 1e-6
 
@@ -66,7 +72,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="ns2d", choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched"])
+    ap.add_argument("--config", default="ns2d",
+                    choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched", "timing3d"])
+    ap.add_argument("--size", type=int, default=256, choices=[128, 256, 512],
+                    help="timing3d: cells per side of the cubic domain")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--guess", default="zero", choices=["zero", "net"],
                     help="ns3d: initial guess of each pressure solve (net = the learned guess, trained in the run)")
@@ -128,6 +137,52 @@ class NS3D:
         return {"workload": "3D projection step, flow past a cube", "cells": list(self.cells), "block": self.block,
                 "nu": self.nu, "dt": self.dt, "u_inflow": self.uin, "solve_rel_tol": TOL,
                 "unknowns_per_step": self.units, "momentum_filters": FILTERS[self.fe],
+                "l2": "256 MiB buffer written between timed steps"}
+
+
+class Timing3D:
+    """The timing workload of Sec. 3.4 (the paper's timing table): flow past
+    a cube in an n^3 domain (h = 1), the cube 10/128 of the side, centred at
+    (n/4, n/2, n/2) as in the paper's 128^3 case, Re = 200 on the cube side
+    (nu = side / 200), dt = 0.1, the fluid at rest with u = 1 on the inflow
+    faces and the finite-element 27-point filters.  Pressure solve: the
+    paper's form, a fixed 20 stationary sawtooth cycles per time step with no
+    tolerance (``--cycle sawtooth``), or this library's default solve,
+    V(2,2)-preconditioned CG with float-float refinement to relres 1e-6
+    (``--cycle v``; its iteration count is reported)."""
+    dim = 3
+    iters = 20
+    # the paper's seconds for five steps x 20 iterations (Tesla T4; one
+    # Xeon 2.3 GHz CPU), context only
+    paper_s = {128: (3.0, 165.0), 256: (11.0, 1275.0), 512: (34.0, 14376.0)}
+
+    def __init__(self, n=256, cycle="sawtooth", scale=1):
+        self.fe = True
+        self.cycle = cycle
+        n = n // scale
+        self.n = n
+        self.name = "ns3d_timing_%d" % n
+        self.cells = (n, n, n)
+        self.block = max(2, round(10 * n / 128))
+        self.centre = (n // 4, n // 2, n // 2)
+        self.nu, self.dt, self.uin = self.block / 200.0, 0.1, 1.0
+        self.solid = I.block_mask(self.cells, self.centre, self.block)
+        self.units = int((~self.solid).sum())
+
+    def initial_velocity(self):
+        q = [np.zeros((self.n, self.n, self.n + 1), np.float32), np.zeros((self.n, self.n + 1, self.n), np.float32),
+             np.zeros((self.n + 1, self.n, self.n), np.float32)]
+        q[0][..., 0] = self.uin
+        return q
+
+    def config(self):
+        t4, cpu = self.paper_s.get(self.n, (None, None))
+        return {"workload": "3D flow past a cube, five time steps x 20 multigrid iterations (the paper's timing table)",
+                "cells": list(self.cells), "block": self.block, "centre": list(self.centre), "nu": self.nu,
+                "dt": self.dt, "u_inflow": self.uin, "momentum_filters": FILTERS[True],
+                "solver": ("20 stationary sawtooth cycles (coarse scale 1/2) per step" if self.cycle == "sawtooth"
+                           else "V(2,2)-preconditioned CG to relres 1e-6 per step"),
+                "paper_seconds_t4": t4, "paper_seconds_xeon_cpu": cpu,
                 "l2": "256 MiB buffer written between timed steps"}
 
 
@@ -346,15 +401,29 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     guess = None
 
-    if args.config in ("ns2d", "ns3d"):
+    if args.config in ("ns2d", "ns3d", "timing3d"):
         fe = args.stencil == "fe"
-        wl = NS2D(fe=fe) if args.config == "ns2d" else NS3D(fe=fe)
+        opt, tol = None, TOL
+        if args.config == "timing3d":
+            wl = Timing3D(args.size, args.cycle)
+            fe = True
+            if args.cycle == "sawtooth":
+                # a fixed 20 cycles: one inner solve of 20 cycles, with no
+                # tolerance that could end it earlier
+                opt = L.default_options(cycle=L.MG_CYCLE_SAWTOOTH, krylov=0, coarse_scale=0.5, max_inner=wl.iters,
+                                        max_outer=1, inner_floor=1e-30)
+                tol = 1e-30
+        else:
+            wl = NS2D(fe=fe) if args.config == "ns2d" else NS3D(fe=fe)
         solid_t = torch.from_numpy(wl.solid.astype(np.uint8)).to(dev)
-        ns = L.ns_create(wl.dim, wl.cells, 1.0, solid_t)
+        ns = L.ns_create(wl.dim, wl.cells, 1.0, solid_t, options=opt)
         if fe:
             L.ns_set_stencils(ns, L.NS_STENCIL_FE)
         mg = L.ns_pressure_handle(ns)
-        q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
+        if args.config == "timing3d":
+            q = wl.initial_velocity()
+        else:
+            q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
         host = [torch.from_numpy(a).pin_memory() for a in q + [np.zeros(wl.solid.shape, np.float32)]]
         fields = [t.to(dev) for t in host]
         u, v, p = fields[0], fields[1], fields[-1]
@@ -370,7 +439,7 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
 
         def step():
-            _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, TOL)
+            _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, tol)
             stats.append(st)
 
         def e2e_step():
@@ -510,9 +579,10 @@ def run_gpu(args, rank, world):
         tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
         dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
         ms_dom, n_dom = prof[dom]
-        ncell = int(np.prod(wl.cells)) if args.config in ("ns2d", "ns3d") else wl.units
-        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if args.config in ("ns2d", "ns3d") and dom != "xr_update" else 0)
-        if args.prec != "fp32" and args.config not in ("ns2d", "ns3d"):
+        is_ns = args.config in ("ns2d", "ns3d", "timing3d")
+        ncell = int(np.prod(wl.cells)) if is_ns else wl.units
+        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if is_ns and dom != "xr_update" else 0)
+        if args.prec != "fp32" and not is_ns:
             per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
         algo = per_cell * ncell
         achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
@@ -538,6 +608,14 @@ def run_gpu(args, rank, world):
                   "relres_max": max(s["relres"] for s in step_stats) if step_stats else None,
                   "outer_mean": statistics.mean(s["outer"] for s in step_stats) if step_stats else None},
     }
+    if args.config == "timing3d":
+        # the paper's metric: seconds for five time steps of 20 iterations
+        t4 = wl.paper_s.get(wl.n, (None, None))[0]
+        five = 5 * total_ms / args.steps / 1e3
+        out.update(metric=TIMING_METRIC, value=five, unit="s", higher_is_better=False,
+                   vs_baseline=(five / t4 if t4 and args.cycle == "sawtooth" else None), unknowns_per_s=value)
+        out["e2e"] = dict(out["e2e"], value=5 * e2e_total / args.steps / 1e3, unit="s")
+        out["solve"]["relres_per_step"] = [s["relres"] for s in step_stats]
     return out, wl
 
 
@@ -547,21 +625,31 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
     from oracle import ns as N
     from oracle import poisson as P
     t_total, steps, units = 0.0, 0, 0
-    if isinstance(wl, (NS2D, NS3D)):
+    if isinstance(wl, (NS2D, NS3D, Timing3D)):
         g = N.MacGrid(wl.cells, 1.0, wl.solid)
         hier = P.build_hierarchy(g.shape, (1.0,) * wl.dim, g.p_bc, wl.solid)
-        mg = P.Multigrid(hier, s=1.0)
-        q = I.ns_initial_velocity(wl.cells, 0)
+        if isinstance(wl, Timing3D) and wl.cycle == "sawtooth":
+            q = [a.astype(np.float64) for a in wl.initial_velocity()]
+            mg = P.Multigrid(hier, post=2, s=0.5, cycle='sawtooth')
+            solve = lambda b: mg.stationary(b, wl.iters)[0]  # noqa: E731
+        elif isinstance(wl, Timing3D):
+            q = [a.astype(np.float64) for a in wl.initial_velocity()]
+            mg = P.Multigrid(hier, s=1.0)
+            solve = lambda b: P.pcg_ir(mg, b, tol=TOL)[0]  # noqa: E731
+        else:
+            mg = P.Multigrid(hier, s=1.0)
+            q = I.ns_initial_velocity(wl.cells, 0)
+            solve = lambda b: P.pcg_ir(mg, b, tol=TOL)[0]  # noqa: E731
         p = np.zeros(g.shape)
         while steps < max_steps and t_total < budget_s:
             t0 = time.perf_counter()
-            q, p, _, _, _ = N.ns_step(g, q, p, wl.dt, wl.nu, wl.uin,
-                                      solve=lambda b: P.pcg_ir(mg, b, tol=TOL)[0], fe=wl.fe)
+            q, p, _, _, _ = N.ns_step(g, q, p, wl.dt, wl.nu, wl.uin, solve=solve, fe=wl.fe)
             t_total += time.perf_counter() - t0
             steps += 1
             units += wl.units
-        sample = "%d oracle step(s) of the %s projection workload (pressure solve to 1e-6)" % (
-            steps, "x".join(map(str, wl.cells)))
+        sample = "%d oracle step(s) of the %s projection workload (%s)" % (
+            steps, "x".join(map(str, wl.cells)),
+            "20 sawtooth cycles" if isinstance(wl, Timing3D) and wl.cycle == "sawtooth" else "pressure solve to 1e-6")
     elif isinstance(wl, Batched):
         for k in range(len(wl.shapes)):
             if steps >= max_steps or t_total >= budget_s:
@@ -634,7 +722,8 @@ def main():
         fe = args.stencil == "fe"
         samples = {"ns2d": lambda: NS2D(scale=4, fe=fe), "ns3d": lambda: NS3D(scale=4, fe=fe),
                    "poisson2d": lambda: Poisson((256, 256), args.prec),
-                   "poisson3d": lambda: Poisson((64, 64, 64), args.prec), "batched": lambda: Batched(limit=16)}
+                   "poisson3d": lambda: Poisson((64, 64, 64), args.prec), "batched": lambda: Batched(limit=16),
+                   "timing3d": lambda: Timing3D(args.size, args.cycle, scale=args.size // 32)}
         wl = samples[args.config]()
         t0 = time.perf_counter()
         rate, sample, n = oracle_step_time(wl, budget_s=1e9, max_steps=args.warmup + args.steps)
@@ -646,10 +735,18 @@ def main():
                     "ns2d": "quarter-resolution copy (512x256 cells, 16-cell block, Re kept at 100)",
                     "ns3d": "quarter-resolution copy (64x32x32 cells, 8-cell cube, Re kept at 100)",
                     "poisson3d": "64^3 copy of the blob workload",
-                    "batched": "the first 16 instances of the batch"}.get(args.config, "the workload itself")),
+                    "batched": "the first 16 instances of the batch",
+                    "timing3d": "32^3 copy (cube and Re scaled alike); seconds scaled to the full size by cells"}.get(
+                        args.config, "the workload itself")),
                 "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
                 "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
+        if args.config == "timing3d":
+            full = Timing3D(args.size, args.cycle)
+            secs = 5 * full.units / rate
+            line.update(metric=TIMING_METRIC, value=secs, unit="s", higher_is_better=False, unknowns_per_s=rate)
+            line["cpu_baseline"] = dict(line["cpu_baseline"], value=secs, unit="s")
+            line["e2e"] = dict(line["e2e"], value=secs, unit="s")
         print(json.dumps(line))
         return
     out, wl = run_gpu(args, rank, world)
@@ -657,10 +754,16 @@ def main():
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
             ms = {"poisson2d": 5, "batched": 64}.get(args.config, 1)
             # 3D: the full-size oracle step takes minutes; time a smaller copy
-            cpu_wl = {"ns3d": lambda: NS3D(scale=2, fe=wl.fe), "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
+            cpu_wl = {"ns3d": lambda: NS3D(scale=2, fe=wl.fe),
+                      "timing3d": lambda: Timing3D(args.size, args.cycle, scale=max(1, args.size // 64)),
+                      "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
                 args.config, lambda: wl)()
             rate, sample, n = oracle_step_time(cpu_wl, budget_s=25.0, max_steps=ms)
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            if args.config == "timing3d":
+                # the line's unit: seconds for five steps, scaled by cells
+                out["cpu_baseline"].update(value=5 * wl.units / rate, unit="s",
+                                           sample=sample + "; seconds scaled to the full size by cells")
         print(json.dumps(out))
 
 

@@ -49,6 +49,11 @@ int coarse_start_level(const LevelDev* lv, int L, int dim, size_t smem_limit);
 template <int DIM, typename T, bool MASKED, typename TB = T>
 cudaError_t launch_down(const LevelDev& L, const void* b, void* x, void* bcoarse, int pre, float omega,
                         const SolveState* st, cudaStream_t s);
+// Sawtooth down leg (no sweeps: x = b / d, coarse b = average of b); b and
+// x must be 8-byte aligned (levels with a down leg have even sides).
+template <int DIM, typename T, bool MASKED, typename TB = T>
+cudaError_t launch_down_saw(const LevelDev& L, const void* b, void* x, void* bcoarse, const SolveState* st,
+                            cudaStream_t s);
 template <int DIM, typename T, bool MASKED, bool FINEST, typename TB = T>
 cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* xout, const void* e, int post,
                       float omega, float sc, SolveState* st, double* partials, cudaStream_t s);

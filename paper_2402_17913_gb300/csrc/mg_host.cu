@@ -97,6 +97,13 @@ template <int DIM, typename T, bool M, typename TB>
 static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevelMaps* tm, SolveState* st,
                             cudaStream_t s) {
   const float om = (float)h->opt.omega;
+  // the sawtooth down leg (no sweeps: x = b / d, the restriction of b) is
+  // a plain stream; pre = -1 asks the tile kernel for it when b is not
+  // aligned for paired loads.  The fused kernels below run V legs.
+  if (h->opt.cycle == MG_CYCLE_SAWTOOTH) {
+    if (stream2d_aligned(b)) return launch_down_saw<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], st, s);
+    return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], -1, om, st, s);
+  }
   if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
     return launch_down_w<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
   if constexpr (std::is_same<T, TB>::value) {
@@ -105,9 +112,7 @@ static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevel
   if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
     return launch_down_r3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
   if (DIM == 3 && h->s3_ok[k]) return launch_down_s3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
-  // pre = -1 asks the tile kernel for the sawtooth down leg
-  const int pre = h->opt.cycle == MG_CYCLE_SAWTOOTH ? -1 : h->opt.pre;
-  return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], pre, om, st, s);
+  return launch_down<DIM, T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], h->opt.pre, om, st, s);
 }
 
 template <int DIM, typename T, bool M, bool F, typename TB>
@@ -598,19 +603,21 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_r3_kernels<T, M>();
+    // the fused kernels serve both legs of the V cycle and the up leg of
+    // the sawtooth (whose up leg is the V cycle's: x, here b / d from the
+    // down leg, plus the scaled correction, then the post sweeps); their
+    // two-sweep form is fixed, so the sawtooth asks them for post = 2 only
+    const int pre_e = o.cycle == MG_CYCLE_SAWTOOTH ? 2 : o.pre;
     for (int k = 0; k < h->kc; ++k) {
-      // the sawtooth cycle runs on the general tile kernels only
-      const bool v = o.cycle == MG_CYCLE_V;
-      h->s3_ok[k] = v && getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, o.pre, o.post, h->lv[k]);
-      h->s2_ok[k] = v && getenv("NPMG_NO_STREAM2D") == nullptr &&
-                    stream2d_eligible(dim, o.pre, o.post, h->lv[k]) && h->ncell[k] >= stream2d_min_cells();
-      h->r3_ok[k] = v && getenv("NPMG_NO_ROWS3D") == nullptr && rows3d_eligible(dim, o.pre, o.post, h->lv[k]);
+      h->s3_ok[k] = getenv("NPMG_NO_STREAM3D") == nullptr && stream3d_eligible(dim, pre_e, o.post, h->lv[k]);
+      h->s2_ok[k] = getenv("NPMG_NO_STREAM2D") == nullptr && stream2d_eligible(dim, pre_e, o.post, h->lv[k]) &&
+                    h->ncell[k] >= stream2d_min_cells();
+      h->r3_ok[k] = getenv("NPMG_NO_ROWS3D") == nullptr && rows3d_eligible(dim, pre_e, o.post, h->lv[k]);
     }
     // tensor maps of the TMA level kernels (2D, two sweeps, rows of 16k cells)
     for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
       // level 0 of a 16-bit handle reads float32 r: no TMA tile kernels there
-      h->tma_ok[k] = o.cycle == MG_CYCLE_V && getenv("NPMG_NO_TMA") == nullptr &&
-                     tma_level_eligible(dim, o.pre, o.post, h->lv[k]) &&
+      h->tma_ok[k] = getenv("NPMG_NO_TMA") == nullptr && tma_level_eligible(dim, pre_e, o.post, h->lv[k]) &&
                      (k > 0 || std::is_same<T, float>::value) &&
                      tma_encode_level<T>(&h->tmaps[k], h->lv[k], k == 0 ? h->r : h->bk[k], h->xk[k],
                                          h->yk[k + 1]);

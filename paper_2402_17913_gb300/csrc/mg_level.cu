@@ -58,6 +58,92 @@ cudaError_t launch_up(const LevelDev& L, const void* b, const void* xin, void* x
                       (const T*)xin, (TB*)xout, (const T*)e, post, omega, sc, st, partials);
 }
 
+// ---------------------------------------------------------------------------
+// Sawtooth down leg (App. B): no sweeps.  Every cell gets x = b / d (one
+// Jacobi step from a zero guess, for the up leg) and every coarse cell the
+// 2x2(x2) average of b over its fluid children (the residual of x = 0).
+// There is no stencil, so the kernel is a plain stream: one thread per
+// coarse cell reads its children as pairs along x (coalesced 2-element
+// loads; levels with a down leg have even sides), in a grid-stride loop
+// over a grid of 8 blocks per SM.
+template <typename T> __device__ __forceinline__ float2 ld2(const T* p, size_t i);
+template <> __device__ __forceinline__ float2 ld2<float>(const float* p, size_t i) {
+  return *reinterpret_cast<const float2*>(p + i);
+}
+template <> __device__ __forceinline__ float2 ld2<__half>(const __half* p, size_t i) {
+  return __half22float2(*reinterpret_cast<const __half2*>(p + i));
+}
+template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16* p, size_t i) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + i));
+}
+template <typename T> __device__ __forceinline__ void st2(T* p, size_t i, float a, float b);
+template <> __device__ __forceinline__ void st2<float>(float* p, size_t i, float a, float b) {
+  *reinterpret_cast<float2*>(p + i) = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void st2<__half>(__half* p, size_t i, float a, float b) {
+  *reinterpret_cast<__half2*>(p + i) = __floats2half2_rn(a, b);
+}
+template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16* p, size_t i, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p + i) = __floats2bfloat162_rn(a, b);
+}
+
+template <int DIM, typename T, bool MASKED, typename TB>
+__global__ void __launch_bounds__(256) k_down_saw(LevelDev L, const TB* __restrict__ b, T* __restrict__ x,
+                                                  T* __restrict__ bcoarse, const SolveState* __restrict__ st) {
+  chain_enter();
+  if (st && st->inner_done) return;
+  const int cnx = L.nx >> 1, cny = L.ny >> 1, cnz = DIM == 3 ? L.nz >> 1 : 1;
+  const size_t nc = (size_t)cnx * cny * cnz;
+  const float inv_children = DIM == 3 ? 0.125f : 0.25f;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (size_t)gridDim.x * blockDim.x) {
+    const int cx = (int)(c % cnx);
+    const size_t t = c / cnx;
+    const int cy = (int)(t % cny), cz = (int)(t / cny);
+    const int gx = 2 * cx;
+    float sum = 0.f;
+#pragma unroll
+    for (int az = 0; az < (DIM == 3 ? 2 : 1); ++az)
+#pragma unroll
+      for (int ay = 0; ay < 2; ++ay) {
+        const int gy = 2 * cy + ay, gz = DIM == 3 ? 2 * cz + az : 0;
+        const size_t i = gidx(L, gx, gy, gz);
+        const float2 bv = ld2(b, i);
+        uint8_t m0 = kFluidBit, m1 = kFluidBit;
+        if (MASKED) {
+          m0 = L.cell[i];
+          m1 = L.cell[i + 1];
+        }
+        const float x0 = m0 ? bv.x / diag_at<DIM, MASKED>(L, gx, gy, gz, m0) : 0.f;
+        const float x1 = m1 ? bv.y / diag_at<DIM, MASKED>(L, gx + 1, gy, gz, m1) : 0.f;
+        st2(x, i, x0, x1);
+        if (m0) sum += bv.x;
+        if (m1) sum += bv.y;
+      }
+    bcoarse[c] = cvt<T>(sum * inv_children);
+  }
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+      n = 1;
+  }
+  return n;
+}
+
+template <int DIM, typename T, bool MASKED, typename TB>
+cudaError_t launch_down_saw(const LevelDev& L, const void* b, void* x, void* bcoarse, const SolveState* st,
+                            cudaStream_t s) {
+  const size_t nc = (size_t)(L.nx / 2) * (L.ny / 2) * (DIM == 3 ? L.nz / 2 : 1);
+  const size_t want = (nc + 255) / 256, cap = (size_t)sm_count() * 8;
+  const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+  return launch_chain(k_down_saw<DIM, T, MASKED, TB>, dim3(blocks), dim3(256), 0, s, L, (const TB*)b, (T*)x,
+                      (T*)bcoarse, st);
+}
+
 // Raise the dynamic shared-memory limit of the level kernels once (at
 // create, outside any stream capture).
 template <int DIM, typename T, bool MASKED, typename TB>
@@ -83,6 +169,8 @@ cudaError_t prepare_level_kernels(int pre, int post) {
 #define NPMG_INST_LEVEL_TB(DIM, T, M, TB)                                                                    \
   template cudaError_t launch_down<DIM, T, M, TB>(const LevelDev&, const void*, void*, void*, int, float,      \
                                                   const SolveState*, cudaStream_t);                            \
+  template cudaError_t launch_down_saw<DIM, T, M, TB>(const LevelDev&, const void*, void*, void*,              \
+                                                      const SolveState*, cudaStream_t);                        \
   template cudaError_t launch_up<DIM, T, M, false, TB>(const LevelDev&, const void*, const void*, void*,      \
                                                        const void*, int, float, float, SolveState*, double*,   \
                                                        cudaStream_t);                                          \

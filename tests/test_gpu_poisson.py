@@ -163,11 +163,13 @@ def test_streaming_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
     thresholds keep for large levels (>= 2^19 / 2^15 cells), forced onto
     every eligible level and, in 3D, onto the split (column, plane)
     schedule: one cycle and full solves (float32 and FP16 level storage)
-    match the oracle with the bounds above."""
+    match the oracle with the bounds above, and so does one sawtooth cycle
+    (whose up legs run on these kernels)."""
     monkeypatch.setenv("NPMG_STREAM2D_MIN", "0")
     monkeypatch.setenv("NPMG_ROWS3D_MIN", "0")
     monkeypatch.setenv("NPMG_ROWS3D_SPLIT", "2")
     test_one_cycle_matches_oracle(L, shape, bc, frac)
+    test_sawtooth_cycle_matches_oracle(L, shape, bc, frac)
     solid, h = make_case(shape, bc, frac)
     b = I.blob_rhs(shape, 2, solid=solid).astype(np.float32)
     solve_and_check(L, shape, bc, solid, h, b)
@@ -178,7 +180,8 @@ def test_streaming_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
 def test_sawtooth_cycle_matches_oracle(L, shape, bc, frac):
     """One cycle of the paper's sawtooth (App. B recursion; omega 2/3, two
     post sweeps, coarse scale 1/2) equals the oracle's sawtooth cycle, up to
-    the h_0x^2 scaling of A'."""
+    the h_0x^2 scaling of A' (down legs on the tile kernel, up legs on the
+    level's fused kernel, as in the V cycle)."""
     solid, h = make_case(shape, bc, frac)
     hdl = create(L, shape, bc, solid, h, cycle=L.MG_CYCLE_SAWTOOTH, coarse_scale=0.5)
     try:
