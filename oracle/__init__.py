@@ -17,7 +17,12 @@ checked against the paper by eye:
   refinement loop, plus the dense direct solve that defines the answer.
 * ``ns``       -- one projection time step of Algorithm 1 on a staggered
   (MAC) grid, with the predictor-corrector momentum update of Sec. 2.3
-  (Eq. predictor-Burgers / Tn+1) and the solid-body absorption term sigma.
+  (Eq. predictor-Burgers / Tn+1) and the solid-body absorption term sigma;
+  optionally the finite-element 9/27-point filters of App. A.
+* ``advdiff``  -- one implicit backward-Euler advection-diffusion step
+  (Eq. BE-advection-concise, upwind or central advection) and its multigrid
+  solution by V or sawtooth cycles as a stationary iteration (Sec. 3.2).
+* ``convnet``  -- the learned initial-guess network and its training step.
 
 Pins for every function live in ``tests/test_oracle_*.py`` (closed-form
 eigenpairs, manufactured solutions, dense solves, invariants).  Functions that
