@@ -17,7 +17,10 @@ Dirichlet), ``poisson3d`` (256^3, 8 blobs; ``--prec fp32|fp16|bf16``),
 instances) and ``timing3d`` (the paper's timing workload of Sec. 3.4: flow
 past a cube in an n^3 domain, ``--size 128|256|512``, 20 multigrid
 iterations per time step with the finite-element filters; metric: seconds
-for five time steps).
+for five time steps); ``advdiff`` (one implicit advection-diffusion step
+of Sec. 3.2: 128^2 nodes, upwind, C = 50, ``--ad-size 128|1024|4096``;
+V(2,2) cycles to relres 1e-6, or ``--cycle sawtooth`` for the paper's form
+stopped on the L1 change 1e-5).
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (each step one oracle step of a bounded
@@ -44,6 +47,7 @@ from paper_2402_17913_gb300 import inputs as I  # noqa: E402
 
 METRIC = "solved unknowns/sec to 1e-6 rel residual"
 TIMING_METRIC = "seconds for 5 time steps of the 3D flow past a cube"
+AD_L1_METRIC = "solved unknowns/sec to an L1 change of 1e-5 per cycle"
 UNIT = "unknowns/s"
 TOL = 1e-6
 
@@ -73,7 +77,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="ns2d",
-                    choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched", "timing3d"])
+                    choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched", "timing3d", "advdiff"])
+    ap.add_argument("--ad-size", type=int, default=128, choices=[128, 1024, 4096],
+                    help="advdiff: nodes per side")
     ap.add_argument("--size", type=int, default=256, choices=[128, 256, 512],
                     help="timing3d: cells per side of the cubic domain")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
@@ -183,6 +189,36 @@ class Timing3D:
                 "solver": ("20 stationary sawtooth cycles (coarse scale 1/2) per step" if self.cycle == "sawtooth"
                            else "V(2,2)-preconditioned CG to relres 1e-6 per step"),
                 "paper_seconds_t4": t4, "paper_seconds_xeon_cpu": cpu,
+                "l2": "256 MiB buffer written between timed steps"}
+
+
+class AdvDiff:
+    """One backward-Euler advection-diffusion step (Sec. 3.2): n^2 nodes
+    (h = 1), (u, v) = (1, 1), nu = 2, dt = 50 (C = 50), upwind advection, a
+    Gaussian of width 10 n / 128 at the centre as T^n and initial guess.
+    ``cycle='v'``: V(2,2) cycles (omega 2/3, re-discretised coarse levels)
+    to relres 1e-6; ``'sawtooth'``: the paper's form (Jacobi alpha = 1, one
+    sweep, halved coarse correction) until the L1 change of one cycle is
+    <= 1e-5."""
+    dim = 2
+    h, dt, nu, u, v = 1.0, 50.0, 2.0, 1.0, 1.0
+
+    def __init__(self, n=128, cycle="v"):
+        self.n, self.cycle = n, cycle
+        self.name = "advdiff_%d" % n
+        self.shape = (n, n)
+        self.units = n * n
+        self.gamma = 10.0 * n / 128.0
+
+    def rhs(self):
+        return I.advdiff_gaussian(self.shape, gamma=self.gamma).astype(np.float32)
+
+    def config(self):
+        return {"workload": "one implicit advection-diffusion step (upwind, C = 50) solved by multigrid",
+                "nodes": [self.n, self.n], "u": self.u, "v": self.v, "nu": self.nu, "dt": self.dt,
+                "gaussian_width": self.gamma,
+                "solver": ("V(2,2) cycles to relres 1e-6" if self.cycle == "v"
+                           else "sawtooth (alpha 1, one sweep, coarse scale 1/2) to L1 change 1e-5"),
                 "l2": "256 MiB buffer written between timed steps"}
 
 
@@ -477,6 +513,34 @@ def run_gpu(args, rank, world):
                 hdst.copy_(d, non_blocking=True)
         io_bytes = sum(t.numel() * 4 for t in hb)
         cleanup = lambda: L.mg_destroy_batched(bh)  # noqa: E731
+    elif args.config == "advdiff":
+        wl = AdvDiff(args.ad_size, args.cycle)
+        if args.cycle == "sawtooth":
+            opt = L.ad_default_options(cycle=L.MG_CYCLE_SAWTOOTH, pre=0, post=1, omega=1.0, coarse_scale=0.5,
+                                       max_cycles=5000)
+            ad_tol, ad_l1 = 0.0, 1e-5
+        else:
+            opt = L.ad_default_options()
+            ad_tol, ad_l1 = TOL, 0.0
+        hd = L.ad_create((wl.n, wl.n), wl.h, wl.dt, wl.nu, wl.u, wl.v, L.AD_UPWIND, opt)
+        mg = None
+        b_host = torch.from_numpy(wl.rhs()).pin_memory()
+        x_host = torch.zeros_like(b_host).pin_memory()
+        b = b_host.to(dev)
+        x = torch.zeros_like(b)
+        stats = []
+        wl.levels, wl.kc = L.ad_num_levels(hd), L.ad_coarse_start(hd)
+
+        def step():
+            _, st = L.ad_solve(hd, b, x, rel_tol=ad_tol, l1_tol=ad_l1)
+            stats.append(dict(st, iters=st["cycles"], outer=1))
+
+        def e2e_step():
+            b.copy_(b_host, non_blocking=True)
+            step()
+            x_host.copy_(x, non_blocking=True)
+        io_bytes = b_host.numel() * 4
+        cleanup = lambda: L.ad_destroy(hd)  # noqa: E731
     else:
         shape = (256, 256) if args.config == "poisson2d" else (256, 256, 256)
         wl = Poisson(shape, args.prec, args.cycle)
@@ -513,7 +577,7 @@ def run_gpu(args, rank, world):
     gn_launches0 = L.gn_kernel_launches()
     dist_barrier(world)
     # ---- timed: device-resident inputs, L2 flushed between steps
-    launches0 = L.mg_kernel_launches(mg) if mg else 0
+    launches0 = L.mg_kernel_launches(mg) if mg else (L.ad_kernel_launches(hd) if args.config == "advdiff" else 0)
     cp, cf, cpath = clocks_sampler()
     times = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -528,6 +592,8 @@ def run_gpu(args, rank, world):
     times = [a.elapsed_time(b) for a, b in ev]
     # the batched solve is one persistent kernel per solve (one graph launch)
     launches = (L.mg_kernel_launches(mg) - launches0) if mg else args.steps
+    if args.config == "advdiff":
+        launches = L.ad_kernel_launches(hd) - launches0
     launches += L.gn_kernel_launches() - gn_launches0
     step_stats = list(stats)
     total_ms = dist_max(sum(times), world)
@@ -565,6 +631,24 @@ def run_gpu(args, rank, world):
                     "traffic": recorded_traffic(wl.name, "k_batched"), "algorithmic_bytes_per_launch": algo,
                     "avg_launch_us": round(ms_solve * 1e3, 2), "share_of_step": 1.0,
                     "autotuned": {"tile": [tuned[0], tuned[1]], "sweeps": tuned[2]}}
+    elif args.config == "advdiff":
+        # the whole solve: algorithmic bytes of one cycle over the
+        # event-timed solve (level 0: residual 16 B per node - b, float64 x,
+        # r -; down leg 9 B; up leg 25 B - b, x, 1/4 e, float64 x read and
+        # written -; each tile level below: 22 B per node; the single block's
+        # levels stay on chip)
+        cleanup()
+        n0 = wl.units
+        per_cycle = 50 * n0 + sum(22 * (n0 >> (2 * k)) for k in range(1, wl.kc))
+        cyc = statistics.mean(st["cycles"] for st in step_stats)
+        ms_solve = total_ms / args.steps
+        achieved = per_cycle * cyc / (ms_solve * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "whole solve (k_ad_resid, k_ad_down, k_ad_coarse, k_ad_up)",
+                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                    "algorithmic_bytes_per_cycle": per_cycle, "cycles_per_solve": cyc,
+                    "levels": wl.levels, "single_block_from_level": wl.kc,
+                    "avg_cycle_us": round(ms_solve * 1e3 / max(cyc, 1), 2)}
     else:
         # ---- profiled pass: per-kernel-class event times (graph off)
         L.mg_profile_enable(mg, True)
@@ -608,6 +692,12 @@ def run_gpu(args, rank, world):
                   "relres_max": max(s["relres"] for s in step_stats) if step_stats else None,
                   "outer_mean": statistics.mean(s["outer"] for s in step_stats) if step_stats else None},
     }
+    if args.config == "advdiff":
+        out["solve"].update(cycles_mean=out["solve"].pop("cg_iters_mean"),
+                            l1_first=step_stats[-1]["l1_first"], l1_last=step_stats[-1]["l1_last"])
+        if args.cycle == "sawtooth":
+            out["metric"] = AD_L1_METRIC
+            out["e2e"]["unit"] = UNIT
     if args.config == "timing3d":
         # the paper's metric: seconds for five time steps of 20 iterations
         t4 = wl.paper_s.get(wl.n, (None, None))[0]
@@ -650,6 +740,23 @@ def oracle_step_time(wl, budget_s=30.0, max_steps=3):
         sample = "%d oracle step(s) of the %s projection workload (%s)" % (
             steps, "x".join(map(str, wl.cells)),
             "20 sawtooth cycles" if isinstance(wl, Timing3D) and wl.cycle == "sawtooth" else "pressure solve to 1e-6")
+    elif isinstance(wl, AdvDiff):
+        from oracle import advdiff as AD
+        hier = AD.build_hierarchy(wl.shape, wl.h, wl.dt, wl.nu, wl.u, wl.v, 'upwind', 'rediscretise')
+        if wl.cycle == "sawtooth":
+            mg = AD.ADMultigrid(hier, 'sawtooth', 0, 1, 1.0, 0.5)
+            kw = dict(tol=0.0, l1_tol=1e-5, max_cycles=5000)
+        else:
+            mg = AD.ADMultigrid(hier, 'V', 2, 2, 2.0 / 3.0, 1.0)
+            kw = dict(tol=TOL)
+        b = wl.rhs().astype(np.float64)
+        while steps < max_steps and t_total < budget_s:
+            t0 = time.perf_counter()
+            mg.solve(b, **kw)
+            t_total += time.perf_counter() - t0
+            steps += 1
+            units += wl.units
+        sample = "%d oracle solve(s) of the %d^2 advection-diffusion step" % (steps, wl.n)
     elif isinstance(wl, Batched):
         for k in range(len(wl.shapes)):
             if steps >= max_steps or t_total >= budget_s:
@@ -723,7 +830,8 @@ def main():
         samples = {"ns2d": lambda: NS2D(scale=4, fe=fe), "ns3d": lambda: NS3D(scale=4, fe=fe),
                    "poisson2d": lambda: Poisson((256, 256), args.prec),
                    "poisson3d": lambda: Poisson((64, 64, 64), args.prec), "batched": lambda: Batched(limit=16),
-                   "timing3d": lambda: Timing3D(args.size, args.cycle, scale=args.size // 32)}
+                   "timing3d": lambda: Timing3D(args.size, args.cycle, scale=args.size // 32),
+                   "advdiff": lambda: AdvDiff(min(args.ad_size, 512), args.cycle)}
         wl = samples[args.config]()
         t0 = time.perf_counter()
         rate, sample, n = oracle_step_time(wl, budget_s=1e9, max_steps=args.warmup + args.steps)
@@ -736,11 +844,14 @@ def main():
                     "ns3d": "quarter-resolution copy (64x32x32 cells, 8-cell cube, Re kept at 100)",
                     "poisson3d": "64^3 copy of the blob workload",
                     "batched": "the first 16 instances of the batch",
-                    "timing3d": "32^3 copy (cube and Re scaled alike); seconds scaled to the full size by cells"}.get(
+                    "timing3d": "32^3 copy (cube and Re scaled alike); seconds scaled to the full size by cells",
+                    "advdiff": "the step itself up to 512^2 nodes, else a 512^2 copy"}.get(
                         args.config, "the workload itself")),
                 "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
                 "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
+        if args.config == "advdiff" and args.cycle == "sawtooth":
+            line["metric"] = AD_L1_METRIC
         if args.config == "timing3d":
             full = Timing3D(args.size, args.cycle)
             secs = 5 * full.units / rate
@@ -756,6 +867,7 @@ def main():
             # 3D: the full-size oracle step takes minutes; time a smaller copy
             cpu_wl = {"ns3d": lambda: NS3D(scale=2, fe=wl.fe),
                       "timing3d": lambda: Timing3D(args.size, args.cycle, scale=max(1, args.size // 64)),
+                      "advdiff": lambda: AdvDiff(min(args.ad_size, 512), args.cycle),
                       "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
                 args.config, lambda: wl)()
             rate, sample, n = oracle_step_time(cpu_wl, budget_s=25.0, max_steps=ms)

@@ -466,6 +466,79 @@ mg_status ns_last_fields(ns_handle ns, const float** d_b, const float** d_dp);
 mg_status ns_coarse_fields(ns_handle ns, int level, const float* d_p, float* d_b_c, float* d_p_c, float* d_dp_c,
                            uint8_t* d_solid_c, void* stream);
 
+/*
+ * Implicit advection-diffusion step (Sec. 2.2, Eq. BE-advection-concise;
+ * Sec. 3.2 "Multigrid solver for the advection-diffusion equation").
+ *
+ * One backward-Euler step of dT/dt + u dT/dx + v dT/dy - nu Lap T = 0 on an
+ * nx x ny node grid of spacing h with zero padding (Sec. 2.1):
+ *   A T^{n+1} = T^n,  A = I + dt (u D_x + v D_y - nu Lap_h),
+ * D_x the central difference (Eq. A) or the first-order upwind difference
+ * (backward for u >= 0, forward for u < 0; the printed Eq. A-up holds the
+ * forward differences, the upwind scheme of a velocity along -x and -y),
+ * Lap_h the 5-point filter of App. A.  A is nonsymmetric, so the solve is
+ * the cycle as a stationary iteration x <- x + M (b - A x) (no CG), with a
+ * float64 iterate, a float64 residual and the cycle in float32.
+ *
+ * Levels: nodes halved per level (2x2 average restriction, copy
+ * prolongation); the coarse stencils re-discretised at spacing 2^k h
+ * (AD_COARSE_REDISCRETISE, App. B) or the Galerkin product R A P
+ * (AD_COARSE_GALERKIN: the re-discretised stencil with the diffusion term
+ * times 2^k).  Cycle MG_CYCLE_V: `pre` relaxed Jacobi sweeps from zero,
+ * residual restricted, recursion, `coarse_scale` times the copied
+ * correction, `post` sweeps; the coarsest level (<= 256 nodes) by a dense
+ * inverse computed at create.  MG_CYCLE_SAWTOOTH: the paper's cycle (the
+ * residual restricted without smoothing, r / c plus the scaled correction
+ * on the way up, then `post` sweeps; its alpha = 1 and one sweep are
+ * omega = 1, post = 1).
+ *
+ * ad_create: cells = {nx, ny} (8 .. 65536, divisible by 2^(levels-1));
+ *   h, dt > 0; nu >= 0; scheme AD_UPWIND or AD_CENTRAL; opt NULL = defaults.
+ *   Allocates every buffer; MG_ERR_INVALID / MG_ERR_OOM / MG_ERR_CUDA.
+ * ad_solve: d_b = T^n, d_x0 = initial guess or NULL (= T^n, the previous
+ *   time level, Sec. 3.2), d_x = T^{n+1} out (nx * ny float32 device
+ *   arrays, [y][x], x fastest; d_x may alias d_x0).  Stops when
+ *   ||b - A x||_2 / ||b||_2 <= rel_tol (checked before every cycle), when
+ *   the L1 norm of one cycle's change of x is <= l1_tol (the paper's gauge;
+ *   0 disables it), or after opt.max_cycles cycles (MG_NOT_CONVERGED);
+ *   MG_DIVERGED when the residual grows 1000-fold.  Enqueued on stream and
+ *   synchronised every 8 cycles.
+ */
+enum { AD_UPWIND = 0, AD_CENTRAL = 1 };
+enum { AD_COARSE_REDISCRETISE = 0, AD_COARSE_GALERKIN = 1 };
+typedef struct {
+  int cycle;            /* MG_CYCLE_V (default) or MG_CYCLE_SAWTOOTH          */
+  int pre;              /* V: Jacobi sweeps before restriction, 0..2 (2)     */
+  int post;             /* sweeps after the correction, 0..2 (2)              */
+  double omega;         /* Jacobi relaxation (2/3)                            */
+  double coarse_scale;  /* factor on every coarse correction (1)              */
+  int coarse_op;        /* AD_COARSE_REDISCRETISE (default) or _GALERKIN      */
+  int levels;           /* 0 = halve while both sides stay even and >= 4      */
+  int max_cycles;       /* (1000)                                             */
+} ad_options;
+typedef struct {
+  int status;           /* mg_status of the solve                             */
+  int cycles;           /* cycles run                                         */
+  double relres0;       /* relres of the initial guess                        */
+  double relres;        /* relres of the returned iterate (float64)           */
+  double l1_first;      /* L1 norm of the first cycle's change of x           */
+  double l1_last;       /* L1 norm of the last cycle's change of x            */
+  float ms;             /* device time of the solve, milliseconds             */
+} ad_stats;
+typedef struct ad_handle_s* ad_handle;
+mg_status ad_default_options(ad_options* opt);
+mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
+                    double nu, double u, double v, int scheme,
+                    const ad_options* opt, void* stream);
+mg_status ad_solve(ad_handle h, const float* d_b, const float* d_x0, float* d_x,
+                   double rel_tol, double l1_tol, void* stream, ad_stats* out);
+/* Levels of the hierarchy; the first level handled by the single-block
+   kernel; kernels launched so far (0 for NULL). */
+int ad_num_levels(ad_handle h);
+int ad_coarse_start(ad_handle h);
+int64_t ad_kernel_launches(ad_handle h);
+mg_status ad_destroy(ad_handle h);
+
 /* The pressure handle inside ns (owned by ns; do not destroy). */
 mg_handle ns_pressure_handle(ns_handle ns);
 mg_status ns_destroy(ns_handle ns);

@@ -194,12 +194,3 @@ class ADMultigrid:
                 break
         return x, k, rr, l1
 
-
-def gaussian(shape, gamma=10.0, centre=(0.0, 0.0)):
-    """Eq. Gaussian_distribution_T (the Gaussian term) on nodes x_l = l -
-    (n - 1) / 2 (the domain centred on the origin, spacing 1)."""
-    ny, nx = shape
-    x = np.arange(nx) - (nx - 1) / 2.0
-    y = np.arange(ny) - (ny - 1) / 2.0
-    X, Y = np.meshgrid(x, y)
-    return np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / (2.0 * gamma * gamma))

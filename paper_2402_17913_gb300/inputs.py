@@ -208,3 +208,15 @@ def convnet_weights(seed, layer_io=((2, 16), (16, 16), (16, 16), (16, 16), (16, 
     w = [rng.standard_normal((27, ci, co)) * np.sqrt(2.0 / (27 * ci)) for ci, co in layer_io]
     w[-1] = w[-1] * last_scale
     return w
+
+
+def advdiff_gaussian(shape, gamma=10.0, centre=(0.0, 0.0)):
+    """The Gaussian initial condition of the advection-diffusion tests (Eq.
+    Gaussian_distribution_T, its first term): exp(-((x - x0)^2 + (y -
+    y0)^2) / (2 gamma^2)) on nodes x_l = l - (n - 1) / 2, y likewise (the
+    domain centred on the origin, spacing 1), float64 array [y, x]."""
+    ny, nx = shape
+    x = np.arange(nx) - (nx - 1) / 2.0
+    y = np.arange(ny) - (ny - 1) / 2.0
+    X, Y = np.meshgrid(x, y)
+    return np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / (2.0 * gamma * gamma))

@@ -16,6 +16,8 @@ MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1
 MG_FP32, MG_MIXED_FP16, MG_MIXED_BF16 = 0, 1, 2
 MG_CYCLE_V, MG_CYCLE_SAWTOOTH = 0, 1
 NS_STENCIL_FD, NS_STENCIL_FE = 0, 1
+AD_UPWIND, AD_CENTRAL = 0, 1
+AD_COARSE_REDISCRETISE, AD_COARSE_GALERKIN = 0, 1
 
 STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
                 4: "MG_NOT_CONVERGED", 5: "MG_DIVERGED", 6: "MG_TIMEOUT"}
@@ -30,7 +32,8 @@ EXPORTED = [
     "gn_create", "gn_set_weights", "gn_get_weights", "gn_forward", "gn_gradients", "gn_adam_step",
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
     "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches", "ns_set_guess_level",
-    "ns_coarse_fields", "ns_set_stencils",
+    "ns_coarse_fields", "ns_set_stencils", "ad_default_options", "ad_create", "ad_solve", "ad_num_levels",
+    "ad_coarse_start", "ad_kernel_launches", "ad_destroy",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
@@ -69,6 +72,23 @@ class MGError(RuntimeError):
 
 _lib = None
 _vp = ctypes.c_void_p
+class AdOptions(ctypes.Structure):
+    _fields_ = [("cycle", ctypes.c_int), ("pre", ctypes.c_int), ("post", ctypes.c_int),
+                ("omega", ctypes.c_double), ("coarse_scale", ctypes.c_double), ("coarse_op", ctypes.c_int),
+                ("levels", ctypes.c_int), ("max_cycles", ctypes.c_int)]
+
+
+class AdStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int), ("relres0", ctypes.c_double),
+                ("relres", ctypes.c_double), ("l1_first", ctypes.c_double), ("l1_last", ctypes.c_double),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
 _i64_3 = ctypes.c_int64 * 3
 _d3 = ctypes.c_double * 3
 _i6 = ctypes.c_int * 6
@@ -142,6 +162,16 @@ def load():
         "ns_set_guess": (ctypes.c_int, [_vp, _vp]),
         "ns_set_guess_level": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
         "ns_set_stencils": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "ad_default_options": (ctypes.c_int, [ctypes.POINTER(AdOptions)]),
+        "ad_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64 * 2, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(AdOptions), _vp]),
+        "ad_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp,
+                                    ctypes.POINTER(AdStats)]),
+        "ad_num_levels": (ctypes.c_int, [_vp]),
+        "ad_coarse_start": (ctypes.c_int, [_vp]),
+        "ad_kernel_launches": (ctypes.c_int64, [_vp]),
+        "ad_destroy": (ctypes.c_int, [_vp]),
         "ns_coarse_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -479,6 +509,48 @@ def ns_set_guess(ns, g):
 
 def ns_set_guess_level(ns, g, level):
     _check(load().ns_set_guess_level(ns, g, int(level)))
+
+
+def ad_default_options(**kw):
+    o = AdOptions()
+    _check(load().ad_default_options(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ad_create(cells, h, dt, nu, u, v, scheme=AD_UPWIND, options=None, stream=None):
+    """Implicit advection-diffusion step handle; cells = (nx, ny)."""
+    out = _vp()
+    opt = options if options is not None else ad_default_options()
+    _check(load().ad_create(ctypes.byref(out), (ctypes.c_int64 * 2)(*cells), h, dt, nu, u, v, int(scheme),
+                            ctypes.byref(opt), stream_ptr(stream)))
+    return out.value
+
+
+def ad_solve(hd, b, x, rel_tol=1e-6, l1_tol=0.0, x0=None, stream=None):
+    """T^{n+1} into x from T^n = b (initial guess x0, default b); returns (status, stats)."""
+    st = AdStats()
+    status = load().ad_solve(hd, ptr(b), ptr(x0), ptr(x), rel_tol, l1_tol, stream_ptr(stream), ctypes.byref(st))
+    _check(status, allow=(MG_OK, MG_NOT_CONVERGED, MG_DIVERGED))
+    return status, st.as_dict()
+
+
+def ad_num_levels(hd):
+    return load().ad_num_levels(hd)
+
+
+def ad_coarse_start(hd):
+    return load().ad_coarse_start(hd)
+
+
+def ad_kernel_launches(hd):
+    return load().ad_kernel_launches(hd)
+
+
+def ad_destroy(hd):
+    if hd:
+        load().ad_destroy(hd)
 
 
 def ns_set_stencils(ns, stencil):

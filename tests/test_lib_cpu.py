@@ -24,7 +24,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", path)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:mg|ns|gn)_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:mg|ns|gn|ad)_\w+)\s*\(", text, flags=re.M):
             names.append(m.group(1))
     return sorted(set(names))
 
@@ -80,6 +80,29 @@ def test_solve_rejects_null(lib):
     assert lib.mg_solve(None, None, None, 1e-6, None, None) == L.MG_ERR_INVALID
     assert lib.ns_step(None, None, None, None, None, 0.1, 0.1, 1.0, 1e-6, None, None) == L.MG_ERR_INVALID
     assert lib.ns_set_stencils(None, L.NS_STENCIL_FE) == L.MG_ERR_INVALID
+    assert lib.ad_solve(None, None, None, None, 1e-6, 0.0, None, None) == L.MG_ERR_INVALID
+    assert lib.ad_num_levels(None) == 0 and lib.ad_kernel_launches(None) == 0 and lib.ad_destroy(None) == L.MG_OK
+
+
+def test_ad_create_rejects_invalid_arguments(lib):
+    """Argument checks of ad_create run before any CUDA call."""
+    from paper_2402_17913_gb300 import lib as L
+    out = ctypes.c_void_p()
+    cells = (ctypes.c_int64 * 2)(128, 128)
+    o = L.ad_default_options()
+    assert lib.ad_create(ctypes.byref(out), cells, 1.0, 0.0, 2.0, 1.0, 1.0, L.AD_UPWIND, ctypes.byref(o),
+                         None) == L.MG_ERR_INVALID  # dt = 0
+    assert lib.ad_create(ctypes.byref(out), (ctypes.c_int64 * 2)(6, 128), 1.0, 1.0, 2.0, 1.0, 1.0, L.AD_UPWIND,
+                         ctypes.byref(o), None) == L.MG_ERR_INVALID  # side < 8
+    assert lib.ad_create(ctypes.byref(out), cells, 1.0, 1.0, 2.0, 1.0, 1.0, 7, ctypes.byref(o),
+                         None) == L.MG_ERR_INVALID  # scheme
+    bad = L.ad_default_options(pre=3)
+    assert lib.ad_create(ctypes.byref(out), cells, 1.0, 1.0, 2.0, 1.0, 1.0, L.AD_UPWIND, ctypes.byref(bad),
+                         None) == L.MG_ERR_INVALID
+    big = L.ad_default_options(levels=2)  # coarsest 64 x 64 > 256 nodes for the dense inverse
+    assert lib.ad_create(ctypes.byref(out), cells, 1.0, 1.0, 2.0, 1.0, 1.0, L.AD_UPWIND, ctypes.byref(big),
+                         None) == L.MG_ERR_INVALID
+    assert not out.value
 
 
 def test_guess_network_rejects_invalid_arguments(lib):

@@ -9,6 +9,7 @@ import pytest
 import scipy.fft
 
 from oracle import advdiff as A
+from paper_2402_17913_gb300 import inputs as I
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "advdiff_filters_sec2.txt")
 
@@ -136,7 +137,7 @@ def test_multigrid_solves_to_the_dense_answer(cycle, coarse, pre, post, omega, s
     """The stationary multigrid iteration reaches relres 1e-10 and the dense
     solution on a 32x32 copy of the Sec. 3.2 test (upwind, C = 50)."""
     shape = (32, 32)
-    b = A.gaussian(shape, gamma=3.0)
+    b = I.advdiff_gaussian(shape, gamma=3.0)
     hier = A.build_hierarchy(shape, 1.0, 50.0 / 4, 2.0 / 4, 1.0, 1.0, 'upwind', coarse)
     mg = A.ADMultigrid(hier, cycle, pre, post, omega, s)
     x, k, rr, _ = mg.solve(b, tol=1e-10, max_cycles=400)
@@ -165,7 +166,7 @@ def test_paper_reported_l1_reduction():
     coarse correction (the reading the stationary sawtooth needs) the
     oracle's iteration does; with the plain correction it diverges."""
     shape = (128, 128)
-    b = A.gaussian(shape, gamma=10.0)
+    b = I.advdiff_gaussian(shape, gamma=10.0)
     hier = A.build_hierarchy(shape, 1.0, 50.0, 2.0, 1.0, 1.0, 'upwind', 'rediscretise')
     _, _, _, l1 = A.ADMultigrid(hier, 'sawtooth', 0, 1, 1.0, 0.5).solve(b, tol=0.0, max_cycles=50)
     assert len(l1) == 50 and l1[49] < 1e-3 * l1[0], (l1[0], l1[49])
