@@ -5,10 +5,13 @@
 // padding (Sec. 2.1):
 //   (A T)_l = c T_l + xm T_{l-1} + xp T_{l+1} + ym T_{m-1} + yp T_{m+1}.
 //
-// Layout: node arrays [y][x], x fastest.  The iterate is float64 (the
+// Layout: node arrays [y][x], x fastest.  The iterate is float-float (a
+// pair hi + lo of float32 per node, about 48 significant bits: the
 // operator's norm is about 1 + 8 nu dt / h^2, so a float32 iterate alone
 // leaves a relative residual near 1e-4); the residual is evaluated in
-// float64 and the cycle runs on it in float32.
+// float-float with error-free products and sums (FP32 arithmetic: GB300's
+// FP64 rate is a small fraction of its FP32 rate) and the cycle runs on it
+// in float32.
 //
 // Per cycle: k_ad_resid (r = b - A x and ||r||, the convergence decision),
 // on levels 0 .. kc-1 a tile down leg (V: pre sweeps from zero, residual,
@@ -102,16 +105,34 @@ __device__ bool grid_sum(double v, double* partials, unsigned int* counter, unsi
   return true;
 }
 
-// x = x0 (or b), ||b||^2, state reset.
+// Error-free transformations (Knuth's two-sum, the FMA two-product): a + b
+// = s + e and a * b = p + e exactly in float32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// Nodes are visited row by row: blocks stride over rows, threads over x
+// (no 64-bit index division).
+#define AD_FOR_NODES(L)                                                 \
+  for (int iy = blockIdx.x; iy < (L).ny; iy += gridDim.x)               \
+    for (int ix = threadIdx.x; ix < (L).nx; ix += blockDim.x)
+
+// x = x0 (or b) as (hi, lo = 0), ||b||^2, state reset.
 __global__ void __launch_bounds__(kT) k_ad_init(Lev L, const float* __restrict__ b, const float* __restrict__ x0,
-                                                double* __restrict__ x, State* st, double tol, double l1_tol,
+                                                float2* __restrict__ x, State* st, double tol, double l1_tol,
                                                 int max_cycles, double* partials) {
-  const size_t n = (size_t)L.nx * L.ny;
-  double acc = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  float acc = 0.f;
+  AD_FOR_NODES(L) {
+    const size_t i = (size_t)iy * L.nx + ix;
     const float bv = b[i];
-    x[i] = (double)(x0 ? x0[i] : bv);
-    acc += (double)bv * bv;
+    x[i] = make_float2(x0 ? x0[i] : bv, 0.f);
+    acc = fmaf(bv, bv, acc);
   }
   double tot;
   if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) {
@@ -128,25 +149,34 @@ __global__ void __launch_bounds__(kT) k_ad_init(Lev L, const float* __restrict__
   }
 }
 
-// r = b - A x in float64 (rounded to float32 for the cycle), relres and the
-// stopping decision.  `final` computes the relres of the returned iterate
-// whatever the flag says and decides nothing.
-__global__ void __launch_bounds__(kT) k_ad_resid(Lev L, const float* __restrict__ b, const double* __restrict__ x,
+// One term -w * (hi + lo) of b - A x into the float-float sum (S, E).
+__device__ __forceinline__ void ff_sub_term(float w, float2 x, float& S, float& E) {
+  float p, pe, se;
+  two_prod(-w, x.x, p, pe);
+  two_sum(S, p, S, se);
+  E += se + pe;
+  E = fmaf(-w, x.y, E);
+}
+
+// r = b - A x in float-float (rounded to float32 for the cycle), relres and
+// the stopping decision.  `final` computes the relres of the returned
+// iterate whatever the flag says and decides nothing.
+__global__ void __launch_bounds__(kT) k_ad_resid(Lev L, const float* __restrict__ b, const float2* __restrict__ x,
                                                  float* __restrict__ r, State* st, double* partials, int final) {
   chain_enter();
   if (!final && st->done) return;
-  const size_t n = (size_t)L.nx * L.ny;
-  double acc = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % L.nx), iy = (int)(i / L.nx);
-    double a = (double)L.c * x[i];
-    if (ix > 0) a += (double)L.xm * x[i - 1];
-    if (ix + 1 < L.nx) a += (double)L.xp * x[i + 1];
-    if (iy > 0) a += (double)L.ym * x[i - L.nx];
-    if (iy + 1 < L.ny) a += (double)L.yp * x[i + L.nx];
-    const double rv = (double)b[i] - a;
-    if (!final) r[i] = (float)rv;
-    acc += rv * rv;
+  float acc = 0.f;
+  AD_FOR_NODES(L) {
+    const size_t i = (size_t)iy * L.nx + ix;
+    float S = b[i], E = 0.f;
+    ff_sub_term(L.c, x[i], S, E);
+    if (ix > 0) ff_sub_term(L.xm, x[i - 1], S, E);
+    if (ix + 1 < L.nx) ff_sub_term(L.xp, x[i + 1], S, E);
+    if (iy > 0) ff_sub_term(L.ym, x[i - L.nx], S, E);
+    if (iy + 1 < L.ny) ff_sub_term(L.yp, x[i + L.nx], S, E);
+    const float rv = S + E;
+    if (!final) r[i] = rv;
+    acc = fmaf(rv, rv, acc);
   }
   double tot;
   if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) {
@@ -258,7 +288,7 @@ __global__ void __launch_bounds__(kT) k_ad_down_saw(Lev L, const float* __restri
 template <int POST, bool FINEST>
 __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b, const float* __restrict__ x,
                                               const float* __restrict__ e, float* __restrict__ y,
-                                              double* __restrict__ x64, float s, float omega, State* st,
+                                              float2* __restrict__ xff, float s, float omega, State* st,
                                               double* partials) {
   chain_enter();
   if (st->done) return;
@@ -297,7 +327,7 @@ __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b
     cur = nxt;
     nxt = t;
   }
-  double acc = 0.0;
+  float acc = 0.f;
   for (int i = threadIdx.x; i < TX * TY; i += kT) {
     const int tx = i % TX, ty = i / TX;
     const int gx = blockIdx.x * TX + tx, gy = blockIdx.y * TY + ty;
@@ -305,8 +335,14 @@ __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b
       const size_t gi = (size_t)gy * L.nx + gx;
       const float v = cur[(R + ty) * RX + R + tx];
       if (FINEST) {
-        x64[gi] += (double)v;
-        acc += fabs((double)v);
+        // x += v in float-float, renormalised
+        const float2 xo = xff[gi];
+        float hs, he;
+        two_sum(xo.x, v, hs, he);
+        he += xo.y;
+        const float hi = hs + he;
+        xff[gi] = make_float2(hi, he - (hi - hs));
+        acc += fabsf(v);
       } else {
         y[gi] = v;
       }
@@ -446,10 +482,12 @@ __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* 
   }
 }
 
-// x (float32 output) = the float64 iterate rounded once.
-__global__ void __launch_bounds__(kT) k_ad_out(size_t n, const double* __restrict__ x64, float* __restrict__ x) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    x[i] = (float)x64[i];
+// x (float32 output) = the float-float iterate rounded once.
+__global__ void __launch_bounds__(kT) k_ad_out(size_t n, const float2* __restrict__ xff, float* __restrict__ x) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = xff[i];
+    x[i] = v.x + v.y;
+  }
 }
 
 }  // namespace ad
@@ -465,7 +503,7 @@ struct ad_handle_s {
   char* pool;
   float* b;        // copy of the caller's right-hand side (the graph's input)
   float* r;        // level-0 residual = the cycle's level-0 right-hand side
-  double* x64;     // the iterate
+  float2* xff;     // the iterate (hi, lo)
   float* bk[kMaxLevels];
   float* xk[kMaxLevels];
   float* tk[kMaxLevels];
@@ -566,6 +604,9 @@ static int grid_1d(const ad_handle_s* h, size_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// Row-strided kernels: one block per row up to 8 blocks per SM.
+static int row_grid(const ad_handle_s* h) { return std::min(h->ny, h->nsm * 8); }
+
 static dim3 tile_grid(const Lev& L) { return dim3((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY); }
 
 // One cycle: residual, down legs, the coarse block, up legs.
@@ -573,8 +614,8 @@ static cudaError_t enqueue_cycle(ad_handle_s* h, cudaStream_t s) {
   const ad_options& o = h->opt;
   const float om = (float)o.omega, sc = (float)o.coarse_scale;
   const bool saw = o.cycle == MG_CYCLE_SAWTOOTH;
-  cudaError_t e = launch_chain(k_ad_resid, dim3(grid_1d(h, (size_t)h->nx * h->ny)), dim3(kT), 0, s, h->lv[0],
-                               (const float*)h->b, (const double*)h->x64, h->r, h->st, h->partials, 0);
+  cudaError_t e = launch_chain(k_ad_resid, dim3(row_grid(h)), dim3(kT), 0, s, h->lv[0], (const float*)h->b,
+                               (const float2*)h->xff, h->r, h->st, h->partials, 0);
   h->launches += 1;
   for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
     const float* bk = k == 0 ? h->r : h->bk[k];
@@ -624,7 +665,7 @@ static cudaError_t enqueue_cycle(ad_handle_s* h, cudaStream_t s) {
     const dim3 g = tile_grid(L);
 #define NPMG_AD_UP(P, F)                                                                                      \
   launch_chain(k_ad_up<P, F>, g, dim3(kT), 0, s, L, bk, (const float*)h->xk[k], (const float*)h->yk[k + 1], \
-               h->yk[k], h->x64, sc, om, h->st, h->partials)
+               h->yk[k], h->xff, sc, om, h->st, h->partials)
     if (k == 0)
       e = o.post == 0 ? NPMG_AD_UP(0, true) : (o.post == 1 ? NPMG_AD_UP(1, true) : NPMG_AD_UP(2, true));
     else
@@ -781,7 +822,7 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
       return MG_ERR_INVALID;
     }
   }
-  // one pool: b, r, x64, per-level arrays, the inverse, partials, state
+  // one pool: b, r, the iterate, per-level arrays, the inverse, partials, state
   const size_t n0 = (size_t)nx * ny;
   const size_t tiles0 = (size_t)tile_grid(hd->lv[0]).x * tile_grid(hd->lv[0]).y;
   const size_t npart = std::max(tiles0, (size_t)hd->nsm * 8) + 1;
@@ -804,7 +845,7 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
   };
   hd->b = (float*)take(n0 * 4);
   hd->r = (float*)take(n0 * 4);
-  hd->x64 = (double*)take(n0 * 8);
+  hd->xff = (float2*)take(n0 * 8);
   hd->partials = (double*)take(npart * 8);
   hd->st = (State*)take(sizeof(State));
   hd->inv = (float*)take(inv.size() * 4 + 4);
@@ -847,7 +888,7 @@ mg_status ad_solve(ad_handle hd, const float* d_b, const float* d_x0, float* d_x
   NPMG_CUDA(cudaEventCreate(&e1));
   NPMG_CUDA(cudaEventRecord(e0, s));
   NPMG_CUDA(cudaMemcpyAsync(hd->b, d_b, n0 * 4, cudaMemcpyDeviceToDevice, s));
-  k_ad_init<<<grid_1d(hd, n0), kT, 0, s>>>(hd->lv[0], hd->b, d_x0, hd->x64, hd->st, rel_tol, l1_tol,
+  k_ad_init<<<row_grid(hd), kT, 0, s>>>(hd->lv[0], hd->b, d_x0, hd->xff, hd->st, rel_tol, l1_tol,
                                            hd->opt.max_cycles, hd->partials);
   hd->launches += 1;
   NPMG_CUDA(cudaGetLastError());
@@ -863,8 +904,8 @@ mg_status ad_solve(ad_handle hd, const float* d_b, const float* d_x0, float* d_x
     if (hd->st_host->done) break;
   }
   // relres of the returned iterate, and the float32 output
-  k_ad_resid<<<grid_1d(hd, n0), kT, 0, s>>>(hd->lv[0], hd->b, hd->x64, hd->r, hd->st, hd->partials, 1);
-  k_ad_out<<<grid_1d(hd, n0), kT, 0, s>>>(n0, hd->x64, d_x);
+  k_ad_resid<<<row_grid(hd), kT, 0, s>>>(hd->lv[0], hd->b, hd->xff, hd->r, hd->st, hd->partials, 1);
+  k_ad_out<<<grid_1d(hd, n0), kT, 0, s>>>(n0, hd->xff, d_x);
   hd->launches += 2;
   NPMG_CUDA(cudaGetLastError());
   NPMG_CUDA(cudaEventRecord(e1, s));
