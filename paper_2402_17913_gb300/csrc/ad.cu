@@ -16,7 +16,7 @@
 // Per cycle: k_ad_resid (r = b - A x and ||r||, the convergence decision),
 // on levels 0 .. kc-1 a tile down leg (V: pre sweeps from zero, residual,
 // 2x2 average; sawtooth: x = b / c, average of b), one single-block kernel
-// for levels kc .. L-1 (<= 1024 nodes; coarsest level by a dense inverse
+// for levels kc .. L-1 (<= 4096 nodes; coarsest level by a dense inverse
 // in the V cycle), tile up legs back to level 0 (x + s P e, post sweeps);
 // the level-0 up leg adds the correction to the float64 iterate and sums
 // its L1 norm (the paper's stopping gauge).  Every kernel returns at once
@@ -39,7 +39,7 @@ namespace ad {
 constexpr int TX = 64, TY = 16;  // tile of the level-leg kernels
 constexpr int kT = 256;          // threads per tile block
 constexpr int kCB = 1024;        // threads of the coarse block
-constexpr int kCoarseCells = 1024;
+constexpr int kCoarseCells = 4096;
 constexpr int kCoarsestMax = 256;
 constexpr int kChunk = 8;        // cycles per graph launch
 
@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b
 
 // ---------------------------------------------------------------------------
 // Single-block kernel for levels kc .. L-1 (each <= kCoarseCells nodes, all
-// of them held in shared memory: b, x and a sweep buffer per level); the
+// of them held in dynamic shared memory, at most 64 KB: b, x and a sweep
+// buffer per level); the
 // right-hand side of level kc comes from global memory and its correction
 // goes back there.
 constexpr int kCoarseSmem = 3 * (kCoarseCells * 4 / 3 + 2);
@@ -397,7 +398,7 @@ __device__ void cb_sweeps(const Lev& L, const float* b, float*& cur, float*& oth
 __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* st) {
   chain_enter();
   if (st->done) return;
-  __shared__ float sm[kCoarseSmem];
+  extern __shared__ float sm[];
   float* res[kMaxLevels];
   const bool saw = a.cycle == MG_CYCLE_SAWTOOTH;
   auto B = [&](int k) { return sm + a.off[k]; };
@@ -656,8 +657,9 @@ static cudaError_t enqueue_cycle(ad_handle_s* h, cudaStream_t s) {
   }
   ca.b_first = h->bk[h->kc];
   ca.y_first = h->yk[h->kc];
+  const size_t cb_smem = (size_t)off * sizeof(float);
   ca.inv = h->inv;
-  e = launch_chain(k_ad_coarse, dim3(1), dim3(kCB), 0, s, ca, (const State*)h->st);
+  e = launch_chain(k_ad_coarse, dim3(1), dim3(kCB), cb_smem, s, ca, (const State*)h->st);
   h->launches += 1;
   for (int k = h->kc - 1; k >= 0 && e == cudaSuccess; --k) {
     const float* bk = k == 0 ? h->r : h->bk[k];
@@ -777,7 +779,7 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
     const double scale = o.coarse_op == AD_COARSE_GALERKIN ? (double)(1 << k) : 1.0;
     hd->lv[k] = make_level((int)(nx >> k), (int)(ny >> k), h * (1 << k), dt, nu, u, v, scheme, scale);
   }
-  // the single block takes every level from the first one of <= 1024 nodes
+  // the single block takes every level from the first one of <= 4096 nodes
   // (never the finest, whose up leg updates the iterate)
   hd->kc = L - 1;
   for (int k = 1; k < L; ++k)
@@ -798,6 +800,12 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
       delete hd;
       return MG_ERR_INVALID;
     }
+  }
+  if (cudaFuncSetAttribute(k_ad_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kCoarseSmem * sizeof(float))) != cudaSuccess) {
+    set_error("ad_create: %s", cudaGetErrorString(cudaGetLastError()));
+    delete hd;
+    return MG_ERR_CUDA;
   }
   std::vector<float> inv;
   if (o.cycle == MG_CYCLE_V) {
