@@ -322,20 +322,35 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def source_hash():
+# The translation unit of the dominant kernel of each workload with a
+# committed traffic summary; its hash also covers the headers it includes.
+TRAFFIC_TU = {"ns2d_block_2048x1024": "mg_stream2d.cu", "poisson3d_256x256x256_fp32": "mg_rows3d.cu",
+              "ns3d_cube_256x128x128": "mg_rows3d.cu"}
+KERNEL_HEADERS = ["mg_kernels.cuh", "launch.h", "npmg_internal.cuh"]
+
+
+def source_hash(tu=None):
+    """Hash of the sources a kernel is compiled from: translation unit `tu`
+    with the level-kernel headers and the public header (every csrc file
+    when tu is None)."""
+    csrc = os.path.join(ROOT, "paper_2402_17913_gb300", "csrc")
+    if tu is None:
+        paths = sorted(glob.glob(os.path.join(csrc, "*")))
+    else:
+        paths = [os.path.join(csrc, f) for f in [tu] + KERNEL_HEADERS] + [os.path.join(ROOT, "include", "npmg.h")]
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2402_17913_gb300", "csrc", "*"))):
+    for p in paths:
         h.update(open(p, "rb").read())
     return h.hexdigest()[:12]
 
 
 def recorded_traffic(workload, cls):
     """DRAM bytes per launch of kernel class `cls` from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+    summary, if it was taken on the current sources of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic_%s.md" % workload)
-    if not os.path.exists(path):
+    if not os.path.exists(path) or workload not in TRAFFIC_TU:
         return None
-    src = source_hash()
+    src = source_hash(TRAFFIC_TU[workload])
     for line in open(path):
         m = re.match(r"\s*traffic_bytes_per_launch:\s*(\w+)\s+([0-9.eE+]+)\s+src=(\w+)", line)
         if m and m.group(1) == cls and m.group(3) == src:
