@@ -13,9 +13,11 @@
 // FP64 rate is a small fraction of its FP32 rate) and the cycle runs on it
 // in float32.
 //
-// Per cycle: k_ad_resid (r = b - A x and ||r||, the convergence decision),
-// on levels 0 .. kc-1 a tile down leg (V: pre sweeps from zero, residual,
-// 2x2 average; sawtooth: x = b / c, average of b), one single-block kernel
+// Per cycle: k_ad_resid (V: r = b - A x of the iterate and ||r||, from
+// which its last block takes the convergence decision), on levels 0 .. kc-1
+// a tile down leg (V: pre sweeps from zero, residual, 2x2 average;
+// sawtooth: x = b / c, average of b, on level 0 after forming r and ||r||
+// itself), one single-block kernel
 // for levels kc .. L-1 (<= 4096 nodes; coarsest level by a dense inverse
 // in the V cycle), tile up legs back to level 0 (x + s P e, post sweeps);
 // the level-0 up leg adds the correction to the float64 iterate and sums
@@ -149,6 +151,25 @@ __global__ void __launch_bounds__(kT) k_ad_init(Lev L, const float* __restrict__
   }
 }
 
+// relres from ||b - A x||^2 and, unless `final`, the stopping decision taken
+// before each cycle: converged, diverged (1000-fold growth) or out of cycles.
+__device__ void decide(State* st, double rr, bool final) {
+  const double rel = st->bnorm2 > 0.0 ? sqrt(rr / st->bnorm2) : 0.0;
+  st->relres = rel;
+  if (final) return;
+  if (st->cycles == 0) st->relres0 = rel;
+  if (rel <= st->tol) {
+    st->status = MG_OK;
+    st->done = 1;
+  } else if (!isfinite(rel) || rel > 1e3 * fmax(st->relres0, 1.0)) {
+    st->status = MG_DIVERGED;
+    st->done = 1;
+  } else if (st->cycles >= st->max_cycles) {
+    st->status = MG_NOT_CONVERGED;
+    st->done = 1;
+  }
+}
+
 // One term -w * (hi + lo) of b - A x into the float-float sum (S, E).
 __device__ __forceinline__ void ff_sub_term(float w, float2 x, float& S, float& E) {
   float p, pe, se;
@@ -179,22 +200,7 @@ __global__ void __launch_bounds__(kT) k_ad_resid(Lev L, const float* __restrict_
     acc = fmaf(rv, rv, acc);
   }
   double tot;
-  if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) {
-    const double rel = st->bnorm2 > 0.0 ? sqrt(tot / st->bnorm2) : 0.0;
-    st->relres = rel;
-    if (final) return;
-    if (st->cycles == 0) st->relres0 = rel;
-    if (rel <= st->tol) {
-      st->status = MG_OK;
-      st->done = 1;
-    } else if (!isfinite(rel) || rel > 1e3 * fmax(st->relres0, 1.0)) {
-      st->status = MG_DIVERGED;
-      st->done = 1;
-    } else if (st->cycles >= st->max_cycles) {
-      st->status = MG_NOT_CONVERGED;
-      st->done = 1;
-    }
-  }
+  if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) decide(st, tot, final != 0);
 }
 
 // V down leg of one level: PRE relaxed Jacobi sweeps from zero on the tile
@@ -261,22 +267,48 @@ __global__ void __launch_bounds__(kT) k_ad_down(Lev L, const float* __restrict__
 }
 
 // Sawtooth down leg: x = b / c on every node, the 2x2 average of b to the
-// coarse right-hand side (no sweeps); one thread per coarse node.
+// coarse right-hand side (no sweeps); one thread per coarse node.  On level
+// 0 (FUSED) b is the residual of the float-float iterate, computed here,
+// written to r and summed for the stopping decision (as k_ad_down).
+template <bool FUSED>
 __global__ void __launch_bounds__(kT) k_ad_down_saw(Lev L, const float* __restrict__ b, float* __restrict__ x,
-                                                    float* __restrict__ bc, const State* st) {
+                                                    float* __restrict__ bc, State* st,
+                                                    const float2* __restrict__ xff, float* __restrict__ r,
+                                                    double* partials) {
   chain_enter();
   if (st->done) return;
   const int cnx = L.nx / 2;
   const size_t nc = (size_t)cnx * (L.ny / 2);
+  float acc = 0.f;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (size_t)gridDim.x * blockDim.x) {
     const int cx = (int)(c % cnx), cy = (int)(c / cnx);
-    const size_t i0 = (size_t)(2 * cy) * L.nx + 2 * cx, i1 = i0 + L.nx;
-    const float b00 = b[i0], b01 = b[i0 + 1], b10 = b[i1], b11 = b[i1 + 1];
-    x[i0] = b00 * L.inv_c;
-    x[i0 + 1] = b01 * L.inv_c;
-    x[i1] = b10 * L.inv_c;
-    x[i1 + 1] = b11 * L.inv_c;
-    bc[c] = 0.25f * ((b00 + b01) + (b10 + b11));
+    float v[4];
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ix = 2 * cx + (k & 1), iy = 2 * cy + (k >> 1);
+      const size_t i = (size_t)iy * L.nx + ix;
+      float bv = b[i];
+      if (FUSED) {
+        float S = bv, E = 0.f;
+        ff_sub_term(L.c, xff[i], S, E);
+        if (ix > 0) ff_sub_term(L.xm, xff[i - 1], S, E);
+        if (ix + 1 < L.nx) ff_sub_term(L.xp, xff[i + 1], S, E);
+        if (iy > 0) ff_sub_term(L.ym, xff[i - L.nx], S, E);
+        if (iy + 1 < L.ny) ff_sub_term(L.yp, xff[i + L.nx], S, E);
+        bv = S + E;
+        r[i] = bv;
+        acc = fmaf(bv, bv, acc);
+      }
+      v[k] = bv;
+      x[i] = bv * L.inv_c;
+    }
+    sum = (v[0] + v[1]) + (v[2] + v[3]);
+    bc[c] = 0.25f * sum;
+  }
+  if (FUSED) {
+    double tot;
+    if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) decide(st, tot, false);
   }
 }
 
@@ -615,25 +647,33 @@ static cudaError_t enqueue_cycle(ad_handle_s* h, cudaStream_t s) {
   const ad_options& o = h->opt;
   const float om = (float)o.omega, sc = (float)o.coarse_scale;
   const bool saw = o.cycle == MG_CYCLE_SAWTOOTH;
-  cudaError_t e = launch_chain(k_ad_resid, dim3(row_grid(h)), dim3(kT), 0, s, h->lv[0], (const float*)h->b,
-                               (const float2*)h->xff, h->r, h->st, h->partials, 0);
-  h->launches += 1;
+  // level 0: the residual of the iterate comes from k_ad_resid for the V
+  // cycle (fusing it into the down leg, which recomputes it on the tile's
+  // halo, measured slower on GB300: 4096^2 5.55 -> 6.53 ms) and is formed
+  // inside the sawtooth's down leg, which has no halo
+  cudaError_t e = cudaSuccess;
+  if (!saw) {
+    e = launch_chain(k_ad_resid, dim3(row_grid(h)), dim3(kT), 0, s, h->lv[0], (const float*)h->b,
+                     (const float2*)h->xff, h->r, h->st, h->partials, 0);
+    h->launches += 1;
+  }
   for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
-    const float* bk = k == 0 ? h->r : h->bk[k];
+    const float* bk = k == 0 ? (saw ? h->b : h->r) : h->bk[k];
     const Lev& L = h->lv[k];
+    const float2* xf = h->xff;
+    float* rr = h->r;
+    double* pt = h->partials;
     if (saw) {
       const size_t nc = (size_t)(L.nx / 2) * (L.ny / 2);
-      e = launch_chain(k_ad_down_saw, dim3(grid_1d(h, nc)), dim3(kT), 0, s, L, bk, h->xk[k], h->bk[k + 1],
-                       (const State*)h->st);
-    } else if (o.pre == 0) {
-      e = launch_chain(k_ad_down<0>, tile_grid(L), dim3(kT), 0, s, L, bk, h->xk[k], h->bk[k + 1], om,
-                       (const State*)h->st);
-    } else if (o.pre == 1) {
-      e = launch_chain(k_ad_down<1>, tile_grid(L), dim3(kT), 0, s, L, bk, h->xk[k], h->bk[k + 1], om,
-                       (const State*)h->st);
+      e = k == 0 ? launch_chain(k_ad_down_saw<true>, dim3(grid_1d(h, nc)), dim3(kT), 0, s, L, bk, h->xk[k],
+                                h->bk[k + 1], h->st, xf, rr, pt)
+                 : launch_chain(k_ad_down_saw<false>, dim3(grid_1d(h, nc)), dim3(kT), 0, s, L, bk, h->xk[k],
+                                h->bk[k + 1], h->st, xf, rr, pt);
     } else {
-      e = launch_chain(k_ad_down<2>, tile_grid(L), dim3(kT), 0, s, L, bk, h->xk[k], h->bk[k + 1], om,
-                       (const State*)h->st);
+#define NPMG_AD_DOWN(P) \
+  launch_chain(k_ad_down<P>, tile_grid(L), dim3(kT), 0, s, L, bk, h->xk[k], h->bk[k + 1], om, (const State*)h->st)
+      e = o.pre == 0 ? NPMG_AD_DOWN(0) : (o.pre == 1 ? NPMG_AD_DOWN(1) : NPMG_AD_DOWN(2));
+#undef NPMG_AD_DOWN
     }
     h->launches += 1;
   }
