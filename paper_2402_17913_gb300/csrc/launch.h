@@ -106,9 +106,18 @@ template <typename T>
 cudaError_t launch_xr_update(const LevelDev& L, const void* p, const void* Ap, void* d, void* r, SolveState* st,
                              double* partials, cudaStream_t s);
 // x: float-float iterate (float2 per cell); w: operator weights c / h_a^2.
+// dyn: xin / xout are the two buffers and the state's `cur` picks the one
+// holding the iterate (flipped after an update).
 template <int DIM, typename T, bool MASKED, bool UPDATE>
 cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
-                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s);
+                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s,
+                         int dyn = 0);
+// Conditional values of the device-side solve loop (see mg_cg.cu).
+cudaError_t launch_loop_start(cudaGraphConditionalHandle outer, SolveState* st, cudaStream_t s);
+cudaError_t launch_loop_inner(cudaGraphConditionalHandle inner, SolveState* st, unsigned int cap, int body,
+                              cudaStream_t s);
+cudaError_t launch_loop_outer(cudaGraphConditionalHandle outer, SolveState* st, unsigned int cap, cudaStream_t s);
+cudaError_t launch_loop_set_cur(SolveState* st, int cur, cudaStream_t s);
 
 struct SolveParams {
   double tol, inner_floor;

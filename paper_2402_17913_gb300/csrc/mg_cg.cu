@@ -446,11 +446,18 @@ struct OuterArgs {
   double c2;      // c^2 (to turn ||r||^2 back into unscaled units)
 };
 
+// With `dyn` the two float-float buffers are xa, xb and the state's `cur`
+// says which one holds the iterate (a device-side loop cannot swap the
+// pointers); the last block flips it after an update.  Otherwise x is read
+// from xa and the update written to xb.
 template <int DIM, typename T, bool MASKED, bool UPDATE>
 __global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const float* __restrict__ b,
-                                               const float2* __restrict__ xin, float2* __restrict__ xout,
+                                               float2* xa, float2* xb, int dyn,
                                                const T* __restrict__ dprime, T* __restrict__ rprime,
                                                SolveState* __restrict__ st, double* __restrict__ partials) {
+  const bool swap = dyn && st->cur;
+  const float2* __restrict__ xin = swap ? xb : xa;
+  float2* __restrict__ xout = swap ? xa : xb;
   const double sig_old_d = st->sigma;
   double sig_new_d = sig_old_d;
   if (UPDATE) sig_new_d = pow2_floor(sig_old_d * sqrt(fmax(st->rnorm2, 1e-300) / (double)st->n_fluid));
@@ -552,7 +559,10 @@ __global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const f
   }
   double tot;
   if (grid_sum_last((double)acc, partials, &st->counter[kCntOuter], &tot)) {
-    if (threadIdx.x == 0) outer_decide(st, tot, oa.c2, sig_new_d, UPDATE);
+    if (threadIdx.x == 0) {
+      outer_decide(st, tot, oa.c2, sig_new_d, UPDATE);
+      if (UPDATE && dyn) st->cur ^= 1;
+    }
   }
 }
 
@@ -570,10 +580,51 @@ static OuterArgs outer_args(const double w[3], double c) {
 
 template <int DIM, typename T, bool MASKED, bool UPDATE>
 cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
-                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s) {
-  k_outer<DIM, T, MASKED, UPDATE><<<row_grid(L), 256, 0, s>>>(L, outer_args(w, c), b, (const float2*)xin,
-                                                              (float2*)xout, (const T*)dprime, (T*)rprime, st,
-                                                              partials);
+                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s, int dyn) {
+  k_outer<DIM, T, MASKED, UPDATE><<<row_grid(L), 256, 0, s>>>(L, outer_args(w, c), b, (float2*)xin, (float2*)xout,
+                                                              dyn, (const T*)dprime, (T*)rprime, st, partials);
+  return cudaGetLastError();
+}
+
+// The conditional values of the device-side solve loop (one thread each):
+// the outer loop runs while the refinement is not done, the inner loop of
+// CG chunks while the inner solve is not done; `cap` bounds the checks of
+// each loop so that it ends whatever the flags say.
+__global__ void k_loop_start(cudaGraphConditionalHandle outer, SolveState* st) {
+  st->loop_checks = 0;
+  st->loop_bodies = 0;
+  st->loop_outer = 0;
+  cudaGraphSetConditional(outer, st->outer_done ? 0u : 1u);
+}
+
+__global__ void k_loop_inner(cudaGraphConditionalHandle inner, SolveState* st, unsigned int cap, int body) {
+  const unsigned int n = ++st->loop_checks;
+  st->loop_bodies += body;
+  cudaGraphSetConditional(inner, (!st->inner_done && !st->outer_done && n <= cap) ? 1u : 0u);
+}
+
+__global__ void k_loop_outer(cudaGraphConditionalHandle outer, SolveState* st, unsigned int cap) {
+  const unsigned int n = ++st->loop_outer;
+  cudaGraphSetConditional(outer, (!st->outer_done && n < cap) ? 1u : 0u);
+}
+
+__global__ void k_loop_set_cur(SolveState* st, int cur) { st->cur = cur; }
+
+cudaError_t launch_loop_start(cudaGraphConditionalHandle outer, SolveState* st, cudaStream_t s) {
+  k_loop_start<<<1, 1, 0, s>>>(outer, st);
+  return cudaGetLastError();
+}
+cudaError_t launch_loop_inner(cudaGraphConditionalHandle inner, SolveState* st, unsigned int cap, int body,
+                              cudaStream_t s) {
+  k_loop_inner<<<1, 1, 0, s>>>(inner, st, cap, body);
+  return cudaGetLastError();
+}
+cudaError_t launch_loop_outer(cudaGraphConditionalHandle outer, SolveState* st, unsigned int cap, cudaStream_t s) {
+  k_loop_outer<<<1, 1, 0, s>>>(outer, st, cap);
+  return cudaGetLastError();
+}
+cudaError_t launch_loop_set_cur(SolveState* st, int cur, cudaStream_t s) {
+  k_loop_set_cur<<<1, 1, 0, s>>>(st, cur);
   return cudaGetLastError();
 }
 
@@ -582,10 +633,10 @@ cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const f
                                                   SolveState*, double*, cudaStream_t);                           \
   template cudaError_t launch_outer<DIM, T, M, false>(const LevelDev&, const double*, double, const float*,     \
                                                       const void*, void*, const void*, void*, SolveState*,       \
-                                                      double*, cudaStream_t);                                    \
+                                                      double*, cudaStream_t, int);                               \
   template cudaError_t launch_outer<DIM, T, M, true>(const LevelDev&, const double*, double, const float*,      \
                                                      const void*, void*, const void*, void*, SolveState*,        \
-                                                     double*, cudaStream_t);
+                                                     double*, cudaStream_t, int);
 
 NPMG_INST_VEC(2, float, false)
 NPMG_INST_VEC(2, float, true)

@@ -49,6 +49,12 @@ struct mg_handle_s {
   int nb1d;
   cudaEvent_t ev0, ev1;
   cudaGraphExec_t graph_exec;
+  // the whole refinement loop after the first residual as one graph with
+  // nested conditional while nodes (built on first use; loop_state 0 = not
+  // built, 1 = built, -1 = not available, the host loop runs instead)
+  cudaGraphExec_t loop_exec;
+  int loop_state;
+  float* bsave;            // the right-hand side the loop graph reads
   npmg::TmaLevelMaps tmaps[npmg::kMaxLevels];  // TMA tensor maps per level (levels < kc)
   bool tma_ok[npmg::kMaxLevels];
   bool s3_ok[npmg::kMaxLevels];   // 3D levels on the z-streaming kernels

@@ -253,6 +253,93 @@ static cudaError_t ensure_graph(mg_handle_s* h, cudaStream_t s) {
   return e;
 }
 
+// Add a conditional while node at the capture point of cs; returns its body.
+static cudaError_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle hd, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = hd;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The refinement loop after the first residual as one graph, so that a solve
+// needs no host round trip per CG chunk or refinement step:
+//   while (refinement not done) {            // outer conditional
+//     while (inner solve not done) { kChunk CG iterations }
+//     refinement step (k_outer, buffers picked by the state's `cur`)
+//   }
+// The loop kernels bound both loops by a count as well as by the flags.
+static cudaError_t build_loop_graph(mg_handle_s* h) {
+  const mg_options& o = h->opt;
+  if (!h->bsave) {
+    cudaError_t e = cudaMalloc((void**)&h->bsave, h->ncell[0] * sizeof(float));
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned int cap_in = (unsigned int)((o.max_outer + 2) * (o.max_inner / kChunk + 3));
+  const unsigned int cap_out = (unsigned int)(o.max_outer + 2);
+  cudaGraph_t G = nullptr;
+  cudaError_t e = cudaGraphCreate(&G, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle ho, hi;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t body_outer = nullptr, body_inner = nullptr, tmp = nullptr;
+  const int64_t before = h->launches;
+  h->capturing = 1;
+  e = cudaGraphConditionalHandleCreate(&ho, G, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, G, 0, 0);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  // top level: reset the loop counters and set the outer condition
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = launch_loop_start(ho, h->st, cs);
+    if (e2 == cudaSuccess) e2 = capture_while(cs, ho, &body_outer);
+    e = cudaStreamEndCapture(cs, &tmp);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  // outer body: inner condition, inner loop, refinement step, outer condition
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = launch_loop_inner(hi, h->st, cap_in, 0, cs);
+    if (e2 == cudaSuccess) e2 = capture_while(cs, hi, &body_inner);
+    if (e2 == cudaSuccess)
+      e2 = dispatch(h, [&](auto dimc, auto*, auto mc) -> cudaError_t {
+        constexpr int DIM = decltype(dimc)::value;
+        constexpr bool M = decltype(mc)::value;
+        return launch_outer<DIM, float, M, true>(h->lv[0], h->w0, h->c, h->bsave, h->xff[0], h->xff[1], h->d, h->r,
+                                                 h->st, h->partials, cs, 1);
+      });
+    if (e2 == cudaSuccess) e2 = launch_loop_outer(ho, h->st, cap_out, cs);
+    e = cudaStreamEndCapture(cs, &tmp);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  // inner body: kChunk CG iterations, then the inner condition
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = enqueue_chunk(h, cs);
+    if (e2 == cudaSuccess) e2 = launch_loop_inner(hi, h->st, cap_in, 1, cs);
+    e = cudaStreamEndCapture(cs, &tmp);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  h->capturing = 0;
+  h->launches = before;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->loop_exec, G, 0);
+  cudaGraphDestroy(G);
+  if (cs) cudaStreamDestroy(cs);
+  return e;
+}
+
 mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaStream_t s, mg_stats* out) {
   const mg_options& o = h->opt;
   SolveParams prm;
@@ -282,6 +369,20 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
   }
   const bool graph = h->use_graph && !h->prof;
   if (graph) NPMG_CUDA(ensure_graph(h, s));
+  if (graph && h->loop_state == 0) {
+    // on failure (for instance a driver without conditional nodes) the host
+    // loop below runs the same kernels
+    h->loop_state = getenv("NPMG_NO_DEVICE_LOOP") == nullptr && build_loop_graph(h) == cudaSuccess ? 1 : -1;
+    cudaGetLastError();
+  }
+  if (graph && h->loop_state == 1 && !h->st_host->outer_done) {
+    NPMG_CUDA(cudaMemcpyAsync(h->bsave, b, h->ncell[0] * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    NPMG_CUDA(launch_loop_set_cur(h->st, h->cur64, s));
+    NPMG_CUDA(cudaGraphLaunch(h->loop_exec, s));
+    NPMG_CUDA(read_state(h, s));
+    h->cur64 = h->st_host->cur;
+    h->launches += 2 + 3 * (int64_t)h->st_host->loop_outer + (h->chunk_kernels + 1) * (int64_t)h->st_host->loop_bodies;
+  }
   int guard = 0;
   while (!h->st_host->outer_done && guard < 4 * (o.max_outer + 1)) {
     ++guard;
@@ -807,6 +908,8 @@ mg_status mg_destroy(mg_handle h) {
     free(h->pev);
   }
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+  if (h->bsave) cudaFree(h->bsave);
   if (h->pool) cudaFree(h->pool);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);

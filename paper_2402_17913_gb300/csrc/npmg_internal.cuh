@@ -47,6 +47,10 @@ struct SolveState {
   double r0norm2, rz, rz_old, alpha, beta, rnorm2, pAp;
   // reduction counters (one per reducing kernel family)
   unsigned int counter[8];
+  // device-side solve loop: the float-float buffer holding the iterate, and
+  // the checks and bodies run by the loop's conditional nodes
+  int cur;
+  unsigned int loop_checks, loop_bodies, loop_outer;
 };
 
 enum Counter { kCntInit = 0, kCntOuter = 1, kCntRZ = 2, kCntPAP = 3, kCntRR = 4, kCntMisc = 5 };
