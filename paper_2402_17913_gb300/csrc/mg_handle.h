@@ -55,6 +55,7 @@ struct mg_handle_s {
   cudaGraphExec_t loop_exec;
   int loop_state;
   float* bsave;            // the right-hand side the loop graph reads
+  int64_t loop_kernels;    // kernels in one inner body of the loop graph
   npmg::TmaLevelMaps tmaps[npmg::kMaxLevels];  // TMA tensor maps per level (levels < kc)
   bool tma_ok[npmg::kMaxLevels];
   bool s3_ok[npmg::kMaxLevels];   // 3D levels on the z-streaming kernels

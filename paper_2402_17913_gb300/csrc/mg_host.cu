@@ -194,17 +194,28 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
   return launch_xr_update<float>(h->lv[0], h->p[1 - parity], h->Ap, h->d, h->r, h->st, h->partials, s);
 }
 
-cudaError_t enqueue_chunk(mg_handle_s* h, cudaStream_t s) {
+static cudaError_t enqueue_iterations(mg_handle_s* h, int count, cudaStream_t s) {
   return dispatch(h, [&](auto dimc, auto* tp, auto mc) -> cudaError_t {
     constexpr int DIM = decltype(dimc)::value;
     using T = std::remove_pointer_t<decltype(tp)>;
     constexpr bool M = decltype(mc)::value;
-    for (int j = 0; j < kChunk; ++j) {
+    for (int j = 0; j < count; ++j) {
       cudaError_t e = enqueue_iteration<DIM, T, M>(h, j & 1, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   });
+}
+
+cudaError_t enqueue_chunk(mg_handle_s* h, cudaStream_t s) { return enqueue_iterations(h, kChunk, s); }
+
+// CG iterations per body of the device-side loop (even: the p double
+// buffer alternates within a body); 4 measured best on GB300 (2 and 8
+// within 1%).
+static int loop_chunk() {
+  const char* e = getenv("NPMG_LOOP_CHUNK");
+  const int v = e ? atoi(e) : 4;
+  return v >= 2 && v <= 16 && v % 2 == 0 ? v : 4;
 }
 
 static cudaError_t enqueue_outer(mg_handle_s* h, const float* b, bool update, cudaStream_t s) {
@@ -275,7 +286,7 @@ static cudaError_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle hd,
 // The refinement loop after the first residual as one graph, so that a solve
 // needs no host round trip per CG chunk or refinement step:
 //   while (refinement not done) {            // outer conditional
-//     while (inner solve not done) { kChunk CG iterations }
+//     while (inner solve not done) { loop_chunk() CG iterations }
 //     refinement step (k_outer, buffers picked by the state's `cur`)
 //   }
 // The loop kernels bound both loops by a count as well as by the flags.
@@ -285,7 +296,8 @@ static cudaError_t build_loop_graph(mg_handle_s* h) {
     cudaError_t e = cudaMalloc((void**)&h->bsave, h->ncell[0] * sizeof(float));
     if (e != cudaSuccess) return e;
   }
-  const unsigned int cap_in = (unsigned int)((o.max_outer + 2) * (o.max_inner / kChunk + 3));
+  const int chunk = loop_chunk();
+  const unsigned int cap_in = (unsigned int)((o.max_outer + 2) * (o.max_inner / chunk + 3));
   const unsigned int cap_out = (unsigned int)(o.max_outer + 2);
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
@@ -327,7 +339,9 @@ static cudaError_t build_loop_graph(mg_handle_s* h) {
   if (e == cudaSuccess)
     e = cudaStreamBeginCaptureToGraph(cs, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e2 = enqueue_chunk(h, cs);
+    const int64_t k0 = h->launches;
+    cudaError_t e2 = enqueue_iterations(h, chunk, cs);
+    h->loop_kernels = h->launches - k0;
     if (e2 == cudaSuccess) e2 = launch_loop_inner(hi, h->st, cap_in, 1, cs);
     e = cudaStreamEndCapture(cs, &tmp);
     if (e2 != cudaSuccess) e = e2;
@@ -381,7 +395,7 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     NPMG_CUDA(cudaGraphLaunch(h->loop_exec, s));
     NPMG_CUDA(read_state(h, s));
     h->cur64 = h->st_host->cur;
-    h->launches += 2 + 3 * (int64_t)h->st_host->loop_outer + (h->chunk_kernels + 1) * (int64_t)h->st_host->loop_bodies;
+    h->launches += 2 + 3 * (int64_t)h->st_host->loop_outer + (h->loop_kernels + 1) * (int64_t)h->st_host->loop_bodies;
   }
   int guard = 0;
   while (!h->st_host->outer_done && guard < 4 * (o.max_outer + 1)) {

@@ -352,3 +352,35 @@ def test_misaligned_pointer_is_rejected_on_the_host(L):
         assert "aligned" in L.last_error()
     finally:
         L.mg_destroy(hdl)
+
+
+@pytest.mark.parametrize("shape,bc,frac", [CASES[1], CASES[4]])
+def test_device_loop_matches_host_loop(L, shape, bc, frac, monkeypatch):
+    """The refinement loop run on the device (one graph with conditional
+    while nodes) and on the host (a graph launch and a state read per CG
+    chunk) launch the same kernels in the same order: the same iterations,
+    the same float32 solution bit for bit, and the float-float iterate read
+    back from the buffer the device loop left current."""
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 4, solid=solid).astype(np.float32)
+    out = []
+    for host in (False, True):
+        if host:
+            monkeypatch.setenv("NPMG_NO_DEVICE_LOOP", "1")
+        hdl = create(L, shape, bc, solid, h)
+        try:
+            x = torch.zeros(shape, dtype=torch.float32, device="cuda")
+            runs = []
+            for _ in range(2):  # a second solve on the same handle reuses the graphs
+                x.zero_()
+                status, st = L.mg_solve(hdl, dev(b), x, 1e-6)
+                assert status == L.MG_OK and st["relres"] <= 1e-6
+                x64 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+                L.mg_get_solution_f64(hdl, x64)
+                runs.append((st["iters"], st["outer"], x.clone(), x64))
+            out.append(runs)
+        finally:
+            L.mg_destroy(hdl)
+    for (it_d, ou_d, x_d, x64_d), (it_h, ou_h, x_h, x64_h) in zip(*out):
+        assert (it_d, ou_d) == (it_h, ou_h)
+        assert torch.equal(x_d, x_h) and torch.equal(x64_d, x64_h)
