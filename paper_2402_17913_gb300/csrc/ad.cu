@@ -539,7 +539,6 @@ struct ad_handle_s {
   float2* xff;     // the iterate (hi, lo)
   float* bk[kMaxLevels];
   float* xk[kMaxLevels];
-  float* tk[kMaxLevels];
   float* yk[kMaxLevels];
   float* inv;
   double* partials;
@@ -877,7 +876,9 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   size_t bytes = al(n0 * 4) * 2 + al(n0 * 8) + al(npart * 8) + al(sizeof(State)) + al(inv.size() * 4 + 4);
   bytes += al(n0 * 4);  // x on level 0 (the V down leg's smoothed iterate)
-  for (int k = 1; k < L; ++k) bytes += 4 * al((size_t)hd->lv[k].nx * hd->lv[k].ny * 4);
+  // levels 1 .. kc: right-hand side and correction; below kc also the
+  // smoothed iterate; the single block keeps levels kc .. L-1 on chip
+  for (int k = 1; k <= hd->kc; ++k) bytes += (k < hd->kc ? 3 : 2) * al((size_t)hd->lv[k].nx * hd->lv[k].ny * 4);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMalloc((void**)&hd->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -899,13 +900,13 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
   hd->inv = (float*)take(inv.size() * 4 + 4);
   hd->xk[0] = (float*)take(n0 * 4);
   hd->bk[0] = hd->r;
-  hd->tk[0] = hd->yk[0] = nullptr;
-  for (int k = 1; k < L; ++k) {
+  hd->yk[0] = nullptr;
+  for (int k = 1; k < L; ++k) hd->bk[k] = hd->xk[k] = hd->yk[k] = nullptr;
+  for (int k = 1; k <= hd->kc; ++k) {
     const size_t nk = (size_t)hd->lv[k].nx * hd->lv[k].ny * 4;
     hd->bk[k] = (float*)take(nk);
-    hd->xk[k] = (float*)take(nk);
-    hd->tk[k] = (float*)take(nk);
     hd->yk[k] = (float*)take(nk);
+    if (k < hd->kc) hd->xk[k] = (float*)take(nk);
   }
   mg_status st = MG_OK;
   if (cudaMemsetAsync(hd->pool, 0, bytes, s) != cudaSuccess ||
