@@ -20,7 +20,7 @@
 // itself), one single-block kernel
 // for levels kc .. L-1 (<= 4096 nodes; coarsest level by a dense inverse
 // in the V cycle), tile up legs back to level 0 (x + s P e, post sweeps);
-// the level-0 up leg adds the correction to the float64 iterate and sums
+// the level-0 up leg adds the correction to the float-float iterate and sums
 // its L1 norm (the paper's stopping gauge).  Every kernel returns at once
 // after the state's done flag is set, so a CUDA graph of kChunk cycles is
 // replayed until the host sees the flag.
@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(kT) k_ad_down(Lev L, const float* __restrict__
 // Sawtooth down leg: x = b / c on every node, the 2x2 average of b to the
 // coarse right-hand side (no sweeps); one thread per coarse node.  On level
 // 0 (FUSED) b is the residual of the float-float iterate, computed here,
-// written to r and summed for the stopping decision (as k_ad_down).
+// written to r and summed for the stopping decision, which the last block
+// takes (the V cycle gets it from k_ad_resid).
 template <bool FUSED>
 __global__ void __launch_bounds__(kT) k_ad_down_saw(Lev L, const float* __restrict__ b, float* __restrict__ x,
                                                     float* __restrict__ bc, State* st,
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kT) k_ad_down_saw(Lev L, const float* __restri
 
 // Up leg of one level: x + s P e (copy of the coarse value to the 2x2
 // children), then POST relaxed Jacobi sweeps on A x = b, over the tile
-// grown by POST.  Written to y; on level 0 (FINEST) added to the float64
+// grown by POST.  Written to y; on level 0 (FINEST) added to the float-float
 // iterate instead, with the L1 norm of the correction summed and the
 // cycle's bookkeeping done by the last block.
 template <int POST, bool FINEST>

@@ -1,7 +1,7 @@
 """GPU parity of the implicit advection-diffusion multigrid (one
 backward-Euler step, Sec. 2.2 operator, Sec. 3.2 solver) against the FP64
 oracle, through the C ABI: one cycle elementwise (the cycle runs in
-float32 on a float64 residual, so the bound is a few float32 ulps of the
+float32 on a float-float residual, so the bound is a few float32 ulps of the
 correction times the cycle's depth), full solves against the dense answer,
 and the paper's L1 gauge."""
 import numpy as np
@@ -53,7 +53,7 @@ CASES = [
 @pytest.mark.parametrize("shape,cycle,coarse,scheme", CASES)
 def test_one_cycle_matches_oracle(L, shape, cycle, coarse, scheme):
     """x1 = x0 + M (b - A x0) for one cycle from a random x0 against the
-    oracle's cycle on the same float64 residual."""
+    oracle's cycle on the residual of the same x0 (float64 there)."""
     post, omega, s = (1, 1.0, 0.5) if cycle == "sawtooth" else (2, 2 / 3, 1.0)
     hd, mg = make(L, shape, cycle, coarse, scheme, post=post, omega=omega, s=s, max_cycles=1)
     try:
