@@ -203,6 +203,50 @@ __global__ void __launch_bounds__(kT) k_ad_resid(Lev L, const float* __restrict_
   if (grid_sum(acc, partials, &st->counter[0], gridDim.x, blockIdx.x, &tot)) decide(st, tot, final != 0);
 }
 
+// One relaxed Jacobi sweep over window J, [J, RX - J) x [J, RY - J), of a
+// shared-memory region RX x RY whose node (0, 0) is node (ox, oy) of the
+// level.  The window shrinks by one per sweep, so nothing outside it is
+// read again; nodes outside the level are skipped and keep the 0 both
+// buffers were loaded with (zero padding).  `interior`: the region lies
+// inside the level (block-uniform), no per-node test.
+template <int RX, int RY, int J>
+__device__ __forceinline__ void region_sweep(const Lev& L, const float* cur, float* nxt, const float* sb, int ox,
+                                             int oy, bool interior, float omega) {
+  constexpr int WX = RX - 2 * J, WN = WX * (RY - 2 * J);
+  for (int k = threadIdx.x; k < WN; k += kT) {
+    const int lx = J + k % WX, ly = J + k / WX;
+    if (!interior) {
+      const int gx = ox + lx, gy = oy + ly;
+      if (gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) continue;
+    }
+    const int i = ly * RX + lx;
+    const float a = L.c * cur[i] + L.xm * cur[i - 1] + L.xp * cur[i + 1] + L.ym * cur[i - RX] + L.yp * cur[i + RX];
+    nxt[i] = cur[i] + omega * (sb[i] - a) * L.inv_c;
+  }
+}
+
+// Sweeps 1 .. S (S <= 2) over the shrinking windows; returns the buffer
+// that holds the last one.
+template <int RX, int RY, int S>
+__device__ __forceinline__ float* region_sweeps(const Lev& L, float* cur, float* nxt, const float* sb, int ox,
+                                                int oy, float omega) {
+  static_assert(S >= 0 && S <= 2, "at most two sweeps");
+  const bool interior = ox >= 0 && oy >= 0 && ox + RX <= L.nx && oy + RY <= L.ny;
+  if constexpr (S >= 1) {
+    region_sweep<RX, RY, 1>(L, cur, nxt, sb, ox, oy, interior, omega);
+    __syncthreads();
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if constexpr (S >= 2) {
+    region_sweep<RX, RY, 2>(L, cur, nxt, sb, ox, oy, interior, omega);
+    __syncthreads();
+    cur = nxt;
+  }
+  return cur;
+}
+
 // V down leg of one level: PRE relaxed Jacobi sweeps from zero on the tile
 // grown by PRE + 1 (temporal blocking), x written on the tile, the residual
 // of its 2x2 blocks averaged into the coarse right-hand side.
@@ -219,28 +263,10 @@ __global__ void __launch_bounds__(kT) k_ad_down(Lev L, const float* __restrict__
     const bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
     sb[i] = in ? b[(size_t)gy * L.nx + gx] : 0.f;
     sa[i] = 0.f;
+    sc[i] = 0.f;
   }
   __syncthreads();
-  float* cur = sa;
-  float* nxt = sc;
-#pragma unroll
-  for (int j = 1; j <= PRE; ++j) {
-    // the window shrinks by one per sweep; outside it nothing is read again
-    for (int i = threadIdx.x; i < RN; i += kT) {
-      const int lx = i % RX, ly = i / RX;
-      const int gx = ox + lx, gy = oy + ly;
-      float v = 0.f;
-      if (lx >= j && lx < RX - j && ly >= j && ly < RY - j && gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-        const float a = L.c * cur[i] + L.xm * cur[i - 1] + L.xp * cur[i + 1] + L.ym * cur[i - RX] + L.yp * cur[i + RX];
-        v = cur[i] + omega * (sb[i] - a) * L.inv_c;
-      }
-      nxt[i] = v;
-    }
-    __syncthreads();
-    float* t = cur;
-    cur = nxt;
-    nxt = t;
-  }
+  const float* cur = region_sweeps<RX, RY, PRE>(L, sa, sc, sb, ox, oy, omega);
   // one coarse node per thread (the tile holds TX/2 x TY/2 = kT of them)
   {
     const int cx = threadIdx.x % (TX / 2), cy = threadIdx.x / (TX / 2);
@@ -339,27 +365,10 @@ __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b
     }
     sb[i] = bv;
     sa[i] = xv;
+    sc[i] = 0.f;
   }
   __syncthreads();
-  float* cur = sa;
-  float* nxt = sc;
-#pragma unroll
-  for (int j = 1; j <= POST; ++j) {
-    for (int i = threadIdx.x; i < RN; i += kT) {
-      const int lx = i % RX, ly = i / RX;
-      const int gx = ox + lx, gy = oy + ly;
-      float v = 0.f;
-      if (lx >= j && lx < RX - j && ly >= j && ly < RY - j && gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-        const float a = L.c * cur[i] + L.xm * cur[i - 1] + L.xp * cur[i + 1] + L.ym * cur[i - RX] + L.yp * cur[i + RX];
-        v = cur[i] + omega * (sb[i] - a) * L.inv_c;
-      }
-      nxt[i] = v;
-    }
-    __syncthreads();
-    float* t = cur;
-    cur = nxt;
-    nxt = t;
-  }
+  const float* cur = region_sweeps<RX, RY, POST>(L, sa, sc, sb, ox, oy, omega);
   float acc = 0.f;
   for (int i = threadIdx.x; i < TX * TY; i += kT) {
     const int tx = i % TX, ty = i / TX;
