@@ -1,0 +1,53 @@
+"""Host-side checks of bench.py that need no GPU: the reference arm prints
+one well-formed JSON line per configuration (the FP64 oracle on a bounded
+sample, in the unit of the GPU arm), and the traffic records are keyed on
+the sources of their own kernel."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _reference_line(*args):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", *args],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+@pytest.mark.parametrize("args,unit,higher", [
+    (["--config", "advdiff"], "unknowns/s", True),
+    (["--config", "advdiff", "--cycle", "sawtooth"], "unknowns/s", True),
+    (["--config", "timing3d", "--size", "128", "--cycle", "sawtooth"], "s", False),
+    (["--config", "poisson2d"], "unknowns/s", True),
+])
+def test_reference_arm_line(args, unit, higher):
+    d = _reference_line(*args)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == unit
+    assert d["higher_is_better"] is higher
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["unit"] == unit
+    assert d["e2e"] == {"value": d["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] and d["dtype"] == "f64"
+    if "sawtooth" in args and "advdiff" in args:
+        assert "L1" in d["metric"]
+
+
+def test_traffic_records_follow_their_kernel_sources():
+    sys.path.insert(0, ROOT)
+    import bench
+    for workload, tu in bench.TRAFFIC_TU.items():
+        assert os.path.exists(os.path.join(ROOT, "paper_2402_17913_gb300", "csrc", tu))
+        h = bench.source_hash(tu)
+        assert len(h) == 12 and h != bench.source_hash()
+        path = os.path.join(ROOT, "profiles", "traffic_%s.md" % workload)
+        text = open(path).read()
+        # the committed summary carries the hash of the sources it was taken on
+        assert "src=" in text
+    assert bench.recorded_traffic("no_such_workload", "up_fine") is None
