@@ -58,15 +58,6 @@ struct State {
   unsigned int counter[2];
 };
 
-__device__ __forceinline__ float apply_at(const Lev& L, const float* x, int i, int ix, int iy) {
-  float a = L.c * x[i];
-  if (ix > 0) a = fmaf(L.xm, x[i - 1], a);
-  if (ix + 1 < L.nx) a = fmaf(L.xp, x[i + 1], a);
-  if (iy > 0) a = fmaf(L.ym, x[i - L.nx], a);
-  if (iy + 1 < L.ny) a = fmaf(L.yp, x[i + L.nx], a);
-  return a;
-}
-
 // Sum of v over the block, in a fixed shuffle-tree order; the result is
 // valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
@@ -406,29 +397,49 @@ __global__ void __launch_bounds__(kT) k_ad_up(Lev L, const float* __restrict__ b
 
 // ---------------------------------------------------------------------------
 // Single-block kernel for levels kc .. L-1 (each <= kCoarseCells nodes, all
-// of them held in dynamic shared memory, at most 64 KB: b, x and a sweep
-// buffer per level); the
+// of them held in dynamic shared memory, at most 96 KB: b, and x and a
+// sweep buffer with a zero ring per level); the
 // right-hand side of level kc comes from global memory and its correction
 // goes back there.
-constexpr int kCoarseSmem = 3 * (kCoarseCells * 4 / 3 + 2);
+constexpr int kCoarseSmemMax = 24576;  // floats (96 KB) of the single block
 
 struct AdCoarseArgs {
   int first, last;  // level range kc .. L-1
   int cycle, pre, post;
   float omega, s;
   Lev lv[kMaxLevels];
-  int off[kMaxLevels];  // shared-memory offset of level k's b (x, t follow)
+  int off[kMaxLevels];  // shared-memory offset of level k: b (nx ny), then
+                        // x and t, each (nx + 2)(ny + 2) with a zero ring
+  int lnx[kMaxLevels];  // log2(nx) when nx is a power of two, else -1
+  int words;            // floats of shared memory in use
   const float* b_first;
   float* y_first;
   const float* inv;  // dense inverse of the coarsest level (V cycle)
 };
 
-__device__ void cb_sweeps(const Lev& L, const float* b, float*& cur, float*& oth, int sweeps, float omega) {
-  const int n = L.nx * L.ny;
+__device__ __forceinline__ void node_xy(int i, int nx, int lnx, int& ix, int& iy) {
+  if (lnx >= 0) {
+    ix = i & (nx - 1);
+    iy = i >> lnx;
+  } else {
+    ix = i % nx;
+    iy = i / nx;
+  }
+}
+
+// A x at padded index p (row width W): the zero ring is the zero padding.
+__device__ __forceinline__ float apply_pad(const Lev& L, const float* x, int p, int W) {
+  return L.c * x[p] + L.xm * x[p - 1] + L.xp * x[p + 1] + L.ym * x[p - W] + L.yp * x[p + W];
+}
+
+__device__ void cb_sweeps(const Lev& L, int lnx, const float* b, float*& cur, float*& oth, int sweeps, float omega) {
+  const int n = L.nx * L.ny, W = L.nx + 2;
   for (int j = 0; j < sweeps; ++j) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int ix = i % L.nx, iy = i / L.nx;
-      oth[i] = cur[i] + omega * (b[i] - apply_at(L, cur, i, ix, iy)) * L.inv_c;
+      int ix, iy;
+      node_xy(i, L.nx, lnx, ix, iy);
+      const int p = (iy + 1) * W + ix + 1;
+      oth[p] = cur[p] + omega * (b[i] - apply_pad(L, cur, p, W)) * L.inv_c;
     }
     __syncthreads();
     float* t = cur;
@@ -445,7 +456,10 @@ __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* 
   const bool saw = a.cycle == MG_CYCLE_SAWTOOTH;
   auto B = [&](int k) { return sm + a.off[k]; };
   auto X = [&](int k) { return sm + a.off[k] + a.lv[k].nx * a.lv[k].ny; };
-  auto T = [&](int k) { return sm + a.off[k] + 2 * a.lv[k].nx * a.lv[k].ny; };
+  auto T = [&](int k) { return sm + a.off[k] + a.lv[k].nx * a.lv[k].ny + (a.lv[k].nx + 2) * (a.lv[k].ny + 2); };
+  // zero rings, and every iterate starts from zero
+  for (int i = threadIdx.x; i < a.words; i += blockDim.x) sm[i] = 0.f;
+  __syncthreads();
   {
     const int n = a.lv[a.first].nx * a.lv[a.first].ny;
     for (int i = threadIdx.x; i < n; i += blockDim.x) B(a.first)[i] = a.b_first[i];
@@ -456,23 +470,20 @@ __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* 
   for (int k = a.first; k < a.last; ++k) {
     const Lev& L = a.lv[k];
     const Lev& C = a.lv[k + 1];
+    const int W = L.nx + 2;
     float* cur = X(k);
     float* oth = T(k);
     const float* b = B(k);
-    const int n = L.nx * L.ny;
-    if (!saw) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) cur[i] = 0.f;
-      __syncthreads();
-      cb_sweeps(L, b, cur, oth, a.pre, a.omega);
-    }
+    if (!saw) cb_sweeps(L, a.lnx[k], b, cur, oth, a.pre, a.omega);
     float* bc = B(k + 1);
     for (int c = threadIdx.x; c < C.nx * C.ny; c += blockDim.x) {
-      const int cx = c % C.nx, cy = c / C.nx;
+      int cx, cy;
+      node_xy(c, C.nx, a.lnx[k + 1], cx, cy);
       float sum = 0.f;
       for (int ay = 0; ay < 2; ++ay)
         for (int ax = 0; ax < 2; ++ax) {
           const int ix = 2 * cx + ax, iy = 2 * cy + ay, i = iy * L.nx + ix;
-          sum += saw ? b[i] : b[i] - apply_at(L, cur, i, ix, iy);
+          sum += saw ? b[i] : b[i] - apply_pad(L, cur, (iy + 1) * W + ix + 1, W);
         }
       bc[c] = 0.25f * sum;
     }
@@ -483,21 +494,24 @@ __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* 
   {
     const int k = a.last;
     const Lev& L = a.lv[k];
-    const int n = L.nx * L.ny;
+    const int n = L.nx * L.ny, W = L.nx + 2;
     float* cur = X(k);
     float* oth = T(k);
     const float* b = B(k);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int ix, iy;
+      node_xy(i, L.nx, a.lnx[k], ix, iy);
+      float v;
       if (saw) {
-        cur[i] = b[i] * L.inv_c;
+        v = b[i] * L.inv_c;
       } else {
-        float v = 0.f;
+        v = 0.f;
         for (int j = 0; j < n; ++j) v = fmaf(a.inv[(size_t)i * n + j], b[j], v);
-        cur[i] = v;
       }
+      cur[(iy + 1) * W + ix + 1] = v;
     }
     __syncthreads();
-    if (saw) cb_sweeps(L, b, cur, oth, a.post, a.omega);
+    if (saw) cb_sweeps(L, a.lnx[k], b, cur, oth, a.post, a.omega);
     res[k] = cur;
   }
   // up: x + s P e (x = the smoothed iterate, or r / c for the sawtooth), post
@@ -505,23 +519,31 @@ __global__ void __launch_bounds__(kCB) k_ad_coarse(AdCoarseArgs a, const State* 
   for (int k = a.last - 1; k >= a.first; --k) {
     const Lev& L = a.lv[k];
     const Lev& C = a.lv[k + 1];
+    const int W = L.nx + 2, WC = C.nx + 2;
     float* cur = res[k];
     float* oth = cur == X(k) ? T(k) : X(k);
     const float* b = B(k);
     const int n = L.nx * L.ny;
     const float* e = res[k + 1];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int ix = i % L.nx, iy = i / L.nx;
-      const float base = saw ? b[i] * L.inv_c : cur[i];
-      cur[i] = fmaf(a.s, e[(iy >> 1) * C.nx + (ix >> 1)], base);
+      int ix, iy;
+      node_xy(i, L.nx, a.lnx[k], ix, iy);
+      const int p = (iy + 1) * W + ix + 1;
+      const float base = saw ? b[i] * L.inv_c : cur[p];
+      cur[p] = fmaf(a.s, e[((iy >> 1) + 1) * WC + (ix >> 1) + 1], base);
     }
     __syncthreads();
-    cb_sweeps(L, b, cur, oth, a.post, a.omega);
+    cb_sweeps(L, a.lnx[k], b, cur, oth, a.post, a.omega);
     res[k] = cur;
   }
   {
     const Lev& L = a.lv[a.first];
-    for (int i = threadIdx.x; i < L.nx * L.ny; i += blockDim.x) a.y_first[i] = res[a.first][i];
+    const int n = L.nx * L.ny, W = L.nx + 2;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int ix, iy;
+      node_xy(i, L.nx, a.lnx[a.first], ix, iy);
+      a.y_first[i] = res[a.first][(iy + 1) * W + ix + 1];
+    }
   }
 }
 
@@ -699,11 +721,14 @@ static cudaError_t enqueue_cycle(ad_handle_s* h, cudaStream_t s) {
   int off = 0;
   for (int k = 0; k < h->L; ++k) {
     ca.lv[k] = h->lv[k];
+    const int nx = h->lv[k].nx, ny = h->lv[k].ny;
+    ca.lnx[k] = (nx & (nx - 1)) ? -1 : __builtin_ctz((unsigned)nx);
     if (k >= h->kc) {
       ca.off[k] = off;
-      off += 3 * h->lv[k].nx * h->lv[k].ny;
+      off += nx * ny + 2 * (nx + 2) * (ny + 2);
     }
   }
+  ca.words = off;
   ca.b_first = h->bk[h->kc];
   ca.y_first = h->yk[h->kc];
   const size_t cb_smem = (size_t)off * sizeof(float);
@@ -843,15 +868,18 @@ mg_status ad_create(ad_handle* out, const int64_t cells[2], double h, double dt,
   }
   {
     int64_t words = 0;
-    for (int k = hd->kc; k < L; ++k) words += 3 * (int64_t)hd->lv[k].nx * hd->lv[k].ny;
-    if (words > kCoarseSmem) {
-      set_error("ad_create: coarse levels need %lld shared words (> %d)", (long long)words, kCoarseSmem);
+    for (int k = hd->kc; k < L; ++k) {
+      const int64_t nx = hd->lv[k].nx, ny = hd->lv[k].ny;
+      words += nx * ny + 2 * (nx + 2) * (ny + 2);
+    }
+    if (words > kCoarseSmemMax) {
+      set_error("ad_create: coarse levels need %lld shared words (> %d)", (long long)words, kCoarseSmemMax);
       delete hd;
       return MG_ERR_INVALID;
     }
   }
   if (cudaFuncSetAttribute(k_ad_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kCoarseSmem * sizeof(float))) != cudaSuccess) {
+                           (int)(kCoarseSmemMax * sizeof(float))) != cudaSuccess) {
     set_error("ad_create: %s", cudaGetErrorString(cudaGetLastError()));
     delete hd;
     return MG_ERR_CUDA;
