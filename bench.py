@@ -329,10 +329,18 @@ TRAFFIC_TU = {"ns2d_block_2048x1024": "mg_stream2d.cu", "poisson3d_256x256x256_f
 KERNEL_HEADERS = ["mg_kernels.cuh", "launch.h", "npmg_internal.cuh"]
 
 
+def _code_only(text):
+    """C/C++ source with comments removed and whitespace collapsed, so that
+    a comment edit does not count as a change of the kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash(tu=None):
-    """Hash of the sources a kernel is compiled from: translation unit `tu`
+    """Hash of the code a kernel is compiled from: translation unit `tu`
     with the level-kernel headers and the public header (every csrc file
-    when tu is None)."""
+    when tu is None), comments ignored."""
     csrc = os.path.join(ROOT, "paper_2402_17913_gb300", "csrc")
     if tu is None:
         paths = sorted(glob.glob(os.path.join(csrc, "*")))
@@ -340,7 +348,7 @@ def source_hash(tu=None):
         paths = [os.path.join(csrc, f) for f in [tu] + KERNEL_HEADERS] + [os.path.join(ROOT, "include", "npmg.h")]
     h = hashlib.sha256()
     for p in paths:
-        h.update(open(p, "rb").read())
+        h.update(_code_only(open(p, encoding="utf-8", errors="replace").read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -158,8 +158,16 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3],
  *         as float64 with mg_get_solution_f64).
  *   rel_tol  > 0.
  *   out   host stats or NULL.
- * Synchronises the stream: the host launches CUDA graphs of 4 CG iterations
- * and reads the device control block between them.  Returns MG_OK,
+ * Synchronises the stream.  After the first residual the refinement loop
+ * runs on the device as one CUDA graph with conditional while nodes (4 CG
+ * iterations per inner body, both loops bounded by counts as well as by the
+ * convergence flags); where that graph cannot be built, or with the
+ * environment variable NPMG_NO_DEVICE_LOOP set when the handle first
+ * solves, the host launches graphs of 4 CG iterations and reads the device
+ * control block between them (the same kernels in the same order; kernels
+ * inside graphs with conditional nodes are not visible to ncu).  The
+ * device loop allocates one float32 copy of the right-hand side when its
+ * graph is first built.  Returns MG_OK,
  * MG_NOT_CONVERGED, MG_DIVERGED, or an error (MG_ERR_INVALID for NULL or
  * misaligned pointers or rel_tol <= 0).
  */
