@@ -246,12 +246,16 @@ class Batched:
     """1024 independent square instances, sides uniform in {64, 128, 256,
     512} (seed 1234), random rectangle solids covering U(0, 0.1) of the
     cells (flood-filled), 8-blob right-hand sides (seed = instance index),
-    zero Dirichlet faces."""
+    zero Dirichlet faces.  Under several ranks each rank solves its own
+    1024 instances (sides seed 1234 + rank, right-hand-side seeds offset by
+    rank x 1024): the batch shards by instances with no collective; rank 0
+    has the single-GPU workload."""
     name = "batched_1024"
     dim = 2
 
-    def __init__(self, count=1024, seed=1234, limit=None):
-        sides, fracs, rng = I.batched_sides(count, seed)
+    def __init__(self, count=1024, seed=1234, limit=None, rank=0):
+        self.rank = rank
+        sides, fracs, rng = I.batched_sides(count, seed + rank)
         self.shapes, self.spacings, self.solids, self.rhs = [], [], [], []
         for k, (n, f) in enumerate(zip(sides, fracs)):
             if limit is not None and k >= limit:
@@ -260,14 +264,15 @@ class Batched:
             self.shapes.append((n, n))
             self.spacings.append((1.0 / (n + 1), 1.0 / (n + 1)))
             self.solids.append(solid)
-            self.rhs.append(I.blob_rhs((n, n), k, solid=solid).astype(np.float32))
+            self.rhs.append(I.blob_rhs((n, n), k + rank * count, solid=solid).astype(np.float32))
         self.units = int(sum((~s).sum() for s in self.solids))
         self.cells = int(sum(n * n for n, _ in self.shapes))
 
     def config(self):
         return {"workload": "batched 2D Poisson, %d instances of sides {64,128,256,512}, random solids"
                 % len(self.shapes), "cells": self.cells, "solve_rel_tol": TOL, "unknowns_per_step": self.units,
-                "l2": "inputs (%.1f GB) larger than L2" % (self.cells * 60 / 1e9)}
+                "l2": "inputs (%.1f GB) larger than L2" % (self.cells * 60 / 1e9),
+                "sharding": "each rank solves its own instances (seeds offset by rank), no collective"}
 
 
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
@@ -510,7 +515,7 @@ def run_gpu(args, rank, world):
         io_bytes = sum(t.numel() * 4 for t in host)
         cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
     elif args.config == "batched":
-        wl = Batched()
+        wl = Batched(rank=rank)
         masks = [torch.from_numpy(m.astype(np.uint8)).to(dev) for m in wl.solids]
         bh = L.mg_create_batched(wl.shapes, wl.spacings, (0, 0, 0, 0), masks)
         mg = None

@@ -51,3 +51,16 @@ def test_traffic_records_follow_their_kernel_sources():
         # the committed summary carries the hash of the sources it was taken on
         assert "src=" in text
     assert bench.recorded_traffic("no_such_workload", "up_fine") is None
+
+
+def test_batched_instances_shard_by_rank():
+    """Rank 0 keeps the single-GPU batch; another rank draws its own
+    instances (distinct units, no collective needed)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    a = bench.Batched(count=6)
+    b = bench.Batched(count=6, rank=0)
+    c = bench.Batched(count=6, rank=1)
+    assert a.shapes == b.shapes and all(np.array_equal(x, y) for x, y in zip(a.rhs, b.rhs))
+    assert a.shapes != c.shapes or any(not np.array_equal(x, y) for x, y in zip(a.rhs, c.rhs))
