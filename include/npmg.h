@@ -166,8 +166,8 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3],
  * solves, the host launches graphs of 4 CG iterations and reads the device
  * control block between them (the same kernels in the same order; kernels
  * inside graphs with conditional nodes are not visible to ncu).  The
- * device loop allocates one float32 copy of the right-hand side when its
- * graph is first built.  Returns MG_OK,
+ * device loop reads a copy of the right-hand side in the handle's
+ * workspace; the graphs are built on the first solve.  Returns MG_OK,
  * MG_NOT_CONVERGED, MG_DIVERGED, or an error (MG_ERR_INVALID for NULL or
  * misaligned pointers or rel_tol <= 0).
  */

@@ -54,7 +54,7 @@ struct mg_handle_s {
   // built, 1 = built, -1 = not available, the host loop runs instead)
   cudaGraphExec_t loop_exec;
   int loop_state;
-  float* bsave;            // the right-hand side the loop graph reads
+  float* bsave;            // the right-hand side the loop graph reads (pool)
   int64_t loop_kernels;    // kernels in one inner body of the loop graph
   npmg::TmaLevelMaps tmaps[npmg::kMaxLevels];  // TMA tensor maps per level (levels < kc)
   bool tma_ok[npmg::kMaxLevels];

@@ -292,10 +292,6 @@ static cudaError_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle hd,
 // The loop kernels bound both loops by a count as well as by the flags.
 static cudaError_t build_loop_graph(mg_handle_s* h) {
   const mg_options& o = h->opt;
-  if (!h->bsave) {
-    cudaError_t e = cudaMalloc((void**)&h->bsave, h->ncell[0] * sizeof(float));
-    if (e != cudaSuccess) return e;
-  }
   const int chunk = loop_chunk();
   const unsigned int cap_in = (unsigned int)((o.max_outer + 2) * (o.max_inner / chunk + 3));
   const unsigned int cap_out = (unsigned int)(o.max_outer + 2);
@@ -616,6 +612,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
   plan.push_back({&h->d, n0c * 4});
   plan.push_back({&h->xff[0], n0c * 8});
   plan.push_back({&h->xff[1], n0c * 8});
+  plan.push_back({(void**)&h->bsave, n0c * 4});
   plan.push_back({(void**)&h->inv, (size_t)2 * h->ncoarse * h->ncoarse * 8});
   plan.push_back({(void**)&h->cimage, h->ca_smem});
   plan.push_back({(void**)&h->partials, (size_t)kMaxPartials * 8});
@@ -923,7 +920,6 @@ mg_status mg_destroy(mg_handle h) {
   }
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
-  if (h->bsave) cudaFree(h->bsave);
   if (h->pool) cudaFree(h->pool);
   if (h->st_host) cudaFreeHost(h->st_host);
   if (h->ev0) cudaEventDestroy(h->ev0);
