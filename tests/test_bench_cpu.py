@@ -64,3 +64,20 @@ def test_batched_instances_shard_by_rank():
     c = bench.Batched(count=6, rank=1)
     assert a.shapes == b.shapes and all(np.array_equal(x, y) for x, y in zip(a.rhs, b.rhs))
     assert a.shapes != c.shapes or any(not np.array_equal(x, y) for x, y in zip(a.rhs, c.rhs))
+
+
+def test_paper_workload_parameters():
+    """The timing workload and the implicit advection-diffusion test use the
+    paper's printed parameters: a 10^3 cube centred at (32, 64, 64) in the
+    128^3 domain with Re = 200 and dt = 0.1 (Sec. 3.4); (u, v) = (1, 1),
+    nu = 2, dt = 50 (C = 50), a Gaussian of width 10 on 128^2 nodes
+    (Sec. 3.2)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    t = bench.Timing3D(128)
+    assert t.cells == (128, 128, 128) and t.block == 10 and t.centre == (32, 64, 64)
+    assert abs(t.nu * 200.0 / (t.uin * t.block) - 1.0) < 1e-12 and t.dt == 0.1 and t.iters == 20
+    assert t.paper_s[128] == (3.0, 165.0) and t.paper_s[256] == (11.0, 1275.0) and t.paper_s[512] == (34.0, 14376.0)
+    a = bench.AdvDiff(128)
+    assert a.shape == (128, 128) and (a.u, a.v, a.nu, a.dt, a.h) == (1.0, 1.0, 2.0, 50.0, 1.0)
+    assert a.u * a.dt / a.h == 50.0 and a.gamma == 10.0
