@@ -11,9 +11,16 @@
 // vectors, the coarsest-level inverse) is carved out of one file-scope
 // device array, kScratchBytes long, that exists on every GPU that loads the
 // library until the process exits.  Host code cannot use the array's name
-// as a device address, so the first call on each device looks the address
-// up with cudaGetSymbolAddress (with that device current) and caches it.
-// That first call should therefore come before any stream capture.
+// as a device address, so the first call on each device, with that device
+// current, looks the address up with cudaGetSymbolAddress and caches it,
+// and raises the shared-memory limit of every kernel variant this entry
+// point can launch (2D and 3D, with and without a mask, any sweep count).
+// That first call should therefore come before any stream capture; later
+// calls make no CUDA call other than kernel launches and device queries
+// (cudaGetDevice, cudaDeviceGetAttribute).
+// cudaDeviceReset destroys the array together with the context: the cached
+// address is then stale, so do not call this entry point on a device after
+// resetting it.
 //
 // Every call shares the one array and leaves its contents behind; nothing in
 // the cycle reads a value that an earlier call left (each buffer is written
@@ -38,6 +45,19 @@ constexpr int kMaxDevices = 64;
 static unsigned char* g_scratch_ptr[kMaxDevices];
 static std::mutex g_scratch_mutex;
 
+// Set-up of the current device, done once: the array's device address and
+// the shared-memory opt-in of every kernel variant of the cycle.
+static cudaError_t prepare_all_variants() {
+  // the opt-in is the same for every sweep count (the device maximum); the
+  // largest sweep count checks that the widest halo still fits
+  cudaError_t e = prepare_level_kernels<2, float, false>(kMaxHalo, kMaxHalo);
+  if (e == cudaSuccess) e = prepare_level_kernels<2, float, true>(kMaxHalo, kMaxHalo);
+  if (e == cudaSuccess) e = prepare_level_kernels<3, float, false>(kMaxHalo, kMaxHalo);
+  if (e == cudaSuccess) e = prepare_level_kernels<3, float, true>(kMaxHalo, kMaxHalo);
+  if (e == cudaSuccess) e = prepare_coarse<float>(0);
+  return e;
+}
+
 static cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -47,6 +67,7 @@ static cudaError_t scratch_address(unsigned char** out) {
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = prepare_all_variants();
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = (unsigned char*)p;
   }
@@ -63,6 +84,10 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
                                        void* stream) {
   if ((dim != 2 && dim != 3) || !shape || !spacing || !bc || !d_r || !d_z) {
     set_error("mg_vcycle_noalloc: invalid arguments");
+    return MG_ERR_INVALID;
+  }
+  if (((uintptr_t)d_r | (uintptr_t)d_z) & 15) {
+    set_error("mg_vcycle_noalloc: d_r and d_z must be 16-byte aligned");
     return MG_ERR_INVALID;
   }
   mg_options o;
@@ -202,16 +227,15 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
     for (int k = 0; k < L; ++k) NPMG_CUDA(launch_cell_bytes(dim, nk[k], bcD, k == 0 ? d_solid : solid[k], cell[k], s));
   }
   {
-    const LevelDev& C = lv[L - 1];
-    const double w[3] = {C.wx, C.wy, C.wz};
     const double hk[3] = {spacing[0] * (1 << (L - 1)), spacing[1] * (1 << (L - 1)),
                           dim == 3 ? spacing[2] * (1 << (L - 1)) : 1.0};
     const double wd[3] = {c / (hk[0] * hk[0]), c / (hk[1] * hk[1]), dim == 3 ? c / (hk[2] * hk[2]) : 0.0};
-    (void)w;
     NPMG_CUDA(launch_coarse_inverse(dim, nk[L - 1], wd, bcD, masked ? cell[L - 1] : nullptr, inv, s));
   }
   CoarseArgs ca;
   memset(&ca, 0, sizeof(ca));
+  // (the coarse block's shared memory was opted in to the device maximum at
+  // set-up; coarse_start_level keeps the layout within it)
   ca.nlev = L - kc;
   ca.dim = dim;
   for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = lv[kc + l];
@@ -230,8 +254,7 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   auto cycle = [&](auto dimc, auto mc) -> cudaError_t {
     constexpr int DIM = decltype(dimc)::value;
     constexpr bool M = decltype(mc)::value;
-    cudaError_t e = prepare_level_kernels<DIM, float, M>(o.pre, o.post);
-    if (e == cudaSuccess) e = prepare_coarse<float>(moff);
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < kc && e == cudaSuccess; ++k)
       e = launch_down<DIM, float, M>(lv[k], k == 0 ? (const void*)d_r : bk[k], xk[k], bk[k + 1], o.pre, om,
                                      nullptr, s);

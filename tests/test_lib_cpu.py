@@ -121,3 +121,18 @@ def test_guess_network_rejects_invalid_arguments(lib):
     assert lib.gn_dataset_size(None) == 0
     assert lib.ns_set_guess(None, None) == L.MG_ERR_INVALID
     assert "ns_set_guess" in L.last_error()
+
+
+def test_noalloc_rejects_misaligned_arrays_before_any_cuda_call(lib):
+    """mg_vcycle_noalloc checks the caller's arrays on the host: a pointer
+    that is not 16-byte aligned is refused before the device is touched (the
+    fake addresses here are never dereferenced)."""
+    from paper_2402_17913_gb300 import lib as L
+    shp = (ctypes.c_int64 * 3)(32, 32, 1)
+    sp = (ctypes.c_double * 3)(1 / 33, 1 / 33, 1.0)
+    b6 = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
+    o = L.default_options()
+    for r, z in ((0x10004, 0x20000), (0x10000, 0x20008)):
+        st = lib.mg_vcycle_noalloc(2, shp, sp, b6, None, ctypes.byref(o), r, z, None)
+        assert st == L.MG_ERR_INVALID
+        assert "aligned" in L.last_error()
