@@ -51,23 +51,39 @@ AD_L1_METRIC = "solved unknowns/sec to an L1 change of 1e-5 per cycle"
 UNIT = "unknowns/s"
 TOL = 1e-6
 
-# Algorithmic bytes per fine-grid cell of one launch of each kernel class
-# (float32 storage, the method's own minimum: each array read or written
-# once per launch; masked levels read one cell byte more).  Only classes
-# that dominate a step are listed.
 # Batched solve: bytes per fine cell of one CG iteration (the four fine
-# passes above, plus one cell byte in three of them, plus about a third more
+# passes below, plus one cell byte in three of them, plus about a third more
 # for the coarser levels) and of one float-float refinement pass.
 BATCH_ITER_BYTES = 72
 OUTER_BYTES = 28
+KERNEL_CLASSES = ("down_fine", "up_fine", "p_update", "xr_update", "outer")
 
-ALGO_BYTES_PER_CELL = {
-    "down_fine": 4 + 4 + 1,          # read b (= CG residual); write x, coarse b (1/4)
-    "up_fine": 4 + 4 + 1 + 4,        # read b, x, coarse e (1/4); write z
-    "p_update": 4 + 4 + 4 + 4,       # read z, p_old; write p, Ap
-    "xr_update": 4 + 4 + 8 + 8,      # read p, Ap; read+write d, r
-    "outer": 4 + 8 + 4 + 8 + 4,      # read b, x64, d; write x64, r'
-}
+
+def algo_bytes_per_cell(cls, dim, prec="fp32", masked=False):
+    """Algorithmic bytes per fine-grid cell of one launch of kernel class
+    `cls` (the method's own minimum: each array read or written once per
+    launch, at its own storage width).  The level arrays (the finest
+    iterate x and every coarser level's arrays) are 4 bytes in float32 and 2
+    in FP16/BF16; the finest right-hand side (the CG residual r) and output
+    z, and the CG vectors, are float32 in every form; a masked grid reads one
+    cell byte per cell in the level kernels; the coarse level has 1/2^dim of
+    the cells."""
+    t = 4 if prec == "fp32" else 2
+    c = 1.0 / (1 << dim)
+    m = 1 if masked else 0
+    return {
+        "down_fine": 4 + t + t * c + m,      # read b; write x, coarse b
+        "up_fine": 4 + t + t * c + 4 + m,    # read b, x, coarse e; write z
+        "p_update": 4 + 4 + 4 + 4,           # read z, p_old; write p, Ap
+        "xr_update": 4 + 4 + 8 + 8,          # read p, Ap; read+write d, r
+        "outer": 4 + 8 + 4 + 8 + 4,          # read b, iterate, d; write iterate, r
+    }[cls]
+
+
+# Bytes per cell a solve keeps live (the right-hand side and its copy, the
+# iterate, the CG vectors, the refinement pair, about a third more for the
+# coarser levels): a grid below L2 / this stays L2-resident between launches.
+LIVE_BYTES_PER_CELL = 48
 
 
 def parse():
@@ -76,7 +92,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="ns2d",
+    ap.add_argument("--config", default="poisson3d",
                     choices=["ns2d", "ns3d", "poisson2d", "poisson3d", "batched", "timing3d", "advdiff"])
     ap.add_argument("--ad-size", type=int, default=128, choices=[128, 1024, 4096],
                     help="advdiff: nodes per side")
@@ -92,6 +108,9 @@ def parse():
     ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1, 2],
                     help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--advance", type=int, default=None,
+                    help="ns2d/ns3d: untimed steps from the seeded initial state before the warm-up "
+                         "(default: ns2d 480, ns3d 180, so that the timed steps end near step 500 / 200)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true",
                     help="run warm-up and timed steps only (for launch-list captures)")
@@ -120,7 +139,8 @@ class NS2D:
         return {"workload": "2D projection step, flow past a square block", "cells": list(self.cells),
                 "block": self.block, "nu": self.nu, "dt": self.dt, "u_inflow": self.uin,
                 "solve_rel_tol": TOL, "unknowns_per_step": self.units,
-                "momentum_filters": FILTERS[self.fe], "l2": "256 MiB buffer written between timed steps"}
+                "momentum_filters": FILTERS[self.fe], "l2": "256 MiB buffer written between timed steps",
+                "timed_steps": list(getattr(self, "window", ()))}
 
 
 class NS3D:
@@ -143,7 +163,7 @@ class NS3D:
         return {"workload": "3D projection step, flow past a cube", "cells": list(self.cells), "block": self.block,
                 "nu": self.nu, "dt": self.dt, "u_inflow": self.uin, "solve_rel_tol": TOL,
                 "unknowns_per_step": self.units, "momentum_filters": FILTERS[self.fe],
-                "l2": "256 MiB buffer written between timed steps"}
+                "l2": "256 MiB buffer written between timed steps", "timed_steps": list(getattr(self, "window", ()))}
 
 
 class Timing3D:
@@ -242,37 +262,61 @@ class Poisson:
         return c
 
 
+def shard_by_work(weights, world):
+    """Split items over `world` ranks by work: heaviest first, each onto the
+    rank with the least work so far (ties: the lowest rank).  Returns one
+    sorted list of item indices per rank."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for k in sorted(range(len(weights)), key=lambda i: (-weights[i], i)):
+        r = min(range(world), key=lambda j: (load[j], j))
+        load[r] += weights[k]
+        parts[r].append(k)
+    return [sorted(p) for p in parts]
+
+
 class Batched:
     """1024 independent square instances, sides uniform in {64, 128, 256,
     512} (seed 1234), random rectangle solids covering U(0, 0.1) of the
     cells (flood-filled), 8-blob right-hand sides (seed = instance index),
-    zero Dirichlet faces.  Under several ranks each rank solves its own
-    1024 instances (sides seed 1234 + rank, right-hand-side seeds offset by
-    rank x 1024): the batch shards by instances with no collective; rank 0
-    has the single-GPU workload."""
+    zero Dirichlet faces.  Under several ranks the one batch is split by
+    work (sum of N^2, heaviest instance first onto the least-loaded rank):
+    each rank solves its share with no collective, and the whole job is the
+    1024 instances (strong scaling)."""
     name = "batched_1024"
     dim = 2
 
-    def __init__(self, count=1024, seed=1234, limit=None, rank=0):
-        self.rank = rank
-        sides, fracs, rng = I.batched_sides(count, seed + rank)
-        self.shapes, self.spacings, self.solids, self.rhs = [], [], [], []
-        for k, (n, f) in enumerate(zip(sides, fracs)):
-            if limit is not None and k >= limit:
-                break
-            solid = I.random_solid_mask((n, n), rng, f)
+    def __init__(self, count=1024, seed=1234, limit=None, rank=0, world=1):
+        self.rank, self.world = rank, world
+        sides, fracs, rng = I.batched_sides(count, seed)
+        n_all = len(sides) if limit is None else min(limit, len(sides))
+        self.count = n_all
+        self.own = set(shard_by_work([sides[k] ** 2 for k in range(n_all)], world)[rank])
+        self.index, self.shapes, self.spacings, self.solids, self.rhs = [], [], [], [], []
+        self.job_units = 0
+        for k in range(n_all):
+            n, f = sides[k], fracs[k]
+            solid = I.random_solid_mask((n, n), rng, f)  # every mask, in draw order
+            self.job_units += int((~solid).sum())
+            if k not in self.own:
+                continue
+            self.index.append(k)
             self.shapes.append((n, n))
             self.spacings.append((1.0 / (n + 1), 1.0 / (n + 1)))
             self.solids.append(solid)
-            self.rhs.append(I.blob_rhs((n, n), k + rank * count, solid=solid).astype(np.float32))
+            self.rhs.append(I.blob_rhs((n, n), k, solid=solid).astype(np.float32))
         self.units = int(sum((~s).sum() for s in self.solids))
         self.cells = int(sum(n * n for n, _ in self.shapes))
 
     def config(self):
-        return {"workload": "batched 2D Poisson, %d instances of sides {64,128,256,512}, random solids"
-                % len(self.shapes), "cells": self.cells, "solve_rel_tol": TOL, "unknowns_per_step": self.units,
-                "l2": "inputs (%.1f GB) larger than L2" % (self.cells * 60 / 1e9),
-                "sharding": "each rank solves its own instances (seeds offset by rank), no collective"}
+        c = {"workload": "batched 2D Poisson, %d instances of sides {64,128,256,512}, random solids"
+             % self.count, "cells": self.cells,
+             "solve_rel_tol": TOL, "unknowns_per_step": self.units,
+             "l2": "inputs (%.1f GB) larger than L2" % (self.cells * 60 / 1e9)}
+        if self.world > 1:
+            c["sharding"] = ("one batch split over %d ranks by sum of N^2 (heaviest first), no collective; "
+                             "this rank: %d instances" % (self.world, len(self.shapes)))
+        return c
 
 
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
@@ -325,6 +369,27 @@ def measured_peak():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def l2_read_peak(L, dev, l2_size):
+    """L2 read bandwidth (GB/s) of a streaming kernel on this GPU: a buffer
+    of a quarter of L2 read 64 times in one launch (best of 5 launches,
+    CUDA events)."""
+    import torch
+    n = (l2_size // 4 // 4) // 4 * 4
+    buf = torch.ones(n, dtype=torch.float32, device=dev)
+    sink = torch.empty(4 * torch.cuda.get_device_properties(dev).multi_processor_count, dtype=torch.float32,
+                       device=dev)
+    reps, best = 64, float("inf")
+    L.mg_probe_l2_read(buf, reps, sink)
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.mg_probe_l2_read(buf, reps, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return n * 4.0 * reps / (best * 1e-3) / 1e9
 
 
 # The translation unit of the dominant kernel of each workload with a
@@ -488,7 +553,8 @@ def run_gpu(args, rank, world):
             q = wl.initial_velocity()
         else:
             q = [a.astype(np.float32) for a in I.ns_initial_velocity(wl.cells, 0)]
-        host = [torch.from_numpy(a).pin_memory() for a in q + [np.zeros(wl.solid.shape, np.float32)]]
+        init = [a.copy() for a in q] + [np.zeros(wl.solid.shape, np.float32)]
+        host = [torch.from_numpy(a.copy()).pin_memory() for a in init]
         fields = [t.to(dev) for t in host]
         u, v, p = fields[0], fields[1], fields[-1]
         w = fields[2] if wl.dim == 3 else None
@@ -501,10 +567,25 @@ def run_gpu(args, rank, world):
             for d, t in zip(host, fields):
                 t.copy_(d)
             torch.cuda.synchronize()
+        advance = args.advance if args.advance is not None else {"ns2d": 480, "ns3d": 180}.get(args.config, 0)
+        for _ in range(advance):
+            L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, tol, stats=False)
+        torch.cuda.synchronize()
+        wl.window = (advance + args.warmup + 1, advance + args.warmup + args.steps)
 
         def step():
             _, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, tol)
             stats.append(st)
+
+        def check():
+            """One step from the seeded initial state (the state the oracle
+            step starts from), fields as float32 numpy arrays."""
+            for d, a in zip(fields, init):
+                d.copy_(torch.from_numpy(a))
+            status, st = L.ns_step(ns, u, v, w, p, wl.dt, wl.nu, wl.uin, tol)
+            torch.cuda.synchronize()
+            return {"kind": "ns", "q": [t.cpu().numpy() for t in fields[:-1]], "p": fields[-1].cpu().numpy(),
+                    "relres": st["relres"], "status": status}
 
         def e2e_step():
             for d, hsrc in zip(fields, host):
@@ -515,7 +596,7 @@ def run_gpu(args, rank, world):
         io_bytes = sum(t.numel() * 4 for t in host)
         cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
     elif args.config == "batched":
-        wl = Batched(rank=rank)
+        wl = Batched(rank=rank, world=world)
         masks = [torch.from_numpy(m.astype(np.uint8)).to(dev) for m in wl.solids]
         bh = L.mg_create_batched(wl.shapes, wl.spacings, (0, 0, 0, 0), masks)
         mg = None
@@ -525,6 +606,12 @@ def run_gpu(args, rank, world):
         dx = [torch.zeros_like(t) for t in db]
         tuned = L.mg_tune_batched(bh, db, dx, TOL)
         stats = []
+
+        def check():
+            """The float32 results of the instances the oracle leg solves
+            (the first 16 of the batch), from the last solve."""
+            torch.cuda.synchronize()
+            return {"kind": "batched", "x": {k: t.cpu().numpy() for k, t in zip(wl.index, dx) if k < 16}}
 
         def step():
             for t in dx:
@@ -568,6 +655,7 @@ def run_gpu(args, rank, world):
             step()
             x_host.copy_(x, non_blocking=True)
         io_bytes = b_host.numel() * 4
+        check = None
         cleanup = lambda: L.ad_destroy(hd)  # noqa: E731
     else:
         shape = (256, 256) if args.config == "poisson2d" else (256, 256, 256)
@@ -590,6 +678,14 @@ def run_gpu(args, rank, world):
             x.zero_()
             _, st = L.mg_solve(mg, b, x, TOL)
             stats.append(st)
+
+        def check():
+            """The float64 iterate and the float32 output of the last solve."""
+            x64 = torch.zeros(shape, dtype=torch.float64, device=dev)
+            L.mg_get_solution_f64(mg, x64)
+            torch.cuda.synchronize()
+            return {"kind": "poisson", "x64": x64.cpu().numpy(), "x32": x.cpu().numpy(),
+                    "relres": stats[-1]["relres"] if stats else None}
 
         def e2e_step():
             b.copy_(b_host, non_blocking=True)
@@ -642,6 +738,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append(t0.elapsed_time(t1))
     e2e_total = dist_max(sum(e2e_ms), world)
+    check_data = check() if (check is not None and rank == 0) else None
     guess_rec = guess_report(L, guess, step_stats, ns, wl, u, v, w, p) if guess else None
     peak, peak_kind = measured_peak()
     if args.config == "batched":
@@ -689,30 +786,44 @@ def run_gpu(args, rank, world):
         L.mg_profile_enable(mg, False)
         cleanup()
         tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
-        dom = max(ALGO_BYTES_PER_CELL, key=lambda k: prof[k][0])
+        dom = max(KERNEL_CLASSES, key=lambda k: prof[k][0])
         ms_dom, n_dom = prof[dom]
         is_ns = args.config in ("ns2d", "ns3d", "timing3d")
         ncell = int(np.prod(wl.cells)) if is_ns else wl.units
-        per_cell = ALGO_BYTES_PER_CELL[dom] + (1 if is_ns and dom != "xr_update" else 0)
-        if args.prec != "fp32" and not is_ns:
-            per_cell = per_cell / 2.0 if dom not in ("outer",) else 8 + 4 + 2 + 8 + 2
+        per_cell = algo_bytes_per_cell(dom, wl.dim, "fp32" if is_ns else args.prec, masked=is_ns)
         algo = per_cell * ncell
-        achieved = algo / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                    "traffic": recorded_traffic(wl.name, dom), "algorithmic_bytes_per_launch": algo,
-                    "avg_launch_us": round(ms_dom / max(n_dom, 1) * 1e3, 2),
-                    "share_of_step": round(ms_dom / tot_prof, 3),
+        us = ms_dom / max(n_dom, 1) * 1e3
+        achieved = algo / (us * 1e-6) / 1e9
+        roofline = {"kernel": dom, "achieved": round(achieved, 1), "unit": "GB/s",
+                    "algorithmic_bytes_per_cell": per_cell, "algorithmic_bytes_per_launch": algo,
+                    "avg_launch_us": round(us, 2), "share_of_step": round(ms_dom / tot_prof, 3),
                     "class_shares": {k: round(v[0] / tot_prof, 3) for k, v in prof.items() if v[1]}}
-    value = job_rate(wl.units, args.steps, world, total_ms)
+        l2_size = torch.cuda.get_device_properties(dev).L2_cache_size
+        if ncell * LIVE_BYTES_PER_CELL < l2_size:
+            # the solve's arrays stay in L2 between launches (DRAM sees almost
+            # none of the traffic): the roof is L2, measured live
+            l2 = l2_read_peak(L, dev, l2_size)
+            roofline.update(bound="l2", peak=round(l2, 1), peak_source="measured live (mg_probe_l2_read)",
+                            frac=round(achieved / l2, 4), traffic=None,
+                            hbm={"peak": peak, "peak_source": peak_kind, "frac": round(achieved / peak, 4)})
+        else:
+            roofline.update(bound="hbm", peak=peak, peak_source=peak_kind, frac=round(achieved / peak, 4),
+                            traffic=recorded_traffic(wl.name, dom))
+    # whole-job rate: replicas each solve their own step (weak scaling); the
+    # batched workload is one batch split over the ranks (strong scaling)
+    split = getattr(wl, "job_units", None)
+    value = job_rate(wl.units, args.steps, world, total_ms) if split is None else \
+        split * args.steps / (total_ms * 1e-3)
+    e2e_value = (wl.units * args.steps * world if split is None else split * args.steps) / (e2e_total * 1e-3)
     its = [s["iters"] for s in step_stats]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
+        "scaling": "weak" if split is None else "strong", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else args.prec,
         "data": "synthetic", "config": dict(wl.config(), parallelism="replicas" if world > 1 else "single"),
         "clocks": clocks, "gpu_launches": int(launches),
-        "e2e": {"value": wl.units * args.steps * world / (e2e_total * 1e-3), "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "roofline": roofline,
         "guess": guess_rec,
@@ -734,7 +845,64 @@ def run_gpu(args, rank, world):
                    vs_baseline=(five / t4 if t4 and args.cycle == "sawtooth" else None), unknowns_per_s=value)
         out["e2e"] = dict(out["e2e"], value=5 * e2e_total / args.steps / 1e3, unit="s")
         out["solve"]["relres_per_step"] = [s["relres"] for s in step_stats]
+    if args.config == "poisson3d" and args.prec == "fp32" and args.cycle == "v":
+        # the same solve with FP16 / BF16 level storage, against this line's
+        # plain float32 form
+        out["mixed_precision"] = {}
+        for prec in ("fp16", "bf16"):
+            rec = time_poisson(L, dev, flush, wl.shape, prec, args.steps, args.warmup)
+            rec["vs_fp32"] = round(rec["value"] / value, 4)
+            out["mixed_precision"][prec] = rec
+    out["_check"] = check_data
     return out, wl
+
+
+def time_poisson(L, dev, flush, shape, prec, steps, warmup):
+    """Solves of the blob workload to relres 1e-6 with level storage `prec`:
+    unknowns/s over `steps` event-timed solves (L2 flushed between them),
+    iterations, relres, and the up_fine class's fraction of the measured
+    copy bandwidth from a profiled pass."""
+    import torch
+    h = I.poisson_spacing(shape)
+    mg = L.mg_create(len(shape), tuple(reversed(shape)), h, (0,) * (2 * len(shape)), None,
+                     L.default_options(prec=PREC[prec]))
+    try:
+        b = torch.from_numpy(I.blob_rhs(shape, 0).astype(np.float32)).to(dev)
+        x = torch.zeros_like(b)
+        stats = []
+        for _ in range(warmup):
+            x.zero_()
+            L.mg_solve(mg, b, x, TOL)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.fill_(float(i))
+            x.zero_()
+            ev[i][0].record()
+            stats.append(L.mg_solve(mg, b, x, TOL)[1])
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+        L.mg_profile_enable(mg, True)
+        L.mg_profile_read(mg, reset=True)
+        for i in range(min(steps, 5)):
+            flush.fill_(float(i))
+            x.zero_()
+            L.mg_solve(mg, b, x, TOL)
+        prof = L.mg_profile_read(mg, reset=True)
+        L.mg_profile_enable(mg, False)
+    finally:
+        L.mg_destroy(mg)
+    units = int(np.prod(shape))
+    per_cell = algo_bytes_per_cell("up_fine", len(shape), prec)
+    ms_up, n_up = prof["up_fine"]
+    achieved = per_cell * units / (ms_up / max(n_up, 1) * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    return {"value": units / (ms * 1e-3), "ms_per_step": round(ms, 4),
+            "cg_iters_mean": statistics.mean(s["iters"] for s in stats),
+            "relres_max": max(s["relres"] for s in stats),
+            "up_fine": {"algorithmic_bytes_per_cell": per_cell, "achieved": round(achieved, 1),
+                        "frac": round(achieved / peak, 4), "peak": peak, "peak_source": peak_kind}}
 
 
 def oracle_step_time(wl, budget_s=30.0, max_steps=3):
@@ -846,8 +1014,26 @@ def dist_max(v, world):
     return float(t.item())
 
 
+def launch_ranks(n):
+    """`--gpus N` without a launcher: run this command under
+    torch.distributed.run with N ranks on this node (127.0.0.1) and return
+    its exit code."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    world_env = os.environ.get("WORLD_SIZE")
+    if world_env is None and args.gpus > 1:
+        sys.exit(launch_ranks(args.gpus))
+    if int(world_env or "1") != args.gpus:
+        sys.exit("bench.py: --gpus %d but WORLD_SIZE=%s; launch one rank per GPU" % (args.gpus, world_env))
     rank, world = dist_init()
     if args.impl == "reference":
         if rank != 0:
@@ -888,23 +1074,131 @@ def main():
             line["e2e"] = dict(line["e2e"], value=secs, unit="s")
         print(json.dumps(line))
         return
+    # the oracle's answer to the GPU line's own problem, computed in a spawn
+    # worker (started before this process touches the GPU) while the GPU runs
+    pool = fut = None
+    want_check = (rank == 0 and world == 1 and not args.only_timed and not args.no_cpu_baseline
+                  and args.config in ("poisson2d", "poisson3d", "ns2d", "ns3d") and args.cycle == "v")
+    if want_check:
+        import concurrent.futures
+        import multiprocessing
+        pool = concurrent.futures.ProcessPoolExecutor(1, mp_context=multiprocessing.get_context("spawn"))
+        fut = pool.submit(oracle_reference, args.config, args.stencil == "fe")
     out, wl = run_gpu(args, rank, world)
+    check = out.pop("_check", None)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
-            ms = {"poisson2d": 5, "batched": 64}.get(args.config, 1)
-            # 3D: the full-size oracle step takes minutes; time a smaller copy
-            cpu_wl = {"ns3d": lambda: NS3D(scale=2, fe=wl.fe),
-                      "timing3d": lambda: Timing3D(args.size, args.cycle, scale=max(1, args.size // 64)),
-                      "advdiff": lambda: AdvDiff(min(args.ad_size, 512), args.cycle),
-                      "poisson3d": lambda: Poisson((128, 128, 128), args.prec)}.get(
-                args.config, lambda: wl)()
-            rate, sample, n = oracle_step_time(cpu_wl, budget_s=25.0, max_steps=ms)
+            spec = sample_spec(args)
+            rate, sample, n = oracle_step_time(cpu_sample(spec), budget_s=25.0, max_steps=spec["max_steps"])
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            agg, procs = oracle_all_cores(spec)
+            out["cpu_baseline"]["all_cores"] = {
+                "value": agg, "unit": UNIT, "cores": procs, "kind": "oracle",
+                "sample": "%d copies of the same sample at once, one process per core" % procs}
             if args.config == "timing3d":
                 # the line's unit: seconds for five steps, scaled by cells
                 out["cpu_baseline"].update(value=5 * wl.units / rate, unit="s",
                                            sample=sample + "; seconds scaled to the full size by cells")
+                out["cpu_baseline"]["all_cores"].update(value=5 * wl.units / agg, unit="s")
+        if fut is not None:
+            out["oracle_check"] = compare_with_oracle(args.config, check, fut.result(), args.stencil == "fe")
+            pool.shutdown()
         print(json.dumps(out))
+
+
+def sample_spec(args):
+    """The bounded sample the CPU baseline times (picklable)."""
+    return {"config": args.config, "prec": args.prec, "size": args.size, "cycle": args.cycle,
+            "ad_size": args.ad_size, "fe": args.stencil == "fe",
+            "max_steps": {"poisson2d": 5, "batched": 64}.get(args.config, 1)}
+
+
+def cpu_sample(spec):
+    """Workload of the CPU baseline: the GPU line's own workload, or (3D, and
+    the large advection-diffusion grids) a smaller copy the oracle finishes
+    in seconds."""
+    c, fe = spec["config"], spec["fe"]
+    if c == "ns2d":
+        return NS2D(fe=fe)
+    if c == "ns3d":
+        return NS3D(scale=2, fe=fe)
+    if c == "timing3d":
+        return Timing3D(spec["size"], spec["cycle"], scale=max(1, spec["size"] // 64))
+    if c == "advdiff":
+        return AdvDiff(min(spec["ad_size"], 512), spec["cycle"])
+    if c == "poisson3d":
+        return Poisson((128, 128, 128), spec["prec"])
+    if c == "poisson2d":
+        return Poisson((256, 256), spec["prec"], spec["cycle"])
+    return Batched()
+
+
+def _oracle_sample_worker(spec, start_at):
+    wl = cpu_sample(spec)
+    while time.time() < start_at:  # every process starts its timing together
+        time.sleep(0.01)
+    t0 = time.time()
+    rate, _, n = oracle_step_time(wl, budget_s=1.0, max_steps=1)
+    return rate * (time.time() - t0), t0, time.time()
+
+
+def oracle_all_cores(spec):
+    """The oracle on every host core at once: one process per core, each
+    timing one step of the same sample; aggregate unknowns/s = all units /
+    the span from the first start to the last end."""
+    import concurrent.futures
+    import multiprocessing
+    procs = min(os.cpu_count() or 1, 16)
+    with concurrent.futures.ProcessPoolExecutor(procs, mp_context=multiprocessing.get_context("spawn")) as ex:
+        start_at = time.time() + 20.0 + 0.5 * procs  # time to spawn and build the samples
+        res = list(ex.map(_oracle_sample_worker, [spec] * procs, [start_at] * procs))
+    units = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / span, procs
+
+
+def oracle_reference(config, fe=False):
+    """The FP64 oracle's answer to the problem the GPU line also solves:
+    the Poisson blob workload solved by the oracle's MG-PCG with refinement
+    to relres 1e-6 (the same stopping rule), or one projection step from the
+    seeded initial state with the pressure solved to relres 1e-12."""
+    from oracle import ns as N
+    from oracle import poisson as P
+    if config in ("poisson2d", "poisson3d"):
+        shape = (256, 256) if config == "poisson2d" else (256, 256, 256)
+        b = I.blob_rhs(shape, 0).astype(np.float32).astype(np.float64)
+        mg = P.Multigrid(P.build_hierarchy(shape, I.poisson_spacing(shape), (0,) * (2 * len(shape))), s=1.0)
+        x, hist, inner = P.pcg_ir(mg, b, tol=TOL)
+        return {"x": x, "relres": hist[-1], "iters": inner}
+    wl = NS2D(fe=fe) if config == "ns2d" else NS3D(fe=fe)
+    q = [a.astype(np.float32).astype(np.float64) for a in I.ns_initial_velocity(wl.cells, 0)]
+    g = N.MacGrid(wl.cells, 1.0, wl.solid)
+    qn, pn, _, _, _ = N.ns_step(g, q, np.zeros(wl.solid.shape), wl.dt, wl.nu, wl.uin, fe=fe)
+    return {"q": qn, "p": pn}
+
+
+def compare_with_oracle(config, gpu, ref, fe=False):
+    """Error of the GPU result against the oracle's, per result."""
+    from oracle import poisson as P
+    if gpu is None or ref is None:
+        return None
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))  # noqa: E731
+    if gpu["kind"] == "poisson":
+        shape = (256, 256) if config == "poisson2d" else (256, 256, 256)
+        lv = P.Level(shape, I.poisson_spacing(shape), (0,) * (2 * len(shape)))
+        b = I.blob_rhs(shape, 0).astype(np.float32).astype(np.float64)
+        return {"what": "the timed solve's result vs the oracle's MG-PCG solve to the same relres 1e-6",
+                "relres_gpu_float64_iterate": P.relres(lv, b, gpu["x64"]),
+                "relres_gpu_float32_output": P.relres(lv, b, gpu["x32"].astype(np.float64)),
+                "relerr_float64_iterate": rel(gpu["x64"], ref["x"]), "relerr_float32_output":
+                rel(gpu["x32"].astype(np.float64), ref["x"]),
+                "oracle_relres": ref["relres"], "oracle_cg_iters": ref["iters"]}
+    out = {"what": "one step from the seeded initial state vs the oracle's step (pressure solved to 1e-12)",
+           "relres_gpu": gpu["relres"]}
+    for c, name in enumerate("uvw"[:len(gpu["q"])]):
+        out["relerr_" + name] = rel(gpu["q"][c].astype(np.float64), ref["q"][c])
+    out["relerr_p"] = rel(gpu["p"].astype(np.float64), ref["p"])
+    return out
 
 
 if __name__ == "__main__":

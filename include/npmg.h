@@ -192,6 +192,8 @@ int mg_num_levels(mg_handle h);
  *   mg_residual_restrict: d_bc (level k+1) = R (b - A'_k x).
  *   mg_prolong_correct: x += s * P e (e on level k+1), 0 on solid cells.
  *   mg_precondition: d_z = one cycle of the preconditioner on r, level 0.
+ * Every array must be 16-byte aligned (the kernels move float4 vectors);
+ * a NULL or misaligned array returns MG_ERR_INVALID with nothing enqueued.
  */
 mg_status mg_apply_operator(mg_handle h, int k, const float* d_x, float* d_y,
                             void* stream);
@@ -257,6 +259,18 @@ typedef enum {
 mg_status mg_profile_enable(mg_handle h, int on);
 mg_status mg_profile_read(mg_handle h, double* h_ms, int64_t* h_launches, int reset);
 int64_t mg_kernel_launches(mg_handle h);
+
+/*
+ * mg_probe_l2_read (instrumentation, no counterpart in the paper): the
+ * roof for kernels whose working set stays in L2.  One kernel launch on
+ * `stream` reads the n floats of d_buf (device, 16-byte aligned, n a
+ * multiple of 4) `reps` times with coalesced 16-byte loads over 4 blocks per
+ * SM, and writes one partial sum per block into d_sink (device, at least
+ * 4 x the SM count floats).  With d_buf smaller than L2, the caller's CUDA
+ * events around the call give the L2 read bandwidth (n * 4 * reps bytes /
+ * time).  Errors: MG_ERR_INVALID (bad sizes or alignment), MG_ERR_CUDA.
+ */
+mg_status mg_probe_l2_read(const float* d_buf, int64_t n, int reps, float* d_sink, int sink_len, void* stream);
 
 /*
  * Projection step (Algorithm 1) on a staggered grid of cells (x, y[, z])

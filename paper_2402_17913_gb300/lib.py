@@ -33,7 +33,7 @@ EXPORTED = [
     "gn_dataset_reserve", "gn_dataset_add", "gn_dataset_size", "gn_train", "gn_conv3d", "gn_conv3d_wgrad",
     "gn_destroy", "ns_set_guess", "ns_last_fields", "gn_kernel_launches", "ns_set_guess_level",
     "ns_coarse_fields", "ns_set_stencils", "ad_default_options", "ad_create", "ad_solve", "ad_num_levels",
-    "ad_coarse_start", "ad_kernel_launches", "ad_destroy",
+    "ad_coarse_start", "ad_kernel_launches", "ad_destroy", "mg_probe_l2_read",
 ]
 GN_NUM_WEIGHTS = 49680
 GN_CONV_SCRATCH_BYTES = 28160
@@ -175,6 +175,7 @@ def load():
         "ns_coarse_fields": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "gn_kernel_launches": (ctypes.c_int64, []),
         "ns_last_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+        "mg_probe_l2_read": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, _vp, ctypes.c_int, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +273,13 @@ def mg_prolong_correct(h, k, e, x, stream=None):
 
 def mg_precondition(h, r, z, stream=None):
     _check(load().mg_precondition(h, ptr(r), ptr(z), stream_ptr(stream)))
+
+
+def mg_probe_l2_read(buf, reps, sink, stream=None):
+    """One launch reading the float32 device tensor ``buf`` ``reps`` times
+    (the L2 roof when ``buf`` fits in L2); ``sink`` holds one float per
+    block (4 x the SM count)."""
+    _check(load().mg_probe_l2_read(ptr(buf), buf.numel(), reps, ptr(sink), sink.numel(), stream_ptr(stream)))
 
 
 def mg_destroy(h):

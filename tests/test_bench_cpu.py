@@ -53,17 +53,25 @@ def test_traffic_records_follow_their_kernel_sources():
     assert bench.recorded_traffic("no_such_workload", "up_fine") is None
 
 
-def test_batched_instances_shard_by_rank():
-    """Rank 0 keeps the single-GPU batch; another rank draws its own
-    instances (distinct units, no collective needed)."""
+def test_batched_batch_splits_over_ranks_by_work():
+    """One batch split over the ranks: disjoint shares that together are the
+    whole batch, balanced by sum of N^2; rank 0 of one rank is the whole
+    single-GPU batch, with the same instances (masks and right-hand sides)."""
     sys.path.insert(0, ROOT)
     import numpy as np
     import bench
-    a = bench.Batched(count=6)
-    b = bench.Batched(count=6, rank=0)
-    c = bench.Batched(count=6, rank=1)
-    assert a.shapes == b.shapes and all(np.array_equal(x, y) for x, y in zip(a.rhs, b.rhs))
-    assert a.shapes != c.shapes or any(not np.array_equal(x, y) for x, y in zip(a.rhs, c.rhs))
+    whole = bench.Batched(count=12)
+    assert whole.index == list(range(12)) and whole.job_units == whole.units
+    parts = [bench.Batched(count=12, rank=r, world=3) for r in range(3)]
+    idx = sorted(k for p in parts for k in p.index)
+    assert idx == list(range(12))
+    assert all(p.job_units == whole.job_units for p in parts)
+    for p in parts:
+        for k, rhs, solid in zip(p.index, p.rhs, p.solids):
+            assert np.array_equal(rhs, whole.rhs[k]) and np.array_equal(solid, whole.solids[k])
+    work = [sum(n * n for n, _ in p.shapes) for p in parts]
+    assert max(work) - min(work) <= 512 * 512
+    assert bench.shard_by_work([4, 3, 3, 2, 2, 2], 2) == [[0, 3, 4], [1, 2, 5]]
 
 
 def test_paper_workload_parameters():
@@ -81,3 +89,22 @@ def test_paper_workload_parameters():
     a = bench.AdvDiff(128)
     assert a.shape == (128, 128) and (a.u, a.v, a.nu, a.dt, a.h) == (1.0, 1.0, 2.0, 50.0, 1.0)
     assert a.u * a.dt / a.h == 50.0 and a.gamma == 10.0
+
+
+def test_gpus_flag_must_match_the_launch():
+    """--gpus N under a launcher that started a different number of ranks is
+    an error (the line would otherwise claim the wrong GPU count)."""
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0")
+    out = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--steps", "1"], cwd=ROOT, env=env,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode != 0 and "WORLD_SIZE" in out.stderr
+
+
+def test_algorithmic_bytes_count_each_array_at_its_width():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.algo_bytes_per_cell("up_fine", 2) == 13.0
+    assert bench.algo_bytes_per_cell("up_fine", 3) == 12.5
+    assert bench.algo_bytes_per_cell("up_fine", 3, "fp16") == 4 + 2 + 0.25 + 4
+    assert bench.algo_bytes_per_cell("down_fine", 3, "bf16", masked=True) == 4 + 2 + 0.25 + 1
+    assert bench.algo_bytes_per_cell("p_update", 3, "fp16") == 16
