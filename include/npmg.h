@@ -95,9 +95,18 @@ typedef struct {
                            (no exact coarsest solve; `pre` is ignored).  With
                            the re-discretised coarse levels the stationary
                            sawtooth needs coarse_scale ~ 0.5.                 */
+  int refine;           /* arithmetic of the refinement loop's iterate and
+                           outer residual (Sec. 4 item (4), mixed precision
+                           with iterative refinement): MG_REFINE_FP64
+                           (default) keeps the iterate in float64 and forms
+                           r = b - A x in float64; MG_REFINE_FF keeps it as
+                           float-float pairs (hi + lo float32, about 48
+                           significant bits) and forms r with error-free
+                           float32 products (faster where float64 is slow).  */
 } mg_options;
 
 enum { MG_CYCLE_V = 0, MG_CYCLE_SAWTOOTH = 1 };
+enum { MG_REFINE_FP64 = 0, MG_REFINE_FF = 1 };
 
 typedef struct {
   int status;           /* mg_status of the solve                             */
@@ -149,8 +158,8 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3],
 
 /*
  * mg_solve: solve A_h x = b until ||b - A_h x||_2 <= rel_tol * ||b||_2.  The
- * iterate is kept in float-float (pairs of floats, about 48 significant
- * bits) and the refinement residual is evaluated in that precision.
+ * iterate is kept in float64 and the refinement residual is evaluated in
+ * float64 (or both in float-float with opt->refine = MG_REFINE_FF).
  *   d_b   device float32 right-hand side (values on solid cells ignored),
  *         16-byte aligned.
  *   d_x   device float32, 16-byte aligned: initial guess on entry, solution

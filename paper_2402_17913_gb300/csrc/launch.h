@@ -108,10 +108,12 @@ cudaError_t launch_xr_update(const LevelDev& L, const void* p, const void* Ap, v
 // x: float-float iterate (float2 per cell); w: operator weights c / h_a^2.
 // dyn: xin / xout are the two buffers and the state's `cur` picks the one
 // holding the iterate (flipped after an update).
+// f64: the iterate is a float64 array and the residual is formed in
+// float64 (T must then be float); otherwise float-float pairs.
 template <int DIM, typename T, bool MASKED, bool UPDATE>
 cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
                          const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s,
-                         int dyn = 0);
+                         int dyn = 0, bool f64 = false);
 // Conditional values of the device-side solve loop (see mg_cg.cu).
 cudaError_t launch_loop_start(cudaGraphConditionalHandle outer, SolveState* st, cudaStream_t s);
 cudaError_t launch_loop_inner(cudaGraphConditionalHandle inner, SolveState* st, unsigned int cap, int body,
@@ -123,10 +125,12 @@ struct SolveParams {
   double tol, inner_floor;
   int max_inner, max_outer, krylov, n_fluid;
 };
+// f64: the iterate x is a float64 array (else float-float pairs).
 cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, void* x, double c, SolveParams prm,
-                        SolveState* st, double* partials, cudaStream_t s);
-cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s);
-cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s);
+                        SolveState* st, double* partials, cudaStream_t s, bool f64);
+cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s,
+                          bool f64);
+cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s, bool f64);
 
 // set-up kernels
 cudaError_t launch_coarsen_solid(int dim, const int64_t fine[3], const uint8_t* sf, uint8_t* sc, cudaStream_t s);

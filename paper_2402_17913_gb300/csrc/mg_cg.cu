@@ -566,6 +566,100 @@ __global__ void __launch_bounds__(256) k_outer(LevelDev L, OuterArgs oa, const f
   }
 }
 
+// Refinement step in float64: the iterate x is a float64 array.  With
+// UPDATE, k_update64 first writes x + sigma d' (float64) into the other
+// buffer; k_outer64 then forms, in the scaled units of the inner solve,
+// r = c b - A' x in float64 from the (updated) iterate, reduces ||r|| in
+// float64 and writes r' = r / sigma_new rounded to float32.  The last block
+// decides as in the float-float form (outer_decide).  The update is its own
+// pass so that every cell is updated once (not once per neighbour that
+// reads it): GB300's float64 rate is 1/64 of its float32 rate.
+__global__ void __launch_bounds__(256) k_update64(size_t n, const uint8_t* __restrict__ cell, double* xa,
+                                                  double* xb, int dyn, const float* __restrict__ dprime,
+                                                  const SolveState* __restrict__ st) {
+  const bool swap = dyn && st->cur;
+  const double* __restrict__ xin = swap ? xb : xa;
+  double* __restrict__ xout = swap ? xa : xb;
+  const double sig = st->sigma;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const bool fl = cell == nullptr || cell[i] != 0;
+    xout[i] = fl ? fma(sig, (double)dprime[i], xin[i]) : 0.0;
+  }
+}
+
+template <int DIM, bool MASKED, bool UPDATE>
+__global__ void __launch_bounds__(256) k_outer64(LevelDev L, double w0, double w1, double w2, double c, double c2,
+                                                 const float* __restrict__ b, double* xa, double* xb, int dyn,
+                                                 float* __restrict__ rprime, SolveState* __restrict__ st,
+                                                 double* __restrict__ partials) {
+  // the iterate: the buffer the update wrote (UPDATE), else the current one
+  const bool swap = dyn && st->cur;
+  const double* __restrict__ x = (swap != UPDATE) ? xb : xa;
+  const double sig_old = st->sigma;
+  double sig_new = sig_old;
+  if (UPDATE) sig_new = pow2_floor(sig_old * sqrt(fmax(st->rnorm2, 1e-300) / (double)st->n_fluid));
+  const float inv_sig_new = (float)(1.0 / sig_new);
+  double acc = 0.0;
+  for (RowIter it(L); it.more(); it.next(L)) {
+    if (!it.active) continue;
+    const int x0 = it.x0, y = it.y, zz = it.z;
+    const Nbr n = neighbours<DIM>(L, x0, y, zz);
+    const bool vec = (L.nx & 3) == 0;
+    double xc[6], yu[4], yd[4], zb[4], zf[4];  // xc: x0-1 .. x0+4
+    xc[0] = n.hl ? x[n.il] : 0.0;
+    xc[5] = n.hr ? x[n.ir] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = vec || x0 + k < L.nx;
+      xc[k + 1] = ok ? x[n.i + k] : 0.0;
+      yu[k] = ok && n.hu ? x[n.iu + k] : 0.0;
+      yd[k] = ok && n.hd ? x[n.id + k] : 0.0;
+      if (DIM == 3) {
+        zb[k] = ok && n.hb ? x[n.ib + k] : 0.0;
+        zf[k] = ok && n.hf ? x[n.iF + k] : 0.0;
+      }
+    }
+    float bv[4];
+    ld4(b, n.i, x0, L.nx, bv);
+    uint8_t m[4];
+    cells4<MASKED>(L, n.i, x0, m);
+    float rv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      rv[k] = 0.f;
+      if (!m[k]) continue;
+      int kx, ky, kz = 0;
+      if (MASKED) {
+        kx = m[k] & 3;
+        ky = (m[k] >> 2) & 3;
+        kz = (m[k] >> 4) & 3;
+      } else {
+        kx = axis_count(x0 + k, L.nx, L.bcD, 0);
+        ky = axis_count(y, L.ny, L.bcD, 2);
+        if (DIM == 3) kz = axis_count(zz, L.nz, L.bcD, 4);
+      }
+      // A' x = d x_c - sum_a w_a (x_minus + x_plus), d = sum_a w_a k_a; a
+      // missing link or solid neighbour holds 0
+      double d = w0 * kx + w1 * ky;
+      if (DIM == 3) d += w2 * kz;
+      double s = w0 * (xc[k] + xc[k + 2]);
+      s = fma(w1, yu[k] + yd[k], s);
+      if (DIM == 3) s = fma(w2, zb[k] + zf[k], s);
+      const double r = fma(c, (double)bv[k], s - d * xc[k + 1]);
+      rv[k] = (float)r * inv_sig_new;
+      acc = fma(r, r, acc);
+    }
+    st4(rprime, n.i, x0, L.nx, rv);
+  }
+  double tot;
+  if (grid_sum_last(acc, partials, &st->counter[kCntOuter], &tot)) {
+    if (threadIdx.x == 0) {
+      outer_decide(st, tot, c2, sig_new, UPDATE);
+      if (UPDATE && dyn) st->cur ^= 1;
+    }
+  }
+}
+
 static OuterArgs outer_args(const double w[3], double c) {
   OuterArgs a;
   for (int k = 0; k < 3; ++k) {
@@ -580,7 +674,20 @@ static OuterArgs outer_args(const double w[3], double c) {
 
 template <int DIM, typename T, bool MASKED, bool UPDATE>
 cudaError_t launch_outer(const LevelDev& L, const double w[3], double c, const float* b, const void* xin, void* xout,
-                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s, int dyn) {
+                         const void* dprime, void* rprime, SolveState* st, double* partials, cudaStream_t s, int dyn,
+                         bool f64) {
+  if (f64) {
+    if (UPDATE) {
+      const size_t n = (size_t)L.nx * L.ny * L.nz;
+      const size_t want = (n + 255) / 256, cap = (size_t)sm_count() * 8;
+      k_update64<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(n, MASKED ? L.cell : nullptr,
+                                                                     (double*)xin, (double*)xout, dyn,
+                                                                     (const float*)dprime, st);
+    }
+    k_outer64<DIM, MASKED, UPDATE><<<row_grid(L), 256, 0, s>>>(L, w[0], w[1], w[2], c, c * c, b, (double*)xin,
+                                                               (double*)xout, dyn, (float*)rprime, st, partials);
+    return cudaGetLastError();
+  }
   k_outer<DIM, T, MASKED, UPDATE><<<row_grid(L), 256, 0, s>>>(L, outer_args(w, c), b, (float2*)xin, (float2*)xout,
                                                               dyn, (const T*)dprime, (T*)rprime, st, partials);
   return cudaGetLastError();
@@ -633,10 +740,10 @@ cudaError_t launch_loop_set_cur(SolveState* st, int cur, cudaStream_t s) {
                                                   SolveState*, double*, cudaStream_t);                           \
   template cudaError_t launch_outer<DIM, T, M, false>(const LevelDev&, const double*, double, const float*,     \
                                                       const void*, void*, const void*, void*, SolveState*,       \
-                                                      double*, cudaStream_t, int);                               \
+                                                      double*, cudaStream_t, int, bool);                         \
   template cudaError_t launch_outer<DIM, T, M, true>(const LevelDev&, const double*, double, const float*,      \
                                                      const void*, void*, const void*, void*, SolveState*,        \
-                                                     double*, cudaStream_t, int);
+                                                     double*, cudaStream_t, int, bool);
 
 NPMG_INST_VEC(2, float, false)
 NPMG_INST_VEC(2, float, true)
@@ -660,9 +767,12 @@ template cudaError_t launch_xr_update<__nv_bfloat16>(const LevelDev&, const void
 
 // ---------------------------------------------------------------------------
 // Solve start: x = (guess, 0) on fluid cells; ||b||^2; reset the state.
+template <bool F64>
 __global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restrict__ b, const float* __restrict__ xg,
-                                              float2* __restrict__ x, double c, SolveParams prm,
+                                              void* __restrict__ xv_, double c, SolveParams prm,
                                               SolveState* __restrict__ st, double* __restrict__ partials) {
+  float2* x = (float2*)xv_;
+  double* x64 = (double*)xv_;
 
   float acc = 0.f;
   const size_t sxy = (size_t)L.nx * L.ny;
@@ -681,7 +791,8 @@ __global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restric
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (x0 + k >= L.nx) continue;
-        x[i + k] = make_float2(m[k] ? xv[k] : 0.f, 0.f);
+        if (F64) x64[i + k] = m[k] ? (double)xv[k] : 0.0;
+        else x[i + k] = make_float2(m[k] ? xv[k] : 0.f, 0.f);
         if (m[k]) acc = fmaf(bv[k], bv[k], acc);
       }
     }
@@ -693,20 +804,28 @@ __global__ void __launch_bounds__(256) k_init(LevelDev L, const float* __restric
 }
 
 cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, void* x, double c, SolveParams prm,
-                        SolveState* st, double* partials, cudaStream_t s) {
-  k_init<<<row_grid(L), 256, 0, s>>>(L, b, xguess, (float2*)x, c, prm, st, partials);
+                        SolveState* st, double* partials, cudaStream_t s, bool f64) {
+  if (f64) k_init<true><<<row_grid(L), 256, 0, s>>>(L, b, xguess, x, c, prm, st, partials);
+  else k_init<false><<<row_grid(L), 256, 0, s>>>(L, b, xguess, x, c, prm, st, partials);
   return cudaGetLastError();
 }
 
-// Solve end: the float32 output is hi (hi + lo rounded); a zero right-hand
-// side has the zero solution.
-__global__ void k_finish(size_t n, float2* __restrict__ x, float* __restrict__ out,
+// Solve end: the float32 output is the iterate rounded once (float-float:
+// hi + lo; float64: the value); a zero right-hand side has the zero
+// solution.
+template <bool F64>
+__global__ void k_finish(size_t n, void* __restrict__ xv_, float* __restrict__ out,
                          const SolveState* __restrict__ st) {
+  float2* x = (float2*)xv_;
+  double* x64 = (double*)xv_;
   const bool zero = st->bnorm2 == 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (zero) {
-      x[i] = make_float2(0.f, 0.f);
+      if (F64) x64[i] = 0.0;
+      else x[i] = make_float2(0.f, 0.f);
       out[i] = 0.f;
+    } else if (F64) {
+      out[i] = (float)x64[i];
     } else {
       const float2 v = x[i];
       out[i] = v.x + v.y;
@@ -714,21 +833,29 @@ __global__ void k_finish(size_t n, float2* __restrict__ x, float* __restrict__ o
   }
 }
 
-cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s) {
-  k_finish<<<nblocks, 256, 0, s>>>(n, (float2*)x, out, st);
+cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s,
+                          bool f64) {
+  if (f64) k_finish<true><<<nblocks, 256, 0, s>>>(n, x, out, st);
+  else k_finish<false><<<nblocks, 256, 0, s>>>(n, x, out, st);
   return cudaGetLastError();
 }
 
-// The float64 value of the iterate: (double)hi + (double)lo.
-__global__ void k_ff_to_f64(size_t n, const float2* __restrict__ x, double* __restrict__ out) {
+// The float64 value of the iterate: (double)hi + (double)lo, or a copy.
+template <bool F64>
+__global__ void k_ff_to_f64(size_t n, const void* __restrict__ xv_, double* __restrict__ out) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float2 v = x[i];
-    out[i] = (double)v.x + (double)v.y;
+    if (F64) {
+      out[i] = ((const double*)xv_)[i];
+    } else {
+      const float2 v = ((const float2*)xv_)[i];
+      out[i] = (double)v.x + (double)v.y;
+    }
   }
 }
 
-cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s) {
-  k_ff_to_f64<<<nblocks, 256, 0, s>>>(n, (const float2*)x, out);
+cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s, bool f64) {
+  if (f64) k_ff_to_f64<true><<<nblocks, 256, 0, s>>>(n, x, out);
+  else k_ff_to_f64<false><<<nblocks, 256, 0, s>>>(n, x, out);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ struct mg_handle_s {
   void* yk[npmg::kMaxLevels];
   void* bk[npmg::kMaxLevels];
   void *r, *z, *p[2], *Ap, *d;
-  void* xff[2];    // float-float iterate (hi, lo) per cell, double-buffered
+  void* xff[2];    // refinement iterate per cell (float64, or float-float hi/lo pairs), double-buffered
   int cur64;
   double* inv;
   float* cimage;   // constant shared-memory image of the single-block kernel
@@ -61,6 +61,10 @@ struct mg_handle_s {
   bool s3_ok[npmg::kMaxLevels];   // 3D levels on the z-streaming kernels
   bool s2_ok[npmg::kMaxLevels];   // 2D levels on the y-streaming warp kernels
   bool r3_ok[npmg::kMaxLevels];   // 3D levels on the row-warp z-streaming kernels
+  npmg::Tma3Maps t3maps[npmg::kMaxLevels];  // tensor maps of the TMA-fed 3D kernels (levels < kc)
+  bool t3_ok[npmg::kMaxLevels];   // 3D levels on the TMA-fed z-streaming kernels
+  npmg::Tma3CgMaps t3cg;          // the finest level's CG direction update on the TMA-fed kernel
+  bool t3cg_ok;
   int64_t chunk_kernels;   // kernels in one graph launch
   // instrumentation
   int64_t launches;

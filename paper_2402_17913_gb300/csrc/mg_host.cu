@@ -1,6 +1,7 @@
 // C ABI of the multigrid solver: create / solve / destroy and the
 // per-kernel building blocks.  Host code only orchestrates: every arithmetic
 // step of a solve runs in the library's kernels.
+#include <initializer_list>
 #include <stdarg.h>
 #include <stdlib.h>
 #include <string.h>
@@ -59,6 +60,10 @@ cudaError_t prof_flush(mg_handle_s* h) {
   return cudaSuccess;
 }
 
+// The refinement iterate and residual in float64 (MG_REFINE_FP64, the
+// default) or in float-float pairs (MG_REFINE_FF); 8 bytes per cell either way.
+static bool f64_iterate(const mg_handle_s* h) { return h->opt.refine != MG_REFINE_FF; }
+
 int default_blocks_1d(const mg_handle_s* h, size_t n) {
   size_t b = (n + 255) / 256;
   const size_t cap = (size_t)h->nsm * 8;
@@ -94,8 +99,8 @@ static cudaError_t dispatch(const mg_handle_s* h, F&& f) {
 // finest level, whose b and z are CG vectors; T elsewhere).  `tma` selects
 // the TMA tile kernels (only for TB == T).
 template <int DIM, typename T, bool M, typename TB>
-static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevelMaps* tm, SolveState* st,
-                            cudaStream_t s) {
+static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevelMaps* tm, const Tma3Maps* t3,
+                            SolveState* st, cudaStream_t s) {
   const float om = (float)h->opt.omega;
   // the sawtooth down leg (no sweeps: x = b / d, the restriction of b) is
   // a plain stream; pre = -1 asks the tile kernel for it when b is not
@@ -109,6 +114,7 @@ static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevel
   if constexpr (std::is_same<T, TB>::value) {
     if (tm) return launch_down_tma<T, M>(*tm, h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
   }
+  if (DIM == 3 && t3) return launch_down_t3<T, M, TB>(*t3, h->lv[k], h->xk[k], h->bk[k + 1], om, st, s);
   if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
     return launch_down_r3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
   if (DIM == 3 && h->s3_ok[k]) return launch_down_s3<T, M, TB>(h->lv[k], b, h->xk[k], h->bk[k + 1], om, st, s);
@@ -116,14 +122,15 @@ static cudaError_t down_leg(mg_handle_s* h, int k, const void* b, const TmaLevel
 }
 
 template <int DIM, typename T, bool M, bool F, typename TB>
-static cudaError_t up_leg(mg_handle_s* h, int k, const void* b, void* xo, const TmaLevelMaps* tm, SolveState* st,
-                          cudaStream_t s) {
+static cudaError_t up_leg(mg_handle_s* h, int k, const void* b, void* xo, const TmaLevelMaps* tm,
+                          const Tma3Maps* t3, SolveState* st, cudaStream_t s) {
   const float om = (float)h->opt.omega, sc = (float)h->opt.coarse_scale;
   if (DIM == 2 && h->s2_ok[k] && stream2d_aligned(b))
     return launch_up_w<T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
   if constexpr (std::is_same<T, TB>::value) {
     if (tm) return launch_up_tma<T, M, F>(*tm, h->lv[k], xo, om, sc, st, h->partials, s);
   }
+  if (DIM == 3 && t3) return launch_up_t3<T, M, F, TB>(*t3, h->lv[k], xo, om, sc, st, h->partials, s);
   if (DIM == 3 && h->r3_ok[k] && stream2d_aligned(b))
     return launch_up_r3<T, M, F, TB>(h->lv[k], b, h->xk[k], xo, h->yk[k + 1], om, sc, st, h->partials, s);
   if (DIM == 3 && h->s3_ok[k])
@@ -150,12 +157,22 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     m0 = h->tmaps[0];
     if (r != h->r) tma0 = tma_encode_b<float>(&m0.b, h->lv[0], r);
   }
+  Tma3Maps t30;
+  bool t3ok0 = h->t3_ok[0];
+  if (t3ok0) {
+    t30 = h->t3maps[0];
+    if (r != h->r) t3ok0 = tma3d_encode_b<float>(&t30.b, h->lv[0], r);
+  }
+  auto t3of = [&](int k) -> const Tma3Maps* {
+    if (k == 0) return t3ok0 ? &t30 : nullptr;
+    return h->t3_ok[k] ? &h->t3maps[k] : nullptr;
+  };
   for (int k = 0; k < h->kc; ++k) {
     LaunchScope ls(h, k == 0 ? MG_K_DOWN_FINE : MG_K_DOWN, s);
     if (k == 0)
-      e = down_leg<DIM, T, M, float>(h, 0, r, tma0 ? &m0 : nullptr, st, s);
+      e = down_leg<DIM, T, M, float>(h, 0, r, tma0 ? &m0 : nullptr, t3of(0), st, s);
     else
-      e = down_leg<DIM, T, M, T>(h, k, h->bk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, st, s);
+      e = down_leg<DIM, T, M, T>(h, k, h->bk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, t3of(k), st, s);
     if (e != cudaSuccess) return e;
   }
   CoarseArgs ca = h->ca;
@@ -169,11 +186,12 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
   for (int k = h->kc - 1; k >= 0; --k) {
     LaunchScope ls(h, k == 0 ? MG_K_UP_FINE : MG_K_UP, s);
     if (k == 0 && st)
-      e = up_leg<DIM, T, M, true, float>(h, 0, r, z, tma0 ? &m0 : nullptr, st, s);
+      e = up_leg<DIM, T, M, true, float>(h, 0, r, z, tma0 ? &m0 : nullptr, t3of(0), st, s);
     else if (k == 0)
-      e = up_leg<DIM, T, M, false, float>(h, 0, r, z, tma0 ? &m0 : nullptr, st, s);
+      e = up_leg<DIM, T, M, false, float>(h, 0, r, z, tma0 ? &m0 : nullptr, t3of(0), st, s);
     else
-      e = up_leg<DIM, T, M, false, T>(h, k, h->bk[k], h->yk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, st, s);
+      e = up_leg<DIM, T, M, false, T>(h, k, h->bk[k], h->yk[k], h->tma_ok[k] ? &h->tmaps[k] : nullptr, t3of(k),
+                                      st, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -187,7 +205,12 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(h, MG_K_P_UPDATE, s);
-    e = launch_p_update<DIM, float, M>(h->lv[0], h->z, h->p[parity], h->p[1 - parity], h->Ap, h->st, h->partials, s);
+    if (DIM == 3 && h->t3cg_ok)
+      e = launch_p_update_t3<M>(h->t3cg, parity, h->lv[0], (float*)h->p[1 - parity], (float*)h->Ap, h->st,
+                                h->partials, s);
+    else
+      e = launch_p_update<DIM, float, M>(h->lv[0], h->z, h->p[parity], h->p[1 - parity], h->Ap, h->st, h->partials,
+                                         s);
   }
   if (e != cudaSuccess) return e;
   LaunchScope ls(h, MG_K_XR_UPDATE, s);
@@ -226,9 +249,12 @@ static cudaError_t enqueue_outer(mg_handle_s* h, const float* b, bool update, cu
     const void* xin = h->xff[h->cur64];
     void* xout = h->xff[1 - h->cur64];
     LaunchScope ls(h, MG_K_OUTER, s);
+    if (update && f64_iterate(h)) h->launches += 1;  // the float64 update pass
     if (update)
-      return launch_outer<DIM, float, M, true>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
-    return launch_outer<DIM, float, M, false>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s);
+      return launch_outer<DIM, float, M, true>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s,
+                                               0, f64_iterate(h));
+    return launch_outer<DIM, float, M, false>(h->lv[0], h->w0, h->c, b, xin, xout, h->d, h->r, h->st, h->partials, s,
+                                              0, f64_iterate(h));
   });
 }
 
@@ -325,7 +351,7 @@ static cudaError_t build_loop_graph(mg_handle_s* h) {
         constexpr int DIM = decltype(dimc)::value;
         constexpr bool M = decltype(mc)::value;
         return launch_outer<DIM, float, M, true>(h->lv[0], h->w0, h->c, h->bsave, h->xff[0], h->xff[1], h->d, h->r,
-                                                 h->st, h->partials, cs, 1);
+                                                 h->st, h->partials, cs, 1, f64_iterate(h));
       });
     if (e2 == cudaSuccess) e2 = launch_loop_outer(ho, h->st, cap_out, cs);
     e = cudaStreamEndCapture(cs, &tmp);
@@ -362,7 +388,7 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
   NPMG_CUDA(cudaEventRecord(h->ev0, s));
   {
     LaunchScope ls(h, MG_K_INIT_FINISH, s);
-    NPMG_CUDA(launch_init(h->lv[0], b, x, h->xff[h->cur64], h->c, prm, h->st, h->partials, s));
+    NPMG_CUDA(launch_init(h->lv[0], b, x, h->xff[h->cur64], h->c, prm, h->st, h->partials, s, f64_iterate(h)));
   }
   NPMG_CUDA(enqueue_outer(h, b, false, s));
   NPMG_CUDA(read_state(h, s));
@@ -372,7 +398,8 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     // the guess is worse than zero: the plain solve from x = 0 takes over
     {
       LaunchScope ls(h, MG_K_INIT_FINISH, s);
-      NPMG_CUDA(launch_init(h->lv[0], b, nullptr, h->xff[h->cur64], h->c, prm, h->st, h->partials, s));
+      NPMG_CUDA(launch_init(h->lv[0], b, nullptr, h->xff[h->cur64], h->c, prm, h->st, h->partials, s,
+                            f64_iterate(h)));
     }
     NPMG_CUDA(enqueue_outer(h, b, false, s));
     NPMG_CUDA(read_state(h, s));
@@ -391,7 +418,11 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     NPMG_CUDA(cudaGraphLaunch(h->loop_exec, s));
     NPMG_CUDA(read_state(h, s));
     h->cur64 = h->st_host->cur;
-    h->launches += 2 + 3 * (int64_t)h->st_host->loop_outer + (h->loop_kernels + 1) * (int64_t)h->st_host->loop_bodies;
+    // per outer body: the inner condition, the refinement step (two kernels
+    // with the float64 iterate: update and residual) and the outer condition
+    const int64_t per_outer = f64_iterate(h) ? 4 : 3;
+    h->launches += 2 + per_outer * (int64_t)h->st_host->loop_outer +
+                   (h->loop_kernels + 1) * (int64_t)h->st_host->loop_bodies;
   }
   int guard = 0;
   while (!h->st_host->outer_done && guard < 4 * (o.max_outer + 1)) {
@@ -414,7 +445,7 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
   }
   {
     LaunchScope ls(h, MG_K_INIT_FINISH, s);
-    NPMG_CUDA(launch_finish(h->ncell[0], h->xff[h->cur64], x, h->st, h->nb1d, s));
+    NPMG_CUDA(launch_finish(h->ncell[0], h->xff[h->cur64], x, h->st, h->nb1d, s, f64_iterate(h)));
   }
   NPMG_CUDA(cudaEventRecord(h->ev1, s));
   NPMG_CUDA(read_state(h, s));
@@ -462,6 +493,7 @@ void mg_default_options(mg_options* o) {
   o->prec = MG_FP32;
   o->inner_floor = 0.0;
   o->cycle = MG_CYCLE_V;
+  o->refine = MG_REFINE_FP64;
 }
 
 mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const double spacing[3], const int bc[6],
@@ -488,9 +520,10 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
   }
   if (!(o.omega > 0.0 && o.omega <= 2.0) || !(o.coarse_scale > 0.0) || o.max_inner < 1 || o.max_outer < 1 ||
       o.prec < MG_FP32 || o.prec > MG_MIXED_BF16 || o.levels < 0 || o.levels > kMaxLevels ||
-      (o.cycle != MG_CYCLE_V && o.cycle != MG_CYCLE_SAWTOOTH)) {
+      (o.cycle != MG_CYCLE_V && o.cycle != MG_CYCLE_SAWTOOTH) ||
+      (o.refine != MG_REFINE_FP64 && o.refine != MG_REFINE_FF)) {
     set_error("mg_create: invalid options (omega in (0,2], coarse_scale > 0, max_inner/max_outer >= 1, "
-              "levels in [0,%d], cycle V or sawtooth)", kMaxLevels);
+              "levels in [0,%d], cycle V or sawtooth, refine FP64 or FF)", kMaxLevels);
     return MG_ERR_INVALID;
   }
   int64_t n0[3] = {shape[0], shape[1], dim == 3 ? shape[2] : 1};
@@ -715,6 +748,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     if (e == cudaSuccess && DIM == 2) e = prepare_tma_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_s3_kernels<T, M>();
     if (e == cudaSuccess && DIM == 3) e = prepare_r3_kernels<T, M>();
+    if (e == cudaSuccess && DIM == 3) e = prepare_t3_kernels<T, M>();
     // the fused kernels serve both legs of the V cycle and the up leg of
     // the sawtooth (whose up leg is the V cycle's: x, here b / d from the
     // down leg, plus the scaled correction, then the post sweeps); their
@@ -734,6 +768,18 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
                      tma_encode_level<T>(&h->tmaps[k], h->lv[k], k == 0 ? h->r : h->bk[k], h->xk[k],
                                          h->yk[k + 1]);
     }
+    // tensor maps of the TMA-fed 3D kernels (two sweeps); level 0 reads the
+    // float32 CG residual r
+    for (int k = 0; k < h->kc && e == cudaSuccess; ++k) {
+      h->t3_ok[k] = DIM == 3 && tma3d_eligible(dim, pre_e, o.post, h->lv[k]) &&
+                    (k == 0 ? tma3d_encode<T, float>(&h->t3maps[0], h->lv[0], h->r, h->xk[0], h->yk[1])
+                            : tma3d_encode<T, T>(&h->t3maps[k], h->lv[k], h->bk[k], h->xk[k], h->yk[k + 1]));
+    }
+    // the finest level's CG direction update on the TMA-fed kernel where
+    // the level's legs are (NPMG_NO_TMA3D_CG keeps the marching kernel)
+    h->t3cg_ok = DIM == 3 && h->kc > 0 && h->t3_ok[0] && getenv("NPMG_NO_TMA3D_CG") == nullptr &&
+                 tma3d_encode_cg(&h->t3cg, h->lv[0], (const float*)h->z, (const float*)h->p[0],
+                                 (const float*)h->p[1]);
     return e;
   }));
   NPMG_TRY(cudaStreamSynchronize(s));
@@ -767,7 +813,8 @@ mg_status mg_get_solution_f64(mg_handle h, double* d_x64, void* stream) {
     set_error("mg_get_solution_f64: NULL argument");
     return MG_ERR_INVALID;
   }
-  const cudaError_t e = launch_ff_to_f64(h->ncell[0], h->xff[h->cur64], d_x64, h->nb1d, (cudaStream_t)stream);
+  const cudaError_t e =
+      launch_ff_to_f64(h->ncell[0], h->xff[h->cur64], d_x64, h->nb1d, (cudaStream_t)stream, f64_iterate(h));
   if (e != cudaSuccess) {
     set_error("mg_get_solution_f64: %s", cudaGetErrorString(e));
     return MG_ERR_CUDA;
@@ -786,12 +833,29 @@ mg_status mg_level_shape(mg_handle h, int k, int64_t shape_out[3]) {
   return MG_OK;
 }
 
-static mg_status check_bb(mg_handle h, int k, bool need_coarse, const char* who) {
+// Caller arrays of the building blocks: non-NULL and 16-byte aligned (the
+// level kernels and the coarse block move them as float4 vectors).
+static mg_status check_arrays(const char* who, std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs) {
+    if (!p) {
+      set_error("%s: NULL array", who);
+      return MG_ERR_INVALID;
+    }
+    if ((uintptr_t)p & 15) {
+      set_error("%s: arrays must be 16-byte aligned", who);
+      return MG_ERR_INVALID;
+    }
+  }
+  return MG_OK;
+}
+
+static mg_status check_bb(mg_handle h, int k, bool need_coarse, const char* who,
+                          std::initializer_list<const void*> ptrs) {
   if (!h || k < 0 || k >= h->L || (need_coarse && k >= h->L - 1)) {
     set_error("%s: bad handle or level %d", who, k);
     return MG_ERR_INVALID;
   }
-  return MG_OK;
+  return check_arrays(who, ptrs);
 }
 
 #define NPMG_BB(EXPR)                                                              \
@@ -806,7 +870,7 @@ static mg_status check_bb(mg_handle h, int k, bool need_coarse, const char* who)
   } while (0)
 
 mg_status mg_apply_operator(mg_handle h, int k, const float* d_x, float* d_y, void* stream) {
-  if (check_bb(h, k, false, "mg_apply_operator") != MG_OK || !d_x || !d_y) return MG_ERR_INVALID;
+  if (check_bb(h, k, false, "mg_apply_operator", {d_x, d_y}) != MG_OK) return MG_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
 #define E(D, M) launch_apply<D, M>(h->lv[k], d_x, d_y, s)
   NPMG_BB(E);
@@ -815,7 +879,11 @@ mg_status mg_apply_operator(mg_handle h, int k, const float* d_x, float* d_y, vo
 }
 
 mg_status mg_smooth(mg_handle h, int k, float* d_x, const float* d_b, int sweeps, void* stream) {
-  if (check_bb(h, k, false, "mg_smooth") != MG_OK || !d_x || !d_b || sweeps < 0) return MG_ERR_INVALID;
+  if (check_bb(h, k, false, "mg_smooth", {d_x, d_b}) != MG_OK) return MG_ERR_INVALID;
+  if (sweeps < 0) {
+    set_error("mg_smooth: sweeps must be >= 0");
+    return MG_ERR_INVALID;
+  }
   if (sweeps == 0) return MG_OK;
   if (h->opt.prec != MG_FP32) {
     set_error("mg_smooth: building blocks need a float32 handle");
@@ -836,7 +904,7 @@ mg_status mg_smooth(mg_handle h, int k, float* d_x, const float* d_b, int sweeps
 }
 
 mg_status mg_residual_restrict(mg_handle h, int k, const float* d_x, const float* d_b, float* d_bc, void* stream) {
-  if (check_bb(h, k, true, "mg_residual_restrict") != MG_OK || !d_x || !d_b || !d_bc) return MG_ERR_INVALID;
+  if (check_bb(h, k, true, "mg_residual_restrict", {d_x, d_b, d_bc}) != MG_OK) return MG_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
 #define E(D, M) launch_restrict_residual<D, M>(h->lv[k], d_x, d_b, d_bc, s)
   NPMG_BB(E);
@@ -845,7 +913,7 @@ mg_status mg_residual_restrict(mg_handle h, int k, const float* d_x, const float
 }
 
 mg_status mg_prolong_correct(mg_handle h, int k, const float* d_e, float* d_x, void* stream) {
-  if (check_bb(h, k, true, "mg_prolong_correct") != MG_OK || !d_e || !d_x) return MG_ERR_INVALID;
+  if (check_bb(h, k, true, "mg_prolong_correct", {d_e, d_x}) != MG_OK) return MG_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
 #define E(D, M) launch_prolong_correct<D, M>(h->lv[k], d_e, d_x, (float)h->opt.coarse_scale, s)
   NPMG_BB(E);
@@ -854,10 +922,11 @@ mg_status mg_prolong_correct(mg_handle h, int k, const float* d_e, float* d_x, v
 }
 
 mg_status mg_precondition(mg_handle h, const float* d_r, float* d_z, void* stream) {
-  if (!h || !d_r || !d_z) {
-    set_error("mg_precondition: NULL argument");
+  if (!h) {
+    set_error("mg_precondition: NULL handle");
     return MG_ERR_INVALID;
   }
+  if (check_arrays("mg_precondition", {d_r, d_z}) != MG_OK) return MG_ERR_INVALID;
   if (h->opt.prec != MG_FP32) {
     set_error("mg_precondition: building blocks need a float32 handle");
     return MG_ERR_INVALID;

@@ -31,4 +31,34 @@ cudaError_t launch_up_tma(const TmaLevelMaps& m, const LevelDev& L, void* xout, 
 template <typename T, bool MASKED>
 cudaError_t prepare_tma_kernels();
 
+// Tensor maps of one 3D level for the TMA-fed z-streaming kernels
+// (mg_tma3d.cu): b, the up leg's x, the coarse correction e, the cell bytes.
+struct Tma3Maps {
+  CUtensorMap x, b, e, m;
+};
+
+bool tma3d_eligible(int dim, int pre, int post, const LevelDev& L);
+template <typename T, typename TB>
+bool tma3d_encode(Tma3Maps* out, const LevelDev& L, const void* b, const void* x, const void* e);
+template <typename TB>
+bool tma3d_encode_b(CUtensorMap* out, const LevelDev& L, const void* b);
+template <typename T, bool MASKED, typename TB>
+cudaError_t launch_down_t3(const Tma3Maps& m, const LevelDev& L, void* x, void* bcoarse, float omega,
+                           const SolveState* st, cudaStream_t s);
+template <typename T, bool MASKED, bool FINEST, typename TB>
+cudaError_t launch_up_t3(const Tma3Maps& m, const LevelDev& L, void* xout, float omega, float sc, SolveState* st,
+                         double* partials, cudaStream_t s);
+template <typename T, bool MASKED>
+cudaError_t prepare_t3_kernels();
+
+// Tensor maps of the finest level's CG direction update (float32): z, the
+// two p buffers, the cell bytes.
+struct Tma3CgMaps {
+  CUtensorMap z, p[2], m;
+};
+bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const float* p0, const float* p1);
+template <bool MASKED>
+cudaError_t launch_p_update_t3(const Tma3CgMaps& m, int parity, const LevelDev& L, float* pnew, float* Ap,
+                               SolveState* st, double* partials, cudaStream_t s);
+
 }  // namespace npmg

@@ -15,6 +15,7 @@ MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_NOT_CONVERGED, MG_DIVERGED, M
 MG_BC_DIRICHLET, MG_BC_NEUMANN = 0, 1
 MG_FP32, MG_MIXED_FP16, MG_MIXED_BF16 = 0, 1, 2
 MG_CYCLE_V, MG_CYCLE_SAWTOOTH = 0, 1
+MG_REFINE_FP64, MG_REFINE_FF = 0, 1
 NS_STENCIL_FD, NS_STENCIL_FE = 0, 1
 AD_UPWIND, AD_CENTRAL = 0, 1
 AD_COARSE_REDISCRETISE, AD_COARSE_GALERKIN = 0, 1
@@ -48,7 +49,7 @@ class MgOptions(ctypes.Structure):
     _fields_ = [("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_scale", ctypes.c_double), ("levels", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner_floor", ctypes.c_double), ("cycle", ctypes.c_int)]
+                ("inner_floor", ctypes.c_double), ("cycle", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 class MgStats(ctypes.Structure):

@@ -3,6 +3,8 @@ the C ABI.  Tolerances: single float32 kernels are compared elementwise to
 ~1e-5 of the field's scale (a few float32 ulps times the stencil growth);
 whole solves must reach relres <= 1e-6 (float64 iterate, checked here with
 the oracle's operator) and relative L2 error <= 1e-5 against x*."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -168,12 +170,41 @@ def test_streaming_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
     monkeypatch.setenv("NPMG_STREAM2D_MIN", "0")
     monkeypatch.setenv("NPMG_ROWS3D_MIN", "0")
     monkeypatch.setenv("NPMG_ROWS3D_SPLIT", "2")
+    monkeypatch.setenv("NPMG_NO_TMA3D", "1")  # the row-warp kernels, not the TMA-fed ones
     test_one_cycle_matches_oracle(L, shape, bc, frac)
     test_sawtooth_cycle_matches_oracle(L, shape, bc, frac)
     solid, h = make_case(shape, bc, frac)
     b = I.blob_rhs(shape, 2, solid=solid).astype(np.float32)
     solve_and_check(L, shape, bc, solid, h, b)
     solve_and_check(L, shape, bc, solid, h, b, prec=1)
+
+
+T3_CASES = [
+    ((32, 32, 32), (0,) * 6, 0.0),
+    ((16, 24, 144), (1, 0, 1, 1, 0, 1), 0.06),   # a second, mostly empty 128-wide strip; rows ragged vs 16
+    ((40, 40, 160), (0, 1, 0, 0, 1, 0), 0.05),   # several strips, tiles and z-runs
+    ((64, 48, 64), (0, 0, 0, 0, 1, 1), 0.0),     # Neumann z faces: the plane link counts 1 and 2
+]
+
+
+@pytest.mark.parametrize("shape,bc,frac", T3_CASES)
+def test_tma3d_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
+    """The TMA-fed 3D level kernels (plane loads into an mbarrier ring, one
+    block barrier per plane), which the default threshold keeps for levels
+    of >= 2^15 cells, forced onto every eligible level: one V cycle and one
+    sawtooth cycle match the oracle, and full solves with float32, FP16 and
+    BF16 level storage reach relres 1e-6 within 1e-5 of x*."""
+    monkeypatch.setenv("NPMG_TMA3D_MIN", "0")
+    test_one_cycle_matches_oracle(L, shape, bc, frac)
+    test_sawtooth_cycle_matches_oracle(L, shape, bc, frac)
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 2, solid=solid).astype(np.float32)
+    its = [solve_and_check(L, shape, bc, solid, h, b, prec=prec)["iters"] for prec in (0, 1, 2)]
+    # the CG direction update on the TMA-fed kernel (the default with these
+    # level kernels) and on the marching kernel: the same iterations
+    monkeypatch.setenv("NPMG_NO_TMA3D_CG", "1")
+    st = solve_and_check(L, shape, bc, solid, h, b)
+    assert abs(st["iters"] - its[0]) <= 1, (st["iters"], its)
 
 
 @pytest.mark.parametrize("shape,bc,frac", CASES)
@@ -384,3 +415,56 @@ def test_device_loop_matches_host_loop(L, shape, bc, frac, monkeypatch):
     for (it_d, ou_d, x_d, x64_d), (it_h, ou_h, x_h, x64_h) in zip(*out):
         assert (it_d, ou_d) == (it_h, ou_h)
         assert torch.equal(x_d, x_h) and torch.equal(x64_d, x64_h)
+
+
+def test_building_blocks_reject_misaligned_arrays(L):
+    """Every entry point that takes caller arrays refuses a view at a 4-byte
+    offset (the kernels move float4 vectors) with MG_ERR_INVALID before it
+    enqueues anything: the output arrays are left untouched."""
+    shape = (64, 64)
+    h = I.poisson_spacing(shape)
+    hdl = create(L, shape, (0, 0, 0, 0), None, h)
+    lib = L.load()
+    s = L.stream_ptr()
+    try:
+        n = 64 * 64
+        buf = torch.full((n + 4,), 7.0, dtype=torch.float32, device="cuda")
+        bad = buf[1:n + 1]
+        good = torch.full((n,), 7.0, dtype=torch.float32, device="cuda")
+        coarse = torch.full((n // 4,), 7.0, dtype=torch.float32, device="cuda")
+        calls = {
+            "mg_apply_operator": lambda a, c: lib.mg_apply_operator(hdl, 0, a.data_ptr(), c.data_ptr(), s),
+            "mg_smooth": lambda a, c: lib.mg_smooth(hdl, 0, c.data_ptr(), a.data_ptr(), 2, s),
+            "mg_residual_restrict": lambda a, c: lib.mg_residual_restrict(hdl, 0, a.data_ptr(), a.data_ptr(),
+                                                                          coarse.data_ptr(), s),
+            "mg_prolong_correct": lambda a, c: lib.mg_prolong_correct(hdl, 0, coarse.data_ptr(), a.data_ptr(), s),
+            "mg_precondition": lambda a, c: lib.mg_precondition(hdl, a.data_ptr(), c.data_ptr(), s),
+        }
+        o = L.default_options()
+        calls["mg_vcycle_noalloc"] = lambda a, c: lib.mg_vcycle_noalloc(
+            2, L._i64_3(64, 64, 1), L._d3(h[0], h[1], 1.0), L._i6(0, 0, 0, 0, 0, 0), None, ctypes.byref(o),
+            a.data_ptr(), c.data_ptr(), s)
+        for name, call in calls.items():
+            torch.cuda.synchronize()
+            st = call(bad, good)
+            assert st == L.MG_ERR_INVALID, name
+            assert "aligned" in L.last_error(), (name, L.last_error())
+            torch.cuda.synchronize()
+            assert torch.all(good == 7.0) and torch.all(buf == 7.0) and torch.all(coarse == 7.0), name
+    finally:
+        L.mg_destroy(hdl)
+
+
+@pytest.mark.parametrize("shape,bc,frac", [CASES[1], CASES[2]])
+def test_float_float_refinement_matches_float64(L, shape, bc, frac):
+    """The refinement loop's iterate and outer residual in float64 (the
+    default) and in float-float pairs (MG_REFINE_FF): both reach relres 1e-6
+    within 1e-5 of x*, with the same refinement steps and CG iterations up
+    to one (the two residuals differ only in their last bits), for float32
+    and FP16 level storage."""
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 1, solid=solid).astype(np.float32)
+    for prec in (0, 1):
+        s64 = solve_and_check(L, shape, bc, solid, h, b, prec=prec)
+        sff = solve_and_check(L, shape, bc, solid, h, b, prec=prec, refine=L.MG_REFINE_FF)
+        assert abs(s64["iters"] - sff["iters"]) <= 1 and s64["outer"] == sff["outer"], (s64, sff)

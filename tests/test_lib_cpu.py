@@ -44,7 +44,7 @@ def test_binding_covers_every_declared_symbol():
 def test_default_options(lib):
     from paper_2402_17913_gb300 import lib as L
     o = L.default_options()
-    assert (o.pre, o.post, o.krylov, o.levels, o.prec) == (2, 2, 1, 0, 0)
+    assert (o.pre, o.post, o.krylov, o.levels, o.prec, o.refine) == (2, 2, 1, 0, 0, L.MG_REFINE_FP64)
     assert abs(o.omega - 2.0 / 3.0) < 1e-15 and o.coarse_scale == 1.0
 
 
@@ -66,9 +66,10 @@ def test_create_rejects_invalid_arguments(lib, dim, shape, bc, why):
     assert len(lib.mg_last_error()) > 0
 
 
-def test_create_rejects_bad_options(lib):
+@pytest.mark.parametrize("bad", [dict(pre=9), dict(refine=2), dict(cycle=5)])
+def test_create_rejects_bad_options(lib, bad):
     from paper_2402_17913_gb300 import lib as L
-    o = L.default_options(pre=9)
+    o = L.default_options(**bad)
     h = ctypes.c_void_p()
     st = lib.mg_create(ctypes.byref(h), 2, (ctypes.c_int64 * 3)(8, 8, 1), (ctypes.c_double * 3)(1, 1, 1),
                        (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0), None, ctypes.byref(o), None)
