@@ -74,8 +74,8 @@ def algo_bytes_per_cell(cls, dim, prec="fp32", masked=False):
     return {
         "down_fine": 4 + t + t * c + m,      # read b; write x, coarse b
         "up_fine": 4 + t + t * c + 4 + m,    # read b, x, coarse e; write z
-        "p_update": 4 + 4 + 4 + 4,           # read z, p_old; write p, Ap
-        "xr_update": 4 + 4 + 8 + 8,          # read p, Ap; read+write d, r
+        "p_update": 4 + 4 + 4,               # read z, p_old; write p ((p, A p) reduced)
+        "xr_update": 4 + 8 + 8,              # read p; read+write d, r (A p formed from p)
         "outer": 4 + 8 + 4 + 8 + 4,          # read b, iterate, d; write iterate, r
     }[cls]
 
@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--guess-level", type=int, default=1, choices=[0, 1, 2],
                     help="ns3d --guess net: the network runs on the grid coarsened this many times")
     ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--batch-count", type=int, default=1024,
+                    help="batched: instances in the batch (the workload has 1024; fewer for profiling captures)")
     ap.add_argument("--advance", type=int, default=None,
                     help="ns2d/ns3d: untimed steps from the seeded initial state before the warm-up "
                          "(default: ns2d 480, ns3d 180, so that the timed steps end near step 500 / 200)")
@@ -283,7 +285,7 @@ class Batched:
     work (sum of N^2, heaviest instance first onto the least-loaded rank):
     each rank solves its share with no collective, and the whole job is the
     1024 instances (strong scaling)."""
-    name = "batched_1024"
+    name = "batched_1024"  # the workload; config() states the instance count of a run
     dim = 2
 
     def __init__(self, count=1024, seed=1234, limit=None, rank=0, world=1):
@@ -596,7 +598,7 @@ def run_gpu(args, rank, world):
         io_bytes = sum(t.numel() * 4 for t in host)
         cleanup = lambda: L.ns_destroy(ns)  # noqa: E731
     elif args.config == "batched":
-        wl = Batched(rank=rank, world=world)
+        wl = Batched(count=args.batch_count, rank=rank, world=world)
         masks = [torch.from_numpy(m.astype(np.uint8)).to(dev) for m in wl.solids]
         bh = L.mg_create_batched(wl.shapes, wl.spacings, (0, 0, 0, 0), masks)
         mg = None

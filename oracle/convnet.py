@@ -16,6 +16,11 @@ resolutions.  Everything here is plain numpy in float64:
 * ``backward``: the analytic gradient of 0.5 * mean((y - t)^2), checked
   against finite differences in the tests.
 * ``adam``: Kingma & Ba's update (beta1 0.9, beta2 0.999, eps 1e-8).
+* ``bf16_round`` and the ``rnd`` argument of ``forward`` / ``backward``:
+  the same arithmetic with every stored tensor rounded to bfloat16, the
+  storage format the workload fixes for the network's activations (BF16
+  weights and activations, FP32 accumulation); the weight gradients and
+  all arithmetic stay float64.
 * ``residual_loss``: the warm-start objective.  The solve that follows
   stops on ||b - A x|| / ||b||, so a guess is worth what its residual is
   worth: 0.5 * sum over interior fluid cells of (A_crop y - b)^2 / size,
@@ -94,22 +99,45 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(W, x):
-    """Returns (y, cache)."""
-    c = {"x": x}
-    c["a1"] = conv3d(x, W[0]); c["e1a"] = relu(c["a1"])
-    c["a2"] = conv3d(c["e1a"], W[1]); c["e1"] = relu(c["a2"])
-    c["p1"] = pool(c["e1"])
-    c["a3"] = conv3d(c["p1"], W[2]); c["e2a"] = relu(c["a3"])
-    c["a4"] = conv3d(c["e2a"], W[3]); c["e2"] = relu(c["a4"])
-    c["p2"] = pool(c["e2"])
-    c["a5"] = conv3d(c["p2"], W[4]); c["e3a"] = relu(c["a5"])
-    c["a6"] = conv3d(c["e3a"], W[5]); c["e3"] = relu(c["a6"])
-    c["s2"] = up(c["e3"]) + c["e2"]
-    c["a7"] = conv3d(c["s2"], W[6]); c["d2"] = relu(c["a7"])
-    c["s1"] = up(c["d2"]) + c["e1"]
-    c["a8"] = conv3d(c["s1"], W[7]); c["d1"] = relu(c["a8"])
+def bf16_round(a):
+    """The value of float array ``a`` stored as bfloat16: rounded to float32,
+    then to the nearest bfloat16 (8 significant bits, ties to the even
+    significand), returned as float64.  bfloat16 is the upper half of a
+    float32, so rounding adds half an ulp of the lower half (plus the
+    tie-breaking bit) and clears it.  Inf/NaN are not expected here."""
+    u = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(a):
+    return a
+
+
+def forward(W, x, rnd=None):
+    """Returns (y, cache).  ``rnd`` (default: none) rounds every tensor the
+    way a storage format would, at the points where an implementation that
+    keeps its activations in that format stores them: the input, each
+    activation after its ReLU, each pooled and each upsampled-plus-skip
+    tensor; the output y is rounded to float32 when ``rnd`` is given.  The
+    pre-activations a_k stay as computed (they decide the ReLU masks)."""
+    r = rnd or _identity
+    c = {"x": r(x)}
+    c["a1"] = conv3d(c["x"], W[0]); c["e1a"] = r(relu(c["a1"]))
+    c["a2"] = conv3d(c["e1a"], W[1]); c["e1"] = r(relu(c["a2"]))
+    c["p1"] = r(pool(c["e1"]))
+    c["a3"] = conv3d(c["p1"], W[2]); c["e2a"] = r(relu(c["a3"]))
+    c["a4"] = conv3d(c["e2a"], W[3]); c["e2"] = r(relu(c["a4"]))
+    c["p2"] = r(pool(c["e2"]))
+    c["a5"] = conv3d(c["p2"], W[4]); c["e3a"] = r(relu(c["a5"]))
+    c["a6"] = conv3d(c["e3a"], W[5]); c["e3"] = r(relu(c["a6"]))
+    c["s2"] = r(up(c["e3"]) + c["e2"])
+    c["a7"] = conv3d(c["s2"], W[6]); c["d2"] = r(relu(c["a7"]))
+    c["s1"] = r(up(c["d2"]) + c["e1"])
+    c["a8"] = conv3d(c["s1"], W[7]); c["d1"] = r(relu(c["a8"]))
     y = conv3d(c["d1"], W[8])
+    if rnd is not None:
+        y = y.astype(np.float32).astype(np.float64)
     return y, c
 
 
@@ -118,37 +146,43 @@ def loss(y, t):
     return 0.5 * float(np.mean((y - t) ** 2))
 
 
-def backward(W, c, y, t):
+def backward(W, c, y, t, rnd=None):
     """Gradients of ``loss(forward(W, x), t)`` with respect to every W[k]."""
-    return backward_from(W, c, (y - t) / y.size)
+    return backward_from(W, c, (y - t) / y.size, rnd)
 
 
-def backward_from(W, c, g):
+def backward_from(W, c, g, rnd=None):
     """Gradients of a loss with respect to every W[k], given its gradient
-    ``g`` with respect to the network output y ([1, Z, Y, X])."""
+    ``g`` with respect to the network output y ([1, Z, Y, X]).  ``rnd``
+    (default: none) rounds the output gradient and every gradient tensor
+    an implementation would store (after each data gradient with its ReLU
+    mask, and the data gradients that feed a skip or a pooling branch), as
+    in ``forward``; the weight gradients themselves are exact sums."""
+    r = rnd or _identity
     dW = [None] * NLAYERS
+    g = r(g)
     dW[8] = conv3d_wgrad(c["d1"], g)
-    g = conv3d_dgrad(g, W[8]) * (c["a8"] > 0)
+    g = r(conv3d_dgrad(g, W[8]) * (c["a8"] > 0))
     dW[7] = conv3d_wgrad(c["s1"], g)
-    g_s1 = conv3d_dgrad(g, W[7])
+    g_s1 = r(conv3d_dgrad(g, W[7]))
     g_e1 = g_s1.copy()
-    g = up_bwd(g_s1) * (c["a7"] > 0)
+    g = r(up_bwd(g_s1) * (c["a7"] > 0))
     dW[6] = conv3d_wgrad(c["s2"], g)
-    g_s2 = conv3d_dgrad(g, W[6])
+    g_s2 = r(conv3d_dgrad(g, W[6]))
     g_e2 = g_s2.copy()
-    g = up_bwd(g_s2) * (c["a6"] > 0)
+    g = r(up_bwd(g_s2) * (c["a6"] > 0))
     dW[5] = conv3d_wgrad(c["e3a"], g)
-    g = conv3d_dgrad(g, W[5]) * (c["a5"] > 0)
+    g = r(conv3d_dgrad(g, W[5]) * (c["a5"] > 0))
     dW[4] = conv3d_wgrad(c["p2"], g)
-    g_e2 = g_e2 + pool_bwd(conv3d_dgrad(g, W[4]))
-    g = g_e2 * (c["a4"] > 0)
+    g_e2 = g_e2 + pool_bwd(r(conv3d_dgrad(g, W[4])))
+    g = r(g_e2 * (c["a4"] > 0))
     dW[3] = conv3d_wgrad(c["e2a"], g)
-    g = conv3d_dgrad(g, W[3]) * (c["a3"] > 0)
+    g = r(conv3d_dgrad(g, W[3]) * (c["a3"] > 0))
     dW[2] = conv3d_wgrad(c["p1"], g)
-    g_e1 = g_e1 + pool_bwd(conv3d_dgrad(g, W[2]))
-    g = g_e1 * (c["a2"] > 0)
+    g_e1 = g_e1 + pool_bwd(r(conv3d_dgrad(g, W[2])))
+    g = r(g_e1 * (c["a2"] > 0))
     dW[1] = conv3d_wgrad(c["e1a"], g)
-    g = conv3d_dgrad(g, W[1]) * (c["a1"] > 0)
+    g = r(conv3d_dgrad(g, W[1]) * (c["a1"] > 0))
     dW[0] = conv3d_wgrad(c["x"], g)
     return dW
 

@@ -205,8 +205,10 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(h, MG_K_P_UPDATE, s);
+    // on the TMA-fed kernels A p is not stored: the vector update forms it
+    // again from p
     if (DIM == 3 && h->t3cg_ok)
-      e = launch_p_update_t3<M>(h->t3cg, parity, h->lv[0], (float*)h->p[1 - parity], (float*)h->Ap, h->st,
+      e = launch_p_update_t3<M>(h->t3cg, parity, h->lv[0], (float*)h->p[1 - parity], (float*)h->Ap, false, h->st,
                                 h->partials, s);
     else
       e = launch_p_update<DIM, float, M>(h->lv[0], h->z, h->p[parity], h->p[1 - parity], h->Ap, h->st, h->partials,
@@ -214,6 +216,8 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
   }
   if (e != cudaSuccess) return e;
   LaunchScope ls(h, MG_K_XR_UPDATE, s);
+  if (DIM == 3 && h->t3cg_ok)
+    return launch_xr_update_t3<M>(h->t3cg, 1 - parity, h->lv[0], (float*)h->d, (float*)h->r, h->st, h->partials, s);
   return launch_xr_update<float>(h->lv[0], h->p[1 - parity], h->Ap, h->d, h->r, h->st, h->partials, s);
 }
 
@@ -779,7 +783,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     // the level's legs are (NPMG_NO_TMA3D_CG keeps the marching kernel)
     h->t3cg_ok = DIM == 3 && h->kc > 0 && h->t3_ok[0] && getenv("NPMG_NO_TMA3D_CG") == nullptr &&
                  tma3d_encode_cg(&h->t3cg, h->lv[0], (const float*)h->z, (const float*)h->p[0],
-                                 (const float*)h->p[1]);
+                                 (const float*)h->p[1], (const float*)h->d, (const float*)h->r);
     return e;
   }));
   NPMG_TRY(cudaStreamSynchronize(s));

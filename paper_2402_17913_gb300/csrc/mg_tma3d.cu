@@ -37,6 +37,7 @@
 
 #include "launch.h"
 #include "mg_kernels.cuh"
+#include "refine.cuh"
 #include "tma.cuh"
 #include "tma_host.h"
 
@@ -173,8 +174,15 @@ __device__ __forceinline__ int plane_kz(const LevelDev& L, int p) {
   return (p >= 0 && p < L.nz) ? axis_count(p, L.nz, L.bcD, 4) : 0;
 }
 
-// omega / d (w) or d of cell j on a plane with z link count kz.
-__device__ __forceinline__ float pick(int kz, float v1, float v2) { return kz == 2 ? v2 : (kz == 1 ? v1 : 0.f); }
+// Runs f with a getter of the per-cell value (omega / d or d) of the
+// thread's cells on a plane with z link count kz: one uniform branch per
+// plane instead of a select per cell.
+template <typename F>
+__device__ __forceinline__ void with_plane(int kz, const float (&v1)[2][4], const float (&v2)[2][4], F&& f) {
+  if (kz == 2) f([&](int h, int j) { return v2[h][j]; });
+  else if (kz == 1) f([&](int h, int j) { return v1[h][j]; });
+  else f([](int, int) { return 0.f; });
+}
 
 __device__ __forceinline__ void fill_lut(const LevelDev& L, float omega, float* lut) {
   if (threadIdx.x < 64) {
@@ -372,14 +380,14 @@ __global__ void __launch_bounds__(NT, 1)
       if (i >= 2) {
         float nb[2][4];
         neighbours(L, t, XS + ((i - 1) & 1) * PL, XQ[C1], XQ[C2], XQ[C0], nb);
-        const int kz = MASKED ? 0 : plane_kz(L, p - 1);
+        auto sweep = [&](auto W) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float w = MASKED ? WQ[C1][h][j] : pick(kz, D.w1[h][j], D.w2[h][j]);
-            SQ[C1][h][j] = fmaf(keep, XQ[C1][h][j], w * (BQ[C1][h][j] + nb[h][j]));
-          }
+            for (int j = 0; j < 4; ++j) SQ[C1][h][j] = fmaf(keep, XQ[C1][h][j], W(h, j) * (BQ[C1][h][j] + nb[h][j]));
+        };
+        if constexpr (MASKED) sweep([&](int h, int j) { return WQ[C1][h][j]; });
+        else with_plane(plane_kz(L, p - 1), D.w1, D.w2, sweep);
         sts8(SS + ((i - 1) & 1) * PL, t, SQ[C1]);
       }
       // C: second sweep on plane o = p - 2, written out
@@ -387,14 +395,14 @@ __global__ void __launch_bounds__(NT, 1)
       if (i >= 4 && t.own) {
         float nb[2][4], z[2][4];
         neighbours(L, t, SS + (i & 1) * PL, SQ[C2], SQ[C0], SQ[C1], nb);
-        const int kz = MASKED ? 0 : plane_kz(L, o);
+        auto sweep = [&](auto W) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float w = MASKED ? WQ[C2][h][j] : pick(kz, D.w1[h][j], D.w2[h][j]);
-            z[h][j] = fmaf(keep, SQ[C2][h][j], w * (BQ[C2][h][j] + nb[h][j]));
-          }
+            for (int j = 0; j < 4; ++j) z[h][j] = fmaf(keep, SQ[C2][h][j], W(h, j) * (BQ[C2][h][j] + nb[h][j]));
+        };
+        if constexpr (MASKED) sweep([&](int h, int j) { return WQ[C2][h][j]; });
+        else with_plane(plane_kz(L, o), D.w1, D.w2, sweep);
         if (t.xin) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -488,7 +496,6 @@ __global__ void __launch_bounds__(NT, 1)
       // A: b (and omega / d, d) of plane p and the first sweep from zero
       {
         const unsigned char* sg = R.base + (R.g % S::NS) * S::STAGE;
-        const int kz = MASKED ? 0 : plane_kz(L, p);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = 2 * t.q + h;
@@ -504,25 +511,31 @@ __global__ void __launch_bounds__(NT, 1)
             }
           }
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            BQ[C0][h][j] = bv[j];
-            S1Q[C0][h][j] = (MASKED ? WQ[C0][h][j] : pick(kz, D.w1[h][j], D.w2[h][j])) * bv[j];
-          }
+          for (int j = 0; j < 4; ++j) BQ[C0][h][j] = bv[j];
         }
+        auto first = [&](auto W) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) S1Q[C0][h][j] = W(h, j) * BQ[C0][h][j];
+        };
+        if constexpr (MASKED) first([&](int h, int j) { return WQ[C0][h][j]; });
+        else with_plane(plane_kz(L, p), D.w1, D.w2, first);
         sts8(S1 + (i & 1) * PL, t, S1Q[C0]);
       }
       // B: second sweep on plane p - 1; the output x
       if (i >= 2) {
         float nb[2][4];
         neighbours(L, t, S1 + ((i - 1) & 1) * PL, S1Q[C1], S1Q[C2], S1Q[C0], nb);
-        const int kz = MASKED ? 0 : plane_kz(L, p - 1);
+        auto sweep = [&](auto W) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float w = MASKED ? WQ[C1][h][j] : pick(kz, D.w1[h][j], D.w2[h][j]);
-            XQ[C1][h][j] = fmaf(keep, S1Q[C1][h][j], w * (BQ[C1][h][j] + nb[h][j]));
-          }
+            for (int j = 0; j < 4; ++j)
+              XQ[C1][h][j] = fmaf(keep, S1Q[C1][h][j], W(h, j) * (BQ[C1][h][j] + nb[h][j]));
+        };
+        if constexpr (MASKED) sweep([&](int h, int j) { return WQ[C1][h][j]; });
+        else with_plane(plane_kz(L, p - 1), D.w1, D.w2, sweep);
         sts8(XB + ((i - 1) & 1) * PL, t, XQ[C1]);
         const int o = p - 1;
         if (t.own && t.xin && o >= z0 && o < z1) {
@@ -537,16 +550,20 @@ __global__ void __launch_bounds__(NT, 1)
       if (i >= 4 && t.own) {
         float nb[2][4], rx[2] = {0.f, 0.f};
         neighbours(L, t, XB + (i & 1) * PL, XQ[C2], XQ[C0], XQ[C1], nb);
-        const int kz = MASKED ? 0 : plane_kz(L, o);
+        // solid cells (d = 0) are not unknowns: no residual there; unmasked
+        // cells outside the domain belong to threads that store nothing
+        auto resid = [&](auto Dg) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float dj = MASKED ? DQ[C2][h][j] : pick(kz, D.d1[h][j], D.d2[h][j]);
-            // cells with d = 0 (solid, outside) are not unknowns: no residual
-            const float r = dj != 0.f ? BQ[C2][h][j] - (dj * XQ[C2][h][j] - nb[h][j]) : 0.f;
-            rx[j >> 1] += r;
-          }
+            for (int j = 0; j < 4; ++j) {
+              const float dj = Dg(h, j);
+              const float r = BQ[C2][h][j] - (dj * XQ[C2][h][j] - nb[h][j]);
+              rx[j >> 1] += (MASKED && dj == 0.f) ? 0.f : r;
+            }
+        };
+        if constexpr (MASKED) resid([&](int h, int j) { return DQ[C2][h][j]; });
+        else with_plane(plane_kz(L, o), D.d1, D.d2, resid);
         if ((o & 1) == 0) {
           zp[0] = rx[0];
           zp[1] = rx[1];
@@ -612,7 +629,7 @@ __device__ __forceinline__ void issue_pz(Ring<N>& R, const CUtensorMap* mz, cons
   ++R.issued;
 }
 
-template <bool MASKED>
+template <bool MASKED, bool STORE_AP>
 __global__ void __launch_bounds__(NT, 1)
     k_pup_t3(const __grid_constant__ CUtensorMap mz, const __grid_constant__ CUtensorMap mp,
              const __grid_constant__ CUtensorMap mm, LevelDev L, float* __restrict__ pnew, float* __restrict__ Ap,
@@ -685,23 +702,25 @@ __global__ void __launch_bounds__(NT, 1)
       if (i >= 2 && t.own) {
         float nb[2][4];
         neighbours(L, t, PS + ((i - 1) & 1) * PL, PQ[C1], PQ[C2], PQ[C0], nb);
-        const int kz = MASKED ? 0 : plane_kz(L, o);
-        if (t.xin) {
+        auto apply = [&](auto Dg) {
+          if (!t.xin) return;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             if (!t.yin[h]) continue;
             float av[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              const float d = MASKED ? DQ[C1][h][j] : pick(kz, D.d1[h][j], D.d2[h][j]);
+              const float d = Dg(h, j);
               av[j] = d != 0.f ? d * PQ[C1][h][j] - nb[h][j] : 0.f;
               acc = fmaf(PQ[C1][h][j], av[j], acc);
             }
             const size_t gi = ((size_t)o * L.ny + t.gy + h) * L.nx + t.gx;
             stg4<float>(pnew + gi, PQ[C1][h]);
-            stg4<float>(Ap + gi, av);
+            if (STORE_AP) stg4<float>(Ap + gi, av);
           }
-        }
+        };
+        if constexpr (MASKED) apply([&](int h, int j) { return DQ[C1][h][j]; });
+        else with_plane(plane_kz(L, o), D.d1, D.d2, apply);
       }
       if (__syncthreads_or(!ok)) {
         drain(R, R.g);
@@ -727,6 +746,160 @@ __global__ void __launch_bounds__(NT, 1)
       st->pAp = tot;
       st->alpha = st->krylov ? st->rz / tot : 1.0;
     }
+  }
+}
+
+// ---- CG vector update -------------------------------------------------------------
+// d += alpha p, r -= alpha A' p and ||r||^2 on the finest level (float32),
+// with A' p formed again from p (bit for bit the values the direction update
+// reduced (p, A' p) from) instead of being stored by it and read back: the
+// elected thread loads the plane of p (with its halo) and, into the same
+// stage, the planes of d and r one below it; per step the block forms A' p
+// of the plane below the new p and updates d and r there.  The last block
+// takes CG's convergence decision (inner_decide).
+template <bool MASKED>
+struct GX {
+  static constexpr int W = TX + 8;                 // p box width (x0 - 4 .. x0 + 131)
+  static constexpr int PB = W * RY * 4;            // bytes of the p box
+  static constexpr int VB = TX * TY * 4;           // bytes of a d / r box (the column's own cells)
+  static constexpr int WM = TX + 32;
+  static constexpr int MBY = MASKED ? WM * RY : 0;
+  static constexpr int OP = 0, OD = al128(PB), OR = al128(OD + VB), OM = al128(OR + VB);
+  static constexpr int STAGE = al128(OM + MBY);
+  static constexpr int NS = 5;                     // TMA stages
+  static constexpr int RING = 2 * PL * 4;          // one plane buffer of two slots
+  static constexpr int LUT = RING + NS * STAGE;
+  static constexpr int BAR = LUT + 128 * 4;
+  static constexpr int BYTES = BAR + NS * 8;
+  static_assert(RING % 128 == 0 && STAGE % 128 == 0, "TMA destinations 128-byte aligned");
+};
+
+template <bool MASKED, int N>
+__device__ __forceinline__ void issue_xr(Ring<N>& R, const CUtensorMap* mp, const CUtensorMap* md,
+                                         const CUtensorMap* mr, const CUtensorMap* mm, bool first, int x0, int y0,
+                                         int p) {
+  using S = GX<MASKED>;
+  const unsigned st = R.issued % N;
+  unsigned char* dst = R.base + st * S::STAGE;
+  uint64_t* bar = R.bar + st;
+  mbar_arrive_expect_tx(bar, (uint32_t)(S::PB + S::VB * (first ? 1 : 2) + S::MBY));
+  tma_load_3d(dst + S::OP, mp, bar, x0 - 4, y0 - 2, p);
+  if (!first) tma_load_3d(dst + S::OD, md, bar, x0, y0, p - 1);
+  tma_load_3d(dst + S::OR, mr, bar, x0, y0, p - 1);
+  if (MASKED) tma_load_3d(dst + S::OM, mm, bar, x0 - 16, y0 - 2, p);
+  ++R.issued;
+}
+
+template <bool MASKED>
+__global__ void __launch_bounds__(NT, 1)
+    k_xr_t3(const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap md,
+            const __grid_constant__ CUtensorMap mr, const __grid_constant__ CUtensorMap mm, LevelDev L,
+            float* __restrict__ d, float* __restrict__ r, Sched sc, SolveState* __restrict__ st,
+            double* __restrict__ partials) {
+  chain_enter();
+  if (st->inner_done) return;
+  using S = GX<MASKED>;
+  extern __shared__ __align__(128) unsigned char smem_t3[];
+  float* PS = reinterpret_cast<float*>(smem_t3);  // [2][PL]: p
+  const float* lut = reinterpret_cast<const float*>(smem_t3 + S::LUT);
+  Ring<S::NS> R;
+  R.bar = reinterpret_cast<uint64_t*>(smem_t3 + S::BAR);
+  R.base = smem_t3 + S::RING;
+  R.g = R.issued = 0;
+  const bool first = st->first;
+  const float alpha = (float)st->alpha;
+  if (MASKED) fill_lut(L, 1.f, reinterpret_cast<float*>(smem_t3 + S::LUT));
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S::NS; ++k) mbar_init(R.bar + k, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  float acc = 0.f;
+  bool failed = false;
+  for_each_run(L, sc, [&](int x0, int y0, int z0, int z1) -> bool {
+    const Th t = thread_geom(L, x0, y0);
+    Diag D;
+    if (!MASKED) D = unmasked_diag(L, t, 1.f);
+    const int n = z1 - z0 + 2;  // steps: p on planes z0 - 1 .. z1
+    if (threadIdx.x == 0)
+      for (int k = 0; k < S::NS && k < n; ++k) issue_xr<MASKED>(R, &mp, &md, &mr, &mm, first, x0, y0, z0 - 1 + k);
+    float PQ[3][2][4], DQ[3][2][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) PQ[k][h][j] = DQ[k][h][j] = 0.f;
+    auto step = [&](int i, auto phc) -> bool {
+      constexpr int C0 = decltype(phc)::value;             // i % 3
+      constexpr int C1 = (C0 + 2) % 3, C2 = (C0 + 1) % 3;  // (i - 1) % 3, (i - 2) % 3
+      const int p = z0 - 1 + i;
+      const bool ok = mbar_wait_bounded(R.bar + R.g % S::NS, (R.g / S::NS) & 1);
+      const unsigned char* sg = R.base + (R.g % S::NS) * S::STAGE;
+      // A: p of plane p (0 on solid cells and outside the domain)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = 2 * t.q + h;
+        lds4<float>(sg + S::OP + (rr * S::W + 4 * t.c) * 4, PQ[C0][h]);
+        if (MASKED) {
+          const unsigned mw = *reinterpret_cast<const unsigned*>(sg + S::OM + rr * S::WM + 12 + 4 * t.c);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) DQ[C0][h][j] = lut[(mw >> (8 * j)) & 63u];
+        }
+      }
+      sts8(PS + (i & 1) * PL, t, PQ[C0]);
+      // B: A' p on plane o = p - 1; d and r of plane o from this stage
+      const int o = p - 1;
+      if (i >= 2 && t.own) {
+        float nb[2][4];
+        neighbours(L, t, PS + ((i - 1) & 1) * PL, PQ[C1], PQ[C2], PQ[C0], nb);
+        auto update = [&](auto Dg) {
+          if (!t.xin) return;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (!t.yin[h]) continue;
+            const int off = ((2 * t.q - 2 + h) * TX + 4 * (t.c - 1)) * 4;  // own row / chunk in a d, r box
+            float dv[4], rv[4];
+            lds4<float>(sg + S::OR + off, rv);
+            if (!first) lds4<float>(sg + S::OD + off, dv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float dd = Dg(h, j);
+              const float av = dd != 0.f ? dd * PQ[C1][h][j] - nb[h][j] : 0.f;
+              dv[j] = first ? alpha * PQ[C1][h][j] : fmaf(alpha, PQ[C1][h][j], dv[j]);
+              rv[j] = fmaf(-alpha, av, rv[j]);
+              acc = fmaf(rv[j], rv[j], acc);
+            }
+            const size_t gi = ((size_t)o * L.ny + t.gy + h) * L.nx + t.gx;
+            stg4<float>(d + gi, dv);
+            stg4<float>(r + gi, rv);
+          }
+        };
+        if constexpr (MASKED) update([&](int h, int j) { return DQ[C1][h][j]; });
+        else with_plane(plane_kz(L, o), D.d1, D.d2, update);
+      }
+      if (__syncthreads_or(!ok)) {
+        drain(R, R.g);
+        return false;
+      }
+      if (threadIdx.x == 0 && i + S::NS < n)
+        issue_xr<MASKED>(R, &mp, &md, &mr, &mm, first, x0, y0, z0 - 1 + i + S::NS);
+      ++R.g;
+      return true;
+    };
+    for (int i = 0; i < n; i += 3) {
+      if (!step(i, std::integral_constant<int, 0>())) return !(failed = true);
+      if (i + 1 >= n) break;
+      if (!step(i + 1, std::integral_constant<int, 1>())) return !(failed = true);
+      if (i + 2 >= n) break;
+      if (!step(i + 2, std::integral_constant<int, 2>())) return !(failed = true);
+    }
+    return true;
+  });
+  if (failed) fail(st);
+  double tot;
+  if (grid_sum_last((double)acc, partials, &st->counter[kCntRR], &tot)) {
+    if (threadIdx.x == 0 && !failed) inner_decide(st, tot);
   }
 }
 
@@ -849,9 +1022,12 @@ cudaError_t launch_up_t3(const Tma3Maps& m, const LevelDev& L, void* xout, float
                       m.b, m.e, m.m, L, (TB*)xout, omega, sc, pl.sc, st, partials);
 }
 
-bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const float* p0, const float* p1) {
+bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const float* p0, const float* p1,
+                     const float* d, const float* r) {
   constexpr int W = GP<false>::W;
   bool ok = encode_3d(&out->z, z, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.nx, L.ny, L.nz, W, RY);
+  ok = ok && encode_3d(&out->d, d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.nx, L.ny, L.nz, TX, TY);
+  ok = ok && encode_3d(&out->r, r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.nx, L.ny, L.nz, TX, TY);
   ok = ok && encode_3d(&out->p[0], p0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.nx, L.ny, L.nz, W, RY);
   ok = ok && encode_3d(&out->p[1], p1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L.nx, L.ny, L.nz, W, RY);
   if (L.cell)
@@ -862,15 +1038,30 @@ bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const f
 
 template <bool MASKED>
 cudaError_t launch_p_update_t3(const Tma3CgMaps& m, int parity, const LevelDev& L, float* pnew, float* Ap,
-                               SolveState* st, double* partials, cudaStream_t s) {
+                               bool store_ap, SolveState* st, double* partials, cudaStream_t s) {
   const T3Plan pl = t3_plan(L);
-  return launch_chain(k_pup_t3<MASKED>, pl.grid, NT, (size_t)GP<MASKED>::BYTES, s, m.z, m.p[parity], m.m, L, pnew,
-                      Ap, pl.sc, st, partials);
+  if (store_ap)
+    return launch_chain(k_pup_t3<MASKED, true>, pl.grid, NT, (size_t)GP<MASKED>::BYTES, s, m.z, m.p[parity], m.m, L,
+                        pnew, Ap, pl.sc, st, partials);
+  return launch_chain(k_pup_t3<MASKED, false>, pl.grid, NT, (size_t)GP<MASKED>::BYTES, s, m.z, m.p[parity], m.m, L,
+                      pnew, Ap, pl.sc, st, partials);
 }
-template cudaError_t launch_p_update_t3<false>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, SolveState*,
+template cudaError_t launch_p_update_t3<false>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, bool,
+                                               SolveState*, double*, cudaStream_t);
+template cudaError_t launch_p_update_t3<true>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, bool,
+                                              SolveState*, double*, cudaStream_t);
+
+template <bool MASKED>
+cudaError_t launch_xr_update_t3(const Tma3CgMaps& m, int pbuf, const LevelDev& L, float* d, float* r,
+                                SolveState* st, double* partials, cudaStream_t s) {
+  const T3Plan pl = t3_plan(L);
+  return launch_chain(k_xr_t3<MASKED>, pl.grid, NT, (size_t)GX<MASKED>::BYTES, s, m.p[pbuf], m.d, m.r, m.m, L, d, r,
+                      pl.sc, st, partials);
+}
+template cudaError_t launch_xr_update_t3<false>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, SolveState*,
+                                                double*, cudaStream_t);
+template cudaError_t launch_xr_update_t3<true>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, SolveState*,
                                                double*, cudaStream_t);
-template cudaError_t launch_p_update_t3<true>(const Tma3CgMaps&, int, const LevelDev&, float*, float*, SolveState*,
-                                              double*, cudaStream_t);
 
 template <typename T, bool MASKED, typename TB>
 static cudaError_t prepare_t3_pair() {
@@ -887,8 +1078,12 @@ static cudaError_t prepare_t3_pair() {
 
 template <typename T, bool MASKED>
 cudaError_t prepare_t3_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_pup_t3<MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_pup_t3<MASKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        GP<MASKED>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pup_t3<MASKED, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP<MASKED>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_xr_t3<MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, GX<MASKED>::BYTES);
   if (e == cudaSuccess) e = prepare_t3_pair<T, MASKED, T>();
   if (e == cudaSuccess && !std::is_same<T, float>::value) e = prepare_t3_pair<T, MASKED, float>();
   return e;

@@ -51,14 +51,21 @@ cudaError_t launch_up_t3(const Tma3Maps& m, const LevelDev& L, void* xout, float
 template <typename T, bool MASKED>
 cudaError_t prepare_t3_kernels();
 
-// Tensor maps of the finest level's CG direction update (float32): z, the
-// two p buffers, the cell bytes.
+// Tensor maps of the finest level's CG updates (float32): z, the two p
+// buffers, d and r, the cell bytes.
 struct Tma3CgMaps {
-  CUtensorMap z, p[2], m;
+  CUtensorMap z, p[2], d, r, m;
 };
-bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const float* p0, const float* p1);
+bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const float* p0, const float* p1,
+                     const float* d, const float* r);
+// p = z + beta p_old (p_old = p[parity]), (p, A p) and alpha; A p stored
+// only with store_ap.
 template <bool MASKED>
 cudaError_t launch_p_update_t3(const Tma3CgMaps& m, int parity, const LevelDev& L, float* pnew, float* Ap,
-                               SolveState* st, double* partials, cudaStream_t s);
+                               bool store_ap, SolveState* st, double* partials, cudaStream_t s);
+// d += alpha p, r -= alpha A p (A p formed again from p = p[pbuf]), ||r||^2.
+template <bool MASKED>
+cudaError_t launch_xr_update_t3(const Tma3CgMaps& m, int pbuf, const LevelDev& L, float* d, float* r,
+                                SolveState* st, double* partials, cudaStream_t s);
 
 }  // namespace npmg

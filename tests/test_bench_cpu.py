@@ -107,4 +107,5 @@ def test_algorithmic_bytes_count_each_array_at_its_width():
     assert bench.algo_bytes_per_cell("up_fine", 3) == 12.5
     assert bench.algo_bytes_per_cell("up_fine", 3, "fp16") == 4 + 2 + 0.25 + 4
     assert bench.algo_bytes_per_cell("down_fine", 3, "bf16", masked=True) == 4 + 2 + 0.25 + 1
-    assert bench.algo_bytes_per_cell("p_update", 3, "fp16") == 16
+    assert bench.algo_bytes_per_cell("p_update", 3, "fp16") == 12
+    assert bench.algo_bytes_per_cell("xr_update", 3) == 20

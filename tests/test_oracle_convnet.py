@@ -154,3 +154,48 @@ def test_net_input_scales_each_field_by_its_own_rms():
     assert np.allclose(y2, 2.0 * y1, rtol=1e-12)
     z, rz = C.net_input(np.zeros_like(b), np.zeros_like(p))
     assert rz == 1.0 and not z.any()
+
+
+def test_bf16_round_hand_worked_values():
+    """Round-to-nearest-even to 8 significant bits: below / above half an
+    ulp, exact ties to the even significand (down and up), a carry into the
+    exponent, sign, and values already bfloat16 unchanged."""
+    x = np.array([1.0 + 2.0 ** -9, 1.0 + 3 * 2.0 ** -9, 1.0 + 2.0 ** -8, 1.0 + 2.0 ** -7 + 2.0 ** -8,
+                  2.0 - 2.0 ** -9, -3.14159265, 0.15625, -0.0])
+    want = np.array([1.0, 1.0 + 2.0 ** -7, 1.0, 1.0 + 2.0 ** -6, 2.0, -3.140625, 0.15625, -0.0])
+    got = C.bf16_round(x)
+    assert np.array_equal(got, want), got
+    assert np.array_equal(C.bf16_round(got), got)  # idempotent
+
+
+def test_bf16_round_error_bound():
+    """|round(x) - x| <= (2^-8 + 2^-24) |x|: half an ulp of an 8-bit significand,
+    after the rounding to float32 (half an ulp of 24 bits)."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(10000) * 10.0 ** rng.uniform(-6, 6, 10000)
+    r = C.bf16_round(x)
+    assert np.all(np.abs(r - x) <= (2.0 ** -8 + 2.0 ** -24) * np.abs(x))
+    assert np.max(np.abs(r - x) / np.abs(x)) > 0.9 * 2.0 ** -8  # the bound is reached
+    assert np.mean(r != x) > 0.99
+
+
+def test_rounding_hook_is_the_identity_when_absent_and_bounded_when_bf16():
+    """forward/backward with rnd=None are the plain float64 network; with a
+    rounding that does nothing they are bit for bit the same; with bfloat16
+    storage the output and gradients stay within a few bfloat16 roundings."""
+    W = [C.bf16_round(w) for w in I.convnet_weights(21)]
+    rng = np.random.default_rng(22)
+    x = C.bf16_round(rng.standard_normal((2, 8, 8, 8)))
+    t = rng.standard_normal((1, 8, 8, 8))
+    y0, c0 = C.forward(W, x)
+    y1, c1 = C.forward(W, x, rnd=lambda a: a)
+    g0 = C.backward(W, c0, y0, t)
+    g1 = C.backward(W, c1, y0, t, rnd=lambda a: a)
+    assert np.array_equal(y0, y1.astype(np.float32).astype(np.float64)) or np.allclose(y0, y1, rtol=1e-7)
+    for a, b in zip(g0, g1):
+        assert np.allclose(a, b, rtol=1e-6, atol=0)
+    yb, cb = C.forward(W, x, rnd=C.bf16_round)
+    gb = C.backward(W, cb, yb, t, rnd=C.bf16_round)
+    assert np.linalg.norm(yb - y0) <= 2e-2 * np.linalg.norm(y0)
+    for a, b in zip(g0, gb):
+        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(a)
