@@ -396,9 +396,9 @@ def l2_read_peak(L, dev, l2_size):
 
 # The translation unit of the dominant kernel of each workload with a
 # committed traffic summary; its hash also covers the headers it includes.
-TRAFFIC_TU = {"ns2d_block_2048x1024": "mg_stream2d.cu", "poisson3d_256x256x256_fp32": "mg_rows3d.cu",
-              "ns3d_cube_256x128x128": "mg_rows3d.cu"}
-KERNEL_HEADERS = ["mg_kernels.cuh", "launch.h", "npmg_internal.cuh"]
+TRAFFIC_TU = {"ns2d_block_2048x1024": "mg_stream2d.cu", "poisson3d_256x256x256_fp32": "mg_tma3d.cu",
+              "ns3d_cube_256x128x128": "mg_tma3d.cu"}
+KERNEL_HEADERS = ["mg_kernels.cuh", "launch.h", "npmg_internal.cuh", "tma.cuh", "tma_host.h", "refine.cuh"]
 
 
 def _code_only(text):
