@@ -325,7 +325,64 @@ PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 # ---------------------------------------------------------------------------
+class NvmlClocks:
+    """Samples the SM clock, its maximum and the clock-event reasons of
+    every GPU every 10 ms through NVML (read-only queries), in a thread."""
+    # clock-event reason bits (nvml.h)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self):
+        import ctypes
+        import threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        n = ctypes.c_uint(0)
+        lib.nvmlDeviceGetCount_v2(ctypes.byref(n))
+        self.h = []
+        for i in range(n.value):
+            hd = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(i, ctypes.byref(hd)) == 0:
+                self.h.append(hd)
+        if not self.h:
+            raise RuntimeError("no NVML device")
+        self.lib, self.ct = lib, ctypes
+        self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.sm, self.mx, self.reasons = [], [], set()
+        self.stop = threading.Event()
+        self.t = threading.Thread(target=self.run, daemon=True)
+        self.t.start()
+
+    def run(self):
+        ct, lib = self.ct, self.lib
+        while not self.stop.is_set():
+            for hd in self.h:
+                c, m, r = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+                if lib.nvmlDeviceGetClockInfo(hd, 1, ct.byref(c)) == 0:
+                    self.sm.append(float(c.value))
+                if lib.nvmlDeviceGetMaxClockInfo(hd, 1, ct.byref(m)) == 0:
+                    self.mx.append(float(m.value))
+                if self.reason_fn(hd, ct.byref(r)) == 0:
+                    for name, bit in self.BITS.items():
+                        if r.value & bit:
+                            self.reasons.add(name)
+            self.stop.wait(0.01)
+
+    def summary(self):
+        self.stop.set()
+        self.t.join()
+        self.lib.nvmlShutdown()
+        return {"sm_mhz": statistics.median(self.sm) if self.sm else None,
+                "sm_max_mhz": max(self.mx) if self.mx else None, "reasons": sorted(self.reasons),
+                "samples": len(self.sm), "source": "NVML, 10 ms"}
+
+
 def clocks_sampler():
+    try:
+        return NvmlClocks(), None, None
+    except Exception:
+        pass
     path = tempfile.mktemp(suffix=".csv")
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -340,6 +397,8 @@ def clocks_sampler():
 
 
 def clocks_summary(p, f, path):
+    if isinstance(p, NvmlClocks):
+        return p.summary()
     if p is None:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
     p.terminate()
@@ -361,7 +420,7 @@ def clocks_summary(p, f, path):
                 reasons.add(n)
     os.unlink(path)
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-            "reasons": sorted(reasons), "samples": len(sm)}
+            "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def measured_peak():
@@ -708,12 +767,16 @@ def run_gpu(args, rank, world):
     times = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    # an NVTX range around the timed steps: a profiler capture can take
+    # exactly their launches (ncu --nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record()
         step()
         ev[i][1].record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = clocks_summary(cp, cf, cpath)
     times = [a.elapsed_time(b) for a, b in ev]
     # the batched solve is one persistent kernel per solve (one graph launch)
@@ -788,11 +851,21 @@ def run_gpu(args, rank, world):
         L.mg_profile_enable(mg, False)
         cleanup()
         tot_prof = sum(ms for ms, _ in prof.values()) or 1.0
-        dom = max(KERNEL_CLASSES, key=lambda k: prof[k][0])
+        dom = max(KERNEL_CLASSES + ("cluster_pcg",), key=lambda k: prof[k][0])
         ms_dom, n_dom = prof[dom]
         is_ns = args.config in ("ns2d", "ns3d", "timing3d")
         ncell = int(np.prod(wl.cells)) if is_ns else wl.units
-        per_cell = algo_bytes_per_cell(dom, wl.dim, "fp32" if is_ns else args.prec, masked=is_ns)
+        prec_b = "fp32" if is_ns else args.prec
+        if dom == "cluster_pcg":
+            # one launch runs the solve's CG iterations and refinement steps:
+            # their algorithmic bytes as if each pass moved its arrays once
+            its = statistics.mean(st["iters"] for st in step_stats)
+            outs = statistics.mean(st["outer"] for st in step_stats)
+            per_cell = its * sum(algo_bytes_per_cell(k, wl.dim, prec_b, masked=is_ns)
+                                 for k in ("down_fine", "up_fine", "p_update", "xr_update")) + \
+                outs * algo_bytes_per_cell("outer", wl.dim, prec_b, masked=is_ns)
+        else:
+            per_cell = algo_bytes_per_cell(dom, wl.dim, prec_b, masked=is_ns)
         algo = per_cell * ncell
         us = ms_dom / max(n_dom, 1) * 1e3
         achieved = algo / (us * 1e-6) / 1e9

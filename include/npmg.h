@@ -255,7 +255,9 @@ typedef enum {
   MG_K_UP_FINE = 1,     /* prolongation + correction + smoothing, finest     */
   MG_K_DOWN = 2,        /* the same on the other multi-block levels          */
   MG_K_UP = 3,
-  MG_K_COARSE = 4,      /* single-block cycle of the coarse levels           */
+  MG_K_COARSE = 4,      /* single-block cycle of the coarse levels (2D
+                           float32 V(2,2): with the middle levels, one
+                           thread-block-cluster launch)                     */
   MG_K_P_UPDATE = 5,    /* CG: p = z + beta p, Ap, (p, Ap)                   */
   MG_K_XR_UPDATE = 6,   /* CG: d += alpha p, r -= alpha Ap, ||r||            */
   MG_K_OUTER = 7,       /* float64 refinement residual                       */
@@ -263,7 +265,9 @@ typedef enum {
   MG_K_MOMENTUM = 9,
   MG_K_DIVERGENCE = 10,
   MG_K_CORRECT = 11,
-  MG_K_COUNT = 12
+  MG_K_CLUSTER_PCG = 12, /* a small 2D grid's whole CG solve after the first
+                            residual, one thread-block-cluster launch        */
+  MG_K_COUNT = 13
 } mg_kernel_class;
 mg_status mg_profile_enable(mg_handle h, int on);
 mg_status mg_profile_read(mg_handle h, double* h_ms, int64_t* h_launches, int reset);

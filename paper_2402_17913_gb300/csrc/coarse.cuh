@@ -94,14 +94,16 @@ __global__ void k_coarse_image(const __grid_constant__ CoarseArgs a, float* imag
 
 template <int DIM, typename T>
 __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* __restrict__ xout,
-                             SolveState* __restrict__ st, float* S, int total_floats) {
+                             SolveState* __restrict__ st, float* S, int total_floats, bool load_image = true) {
   // level l: X0 | X1 | B | ID, each padded
   auto G = [&](int l) { return cgeo(a.lv[l], a.off[l]); };
   auto PS = [&](const CGeo& g) { return g.WH * (g.nz + (g.nz > 1 ? 2 : 0)); };
   auto X = [&](const CGeo& g, int which) { return S + g.off + which * PS(g); };
   auto B = [&](const CGeo& g) { return S + g.off + 2 * PS(g); };
   auto ID = [&](const CGeo& g) { return S + g.off + 3 * PS(g); };
-  if (a.image) {
+  // a block that keeps the region between calls loads the constant part
+  // once: the cycle writes only the arrays' cells, never the rings or 1/diag
+  if (load_image && a.image) {
     // the constant part of the image (zero rings, inverse diagonals) comes
     // from global memory in bulk asynchronous copies
     __shared__ __align__(8) uint64_t bar;  // initialised on every call (phase 0)
@@ -124,7 +126,7 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
       }
       return;
     }
-  } else {
+  } else if (load_image) {
     coarse_fill_image<DIM>(a, S, total_floats, true);
   }
   // right-hand side of the first level

@@ -99,6 +99,59 @@ cudaError_t prepare_coarse(size_t smem_bytes);
 template <typename T>
 cudaError_t launch_coarse(const CoarseArgs& a, size_t smem_bytes, const void* b, void* x, SolveState* st,
                           cudaStream_t s);
+
+// The middle levels of a 2D V-cycle (float32, two sweeps) in one thread-block
+// cluster, with the coarse cycle of the levels below in its block 0
+// (mg_cluster2d.cu).  A distributed level in every block: three float
+// arrays (two iterate buffers, b) and one byte array (cell bytes) of
+// (R + 2) rows of W = nx + 8 entries: ghost rows 0 and R + 1, the row's
+// cells at columns 4 .. nx + 3 (16-byte aligned), zero ghost columns 3 and
+// nx + 4.
+struct CLev {
+  LevelDev L;      // weights, faces, cell bytes of the whole level (global)
+  int R;           // rows per block (even)
+  int W;           // padded row (nx + 8)
+  int off;         // float offset of the level's arrays
+  int moff;        // byte offset of its cell bytes
+  int loff;        // float offset of its diagonal table (64 d, 64 omega / d)
+  int s4, s8;      // log2 of nx / 4 and nx / 8 when powers of two, else -1
+};
+struct ClusterArgs {
+  int nlev, C;              // distributed levels (k1 .. kd-1), blocks in the cluster
+  CLev lv[kMaxLevels];
+  CoarseArgs ca;            // levels kd .. L-1, on block 0
+  int ca_off;               // float offset of the coarse cycle's region
+  int ca_floats;
+  float omega, s;
+};
+// Plan the cluster launch: the first distributed level k1, the first level
+// of the coarse cycle kd (the first level after k1 within the coarse-cell
+// limit, at least kc), the cluster size, the shared-memory bytes, and the
+// coarse cycle's level offsets (out->ca.off, out->ca.lv, out->ca.nlev).
+// False when no level qualifies.
+bool cluster2d_plan(const LevelDev* lv, int L, int kc, ClusterArgs* out, int* k1_out, int* kd_out,
+                    size_t* smem_out, size_t* ca_bytes_out);
+cudaError_t launch_cluster2d(const ClusterArgs& a, size_t smem, const float* bin, float* yout, float* bkc,
+                             float* ykc, SolveState* st, cudaStream_t s);
+// A small 2D grid's inner CG solve in one cluster launch
+// (mg_cluster_pcg2d.cu): levels 0 .. kd-1 distributed as above (a.lv[0] the
+// finest level), level 0's CG vectors beside them (r is level 0's b, z its
+// x1; two p buffers and d at pcg_off, each in level 0's padded layout).
+struct ClusterPcgArgs {
+  ClusterArgs a;
+  int pcg_off;             // float offset of p0 | p1 | d
+  int red_off;             // float offset of the reduction slots (2 x 16 float pairs)
+};
+bool cluster_pcg2d_plan(const LevelDev* lv, int L, int kc, ClusterPcgArgs* out, int* kd_out, size_t* smem_out,
+                        size_t* ca_bytes_out);
+// Set the kernel's shared-memory and cluster attributes; the number of
+// clusters of C blocks with `smem` bytes each the GPU can hold (0: none).
+int cluster_pcg2d_fit(size_t smem, size_t smem_limit, int C);
+// r0: the scaled residual the inner solve starts from; dout: its solution
+// d' (for the refinement step); st: the solve state (nothing runs when the
+// inner or the outer loop is done).
+cudaError_t launch_cluster_pcg2d(const ClusterPcgArgs& pa, size_t smem, const float* r0, float* dout, float* bkc,
+                                 float* ykc, SolveState* st, cudaStream_t s);
 template <int DIM, typename T, bool MASKED>
 cudaError_t launch_p_update(const LevelDev& L, const void* z, const void* pold, void* pnew, void* Ap,
                             SolveState* st, double* partials, cudaStream_t s);

@@ -65,6 +65,17 @@ struct mg_handle_s {
   bool t3_ok[npmg::kMaxLevels];   // 3D levels on the TMA-fed z-streaming kernels
   npmg::Tma3CgMaps t3cg;          // the finest level's CG direction update on the TMA-fed kernel
   bool t3cg_ok;
+  npmg::ClusterArgs clu;          // 2D: levels clu_k1 .. clu_kd-1 and the coarse cycle in one cluster launch
+  bool clu_ok;
+  int clu_k1, clu_kd;
+  size_t clu_smem;
+  float *clu_b, *clu_y;           // right-hand side and correction of level clu_kd (float32)
+  float* clu_image;               // constant shared-memory image of the cluster's coarse cycle
+  npmg::ClusterPcgArgs cpcg;      // 2D: the whole CG solve of a small grid in one cluster launch
+  bool cpcg_ok;
+  int cpcg_kd;
+  size_t cpcg_smem;
+  float* cpcg_image;              // its coarse cycle's constant image
   int64_t chunk_kernels;   // kernels in one graph launch
   // instrumentation
   int64_t launches;

@@ -167,7 +167,12 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
     if (k == 0) return t3ok0 ? &t30 : nullptr;
     return h->t3_ok[k] ? &h->t3maps[k] : nullptr;
   };
-  for (int k = 0; k < h->kc; ++k) {
+  // 2D float32 V-cycles: the levels clu_k1 .. clu_kd-1 and the coarse cycle
+  // of the levels below in one cluster launch (their legs are not launched
+  // one by one)
+  const bool clu = DIM == 2 && h->clu_ok;
+  const int kdown = clu ? h->clu_k1 : h->kc;
+  for (int k = 0; k < kdown; ++k) {
     LaunchScope ls(h, k == 0 ? MG_K_DOWN_FINE : MG_K_DOWN, s);
     if (k == 0)
       e = down_leg<DIM, T, M, float>(h, 0, r, tma0 ? &m0 : nullptr, t3of(0), st, s);
@@ -179,11 +184,15 @@ static cudaError_t enqueue_vcycle(mg_handle_s* h, const void* r, void* z, SolveS
   ca.finest = (h->kc == 0 && st) ? 1 : 0;
   {
     LaunchScope ls(h, MG_K_COARSE, s);
-    e = h->kc == 0 ? launch_coarse<float>(ca, h->ca_smem, r, z, st, s)
-                   : launch_coarse<T>(ca, h->ca_smem, h->bk[h->kc], h->yk[h->kc], st, s);
+    if (clu)
+      e = launch_cluster2d(h->clu, h->clu_smem, (const float*)h->bk[kdown], (float*)h->yk[kdown], h->clu_b,
+                           h->clu_y, st, s);
+    else
+      e = h->kc == 0 ? launch_coarse<float>(ca, h->ca_smem, r, z, st, s)
+                     : launch_coarse<T>(ca, h->ca_smem, h->bk[h->kc], h->yk[h->kc], st, s);
   }
   if (e != cudaSuccess) return e;
-  for (int k = h->kc - 1; k >= 0; --k) {
+  for (int k = kdown - 1; k >= 0; --k) {
     LaunchScope ls(h, k == 0 ? MG_K_UP_FINE : MG_K_UP, s);
     if (k == 0 && st)
       e = up_leg<DIM, T, M, true, float>(h, 0, r, z, tma0 ? &m0 : nullptr, t3of(0), st, s);
@@ -222,6 +231,13 @@ static cudaError_t enqueue_iteration(mg_handle_s* h, int parity, cudaStream_t s)
 }
 
 static cudaError_t enqueue_iterations(mg_handle_s* h, int count, cudaStream_t s) {
+  if (h->cpcg_ok) {
+    // a small 2D grid: the whole inner solve in one cluster launch (it
+    // returns at once when the inner solve is already done)
+    LaunchScope ls(h, MG_K_CLUSTER_PCG, s);
+    return launch_cluster_pcg2d(h->cpcg, h->cpcg_smem, (const float*)h->r, (float*)h->d, h->clu_b, h->clu_y, h->st,
+                                s);
+  }
   return dispatch(h, [&](auto dimc, auto* tp, auto mc) -> cudaError_t {
     constexpr int DIM = decltype(dimc)::value;
     using T = std::remove_pointer_t<decltype(tp)>;
@@ -652,6 +668,14 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
   plan.push_back({(void**)&h->bsave, n0c * 4});
   plan.push_back({(void**)&h->inv, (size_t)2 * h->ncoarse * h->ncoarse * 8});
   plan.push_back({(void**)&h->cimage, h->ca_smem});
+  if (dim == 2 && o.prec == MG_FP32 && kc >= 1) {
+    // the cluster path's coarse cycle starts at level kc or below: its
+    // right-hand side, correction and shared-memory image fit level kc's
+    plan.push_back({(void**)&h->clu_b, h->ncell[kc] * 4});
+    plan.push_back({(void**)&h->clu_y, h->ncell[kc] * 4});
+    plan.push_back({(void**)&h->clu_image, h->ca_smem});
+    plan.push_back({(void**)&h->cpcg_image, h->ca_smem});
+  }
   plan.push_back({(void**)&h->partials, (size_t)kMaxPartials * 8});
   plan.push_back({(void**)&h->st, sizeof(SolveState)});
   size_t total = 0;
@@ -778,6 +802,58 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
       h->t3_ok[k] = DIM == 3 && tma3d_eligible(dim, pre_e, o.post, h->lv[k]) &&
                     (k == 0 ? tma3d_encode<T, float>(&h->t3maps[0], h->lv[0], h->r, h->xk[0], h->yk[1])
                             : tma3d_encode<T, T>(&h->t3maps[k], h->lv[k], h->bk[k], h->xk[k], h->yk[k + 1]));
+    }
+    // 2D float32 V(2,2) cycles: the middle levels in one cluster launch
+    h->clu_ok = false;
+    if (DIM == 2 && std::is_same<T, float>::value && o.cycle == MG_CYCLE_V && o.pre == 2 && o.post == 2 &&
+        h->kc >= 2 && h->clu_image && e == cudaSuccess) {
+      ClusterArgs ca2;
+      size_t ca_bytes = 0;
+      if (cluster2d_plan(h->lv, h->L, h->kc, &ca2, &h->clu_k1, &h->clu_kd, &h->clu_smem, &ca_bytes) &&
+          ca_bytes <= h->ca_smem) {
+        // the coarse cycle of levels kd .. with its own constant image
+        CoarseArgs cc = h->ca;
+        cc.nlev = ca2.ca.nlev;
+        for (int l = 0; l < cc.nlev; ++l) {
+          cc.lv[l] = ca2.ca.lv[l];
+          cc.off[l] = ca2.ca.off[l];
+        }
+        cc.image = nullptr;
+        cc.finest = 0;
+        e = launch_coarse_image(cc, h->clu_image, ca_bytes, s);
+        cc.image = h->clu_image;
+        ca2.ca = cc;
+        ca2.omega = (float)o.omega;
+        ca2.s = (float)o.coarse_scale;
+        h->clu = ca2;
+        h->clu_ok = e == cudaSuccess;
+      }
+    }
+    // 2D float32 V(2,2) with the float64 refinement: a grid whose levels and
+    // CG vectors fit a cluster's shared memory solves in one launch
+    h->cpcg_ok = false;
+    if (DIM == 2 && std::is_same<T, float>::value && o.cycle == MG_CYCLE_V && o.pre == 2 && o.post == 2 &&
+        f64_iterate(h) && h->kc >= 1 && h->cpcg_image && e == cudaSuccess) {
+      ClusterPcgArgs pa;
+      size_t ca_bytes = 0;
+      if (cluster_pcg2d_plan(h->lv, h->L, h->kc, &pa, &h->cpcg_kd, &h->cpcg_smem, &ca_bytes) &&
+          ca_bytes <= h->ca_smem) {
+        CoarseArgs cc = h->ca;
+        cc.nlev = pa.a.ca.nlev;
+        for (int l = 0; l < cc.nlev; ++l) {
+          cc.lv[l] = pa.a.ca.lv[l];
+          cc.off[l] = pa.a.ca.off[l];
+        }
+        cc.image = nullptr;
+        cc.finest = 0;
+        e = launch_coarse_image(cc, h->cpcg_image, ca_bytes, s);
+        cc.image = h->cpcg_image;
+        pa.a.ca = cc;
+        pa.a.omega = (float)o.omega;
+        pa.a.s = (float)o.coarse_scale;
+        h->cpcg = pa;
+        h->cpcg_ok = e == cudaSuccess;
+      }
     }
     // the finest level's CG direction update on the TMA-fed kernel where
     // the level's legs are (NPMG_NO_TMA3D_CG keeps the marching kernel)

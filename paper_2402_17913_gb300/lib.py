@@ -42,7 +42,7 @@ GN_WGRAD_SCRATCH_MIN = 256 + 27 * 16 * 16 * 4
 GN_CONV_F32, GN_CONV_RELU, GN_CONV_DGRAD, GN_CONV_LIN = range(4)
 GN_LOSS_L2, GN_LOSS_RESIDUAL = 0, 1
 KERNEL_CLASSES = ["down_fine", "up_fine", "down", "up", "coarse", "p_update", "xr_update", "outer",
-                  "init_finish", "momentum", "divergence", "correct"]
+                  "init_finish", "momentum", "divergence", "correct", "cluster_pcg"]
 
 
 class MgOptions(ctypes.Structure):

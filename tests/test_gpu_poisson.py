@@ -207,6 +207,123 @@ def test_tma3d_kernels_on_every_level(L, shape, bc, frac, monkeypatch):
     assert abs(st["iters"] - its[0]) <= 1, (st["iters"], its)
 
 
+CLUSTER_CASES = [
+    ((256, 256), (0, 0, 0, 0), 0.0, None),
+    ((256, 512), (1, 0, 1, 1), 0.05, None),   # masked, mixed faces
+    ((128, 384), (0, 1, 0, 0), 0.08, None),   # rows of 48 and 24 cells per group pass
+    ((256, 256), (0, 0, 0, 0), 0.0, "16"),    # coarse cycle from the deepest distributable level
+    ((512, 256), (1, 0, 1, 1), 0.05, "8192"),  # coarse cycle from the single-block kernel's first level
+]
+
+
+def _cycle_launches(L, shape, bc, solid, h):
+    hdl = create(L, shape, bc, solid, h)
+    try:
+        r = torch.ones(shape, dtype=torch.float32, device="cuda")
+        z = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        n0 = L.mg_kernel_launches(hdl)
+        L.mg_precondition(hdl, r, z)
+        torch.cuda.synchronize()
+        return L.mg_kernel_launches(hdl) - n0
+    finally:
+        L.mg_destroy(hdl)
+
+
+@pytest.mark.parametrize("shape,bc,frac,coarse", CLUSTER_CASES)
+def test_cluster_middle_levels_match_oracle(L, shape, bc, frac, coarse, monkeypatch):
+    """With NPMG_CLUSTER2D=1, 2D float32 V(2,2) cycles run their middle
+    levels and the coarse cycle in one thread-block cluster launch (fewer
+    launches per cycle than the legs launched one by one): one cycle equals
+    the oracle's, full solves reach relres 1e-6 within 1e-5 of x*, and with
+    the cluster path off the solve takes the same iterations."""
+    if coarse:
+        monkeypatch.setenv("NPMG_CLUSTER_COARSE_CELLS", coarse)
+    monkeypatch.setenv("NPMG_CLUSTER2D", "1")
+    solid, h = make_case(shape, bc, frac)
+    n_cl = _cycle_launches(L, shape, bc, solid, h)
+    test_one_cycle_matches_oracle(L, shape, bc, frac)
+    b = I.blob_rhs(shape, 6, solid=solid).astype(np.float32)
+    st = solve_and_check(L, shape, bc, solid, h, b)
+    monkeypatch.setenv("NPMG_CLUSTER2D", "0")
+    n_legs = _cycle_launches(L, shape, bc, solid, h)
+    assert n_cl < n_legs, (n_cl, n_legs)
+    st0 = solve_and_check(L, shape, bc, solid, h, b)
+    assert abs(st["iters"] - st0["iters"]) <= 1 and st["outer"] == st0["outer"], (st, st0)
+
+
+WHOLE_CASES = [
+    ((256, 256), (0, 0, 0, 0), 0.0),     # config 1's grid
+    ((128, 384), (1, 0, 1, 1), 0.06),    # masked, mixed faces, rows of 96 groups
+    ((64, 64), (0, 1, 0, 0), 0.0),
+    ((48, 96), (0, 0, 1, 1), 0.08),      # 48 rows: a cluster of 8 blocks, level 0 alone distributed
+]
+
+
+def _solve_launches(L, shape, bc, solid, h, b):
+    hdl = create(L, shape, bc, solid, h)
+    try:
+        bt = dev(b)
+        xt = torch.zeros_like(bt)
+        n0 = L.mg_kernel_launches(hdl)
+        status, st = L.mg_solve(hdl, bt, xt, 1e-6)
+        return status, st, L.mg_kernel_launches(hdl) - n0, xt.cpu().numpy()
+    finally:
+        L.mg_destroy(hdl)
+
+
+@pytest.mark.parametrize("shape,bc,frac", WHOLE_CASES)
+def test_cluster_whole_solve_matches_oracle(L, shape, bc, frac, monkeypatch):
+    """A small 2D grid runs each inner CG solve in one thread-block-cluster
+    launch (the float64 refinement steps between them on all SMs): relres
+    1e-6 within 1e-5 of the converged
+    oracle, the CG iterations (within 1 or 3%) and refinement steps of the
+    kernels launched one by one, a handful of launches per solve, and the
+    same bits on a second solve."""
+    solid, h = make_case(shape, bc, frac)
+    b = I.blob_rhs(shape, 4, solid=solid).astype(np.float32)
+    st = solve_and_check(L, shape, bc, solid, h, b)
+    status, st1, n_cl, x1 = _solve_launches(L, shape, bc, solid, h, b)
+    status2, _, _, x2 = _solve_launches(L, shape, bc, solid, h, b)
+    assert status == status2 == L.MG_OK and np.array_equal(x1, x2)
+    # per refinement step: the cluster launch, the loop's condition kernels,
+    # the float64 update and residual
+    assert st1["iters"] == st["iters"] and n_cl <= 8 + 6 * st1["outer"], (n_cl, st1)
+    monkeypatch.setenv("NPMG_NO_CLUSTER_PCG", "1")
+    st0 = solve_and_check(L, shape, bc, solid, h, b)
+    _, _, n_legs, _ = _solve_launches(L, shape, bc, solid, h, b)
+    # the dot products sum in another order (block sums over the cluster
+    # instead of the grid's partials): a solve of 100 iterations may end a
+    # few iterations apart
+    assert abs(st["iters"] - st0["iters"]) <= max(1, st0["iters"] // 30), (st, st0)
+    assert st["outer"] == st0["outer"], (st, st0)
+    assert n_legs > 5 * n_cl, (n_legs, n_cl)
+
+
+def test_cluster_whole_solve_limits(L):
+    """In the cluster-launch solve the inner iteration cap ends each inner
+    solve and the refinement cap ends the solve: max_inner = 2, max_outer = 1
+    gives MG_NOT_CONVERGED after two CG iterations, with the oracle's
+    relres after two PCG iterations; a zero right-hand side returns zero
+    without iterating."""
+    shape = (256, 256)
+    h = I.poisson_spacing(shape)
+    b32 = I.blob_rhs(shape, 0).astype(np.float32)
+    b = dev(b32)
+    hdl = create(L, shape, (0, 0, 0, 0), None, h, max_inner=2, max_outer=1)
+    try:
+        x = torch.zeros_like(b)
+        status, st = L.mg_solve(hdl, b, x, 1e-6)
+        assert status == L.MG_NOT_CONVERGED and st["iters"] == 2, st
+        z = torch.zeros_like(b)
+        status0, st0 = L.mg_solve(hdl, z, x, 1e-6)
+        assert status0 == L.MG_OK and st0["iters"] == 0 and float(x.abs().max()) == 0.0
+    finally:
+        L.mg_destroy(hdl)
+    mg = P.Multigrid(P.build_hierarchy(shape, h, (0, 0, 0, 0)), s=1.0)
+    _, hist, _ = P.pcg(mg, b32.astype(np.float64), tol=1e-6, max_iters=2)
+    assert abs(st["relres"] - hist[-1]) <= 1e-4 * hist[-1], (st["relres"], hist)
+
+
 @pytest.mark.parametrize("shape,bc,frac", CASES)
 def test_sawtooth_cycle_matches_oracle(L, shape, bc, frac):
     """One cycle of the paper's sawtooth (App. B recursion; omega 2/3, two
