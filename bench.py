@@ -857,13 +857,11 @@ def run_gpu(args, rank, world):
         ncell = int(np.prod(wl.cells)) if is_ns else wl.units
         prec_b = "fp32" if is_ns else args.prec
         if dom == "cluster_pcg":
-            # one launch runs the solve's CG iterations and refinement steps:
-            # their algorithmic bytes as if each pass moved its arrays once
-            its = statistics.mean(st["iters"] for st in step_stats)
-            outs = statistics.mean(st["outer"] for st in step_stats)
+            # one launch runs an inner solve's CG iterations: their algorithmic
+            # bytes as if each pass moved its finest arrays once
+            its = statistics.mean(st["iters"] for st in step_stats) * nprof / max(n_dom, 1)
             per_cell = its * sum(algo_bytes_per_cell(k, wl.dim, prec_b, masked=is_ns)
-                                 for k in ("down_fine", "up_fine", "p_update", "xr_update")) + \
-                outs * algo_bytes_per_cell("outer", wl.dim, prec_b, masked=is_ns)
+                                 for k in ("down_fine", "up_fine", "p_update", "xr_update"))
         else:
             per_cell = algo_bytes_per_cell(dom, wl.dim, prec_b, masked=is_ns)
         algo = per_cell * ncell
@@ -1224,9 +1222,20 @@ def oracle_all_cores(spec):
     import concurrent.futures
     import multiprocessing
     procs = min(os.cpu_count() or 1, 16)
-    with concurrent.futures.ProcessPoolExecutor(procs, mp_context=multiprocessing.get_context("spawn")) as ex:
-        start_at = time.time() + 20.0 + 0.5 * procs  # time to spawn and build the samples
-        res = list(ex.map(_oracle_sample_worker, [spec] * procs, [start_at] * procs))
+    # one core per process: the BLAS and OpenMP pools of each child to one
+    # thread (spawned children read these at start)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in saved})
+    try:
+        with concurrent.futures.ProcessPoolExecutor(procs, mp_context=multiprocessing.get_context("spawn")) as ex:
+            start_at = time.time() + 20.0 + 0.5 * procs  # time to spawn and build the samples
+            res = list(ex.map(_oracle_sample_worker, [spec] * procs, [start_at] * procs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     units = sum(r[0] for r in res)
     span = max(r[2] for r in res) - min(r[1] for r in res)
     return units / span, procs

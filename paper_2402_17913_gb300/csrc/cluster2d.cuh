@@ -74,9 +74,8 @@ __device__ __forceinline__ Map tmap(int ng, int sh) {
   }
   return t;
 }
-// groups of four cells / of eight cells (the restriction's) of level v
+// groups of four cells of level v
 __device__ __forceinline__ Map tmap4(const CLev& v) { return tmap(v.L.nx >> 2, v.s4); }
-__device__ __forceinline__ Map tmap8(const CLev& v) { return tmap(v.L.nx >> 3, v.s8); }
 
 // The same array in the neighbouring blocks (null at the domain's edges).
 struct Nb {
@@ -95,6 +94,13 @@ __device__ __forceinline__ void put(float* a, const Nb& n, const CLev& v, int r,
   st4(a + (r + 1) * v.W + c, o);
   if (r == 0 && n.up) st4(n.up + (v.R + 1) * v.W + c, o);
   if (r == v.R - 1 && n.dn) st4(n.dn + c, o);
+}
+
+// The same for two cells at padded column c (8-byte aligned).
+__device__ __forceinline__ void put2(float* a, const Nb& n, const CLev& v, int r, int c, const float2& o) {
+  *reinterpret_cast<float2*>(a + (r + 1) * v.W + c) = o;
+  if (r == 0 && n.up) *reinterpret_cast<float2*>(n.up + (v.R + 1) * v.W + c) = o;
+  if (r == v.R - 1 && n.dn) *reinterpret_cast<float2*>(n.dn + c) = o;
 }
 
 // One weighted-Jacobi sweep of four cells at padded index q (16-byte
@@ -128,8 +134,9 @@ __device__ __forceinline__ void sweep(cg::cluster_group& cl, const CLev& v, cons
 
 // Residual of x1 on level l and its 2x2 average: into the next level's b,
 // with that level's first sweep from zero (x0 = (omega / d) b), or for the
-// coarse cycle into global memory (bkc, level kd).  A thread takes four
-// coarse cells: two rows of eight fine cells.
+// coarse cycle into global memory (bkc, level kd).  A thread takes two
+// coarse cells: two rows of four fine cells (a restriction thread's chain
+// of loads and sums is the phase's latency, so it is kept short).
 __device__ __forceinline__ void restrict_level(cg::cluster_group& cl, const ClusterArgs& a, int l, float* S,
                                                unsigned char* Sb, float* __restrict__ bkc, int rank, int C) {
   const CLev& v = a.lv[l];
@@ -139,45 +146,31 @@ __device__ __forceinline__ void restrict_level(cg::cluster_group& cl, const Clus
   const LPtr pc = lptr(vc, S, Sb);
   const Nb n = last ? Nb{nullptr, nullptr} : nbrs(cl, pc.x0, rank, C);
   const int W = v.W, cR = v.R / 2, cnx = v.L.nx / 2;
-  const Map t = tmap8(v);
+  const Map t = tmap4(v);
   if (t.r0 >= t.rp) return;
   const float wx = v.L.wx, wy = v.L.wy;
   for (int cr = t.r0; cr < cR; cr += t.rp) {
-    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int ay = 0; ay < 2; ++ay) {
-      const int q = (2 * cr + ay + 1) * W + kG + 8 * t.g;
-      float xc[10], xu[8], xd[8], bb[8];
-      const float4 c0 = ld4(p.x1 + q), c1 = ld4(p.x1 + q + 4);
-      const float4 u0 = ld4(p.x1 + q - W), u1 = ld4(p.x1 + q - W + 4);
-      const float4 d0 = ld4(p.x1 + q + W), d1 = ld4(p.x1 + q + W + 4);
-      const float4 b0 = ld4(p.b + q), b1 = ld4(p.b + q + 4);
-      const uint32_t m0 = ld32(p.m + q), m1 = ld32(p.m + q + 4);
-      xc[0] = p.x1[q - 1];
-      xc[1] = c0.x, xc[2] = c0.y, xc[3] = c0.z, xc[4] = c0.w;
-      xc[5] = c1.x, xc[6] = c1.y, xc[7] = c1.z, xc[8] = c1.w;
-      xc[9] = p.x1[q + 8];
-      xu[0] = u0.x, xu[1] = u0.y, xu[2] = u0.z, xu[3] = u0.w, xu[4] = u1.x, xu[5] = u1.y, xu[6] = u1.z, xu[7] = u1.w;
-      xd[0] = d0.x, xd[1] = d0.y, xd[2] = d0.z, xd[3] = d0.w, xd[4] = d1.x, xd[5] = d1.y, xd[6] = d1.z, xd[7] = d1.w;
-      bb[0] = b0.x, bb[1] = b0.y, bb[2] = b0.z, bb[3] = b0.w, bb[4] = b1.x, bb[5] = b1.y, bb[6] = b1.z, bb[7] = b1.w;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t mi = i < 4 ? m0 : m1;
-        const float dg = p.lut[nib(mi, i & 3)];
-        const float nb = wx * (xc[i] + xc[i + 2]) + wy * (xu[i] + xd[i]);
-        if (fluid(mi, i & 3)) s4[i >> 1] += bb[i] - (dg * xc[i + 1] - nb);
-      }
+      const int q = (2 * cr + ay + 1) * W + kG + 4 * t.g;
+      const float4 c = ld4(p.x1 + q), u = ld4(p.x1 + q - W), d = ld4(p.x1 + q + W), b = ld4(p.b + q);
+      const float xl = p.x1[q - 1], xr = p.x1[q + 4];
+      const uint32_t m = ld32(p.m + q);
+      if (fluid(m, 0)) s0 += b.x - (p.lut[nib(m, 0)] * c.x - (wx * (xl + c.y) + wy * (u.x + d.x)));
+      if (fluid(m, 1)) s0 += b.y - (p.lut[nib(m, 1)] * c.y - (wx * (c.x + c.z) + wy * (u.y + d.y)));
+      if (fluid(m, 2)) s1 += b.z - (p.lut[nib(m, 2)] * c.z - (wx * (c.y + c.w) + wy * (u.z + d.z)));
+      if (fluid(m, 3)) s1 += b.w - (p.lut[nib(m, 3)] * c.w - (wx * (c.z + xr) + wy * (u.w + d.w)));
     }
-    const float4 cb = make_float4(0.25f * s4[0], 0.25f * s4[1], 0.25f * s4[2], 0.25f * s4[3]);
+    const float2 cb = make_float2(0.25f * s0, 0.25f * s1);
     if (last) {
-      st4(bkc + (size_t)(rank * cR + cr) * cnx + 4 * t.g, cb);
+      *reinterpret_cast<float2*>(bkc + (size_t)(rank * cR + cr) * cnx + 2 * t.g) = cb;
     } else {
-      const int c = kG + 4 * t.g, qc = (cr + 1) * vc.W + c;
-      st4(pc.b + qc, cb);
-      const uint32_t mc = ld32(pc.m + qc);
+      const int c2 = kG + 2 * t.g, qc = (cr + 1) * vc.W + c2;
+      *reinterpret_cast<float2*>(pc.b + qc) = cb;
+      const uint32_t mc = *reinterpret_cast<const uint16_t*>(pc.m + qc);
       const float* w = pc.lut + 64;
-      put(pc.x0, n, vc, cr, c,
-          make_float4(w[nib(mc, 0)] * cb.x, w[nib(mc, 1)] * cb.y, w[nib(mc, 2)] * cb.z, w[nib(mc, 3)] * cb.w));
+      put2(pc.x0, n, vc, cr, c2, make_float2(w[nib(mc, 0)] * cb.x, w[nib(mc, 1)] * cb.y));
     }
   }
 }

@@ -230,24 +230,43 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
     }
     if (k) cur |= 1u << l;
   } else {
+    // GB300 runs float64 at 1/64 of the float32 rate: one float64 warp
+    // instruction holds its sub-partition's pipe for 64 cycles.  So the
+    // products use four warps (one per sub-partition) with every lane busy:
+    // thread (row i, chunk q) sums the columns of chunk q (Q chunks of K
+    // columns per row, Q up to 128 / n and 32), and the Q partial sums of a
+    // row, in adjacent lanes, add up by shuffles: a third to a quarter of
+    // the float64 instructions of one warp per row with a lane-strided sum
+    // and a 32-lane tree (measured time-neutral on GB300: the coarse block
+    // is bound by its phases' latency).
     const CGeo c = G(a.nlev - 1);
     const int n = a.ncoarse;
     float* xc = X(c, 0);
     const float* bc = B(c);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < n; i += nw) {
-      double acc = 0.0;
-      // the inverse of the symmetric operator is symmetric: read row i
-      for (int j = lane; j < n; j += 32) {
-        int x, y, z;
-        c.xyz(j, x, y, z);
-        acc += a.inv[(size_t)i * n + j] * (double)bc[c.pad(x, y, z)];
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        int x, y, z;
-        c.xyz(i, x, y, z);
-        xc[c.pad(x, y, z)] = (float)acc;
+    const int nt = blockDim.x >= 128 ? 128 : (int)(blockDim.x & ~31u);  // whole warps
+    int Q = 1;
+    while (Q < 32 && 2 * Q * n <= nt) Q *= 2;
+    const int K = (n + Q - 1) / Q, pass = nt / Q;
+    if ((int)threadIdx.x < nt) {
+      const int q = threadIdx.x & (Q - 1), ri = threadIdx.x / Q;
+      for (int i0 = 0; i0 < n; i0 += pass) {
+        const int i = i0 + ri;
+        double acc = 0.0;
+        if (i < n) {
+          // the inverse of the symmetric operator is symmetric: read row i
+          const int j1 = min(n, (q + 1) * K);
+          for (int j = q * K; j < j1; ++j) {
+            int x, y, z;
+            c.xyz(j, x, y, z);
+            acc = fma(a.inv[(size_t)i * n + j], (double)bc[c.pad(x, y, z)], acc);
+          }
+        }
+        for (int o = Q >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < n && q == 0) {
+          int x, y, z;
+          c.xyz(i, x, y, z);
+          xc[c.pad(x, y, z)] = (float)acc;
+        }
       }
     }
     __syncthreads();

@@ -114,7 +114,7 @@ struct CLev {
   int off;         // float offset of the level's arrays
   int moff;        // byte offset of its cell bytes
   int loff;        // float offset of its diagonal table (64 d, 64 omega / d)
-  int s4, s8;      // log2 of nx / 4 and nx / 8 when powers of two, else -1
+  int s4;          // log2 of nx / 4 when a power of two, else -1
 };
 struct ClusterArgs {
   int nlev, C;              // distributed levels (k1 .. kd-1), blocks in the cluster
@@ -181,7 +181,9 @@ struct SolveParams {
 // f64: the iterate x is a float64 array (else float-float pairs).
 cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, void* x, double c, SolveParams prm,
                         SolveState* st, double* partials, cudaStream_t s, bool f64);
-cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s,
+// xb != nullptr: the iterate is in x when the state's `cur` is 0, else in xb
+// (after the device-side loop, which flips `cur`).
+cudaError_t launch_finish(size_t n, void* x, void* xb, float* out, const SolveState* st, int nblocks, cudaStream_t s,
                           bool f64);
 cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, cudaStream_t s, bool f64);
 

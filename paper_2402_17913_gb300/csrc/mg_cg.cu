@@ -848,8 +848,9 @@ cudaError_t launch_init(const LevelDev& L, const float* b, const float* xguess, 
 // hi + lo; float64: the value); a zero right-hand side has the zero
 // solution.
 template <bool F64>
-__global__ void k_finish(size_t n, void* __restrict__ xv_, float* __restrict__ out,
+__global__ void k_finish(size_t n, void* __restrict__ xa_, void* __restrict__ xb_, float* __restrict__ out,
                          const SolveState* __restrict__ st) {
+  void* xv_ = (xb_ && st->cur) ? xb_ : xa_;
   float2* x = (float2*)xv_;
   double* x64 = (double*)xv_;
   const bool zero = st->bnorm2 == 0.0;
@@ -867,10 +868,10 @@ __global__ void k_finish(size_t n, void* __restrict__ xv_, float* __restrict__ o
   }
 }
 
-cudaError_t launch_finish(size_t n, void* x, float* out, const SolveState* st, int nblocks, cudaStream_t s,
+cudaError_t launch_finish(size_t n, void* x, void* xb, float* out, const SolveState* st, int nblocks, cudaStream_t s,
                           bool f64) {
-  if (f64) k_finish<true><<<nblocks, 256, 0, s>>>(n, x, out, st);
-  else k_finish<false><<<nblocks, 256, 0, s>>>(n, x, out, st);
+  if (f64) k_finish<true><<<nblocks, 256, 0, s>>>(n, x, xb, out, st);
+  else k_finish<false><<<nblocks, 256, 0, s>>>(n, x, xb, out, st);
   return cudaGetLastError();
 }
 

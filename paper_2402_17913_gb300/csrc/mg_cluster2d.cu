@@ -109,7 +109,6 @@ static size_t cluster_layout(ClusterArgs& a, const LevelDev* lv, int k1, int kd,
     f += 128;
     auto lg = [](int n) { return n > 0 && (n & (n - 1)) == 0 ? __builtin_ctz((unsigned)n) : -1; };
     v.s4 = lg(lv[k].nx / 4);
-    v.s8 = lg(lv[k].nx / 8);
   }
   if (extra_off) *extra_off = (int)f;
   f += (extra + 3) / 4 * 4;

@@ -21,9 +21,9 @@
 // cycle's first sweep of level 0 from r.  Each reduction is a block sum
 // stored into every block's slot array, one cluster barrier, and the 16
 // slots summed in the same order in every block, so every block takes the
-// same decisions (the logic of the separate kernels, `inner_decide`, on a
-// per-block copy of the solve state; the scalars alpha and beta in float32,
-// as the vector kernels use them).
+// same decisions (the test of the separate kernels' `inner_decide`, on a
+// per-block copy of the solve state; the scalars alpha and beta and the
+// convergence test in float32).
 #include <math.h>
 
 #include "cluster2d.cuh"
@@ -64,12 +64,11 @@ __device__ __forceinline__ void push_ff(cg::cluster_group& cl, ff v, float2* slo
 }
 
 // Warp 0: the sum of the slots in a fixed order (the same value in every
-// block); returned as float64 in thread 0.
-__device__ __forceinline__ double slots_total(const float2* slots, int C) {
+// block), in lane 0.
+__device__ __forceinline__ ff slots_total(const float2* slots, int C) {
   const int lane = threadIdx.x & 31;
   const float2 q = lane < C ? slots[lane] : make_float2(0.f, 0.f);
-  const ff t = warp_sum_ff({q.x, q.y});
-  return (double)t.hi + (double)t.lo;
+  return warp_sum_ff({q.x, q.y});
 }
 
 // Level 0's first sweep from zero, x0 = (omega / d) r, ghost rows stored.
@@ -223,7 +222,6 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_pcg2d(const __grid_constant_
   __shared__ SolveState sst;   // this block's copy of the solve state
   __shared__ SolveState cst;   // block 0: the coarse cycle's timeout report
   __shared__ float2 wsum[32];
-  __shared__ float fscal[2];   // beta and alpha as float32
   float2* slots = reinterpret_cast<float2*>(S + pa.red_off);
   if (threadIdx.x == 0) {
     sst = *st;
@@ -263,54 +261,73 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_pcg2d(const __grid_constant_
   int par = 0, set = 0;
   bool load = true;
   // block sums into the slots, one cluster barrier; the total in thread 0
-  auto reduce = [&](ff v) -> double {
+  auto reduce = [&](ff v) -> float {
     float2* sl = slots + 16 * set;
     push_ff(cl, v, sl, wsum, rank, C);
     cl.sync();
     set ^= 1;
-    double t = 0.0;
-    if (threadIdx.x < 32) t = slots_total(sl, C);
-    return t;
+    const ff t = slots_total(sl, C);
+    return __shfl_sync(0xffffffffu, t.hi + t.lo, 0);
   };
-  float rzf = 0.f, rzf_old = 0.f;  // thread 0: (r, z) of this and the last iteration
-  unsigned guard = 0;
-  const unsigned cap = (unsigned)sst.max_inner + 2u;
-  while (!sst.inner_done && !sst.outer_done) {
+  // Every thread runs the inner loop's control itself, in float32, on the
+  // totals every warp sums from the slots (the same values in every thread
+  // of every block; no block barrier or float64 operation between two
+  // cluster barriers): beta, alpha, and the test of inner_decide with its
+  // bounds rounded once, ||r||^2 <= eta^2 ||r_0||^2 (converged) and
+  // > 1e12 ||r_0||^2 or not finite (diverged).  Thread 0 writes the state
+  // at the end.
+  __shared__ float bounds[2];
+  if (threadIdx.x == 0) {
+    bounds[0] = (float)(sst.eta * sst.eta * sst.r0norm2);
+    bounds[1] = (float)(1e12 * sst.r0norm2);
+  }
+  __syncthreads();
+  const bool krylov = sst.krylov != 0;
+  bool first = sst.first != 0, diverged = false;
+  int it = sst.it, done_its = 0;
+  float rz = 0.f, rz_old = 0.f, pAp = 0.f, r2 = 0.f, alpha = 0.f, beta = 0.f;
+  for (bool more = !sst.inner_done && !sst.outer_done; more;) {
     // z = M r
     vcycle_body(cl, a, S, Sb, bkc, ykc, rank == 0 ? &cst : nullptr, rank, C, keep, load);
     load = false;
     const bool tmo = rank == 0 && cst.status == MG_TIMEOUT;
     const float rzp = sweep_z(cl, v0, p0, keep, rank, C);
-    double tot = reduce({tmo ? __int_as_float(0x7fc00000) : rzp, 0.f});
-    // the CG scalars in float32 (the kernels use them as float32; the
-    // totals stay float64 in the state)
-    const bool pfirst = sst.first || !sst.krylov;
-    if (threadIdx.x == 0) {
-      rzf = (float)tot;
-      const float beta = pfirst ? 0.f : rzf / rzf_old;
-      rzf_old = rzf;
-      sst.rz = sst.rz_old = tot;
-      sst.beta = beta;
-      fscal[0] = beta;
-    }
-    __syncthreads();
+    rz = reduce({tmo ? __int_as_float(0x7fc00000) : rzp, 0.f});
+    const bool pfirst = first || !krylov;
+    beta = pfirst ? 0.f : rz / rz_old;
+    rz_old = rz;
     // p = z + beta p, A' p, alpha
-    tot = reduce({p_update(cl, v0, p0, P0 + par * P, P0 + (1 - par) * P, fscal[0], pfirst, rank, C), 0.f});
-    if (threadIdx.x == 0) {
-      const float alpha = sst.krylov ? rzf / (float)tot : 1.f;
-      sst.pAp = tot;
-      sst.alpha = alpha;
-      fscal[1] = alpha;
-    }
-    __syncthreads();
+    pAp = reduce({p_update(cl, v0, p0, P0 + par * P, P0 + (1 - par) * P, beta, pfirst, rank, C), 0.f});
+    alpha = krylov ? rz / pAp : 1.f;
     // d += alpha p, r -= alpha A' p, ||r||^2, the next cycle's first sweep
-    tot = reduce({xr_update(cl, v0, p0, P0 + (1 - par) * P, D, fscal[1], sst.first != 0, rank, C), 0.f});
-    if (threadIdx.x == 0) {
-      inner_decide(&sst, tot);
-      if (++guard > cap) sst.inner_done = 1;
-    }
-    __syncthreads();
+    r2 = reduce({xr_update(cl, v0, p0, P0 + (1 - par) * P, D, alpha, first, rank, C), 0.f});
+    first = false;
+    ++it;
+    ++done_its;
     par ^= 1;
+    if (!(r2 <= bounds[1])) {  // not finite, or blown up
+      diverged = true;
+      more = false;
+    } else if (r2 <= bounds[0] || it >= sst.max_inner || done_its > sst.max_inner + 1) {
+      more = false;
+    }
+  }
+  if (threadIdx.x == 0) {
+    sst.it = it;
+    sst.iters_total += done_its;
+    if (done_its > 0) {
+      sst.first = 0;
+      sst.inner_done = 1;
+      sst.rnorm2 = (double)r2;
+      sst.rz = sst.rz_old = (double)rz;
+      sst.pAp = (double)pAp;
+      sst.beta = (double)beta;
+      sst.alpha = (double)alpha;
+    }
+    if (diverged) {
+      sst.status = MG_DIVERGED;
+      sst.outer_done = 1;
+    }
   }
   // the inner solution d' for the refinement step, and the state
   {

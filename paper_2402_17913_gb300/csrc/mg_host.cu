@@ -411,9 +411,22 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     NPMG_CUDA(launch_init(h->lv[0], b, x, h->xff[h->cur64], h->c, prm, h->st, h->partials, s, f64_iterate(h)));
   }
   NPMG_CUDA(enqueue_outer(h, b, false, s));
-  NPMG_CUDA(read_state(h, s));
-  const double guess_relres = h->st_host->relres0;
-  const bool rejected = h->guess_check && !h->st_host->outer_done && guess_relres > 1.0;
+  const bool graph = h->use_graph && !h->prof;
+  if (graph) NPMG_CUDA(ensure_graph(h, s));
+  if (graph && h->loop_state == 0) {
+    // on failure (for instance a driver without conditional nodes) the host
+    // loop below runs the same kernels
+    h->loop_state = getenv("NPMG_NO_DEVICE_LOOP") == nullptr && build_loop_graph(h) == cudaSuccess ? 1 : -1;
+    cudaGetLastError();
+  }
+  const bool device_loop = graph && h->loop_state == 1;
+  // the device-side loop reads the state itself (it skips its body when
+  // the first residual already meets the tolerance): without a guess to
+  // check, a solve synchronises with the host once, at the end
+  const bool one_sync = device_loop && !h->guess_check;
+  if (!one_sync) NPMG_CUDA(read_state(h, s));
+  const double guess_relres = one_sync ? 0.0 : h->st_host->relres0;
+  const bool rejected = !one_sync && h->guess_check && !h->st_host->outer_done && guess_relres > 1.0;
   if (rejected) {
     // the guess is worse than zero: the plain solve from x = 0 takes over
     {
@@ -424,28 +437,19 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     NPMG_CUDA(enqueue_outer(h, b, false, s));
     NPMG_CUDA(read_state(h, s));
   }
-  const bool graph = h->use_graph && !h->prof;
-  if (graph) NPMG_CUDA(ensure_graph(h, s));
-  if (graph && h->loop_state == 0) {
-    // on failure (for instance a driver without conditional nodes) the host
-    // loop below runs the same kernels
-    h->loop_state = getenv("NPMG_NO_DEVICE_LOOP") == nullptr && build_loop_graph(h) == cudaSuccess ? 1 : -1;
-    cudaGetLastError();
-  }
-  if (graph && h->loop_state == 1 && !h->st_host->outer_done) {
+  bool looped = false;
+  if (device_loop && (one_sync || !h->st_host->outer_done)) {
     NPMG_CUDA(cudaMemcpyAsync(h->bsave, b, h->ncell[0] * sizeof(float), cudaMemcpyDeviceToDevice, s));
     NPMG_CUDA(launch_loop_set_cur(h->st, h->cur64, s));
     NPMG_CUDA(cudaGraphLaunch(h->loop_exec, s));
-    NPMG_CUDA(read_state(h, s));
-    h->cur64 = h->st_host->cur;
-    // per outer body: the inner condition, the refinement step (two kernels
-    // with the float64 iterate: update and residual) and the outer condition
-    const int64_t per_outer = f64_iterate(h) ? 4 : 3;
-    h->launches += 2 + per_outer * (int64_t)h->st_host->loop_outer +
-                   (h->loop_kernels + 1) * (int64_t)h->st_host->loop_bodies;
+    looped = true;
+    if (!one_sync) {
+      NPMG_CUDA(read_state(h, s));
+      h->cur64 = h->st_host->cur;
+    }
   }
   int guard = 0;
-  while (!h->st_host->outer_done && guard < 4 * (o.max_outer + 1)) {
+  while (!looped && !h->st_host->outer_done && guard < 4 * (o.max_outer + 1)) {
     ++guard;
     int launched = 0;
     for (;;) {
@@ -464,11 +468,23 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     NPMG_CUDA(read_state(h, s));
   }
   {
+    // after the one-sync device loop the state's `cur` names the buffer
+    // (0: xff[0], 1: xff[1])
     LaunchScope ls(h, MG_K_INIT_FINISH, s);
-    NPMG_CUDA(launch_finish(h->ncell[0], h->xff[h->cur64], x, h->st, h->nb1d, s, f64_iterate(h)));
+    const bool dyn = one_sync && looped;
+    NPMG_CUDA(launch_finish(h->ncell[0], dyn ? h->xff[0] : h->xff[h->cur64], dyn ? h->xff[1] : nullptr, x, h->st,
+                            h->nb1d, s, f64_iterate(h)));
   }
   NPMG_CUDA(cudaEventRecord(h->ev1, s));
   NPMG_CUDA(read_state(h, s));
+  if (looped) {
+    if (one_sync) h->cur64 = h->st_host->cur;
+    // per outer body: the inner condition, the refinement step (two kernels
+    // with the float64 iterate: update and residual) and the outer condition
+    const int64_t per_outer = f64_iterate(h) ? 4 : 3;
+    h->launches += 2 + per_outer * (int64_t)h->st_host->loop_outer +
+                   (h->loop_kernels + 1) * (int64_t)h->st_host->loop_bodies;
+  }
   const SolveState& st = *h->st_host;
   mg_status status = (mg_status)st.status;
   if (!st.outer_done && status == MG_OK) status = MG_NOT_CONVERGED;
@@ -485,7 +501,7 @@ mg_status run_solve(mg_handle_s* h, const float* b, float* x, double tol, cudaSt
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     out->ms = ms;
     for (int k = 0; k < kHistory && k < 32; ++k) out->history[k] = st.hist[k];
-    out->guess_relres = guess_relres;
+    out->guess_relres = one_sync ? st.relres0 : guess_relres;
     out->guess_rejected = rejected ? 1 : 0;
   }
   return status;
