@@ -230,20 +230,19 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
     }
     if (k) cur |= 1u << l;
   } else {
-    // GB300 runs float64 at 1/64 of the float32 rate: one float64 warp
-    // instruction holds its sub-partition's pipe for 64 cycles.  So the
-    // products use four warps (one per sub-partition) with every lane busy:
-    // thread (row i, chunk q) sums the columns of chunk q (Q chunks of K
-    // columns per row, Q up to 128 / n and 32), and the Q partial sums of a
-    // row, in adjacent lanes, add up by shuffles: a third to a quarter of
-    // the float64 instructions of one warp per row with a lane-strided sum
-    // and a 32-lane tree (measured time-neutral on GB300: the coarse block
-    // is bound by its phases' latency).
+    // Thread (row i, chunk q) sums the columns of chunk q (Q chunks of K
+    // columns per row, Q a power of two up to 32 with Q n <= the block's
+    // threads), and the Q partial sums of a row, in adjacent lanes, add up
+    // by shuffles: the dependent chain of float64 operations is K + log2 Q
+    // (GB300 runs float64 at 1/64 of the float32 rate and with a long
+    // latency, so the coarse block waits on that chain; with four warps, or
+    // with one warp per row and a 32-lane tree, the chain was 2-7 times as
+    // long for the 128-cell coarsest level of the 3D flow step).
     const CGeo c = G(a.nlev - 1);
     const int n = a.ncoarse;
     float* xc = X(c, 0);
     const float* bc = B(c);
-    const int nt = blockDim.x >= 128 ? 128 : (int)(blockDim.x & ~31u);  // whole warps
+    const int nt = (int)(blockDim.x & ~31u);  // whole warps
     int Q = 1;
     while (Q < 32 && 2 * Q * n <= nt) Q *= 2;
     const int K = (n + Q - 1) / Q, pass = nt / Q;
