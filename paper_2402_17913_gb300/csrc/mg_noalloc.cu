@@ -24,9 +24,14 @@
 //
 // Every call shares the one array and leaves its contents behind; nothing in
 // the cycle reads a value that an earlier call left (each buffer is written
-// before it is read), so no clearing is needed.  Calls that overlap on the
-// GPU (different streams, or several host threads) race on the array: the
-// caller must serialise them.
+// before it is read), so no clearing is needed -- except the set-up of an
+// unmasked call: when the previous call on the device had no mask and the
+// same geometry (sizes, spacings, faces, level counts), the coarsest-level
+// inverse and the coarse block's image it left in the array are used again
+// (the set-up was 66-87% of a call's time on 64^2 to 64^3 grids).  A masked
+// call always builds its set-up (the mask's contents may have changed).
+// Calls that overlap on the GPU (different streams, or several host
+// threads) race on the array: the caller must serialise them.
 #include <mutex>
 #include <string.h>
 
@@ -44,6 +49,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 static unsigned char* g_scratch_ptr[kMaxDevices];
 static std::mutex g_scratch_mutex;
+
+// The geometry of the last unmasked call's set-up on each device (valid
+// while no masked or failed call came since).
+struct SetupKey {
+  int dim, L, kc, bcD;
+  int64_t n[3];
+  double h[3];
+};
+static SetupKey g_setup_key[kMaxDevices];
+static bool g_setup_valid[kMaxDevices];
 
 // Set-up of the current device, done once: the array's device address and
 // the shared-memory opt-in of every kernel variant of the cycle.
@@ -220,7 +235,23 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
     lv[k].bcD = bcD;
     lv[k].cell = masked ? cell[k] : nullptr;
   }
-  // hierarchy of the mask and the coarsest inverse (rebuilt every call)
+  SetupKey key;
+  memset(&key, 0, sizeof(key));
+  key.dim = dim;
+  key.L = L;
+  key.kc = kc;
+  key.bcD = bcD;
+  for (int a = 0; a < 3; ++a) {
+    key.n[a] = n0[a];
+    key.h[a] = a < dim ? spacing[a] : 1.0;
+  }
+  bool reuse = false;
+  if (dev >= 0 && dev < kMaxDevices) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    reuse = !masked && g_setup_valid[dev] && memcmp(&key, &g_setup_key[dev], sizeof(key)) == 0;
+    g_setup_valid[dev] = false;  // set again below once this call is enqueued
+  }
+  // hierarchy of the mask and the coarsest inverse
   if (masked) {
     for (int k = 1; k < L; ++k)
       NPMG_CUDA(launch_coarsen_solid(dim, nk[k - 1], k == 1 ? d_solid : solid[k - 1], solid[k], s));
@@ -230,7 +261,7 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
     const double hk[3] = {spacing[0] * (1 << (L - 1)), spacing[1] * (1 << (L - 1)),
                           dim == 3 ? spacing[2] * (1 << (L - 1)) : 1.0};
     const double wd[3] = {c / (hk[0] * hk[0]), c / (hk[1] * hk[1]), dim == 3 ? c / (hk[2] * hk[2]) : 0.0};
-    NPMG_CUDA(launch_coarse_inverse(dim, nk[L - 1], wd, bcD, masked ? cell[L - 1] : nullptr, inv, s));
+    if (!reuse) NPMG_CUDA(launch_coarse_inverse(dim, nk[L - 1], wd, bcD, masked ? cell[L - 1] : nullptr, inv, s));
   }
   CoarseArgs ca;
   memset(&ca, 0, sizeof(ca));
@@ -248,7 +279,7 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   ca.s = (float)o.coarse_scale;
   ca.finest = 0;
   ca.image = nullptr;
-  NPMG_CUDA(launch_coarse_image(ca, image, moff, s));
+  if (!reuse) NPMG_CUDA(launch_coarse_image(ca, image, moff, s));
   ca.image = image;
   const float om = (float)o.omega, sc = (float)o.coarse_scale;
   auto cycle = [&](auto dimc, auto mc) -> cudaError_t {
@@ -277,6 +308,11 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   if (e != cudaSuccess) {
     set_error("mg_vcycle_noalloc: %s", cudaGetErrorString(e));
     return MG_ERR_CUDA;
+  }
+  if (!masked && dev >= 0 && dev < kMaxDevices) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    g_setup_key[dev] = key;
+    g_setup_valid[dev] = true;
   }
   return MG_OK;
 }

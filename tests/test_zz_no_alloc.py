@@ -62,6 +62,34 @@ def test_noalloc_cycle_matches_handle_cycle_twice(L, shape, bc, frac, sweeps):
         L.mg_destroy(hdl)
 
 
+def test_noalloc_reused_setup_follows_the_geometry(L):
+    """An unmasked call reuses the set-up (coarsest inverse, coarse image)
+    the previous call left only for the same geometry: a sequence that
+    changes shape, spacing, faces and mask between calls, and comes back,
+    matches the handle cycle at every call."""
+    seq = [((64, 64), (0, 0, 0, 0), None), ((64, 64), (0, 0, 0, 0), None), ((96, 128), (0, 0, 0, 0), None),
+           ((64, 64), (0, 0, 0, 0), None), ((64, 64), (0, 1, 0, 0), None), ((64, 64), (0, 0, 0, 0), 0.08),
+           ((64, 64), (0, 0, 0, 0), None), ((64, 64), (0, 0, 0, 0), "h")]
+    for i, (shape, bc, frac) in enumerate(seq):
+        rng = np.random.default_rng(40 + i)
+        solid = I.flood_fill_unreachable(rng.random(shape) < frac, bc) if isinstance(frac, float) else None
+        h = tuple((0.5 if frac == "h" else 1.0) / (s + 1) for s in reversed(shape))
+        xyz = tuple(reversed(shape))
+        sol = None if solid is None else torch.from_numpy(solid.astype(np.uint8)).cuda()
+        hdl = L.mg_create(len(shape), xyz, h, bc, sol, L.default_options())
+        try:
+            r = torch.from_numpy(I.blob_rhs(shape, 50 + i, solid=solid).astype(np.float32)).cuda()
+            z_ref = torch.zeros_like(r)
+            z = torch.full_like(r, float("nan"))
+            L.mg_precondition(hdl, r, z_ref)
+            L.mg_vcycle_noalloc(len(shape), xyz, h, bc, r, z, solid=sol)
+            torch.cuda.synchronize()
+            err = (torch.linalg.norm(z.double() - z_ref.double()) / torch.linalg.norm(z_ref.double())).item()
+            assert err <= RTOL, (i, shape, bc, frac, err)
+        finally:
+            L.mg_destroy(hdl)
+
+
 def test_noalloc_rejects_a_coarsest_level_beyond_the_limit(L):
     """Two levels on 64^2 leave a 32^2 coarsest level (1024 cells > 256)."""
     x = torch.zeros(64 * 64, dtype=torch.float32, device="cuda")
