@@ -607,7 +607,9 @@ struct GP {
   static constexpr int MBY = MASKED ? WM * RY : 0;
   static constexpr int OZ = 0, OP = al128(ZB), OM = al128(OP + ZB);
   static constexpr int STAGE = al128(OM + MBY);
-  static constexpr int NS = 6;                     // TMA stages
+  // TMA stages: three, so that two blocks fit an SM (the kernel needs fewer
+  // than 96 registers; twice the warps hide the per-plane barrier)
+  static constexpr int NS = 3;
   static constexpr int RING = 2 * PL * 4;          // one plane buffer of two slots
   static constexpr int LUT = RING + NS * STAGE;
   static constexpr int BAR = LUT + 128 * 4;
@@ -630,7 +632,7 @@ __device__ __forceinline__ void issue_pz(Ring<N>& R, const CUtensorMap* mz, cons
 }
 
 template <bool MASKED, bool STORE_AP>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
     k_pup_t3(const __grid_constant__ CUtensorMap mz, const __grid_constant__ CUtensorMap mp,
              const __grid_constant__ CUtensorMap mm, LevelDev L, float* __restrict__ pnew, float* __restrict__ Ap,
              Sched sc, SolveState* __restrict__ st, double* __restrict__ partials) {
@@ -928,10 +930,11 @@ struct T3Plan {
   dim3 grid;
 };
 
-static T3Plan t3_plan(const LevelDev& L) {
+// bps: blocks of the kernel an SM holds at once.
+static T3Plan t3_plan(const LevelDev& L, int bps = 1) {
   const long strips = (L.nx + TX - 1) / TX, tiles = (L.ny + TY - 1) / TY;
   const long cols = strips * tiles;
-  const long nsm = t3_sms();
+  const long nsm = (long)t3_sms() * bps;
   long best = -1, best_zr = L.nz;
   for (int runs = 1; runs <= L.nz / 2; ++runs) {
     int zr = (L.nz + runs - 1) / runs;
@@ -1039,7 +1042,7 @@ bool tma3d_encode_cg(Tma3CgMaps* out, const LevelDev& L, const float* z, const f
 template <bool MASKED>
 cudaError_t launch_p_update_t3(const Tma3CgMaps& m, int parity, const LevelDev& L, float* pnew, float* Ap,
                                bool store_ap, SolveState* st, double* partials, cudaStream_t s) {
-  const T3Plan pl = t3_plan(L);
+  const T3Plan pl = t3_plan(L, 2);
   if (store_ap)
     return launch_chain(k_pup_t3<MASKED, true>, pl.grid, NT, (size_t)GP<MASKED>::BYTES, s, m.z, m.p[parity], m.m, L,
                         pnew, Ap, pl.sc, st, partials);
