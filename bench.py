@@ -1155,11 +1155,29 @@ def main():
     if want_check:
         import concurrent.futures
         import multiprocessing
-        pool = concurrent.futures.ProcessPoolExecutor(1, mp_context=multiprocessing.get_context("spawn"))
-        fut = pool.submit(oracle_reference, args.config, args.stencil == "fe")
+        # the worker's BLAS and OpenMP pools held to a few threads, so that it
+        # leaves the host cores that drive the GPU alone (spawned children
+        # read these at start)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        os.environ.update({k: "2" for k in saved})
+        try:
+            pool = concurrent.futures.ProcessPoolExecutor(1, mp_context=multiprocessing.get_context("spawn"))
+            fut = pool.submit(oracle_reference, args.config, args.stencil == "fe")
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     out, wl = run_gpu(args, rank, world)
     check = out.pop("_check", None)
     if rank == 0:
+        ref = None
+        if fut is not None:
+            # wait for the worker before the CPU baseline is timed, so that
+            # the two do not share the host cores
+            ref = fut.result()
+            pool.shutdown()
         if not args.no_cpu_baseline and world == 1 and not args.only_timed:
             spec = sample_spec(args)
             rate, sample, n = oracle_step_time(cpu_sample(spec), budget_s=25.0, max_steps=spec["max_steps"])
@@ -1174,8 +1192,7 @@ def main():
                                            sample=sample + "; seconds scaled to the full size by cells")
                 out["cpu_baseline"]["all_cores"].update(value=5 * wl.units / agg, unit="s")
         if fut is not None:
-            out["oracle_check"] = compare_with_oracle(args.config, check, fut.result(), args.stencil == "fe")
-            pool.shutdown()
+            out["oracle_check"] = compare_with_oracle(args.config, check, ref, args.stencil == "fe")
         print(json.dumps(out))
 
 

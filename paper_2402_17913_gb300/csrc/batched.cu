@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const __grid_constant__ B
         if (A.st[w].inner_done) continue;
         const BInst& I = A.inst[w];
         __syncthreads();
-        coarse_cycle<2, float>(I.ca, I.kc == 0 ? I.r : I.b[I.kc], I.kc == 0 ? I.z : I.y[I.kc], nullptr, S,
+        coarse_cycle<2, float, false>(I.ca, I.kc == 0 ? I.r : I.b[I.kc], I.kc == 0 ? I.z : I.y[I.kc], nullptr, S,
                                I.cfloats);
       }
       if (!grid_barrier(A, epoch)) return;

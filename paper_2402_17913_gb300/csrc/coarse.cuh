@@ -92,7 +92,9 @@ __global__ void k_coarse_image(const __grid_constant__ CoarseArgs a, float* imag
   coarse_fill_image<DIM>(a, image, total_floats, false);
 }
 
-template <int DIM, typename T>
+// PREFETCH: load the first level's right-hand side while the image is in
+// flight (callers with few registers to spare turn it off).
+template <int DIM, typename T, bool PREFETCH = true>
 __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* __restrict__ xout,
                              SolveState* __restrict__ st, float* S, int total_floats, bool load_image = true) {
   // level l: X0 | X1 | B | ID, each padded
@@ -101,6 +103,16 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
   auto X = [&](const CGeo& g, int which) { return S + g.off + which * PS(g); };
   auto B = [&](const CGeo& g) { return S + g.off + 2 * PS(g); };
   auto ID = [&](const CGeo& g) { return S + g.off + 3 * PS(g); };
+  // the first two float4 of this thread's share of the right-hand side are
+  // loaded before the wait for the image, so that the two global latencies
+  // overlap
+  const CGeo g0 = G(0);
+  const bool vec = (g0.nx & 3) == 0 && std::is_same<T, float>::value;
+  const int n4 = vec ? g0.n / 4 : 0;
+  const int i40 = (int)threadIdx.x, i41 = i40 + (int)blockDim.x;
+  float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
+  if (PREFETCH && i40 < n4) pre0 = reinterpret_cast<const float4*>(bin)[i40];
+  if (PREFETCH && i41 < n4) pre1 = reinterpret_cast<const float4*>(bin)[i41];
   // a block that keeps the region between calls loads the constant part
   // once: the cycle writes only the arrays' cells, never the rings or 1/diag
   if (load_image && a.image) {
@@ -131,13 +143,14 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
   }
   // right-hand side of the first level
   {
-    const CGeo g = G(0);
+    const CGeo g = g0;
     float* b0 = B(g);
-    if ((g.nx & 3) == 0 && std::is_same<T, float>::value) {
-      const int n4 = g.n / 4;
+    if (vec) {
 #pragma unroll 2
       for (int i4 = threadIdx.x; i4 < n4; i4 += blockDim.x) {
-        const float4 v = reinterpret_cast<const float4*>(bin)[i4];
+        const float4 v = PREFETCH && i4 == i40   ? pre0
+                         : PREFETCH && i4 == i41 ? pre1
+                                                 : reinterpret_cast<const float4*>(bin)[i4];
         int x, y, z;
         g.xyz(4 * i4, x, y, z);
         float* d = b0 + g.pad(x, y, z);
