@@ -144,14 +144,21 @@ struct BSmem {
   }
 };
 
-// one sweep over the tile grown by M cells; from_zero: x_in = 0
+// one sweep over the tile grown by M cells; from_zero: x_in = 0.  The block
+// is always kBThreads wide, so every loop below has a compile-time trip
+// count and is unrolled: a thread's loads are all issued before the first
+// of them is used.
 template <int TX, int TY, int H, int M>
-__device__ __forceinline__ void b_sweep(const LevelDev& L, const float* xin, float* xout, const float* sb,
-                                        const float* sw, float omega, bool from_zero) {
+__device__ __forceinline__ void b_sweep(const LevelDev& L, const float* __restrict__ xin, float* __restrict__ xout,
+                                        const float* __restrict__ sb, const float* __restrict__ sw, float omega,
+                                        bool from_zero) {
   using G = BReg<TX, TY, H>;
-  constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
+  constexpr int SX = TX + 2 * M, SY = TY + 2 * M, NI = (SX * SY + kBThreads - 1) / kBThreads;
   const float keep = 1.f - omega;
-  for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    if (i >= SX * SY) break;
     const int li = (i / SX + H - M) * G::RX + i % SX + H - M;
     const float w = sw[li];
     float v;
@@ -166,6 +173,16 @@ __device__ __forceinline__ void b_sweep(const LevelDev& L, const float* xin, flo
   __syncthreads();
 }
 
+// global index of region element i of a tile, or -1 off the grid (an
+// instance has at most 2^31 cells)
+template <int TX, int TY, int H>
+__device__ __forceinline__ int b_gidx(const LevelDev& L, const BReg<TX, TY, H>& g, int i) {
+  using G = BReg<TX, TY, H>;
+  const int gx = g.ox + i % G::RX, gy = g.oy + i / G::RX;
+  if (i >= G::R || gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) return -1;
+  return gy * L.nx + gx;
+}
+
 // down leg of one tile: H sweeps from zero, x, restricted residual
 template <int TX, int TY, int H>
 __device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
@@ -173,21 +190,25 @@ __device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restr
   using G = BReg<TX, TY, H>;
   const G g(tx, ty);
   const BSmem<TX, TY, H> M(S);
+  constexpr int NR = (G::R + kBThreads - 1) / kBThreads;
+  // all of this thread's region loads in flight at once: b is read whatever
+  // the cell byte says and discarded off the fluid
+  float bv[NR];
+  uint8_t mv[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int gi = b_gidx(L, g, threadIdx.x + j * kBThreads);
+    mv[j] = gi < 0 ? 0 : (L.cell ? L.cell[gi] : kFluidBit);
+    bv[j] = gi < 0 ? 0.f : b[gi];
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < G::R; i += blockDim.x) {
-    const int gx = g.ox + i % G::RX, gy = g.oy + i / G::RX;
-    float v = 0.f, w = 0.f;
-    uint8_t m = 0;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-      const size_t gi = (size_t)gy * L.nx + gx;
-      m = L.cell ? L.cell[gi] : kFluidBit;
-      if (m) {
-        v = b[gi];
-        w = __fdividef(omega, b_diag(L, gx, gy, m));
-      }
-    }
-    M.sb[i] = v;
-    M.sw[i] = w;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    if (i >= G::R) break;
+    const uint8_t m = mv[j];
+    M.sb[i] = m ? bv[j] : 0.f;
+    M.sw[i] = m ? __fdividef(omega, b_diag(L, g.ox + i % G::RX, g.oy + i / G::RX, m)) : 0.f;
     M.sm[i] = m;
   }
   __syncthreads();
@@ -201,13 +222,15 @@ __device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restr
     b_sweep<TX, TY, H, 1>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
     cur = M.s0;
   }
-  for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+#pragma unroll
+  for (int i = threadIdx.x; i < TX * TY; i += kBThreads) {
     const int lx = i % TX + H, ly = i / TX + H;
     const int gx = g.ox + lx, gy = g.oy + ly;
     if (gx < L.nx && gy < L.ny) x[(size_t)gy * L.nx + gx] = cur[ly * G::RX + lx];
   }
   const int cnx = L.nx / 2, cny = L.ny / 2;
-  for (int i = threadIdx.x; i < (TX / 2) * (TY / 2); i += blockDim.x) {
+#pragma unroll
+  for (int i = threadIdx.x; i < (TX / 2) * (TY / 2); i += kBThreads) {
     const int cx = i % (TX / 2), cy = i / (TX / 2);
     const int gcx = tx * (TX / 2) + cx, gcy = ty * (TY / 2) + cy;
     if (gcx >= cnx || gcy >= cny) continue;
@@ -237,24 +260,31 @@ __device__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restri
   using G = BReg<TX, TY, H>;
   const G g(tx, ty);
   const BSmem<TX, TY, H> M(S);
-  __syncthreads();
   const int cnx = L.nx / 2;
-  for (int i = threadIdx.x; i < G::R; i += blockDim.x) {
+  constexpr int NR = (G::R + kBThreads - 1) / kBThreads;
+  // all of this thread's region loads in flight at once (values off the
+  // fluid are read and discarded)
+  float xv[NR], ev[NR], bv[NR];
+  uint8_t mv[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    const int gi = b_gidx(L, g, i);
     const int gx = g.ox + i % G::RX, gy = g.oy + i / G::RX;
-    float v = 0.f, bv = 0.f, w = 0.f;
-    uint8_t m = 0;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-      const size_t gi = (size_t)gy * L.nx + gx;
-      m = L.cell ? L.cell[gi] : kFluidBit;
-      if (m) {
-        v = xin[gi] + s * e[(size_t)(gy >> 1) * cnx + (gx >> 1)];
-        bv = b[gi];
-        w = __fdividef(omega, b_diag(L, gx, gy, m));
-      }
-    }
-    M.s0[i] = v;
-    M.sb[i] = bv;
-    M.sw[i] = w;
+    mv[j] = gi < 0 ? 0 : (L.cell ? L.cell[gi] : kFluidBit);
+    xv[j] = gi < 0 ? 0.f : xin[gi];
+    ev[j] = gi < 0 ? 0.f : e[(size_t)(gy >> 1) * cnx + (gx >> 1)];
+    bv[j] = gi < 0 ? 0.f : b[gi];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    if (i >= G::R) break;
+    const uint8_t m = mv[j];
+    M.s0[i] = m ? xv[j] + s * ev[j] : 0.f;
+    M.sb[i] = m ? bv[j] : 0.f;
+    M.sw[i] = m ? __fdividef(omega, b_diag(L, g.ox + i % G::RX, g.oy + i / G::RX, m)) : 0.f;
     M.sm[i] = m;
   }
   __syncthreads();
@@ -272,7 +302,8 @@ __device__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restri
     cur = M.s1;
   }
   float acc = 0.f;
-  for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+#pragma unroll
+  for (int i = threadIdx.x; i < TX * TY; i += kBThreads) {
     const int lx = i % TX + H, ly = i / TX + H;
     const int gx = g.ox + lx, gy = g.oy + ly;
     if (gx < L.nx && gy < L.ny) {
@@ -301,6 +332,93 @@ __device__ __forceinline__ float b_up(const LevelDev& L, int tx, int ty, const f
   if (sweeps <= 1) return b_up_h<TX, TY, 1>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
   if (sweeps == 2) return b_up_h<TX, TY, 2>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
   return b_up_h<TX, TY, 3>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+}
+
+// p = z + beta p_old on a level-0 tile and one cell of halo (staged in
+// shared memory, zero off the fluid and off the grid), then Ap and the
+// thread's share of (p, Ap) on the tile
+template <int TX, int TY>
+__device__ float b_pupdate(const LevelDev& L, int tx, int ty, const float* __restrict__ z,
+                           const float* __restrict__ pold, float* __restrict__ pnew, float* __restrict__ Ap,
+                           float beta, bool first, float* S) {
+  using G = BReg<TX, TY, 1>;
+  const G g(tx, ty);
+  float* sp = S;
+  uint8_t* sm = reinterpret_cast<uint8_t*>(S + G::R);
+  constexpr int NR = (G::R + kBThreads - 1) / kBThreads;
+  float zv[NR], pv[NR];
+  uint8_t mv[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int gi = b_gidx(L, g, threadIdx.x + j * kBThreads);
+    mv[j] = gi < 0 ? 0 : (L.cell ? L.cell[gi] : kFluidBit);
+    zv[j] = gi < 0 ? 0.f : z[gi];
+    pv[j] = (gi < 0 || first) ? 0.f : pold[gi];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    if (i >= G::R) break;
+    sp[i] = mv[j] ? (first ? zv[j] : fmaf(beta, pv[j], zv[j])) : 0.f;
+    sm[i] = mv[j];
+  }
+  __syncthreads();
+  float acc = 0.f;
+#pragma unroll
+  for (int i = threadIdx.x; i < TX * TY; i += kBThreads) {
+    const int lx = i % TX + 1, ly = i / TX + 1;
+    const int gx = g.ox + lx, gy = g.oy + ly;
+    if (gx >= L.nx || gy >= L.ny) continue;
+    const int li = ly * G::RX + lx;
+    const size_t gi = (size_t)gy * L.nx + gx;
+    const uint8_t m = sm[li];
+    float pc = 0.f, ap = 0.f;
+    if (m) {
+      pc = sp[li];
+      float nb = 0.f;
+      nb += L.wx * sp[li - 1];
+      nb += L.wx * sp[li + 1];
+      nb += L.wy * sp[li - G::RX];
+      nb += L.wy * sp[li + G::RX];
+      ap = b_diag(L, gx, gy, m) * pc - nb;
+      acc = fmaf(pc, ap, acc);
+    }
+    pnew[gi] = pc;
+    Ap[gi] = ap;
+  }
+  return acc;
+}
+
+// d += alpha p (d = alpha p on the first iteration), r -= alpha Ap on a
+// level-0 tile; returns the thread's share of ||r||^2
+template <int TX, int TY>
+__device__ float b_xr(const LevelDev& L, int tx, int ty, float* __restrict__ d, const float* __restrict__ p,
+                      const float* __restrict__ Ap, float* __restrict__ r, float alpha, bool first) {
+  constexpr int NC = TX * TY / kBThreads;
+  static_assert(TX * TY % kBThreads == 0, "tile cells a multiple of the block");
+  float dv[NC], pv[NC], av[NC], rv[NC];
+  int gi[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int i = threadIdx.x + j * kBThreads;
+    const int x = tx * TX + i % TX, y = ty * TY + i / TX;
+    gi[j] = (x < L.nx && y < L.ny) ? y * L.nx + x : -1;
+    dv[j] = (gi[j] < 0 || first) ? 0.f : d[gi[j]];
+    pv[j] = gi[j] < 0 ? 0.f : p[gi[j]];
+    av[j] = gi[j] < 0 ? 0.f : Ap[gi[j]];
+    rv[j] = gi[j] < 0 ? 0.f : r[gi[j]];
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    if (gi[j] < 0) continue;
+    d[gi[j]] = first ? alpha * pv[j] : fmaf(alpha, pv[j], dv[j]);
+    const float rn = fmaf(-alpha, av[j], rv[j]);
+    r[gi[j]] = rn;
+    acc = fmaf(rn, rn, acc);
+  }
+  return acc;
 }
 
 // cells of a level-0 tile, one by one: callback(i, x, y)
@@ -340,7 +458,7 @@ __device__ __forceinline__ void count_active(const BatchArgs& A, int slot, bool 
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(kBThreads) k_batched(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(kBThreads, 3) k_batched(const __grid_constant__ BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* S = reinterpret_cast<float*>(smem_raw);
   unsigned epoch = 0;
@@ -503,32 +621,11 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const __grid_constant__ B
         const SolveState& st = A.st[item.x];
         if (st.inner_done) continue;
         const BInst& I = A.inst[item.x];
-        const LevelDev& L = I.lv[0];
         const bool first = st.first || !st.krylov;
         const float beta = first ? 0.f : (float)st.beta;
         const float* pold = (st.it & 1) ? I.p1 : I.p0;
         float* pnew = (st.it & 1) ? I.p0 : I.p1;
-        auto pv = [&](size_t j) { return first ? I.z[j] : fmaf(beta, pold[j], I.z[j]); };
-        float acc = 0.f;
-        b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int cx, int cy) {
-          const uint8_t m = L.cell ? L.cell[i] : kFluidBit;
-          if (!m) {
-            pnew[i] = 0.f;
-            I.Ap[i] = 0.f;
-            return;
-          }
-          const float pc = pv(i);
-          float nb = 0.f;
-          if (cx > 0) nb += L.wx * pv(i - 1);
-          if (cx < L.nx - 1) nb += L.wx * pv(i + 1);
-          if (cy > 0) nb += L.wy * pv(i - L.nx);
-          if (cy < L.ny - 1) nb += L.wy * pv(i + L.nx);
-          const float dg = L.cell ? diag_at<2, true>(L, cx, cy, 0, m) : diag_at<2, false>(L, cx, cy, 0, m);
-          const float ap = dg * pc - nb;
-          pnew[i] = pc;
-          I.Ap[i] = ap;
-          acc = fmaf(pc, ap, acc);
-        });
+        const float acc = b_pupdate<TX, TY>(I.lv[0], item.y, item.z, I.z, pold, pnew, I.Ap, beta, first, S);
         const double t = block_total(acc);
         if (threadIdx.x == 0) A.partials[item.w] = t;
       }
@@ -550,15 +647,8 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const __grid_constant__ B
         if (st.inner_done) continue;
         const BInst& I = A.inst[item.x];
         const float alpha = (float)st.alpha;
-        const bool first = st.first;
         const float* p = (st.it & 1) ? I.p0 : I.p1;
-        float acc = 0.f;
-        b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
-          I.d[i] = first ? alpha * p[i] : fmaf(alpha, p[i], I.d[i]);
-          const float rv = fmaf(-alpha, I.Ap[i], I.r[i]);
-          I.r[i] = rv;
-          acc = fmaf(rv, rv, acc);
-        });
+        const float acc = b_xr<TX, TY>(I.lv[0], item.y, item.z, I.d, p, I.Ap, I.r, alpha, st.first != 0);
         const double t = block_total(acc);
         if (threadIdx.x == 0) A.partials[item.w] = t;
       }
