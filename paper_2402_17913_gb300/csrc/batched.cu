@@ -183,9 +183,11 @@ __device__ __forceinline__ int b_gidx(const LevelDev& L, const BReg<TX, TY, H>& 
   return gy * L.nx + gx;
 }
 
-// down leg of one tile: H sweeps from zero, x, restricted residual
+// down leg of one tile: H sweeps from zero, x, restricted residual (the
+// scalar path, for a level whose width is not a multiple of 4; kept out of
+// line so that its registers do not weigh on the float4 path)
 template <int TX, int TY, int H>
-__device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
+__device__ __noinline__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
                          float* __restrict__ bc, float omega, float* S) {
   using G = BReg<TX, TY, H>;
   const G g(tx, ty);
@@ -254,7 +256,7 @@ __device__ void b_down_h(const LevelDev& L, int tx, int ty, const float* __restr
 // up leg of one tile: x + s P e, H sweeps, output; returns this thread's
 // share of (b, out) when `dot`
 template <int TX, int TY, int H>
-__device__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+__device__ __noinline__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
                         const float* __restrict__ xin, float* __restrict__ xout, const float* __restrict__ e,
                         float omega, float s, bool dot, float* S) {
   using G = BReg<TX, TY, H>;
@@ -315,13 +317,390 @@ __device__ float b_up_h(const LevelDev& L, int tx, int ty, const float* __restri
   return acc;
 }
 
+// ---------------------------------------------------------------------------
+// float4 tile path, for a level whose width is a multiple of 4 (every level-0
+// grid; coarser levels while their width stays a multiple of 4).  The region
+// is the tile plus one group of four cells on each side in x and H rows in y,
+// so a global access is a whole float4 (uchar4 for the cell bytes) that is
+// either all on the grid or all off it, and a sweep updates four cells per
+// thread.  A sweep updates every group of its rows: the outermost groups'
+// outer neighbours lie outside the region (a pad float), which spoils one
+// more cell per sweep from the region's x edges inward -- at most H - 1 <= 2
+// cells after the last sweep, so the tile and the one-cell ring around it
+// that the restriction reads stay exact.
+template <int TX, int TY, int H>
+struct VReg {
+  static constexpr int RX = TX + 8, RY = TY + 2 * H, R = RX * RY, W4 = RX / 4, PAD = 4;
+  static constexpr int A = R + 2 * PAD;  // floats per padded array
+  static constexpr int NG = RY * W4;     // groups in the region
+  int ox, oy;
+  __device__ __forceinline__ VReg(int tx, int ty) : ox(tx * TX - 4), oy(ty * TY - H) {}
+  // global index of group q's first cell, or -1 off the grid
+  __device__ __forceinline__ int gidx(const LevelDev& L, int q) const {
+    const int gx = ox + 4 * (q % W4), gy = oy + q / W4;
+    if (q >= NG || gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) return -1;
+    return gy * L.nx + gx;
+  }
+};
+
+// smem of one float4 tile: b, two iterates, omega / d (padded float arrays),
+// cell bytes
+template <int TX, int TY, int H>
+struct VSmem {
+  float *sb, *s0, *s1, *sw;
+  uint8_t* sm;
+  __device__ __forceinline__ explicit VSmem(float* S) {
+    using G = VReg<TX, TY, H>;
+    sb = S + G::PAD;
+    s0 = sb + G::A;
+    s1 = s0 + G::A;
+    sw = s1 + G::A;
+    sm = reinterpret_cast<uint8_t*>(S + 4 * G::A);
+  }
+};
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float lane(const float4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ uint8_t lane(const uchar4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_lane(float4& v, int k, float a) {
+  if (k == 0) v.x = a;
+  else if (k == 1) v.y = a;
+  else if (k == 2) v.z = a;
+  else v.w = a;
+}
+// cell bytes of a group (all fluid on a level without solid)
+__device__ __forceinline__ uchar4 v_cells(const LevelDev& L, int gi) {
+  if (gi < 0) return make_uchar4(0, 0, 0, 0);
+  if (!L.cell) return make_uchar4(kFluidBit, kFluidBit, kFluidBit, kFluidBit);
+  return *reinterpret_cast<const uchar4*>(L.cell + gi);
+}
+// left / right / down / up neighbours of lane k of the group at li
+struct VNb {
+  float4 c, d, u;
+  float l, r;
+  __device__ __forceinline__ VNb(const float* x, int li, int RX)
+      : c(lds4(x + li)), d(lds4(x + li - RX)), u(lds4(x + li + RX)), l(x[li - 1]), r(x[li + 4]) {}
+  __device__ __forceinline__ float left(int k) const { return k == 0 ? l : lane(c, k - 1); }
+  __device__ __forceinline__ float right(int k) const { return k == 3 ? r : lane(c, k + 1); }
+};
+
+// one sweep over rows H - M .. H + TY + M - 1 of the region (all groups)
+template <int TX, int TY, int H, int M>
+__device__ __forceinline__ void v_sweep(const LevelDev& L, const float* __restrict__ xin, float* __restrict__ xout,
+                                        const float* __restrict__ sb, const float* __restrict__ sw, float omega,
+                                        bool from_zero) {
+  using G = VReg<TX, TY, H>;
+  constexpr int NG = (TY + 2 * M) * G::W4, NI = (NG + kBThreads - 1) / kBThreads;
+  const float keep = 1.f - omega;
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    if (q >= NG) break;
+    const int li = (q / G::W4 + H - M) * G::RX + 4 * (q % G::W4);
+    const float4 w = lds4(sw + li), bb = lds4(sb + li);
+    float4 v;
+    if (from_zero) {
+      v = make_float4(w.x * bb.x, w.y * bb.y, w.z * bb.z, w.w * bb.w);
+    } else {
+      const VNb n(xin, li, G::RX);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float nb = L.wx * (n.left(k) + n.right(k)) + L.wy * (lane(n.d, k) + lane(n.u, k));
+        const float wk = lane(w, k);
+        set_lane(v, k, wk > 0.f ? keep * lane(n.c, k) + wk * (lane(bb, k) + nb) : 0.f);
+      }
+    }
+    sts4(xout + li, v);
+  }
+  __syncthreads();
+}
+
+// b, omega / d and cell bytes of one region group into shared memory
+template <int TX, int TY, int H>
+__device__ __forceinline__ void v_stage(const LevelDev& L, const VReg<TX, TY, H>& g, const VSmem<TX, TY, H>& M,
+                                        int q, uchar4 m4, float4 b4, float omega) {
+  using G = VReg<TX, TY, H>;
+  const int li = (q / G::W4) * G::RX + 4 * (q % G::W4);
+  const int gx = g.ox + 4 * (q % G::W4), gy = g.oy + q / G::W4;
+  float4 sb, sw;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint8_t m = lane(m4, k);
+    set_lane(sb, k, m ? lane(b4, k) : 0.f);
+    set_lane(sw, k, m ? __fdividef(omega, b_diag(L, gx + k, gy, m)) : 0.f);
+  }
+  sts4(M.sb + li, sb);
+  sts4(M.sw + li, sw);
+  *reinterpret_cast<uchar4*>(M.sm + li) = m4;
+}
+
+// down leg of one tile, float4 path
+template <int TX, int TY, int H>
+__device__ void v_down(const LevelDev& L, int tx, int ty, const float* __restrict__ b, float* __restrict__ x,
+                       float* __restrict__ bc, float omega, float* S) {
+  using G = VReg<TX, TY, H>;
+  const G g(tx, ty);
+  const VSmem<TX, TY, H> M(S);
+  constexpr int NR = (G::NG + kBThreads - 1) / kBThreads;
+  float4 bv[NR];
+  uchar4 mv[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int gi = g.gidx(L, threadIdx.x + j * kBThreads);
+    mv[j] = v_cells(L, gi);
+    bv[j] = gi < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(b + gi);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    if (q >= G::NG) break;
+    v_stage(L, g, M, q, mv[j], bv[j], omega);
+  }
+  __syncthreads();
+  v_sweep<TX, TY, H, H>(L, nullptr, M.s0, M.sb, M.sw, omega, true);
+  float* cur = M.s0;
+  if (H >= 2) {
+    v_sweep<TX, TY, H, (H >= 2 ? H - 1 : 1)>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
+  }
+  if (H >= 3) {
+    v_sweep<TX, TY, H, 1>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+    cur = M.s0;
+  }
+  constexpr int T4 = TX / 4;
+#pragma unroll
+  for (int q = threadIdx.x; q < TY * T4; q += kBThreads) {
+    const int row = q / T4, c = q % T4;
+    const int gx = tx * TX + 4 * c, gy = ty * TY + row;
+    if (gx < L.nx && gy < L.ny)
+      *reinterpret_cast<float4*>(x + gy * L.nx + gx) = lds4(cur + (row + H) * G::RX + 4 * (c + 1));
+  }
+  // residual and restriction, two coarse cells (a 4 x 2 block of fine cells)
+  // per thread
+  const int cnx = L.nx / 2, cny = L.ny / 2;
+#pragma unroll
+  for (int q = threadIdx.x; q < (TY / 2) * T4; q += kBThreads) {
+    const int cy = q / T4, c = q % T4;
+    const int gcx = tx * (TX / 2) + 2 * c, gcy = ty * (TY / 2) + cy;
+    if (gcx >= cnx || gcy >= cny) continue;
+    float sum[2] = {0.f, 0.f};
+#pragma unroll
+    for (int ay = 0; ay < 2; ++ay) {
+      const int ly = H + 2 * cy + ay, li = ly * G::RX + 4 * (c + 1);
+      const VNb n(cur, li, G::RX);
+      const float4 b4 = lds4(M.sb + li);
+      const uchar4 m4 = *reinterpret_cast<const uchar4*>(M.sm + li);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint8_t mm = lane(m4, k);
+        if (!mm) continue;
+        const float d = b_diag(L, g.ox + 4 * (c + 1) + k, g.oy + ly, mm);
+        const float nb = L.wx * (n.left(k) + n.right(k)) + L.wy * (lane(n.d, k) + lane(n.u, k));
+        sum[k >> 1] += lane(b4, k) - (d * lane(n.c, k) - nb);
+      }
+    }
+    *reinterpret_cast<float2*>(bc + gcy * cnx + gcx) = make_float2(0.25f * sum[0], 0.25f * sum[1]);
+  }
+}
+
+// up leg of one tile, float4 path: x + s P e, H sweeps, output; returns this
+// thread's share of (b, out) when `dot`
+template <int TX, int TY, int H>
+__device__ float v_up(const LevelDev& L, int tx, int ty, const float* __restrict__ b, const float* __restrict__ xin,
+                      float* __restrict__ xout, const float* __restrict__ e, float omega, float s, bool dot,
+                      float* S) {
+  using G = VReg<TX, TY, H>;
+  const G g(tx, ty);
+  const VSmem<TX, TY, H> M(S);
+  const int cnx = L.nx / 2;
+  constexpr int NR = (G::NG + kBThreads - 1) / kBThreads;
+  float4 xv[NR], bv[NR];
+  float2 ev[NR];
+  uchar4 mv[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    const int gi = g.gidx(L, q);
+    const int gx = g.ox + 4 * (q % G::W4), gy = g.oy + q / G::W4;
+    mv[j] = v_cells(L, gi);
+    xv[j] = gi < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(xin + gi);
+    bv[j] = gi < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(b + gi);
+    ev[j] = gi < 0 ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(e + (gy >> 1) * cnx + (gx >> 1));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    if (q >= G::NG) break;
+    const int li = (q / G::W4) * G::RX + 4 * (q % G::W4);
+    float4 v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      set_lane(v, k, lane(mv[j], k) ? lane(xv[j], k) + s * (k < 2 ? ev[j].x : ev[j].y) : 0.f);
+    sts4(M.s0 + li, v);
+    v_stage(L, g, M, q, mv[j], bv[j], omega);
+  }
+  __syncthreads();
+  float* cur = M.s0;
+  if (H == 1) {
+    v_sweep<TX, TY, H, 0>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
+  } else if (H == 2) {
+    v_sweep<TX, TY, H, 1>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    v_sweep<TX, TY, H, 0>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+  } else {
+    v_sweep<TX, TY, H, (H >= 3 ? 2 : 0)>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    v_sweep<TX, TY, H, 1>(L, M.s1, M.s0, M.sb, M.sw, omega, false);
+    v_sweep<TX, TY, H, 0>(L, M.s0, M.s1, M.sb, M.sw, omega, false);
+    cur = M.s1;
+  }
+  float acc = 0.f;
+  constexpr int T4 = TX / 4;
+#pragma unroll
+  for (int q = threadIdx.x; q < TY * T4; q += kBThreads) {
+    const int row = q / T4, c = q % T4;
+    const int gx = tx * TX + 4 * c, gy = ty * TY + row;
+    if (gx < L.nx && gy < L.ny) {
+      const int li = (row + H) * G::RX + 4 * (c + 1);
+      const float4 v = lds4(cur + li);
+      *reinterpret_cast<float4*>(xout + gy * L.nx + gx) = v;
+      if (dot) {
+        const float4 bb = lds4(M.sb + li);
+        acc = fmaf(bb.x, v.x, acc);
+        acc = fmaf(bb.y, v.y, acc);
+        acc = fmaf(bb.z, v.z, acc);
+        acc = fmaf(bb.w, v.w, acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// p = z + beta p_old on a level-0 tile and its halo (one group in x, one
+// row in y; staged in shared memory, zero off the fluid and off the grid),
+// then Ap and the thread's share of (p, Ap) on the tile
+template <int TX, int TY>
+__device__ float b_pupdate(const LevelDev& L, int tx, int ty, const float* __restrict__ z,
+                           const float* __restrict__ pold, float* __restrict__ pnew, float* __restrict__ Ap,
+                           float beta, bool first, float* S) {
+  using G = VReg<TX, TY, 1>;
+  const G g(tx, ty);
+  float* sp = S + G::PAD;
+  uint8_t* sm = reinterpret_cast<uint8_t*>(S + G::A);
+  constexpr int NR = (G::NG + kBThreads - 1) / kBThreads;
+  float4 zv[NR], pv[NR];
+  uchar4 mv[NR];
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int gi = g.gidx(L, threadIdx.x + j * kBThreads);
+    mv[j] = v_cells(L, gi);
+    zv[j] = gi < 0 ? zero : *reinterpret_cast<const float4*>(z + gi);
+    pv[j] = (gi < 0 || first) ? zero : *reinterpret_cast<const float4*>(pold + gi);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    if (q >= G::NG) break;
+    const int li = (q / G::W4) * G::RX + 4 * (q % G::W4);
+    float4 v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      set_lane(v, k, lane(mv[j], k) ? (first ? lane(zv[j], k) : fmaf(beta, lane(pv[j], k), lane(zv[j], k))) : 0.f);
+    sts4(sp + li, v);
+    *reinterpret_cast<uchar4*>(sm + li) = mv[j];
+  }
+  __syncthreads();
+  float acc = 0.f;
+  constexpr int T4 = TX / 4;
+#pragma unroll
+  for (int q = threadIdx.x; q < TY * T4; q += kBThreads) {
+    const int row = q / T4, c = q % T4;
+    const int gx = tx * TX + 4 * c, gy = ty * TY + row;
+    if (gx >= L.nx || gy >= L.ny) continue;
+    const int li = (row + 1) * G::RX + 4 * (c + 1);
+    const VNb n(sp, li, G::RX);
+    const uchar4 m4 = *reinterpret_cast<const uchar4*>(sm + li);
+    float4 pc = zero, ap = zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint8_t m = lane(m4, k);
+      if (!m) continue;
+      const float p = lane(n.c, k);
+      float nb = 0.f;
+      nb += L.wx * n.left(k);
+      nb += L.wx * n.right(k);
+      nb += L.wy * lane(n.d, k);
+      nb += L.wy * lane(n.u, k);
+      const float a = b_diag(L, gx + k, gy, m) * p - nb;
+      set_lane(pc, k, p);
+      set_lane(ap, k, a);
+      acc = fmaf(p, a, acc);
+    }
+    *reinterpret_cast<float4*>(pnew + gy * L.nx + gx) = pc;
+    *reinterpret_cast<float4*>(Ap + gy * L.nx + gx) = ap;
+  }
+  return acc;
+}
+
+// d += alpha p (d = alpha p on the first iteration), r -= alpha Ap on a
+// level-0 tile, four cells per access; returns the thread's share of ||r||^2
+template <int TX, int TY>
+__device__ float b_xr(const LevelDev& L, int tx, int ty, float* __restrict__ d, const float* __restrict__ p,
+                      const float* __restrict__ Ap, float* __restrict__ r, float alpha, bool first) {
+  constexpr int T4 = TX / 4, NG = TY * T4, NI = (NG + kBThreads - 1) / kBThreads;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 dv[NI], pv[NI], av[NI], rv[NI];
+  int gi[NI];
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    const int x = tx * TX + 4 * (q % T4), y = ty * TY + q / T4;
+    gi[j] = (q < NG && x < L.nx && y < L.ny) ? y * L.nx + x : -1;
+    dv[j] = (gi[j] < 0 || first) ? zero : *reinterpret_cast<const float4*>(d + gi[j]);
+    pv[j] = gi[j] < 0 ? zero : *reinterpret_cast<const float4*>(p + gi[j]);
+    av[j] = gi[j] < 0 ? zero : *reinterpret_cast<const float4*>(Ap + gi[j]);
+    rv[j] = gi[j] < 0 ? zero : *reinterpret_cast<const float4*>(r + gi[j]);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    if (gi[j] < 0) continue;
+    float4 dn, rn;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float pk = lane(pv[j], k);
+      set_lane(dn, k, first ? alpha * pk : fmaf(alpha, pk, lane(dv[j], k)));
+      const float rk = fmaf(-alpha, lane(av[j], k), lane(rv[j], k));
+      set_lane(rn, k, rk);
+      acc = fmaf(rk, rk, acc);
+    }
+    *reinterpret_cast<float4*>(d + gi[j]) = dn;
+    *reinterpret_cast<float4*>(r + gi[j]) = rn;
+  }
+  return acc;
+}
+
 template <int TX, int TY>
 __device__ __forceinline__ void b_down(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
                                        float* __restrict__ x, float* __restrict__ bc, int sweeps, float omega,
                                        float* S) {
-  if (sweeps <= 1) b_down_h<TX, TY, 1>(L, tx, ty, b, x, bc, omega, S);
-  else if (sweeps == 2) b_down_h<TX, TY, 2>(L, tx, ty, b, x, bc, omega, S);
-  else b_down_h<TX, TY, 3>(L, tx, ty, b, x, bc, omega, S);
+  if ((L.nx & 3) == 0) {
+    if (sweeps <= 1) v_down<TX, TY, 1>(L, tx, ty, b, x, bc, omega, S);
+    else if (sweeps == 2) v_down<TX, TY, 2>(L, tx, ty, b, x, bc, omega, S);
+    else v_down<TX, TY, 3>(L, tx, ty, b, x, bc, omega, S);
+  } else {
+    if (sweeps <= 1) b_down_h<TX, TY, 1>(L, tx, ty, b, x, bc, omega, S);
+    else if (sweeps == 2) b_down_h<TX, TY, 2>(L, tx, ty, b, x, bc, omega, S);
+    else b_down_h<TX, TY, 3>(L, tx, ty, b, x, bc, omega, S);
+  }
 }
 
 template <int TX, int TY>
@@ -329,96 +708,14 @@ __device__ __forceinline__ float b_up(const LevelDev& L, int tx, int ty, const f
                                       const float* __restrict__ xin, float* __restrict__ xout,
                                       const float* __restrict__ e, int sweeps, float omega, float s, bool dot,
                                       float* S) {
+  if ((L.nx & 3) == 0) {
+    if (sweeps <= 1) return v_up<TX, TY, 1>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+    if (sweeps == 2) return v_up<TX, TY, 2>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+    return v_up<TX, TY, 3>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
+  }
   if (sweeps <= 1) return b_up_h<TX, TY, 1>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
   if (sweeps == 2) return b_up_h<TX, TY, 2>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
   return b_up_h<TX, TY, 3>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
-}
-
-// p = z + beta p_old on a level-0 tile and one cell of halo (staged in
-// shared memory, zero off the fluid and off the grid), then Ap and the
-// thread's share of (p, Ap) on the tile
-template <int TX, int TY>
-__device__ float b_pupdate(const LevelDev& L, int tx, int ty, const float* __restrict__ z,
-                           const float* __restrict__ pold, float* __restrict__ pnew, float* __restrict__ Ap,
-                           float beta, bool first, float* S) {
-  using G = BReg<TX, TY, 1>;
-  const G g(tx, ty);
-  float* sp = S;
-  uint8_t* sm = reinterpret_cast<uint8_t*>(S + G::R);
-  constexpr int NR = (G::R + kBThreads - 1) / kBThreads;
-  float zv[NR], pv[NR];
-  uint8_t mv[NR];
-#pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    const int gi = b_gidx(L, g, threadIdx.x + j * kBThreads);
-    mv[j] = gi < 0 ? 0 : (L.cell ? L.cell[gi] : kFluidBit);
-    zv[j] = gi < 0 ? 0.f : z[gi];
-    pv[j] = (gi < 0 || first) ? 0.f : pold[gi];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    const int i = threadIdx.x + j * kBThreads;
-    if (i >= G::R) break;
-    sp[i] = mv[j] ? (first ? zv[j] : fmaf(beta, pv[j], zv[j])) : 0.f;
-    sm[i] = mv[j];
-  }
-  __syncthreads();
-  float acc = 0.f;
-#pragma unroll
-  for (int i = threadIdx.x; i < TX * TY; i += kBThreads) {
-    const int lx = i % TX + 1, ly = i / TX + 1;
-    const int gx = g.ox + lx, gy = g.oy + ly;
-    if (gx >= L.nx || gy >= L.ny) continue;
-    const int li = ly * G::RX + lx;
-    const size_t gi = (size_t)gy * L.nx + gx;
-    const uint8_t m = sm[li];
-    float pc = 0.f, ap = 0.f;
-    if (m) {
-      pc = sp[li];
-      float nb = 0.f;
-      nb += L.wx * sp[li - 1];
-      nb += L.wx * sp[li + 1];
-      nb += L.wy * sp[li - G::RX];
-      nb += L.wy * sp[li + G::RX];
-      ap = b_diag(L, gx, gy, m) * pc - nb;
-      acc = fmaf(pc, ap, acc);
-    }
-    pnew[gi] = pc;
-    Ap[gi] = ap;
-  }
-  return acc;
-}
-
-// d += alpha p (d = alpha p on the first iteration), r -= alpha Ap on a
-// level-0 tile; returns the thread's share of ||r||^2
-template <int TX, int TY>
-__device__ float b_xr(const LevelDev& L, int tx, int ty, float* __restrict__ d, const float* __restrict__ p,
-                      const float* __restrict__ Ap, float* __restrict__ r, float alpha, bool first) {
-  constexpr int NC = TX * TY / kBThreads;
-  static_assert(TX * TY % kBThreads == 0, "tile cells a multiple of the block");
-  float dv[NC], pv[NC], av[NC], rv[NC];
-  int gi[NC];
-#pragma unroll
-  for (int j = 0; j < NC; ++j) {
-    const int i = threadIdx.x + j * kBThreads;
-    const int x = tx * TX + i % TX, y = ty * TY + i / TX;
-    gi[j] = (x < L.nx && y < L.ny) ? y * L.nx + x : -1;
-    dv[j] = (gi[j] < 0 || first) ? 0.f : d[gi[j]];
-    pv[j] = gi[j] < 0 ? 0.f : p[gi[j]];
-    av[j] = gi[j] < 0 ? 0.f : Ap[gi[j]];
-    rv[j] = gi[j] < 0 ? 0.f : r[gi[j]];
-  }
-  float acc = 0.f;
-#pragma unroll
-  for (int j = 0; j < NC; ++j) {
-    if (gi[j] < 0) continue;
-    d[gi[j]] = first ? alpha * pv[j] : fmaf(alpha, pv[j], dv[j]);
-    const float rn = fmaf(-alpha, av[j], rv[j]);
-    r[gi[j]] = rn;
-    acc = fmaf(rn, rn, acc);
-  }
-  return acc;
 }
 
 // cells of a level-0 tile, one by one: callback(i, x, y)
@@ -742,9 +1039,13 @@ struct mg_batch_s {
 
 static size_t batched_smem(int tx, int ty, int sweeps, size_t coarse_bytes) {
   const int h = sweeps < 1 ? 1 : (sweeps > 3 ? 3 : sweeps);
-  const size_t R = (size_t)(tx + 2 * h) * (ty + 2 * h);
-  size_t t = 4 * R * 4 + ((R + 15) & ~size_t(15));  // b, two iterates, omega/d; cell bytes
-  return t > coarse_bytes ? t : coarse_bytes;
+  // scalar tile: halo h on every side; float4 tile: one group of 4 in x and
+  // h rows in y, arrays padded by 4 floats at both ends
+  const size_t R = (size_t)(tx + 2 * h) * (ty + 2 * h), Rv = (size_t)(tx + 8) * (ty + 2 * h);
+  const size_t t = 4 * R * 4 + ((R + 15) & ~size_t(15));  // b, two iterates, omega/d; cell bytes
+  const size_t tv = 4 * (Rv + 8) * 4 + ((Rv + 15) & ~size_t(15));
+  size_t m = t > tv ? t : tv;
+  return m > coarse_bytes ? m : coarse_bytes;
 }
 
 static std::string tune_cache_path() {

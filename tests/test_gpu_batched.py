@@ -90,6 +90,20 @@ def test_other_tiles_and_sweep_depths_converge(L, sweeps, tile):
         assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-5
 
 
+@pytest.mark.parametrize("sweeps,tile", [(2, (64, 16)), (3, (32, 16))])
+def test_level_widths_off_the_float4_grid_use_the_scalar_tiles(L, sweeps, tile):
+    """Instances whose level-1 width is not a multiple of 4 (100 -> 50,
+    68 -> 34, 132 -> 66) run that level on the scalar tile path and every
+    other level on the float4 path; both must give the oracle's solution."""
+    shapes, spacings, solids, rhs = make_batch([(100, 68), (68, 100), (64, 64), (132, 100)], seed=13)
+    status, stats, xs = run_batch(L, shapes, spacings, solids, rhs, sweeps=sweeps, tile=tile)
+    assert status == L.MG_OK, [s["status_name"] for s in stats]
+    for (nx, ny), h, solid, b, x, st in zip(shapes, spacings, solids, rhs, xs, stats):
+        assert st["relres"] <= 1e-6, st
+        ref = P.solve_reference((ny, nx), h, BC, b.astype(np.float64), solid, tol=1e-12, s=1.0)
+        assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-5
+
+
 def test_autotuner_picks_a_valid_choice_and_caches_it(L, tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("NPMG_TUNE_CACHE", str(cache))
