@@ -985,7 +985,8 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batched(const __grid_constant_
 struct TileChoice {
   int tx, ty;
 };
-static const TileChoice kTiles[3] = {{64, 16}, {32, 16}, {128, 8}};
+constexpr int kNTiles = 5;
+static const TileChoice kTiles[kNTiles] = {{64, 16}, {32, 16}, {128, 8}, {64, 32}, {128, 16}};
 
 template <int TX, int TY>
 static void* kernel_ptr() {
@@ -994,7 +995,9 @@ static void* kernel_ptr() {
 static void* batched_kernel(int t) {
   if (t == 0) return kernel_ptr<64, 16>();
   if (t == 1) return kernel_ptr<32, 16>();
-  return kernel_ptr<128, 8>();
+  if (t == 2) return kernel_ptr<128, 8>();
+  if (t == 3) return kernel_ptr<64, 32>();
+  return kernel_ptr<128, 16>();
 }
 
 }  // namespace npmg
@@ -1027,10 +1030,10 @@ struct mg_batch_s {
   char* pool;
   size_t pool_bytes;
   int tile, sweeps;              // current choice (autotuned)
-  size_t smem[3][4];             // dynamic shared memory per (tile, sweeps)
-  int grid[3][4];
-  cudaGraphExec_t graph[3][4];
-  GraphKey gkey[3][4];
+  size_t smem[kNTiles][4];             // dynamic shared memory per (tile, sweeps)
+  int grid[kNTiles][4];
+  cudaGraphExec_t graph[kNTiles][4];
+  GraphKey gkey[kNTiles][4];
   int withhold;
   double timeout_s;
   cudaEvent_t ev0, ev1;
@@ -1064,7 +1067,7 @@ static bool tune_lookup(const std::string& key, int* tile, int* sweeps) {
   double ms;
   bool found = false;
   while (fscanf(f, "%511s %d %d %lf", k, &t, &s, &ms) == 4)
-    if (key == k && t >= 0 && t < 3 && s >= 1 && s <= 3) {
+    if (key == k && t >= 0 && t < kNTiles && s >= 1 && s <= 3) {
       *tile = t;
       *sweeps = s;
       found = true;
@@ -1393,7 +1396,7 @@ mg_status mg_create_batched(mg_batch* out, int count, const int64_t* shapes, con
   NPMG_BTRY(cudaEventCreate(&B->ev0));
   NPMG_BTRY(cudaEventCreate(&B->ev1));
   // shared memory, occupancy and grid per (tile, sweeps)
-  for (int t = 0; t < 3; ++t)
+  for (int t = 0; t < kNTiles; ++t)
     for (int sw = 1; sw <= 3; ++sw) {
       B->smem[t][sw] = batched_smem(kTiles[t].tx, kTiles[t].ty, sw, coarse_bytes);
       NPMG_BTRY(cudaFuncSetAttribute(batched_kernel(t), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1546,7 +1549,7 @@ mg_status mg_tune_batched(mg_batch B, const float* const* d_rhs, float* const* d
   if (st != MG_OK) return st;
   int best_t = B->tile, best_s = B->sweeps;
   float best = 1e30f;
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < kNTiles; ++t) {
     for (int sw = 1; sw <= 3; ++sw) {
       B->tile = t;
       B->sweeps = sw;
@@ -1581,10 +1584,10 @@ mg_status mg_batched_config(mg_batch B, int tile_x, int tile_y, int sweeps, doub
     return MG_ERR_INVALID;
   }
   int t = -1;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < kNTiles; ++k)
     if (kTiles[k].tx == tile_x && kTiles[k].ty == tile_y) t = k;
   if (t < 0) {
-    set_error("mg_batched_config: tile must be 64x16, 32x16 or 128x8");
+    set_error("mg_batched_config: tile must be 64x16, 32x16, 128x8, 64x32 or 128x16");
     return MG_ERR_INVALID;
   }
   const bool rebuild = t != B->tile || sweeps != B->sweeps || B->d_items.empty();
@@ -1598,7 +1601,7 @@ mg_status mg_batched_config(mg_batch B, int tile_x, int tile_y, int sweeps, doub
 
 mg_status mg_destroy_batched(mg_batch B) {
   if (!B) return MG_OK;
-  for (int t = 0; t < 3; ++t)
+  for (int t = 0; t < kNTiles; ++t)
     for (int k = 0; k < 4; ++k)
       if (B->graph[t][k]) cudaGraphExecDestroy(B->graph[t][k]);
   for (int4* p : B->d_items) cudaFree(p);
