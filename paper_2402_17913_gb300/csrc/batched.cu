@@ -389,33 +389,39 @@ struct VNb {
   __device__ __forceinline__ float right(int k) const { return k == 3 ? r : lane(c, k + 1); }
 };
 
-// one sweep over rows H - M .. H + TY + M - 1 of the region (all groups)
+// one sweep over rows H - M .. H + TY + M - 1 of the region (all groups).
+// Thread t owns group column t % W4 of rows t / W4, t / W4 + RPP, ... (RPP
+// = rows per pass), so no group index is divided.  Cells off the fluid and
+// off the grid hold x = 0 and omega / d = 0, so the update gives them 0
+// with no test.
 template <int TX, int TY, int H, int M>
 __device__ __forceinline__ void v_sweep(const LevelDev& L, const float* __restrict__ xin, float* __restrict__ xout,
                                         const float* __restrict__ sb, const float* __restrict__ sw, float omega,
                                         bool from_zero) {
   using G = VReg<TX, TY, H>;
-  constexpr int NG = (TY + 2 * M) * G::W4, NI = (NG + kBThreads - 1) / kBThreads;
+  constexpr int RPP = kBThreads / G::W4, NROW = TY + 2 * M, NI = (NROW + RPP - 1) / RPP;
   const float keep = 1.f - omega;
+  const int c4 = threadIdx.x % G::W4, r0 = threadIdx.x / G::W4;
+  if (r0 < RPP) {
 #pragma unroll
-  for (int j = 0; j < NI; ++j) {
-    const int q = threadIdx.x + j * kBThreads;
-    if (q >= NG) break;
-    const int li = (q / G::W4 + H - M) * G::RX + 4 * (q % G::W4);
-    const float4 w = lds4(sw + li), bb = lds4(sb + li);
-    float4 v;
-    if (from_zero) {
-      v = make_float4(w.x * bb.x, w.y * bb.y, w.z * bb.z, w.w * bb.w);
-    } else {
-      const VNb n(xin, li, G::RX);
+    for (int j = 0; j < NI; ++j) {
+      const int row = r0 + j * RPP;
+      if (row >= NROW) break;
+      const int li = (row + H - M) * G::RX + 4 * c4;
+      const float4 w = lds4(sw + li), bb = lds4(sb + li);
+      float4 v;
+      if (from_zero) {
+        v = make_float4(w.x * bb.x, w.y * bb.y, w.z * bb.z, w.w * bb.w);
+      } else {
+        const VNb n(xin, li, G::RX);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float nb = L.wx * (n.left(k) + n.right(k)) + L.wy * (lane(n.d, k) + lane(n.u, k));
-        const float wk = lane(w, k);
-        set_lane(v, k, wk > 0.f ? keep * lane(n.c, k) + wk * (lane(bb, k) + nb) : 0.f);
+        for (int k = 0; k < 4; ++k) {
+          const float nb = L.wx * (n.left(k) + n.right(k)) + L.wy * (lane(n.d, k) + lane(n.u, k));
+          set_lane(v, k, keep * lane(n.c, k) + lane(w, k) * (lane(bb, k) + nb));
+        }
       }
+      sts4(xout + li, v);
     }
-    sts4(xout + li, v);
   }
   __syncthreads();
 }
@@ -755,7 +761,7 @@ __device__ __forceinline__ void count_active(const BatchArgs& A, int slot, bool 
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(kBThreads, 3) k_batched(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(kBThreads, 4) k_batched(const __grid_constant__ BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* S = reinterpret_cast<float*>(smem_raw);
   unsigned epoch = 0;
