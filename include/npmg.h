@@ -363,9 +363,11 @@ mg_status ns_correct(ns_handle ns, float* d_u, float* d_v, float* d_w,
  *   = host array of `count` stats or NULL.  Synchronises the stream.  Returns
  *   MG_OK when every instance converged, else the first non-OK status.
  * mg_tune_batched: the autotuner.  Solves the given batch with every tile
- *   shape (64x16, 32x16, 128x8, 64x32, 128x16) and sweep depth (1, 2, 3 Jacobi sweeps per
- *   level and leg), keeps the fastest time to rel_tol, writes it to the cache
- *   and reports it (host ints, each nullable).  d_x is overwritten.
+ *   shape (64x16, 32x16, 128x8, 64x32, 128x16) and sweep depth (1, 2, 3
+ *   Jacobi sweeps per level and leg), each solve starting from the guesses
+ *   d_x holds on entry (copied once to a temporary device buffer), keeps the
+ *   fastest time to rel_tol, writes it to the cache and reports it (host
+ *   ints, each nullable).  d_x is overwritten with the last solve's result.
  * mg_batched_config: set the tile shape, sweep depth, barrier timeout
  *   (seconds) and a test hook: with withhold_first_arrival != 0 one block
  *   never arrives at the first barrier, so the solve must end in MG_TIMEOUT.

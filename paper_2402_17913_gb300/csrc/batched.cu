@@ -57,6 +57,7 @@ struct BatchArgs {
   SolveState* st;
   int* cur;              // per instance: which xf buffer holds the iterate
   const float* const* rhs;
+  const float* const* xin;   // initial guesses (the outputs, except in the tuner)
   float* const* xout;
   int count;
   const int4* items[kMaxLevels];  // (instance, tile x, tile y, slot) per level
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(kBThreads, 4) k_batched(const __grid_constant_
     const int4 item = it0[w];
     const BInst& I = A.inst[item.x];
     const float* b = A.rhs[item.x];
-    const float* xg = A.xout[item.x];
+    const float* xg = A.xin[item.x];
     float acc = 0.f;
     b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
       const bool fl = I.lv[0].cell ? I.lv[0].cell[i] != 0 : true;
@@ -1027,6 +1028,7 @@ struct mg_batch_s {
   int* d_cur;
   const float** d_rhs;
   float** d_xout;
+  const float** d_xin;           // guesses read by the init phase
   void** h_ptrs;                 // pinned staging of the pointer tables
   std::vector<int4*> d_items;
   int nitems[kMaxLevels];
@@ -1100,6 +1102,7 @@ static mg_status batched_launch(mg_batch_s* B, int tile, int sweeps, double tol,
   A.cur = B->d_cur;
   A.rhs = B->d_rhs;
   A.xout = B->d_xout;
+  A.xin = B->d_xin;
   A.count = B->count;
   for (int k = 0; k < kMaxLevels; ++k) {
     A.items[k] = k < (int)B->d_items.size() ? B->d_items[k] : nullptr;
@@ -1396,6 +1399,7 @@ mg_status mg_create_batched(mg_batch* out, int count, const int64_t* shapes, con
   NPMG_BTRY(cudaMalloc((void**)&B->d_cur, sizeof(int) * count));
   NPMG_BTRY(cudaMalloc((void**)&B->d_rhs, sizeof(void*) * count));
   NPMG_BTRY(cudaMalloc((void**)&B->d_xout, sizeof(void*) * count));
+  NPMG_BTRY(cudaMalloc((void**)&B->d_xin, sizeof(void*) * count));
   NPMG_BTRY(cudaMallocHost((void**)&B->h_st, sizeof(SolveState) * count));
   NPMG_BTRY(cudaMallocHost((void**)&B->h_ptrs, sizeof(void*) * 2 * count));
   NPMG_BTRY(cudaMemsetAsync(B->d_st, 0, sizeof(SolveState) * count, s));
@@ -1488,6 +1492,8 @@ static mg_status set_pointers(mg_batch_s* B, const float* const* d_rhs, float* c
   NPMG_CUDA(cudaMemcpyAsync((void*)B->d_rhs, B->h_ptrs, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
   NPMG_CUDA(
       cudaMemcpyAsync((void*)B->d_xout, B->h_ptrs + B->count, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
+  NPMG_CUDA(
+      cudaMemcpyAsync((void*)B->d_xin, B->h_ptrs + B->count, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
   return MG_OK;
 }
 
@@ -1553,6 +1559,34 @@ mg_status mg_tune_batched(mg_batch B, const float* const* d_rhs, float* const* d
   cudaStream_t s = (cudaStream_t)stream;
   mg_status st = set_pointers(B, d_rhs, d_x, s);
   if (st != MG_OK) return st;
+  // every candidate solves from the caller's guesses: the init phase reads a
+  // copy of them through the guess table while the results go to d_x (the
+  // table points back at d_x when the tuner returns)
+  struct GuessCopy {
+    mg_batch_s* B;
+    cudaStream_t s;
+    float* buf = nullptr;
+    ~GuessCopy() {
+      cudaMemcpyAsync((void*)B->d_xin, B->h_ptrs + B->count, sizeof(void*) * B->count, cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+      if (buf) cudaFree(buf);
+    }
+  } gc{B, s};
+  {
+    size_t total = 0;
+    for (int i = 0; i < B->count; ++i) total += (size_t)B->inst[i].nx * B->inst[i].ny;
+    NPMG_CUDA(cudaMalloc((void**)&gc.buf, total * sizeof(float)));
+    std::vector<const float*> gp(B->count);
+    size_t off = 0;
+    for (int i = 0; i < B->count; ++i) {
+      const size_t n = (size_t)B->inst[i].nx * B->inst[i].ny;
+      gp[i] = gc.buf + off;
+      NPMG_CUDA(cudaMemcpyAsync(gc.buf + off, d_x[i], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      off += n;
+    }
+    NPMG_CUDA(cudaMemcpyAsync((void*)B->d_xin, gp.data(), sizeof(void*) * B->count, cudaMemcpyHostToDevice, s));
+    NPMG_CUDA(cudaStreamSynchronize(s));
+  }
   int best_t = B->tile, best_s = B->sweeps;
   float best = 1e30f;
   for (int t = 0; t < kNTiles; ++t) {
@@ -1617,6 +1651,7 @@ mg_status mg_destroy_batched(mg_batch B) {
   if (B->d_cur) cudaFree(B->d_cur);
   if (B->d_rhs) cudaFree((void*)B->d_rhs);
   if (B->d_xout) cudaFree(B->d_xout);
+  if (B->d_xin) cudaFree((void*)B->d_xin);
   if (B->h_st) cudaFreeHost(B->h_st);
   if (B->h_ptrs) cudaFreeHost(B->h_ptrs);
   if (B->ev0) cudaEventDestroy(B->ev0);

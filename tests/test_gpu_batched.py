@@ -124,6 +124,30 @@ def test_autotuner_picks_a_valid_choice_and_caches_it(L, tmp_path, monkeypatch):
     assert int(line[1]) in (0, 1, 2, 3, 4) and int(line[2]) == sw
 
 
+def test_autotuner_candidates_start_from_the_given_guess(L, tmp_path, monkeypatch):
+    """Every candidate solve of the tuner starts from the guesses d_x holds
+    on entry, so the result it leaves (the last candidate: 128x16 tiles,
+    three sweeps) is bit for bit a solve from the same guesses with that
+    choice."""
+    monkeypatch.setenv("NPMG_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    shapes, spacings, solids, rhs = make_batch(SIDES[:3], seed=21)
+    masks = [None if s is None else torch.from_numpy(s.astype(np.uint8)).cuda() for s in solids]
+    b = L.mg_create_batched(shapes, spacings, BC, masks)
+    try:
+        bt = [torch.from_numpy(r).cuda() for r in rhs]
+        xt = [torch.zeros_like(t) for t in bt]
+        L.mg_tune_batched(b, bt, xt, 1e-6)
+        tuned = [t.cpu().numpy() for t in xt]
+        L.mg_batched_config(b, 128, 16, 3)
+        xt = [torch.zeros_like(t) for t in bt]
+        status, _ = L.mg_solve_batched(b, bt, xt, 1e-6)
+        assert status == L.MG_OK
+        for a, c in zip(tuned, xt):
+            assert np.array_equal(a, c.cpu().numpy())
+    finally:
+        L.mg_destroy_batched(b)
+
+
 def test_withheld_barrier_arrival_times_out(L):
     """One block never arrives at the first grid barrier: the others wait a
     bounded time (0.2 s), the solve returns MG_TIMEOUT, and the next solve on
