@@ -1385,7 +1385,7 @@ mg_status mg_create_batched(mg_batch* out, int count, const int64_t* shapes, con
       I.cfloats = (int)(cb / 4);
       coarse_bytes = cb > coarse_bytes ? cb : coarse_bytes;
       ca.ncoarse = I.lv[Lc].nx * I.lv[Lc].ny;
-      ca.inv = (double*)(P + f.inv);
+      ca.inv = reinterpret_cast<const float*>(P + f.inv);
       ca.image = nullptr;
       ca.pre = o.pre;
       ca.post = o.post;

@@ -220,8 +220,8 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
     (void)CL;
     __syncthreads();
   }
-  // coarsest: x = A^-1 b in float64, one warp per row (sawtooth: the
-  // Jacobi step from zero and the post sweeps)
+  // coarsest: x = A^-1 b (sawtooth: the Jacobi step from zero and the post
+  // sweeps)
   if (saw) {
     const int l = a.nlev - 1;
     const LevelDev& L = a.lv[l];
@@ -243,14 +243,14 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
     }
     if (k) cur |= 1u << l;
   } else {
-    // Thread (row i, chunk q) sums the columns of chunk q (Q chunks of K
-    // columns per row, Q a power of two up to 32 with Q n <= the block's
-    // threads), and the Q partial sums of a row, in adjacent lanes, add up
-    // by shuffles: the dependent chain of float64 operations is K + log2 Q
-    // (GB300 runs float64 at 1/64 of the float32 rate and with a long
-    // latency, so the coarse block waits on that chain; with four warps, or
-    // with one warp per row and a 32-lane tree, the chain was 2-7 times as
-    // long for the 128-cell coarsest level of the 3D flow step).
+    // Q lanes per row (Q a power of two up to 32 with Q n <= the block's
+    // threads): lane q of row i takes columns q, q + Q, q + 2Q, ... (the Q
+    // lanes of a row read adjacent floats), float32 products, and the Q
+    // partial sums add up by shuffles.  The loop is unrolled so that a lane's
+    // loads are in flight together.  (A float64 product with one chunk of
+    // columns per lane took 18 us of the 37 us cycle of the 3D flow step on
+    // its 128-cell coarsest level: float64 runs at 1/64 of the float32 rate
+    // here, and the chunked loads did not coalesce.)
     const CGeo c = G(a.nlev - 1);
     const int n = a.ncoarse;
     float* xc = X(c, 0);
@@ -258,26 +258,26 @@ __device__ void coarse_cycle(const CoarseArgs& a, const T* __restrict__ bin, T* 
     const int nt = (int)(blockDim.x & ~31u);  // whole warps
     int Q = 1;
     while (Q < 32 && 2 * Q * n <= nt) Q *= 2;
-    const int K = (n + Q - 1) / Q, pass = nt / Q;
+    const int pass = nt / Q;
     if ((int)threadIdx.x < nt) {
       const int q = threadIdx.x & (Q - 1), ri = threadIdx.x / Q;
       for (int i0 = 0; i0 < n; i0 += pass) {
         const int i = i0 + ri;
-        double acc = 0.0;
+        float acc = 0.f;
         if (i < n) {
-          // the inverse of the symmetric operator is symmetric: read row i
-          const int j1 = min(n, (q + 1) * K);
-          for (int j = q * K; j < j1; ++j) {
+          const float* __restrict__ row = a.inv + (size_t)i * n;
+#pragma unroll 8
+          for (int j = q; j < n; j += Q) {
             int x, y, z;
             c.xyz(j, x, y, z);
-            acc = fma(a.inv[(size_t)i * n + j], (double)bc[c.pad(x, y, z)], acc);
+            acc = fmaf(__ldg(row + j), bc[c.pad(x, y, z)], acc);
           }
         }
         for (int o = Q >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (i < n && q == 0) {
           int x, y, z;
           c.xyz(i, x, y, z);
-          xc[c.pad(x, y, z)] = (float)acc;
+          xc[c.pad(x, y, z)] = acc;
         }
       }
     }

@@ -30,7 +30,7 @@ struct CoarseArgs {
   LevelDev lv[kMaxLevels];     // lv[0] = first level handled
   int off[kMaxLevels];         // float offset of level l's padded arrays (x, x', b, 1/diag)
   int ncoarse;                 // cells of the coarsest level
-  const double* inv;           // inverse of the coarsest operator, column-major
+  const float* inv;            // inverse of the coarsest operator (float32, symmetric)
   const float* image;          // constant shared-memory image (zero rings, 1/diag), or nullptr
   int pre, post;
   float omega, s;
@@ -191,6 +191,8 @@ cudaError_t launch_ff_to_f64(size_t n, const void* x, double* out, int nblocks, 
 cudaError_t launch_coarsen_solid(int dim, const int64_t fine[3], const uint8_t* sf, uint8_t* sc, cudaStream_t s);
 cudaError_t launch_cell_bytes(int dim, const int64_t n[3], int bcD, const uint8_t* solid, uint8_t* cell,
                               cudaStream_t s);
+// `mat`: 2 n^2 doubles of workspace; on return its first n^2 floats hold the
+// inverse (computed in float64, stored in float32)
 cudaError_t launch_coarse_inverse(int dim, const int64_t n[3], const double w[3], int bcD, const uint8_t* cell,
                                   double* mat, cudaStream_t s);
 

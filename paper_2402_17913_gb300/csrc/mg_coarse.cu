@@ -26,8 +26,9 @@ static int grid_1d(size_t n, int cap) {
 // ring is the zero padding of Sec. 2.1), the inverse diagonal is computed
 // once per launch (0 marks a non-fluid cell), and a sweep is
 // x <- (1 - omega) x + omega D^-1 (b + sum_a w_a (x_- + x_+)).  The
-// coarsest level is solved exactly: its operator is inverted once at create
-// (float64 Gauss-Jordan) and applied here in float64, one warp per row.
+// coarsest level is solved exactly up to float32 rounding: its operator is
+// inverted once at create (float64 Gauss-Jordan), stored in float32 and
+// applied here as a float32 product, a few lanes per row.
 // The level table stays in kernel-parameter space (__grid_constant__), so
 // indexing it by level needs no local copy.
 template <typename T>
@@ -227,11 +228,12 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ A) {
   }
 }
 
-// Transpose to column-major for coalesced reads in k_coarse.
-__global__ void k_transpose(int n, const double* __restrict__ A, double* __restrict__ At) {
+// The float32 copy the coarse kernels read (column-major; the inverse of the
+// symmetric operator is symmetric, so a row is read as a column).
+__global__ void k_store_inverse(int n, const double* __restrict__ A, float* __restrict__ At) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / n), j = (int)(t % n);
-    At[(size_t)j * n + i] = A[t];
+    At[(size_t)j * n + i] = (float)A[t];
   }
 }
 
@@ -246,7 +248,7 @@ cudaError_t launch_coarse_inverse(int dim, const int64_t nn[3], const double w[3
   k_gauss_jordan<<<1, 1024, 2 * n * sizeof(double), s>>>(n, work);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_transpose<<<grid_1d((size_t)n * n, 1024), 256, 0, s>>>(n, work, mat);
+  k_store_inverse<<<grid_1d((size_t)n * n, 1024), 256, 0, s>>>(n, work, reinterpret_cast<float*>(mat));
   return cudaGetLastError();
 }
 

@@ -761,7 +761,7 @@ mg_status mg_create(mg_handle* out, int dim, const int64_t shape[3], const doubl
     for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = h->lv[kc + l];
     h->ca_smem = coarse_layout(ca.off, ca.lv, ca.nlev, dim);
     ca.ncoarse = h->ncoarse;
-    ca.inv = h->inv;
+    ca.inv = reinterpret_cast<const float*>(h->inv);
     ca.image = nullptr;
     ca.pre = o.cycle == MG_CYCLE_SAWTOOTH ? -1 : o.pre;  // -1: the sawtooth recursion
     ca.post = o.post;

@@ -272,7 +272,7 @@ extern "C" mg_status mg_vcycle_noalloc(int dim, const int64_t shape[3], const do
   for (int l = 0; l < ca.nlev; ++l) ca.lv[l] = lv[kc + l];
   const size_t moff = coarse_layout(ca.off, ca.lv, ca.nlev, dim);
   ca.ncoarse = ncoarse;
-  ca.inv = inv;
+  ca.inv = reinterpret_cast<const float*>(inv);
   ca.pre = o.pre;
   ca.post = o.post;
   ca.omega = (float)o.omega;
