@@ -725,6 +725,131 @@ __device__ __forceinline__ float b_up(const LevelDev& L, int tx, int ty, const f
   return b_up_h<TX, TY, 3>(L, tx, ty, b, xin, xout, e, omega, s, dot, S);
 }
 
+// ---------------------------------------------------------------------------
+// refinement phases on float4 groups of a level-0 tile (the caller's arrays
+// 16-byte aligned; else the cell-by-cell loops below)
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// init: x = (guess, 0) on fluid cells (0 elsewhere); returns the thread's
+// share of ||b||^2
+template <int TX, int TY>
+__device__ float v_init(const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+                        const float* __restrict__ xg, float2* __restrict__ xf) {
+  constexpr int T4 = TX / 4, NG = TY * T4, NI = (NG + kBThreads - 1) / kBThreads;
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    const int x = tx * TX + 4 * (q % T4), y = ty * TY + q / T4;
+    if (q >= NG || x >= L.nx || y >= L.ny) continue;
+    const int gi = y * L.nx + x;
+    const uchar4 m = v_cells(L, gi);
+    const float4 g = *reinterpret_cast<const float4*>(xg + gi), bb = *reinterpret_cast<const float4*>(b + gi);
+    float4* o = reinterpret_cast<float4*>(xf + gi);
+    o[0] = make_float4(m.x ? g.x : 0.f, 0.f, m.y ? g.y : 0.f, 0.f);
+    o[1] = make_float4(m.z ? g.z : 0.f, 0.f, m.w ? g.w : 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (lane(m, k)) acc = fmaf(lane(bb, k), lane(bb, k), acc);
+  }
+  return acc;
+}
+
+// result: the float32 output hi + lo (0 for a zero right-hand side)
+template <int TX, int TY>
+__device__ void v_result(const LevelDev& L, int tx, int ty, const float2* __restrict__ xf, float* __restrict__ out,
+                         bool zero) {
+  constexpr int T4 = TX / 4, NG = TY * T4, NI = (NG + kBThreads - 1) / kBThreads;
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    const int q = threadIdx.x + j * kBThreads;
+    const int x = tx * TX + 4 * (q % T4), y = ty * TY + q / T4;
+    if (q >= NG || x >= L.nx || y >= L.ny) continue;
+    const int gi = y * L.nx + x;
+    const float4 a = reinterpret_cast<const float4*>(xf + gi)[0], c = reinterpret_cast<const float4*>(xf + gi)[1];
+    *reinterpret_cast<float4*>(out + gi) =
+        zero ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(a.x + a.y, a.z + a.w, c.x + c.y, c.z + c.w);
+  }
+}
+
+// refinement residual of the float-float iterate after x += sigma_old d
+// (when `update`): the iterate of the tile and a one-cell ring is staged in
+// shared memory as (hi, lo) planes, then r = c b - A' x per fluid cell in
+// float-float, scaled by 1 / sigma_new into the CG right-hand side; returns
+// the thread's share of ||r||^2
+template <int TX, int TY>
+__device__ float v_resid(const BInst& I, const LevelDev& L, int tx, int ty, const float* __restrict__ b,
+                         const float2* __restrict__ xin, float2* __restrict__ xo, bool update, float sig_old,
+                         float inv_sig_new, float* S) {
+  using G = VReg<TX, TY, 1>;
+  const G g(tx, ty);
+  float* sh = S + G::PAD;
+  float* sl = sh + G::A;
+  uint8_t* sm = reinterpret_cast<uint8_t*>(S + 2 * G::A);
+  auto xv = [&](float hi, float lo, float dd) -> ff {
+    if (!update) return {hi, lo};
+    const ff s2 = two_sum(hi, sig_old * dd);
+    return quick_two_sum(s2.hi, s2.lo + lo);
+  };
+  __syncthreads();
+  for (int q = threadIdx.x; q < G::NG; q += kBThreads) {
+    const int gi = g.gidx(L, q);
+    const int li = (q / G::W4) * G::RX + 4 * (q % G::W4);
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+    uchar4 m = make_uchar4(0, 0, 0, 0);
+    if (gi >= 0) {
+      m = v_cells(L, gi);
+      const float4 a = reinterpret_cast<const float4*>(xin + gi)[0], c = reinterpret_cast<const float4*>(xin + gi)[1];
+      const float4 dd = update ? *reinterpret_cast<const float4*>(I.d + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const ff v0 = xv(a.x, a.y, dd.x), v1 = xv(a.z, a.w, dd.y), v2 = xv(c.x, c.y, dd.z), v3 = xv(c.z, c.w, dd.w);
+      h = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
+      l = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+    }
+    sts4(sh + li, h);
+    sts4(sl + li, l);
+    *reinterpret_cast<uchar4*>(sm + li) = m;
+  }
+  __syncthreads();
+  float acc = 0.f;
+  constexpr int T4 = TX / 4;
+  for (int q = threadIdx.x; q < TY * T4; q += kBThreads) {
+    const int row = q / T4, c4 = q % T4;
+    const int gx = tx * TX + 4 * c4, gy = ty * TY + row;
+    if (gx >= L.nx || gy >= L.ny) continue;
+    const int gi = gy * L.nx + gx;
+    const int li = (row + 1) * G::RX + 4 * (c4 + 1);
+    const VNb H(sh, li, G::RX), Lo(sl, li, G::RX);
+    const uchar4 m4 = *reinterpret_cast<const uchar4*>(sm + li);
+    const float4 bb = *reinterpret_cast<const float4*>(b + gi);
+    float4 rv = make_float4(0.f, 0.f, 0.f, 0.f), oh = rv, ol = rv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint8_t m = lane(m4, k);
+      if (!m) continue;
+      const int kx = L.cell ? (m & 3) : axis_count(gx + k, L.nx, L.bcD, 0);
+      const int ky = L.cell ? ((m >> 2) & 3) : axis_count(gy, L.ny, L.bcD, 2);
+      const ff xc = {lane(H.c, k), lane(Lo.c, k)};
+      const ff xl = {H.left(k), Lo.left(k)}, xr = {H.right(k), Lo.right(k)};
+      const ff xd = {lane(H.d, k), lane(Lo.d, k)}, xu = {lane(H.u, k), lane(Lo.u, k)};
+      ff ax = ff_mul(ff_add(ff_mul(xc, ff{(float)kx, 0.f}), ff_neg(ff_add(xl, xr))), I.wff[0]);
+      ax = ff_add(ax, ff_mul(ff_add(ff_mul(xc, ff{(float)ky, 0.f}), ff_neg(ff_add(xd, xu))), I.wff[1]));
+      const ff r = ff_add(ff_mul(ff{lane(bb, k), 0.f}, I.cff), ff_neg(ax));
+      const float rs = r.hi + r.lo;
+      set_lane(rv, k, rs * inv_sig_new);
+      acc = fmaf(rs, rs, acc);
+      set_lane(oh, k, xc.hi);
+      set_lane(ol, k, xc.lo);
+    }
+    *reinterpret_cast<float4*>(I.r + gi) = rv;
+    if (update) {
+      float4* o = reinterpret_cast<float4*>(xo + gi);
+      o[0] = make_float4(oh.x, ol.x, oh.y, ol.y);
+      o[1] = make_float4(oh.z, ol.z, oh.w, ol.w);
+    }
+  }
+  return acc;
+}
+
 // cells of a level-0 tile, one by one: callback(i, x, y)
 template <int TX, int TY, typename F>
 __device__ __forceinline__ void b_cells(const BInst& I, int tx, int ty, F&& f) {
@@ -777,11 +902,15 @@ __global__ void __launch_bounds__(kBThreads, 4) k_batched(const __grid_constant_
     const float* b = A.rhs[item.x];
     const float* xg = A.xin[item.x];
     float acc = 0.f;
-    b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
-      const bool fl = I.lv[0].cell ? I.lv[0].cell[i] != 0 : true;
-      I.xf0[i] = make_float2(fl ? xg[i] : 0.f, 0.f);
-      if (fl) acc = fmaf(b[i], b[i], acc);
-    });
+    if (aligned16(b) && aligned16(xg)) {
+      acc = v_init<TX, TY>(I.lv[0], item.y, item.z, b, xg, I.xf0);
+    } else {
+      b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
+        const bool fl = I.lv[0].cell ? I.lv[0].cell[i] != 0 : true;
+        I.xf0[i] = make_float2(fl ? xg[i] : 0.f, 0.f);
+        if (fl) acc = fmaf(b[i], b[i], acc);
+      });
+    }
     const double t = block_total(acc);
     if (threadIdx.x == 0) A.partials[item.w] = t;
   }
@@ -822,7 +951,8 @@ __global__ void __launch_bounds__(kBThreads, 4) k_batched(const __grid_constant_
         return quick_two_sum(s2.hi, s2.lo + q.y);
       };
       float acc = 0.f;
-      b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int cx, int cy) {
+      if (aligned16(b)) acc = v_resid<TX, TY>(I, L, item.y, item.z, b, xin, xo, update, sig_old, inv_sig_new, S);
+      else b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int cx, int cy) {
         const uint8_t m = L.cell ? L.cell[i] : kFluidBit;
         if (!m) {
           if (update) xo[i] = make_float2(0.f, 0.f);
@@ -980,10 +1110,14 @@ __global__ void __launch_bounds__(kBThreads, 4) k_batched(const __grid_constant_
     const float2* xf = A.cur[item.x] ? I.xf1 : I.xf0;
     float* out = A.xout[item.x];
     const bool zero = st.bnorm2 == 0.0;
-    b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
-      const float2 v = xf[i];
-      out[i] = zero ? 0.f : v.x + v.y;
-    });
+    if (aligned16(out)) {
+      v_result<TX, TY>(I.lv[0], item.y, item.z, xf, out, zero);
+    } else {
+      b_cells<TX, TY>(I, item.y, item.z, [&](size_t i, int, int) {
+        const float2 v = xf[i];
+        out[i] = zero ? 0.f : v.x + v.y;
+      });
+    }
   }
 }
 

@@ -148,6 +148,30 @@ def test_autotuner_candidates_start_from_the_given_guess(L, tmp_path, monkeypatc
         L.mg_destroy_batched(b)
 
 
+def test_caller_arrays_off_16_byte_boundaries(L):
+    """Right-hand sides, guesses and outputs that start 4 bytes past a
+    16-byte boundary take the cell-by-cell refinement loops instead of the
+    float4 ones, with the same solution."""
+    shapes, spacings, solids, rhs = make_batch(SIDES[:3], seed=17)
+    masks = [None if s is None else torch.from_numpy(s.astype(np.uint8)).cuda() for s in solids]
+    b = L.mg_create_batched(shapes, spacings, BC, masks)
+    try:
+        def view(a):
+            buf = torch.zeros(a.size + 1, dtype=torch.float32, device="cuda")
+            buf[1:] = torch.from_numpy(a.ravel()).cuda()
+            return buf[1:].view(a.shape)
+        bt = [view(r) for r in rhs]
+        xt = [view(np.zeros_like(r)) for r in rhs]
+        assert all(t.data_ptr() % 16 == 4 for t in bt + xt)
+        status, stats = L.mg_solve_batched(b, bt, xt, 1e-6)
+        assert status == L.MG_OK, [s_["status_name"] for s_ in stats]
+        for (nx, ny), h, solid, r, x in zip(shapes, spacings, solids, rhs, xt):
+            ref = P.solve_reference((ny, nx), h, BC, r.astype(np.float64), solid, tol=1e-12, s=1.0)
+            assert np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
+    finally:
+        L.mg_destroy_batched(b)
+
+
 def test_withheld_barrier_arrival_times_out(L):
     """One block never arrives at the first grid barrier: the others wait a
     bounded time (0.2 s), the solve returns MG_TIMEOUT, and the next solve on
